@@ -1,0 +1,333 @@
+"""Pins for the FP64 oracle against things other than itself: brute force on
+tiny inputs, closed forms, invariants and special cases that reduce to a
+textbook result.  Each test names the part of the method it guards."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.optimize as sopt
+
+import synth
+from oracle import pw_oracle as O
+
+TWO_PI = 2 * math.pi
+
+
+def _cell(species="Si", n=1, ecut=10.0, seed=0, **kw):
+    ci = synth.cell_inputs(species, n, seed)
+    return O.make_cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], ecut, **kw), ci
+
+
+# ---------------------------------------------------------------- inputs ----
+
+def test_splitmix64_published_values():
+    # first outputs of SplitMix64 seeded with 0 (Steele, Lea, Flood 2014)
+    z = synth.splitmix64(0, np.arange(3))
+    assert [int(v) for v in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_synth_ranges():
+    ci = synth.cell_inputs("Si", 2, 7)
+    assert ci["tau"].shape == (64, 3)
+    assert np.all((ci["depth"] >= -1.1) & (ci["depth"] < -0.9))
+    assert np.all((ci["dkb"] >= 0.5) & (ci["dkb"] < 1.5))
+    # the 8 basis atoms of the diamond cell: nearest-neighbour distance sqrt(3)/4 a
+    L, tau = synth.diamond_supercell(synth.SI_A, 1)
+    d = np.linalg.norm(tau[:, None] - tau[None], axis=2) + 1e9 * np.eye(8)
+    assert abs(d.min() - math.sqrt(3) / 4 * synth.SI_A) < 1e-12
+
+
+# ---------------------------------------------------------- sphere, grid ----
+
+def _brute_sphere(ecut, L):
+    R = int(math.sqrt(2 * ecut) * L / TWO_PI) + 2
+    out = []
+    for mx in range(-R, R + 1):
+        for my in range(-R, R + 1):
+            for mz in range(-R, R + 1):
+                g2 = (TWO_PI / L) ** 2 * (mx * mx + my * my + mz * mz)
+                if 0.5 * g2 <= ecut:
+                    out.append((mx, my, mz))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("species,ecut", [("Si", 10.0), ("C", 8.0), ("Si", 4.0)])
+def test_sphere_brute_force(species, ecut):
+    L = {"Si": synth.SI_A, "C": synth.C_A}[species]
+    m = O.sphere(ecut, [L] * 3)
+    ref = _brute_sphere(ecut, L)          # loops already run in lexicographic order
+    assert m.shape == ref.shape and np.array_equal(m, ref)
+
+
+def test_sphere_counts_and_volume():
+    # Npw of the three workload cells, and the lattice-point count of a ball
+    for n, ecut, want in [(1, 10.0, 1647), (4, 10.0, 104415), (6, 8.0, 251967)]:
+        L = n * synth.SI_A
+        npw = O.sphere(ecut, [L] * 3).shape[0]
+        assert npw == want
+        R = math.sqrt(2 * ecut) * L / TWO_PI
+        assert abs(npw / (4 / 3 * math.pi * R ** 3) - 1) < 0.05
+
+
+def test_grid_rule():
+    smooth = sorted(2 ** a * 3 ** b for a in range(10) for b in range(7))
+    for ecut, L in [(10.0, 10.26), (10.0, 41.04), (8.0, 61.56), (8.0, 6.74), (12.0, 30.78)]:
+        target = 1.5 * math.sqrt(2 * ecut) * L / math.pi
+        assert O.grid_size_1d(ecut, L) == next(s for s in smooth if s >= target)
+    assert [O.grid_size_1d(10, 10.26), O.grid_size_1d(10, 41.04), O.grid_size_1d(8, 61.56)] == [24, 96, 128]
+    # the grid must hold the sphere without aliasing: 2 mmax < N
+    for ecut, L in [(10.0, 10.26), (8.0, 6.74)]:
+        m = O.sphere(ecut, [L] * 3)
+        assert 2 * np.abs(m).max() < O.grid_size_1d(ecut, L)
+
+
+# ------------------------------------------------------------------ FFT ----
+
+def _tiny_cell(Ns=(6, 9, 8), Ls=(5.0, 7.0, 6.0), ecut=3.0, V=None):
+    tau = np.array([[0.3, 1.1, 2.0], [2.9, 4.0, 0.7]])
+    depth = np.array([-1.0, -0.95])
+    dkb = np.array([[0.7, 0.9, 1.1, 1.3], [0.6, 0.8, 1.0, 1.2]])
+    return O.make_cell(np.array(Ls), tau, depth, dkb, ecut, grid=Ns, V=V)
+
+
+def test_fft_convention_brute_force():
+    cell = _tiny_cell()
+    rng = np.random.default_rng(1)
+    c = rng.standard_normal((cell.npw, 2)) + 1j * rng.standard_normal((cell.npw, 2))
+    psi = O.to_real_space(cell, c)
+    G = TWO_PI * cell.m / cell.Ls
+    for j in [(0, 0, 0), (1, 2, 3), (5, 8, 7), (3, 0, 4)]:
+        r = cell.Ls * np.array(j) / np.array(cell.Ns)
+        direct = (np.exp(1j * (G @ r))[:, None] * c).sum(axis=0)
+        assert np.allclose(psi[j], direct, atol=1e-12)
+    # forward: f_G = N^-3 sum_j f(r_j) exp(-i G.r_j)
+    f = rng.standard_normal(cell.Ns) + 0j
+    fg = O.to_sphere(cell, f[..., None])[:, 0]
+    pts = np.array(list(itertools.product(*[range(n) for n in cell.Ns])))
+    rj = pts * (cell.Ls / np.array(cell.Ns))
+    for g in [0, 5, cell.npw - 1]:
+        direct = (f[tuple(pts.T)] * np.exp(-1j * (rj @ G[g]))).sum() / np.prod(cell.Ns)
+        assert abs(fg[g] - direct) < 1e-12
+
+
+def test_parseval_and_roundtrip():
+    cell, _ = _cell("Si", 1, 10.0)
+    rng = np.random.default_rng(2)
+    c = rng.standard_normal((cell.npw, 3)) + 1j * rng.standard_normal((cell.npw, 3))
+    psi = O.to_real_space(cell, c)
+    n3 = np.prod(cell.Ns)
+    assert np.allclose((np.abs(psi) ** 2).sum(axis=(0, 1, 2)), n3 * (np.abs(c) ** 2).sum(axis=0), rtol=1e-13)
+    assert np.abs(O.to_sphere(cell, psi) - c).max() < 1e-13
+
+
+# ------------------------------------------------------ local potential ----
+
+def test_vloc_direct_image_sum():
+    Ls = np.array([5.0, 6.0, 5.5])
+    Ns = (8, 6, 5)
+    tau = np.array([[0.3, 1.1, 2.0], [4.6, 5.9, 0.1]])
+    depth = np.array([-1.0, -0.9])
+    V = O.vloc_grid(Ls, Ns, tau, depth, 1.2)
+    for j in [(0, 0, 0), (7, 5, 4), (3, 2, 1)]:
+        r = Ls * np.array(j) / np.array(Ns)
+        tot = 0.0
+        for a in range(2):
+            for R in itertools.product(range(-4, 5), repeat=3):
+                d = r - tau[a] - Ls * np.array(R)
+                tot += depth[a] * math.exp(-(d @ d) / (2 * 1.2 ** 2))
+        assert abs(V[j] - tot) < 1e-13
+
+
+def test_vloc_cell_average():
+    # mean of a periodised Gaussian over the cell = its integral / Omega
+    cell, ci = _cell("Si", 1, 10.0)
+    omega = np.prod(cell.Ls)
+    want = ci["depth"].sum() * (2 * math.pi * ci["sigma"] ** 2) ** 1.5 / omega
+    assert abs(cell.V.mean() - want) < 1e-12 * abs(want)
+
+
+def test_vloc_fourier_brute_force():
+    cell = _tiny_cell()
+    Vt = O.vloc_fourier(cell.V)
+    pts = np.array(list(itertools.product(*[range(n) for n in cell.Ns])))
+    for k in [(0, 0, 0), (1, 2, 3), (5, 1, 7)]:
+        ph = np.exp(-2j * math.pi * (pts @ (np.array(k) / np.array(cell.Ns))))
+        assert abs(Vt[k] - (cell.V[tuple(pts.T)] * ph).sum() / len(pts)) < 1e-14
+
+
+# ----------------------------------------------------------- projectors ----
+
+def test_projector_normalisation():
+    # unit real-space norm: sum_G |beta(G)|^2 -> 1 when the sphere holds the
+    # whole Gaussian (its periodic self-overlap is exp(-L^2/(4 rp^2)) ~ 1e-8)
+    L = synth.SI_A
+    m = O.sphere(60.0, [L] * 3)
+    tau = np.array([[1.0, 2.0, 3.0]])
+    beta = O.projectors(m, [L] * 3, tau, 1.2)
+    norms = (np.abs(beta) ** 2).sum(axis=0)
+    assert np.allclose(norms, 1.0, atol=1e-6)
+    ov = beta.conj().T @ beta
+    assert np.abs(ov - np.diag(np.diag(ov))).max() < 1e-10   # s, px, py, pz orthogonal
+
+
+# -------------------------------------------------------- whole operator ----
+
+def test_free_electron_shells():
+    # V = 0, D = 0: eigenvalues are 1/2|G|^2; Si cell unit (2 pi / a)^2 / 2
+    cell, _ = _cell("Si", 1, 10.0)
+    cell.V = np.zeros(cell.Ns)
+    cell.D = np.zeros_like(cell.D)
+    w = np.linalg.eigvalsh(O.dense_H(cell))
+    unit = 0.5 * (TWO_PI / synth.SI_A) ** 2
+    assert abs(unit - 0.187514) < 1e-6
+    shells = [(0, 1), (1, 6), (2, 12), (3, 8), (4, 6), (5, 24), (6, 24), (8, 12)]
+    want = np.concatenate([[s * unit] * g for s, g in shells])
+    assert np.abs(w[:len(want)] - want).max() < 1e-12
+    # LOBPCG reaches the same 19 lowest (the block ends on a shell boundary)
+    X0 = synth.draw_x0(0, 8, cell.npw, 19)
+    lam, X, it, rn = O.eigsolve(cell, X0, tol=1e-9, maxit=200)
+    assert np.abs(lam - want[:19]).max() < 1e-12
+
+
+def test_constant_potential_shift():
+    cell, _ = _cell("C", 1, 8.0)
+    w0 = np.linalg.eigvalsh(O.dense_H(cell))
+    cell.V = cell.V + 0.37
+    w1 = np.linalg.eigvalsh(O.dense_H(cell))
+    assert np.abs(w1 - w0 - 0.37).max() < 1e-12
+
+
+def test_rank_one_secular_equation():
+    # V = 0, one atom with only an s projector: 1 + D sum |b_G|^2 / (t_G - e) = 0
+    L = synth.C_A
+    ecut = 8.0
+    tau = np.array([[0.4, 1.3, 2.2]])
+    dkb = np.array([[0.8, 0.0, 0.0, 0.0]])
+    cell = O.make_cell(L, tau, np.array([0.0]), dkb, ecut)
+    cell.V = np.zeros(cell.Ns)
+    w = np.linalg.eigvalsh(O.dense_H(cell))
+    t = cell.kin
+    b2 = np.abs(cell.beta[:, 0]) ** 2
+    shells = np.unique(np.round(t, 10))
+    wt = np.array([b2[np.abs(t - s) < 1e-9].sum() for s in shells])
+    deg = np.array([(np.abs(t - s) < 1e-9).sum() for s in shells])
+    D = 0.8
+    f = lambda e: 1 + D * np.sum(wt / (shells - e))
+    roots = [sopt.brentq(f, shells[i] + 1e-13, shells[i + 1] - 1e-13, xtol=1e-15)
+             for i in range(len(shells) - 1)]
+    hi = shells[-1] + D * wt.sum() + 1.0
+    roots.append(sopt.brentq(f, shells[-1] + 1e-13, hi, xtol=1e-15))
+    # each shell keeps deg-1 copies of its energy; the secular roots are the rest
+    want = np.sort(np.concatenate([np.repeat(shells, deg - 1), roots]))
+    assert np.abs(w - want).max() < 1e-10
+
+
+def test_hermiticity_and_dense_agreement():
+    cell, _ = _cell("Si", 1, 10.0)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((cell.npw, 2)) + 1j * rng.standard_normal((cell.npw, 2))
+    Hx = O.apply_H(cell, x)
+    a = np.vdot(x[:, 0], Hx[:, 1])
+    b = np.vdot(x[:, 1], Hx[:, 0])
+    assert abs(a - np.conj(b)) < 1e-13 * abs(a)
+    H = O.dense_H(cell)
+    assert np.abs(H - H.conj().T).max() < 1e-15
+    assert np.linalg.norm(H @ x - Hx) < 1e-13 * np.linalg.norm(Hx)
+
+
+def test_grid_shift_and_permutation_invariance():
+    ci = synth.cell_inputs("C", 1, 4)
+    ecut = 8.0
+    base = O.make_cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], ecut)
+    w0 = np.linalg.eigvalsh(O.dense_H(base))
+    N = np.array(base.Ns)
+    shift = ci["L"] * np.array([3, -5, 7]) / N
+    moved = O.make_cell(ci["L"], ci["tau"] + shift, ci["depth"], ci["dkb"], ecut)
+    assert np.abs(np.linalg.eigvalsh(O.dense_H(moved)) - w0).max() < 1e-12
+    p = np.random.default_rng(5).permutation(8)
+    perm = O.make_cell(ci["L"], ci["tau"][p], ci["depth"][p], ci["dkb"][p], ecut)
+    assert np.abs(np.linalg.eigvalsh(O.dense_H(perm)) - w0).max() < 1e-12
+
+
+def test_supercell_folding():
+    # with depths repeating every cell and grid n*N_cell, an eigenvector of the
+    # 8-atom cell, placed on G' = G_cell (c'_{n m} = c_m), is an eigenvector of
+    # the n^3-cell Hamiltonian with the same eigenvalue
+    ecut = 10.0
+    small = synth.periodic_depths("Si", 1, 3)
+    big = synth.periodic_depths("Si", 2, 3)
+    cs = O.make_cell(small["L"], small["tau"], small["depth"], small["dkb"], ecut)
+    cb = O.make_cell(big["L"], big["tau"], big["depth"], big["dkb"], ecut)
+    assert cb.Ns == tuple(2 * n for n in cs.Ns)
+    w, v = O.dense_eigs(cs, 6)
+    # normalisation: beta scales with Omega^-1/2; the nonlocal term
+    # sum_a beta beta^H has 8x the atoms and 1/8 the weight per atom
+    index = {tuple(mm): i for i, mm in enumerate(cb.m)}
+    c = np.zeros((cb.npw, 6), complex)
+    for i, mm in enumerate(cs.m):
+        c[index[tuple(2 * mm)], :] = v[i, :]
+    Hc = O.apply_H(cb, c)
+    assert np.abs(Hc - c * w[None, :]).max() < 1e-12
+
+
+def test_lobpcg_vs_dense_and_bounds():
+    cell, _ = _cell("C", 1, 8.0, seed=2)
+    nb = 18
+    w, _ = O.dense_eigs(cell, nb + 1)
+    X0 = synth.draw_x0(2, 8, cell.npw, nb)
+    lam, X, it, rn = O.eigsolve(cell, X0, tol=1e-9, maxit=300)
+    assert rn.max() <= 1e-9
+    assert np.abs(lam - w[:nb]).max() < 1e-12
+    # Weyl: each Ritz value within its residual norm of an eigenvalue
+    assert np.all(np.abs(lam - w[:nb]) <= rn + 1e-14)
+    assert np.abs(X.conj().T @ X - np.eye(nb)).max() < 1e-12
+
+
+def test_lobpcg_seed_independence():
+    cell, _ = _cell("C", 1, 8.0, seed=1)
+    a = O.eigsolve(cell, synth.draw_x0(11, 8, cell.npw, 12), tol=1e-9)[0]
+    b = O.eigsolve(cell, synth.draw_x0(12, 8, cell.npw, 12), tol=1e-9)[0]
+    assert np.abs(a - b).max() < 1e-12
+
+
+def test_tpa_closed_form():
+    assert O.tpa(np.array([0.0]))[0] == 1.0
+    assert abs(O.tpa(np.array([1.0]))[0] - 65.0 / 81.0) < 1e-15
+    x = np.array([1e4])
+    assert abs(O.tpa(x)[0] * 2 * x[0] - 1) < 1e-3      # ~ 8x^3 / 16x^4
+    xs = np.linspace(0, 10, 101)
+    assert np.all(np.diff(O.tpa(xs)) < 0)
+
+
+def test_rayleigh_ritz_breakdown_and_solution():
+    rng = np.random.default_rng(4)
+    S = rng.standard_normal((50, 4)) + 1j * rng.standard_normal((50, 4))
+    Hm = rng.standard_normal((50, 50))
+    Hm = Hm + Hm.T
+    with pytest.raises(O.CholeskyBreakdown):
+        O.rayleigh_ritz(np.hstack([S, S[:, :1]]), Hm @ np.hstack([S, S[:, :1]]), 2)
+    lam, C = O.rayleigh_ritz(S, Hm @ S, 4)
+    # the Ritz values of the pencil solve the generalized problem
+    import scipy.linalg as sla
+    ref = sla.eigh(S.conj().T @ Hm @ S, S.conj().T @ S, eigvals_only=True)
+    assert np.abs(lam - ref).max() < 1e-10
+    X = S @ C
+    assert np.abs(X.conj().T @ X - np.eye(4)).max() < 1e-12
+
+
+def test_density_sum_rule():
+    cell, _ = _cell("C", 1, 8.0)
+    w, v = O.dense_eigs(cell, 4)
+    rho = O.density(cell, v)
+    assert abs(rho.mean() - 4.0) < 1e-12       # Parseval: each band contributes 1
+
+
+def test_free_electron_golden_table():
+    here = __import__("os").path.dirname(__file__)
+    rows = np.loadtxt(here + "/golden/free_electron_si.txt", dtype=int)
+    L = synth.SI_A
+    m = O.sphere(10.0, [L] * 3)
+    n2 = (m ** 2).sum(axis=1)
+    for s, g in rows:
+        assert (n2 == s).sum() == g
