@@ -1,0 +1,166 @@
+/*
+ * pw.h -- C ABI of the GB300 plane-wave block-eigensolver library.
+ *
+ * The library solves the fixed-potential plane-wave Kohn-Sham eigenproblem
+ * H X = X Lambda (Sec. II-A, Eq. 1) for the lowest nb bands with LOBPCG,
+ * one of the inner eigensolvers of Sec. II-A.  One step applies H to a block
+ * of bands by FFT (the column scheme of Sec. II-B) plus the Kleinman-Bylander
+ * projector contractions (the pseudopotential application of Sec. III-A),
+ * forms the subspace matrices S^H S and S^H (H S) (Sec. II-B), and solves the
+ * small dense eigenproblem (Syevd, Sec. III-D) on the GPU in FP64.
+ *
+ * Conventions shared by every entry point:
+ *  - Units: Hartree atomic units (bohr, Ha).
+ *  - Wavefunction blocks are complex128 (interleaved re, im doubles),
+ *    column-major npw x nb with leading dimension ld >= npw: column j is band
+ *    j, entry g is the coefficient of plane wave G_g = 2 pi m_g / L.  The
+ *    plane-wave order is the library's canonical sphere order: integer
+ *    vectors m with 1/2 |G|^2 <= Ecut, sorted lexicographically by
+ *    (m_x, m_y, m_z), so each z-column of the sphere is contiguous.
+ *    pw_cell_info() returns that order.
+ *  - Device pointers are plain CUDA device addresses (for example from
+ *    torch.Tensor.data_ptr()); host pointers are plain host memory.  The
+ *    caller owns every buffer it passes; the library owns pw_cell and
+ *    pw_solver objects and their device workspaces.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream unless stated.
+ *  - No exceptions cross the ABI.  Every call returns a pw_status;
+ *    pw_strerror() names it.  Calls on the same pw_cell must not overlap.
+ */
+#ifndef PW_H
+#define PW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pw_cell pw_cell;
+typedef struct pw_solver pw_solver;
+
+typedef enum {
+  PW_OK = 0,
+  PW_ERR_ARG = -1,      /* invalid argument or unsupported size */
+  PW_ERR_OOM = -2,      /* device allocation failed */
+  PW_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+  PW_ERR_CHOL = -4,     /* overlap matrix not positive definite, even without P */
+  PW_ERR_NOCONV = -5,   /* maxit reached; partial results are filled in */
+  PW_ERR_TIMEOUT = -6,  /* a bounded device wait ran out */
+  PW_ERR_BUSY = -7,     /* admission refused: not enough device memory */
+  PW_ERR_NUMERIC = -8   /* NaN/Inf met in a residual norm or eigensolve */
+} pw_status;
+
+enum { PW_FP64 = 0, PW_MIXED = 1 };
+
+/* Cell description.  All pointers are caller-owned host memory, copied by
+ * pw_setup_cell.  Inputs follow the synthetic Si/C workloads: Gaussian local
+ * wells V(r) = sum_a d_a sum_R exp(-|r - tau_a - R|^2 / (2 vwidth^2)) and,
+ * per atom, four Gaussian KB projectors (s, p_x, p_y, p_z) of radial width
+ * pwidth with diagonal coefficients dkb. */
+typedef struct {
+  double lattice[9];    /* bohr, column-major 3x3 (columns a1 a2 a3); must be
+                           diagonal (orthorhombic cell) */
+  int natom;
+  const double *tau;    /* natom*3 Cartesian positions, bohr */
+  const double *vdepth; /* natom well depths d_a, Ha */
+  double vwidth;        /* sigma, bohr */
+  double pwidth;        /* r_p, bohr */
+  const double *dkb;    /* natom*4: D_s, D_px, D_py, D_pz, Ha */
+  double ecut;          /* Ha */
+  int grid[3];          /* FFT grid; 0 -> smallest 2^a 3^b >= 1.5 sqrt(2 Ecut) L_i / pi
+                           (the grid rule of Sec. II-A times 1.5) */
+  int precision;        /* PW_FP64 or PW_MIXED */
+} pw_cell_desc;
+
+/* Builds the plane-wave sphere, the FFT grid, V_loc(r) on the grid, the
+ * kinetic table and the projector matrix beta (npw x 4 natom) on the device
+ * of the calling thread, on `stream` (the call synchronises it).
+ * Errors: PW_ERR_ARG (non-orthorhombic lattice, Ecut <= 0, natom < 0, a plane
+ * wave within 1e-9 Ha of Ecut, grid too small for the sphere or not 2^a 3^b,
+ * plane too large for shared memory), PW_ERR_OOM, PW_ERR_CUDA.  On error
+ * *out is NULL. */
+pw_status pw_setup_cell(const pw_cell_desc *desc, void *stream, pw_cell **out);
+
+/* npw, grid and a host pointer to the npw*3 integer vectors m (owned by the
+ * cell, valid until pw_destroy_cell).  Any output pointer may be NULL. */
+pw_status pw_cell_info(const pw_cell *cell, int *npw, int grid[3], const int **mvec);
+
+/* Number of projectors (4 natom) and bytes of device memory held by the cell. */
+pw_status pw_cell_sizes(const pw_cell *cell, int *nproj, size_t *device_bytes);
+
+/* Selects the arithmetic of later pw_apply_H calls on this cell: PW_FP64, or
+ * PW_MIXED (FP32 FFTs and split-BF16 tensor-core projector contractions,
+ * FP64 kinetic term and FP64 accumulation of the result). */
+pw_status pw_cell_set_precision(pw_cell *cell, int precision);
+
+/* hpsi = H psi for nb bands (Sec. II-A Eq. 1; FFT local term per Sec. II-B,
+ * nonlocal term per Sec. III-A).  psi, hpsi: device complex128 npw x nb,
+ * leading dimension ld >= npw; they must not overlap.  nb = 0 is a no-op.
+ * Errors: PW_ERR_ARG (NULL pointer with nb > 0, ld < npw, nb < 0),
+ * PW_ERR_OOM (workspace growth), PW_ERR_CUDA. */
+pw_status pw_apply_H(pw_cell *cell, const void *psi, int ld, int nb, void *hpsi, void *stream);
+
+/* Solver options. */
+typedef struct {
+  int nbands;           /* nb >= 1, nb <= npw / 3 */
+  double tol;           /* residual-norm tolerance (bands below it are locked) */
+  int maxit;            /* maximum LOBPCG steps for pw_eigsolve */
+  uint64_t seed;        /* SplitMix64 stream of the random start when x0 == NULL */
+  const void *x0;       /* optional host complex128 npw x nbands start (ld = npw) */
+  int precision;        /* PW_FP64 or PW_MIXED */
+} pw_solve_opts;
+
+typedef struct {
+  int iter;             /* steps taken so far */
+  int nactive;          /* active (unlocked) bands used in this step */
+  int dropped_p;        /* 1 if P was dropped after a Cholesky breakdown */
+  double max_resid;     /* max_i ||H x_i - theta_i x_i|| of the block the step started from */
+  double ms;            /* wall time of the step (host clock, synchronised) */
+} pw_step_report;
+
+typedef struct {
+  int iters;
+  double max_resid;     /* final max residual norm (FP64) */
+  double orth_err;      /* max |X^H X - I| of the final block (FP64) */
+  double seconds;
+  size_t device_bytes;  /* solver workspace */
+} pw_solve_report;
+
+/* Creates LOBPCG state for `opts->nbands` bands: draws or copies the start
+ * block, applies H, and performs the initial Cholesky-QR + Rayleigh-Ritz.
+ * Synchronises `stream`.  Errors: PW_ERR_ARG, PW_ERR_OOM, PW_ERR_CHOL,
+ * PW_ERR_NUMERIC, PW_ERR_CUDA. */
+pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *opts, void *stream,
+                           pw_solver **out);
+
+/* One LOBPCG step (residual, preconditioner, H W, S^H S and S^H H S,
+ * Cholesky, Rayleigh-Ritz, rotation), Knyazev's method with the
+ * Hetmaniuk-Lehoucq P.  Synchronises the solver's stream.  rep may be NULL.
+ * Errors: PW_ERR_CHOL (overlap not positive definite even without P),
+ * PW_ERR_NUMERIC, PW_ERR_CUDA. */
+pw_status pw_subspace_step(pw_cell *cell, pw_solver *solver, pw_step_report *rep);
+
+/* Current Ritz values (host, nb) and residual norms of the current block
+ * (host, nb; computed in FP64).  Either pointer may be NULL. */
+pw_status pw_solver_eigs(pw_solver *solver, double *eig, double *resid);
+
+/* Copies the current block X (device complex128 npw x nb, leading dim ld). */
+pw_status pw_solver_block(pw_solver *solver, void *psi, int ld);
+
+void pw_solver_destroy(pw_solver *solver);
+
+/* Runs LOBPCG to max residual <= tol or maxit steps.  eig: host nb doubles
+ * (required); psi_out: device complex128 npw x nb (ld) or NULL.  Returns
+ * PW_ERR_NOCONV with eig / psi_out filled if maxit is reached. */
+pw_status pw_eigsolve(pw_cell *cell, const pw_solve_opts *opts, double *eig, void *psi_out,
+                      int ld, pw_solve_report *rep, void *stream);
+
+void pw_destroy_cell(pw_cell *cell);
+const char *pw_strerror(pw_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PW_H */

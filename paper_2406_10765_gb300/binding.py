@@ -1,0 +1,260 @@
+"""Thin ctypes binding of the C ABI in include/pw.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library libpwgb300.so.  Importing this
+module fails loudly if the library has not been built: there is no CPU
+fallback.  Device buffers are torch CUDA tensors (complex128), passed by
+data_ptr() together with the current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpwgb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -c 'import __graft_entry__ as g; g.build()')")
+
+_lib = ct.CDLL(LIB_PATH)
+
+PW_OK, PW_ERR_ARG, PW_ERR_OOM, PW_ERR_CUDA, PW_ERR_CHOL, PW_ERR_NOCONV, PW_ERR_TIMEOUT, \
+    PW_ERR_BUSY, PW_ERR_NUMERIC = 0, -1, -2, -3, -4, -5, -6, -7, -8
+PW_FP64, PW_MIXED = 0, 1
+_PREC = {"fp64": PW_FP64, "mixed": PW_MIXED, PW_FP64: PW_FP64, PW_MIXED: PW_MIXED}
+
+
+class PwError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {pw_strerror(status)} ({status})")
+
+
+class pw_cell_desc(ct.Structure):
+    _fields_ = [("lattice", ct.c_double * 9), ("natom", ct.c_int),
+                ("tau", ct.POINTER(ct.c_double)), ("vdepth", ct.POINTER(ct.c_double)),
+                ("vwidth", ct.c_double), ("pwidth", ct.c_double),
+                ("dkb", ct.POINTER(ct.c_double)), ("ecut", ct.c_double),
+                ("grid", ct.c_int * 3), ("precision", ct.c_int)]
+
+
+class pw_solve_opts(ct.Structure):
+    _fields_ = [("nbands", ct.c_int), ("tol", ct.c_double), ("maxit", ct.c_int),
+                ("seed", ct.c_uint64), ("x0", ct.c_void_p), ("precision", ct.c_int)]
+
+
+class pw_step_report(ct.Structure):
+    _fields_ = [("iter", ct.c_int), ("nactive", ct.c_int), ("dropped_p", ct.c_int),
+                ("max_resid", ct.c_double), ("ms", ct.c_double)]
+
+
+class pw_solve_report(ct.Structure):
+    _fields_ = [("iters", ct.c_int), ("max_resid", ct.c_double), ("orth_err", ct.c_double),
+                ("seconds", ct.c_double), ("device_bytes", ct.c_size_t)]
+
+
+class _Fn:
+    """Resolves a library symbol on first call (with its C signature)."""
+
+    def __init__(self, name, res, args):
+        self.name, self.res, self.args, self.f = name, res, args, None
+
+    def __call__(self, *a):
+        if self.f is None:
+            f = getattr(_lib, self.name)
+            f.restype, f.argtypes = self.res, self.args
+            self.f = f
+        return self.f(*a)
+
+
+def _sig(name, res, args):
+    return _Fn(name, res, args)
+
+
+_vp = ct.c_void_p
+_setup = _sig("pw_setup_cell", ct.c_int, [ct.POINTER(pw_cell_desc), _vp, ct.POINTER(_vp)])
+_info = _sig("pw_cell_info", ct.c_int, [_vp, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
+                                        ct.POINTER(ct.POINTER(ct.c_int))])
+_sizes = _sig("pw_cell_sizes", ct.c_int, [_vp, ct.POINTER(ct.c_int), ct.POINTER(ct.c_size_t)])
+_setprec = _sig("pw_cell_set_precision", ct.c_int, [_vp, ct.c_int])
+_apply = _sig("pw_apply_H", ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp, _vp])
+_destroy = _sig("pw_destroy_cell", None, [_vp])
+_strerror = _sig("pw_strerror", ct.c_char_p, [ct.c_int])
+_screate = _sig("pw_solver_create", ct.c_int, [_vp, ct.POINTER(pw_solve_opts), _vp, ct.POINTER(_vp)])
+_sstep = _sig("pw_subspace_step", ct.c_int, [_vp, _vp, ct.POINTER(pw_step_report)])
+_seigs = _sig("pw_solver_eigs", ct.c_int, [_vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)])
+_sblock = _sig("pw_solver_block", ct.c_int, [_vp, _vp, ct.c_int])
+_sdestroy = _sig("pw_solver_destroy", None, [_vp])
+_eigsolve = _sig("pw_eigsolve", ct.c_int, [_vp, ct.POINTER(pw_solve_opts), ct.POINTER(ct.c_double),
+                                            _vp, ct.c_int, ct.POINTER(pw_solve_report), _vp])
+
+
+def pw_strerror(status: int) -> str:
+    return _strerror(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != PW_OK:
+        raise PwError(status, what)
+
+
+def _stream(stream):
+    if stream is not None:
+        return ct.c_void_p(int(stream))
+    import torch
+    return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t):
+    return ct.c_void_p(t.data_ptr())
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def pw_setup_cell(L, tau, depth, dkb, ecut, vwidth=1.2, pwidth=1.2, grid=None,
+                  precision="fp64", stream=None):
+    """Build a cell on the current device.  L: scalar (cubic) or 3 lengths."""
+    Ls = np.broadcast_to(np.asarray(L, float), (3,))
+    tau, depth, dkb = _f64(tau).reshape(-1, 3), _f64(depth).reshape(-1), _f64(dkb).reshape(-1, 4)
+    d = pw_cell_desc()
+    lat = [0.0] * 9
+    lat[0], lat[4], lat[8] = float(Ls[0]), float(Ls[1]), float(Ls[2])
+    d.lattice = (ct.c_double * 9)(*lat)
+    d.natom = tau.shape[0]
+    keep = (tau, depth, dkb)
+    d.tau = keep[0].ctypes.data_as(ct.POINTER(ct.c_double))
+    d.vdepth = keep[1].ctypes.data_as(ct.POINTER(ct.c_double))
+    d.dkb = keep[2].ctypes.data_as(ct.POINTER(ct.c_double))
+    d.vwidth, d.pwidth, d.ecut = float(vwidth), float(pwidth), float(ecut)
+    d.grid = (ct.c_int * 3)(*(grid if grid is not None else (0, 0, 0)))
+    d.precision = _PREC[precision]
+    h = ct.c_void_p()
+    _check(_setup(ct.byref(d), _stream(stream), ct.byref(h)), "pw_setup_cell")
+    return h
+
+
+def pw_cell_info(cell):
+    npw = ct.c_int()
+    grid = (ct.c_int * 3)()
+    mp = ct.POINTER(ct.c_int)()
+    _check(_info(cell, ct.byref(npw), grid, ct.byref(mp)), "pw_cell_info")
+    m = np.ctypeslib.as_array(mp, shape=(npw.value * 3,)).reshape(-1, 3).astype(np.int64)
+    return npw.value, tuple(grid), m
+
+
+def pw_cell_sizes(cell):
+    nproj = ct.c_int()
+    nbytes = ct.c_size_t()
+    _check(_sizes(cell, ct.byref(nproj), ct.byref(nbytes)), "pw_cell_sizes")
+    return nproj.value, nbytes.value
+
+
+def pw_cell_set_precision(cell, precision):
+    _check(_setprec(cell, _PREC[precision]), "pw_cell_set_precision")
+
+
+def pw_apply_H(cell, psi, hpsi, stream=None):
+    """hpsi <- H psi; psi, hpsi: CUDA complex128 tensors (npw, nb), column-major."""
+    assert psi.dtype == hpsi.dtype and psi.is_cuda and hpsi.is_cuda
+    npw, nb = psi.shape
+    ld = psi.stride(1) if nb > 1 else npw
+    assert psi.stride(0) == 1 and hpsi.stride(0) == 1 and (nb <= 1 or hpsi.stride(1) == ld)
+    _check(_apply(cell, _dptr(psi), ld, nb, _dptr(hpsi), _stream(stream)), "pw_apply_H")
+
+
+def pw_destroy_cell(cell):
+    _destroy(cell)
+
+
+def _opts(nbands, tol, maxit, seed, x0, precision):
+    o = pw_solve_opts()
+    o.nbands, o.tol, o.maxit, o.seed = int(nbands), float(tol), int(maxit), int(seed)
+    o.precision = _PREC[precision]
+    keep = None
+    if x0 is not None:
+        keep = np.asfortranarray(x0, dtype=np.complex128)
+        o.x0 = keep.ctypes.data
+    return o, keep
+
+
+def pw_solver_create(cell, nbands, tol=1e-8, maxit=200, seed=0, x0=None, precision="fp64",
+                     stream=None):
+    o, keep = _opts(nbands, tol, maxit, seed, x0, precision)
+    h = ct.c_void_p()
+    _check(_screate(cell, ct.byref(o), _stream(stream), ct.byref(h)), "pw_solver_create")
+    del keep
+    return h
+
+
+def pw_subspace_step(cell, solver):
+    r = pw_step_report()
+    _check(_sstep(cell, solver, ct.byref(r)), "pw_subspace_step")
+    return r
+
+
+def pw_solver_eigs(solver, nbands):
+    e = np.zeros(nbands)
+    r = np.zeros(nbands)
+    _check(_seigs(solver, e.ctypes.data_as(ct.POINTER(ct.c_double)),
+                  r.ctypes.data_as(ct.POINTER(ct.c_double))), "pw_solver_eigs")
+    return e, r
+
+
+def pw_solver_block(solver, out):
+    _check(_sblock(solver, _dptr(out), out.shape[0]), "pw_solver_block")
+
+
+def pw_solver_destroy(solver):
+    _sdestroy(solver)
+
+
+def pw_eigsolve(cell, nbands, tol=1e-8, maxit=200, seed=0, x0=None, precision="fp64",
+                psi_out=None, stream=None, raise_noconv=True):
+    o, keep = _opts(nbands, tol, maxit, seed, x0, precision)
+    eig = np.zeros(nbands)
+    rep = pw_solve_report()
+    ptr = _dptr(psi_out) if psi_out is not None else ct.c_void_p()
+    ld = psi_out.shape[0] if psi_out is not None else 0
+    st = _eigsolve(cell, ct.byref(o), eig.ctypes.data_as(ct.POINTER(ct.c_double)), ptr, ld,
+                   ct.byref(rep), _stream(stream))
+    del keep
+    if st != PW_OK and (st != PW_ERR_NOCONV or raise_noconv):
+        raise PwError(st, "pw_eigsolve")
+    return eig, rep, st
+
+
+class Cell:
+    """Owning wrapper around a pw_cell handle."""
+
+    def __init__(self, L, tau, depth, dkb, ecut, vwidth=1.2, pwidth=1.2, grid=None,
+                 precision="fp64", stream=None):
+        self.h = pw_setup_cell(L, tau, depth, dkb, ecut, vwidth, pwidth, grid, precision, stream)
+        self.npw, self.grid, self.m = pw_cell_info(self.h)
+        self.nproj, _ = pw_cell_sizes(self.h)
+
+    def apply_H(self, psi, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(psi)
+        pw_apply_H(self.h, psi, out, stream)
+        return out
+
+    def set_precision(self, p):
+        pw_cell_set_precision(self.h, p)
+
+    def close(self):
+        if self.h:
+            pw_destroy_cell(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

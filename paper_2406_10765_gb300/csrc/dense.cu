@@ -1,0 +1,901 @@
+// FP64 dense linear algebra of the Rayleigh-Ritz step (the paper's Syevd hot
+// spot, Sec. III-D), all on the GPU in FP64:
+//
+//  * Jacobi scaling and blocked Cholesky of the Gram matrix, with the pivot
+//    test that drives the drop-P fallback;
+//  * triangular inverse L^-1 (recursive, GEMM based);
+//  * Hermitian eigensolver: Householder reduction to a real symmetric
+//    tridiagonal T, Cuppen's divide and conquer on T (deflation, secular
+//    equation solved per root with a two-pole rational model, eigenvectors
+//    from the Gu-Eisenstat (Lowner) recomputed z), and back-transformation of
+//    the wanted eigenvectors.
+//
+// The divide and conquer runs level by level over a binary tree with leaves
+// of size 1; every node of a level is handled by the same few batched
+// launches.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <functional>
+#include <vector>
+
+#include "dense.cuh"
+
+namespace {
+
+constexpr double kEps = 2.220446049250313e-16;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_prod(double v) {
+  for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// block-wide sum of one double (blockDim.x multiple of 32, <= 1024)
+__device__ double block_sum(double v, double *sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    r = warp_sum(r);
+    if (threadIdx.x == 0) sh[0] = r;
+  }
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+__device__ double block_max(double v, double *sh) {
+  v = warp_max(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    r = warp_max(r);
+    if (threadIdx.x == 0) sh[0] = r;
+  }
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// ======================================================================
+// Cholesky, scaling, triangular inverse
+// ======================================================================
+
+// dscale_i = Re(G_ii)^-1/2; flag[0] |= 1 if a diagonal is not positive
+__global__ void k_diag_scale(const double2 *G, int ld, int n, double *dscale, int *flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double g = G[i + (long)i * ld].x;
+  if (!(g > 0.0)) { atomicOr(flag, 1); dscale[i] = 0.0; return; }
+  dscale[i] = 1.0 / sqrt(g);
+}
+
+// out = d o (0.5 (M + M^H)) o d  (n x n, out ld n)
+__global__ void k_scale_herm(const double2 *M, int ld, int n, const double *d, double2 *out) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const double2 a = M[i + (long)j * ld], b = M[j + (long)i * ld];
+  const double s = 0.5 * d[i] * d[j];
+  out[i + (long)j * n] = make_double2(s * (a.x + b.x), s * (a.y - b.y));
+}
+
+// in-place Hermitian average of an n x n matrix (ld n)
+__global__ void k_hermitize(double2 *M, int n) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
+  if (i >= n || j >= n || i < j) return;
+  if (i == j) { M[i + (long)i * n].y = 0.0; return; }
+  double2 a = M[i + (long)j * n], b = M[j + (long)i * n];
+  const double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  M[i + (long)j * n] = h;
+  M[j + (long)i * n] = make_double2(h.x, -h.y);
+}
+
+constexpr int CB = 32;   // Cholesky / inverse block
+
+// unblocked Cholesky of the diagonal block at j0 (size b <= 32), in place
+__global__ void k_potf2(double2 *A, int n, int j0, int b, double *piv, int *flag) {
+  __shared__ double2 L[CB][CB + 1];
+  __shared__ int bad;
+  const int t = threadIdx.x;
+  for (int e = t; e < b * b; e += blockDim.x) {
+    const int i = e % b, j = e / b;
+    L[i][j] = A[(j0 + i) + (long)(j0 + j) * n];
+  }
+  if (t == 0) bad = 0;
+  __syncthreads();
+  for (int c = 0; c < b; ++c) {
+    if (t == 0) {
+      const double p = L[c][c].x;
+      piv[j0 + c] = p;
+      if (!(p > 0.0)) { bad = 1; L[c][c] = make_double2(1.0, 0.0); }
+      else L[c][c] = make_double2(sqrt(p), 0.0);
+    }
+    __syncthreads();
+    const double inv = 1.0 / L[c][c].x;
+    for (int i = c + 1 + t; i < b; i += blockDim.x) { L[i][c].x *= inv; L[i][c].y *= inv; }
+    __syncthreads();
+    for (int e = t; e < b * b; e += blockDim.x) {
+      const int i = e % b, j = e / b;
+      if (j > c && i >= j) {
+        const double2 li = L[i][c], lj = L[j][c];
+        // L[i][j] -= li * conj(lj)
+        L[i][j].x -= li.x * lj.x + li.y * lj.y;
+        L[i][j].y -= li.y * lj.x - li.x * lj.y;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < b * b; e += blockDim.x) {
+    const int i = e % b, j = e / b;
+    if (i >= j) A[(j0 + i) + (long)(j0 + j) * n] = L[i][j];
+  }
+  if (t == 0 && bad) atomicOr(flag, 2);
+}
+
+// rows i >= j0 + b:  A[i, j0:j0+b] <- A[i, j0:j0+b] L11^-H
+__global__ void k_trsm_rows(double2 *A, int n, int j0, int b) {
+  __shared__ double2 L[CB][CB + 1];
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e % b, j = e / b;
+    L[i][j] = A[(j0 + i) + (long)(j0 + j) * n];
+  }
+  __syncthreads();
+  const int i = j0 + b + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double2 x[CB];
+  for (int c = 0; c < b; ++c) {
+    double2 a = A[i + (long)(j0 + c) * n];
+    for (int l = 0; l < c; ++l) {
+      // a -= x_l * conj(L[c][l])
+      const double2 lc = L[c][l];
+      a.x -= x[l].x * lc.x + x[l].y * lc.y;
+      a.y -= x[l].y * lc.x - x[l].x * lc.y;
+    }
+    const double inv = 1.0 / L[c][c].x;
+    x[c] = make_double2(a.x * inv, a.y * inv);
+    A[i + (long)(j0 + c) * n] = x[c];
+  }
+}
+
+__global__ void k_zero_upper(double2 *A, int n) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
+  if (i < n && j < n && i < j) A[i + (long)j * n] = make_double2(0.0, 0.0);
+}
+
+// flag |= 4 if min pivot <= tol * max pivot (or a pivot is not finite)
+__global__ void k_chol_check(const double *piv, int n, double tol, int *flag) {
+  __shared__ double sh[32];
+  double mn = 1e300, mx = 0.0;
+  int bad = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double p = piv[i];
+    if (!isfinite(p)) bad = 1;
+    mn = fmin(mn, p);
+    mx = fmax(mx, p);
+  }
+  mx = block_max(mx, sh);
+  mn = -block_max(-mn, sh);
+  if (bad) atomicOr(flag, 4);
+  if (threadIdx.x == 0 && !(mn > tol * mx)) atomicOr(flag, 4);
+}
+
+// inverse of lower-triangular diagonal blocks (size <= 32), one CTA per block
+__global__ void k_trinv_small(const double2 *L, double2 *X, int n, const int *blk_lo,
+                              const int *blk_sz) {
+  __shared__ double2 Ls[CB][CB + 1];
+  const int lo = blk_lo[blockIdx.x], b = blk_sz[blockIdx.x];
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e % b, j = e / b;
+    Ls[i][j] = L[(lo + i) + (long)(lo + j) * n];
+  }
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (j >= b) return;
+  double2 x[CB];
+  for (int i = 0; i < b; ++i) {
+    if (i < j) { x[i] = make_double2(0.0, 0.0); continue; }
+    double2 s = (i == j) ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
+    for (int l = j; l < i; ++l) s = csub(s, cmul(Ls[i][l], x[l]));
+    const double inv = 1.0 / Ls[i][i].x;
+    x[i] = make_double2(s.x * inv, s.y * inv);
+  }
+  for (int i = 0; i < b; ++i) X[(lo + i) + (long)(lo + j) * n] = x[i];
+}
+
+__global__ void k_scale_rows_real(double2 *C, int ld, int n, int nb, const double *d) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)n * nb) return;
+  const int i = (int)(idx % n), j = (int)(idx / n);
+  double2 &c = C[i + (long)j * ld];
+  c.x *= d[i];
+  c.y *= d[i];
+}
+
+// ======================================================================
+// Householder tridiagonalisation (lower, unblocked), complex Hermitian
+// ======================================================================
+
+// reflector from column k: v (stored in place below the diagonal), tau[k], e[k], d[k]
+__global__ void k_house(double2 *A, int n, int k, double *d, double *e, double2 *tau) {
+  __shared__ double sh[32];
+  const int m = n - k - 1;
+  double2 *x = A + (k + 1) + (long)k * n;
+  double s = 0.0;
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += x[i].x * x[i].x + x[i].y * x[i].y;
+  const double xn2 = block_sum(s, sh);
+  const double2 alpha = x[0];
+  double beta;
+  double2 tk, scal;
+  const bool identity = (xn2 == 0.0 && alpha.y == 0.0);
+  if (identity) {
+    beta = alpha.x;
+    tk = make_double2(0.0, 0.0);
+    scal = make_double2(0.0, 0.0);
+  } else {
+    beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2), alpha.x);
+    tk = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+    // scal = 1 / (alpha - beta)
+    const double2 den = make_double2(alpha.x - beta, alpha.y);
+    const double q = 1.0 / (den.x * den.x + den.y * den.y);
+    scal = make_double2(den.x * q, -den.y * q);
+  }
+  __syncthreads();
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] = cmul(x[i], scal);
+  if (threadIdx.x == 0) {
+    x[0] = make_double2(1.0, 0.0);
+    tau[k] = tk;
+    e[k] = beta;
+    d[k] = A[k + (long)k * n].x;
+  }
+}
+
+constexpr int HV_ROWS = 128, HV_COLS = 128;
+
+// partial p = A22 v over a column chunk
+__global__ void k_hemv(const double2 *A, int n, int k, double2 *part, int nmax) {
+  const int m = n - k - 1;
+  const int i = blockIdx.x * HV_ROWS + threadIdx.x;
+  const int c0 = blockIdx.y * HV_COLS, c1 = min(m, c0 + HV_COLS);
+  if (i >= m) return;
+  const double2 *v = A + (k + 1) + (long)k * n;
+  const double2 *Ai = A + (k + 1 + i) + (long)(k + 1) * n;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int j = c0; j < c1; ++j) acc = cadd(acc, cmul(Ai[(long)j * n], v[j]));
+  part[(long)blockIdx.y * nmax + i] = acc;
+}
+
+// p = tau sum(part); w = p - 1/2 tau (p^H v) v
+__global__ void k_hemv_fin(const double2 *A, int n, int k, const double2 *part, int nchunk,
+                           int nmax, const double2 *tau, double2 *p, double2 *w) {
+  __shared__ double sh[32];
+  const int m = n - k - 1;
+  const double2 *v = A + (k + 1) + (long)k * n;
+  const double2 t = tau[k];
+  double dr = 0.0, di = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int c = 0; c < nchunk; ++c) s = cadd(s, part[(long)c * nmax + i]);
+    s = cmul(t, s);
+    p[i] = s;
+    const double2 pv = cmulc(s, v[i]);   // conj(p_i) v_i
+    dr += pv.x;
+    di += pv.y;
+  }
+  dr = block_sum(dr, sh);
+  di = block_sum(di, sh);
+  // alpha = -1/2 tau (p^H v)
+  const double2 al = cmul(make_double2(-0.5 * t.x, -0.5 * t.y), make_double2(dr, di));
+  for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = cadd(p[i], cmul(al, v[i]));
+}
+
+// A22 -= v w^H + w v^H
+__global__ void k_her2(double2 *A, int n, int k, const double2 *w) {
+  const int m = n - k - 1;
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
+  if (i >= m || j >= m) return;
+  const double2 *v = A + (k + 1) + (long)k * n;
+  const double2 vi = v[i], vj = v[j], wi = w[i], wj = w[j];
+  double2 &a = A[(k + 1 + i) + (long)(k + 1 + j) * n];
+  // v_i conj(w_j) + w_i conj(v_j)
+  a.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
+  a.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
+}
+
+__global__ void k_last_diag(const double2 *A, int n, double *d) { d[n - 1] = A[(n - 1) + (long)(n - 1) * n].x; }
+
+// ======================================================================
+// divide and conquer on the symmetric tridiagonal (d, e)
+// ======================================================================
+
+// leaves of size 1: every boundary is a split, so d_i loses |e_{i-1}| + |e_i|
+__global__ void k_dc_init(const double *d, const double *e, int n, double *lam, double *Z) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = d[i];
+  if (i > 0) v -= fabs(e[i - 1]);
+  if (i < n - 1) v -= fabs(e[i]);
+  lam[i] = v;
+}
+__global__ void k_identity(double *Z, int n) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)n * n) return;
+  Z[idx] = (idx % n == idx / n) ? 1.0 : 0.0;
+}
+
+struct DcArrays {
+  double *lam, *Z, *W, *U;
+  double *Ds, *zs, *DK, *zK, *tauK, *zh, *lamK, *dD, *lnew;
+  int *perm, *colK, *orig, *dcol, *src, *defl;
+  int *knode;
+  double *rhonode;
+};
+
+// sort, z-vector, deflation and compaction for one node per CTA
+__global__ void __launch_bounds__(256) k_dc_deflate(const int *nodes, int n, const double *e,
+                                                    DcArrays a) {
+  __shared__ double sh[32];
+  __shared__ int s_rot, s_cj, s_ci, s_prev;
+  __shared__ double s_c, s_s;
+  const int node = blockIdx.x;
+  const int lo = nodes[3 * node], mid = nodes[3 * node + 1], hi = nodes[3 * node + 2];
+  const int size = hi - lo, m1 = mid - lo;
+  const double beta = e[mid - 1];
+  const double rho = fabs(beta), sgn = beta >= 0.0 ? 1.0 : -1.0;
+  if (threadIdx.x == 0) {    // merge of the two sorted halves (ties: left first)
+    int i = 0, j = m1;
+    for (int p = 0; p < size; ++p) {
+      int take;
+      if (i >= m1) take = j++;
+      else if (j >= size) take = i++;
+      else if (a.lam[lo + j] < a.lam[lo + i]) take = j++;
+      else take = i++;
+      a.perm[lo + p] = take;
+    }
+  }
+  __syncthreads();
+  double dmax = 0.0;
+  for (int p = threadIdx.x; p < size; p += blockDim.x) {
+    const int li = a.perm[lo + p];
+    const double Dv = a.lam[lo + li];
+    const double z = li < m1 ? a.Z[(mid - 1) + (long)(lo + li) * n]
+                             : sgn * a.Z[mid + (long)(lo + li) * n];
+    a.Ds[lo + p] = Dv;
+    a.zs[lo + p] = z * 0.70710678118654752440;
+    a.defl[lo + p] = 0;
+    dmax = fmax(dmax, fabs(Dv));
+  }
+  dmax = block_max(dmax, sh);
+  const double rho2 = 2.0 * rho;
+  const double tol = 8.0 * kEps * fmax(dmax, rho2);
+  if (threadIdx.x == 0) s_prev = -1;
+  __syncthreads();
+  for (int p = 0; p < size; ++p) {
+    if (threadIdx.x == 0) {
+      s_rot = 0;
+      const double zp = a.zs[lo + p];
+      if (rho2 * fabs(zp) <= tol) {
+        a.defl[lo + p] = 1;
+      } else {
+        if (s_prev >= 0) {
+          const int j = s_prev;
+          const double zj = a.zs[lo + j];
+          const double r = hypot(zp, zj);
+          const double c = zp / r, s = -zj / r;
+          const double Dj = a.Ds[lo + j], Dp = a.Ds[lo + p];
+          if (fabs(c * s * (Dp - Dj)) <= tol) {
+            s_rot = 1;
+            s_cj = lo + a.perm[lo + j];
+            s_ci = lo + a.perm[lo + p];
+            s_c = c;
+            s_s = s;
+            a.Ds[lo + j] = c * c * Dj + s * s * Dp;
+            a.Ds[lo + p] = s * s * Dj + c * c * Dp;
+            a.zs[lo + j] = 0.0;
+            a.zs[lo + p] = r;
+            a.defl[lo + j] = 1;
+          }
+        }
+        s_prev = p;
+      }
+    }
+    __syncthreads();
+    if (s_rot) {
+      const double c = s_c, s = s_s;
+      double *Qj = a.Z + (long)s_cj * n, *Qi = a.Z + (long)s_ci * n;
+      for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
+        const double qj = Qj[r], qi = Qi[r];
+        Qj[r] = c * qj + s * qi;
+        Qi[r] = -s * qj + c * qi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int t = 0, q = 0;
+    for (int p = 0; p < size; ++p) {
+      const int col = lo + a.perm[lo + p];
+      if (!a.defl[lo + p]) {
+        a.DK[lo + t] = a.Ds[lo + p];
+        a.zK[lo + t] = a.zs[lo + p];
+        a.colK[lo + t] = col;
+        ++t;
+      } else {
+        a.dD[lo + q] = a.Ds[lo + p];
+        a.dcol[lo + q] = col;
+        ++q;
+      }
+    }
+    a.knode[node] = rho2 > 0.0 ? t : 0;
+    if (!(rho2 > 0.0)) {   // no coupling: everything deflates
+      for (int p = 0; p < size; ++p) {
+        a.dD[lo + p] = a.Ds[lo + p];
+        a.dcol[lo + p] = lo + a.perm[lo + p];
+      }
+    }
+    a.rhonode[node] = rho2;
+  }
+}
+
+// one warp per root t of the secular equation 1 + rho sum z_i^2 / (D_i - lam) = 0
+__global__ void __launch_bounds__(256) k_dc_roots(const int *nodes, DcArrays a) {
+  const int node = blockIdx.y;
+  const int lo = nodes[3 * node];
+  const int k = a.knode[node];
+  const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= k) return;
+  const double rho = a.rhonode[node];
+  const double *D = a.DK + lo, *z = a.zK + lo;
+  int o;
+  double blo, bhi;
+  if (t < k - 1) {
+    const double half = 0.5 * (D[t + 1] - D[t]);
+    double s = 0.0;
+    for (int i = lane; i < k; i += 32) s += z[i] * z[i] / ((D[i] - D[t]) - half);
+    s = warp_sum(s);
+    if (1.0 + rho * s >= 0.0) { o = t; blo = 0.0; bhi = half; }
+    else { o = t + 1; blo = -half; bhi = 0.0; }
+  } else {
+    double s = 0.0;
+    for (int i = lane; i < k; i += 32) s += z[i] * z[i];
+    s = warp_sum(s);
+    o = t; blo = 0.0; bhi = rho * s;
+  }
+  const double Do = D[o];
+  const double da = D[t] - Do;                          // left pole
+  const double db = (t < k - 1) ? D[t + 1] - Do : 0.0;  // right pole (if any)
+  double tau = 0.5 * (blo + bhi);
+  for (int it = 0; it < 100; ++it) {
+    double psi = 0.0, dpsi = 0.0, phi = 0.0, dphi = 0.0;
+    for (int i = lane; i < k; i += 32) {
+      const double diff = (D[i] - Do) - tau;
+      const double term = z[i] * z[i] / diff;
+      if (i <= t) { psi += term; dpsi += term / diff; }
+      else { phi += term; dphi += term / diff; }
+    }
+    psi = rho * warp_sum(psi);
+    dpsi = rho * warp_sum(dpsi);
+    phi = rho * warp_sum(phi);
+    dphi = rho * warp_sum(dphi);
+    const double f = 1.0 + psi + phi;
+    if (f < 0.0) blo = fmax(blo, tau); else bhi = fmin(bhi, tau);
+    if (f == 0.0 || bhi - blo <= 4.0 * kEps * fmax(fabs(blo), fabs(bhi))) break;
+    const double q = dpsi * (da - tau) * (da - tau);
+    const double pp = psi - dpsi * (da - tau);
+    double x;
+    if (t < k - 1) {
+      const double s = dphi * (db - tau) * (db - tau);
+      const double r = phi - dphi * (db - tau);
+      const double Cc = 1.0 + pp + r;
+      const double A2 = Cc, B2 = -(Cc * (da + db) + q + s), C2 = Cc * da * db + q * db + s * da;
+      x = 0.5 * (blo + bhi);
+      if (A2 == 0.0) {
+        if (B2 != 0.0) x = -C2 / B2;
+      } else {
+        const double disc = fmax(B2 * B2 - 4.0 * A2 * C2, 0.0);
+        const double sq = sqrt(disc);
+        const double r1 = (B2 >= 0.0) ? (-B2 - sq) / (2.0 * A2) : (-B2 + sq) / (2.0 * A2);
+        const double r2 = (r1 != 0.0) ? C2 / (A2 * r1) : r1;
+        if (r1 > da && r1 < db) x = r1;
+        else if (r2 > da && r2 < db) x = r2;
+      }
+    } else {
+      const double Cc = 1.0 + pp + phi;
+      x = (Cc > 0.0) ? da + q / Cc : 0.5 * (blo + bhi);
+    }
+    if (!(x > blo && x < bhi)) x = 0.5 * (blo + bhi);
+    if (fabs(x - tau) <= 2.0 * kEps * fabs(x)) { tau = x; break; }
+    tau = x;
+  }
+  if (lane == 0) {
+    a.orig[lo + t] = o;
+    a.tauK[lo + t] = tau;
+    a.lamK[lo + t] = Do + tau;
+  }
+}
+
+// Lowner: rho zh_i^2 = prod_j (lam_j - D_i) / prod_{j != i} (D_j - D_i)
+__global__ void __launch_bounds__(256) k_dc_zhat(const int *nodes, DcArrays a) {
+  const int node = blockIdx.y;
+  const int lo = nodes[3 * node];
+  const int k = a.knode[node];
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= k) return;
+  const double *D = a.DK + lo;
+  const double Di = D[i];
+  double prod = 1.0;
+  for (int j = lane; j < k; j += 32) {
+    const double num = (D[a.orig[lo + j]] - Di) + a.tauK[lo + j];
+    prod *= (j == i) ? num : num / (D[j] - Di);
+  }
+  prod = warp_prod(prod);
+  if (lane == 0) {
+    const double zi = a.zK[lo + i];
+    a.zh[lo + i] = copysign(sqrt(fmax(prod, 0.0) / a.rhonode[node]), zi);
+  }
+}
+
+// eigenvectors of the secular problem: u_t[i] = zh_i / (D_i - lam_t), normalised
+__global__ void __launch_bounds__(256) k_dc_vectors(const int *nodes, int n, DcArrays a) {
+  const int node = blockIdx.y;
+  const int lo = nodes[3 * node];
+  const int k = a.knode[node];
+  const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (t >= k) return;
+  const double *D = a.DK + lo;
+  const double Do = D[a.orig[lo + t]], tau = a.tauK[lo + t];
+  double s = 0.0;
+  for (int i = lane; i < k; i += 32) {
+    const double u = a.zh[lo + i] / ((D[i] - Do) - tau);
+    s += u * u;
+  }
+  const double inv = 1.0 / sqrt(warp_sum(s));
+  double *Ucol = a.U + (long)(lo + t) * n + lo;
+  for (int i = lane; i < k; i += 32) Ucol[i] = inv * a.zh[lo + i] / ((D[i] - Do) - tau);
+}
+
+// W[rows, lo + t] = Z[rows, colK] U[:, t]  (node rows lo..hi-1)
+__global__ void __launch_bounds__(256) k_dc_gemm(const int *nodes, int n, DcArrays a) {
+  const int node = blockIdx.z;
+  const int lo = nodes[3 * node], hi = nodes[3 * node + 2];
+  const int rows = hi - lo, k = a.knode[node];
+  const int r0 = blockIdx.x * 64, t0 = blockIdx.y * 64;
+  if (r0 >= rows || t0 >= k) return;
+  __shared__ double As[16][65], Bs[16][65];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < k; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      const int r = e & 63, kk = e >> 6;
+      double v = 0.0;
+      if (r0 + r < rows && k0 + kk < k) v = a.Z[(lo + r0 + r) + (long)a.colK[lo + k0 + kk] * n];
+      As[kk][r] = v;
+      const int kb = e & 15, tt = e >> 4;
+      double u = 0.0;
+      if (k0 + kb < k && t0 + tt < k) u = a.U[(lo + k0 + kb) + (long)(lo + t0 + tt) * n];
+      Bs[kb][tt] = u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { av[q] = As[kk][tx + 16 * q]; bv[q] = Bs[kk][ty + 16 * q]; }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[q][r] = fma(av[q], bv[r], acc[q][r]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int row = r0 + tx + 16 * q, t = t0 + ty + 16 * r;
+      if (row < rows && t < k) a.W[(lo + row) + (long)(lo + t) * n] = acc[q][r];
+    }
+}
+
+// final order: rank of each (value, source index) among the node's eigenvalues
+__global__ void k_dc_rank(const int *nodes, DcArrays a) {
+  const int node = blockIdx.y;
+  const int lo = nodes[3 * node], hi = nodes[3 * node + 2];
+  const int size = hi - lo, k = a.knode[node];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= size) return;
+  const double v = e < k ? a.lamK[lo + e] : a.dD[lo + e - k];
+  int rank = 0;
+  for (int f = 0; f < size; ++f) {
+    const double w = f < k ? a.lamK[lo + f] : a.dD[lo + f - k];
+    rank += (w < v) || (w == v && f < e);
+  }
+  a.lnew[lo + rank] = v;
+  a.src[lo + rank] = lo + e;     // W column: roots at lo..lo+k-1, deflated copied after them
+}
+
+// copy deflated columns of Z into W after the roots' columns
+__global__ void k_dc_copy_defl(const int *nodes, int n, DcArrays a) {
+  const int node = blockIdx.y;
+  const int lo = nodes[3 * node], hi = nodes[3 * node + 2];
+  const int size = hi - lo, k = a.knode[node];
+  const int q = blockIdx.x;
+  if (q >= size - k) return;
+  const double *src = a.Z + (long)a.dcol[lo + q] * n;
+  double *dst = a.W + (long)(lo + k + q) * n;
+  for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) dst[r] = src[r];
+}
+
+__global__ void k_dc_write(const int *nodes, int n, DcArrays a) {
+  const int node = blockIdx.y;
+  const int lo = nodes[3 * node], hi = nodes[3 * node + 2];
+  const int p = blockIdx.x;
+  if (p >= hi - lo) return;
+  const double *src = a.W + (long)a.src[lo + p] * n;
+  double *dst = a.Z + (long)(lo + p) * n;
+  for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) dst[r] = src[r];
+  if (threadIdx.x == 0) a.lam[lo + p] = a.lnew[lo + p];
+}
+
+// ======================================================================
+// back-transformation  Y = H_0 H_1 ... H_{n-2} Z
+// ======================================================================
+__global__ void k_bt_init(const double *Z, int n, int nb, double2 *Y) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)n * nb) return;
+  Y[idx] = make_double2(Z[idx], 0.0);
+}
+
+// y <- y - tau_k v (v^H y) for every column; one warp per column
+__global__ void k_bt_step(const double2 *A, int n, int k, const double2 *tau, double2 *Y, int nb) {
+  const int col = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= nb) return;
+  const int m = n - k - 1;
+  const double2 *v = A + (k + 1) + (long)k * n;
+  double2 *y = Y + (long)col * n + (k + 1);
+  double sr = 0.0, si = 0.0;
+  for (int i = lane; i < m; i += 32) {
+    const double2 p = cmulc(v[i], y[i]);
+    sr += p.x;
+    si += p.y;
+  }
+  sr = warp_sum(sr);
+  si = warp_sum(si);
+  const double2 f = cmul(tau[k], make_double2(sr, si));
+  for (int i = lane; i < m; i += 32) y[i] = csub(y[i], cmul(f, v[i]));
+}
+
+void build_tree(pw_dense_ws *ws, int n) {
+  ws->levels.clear();
+  std::function<void(int, int, int)> rec = [&](int lo, int hi, int depth) {
+    if (hi - lo <= 1) return;
+    const int mid = lo + (hi - lo) / 2;
+    if ((int)ws->levels.size() <= depth) ws->levels.resize(depth + 1);
+    ws->levels[depth].push_back(lo);
+    ws->levels[depth].push_back(mid);
+    ws->levels[depth].push_back(hi);
+    rec(lo, mid, depth + 1);
+    rec(mid, hi, depth + 1);
+  };
+  rec(0, n, 0);
+  ws->level_off.assign(ws->levels.size(), 0);
+  std::vector<int> flat;
+  ws->max_level_nodes = 0;
+  for (size_t l = 0; l < ws->levels.size(); ++l) {
+    ws->level_off[l] = (int)flat.size() / 3;
+    flat.insert(flat.end(), ws->levels[l].begin(), ws->levels[l].end());
+    ws->max_level_nodes = std::max(ws->max_level_nodes, (int)ws->levels[l].size() / 3);
+  }
+  if (!flat.empty())
+    cudaMemcpy(ws->nodes, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice);
+  ws->tree_n = n;
+}
+
+}  // namespace
+
+// ======================================================================
+// workspace
+// ======================================================================
+pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
+  if (ws->nmax >= nmax && ws->nbmax >= nbmax) return PW_OK;
+  pw_dense_free(ws);
+  const size_t n2 = (size_t)nmax * nmax;
+  size_t total = 0;
+  auto get = [&](void **p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); *p = nullptr; return false; }
+    total += bytes;
+    return true;
+  };
+  bool ok = get((void **)&ws->G, n2 * 16) && get((void **)&ws->A, n2 * 16) &&
+            get((void **)&ws->T, n2 * 16) && get((void **)&ws->Linv, n2 * 16) &&
+            get((void **)&ws->Y, (size_t)nmax * nbmax * 16) &&
+            get((void **)&ws->dscale, nmax * 8) && get((void **)&ws->piv, nmax * 8) &&
+            get((void **)&ws->flag, 64) && get((void **)&ws->d, nmax * 8) &&
+            get((void **)&ws->e, nmax * 8) && get((void **)&ws->lam, nmax * 8) &&
+            get((void **)&ws->tau, nmax * 16) && get((void **)&ws->p, nmax * 16) &&
+            get((void **)&ws->w, nmax * 16) &&
+            get((void **)&ws->part, (size_t)((nmax + HV_COLS - 1) / HV_COLS) * nmax * 16) &&
+            get((void **)&ws->Z, n2 * 8) && get((void **)&ws->W, n2 * 8) && get((void **)&ws->U, n2 * 8);
+  double **dbl[] = {&ws->Ds, &ws->zs, &ws->DK, &ws->zK, &ws->tauK, &ws->zh, &ws->lamK, &ws->dD, &ws->lnew};
+  for (double **q : dbl) ok = ok && get((void **)q, nmax * 8);
+  int **ints[] = {&ws->perm, &ws->colK, &ws->orig, &ws->dcol, &ws->src};
+  for (int **q : ints) ok = ok && get((void **)q, nmax * 4);
+  ok = ok && get((void **)&ws->nodes, (size_t)3 * nmax * 4 + 64) &&
+       get((void **)&ws->knode, (size_t)nmax * 4 + 64) &&
+       get((void **)&ws->rhonode, (size_t)nmax * 8 + 64);
+  ws->gemm_ws_elems = std::max(pw_zgemm_ws_elems(nmax, nmax, nmax), pw_zgemm_ws_elems(nmax, nbmax, nmax));
+  if (ok && ws->gemm_ws_elems) ok = get((void **)&ws->gemm_ws, ws->gemm_ws_elems * 16);
+  if (!ok) { pw_dense_free(ws); return PW_ERR_OOM; }
+  ws->nmax = nmax;
+  ws->nbmax = nbmax;
+  ws->bytes = total;
+  ws->tree_n = -1;
+  return PW_OK;
+}
+
+void pw_dense_free(pw_dense_ws *ws) {
+  void *ptrs[] = {ws->G, ws->A, ws->T, ws->Linv, ws->Y, ws->dscale, ws->piv, ws->flag, ws->d, ws->e,
+                  ws->lam, ws->tau, ws->p, ws->w, ws->part, ws->Z, ws->W, ws->U, ws->Ds, ws->zs,
+                  ws->DK, ws->zK, ws->tauK, ws->zh, ws->lamK, ws->dD, ws->lnew, ws->perm, ws->colK,
+                  ws->orig, ws->dcol, ws->src, ws->nodes, ws->knode, ws->rhonode, ws->gemm_ws};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  *ws = pw_dense_ws();
+}
+
+// ======================================================================
+// Hermitian eigensolver
+// ======================================================================
+pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam, double2 *Y,
+                         cudaStream_t st) {
+  if (n <= 0 || nb <= 0 || nb > n || n > ws->nmax || nb > ws->nbmax) return PW_ERR_ARG;
+  // 1. Householder tridiagonalisation
+  const int nchunk_max = (n + HV_COLS - 1) / HV_COLS;
+  for (int k = 0; k + 1 < n; ++k) {
+    const int m = n - k - 1;
+    k_house<<<1, 256, 0, st>>>(A, n, k, ws->d, ws->e, ws->tau);
+    const int nch = (m + HV_COLS - 1) / HV_COLS;
+    k_hemv<<<dim3((m + HV_ROWS - 1) / HV_ROWS, nch), HV_ROWS, 0, st>>>(A, n, k, ws->part, ws->nmax);
+    k_hemv_fin<<<1, 256, 0, st>>>(A, n, k, ws->part, nch, ws->nmax, ws->tau, ws->p, ws->w);
+    k_her2<<<dim3((m + 31) / 32, (m + 7) / 8), dim3(32, 8), 0, st>>>(A, n, k, ws->w);
+  }
+  (void)nchunk_max;
+  k_last_diag<<<1, 1, 0, st>>>(A, n, ws->d);
+  PW_TRY(pw_check_launch("tridiag"));
+
+  // 2. divide and conquer
+  if (ws->tree_n != n) build_tree(ws, n);
+  DcArrays a{lam, ws->Z, ws->W, ws->U, ws->Ds, ws->zs, ws->DK, ws->zK, ws->tauK, ws->zh,
+             ws->lamK, ws->dD, ws->lnew, ws->perm, ws->colK, ws->orig, ws->dcol, ws->src,
+             (int *)ws->p /* defl scratch: n ints fit in n double2 */, ws->knode, ws->rhonode};
+  k_dc_init<<<(n + 255) / 256, 256, 0, st>>>(ws->d, ws->e, n, lam, ws->Z);
+  k_identity<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(ws->Z, n);
+  for (int l = (int)ws->levels.size() - 1; l >= 0; --l) {
+    const int nn = (int)ws->levels[l].size() / 3;
+    const int *nodes = ws->nodes + 3 * ws->level_off[l];
+    int maxsize = 0;
+    for (int q = 0; q < nn; ++q) maxsize = std::max(maxsize, ws->levels[l][3 * q + 2] - ws->levels[l][3 * q]);
+    k_dc_deflate<<<nn, 256, 0, st>>>(nodes, n, ws->e, a);
+    const dim3 gw((maxsize + 7) / 8, nn);
+    k_dc_roots<<<gw, 256, 0, st>>>(nodes, a);
+    k_dc_zhat<<<gw, 256, 0, st>>>(nodes, a);
+    k_dc_vectors<<<gw, 256, 0, st>>>(nodes, n, a);
+    k_dc_gemm<<<dim3((maxsize + 63) / 64, (maxsize + 63) / 64, nn), 256, 0, st>>>(nodes, n, a);
+    k_dc_rank<<<dim3((maxsize + 127) / 128, nn), 128, 0, st>>>(nodes, a);
+    k_dc_copy_defl<<<dim3(maxsize, nn), 128, 0, st>>>(nodes, n, a);
+    k_dc_write<<<dim3(maxsize, nn), 128, 0, st>>>(nodes, n, a);
+  }
+  PW_TRY(pw_check_launch("divide and conquer"));
+
+  // 3. back-transformation of the wanted columns
+  k_bt_init<<<(unsigned)(((long)n * nb + 255) / 256), 256, 0, st>>>(ws->Z, n, nb, Y);
+  for (int k = n - 2; k >= 0; --k)
+    k_bt_step<<<(nb + 3) / 4, 128, 0, st>>>(A, n, k, ws->tau, Y, nb);
+  return pw_check_launch("back-transform");
+}
+
+// ======================================================================
+// Rayleigh-Ritz
+// ======================================================================
+namespace {
+pw_status cholesky(pw_dense_ws *ws, double2 *A, int n, cudaStream_t st) {
+  const double2 mone = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
+  for (int j0 = 0; j0 < n; j0 += CB) {
+    const int b = std::min(CB, n - j0);
+    k_potf2<<<1, 256, 0, st>>>(A, n, j0, b, ws->piv, ws->flag);
+    const int rest = n - j0 - b;
+    if (rest > 0) {
+      k_trsm_rows<<<(rest + 127) / 128, 128, 0, st>>>(A, n, j0, b);
+      PW_TRY(pw_zgemm('N', 'C', rest, rest, b, mone, A + (j0 + b) + (long)j0 * n, n,
+                      A + (j0 + b) + (long)j0 * n, n, one, A + (j0 + b) + (long)(j0 + b) * n, n,
+                      ws->gemm_ws, ws->gemm_ws_elems, st));
+    }
+  }
+  k_zero_upper<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 32), 0, st>>>(A, n);
+  return pw_check_launch("cholesky");
+}
+
+// X = L^-1 for lower-triangular L (n x n, ld n); T is scratch
+pw_status trinv(pw_dense_ws *ws, const double2 *L, double2 *X, int n, cudaStream_t st) {
+  PW_CUDA(cudaMemsetAsync(X, 0, (size_t)n * n * 16, st));
+  // leaves: blocks of CB along the diagonal
+  std::vector<int> lo, sz;
+  for (int j = 0; j < n; j += CB) { lo.push_back(j); sz.push_back(std::min(CB, n - j)); }
+  int *dlo = ws->src, *dsz = ws->dcol;   // int scratch (n entries each, >= n/CB needed)
+  PW_CUDA(cudaMemcpyAsync(dlo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, st));
+  PW_CUDA(cudaMemcpyAsync(dsz, sz.data(), sz.size() * 4, cudaMemcpyHostToDevice, st));
+  k_trinv_small<<<(unsigned)lo.size(), 32, 0, st>>>(L, X, n, dlo, dsz);
+  PW_TRY(pw_check_launch("trinv_small"));
+  // combine: [L11 0; L21 L22]^-1 = [X11 0; -X22 L21 X11, X22], bottom-up over
+  // block widths 32, 64, 128, ...
+  const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0),
+                zero = make_double2(0.0, 0.0);
+  for (int w = CB; w < n; w *= 2) {
+    for (int off = 0; off + w < n; off += 2 * w) {
+      const int h1 = w, h2 = std::min(w, n - off - w);
+      // T = L21 X11  (h2 x h1)
+      double2 *T = ws->T;
+      PW_TRY(pw_zgemm('N', 'N', h2, h1, h1, one, L + (off + h1) + (long)off * n, n,
+                      X + off + (long)off * n, n, zero, T, h2, ws->gemm_ws, ws->gemm_ws_elems, st));
+      // X21 = -X22 T
+      PW_TRY(pw_zgemm('N', 'N', h2, h1, h2, mone, X + (off + h1) + (long)(off + h1) * n, n, T, h2,
+                      zero, X + (off + h1) + (long)off * n, n, ws->gemm_ws, ws->gemm_ws_elems, st));
+    }
+  }
+  return PW_OK;
+}
+}  // namespace
+
+pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, const double2 *A,
+                           double *theta, double2 *C, int *chol_ok, cudaStream_t st) {
+  if (n > ws->nmax || nb > ws->nbmax || nb > n) return PW_ERR_ARG;
+  *chol_ok = 1;
+  PW_CUDA(cudaMemsetAsync(ws->flag, 0, 16, st));
+  k_diag_scale<<<(n + 127) / 128, 128, 0, st>>>(G, n, n, ws->dscale, ws->flag);
+  const dim3 g2((n + 31) / 32, (n + 31) / 32), b2(32, 32);
+  k_scale_herm<<<g2, b2, 0, st>>>(G, n, n, ws->dscale, ws->G);
+  k_scale_herm<<<g2, b2, 0, st>>>(A, n, n, ws->dscale, ws->A);
+  PW_TRY(pw_check_launch("scale"));
+  PW_TRY(cholesky(ws, ws->G, n, st));
+  k_chol_check<<<1, 256, 0, st>>>(ws->piv, n, 1e-14, ws->flag);
+  int flag = 0;
+  PW_CUDA(cudaMemcpyAsync(&flag, ws->flag, 4, cudaMemcpyDeviceToHost, st));
+  PW_CUDA(cudaStreamSynchronize(st));
+  if (flag) { *chol_ok = 0; return PW_OK; }
+  PW_TRY(trinv(ws, ws->G, ws->Linv, n, st));
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  // At = Linv As Linv^H
+  PW_TRY(pw_zgemm('N', 'N', n, n, n, one, ws->Linv, n, ws->A, n, zero, ws->T, n, ws->gemm_ws,
+                  ws->gemm_ws_elems, st));
+  PW_TRY(pw_zgemm('N', 'C', n, n, n, one, ws->T, n, ws->Linv, n, zero, ws->A, n, ws->gemm_ws,
+                  ws->gemm_ws_elems, st));
+  k_hermitize<<<g2, b2, 0, st>>>(ws->A, n);
+  PW_TRY(pw_heev_lowest(ws, n, nb, ws->A, ws->lam, ws->Y, st));
+  PW_CUDA(cudaMemcpyAsync(theta, ws->lam, nb * 8, cudaMemcpyDeviceToDevice, st));
+  // C = d o (Linv^H Y)
+  PW_TRY(pw_zgemm('C', 'N', n, nb, n, one, ws->Linv, n, ws->Y, n, zero, C, n, ws->gemm_ws,
+                  ws->gemm_ws_elems, st));
+  k_scale_rows_real<<<(unsigned)(((long)n * nb + 255) / 256), 256, 0, st>>>(C, n, n, nb, ws->dscale);
+  return pw_check_launch("rayleigh_ritz");
+}

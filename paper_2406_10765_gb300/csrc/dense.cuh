@@ -1,0 +1,47 @@
+// FP64 dense linear algebra of the Rayleigh-Ritz step, on the GPU.
+#pragma once
+#include "pw_internal.cuh"
+
+// Workspace for Rayleigh-Ritz problems up to order nmax with up to nbmax wanted pairs.
+struct pw_dense_ws {
+  int nmax = 0, nbmax = 0;
+  double2 *G = nullptr, *A = nullptr, *T = nullptr, *Linv = nullptr;  // nmax^2 each
+  double2 *Y = nullptr;       // nmax x nbmax
+  double *dscale = nullptr;   // nmax
+  double *piv = nullptr;      // nmax
+  int *flag = nullptr;        // device status words
+  // tridiagonal eigensolver
+  double *d = nullptr, *e = nullptr, *lam = nullptr;  // nmax
+  double2 *tau = nullptr;                             // nmax
+  double2 *p = nullptr, *w = nullptr;                 // nmax
+  double2 *part = nullptr;                            // hemv partial sums
+  double *Z = nullptr, *W = nullptr, *U = nullptr;    // nmax^2 real
+  double *Ds = nullptr, *zs = nullptr, *DK = nullptr, *zK = nullptr, *tauK = nullptr,
+         *zh = nullptr, *lamK = nullptr, *dD = nullptr, *lnew = nullptr;
+  int *perm = nullptr, *colK = nullptr, *orig = nullptr, *dcol = nullptr, *src = nullptr;
+  int *nodes = nullptr;       // per-level node tables (lo, mid, hi) for nmax
+  int *knode = nullptr;       // per node: nondeflated count
+  double *rhonode = nullptr;
+  double2 *gemm_ws = nullptr; size_t gemm_ws_elems = 0;
+  // host side tree for the current n
+  int tree_n = -1;
+  std::vector<std::vector<int>> levels;   // per level: flat (lo, mid, hi) triples
+  std::vector<int> level_off;             // offset of each level in `nodes` (in triples)
+  int max_level_nodes = 0;
+  size_t bytes = 0;
+};
+
+pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax);
+void pw_dense_free(pw_dense_ws *ws);
+
+// Lowest nb Ritz pairs of the pencil (A, G), both n x n Hermitian (device,
+// ld n).  theta: device nb doubles; C: device n x nb (ld n) coefficients.
+// *chol_ok (host) = 0 on a Cholesky breakdown (pivot <= tol * max pivot).
+pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, const double2 *A,
+                           double *theta, double2 *C, int *chol_ok, cudaStream_t st);
+
+// Hermitian eigensolver: lowest nb eigenpairs of the n x n matrix A (device,
+// destroyed).  lam: device n doubles (all eigenvalues, ascending); Y: device
+// n x nb (ld n) eigenvectors.
+pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam, double2 *Y,
+                         cudaStream_t st);

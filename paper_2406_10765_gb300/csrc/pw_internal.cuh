@@ -1,0 +1,105 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <vector>
+
+#include "pw.h"
+
+#define PW_CUDA(call)                                                   \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) {                                            \
+      pw_last_cuda_error(e_, __FILE__, __LINE__);                       \
+      return PW_ERR_CUDA;                                               \
+    }                                                                   \
+  } while (0)
+
+#define PW_TRY(call)                                                    \
+  do {                                                                  \
+    pw_status s_ = (call);                                              \
+    if (s_ != PW_OK) return s_;                                         \
+  } while (0)
+
+void pw_last_cuda_error(cudaError_t e, const char *file, int line);
+pw_status pw_check_launch(const char *what);
+
+// --------------------------------------------------------------------------
+// complex helpers (double2 / float2)
+// --------------------------------------------------------------------------
+template <typename T> struct cpx_t;
+template <> struct cpx_t<double> { typedef double2 type; };
+template <> struct cpx_t<float> { typedef float2 type; };
+
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b) {  // conj(a) * b
+  C r; r.x = a.x * b.x + a.y * b.y; r.y = a.x * b.y - a.y * b.x; return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) {
+  C r; r.x = a.x + b.x; r.y = a.y + b.y; return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) {
+  C r; r.x = a.x - b.x; r.y = a.y - b.y; return r;
+}
+
+// --------------------------------------------------------------------------
+// the cell
+// --------------------------------------------------------------------------
+#define PW_MAX_PASSES 12
+
+struct pw_fft_axis {
+  int n;
+  int npass;
+  int radix[PW_MAX_PASSES];
+  double2 *tw64;   // device, n entries exp(-2 pi i k / n)
+  float2 *tw32;
+};
+
+struct pw_cell {
+  int precision;
+  double L[3];
+  int N[3];
+  double ecut, vwidth, pwidth;
+  int natom, nproj, npw, ncol;
+  int mxmax;                 // x-extent of the sphere: mx in [-mxmax, mxmax]
+  std::vector<int> m_host;   // npw*3
+  std::vector<double> tau_host, depth_host, dkb_host;
+  // device tables
+  int *d_gcol = nullptr;      // npw: column index of each plane wave
+  int *d_gz = nullptr;        // npw: mz mod Nz
+  int *d_colstart = nullptr;  // ncol+1: first plane wave of each column
+  int *d_colxy = nullptr;     // ncol: (my mod Ny) * Nx + (mx mod Nx)
+  double *d_kin = nullptr;    // npw: 1/2 |G|^2
+  double *d_V = nullptr;      // Nz*Ny*Nx real potential, index (z*Ny + y)*Nx + x
+  float *d_Vf = nullptr;
+  double2 *d_beta = nullptr;  // npw x nproj (ld = npw)
+  double *d_D = nullptr;      // nproj
+  pw_fft_axis ax[3];
+  // apply_H workspace (grown on demand)
+  void *d_z = nullptr; size_t z_bytes = 0;
+  double2 *d_B = nullptr; size_t B_elems = 0;   // nproj x nb projections
+  double2 *d_gemm_ws = nullptr; size_t gemm_ws_elems = 0;
+  size_t bytes = 0;
+  // mixed-precision operand store for beta (split BF16), built on first use
+  void *d_beta_split = nullptr; size_t beta_split_bytes = 0;
+};
+
+// apply_H pieces
+pw_status pw_apply_local(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
+                         int precision, cudaStream_t st);
+pw_status pw_apply_nonlocal(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
+                            int precision, cudaStream_t st);
+
+// dense complex FP64 GEMM: C = alpha op(A) op(B) + beta C, column-major.
+// opA: 'N' (A is m x k) or 'C' (A is k x m, conjugate-transposed);
+// opB: 'N' (B is k x n) or 'C' (B is n x k, conjugate-transposed).
+pw_status pw_zgemm(char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
+                   int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc,
+                   double2 *ws, size_t ws_elems, cudaStream_t st);
+size_t pw_zgemm_ws_elems(int m, int n, int k);
+
+// grow a device buffer
+pw_status pw_ensure(void **ptr, size_t *cur_bytes, size_t need_bytes);

@@ -1,0 +1,106 @@
+"""H psi on the GPU against the oracle (Sec. II-A Eq. 1 operator; FFT local
+term of Sec. II-B, nonlocal term of Sec. III-A)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import pw_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_util import cells, to_dev, rel  # noqa: E402
+
+
+def _run(lib, x, ld=None):
+    import paper_2406_10765_gb300 as pw
+    psi = to_dev(x, ld)
+    npw, nb = x.shape
+    if ld is None:
+        out = pw.new_block(npw, nb)
+    else:
+        out = torch.zeros((nb, ld), dtype=torch.complex128, device="cuda").T
+    pw.pw_apply_H(lib.h, psi, out)
+    torch.cuda.synchronize()
+    return out[:npw].cpu().numpy()
+
+
+@pytest.mark.parametrize("species,n,ecut,nb", [("Si", 1, 10.0, 24), ("C", 1, 8.0, 37), ("Si", 1, 4.0, 5)])
+def test_apply_h_fp64_matches_oracle(species, n, ecut, nb):
+    lib, orc, _ = cells(species, n, ecut)
+    assert lib.npw == orc.npw and np.array_equal(lib.m, orc.m) and lib.grid == orc.Ns
+    x = synth.draw_x0(3, 8 * n ** 3, orc.npw, nb)
+    got = _run(lib, x)
+    assert rel(got, O.apply_H(orc, x)) < 1e-12
+
+
+def test_apply_h_padded_ld_and_ragged_batch():
+    lib, orc, _ = cells("Si", 1, 10.0)
+    x = synth.draw_x0(4, 8, orc.npw, 83)       # more bands than one L2 batch? no: ragged tiles
+    got = _run(lib, x, ld=orc.npw + 13)
+    assert rel(got, O.apply_H(orc, x)) < 1e-12
+
+
+def test_apply_h_orthorhombic_odd_grid():
+    import paper_2406_10765_gb300 as pw
+    Ls = np.array([9.0, 11.0, 7.5])
+    tau = np.array([[0.5, 1.0, 2.0], [4.0, 6.0, 5.0], [8.0, 2.0, 1.0]])
+    depth = np.array([-1.0, -0.95, -1.05])
+    dkb = np.array([[0.7, 0.9, 1.1, 1.3], [0.6, 0.8, 1.0, 1.2], [1.4, 0.5, 0.9, 1.0]])
+    grid = (18, 27, 16)
+    lib = pw.Cell(Ls, tau, depth, dkb, 6.0, grid=grid)
+    orc = O.make_cell(Ls, tau, depth, dkb, 6.0, grid=grid)
+    assert lib.npw == orc.npw and np.array_equal(lib.m, orc.m)
+    x = synth.draw_x0(5, 3, orc.npw, 7)
+    assert rel(_run(lib, x), O.apply_H(orc, x)) < 1e-12
+
+
+def test_apply_h_mixed_precision_error():
+    lib, orc, _ = cells("Si", 1, 10.0, precision="mixed")
+    x = synth.draw_x0(6, 8, orc.npw, 16)
+    err = rel(_run(lib, x), O.apply_H(orc, x))
+    assert err < 1e-5
+
+
+def test_apply_h_si512_sampled_bands():
+    # full-size cell (npw 104,415, grid 96^3) in the bench launch shape, with
+    # a band block spanning several L2 batches; sampled bands vs the oracle
+    lib, orc, ci = cells("Si", 4, 10.0)
+    assert lib.npw == 104415 and lib.grid == (96, 96, 96)
+    nb = 40
+    x = synth.draw_x0(0, 512, orc.npw, nb)
+    got = _run(lib, x)
+    for j in [0, 17, 39]:
+        ref = O.apply_H(orc, x[:, j:j + 1])[:, 0]
+        assert rel(got[:, j], ref) < 1e-12
+
+
+def test_supercell_folding_on_gpu():
+    # eigenvector of the 8-atom cell folded into the 64-atom cell is an
+    # eigenvector of the GPU operator with the same eigenvalue
+    import paper_2406_10765_gb300 as pw
+    small = synth.periodic_depths("Si", 1, 3)
+    big = synth.periodic_depths("Si", 2, 3)
+    cs = O.make_cell(small["L"], small["tau"], small["depth"], small["dkb"], 10.0)
+    w, v = O.dense_eigs(cs, 4)
+    lib = pw.Cell(big["L"], big["tau"], big["depth"], big["dkb"], 10.0)
+    index = {tuple(mm): i for i, mm in enumerate(lib.m)}
+    c = np.zeros((lib.npw, 4), complex)
+    for i, mm in enumerate(cs.m):
+        c[index[tuple(2 * mm)], :] = v[i, :]
+    got = _run(lib, c)
+    assert np.abs(got - c * w[None, :]).max() < 1e-12
+
+
+def test_apply_h_argument_errors():
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("C", 1, 8.0)
+    x = to_dev(synth.draw_x0(1, 8, orc.npw, 2))
+    y = torch.empty_like(x)
+    # nb = 0 is a no-op; ld < npw is rejected
+    import ctypes as ct
+    from paper_2406_10765_gb300 import binding as B
+    st = B._stream(None)
+    assert B._apply(lib.h, B._dptr(x), orc.npw, 0, B._dptr(y), st) == 0
+    assert B._apply(lib.h, B._dptr(x), orc.npw - 1, 2, B._dptr(y), st) == B.PW_ERR_ARG
+    assert B._apply(lib.h, ct.c_void_p(), orc.npw, 2, B._dptr(y), st) == B.PW_ERR_ARG
