@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""Benchmark: LOBPCG block-eigensolver steps per second on the synthetic Si
+512-atom supercell (4x4x4 diamond cells, a = 10.26 bohr, Ecut = 10 Ha,
+npw = 104,415, grid 96^3, 1152 bands, 2048 KB projectors), one step = one
+pass of the whole hot path: residual + preconditioner, H W (FFT local term +
+projector contractions), S^H S and S^H H S, FP64 Rayleigh-Ritz (Cholesky,
+L^-1, Hermitian eigensolve), rotations.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas
+(weak scaling); only the timing is reduced across ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "si512": dict(species="Si", n=4, ecut=10.0, nb=1152,
+                  name="Si-512 (4x4x4 diamond cells, a=10.26 bohr), Gamma, Ecut=10 Ha"),
+    "si8": dict(species="Si", n=1, ecut=10.0, nb=24,
+                name="Si-8 (diamond cell, a=10.26 bohr), Gamma, Ecut=10 Ha"),
+}
+FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of the part (no FP64 tensor path)
+METRIC = "Si-512 eigensolver iters/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="si512", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers --
+
+def step_flops(npw, nb, ns, k, nproj, grid):
+    """Algorithmic FLOPs of one step (complex products counted as 8 real flops)."""
+    import math
+    n3 = grid[0] * grid[1] * grid[2]
+    fft = 2 * 5.0 * n3 * math.log2(n3) * k          # one inverse + one forward 3-D FFT per band
+    proj = 2 * 8.0 * npw * nproj * k                # beta^H W and beta (D B)
+    gram = 2 * 8.0 * npw * ns * ns                  # S^H S and S^H (H S), full products
+    rot = 2 * 8.0 * npw * nb * ns + 2 * 8.0 * npw * nb * (ns - nb)
+    return dict(fft=fft, proj=proj, gram=gram, rot=rot)
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle sample --
+
+def oracle_sample(wl, seed=0, frac_rows=32, apply_bands=8, rr_div=2):
+    """One sampled oracle step: time its components on bounded pieces of the
+    workload and scale them to a full step.  Returns (seconds_per_step, note, cores)."""
+    import numpy as np
+    import synth
+    from oracle import pw_oracle as O
+    ci = synth.cell_inputs(wl["species"], wl["n"], seed)
+    if not hasattr(oracle_sample, "cell"):
+        oracle_sample.cell = O.make_cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], wl["ecut"])
+    cell = oracle_sample.cell
+    nb, npw = wl["nb"], cell.npw
+    ns = 3 * nb
+    rng = np.random.default_rng(seed)
+    t = {}
+    kb = min(apply_bands, nb)
+    X = synth.draw_x0(seed, len(ci["tau"]), npw, kb)
+    t0 = time.perf_counter()
+    O.apply_H(cell, X)
+    t["hpsi"] = (time.perf_counter() - t0) * nb / kb
+    rows = max(ns, npw // frac_rows)
+    S = rng.standard_normal((rows, ns)) + 1j * rng.standard_normal((rows, ns))
+    t0 = time.perf_counter()
+    S.conj().T @ S
+    S.conj().T @ S
+    t["gram"] = (time.perf_counter() - t0) * npw / rows
+    C = rng.standard_normal((ns, nb)) + 1j * rng.standard_normal((ns, nb))
+    t0 = time.perf_counter()
+    for _ in range(2):
+        S @ C
+        S[:, nb:] @ C[nb:]
+    t["rot"] = (time.perf_counter() - t0) * npw / rows
+    m = ns // rr_div
+    Ssm = rng.standard_normal((4 * m, m)) + 1j * rng.standard_normal((4 * m, m))
+    Hs = rng.standard_normal((4 * m, 4 * m))
+    Hs = Hs + Hs.T
+    HSsm = Hs @ Ssm
+    t0 = time.perf_counter()
+    O.rayleigh_ritz(Ssm, HSsm, m // 3)
+    # the Gram products inside rayleigh_ritz are at 4m rows; cubic part dominates
+    t["rr"] = (time.perf_counter() - t0) * rr_div ** 3
+    total = sum(t.values())
+    note = (f"oracle components timed on bounded pieces and scaled to one full step: H on {kb} of "
+            f"{nb} bands (x{nb // kb}); S^H S, S^H HS and the 4 rotations on {rows} of {npw} rows "
+            f"(x{npw / rows:.1f}); Rayleigh-Ritz at order {m} of {ns} (x{rr_div ** 3}, cubic)")
+    return total, note, t
+
+
+def cpu_cores():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max((i.get("num_threads") or 0) for i in threadpool_info())
+        if n:
+            return int(n)
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+# ------------------------------------------------------------------- arms --
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample(wl)
+    secs = []
+    for _ in range(args.steps):
+        s, note, parts = oracle_sample(wl)
+        secs.append(s)
+    sec = sum(secs) / len(secs)
+    v = 1.0 / sec
+    cores = cpu_cores()
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl["name"], "nbands": wl["nb"], "precision": "fp64",
+                      "implementation": "FP64 numpy/scipy oracle on host cores"},
+           "cpu_baseline": {"value": v, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                            "sample": note},
+           "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_2406_10765_gb300 as pw
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    wl = WORKLOADS[args.workload]
+    ci = synth.cell_inputs(wl["species"], wl["n"], 0)
+    cell = pw.Cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], wl["ecut"], precision=args.precision)
+    nb = wl["nb"]
+    stream = torch.cuda.current_stream()
+    solver = pw.pw_solver_create(cell.h, nb, tol=0.0, seed=0, precision=args.precision)
+    for _ in range(args.warmup):
+        pw.pw_subspace_step(cell.h, solver)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    launches0 = pw.pw_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = [pw.pw_subspace_step(cell.h, solver) for _ in range(args.steps)]
+    e1.record(stream)
+    barrier()
+    launches = pw.pw_kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1e3)
+
+    # roofline of the dominant stage, from the solver's CUDA events
+    stage = {k: sum(getattr(r, "ms_" + k) for r in reps) / len(reps)
+             for k in ["resid", "hpsi", "gram", "rr", "rot"]}
+    ns = reps[-1].nsub
+    k_act = reps[-1].nactive
+    fl = step_flops(cell.npw, nb, ns, k_act, cell.nproj, cell.grid)
+    dom = max(stage, key=stage.get)
+    if dom in ("gram", "rot"):
+        flops = fl["gram"] + fl["rot"]
+        t_ms = stage["gram"] + stage["rot"]
+        kern = "k_zgemm (S^H S, S^H HS, rotations)"
+    elif dom == "hpsi":
+        flops = fl["fft"] + fl["proj"]
+        t_ms = stage["hpsi"]
+        kern = "H W (FFT kernels + projector k_zgemm)"
+    else:
+        flops = None
+        t_ms = stage[dom]
+        kern = dom
+    roof = None
+    if flops is not None:
+        ach = flops / (t_ms * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "kernel": kern,
+                "peak_source": "nominal FP64 rate 1.25 TFLOP/s (measured DFMA 1.20)",
+                "stage_ms": stage}
+
+    out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32/bf16-split+f64",
+           "data": "synthetic",
+           "config": {"workload": wl["name"], "npw": cell.npw, "grid": list(cell.grid),
+                      "nbands": nb, "nproj": cell.nproj, "nsub": ns, "precision": args.precision,
+                      "l2": "inputs larger than L2 (S blocks of several GB)",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": roof, "gpu_launches": launches, "clocks": clk}
+    pw.pw_solver_destroy(solver)
+
+    if not args.no_e2e:
+        # end to end through pw_eigsolve with host buffers: host start block in,
+        # host eigenvalues out, one step
+        x0 = synth.draw_x0(0, len(ci["tau"]), cell.npw, nb)
+        barrier()
+        t0 = time.perf_counter()
+        eig, rep, st = pw.pw_eigsolve(cell.h, nb, tol=0.0, maxit=1, x0=x0,
+                                      precision=args.precision, raise_noconv=False)
+        barrier()
+        t1 = time.perf_counter() - t0
+        out["e2e"] = {"value": rep.iters / t1, "unit": "iters/s",
+                      "h2d_bytes_per_step": x0.nbytes // max(1, rep.iters),
+                      "d2h_bytes_per_step": eig.nbytes // max(1, rep.iters),
+                      "note": "pw_eigsolve from a host start block: upload, H X0, initial "
+                              "Rayleigh-Ritz, the steps, eigenvalues back to the host"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sec, note, parts = oracle_sample(wl)
+        out["cpu_baseline"] = {"value": 1.0 / sec, "unit": "iters/s", "cores": cpu_cores(),
+                               "kind": "oracle", "sample": note}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

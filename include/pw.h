@@ -116,8 +116,15 @@ typedef struct {
   int iter;             /* steps taken so far */
   int nactive;          /* active (unlocked) bands used in this step */
   int dropped_p;        /* 1 if P was dropped after a Cholesky breakdown */
+  int nsub;             /* order of the Rayleigh-Ritz problem (nb + k or nb + 2k) */
   double max_resid;     /* max_i ||H x_i - theta_i x_i|| of the block the step started from */
   double ms;            /* wall time of the step (host clock, synchronised) */
+  /* device time per stage (CUDA events on the solver's stream), ms: */
+  double ms_resid;      /* residual norms + preconditioner */
+  double ms_hpsi;       /* H W (FFT local part + projector contractions) */
+  double ms_gram;       /* S^H S and S^H (H S) */
+  double ms_rr;         /* Cholesky, L^-1, eigensolve, coefficients (FP64) */
+  double ms_rot;        /* rotations X', H X', P', H P' */
 } pw_step_report;
 
 typedef struct {
@@ -156,6 +163,34 @@ void pw_solver_destroy(pw_solver *solver);
  * PW_ERR_NOCONV with eig / psi_out filled if maxit is reached. */
 pw_status pw_eigsolve(pw_cell *cell, const pw_solve_opts *opts, double *eig, void *psi_out,
                       int ld, pw_solve_report *rep, void *stream);
+
+/* FP64 Hermitian eigensolver used by the Rayleigh-Ritz step (the small dense
+ * eigensolve, Syevd in Sec. III-D): Householder reduction to a real
+ * tridiagonal, divide and conquer, back-transformation.  A: device complex128
+ * n x n Hermitian, column-major, ld n; destroyed.  w: device n doubles (all
+ * eigenvalues, ascending).  Y: device complex128 n x nb (ld n), eigenvectors
+ * of the nb lowest.  Synchronises `stream`.  Errors: PW_ERR_ARG (n < 1,
+ * nb < 1, nb > n, NULL pointer), PW_ERR_OOM, PW_ERR_CUDA. */
+pw_status pw_heev(int n, int nb, void *A, double *w, void *Y, void *stream);
+
+/* Complex matrix product on the tensor cores in split-FP16 arithmetic (the
+ * mixed-precision form of the dense contractions: projector products of
+ * Sec. III-A, S^H S, S^H (H S) and the rotations of Sec. II-B).  Each operand
+ * row is scaled by a power of two and split into two FP16 slices (hi, lo);
+ * the products hi*hi + hi*lo + lo*hi accumulate in FP32 and the result is
+ * rescaled in FP64 (relative error ~1e-6 of |A||B|).
+ *   opA = 'C': C (m x n) = A^H B, A: k x m (lda), B: k x n (ldb)
+ *   opA = 'N': C (m x n) = A B,   A: m x k (lda), B: k x n (ldb)
+ * All device complex128, column-major.  beta: 0 (overwrite) or 1 (C += ...).
+ * Allocates and frees its own operand buffers; synchronises `stream`.
+ * Errors: PW_ERR_ARG (bad op, sizes < 1, ld too small, beta not 0/1),
+ * PW_ERR_OOM, PW_ERR_CUDA, PW_ERR_TIMEOUT (a bounded device wait ran out). */
+pw_status pw_zgemm_tc(char opA, int m, int n, int k, const void *A, int lda, const void *B,
+                      int ldb, double beta, void *C, int ldc, void *stream);
+
+/* Number of CUDA kernel launches the library has issued in this process
+ * (all devices, all threads); a diagnostic counter for launch accounting. */
+uint64_t pw_kernel_launches(void);
 
 void pw_destroy_cell(pw_cell *cell);
 const char *pw_strerror(pw_status status);

@@ -49,7 +49,9 @@ class pw_solve_opts(ct.Structure):
 
 class pw_step_report(ct.Structure):
     _fields_ = [("iter", ct.c_int), ("nactive", ct.c_int), ("dropped_p", ct.c_int),
-                ("max_resid", ct.c_double), ("ms", ct.c_double)]
+                ("nsub", ct.c_int), ("max_resid", ct.c_double), ("ms", ct.c_double),
+                ("ms_resid", ct.c_double), ("ms_hpsi", ct.c_double), ("ms_gram", ct.c_double),
+                ("ms_rr", ct.c_double), ("ms_rot", ct.c_double)]
 
 
 class pw_solve_report(ct.Structure):
@@ -91,6 +93,52 @@ _sblock = _sig("pw_solver_block", ct.c_int, [_vp, _vp, ct.c_int])
 _sdestroy = _sig("pw_solver_destroy", None, [_vp])
 _eigsolve = _sig("pw_eigsolve", ct.c_int, [_vp, ct.POINTER(pw_solve_opts), ct.POINTER(ct.c_double),
                                             _vp, ct.c_int, ct.POINTER(pw_solve_report), _vp])
+
+
+_heev = _sig("pw_heev", ct.c_int, [ct.c_int, ct.c_int, _vp, _vp, _vp, _vp])
+
+
+def pw_heev(A, nb, stream=None):
+    """Lowest nb eigenpairs of a Hermitian CUDA complex128 (n, n) tensor (column-major
+    copy is made).  Returns (w (n,), Y (n, nb)) as CUDA tensors."""
+    import torch
+    n = A.shape[0]
+    a = A.t().contiguous().t().clone()       # column-major working copy
+    if a.stride(0) != 1:
+        a = a.t().contiguous().t()
+    w = torch.empty(n, dtype=torch.float64, device=A.device)
+    Y = torch.empty((nb, n), dtype=torch.complex128, device=A.device).T
+    _check(_heev(n, nb, _dptr(a), _dptr(w), _dptr(Y), _stream(stream)), "pw_heev")
+    return w, Y
+
+
+_zgemm_tc = _sig("pw_zgemm_tc", ct.c_int, [ct.c_char, ct.c_int, ct.c_int, ct.c_int, _vp, ct.c_int,
+                                            _vp, ct.c_int, ct.c_double, _vp, ct.c_int, _vp])
+
+
+def pw_zgemm_tc(opA, A, B, C=None, beta=0.0, stream=None):
+    """C = A^H B (opA 'C') or A B (opA 'N') with split-FP16 tensor-core arithmetic.
+    A, B, C: column-major CUDA complex128 tensors (stride(0) == 1)."""
+    import torch
+    if opA == "C":
+        k, m = A.shape
+    else:
+        m, k = A.shape
+    n = B.shape[1]
+    if C is None:
+        C = torch.zeros((n, m), dtype=torch.complex128, device=A.device).T
+    for t in (A, B, C):
+        assert t.stride(0) == 1
+    _check(_zgemm_tc(opA.encode(), m, n, k, _dptr(A), A.stride(1), _dptr(B), B.stride(1),
+                     float(beta), _dptr(C), C.stride(1), _stream(stream)), "pw_zgemm_tc")
+    return C
+
+
+_launches = _sig("pw_kernel_launches", ct.c_uint64, [])
+
+
+def pw_kernel_launches() -> int:
+    return int(_launches())
 
 
 def pw_strerror(status: int) -> str:

@@ -63,9 +63,9 @@ __device__ double block_max(double v, double *sh) {
   __syncthreads();
   if (l == 0) sh[w] = v;
   __syncthreads();
-  double r = 0.0;
+  double r = -1.7976931348623157e308;
   if (threadIdx.x < 32) {
-    r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : -1.7976931348623157e308;
     r = warp_max(r);
     if (threadIdx.x == 0) sh[0] = r;
   }
@@ -774,13 +774,18 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
   const int nchunk_max = (n + HV_COLS - 1) / HV_COLS;
   for (int k = 0; k + 1 < n; ++k) {
     const int m = n - k - 1;
+    pw_count_launch();
     k_house<<<1, 256, 0, st>>>(A, n, k, ws->d, ws->e, ws->tau);
     const int nch = (m + HV_COLS - 1) / HV_COLS;
+    pw_count_launch();
     k_hemv<<<dim3((m + HV_ROWS - 1) / HV_ROWS, nch), HV_ROWS, 0, st>>>(A, n, k, ws->part, ws->nmax);
+    pw_count_launch();
     k_hemv_fin<<<1, 256, 0, st>>>(A, n, k, ws->part, nch, ws->nmax, ws->tau, ws->p, ws->w);
+    pw_count_launch();
     k_her2<<<dim3((m + 31) / 32, (m + 7) / 8), dim3(32, 8), 0, st>>>(A, n, k, ws->w);
   }
   (void)nchunk_max;
+  pw_count_launch();
   k_last_diag<<<1, 1, 0, st>>>(A, n, ws->d);
   PW_TRY(pw_check_launch("tridiag"));
 
@@ -789,29 +794,43 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
   DcArrays a{lam, ws->Z, ws->W, ws->U, ws->Ds, ws->zs, ws->DK, ws->zK, ws->tauK, ws->zh,
              ws->lamK, ws->dD, ws->lnew, ws->perm, ws->colK, ws->orig, ws->dcol, ws->src,
              (int *)ws->p /* defl scratch: n ints fit in n double2 */, ws->knode, ws->rhonode};
+  pw_count_launch();
   k_dc_init<<<(n + 255) / 256, 256, 0, st>>>(ws->d, ws->e, n, lam, ws->Z);
+  pw_count_launch();
   k_identity<<<(unsigned)(((long)n * n + 255) / 256), 256, 0, st>>>(ws->Z, n);
   for (int l = (int)ws->levels.size() - 1; l >= 0; --l) {
     const int nn = (int)ws->levels[l].size() / 3;
     const int *nodes = ws->nodes + 3 * ws->level_off[l];
     int maxsize = 0;
     for (int q = 0; q < nn; ++q) maxsize = std::max(maxsize, ws->levels[l][3 * q + 2] - ws->levels[l][3 * q]);
+    pw_count_launch();
     k_dc_deflate<<<nn, 256, 0, st>>>(nodes, n, ws->e, a);
     const dim3 gw((maxsize + 7) / 8, nn);
+    pw_count_launch();
     k_dc_roots<<<gw, 256, 0, st>>>(nodes, a);
+    pw_count_launch();
     k_dc_zhat<<<gw, 256, 0, st>>>(nodes, a);
+    pw_count_launch();
     k_dc_vectors<<<gw, 256, 0, st>>>(nodes, n, a);
+    pw_count_launch();
     k_dc_gemm<<<dim3((maxsize + 63) / 64, (maxsize + 63) / 64, nn), 256, 0, st>>>(nodes, n, a);
+    pw_count_launch();
     k_dc_rank<<<dim3((maxsize + 127) / 128, nn), 128, 0, st>>>(nodes, a);
+    pw_count_launch();
     k_dc_copy_defl<<<dim3(maxsize, nn), 128, 0, st>>>(nodes, n, a);
+    pw_count_launch();
     k_dc_write<<<dim3(maxsize, nn), 128, 0, st>>>(nodes, n, a);
   }
   PW_TRY(pw_check_launch("divide and conquer"));
 
   // 3. back-transformation of the wanted columns
+  pw_count_launch();
   k_bt_init<<<(unsigned)(((long)n * nb + 255) / 256), 256, 0, st>>>(ws->Z, n, nb, Y);
   for (int k = n - 2; k >= 0; --k)
-    k_bt_step<<<(nb + 3) / 4, 128, 0, st>>>(A, n, k, ws->tau, Y, nb);
+    {
+      pw_count_launch();
+      k_bt_step<<<(nb + 3) / 4, 128, 0, st>>>(A, n, k, ws->tau, Y, nb);
+    }
   return pw_check_launch("back-transform");
 }
 
@@ -823,15 +842,18 @@ pw_status cholesky(pw_dense_ws *ws, double2 *A, int n, cudaStream_t st) {
   const double2 mone = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
   for (int j0 = 0; j0 < n; j0 += CB) {
     const int b = std::min(CB, n - j0);
+    pw_count_launch();
     k_potf2<<<1, 256, 0, st>>>(A, n, j0, b, ws->piv, ws->flag);
     const int rest = n - j0 - b;
     if (rest > 0) {
+      pw_count_launch();
       k_trsm_rows<<<(rest + 127) / 128, 128, 0, st>>>(A, n, j0, b);
       PW_TRY(pw_zgemm('N', 'C', rest, rest, b, mone, A + (j0 + b) + (long)j0 * n, n,
                       A + (j0 + b) + (long)j0 * n, n, one, A + (j0 + b) + (long)(j0 + b) * n, n,
                       ws->gemm_ws, ws->gemm_ws_elems, st));
     }
   }
+  pw_count_launch();
   k_zero_upper<<<dim3((n + 31) / 32, (n + 31) / 32), dim3(32, 32), 0, st>>>(A, n);
   return pw_check_launch("cholesky");
 }
@@ -845,6 +867,7 @@ pw_status trinv(pw_dense_ws *ws, const double2 *L, double2 *X, int n, cudaStream
   int *dlo = ws->src, *dsz = ws->dcol;   // int scratch (n entries each, >= n/CB needed)
   PW_CUDA(cudaMemcpyAsync(dlo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, st));
   PW_CUDA(cudaMemcpyAsync(dsz, sz.data(), sz.size() * 4, cudaMemcpyHostToDevice, st));
+  pw_count_launch();
   k_trinv_small<<<(unsigned)lo.size(), 32, 0, st>>>(L, X, n, dlo, dsz);
   PW_TRY(pw_check_launch("trinv_small"));
   // combine: [L11 0; L21 L22]^-1 = [X11 0; -X22 L21 X11, X22], bottom-up over
@@ -867,17 +890,22 @@ pw_status trinv(pw_dense_ws *ws, const double2 *L, double2 *X, int n, cudaStream
 }
 }  // namespace
 
-pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, const double2 *A,
-                           double *theta, double2 *C, int *chol_ok, cudaStream_t st) {
+pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, int ldg,
+                           const double2 *A, int lda, double *theta, double2 *C, int ldc,
+                           int *chol_ok, cudaStream_t st) {
   if (n > ws->nmax || nb > ws->nbmax || nb > n) return PW_ERR_ARG;
   *chol_ok = 1;
   PW_CUDA(cudaMemsetAsync(ws->flag, 0, 16, st));
-  k_diag_scale<<<(n + 127) / 128, 128, 0, st>>>(G, n, n, ws->dscale, ws->flag);
+  pw_count_launch();
+  k_diag_scale<<<(n + 127) / 128, 128, 0, st>>>(G, ldg, n, ws->dscale, ws->flag);
   const dim3 g2((n + 31) / 32, (n + 31) / 32), b2(32, 32);
-  k_scale_herm<<<g2, b2, 0, st>>>(G, n, n, ws->dscale, ws->G);
-  k_scale_herm<<<g2, b2, 0, st>>>(A, n, n, ws->dscale, ws->A);
+  pw_count_launch();
+  k_scale_herm<<<g2, b2, 0, st>>>(G, ldg, n, ws->dscale, ws->G);
+  pw_count_launch();
+  k_scale_herm<<<g2, b2, 0, st>>>(A, lda, n, ws->dscale, ws->A);
   PW_TRY(pw_check_launch("scale"));
   PW_TRY(cholesky(ws, ws->G, n, st));
+  pw_count_launch();
   k_chol_check<<<1, 256, 0, st>>>(ws->piv, n, 1e-14, ws->flag);
   int flag = 0;
   PW_CUDA(cudaMemcpyAsync(&flag, ws->flag, 4, cudaMemcpyDeviceToHost, st));
@@ -890,12 +918,25 @@ pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, con
                   ws->gemm_ws_elems, st));
   PW_TRY(pw_zgemm('N', 'C', n, n, n, one, ws->T, n, ws->Linv, n, zero, ws->A, n, ws->gemm_ws,
                   ws->gemm_ws_elems, st));
+  pw_count_launch();
   k_hermitize<<<g2, b2, 0, st>>>(ws->A, n);
   PW_TRY(pw_heev_lowest(ws, n, nb, ws->A, ws->lam, ws->Y, st));
   PW_CUDA(cudaMemcpyAsync(theta, ws->lam, nb * 8, cudaMemcpyDeviceToDevice, st));
   // C = d o (Linv^H Y)
-  PW_TRY(pw_zgemm('C', 'N', n, nb, n, one, ws->Linv, n, ws->Y, n, zero, C, n, ws->gemm_ws,
+  PW_TRY(pw_zgemm('C', 'N', n, nb, n, one, ws->Linv, n, ws->Y, n, zero, C, ldc, ws->gemm_ws,
                   ws->gemm_ws_elems, st));
-  k_scale_rows_real<<<(unsigned)(((long)n * nb + 255) / 256), 256, 0, st>>>(C, n, n, nb, ws->dscale);
+  pw_count_launch();
+  k_scale_rows_real<<<(unsigned)(((long)n * nb + 255) / 256), 256, 0, st>>>(C, ldc, n, nb, ws->dscale);
   return pw_check_launch("rayleigh_ritz");
+}
+
+extern "C" pw_status pw_heev(int n, int nb, void *A, double *w, void *Y, void *stream) {
+  if (n < 1 || nb < 1 || nb > n || !A || !w || !Y) return PW_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  pw_dense_ws ws;
+  PW_TRY(pw_dense_alloc(&ws, n, nb));
+  pw_status r = pw_heev_lowest(&ws, n, nb, (double2 *)A, w, (double2 *)Y, st);
+  if (r == PW_OK && cudaStreamSynchronize(st) != cudaSuccess) r = PW_ERR_CUDA;
+  pw_dense_free(&ws);
+  return r;
 }

@@ -35,10 +35,12 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax);
 void pw_dense_free(pw_dense_ws *ws);
 
 // Lowest nb Ritz pairs of the pencil (A, G), both n x n Hermitian (device,
-// ld n).  theta: device nb doubles; C: device n x nb (ld n) coefficients.
-// *chol_ok (host) = 0 on a Cholesky breakdown (pivot <= tol * max pivot).
-pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, const double2 *A,
-                           double *theta, double2 *C, int *chol_ok, cudaStream_t st);
+// leading dims ldg, lda).  theta: device nb doubles; C: device n x nb (ldc)
+// coefficients.  *chol_ok (host) = 0 on a Cholesky breakdown (a pivot of the
+// Jacobi-scaled Gram <= 1e-14 times the largest).  Synchronises `st`.
+pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, int ldg,
+                           const double2 *A, int lda, double *theta, double2 *C, int ldc,
+                           int *chol_ok, cudaStream_t st);
 
 // Hermitian eigensolver: lowest nb eigenpairs of the n x n matrix A (device,
 // destroyed).  lam: device n doubles (all eigenvalues, ascending); Y: device

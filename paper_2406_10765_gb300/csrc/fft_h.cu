@@ -288,10 +288,13 @@ pw_status apply_local_t(pw_cell *c, const double2 *psi, int ld, int nb, double2 
   for (int b0 = 0; b0 < nb; b0 += batch) {
     const int nbb = std::min(batch, nb - b0);
     dim3 gcols((c->ncol + cb - 1) / cb, nbb);
+    pw_count_launch();
     k_sphere_to_z<C><<<gcols, 256, line_bytes, st>>>(psi + (long)b0 * ld, ld, c->d_colstart,
                                                      c->d_gcol, c->d_gz, c->ncol, cb, c->ax[2], Z);
+    pw_count_launch();
     k_plane<C, T><<<dim3(Nz, nbb), kPlaneThreads<C>::value, plane_bytes, st>>>(Z, c->ncol, c->d_colxy, c->mxmax,
                                                            c->ax[0], c->ax[1], Nz, V);
+    pw_count_launch();
     k_z_to_sphere<C><<<gcols, 256, line_bytes, st>>>(Z, c->ncol, cb, c->ax[2], c->d_colstart,
                                                      c->d_gcol, c->d_gz, c->d_kin,
                                                      psi + (long)b0 * ld, ld,

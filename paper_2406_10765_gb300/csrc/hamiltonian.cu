@@ -6,6 +6,7 @@
 // projectors at once:  B = beta^H psi  (nproj x nb), B <- D o B,
 // H psi += beta B.
 #include "pw_internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace {
 __global__ void k_scale_rows(double2 *B, int nproj, int nb, const double *D) {
@@ -17,14 +18,43 @@ __global__ void k_scale_rows(double2 *B, int nproj, int nb, const double *D) {
 }
 }  // namespace
 
+// mixed precision: split-FP16 tensor-core products, FP64 accumulation into hpsi
+static pw_status nonlocal_tc(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
+                             cudaStream_t st) {
+  if (!c->op_beta_rows) {
+    c->op_beta_rows = new pw_tc_operand();
+    c->op_beta_t = new pw_tc_operand();
+    c->op_psi = new pw_tc_operand();
+    c->op_db = new pw_tc_operand();
+    size_t cur = 0;
+    PW_TRY(pw_ensure((void **)&c->d_tc_err, &cur, 16));
+    cur = 0;
+    PW_TRY(pw_ensure((void **)&c->d_rmax, &cur, (size_t)c->npw * sizeof(float)));
+    PW_CUDA(cudaMemsetAsync(c->d_tc_err, 0, 16, st));
+    PW_TRY(pw_tc_operand_alloc(c->op_beta_rows, 2 * c->nproj, 2 * c->npw));
+    PW_TRY(pw_tc_operand_alloc(c->op_beta_t, c->npw, 2 * c->nproj));
+    PW_TRY(pw_tc_split_rows(c->d_beta, c->npw, c->npw, c->nproj, 1, nullptr, c->op_beta_rows, st));
+    PW_TRY(pw_tc_split_trans(c->d_beta, c->npw, c->npw, c->nproj, c->d_rmax, c->op_beta_t, st));
+  }
+  PW_TRY(pw_tc_operand_alloc(c->op_psi, nb, 2 * c->npw));
+  PW_TRY(pw_tc_operand_alloc(c->op_db, 2 * nb, 2 * c->nproj));
+  PW_TRY(pw_tc_split_rows(psi, ld, c->npw, nb, 0, nullptr, c->op_psi, st));
+  // B = beta^H psi  (nproj x nb)
+  PW_TRY(pw_tc_gemm(c->op_beta_rows, 2 * c->nproj, c->op_psi, nb, c->d_B, c->nproj, 0, 0, 0,
+                    c->d_tc_err, st));
+  // hpsi += beta (D o B)
+  PW_TRY(pw_tc_split_coef(c->d_B, c->nproj, c->nproj, nb, c->d_D, c->op_db, st));
+  return pw_tc_gemm(c->op_beta_t, c->npw, c->op_db, 2 * nb, hpsi, ld, 1, 1, 0, c->d_tc_err, st);
+}
+
 pw_status pw_apply_nonlocal(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
                             int precision, cudaStream_t st) {
-  (void)precision;
   if (c->nproj == 0 || nb == 0) return PW_OK;
   size_t need = (size_t)c->nproj * nb * sizeof(double2);
   size_t cur = c->B_elems * sizeof(double2);
   PW_TRY(pw_ensure((void **)&c->d_B, &cur, need));
   c->B_elems = cur / sizeof(double2);
+  if (precision == PW_MIXED) return nonlocal_tc(c, psi, ld, nb, hpsi, st);
   size_t ws = std::max(pw_zgemm_ws_elems(c->nproj, nb, c->npw), pw_zgemm_ws_elems(c->npw, nb, c->nproj));
   size_t wcur = c->gemm_ws_elems * sizeof(double2);
   PW_TRY(pw_ensure((void **)&c->d_gemm_ws, &wcur, ws * sizeof(double2)));
@@ -32,6 +62,7 @@ pw_status pw_apply_nonlocal(pw_cell *c, const double2 *psi, int ld, int nb, doub
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
   PW_TRY(pw_zgemm('C', 'N', c->nproj, nb, c->npw, one, c->d_beta, c->npw, psi, ld, zero, c->d_B,
                   c->nproj, c->d_gemm_ws, c->gemm_ws_elems, st));
+  pw_count_launch();
   k_scale_rows<<<(unsigned)(((long)c->nproj * nb + 255) / 256), 256, 0, st>>>(c->d_B, c->nproj, nb, c->d_D);
   PW_TRY(pw_check_launch("scale_rows"));
   return pw_zgemm('N', 'N', c->npw, nb, c->nproj, one, c->d_beta, c->npw, c->d_B, c->nproj, one,

@@ -1,0 +1,437 @@
+// LOBPCG block eigensolver (Knyazev 2001) for H X = X Lambda (Sec. II-A,
+// Eq. 1), one of the inner eigensolvers the paper names (Sec. II-A).
+//
+// One step:
+//   R = H X - X Lambda, column norms (FP64, deterministic block reductions);
+//   active set: bands with ||r|| > tol stay active (once locked, locked);
+//   W = K(R_act), K the Teter-Payne-Allan ratio on 1/2|G|^2 / E_kin(band);
+//   H W (the FFT + projector operator, hamiltonian.cu);
+//   S = [X, W, P_act], Gram G = S^H S and A = S^H (H S) (Sec. II-B row scheme);
+//   Rayleigh-Ritz in FP64 (dense.cu): Jacobi-scaled Cholesky (a failing pivot
+//   drops P and retries), Hermitian eigensolve (Syevd, Sec. III-D);
+//   X' = S C, P' = [0, W, P_act] C (Hetmaniuk-Lehoucq), and the matching H
+//   blocks, so H is applied once per step.
+//
+// Device layout: S and H S are npw x 3nb complex128 column blocks [X | W | P]
+// (ld = npw), ping-ponged between two buffers; P and H P (npw x nb) keep all
+// nb columns.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "dense.cuh"
+#include "pw_internal.cuh"
+
+struct pw_solver {
+  pw_cell *cell = nullptr;
+  int nb = 0, npw = 0, maxit = 0, precision = PW_FP64;
+  double tol = 0.0;
+  cudaStream_t st = nullptr;
+  double2 *S = nullptr, *S2 = nullptr, *HS = nullptr, *HS2 = nullptr, *P = nullptr, *HP = nullptr;
+  double2 *G = nullptr, *A = nullptr, *C = nullptr;
+  double *lam = nullptr, *theta = nullptr, *stats = nullptr;
+  int *act = nullptr;
+  double2 *gws = nullptr; size_t gws_elems = 0;
+  bool haveP = false;
+  std::vector<char> active;
+  std::vector<double> lam_h, resid_h;
+  int iter = 0, dropped = 0;
+  pw_dense_ws dws;
+  size_t bytes = 0;
+  cudaEvent_t ev[8] = {};    // stage boundaries of the last step
+};
+
+namespace {
+
+__device__ __forceinline__ double bsum(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (threadIdx.x == 0) sh[0] = r;
+  }
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// per column j: |HX_j - lam_j X_j|^2, sum kin |x|^2, sum |x|^2
+__global__ void __launch_bounds__(256) k_stats(const double2 *X, const double2 *HX, int ld, int npw,
+                                               const double *lam, const double *kin, double *stats,
+                                               int nb) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x;
+  const double l = lam[j];
+  const double2 *x = X + (long)j * ld, *hx = HX + (long)j * ld;
+  double r2 = 0.0, kx = 0.0, x2 = 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const double2 a = x[g], h = hx[g];
+    const double rx = h.x - l * a.x, ry = h.y - l * a.y;
+    const double aa = a.x * a.x + a.y * a.y;
+    r2 += rx * rx + ry * ry;
+    kx += kin[g] * aa;
+    x2 += aa;
+  }
+  r2 = bsum(r2, sh);
+  kx = bsum(kx, sh);
+  x2 = bsum(x2, sh);
+  if (threadIdx.x == 0) {
+    stats[j] = r2;
+    stats[nb + j] = kx;
+    stats[2 * nb + j] = x2;
+  }
+}
+
+// W[:, a] = K(kin / E_kin(j)) (HX_j - lam_j X_j), j = act[a]
+__global__ void k_precond(const double2 *X, const double2 *HX, int ld, int npw, const double *lam,
+                          const double *kin, const double *stats, int nb, const int *act, int k,
+                          double2 *W) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)npw * k) return;
+  const int g = (int)(idx % npw), a = (int)(idx / npw);
+  const int j = act[a];
+  const double ek = stats[nb + j] / stats[2 * nb + j];
+  const double x = kin[g] / ek;
+  const double p = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
+  const double K = p / (p + 16.0 * x * x * x * x);
+  const double2 xv = X[g + (long)j * ld], h = HX[g + (long)j * ld];
+  const double l = lam[j];
+  W[g + (long)a * ld] = make_double2(K * (h.x - l * xv.x), K * (h.y - l * xv.y));
+}
+
+// dst[:, a] = src[:, act[a]]
+__global__ void k_gather_cols(const double2 *src, int ld, int npw, const int *act, int k,
+                              double2 *dst) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)npw * k) return;
+  const int g = (int)(idx % npw), a = (int)(idx / npw);
+  dst[g + (long)a * ld] = src[g + (long)act[a] * ld];
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// random start: entry (g, j) = (u1 - 1/2) + i (u2 - 1/2), counters 5 natom + 2 (j npw + g) (+1)
+__global__ void k_random_block(double2 *X, int ld, int npw, int nb, uint64_t seed, uint64_t base) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)npw * nb) return;
+  const int g = (int)(idx % npw), j = (int)(idx / npw);
+  const uint64_t c = base + 2ull * ((uint64_t)j * npw + g);
+  const double u1 = (double)(splitmix64(seed, c) >> 11) * 0x1.0p-53;
+  const double u2 = (double)(splitmix64(seed, c + 1) >> 11) * 0x1.0p-53;
+  X[g + (long)j * ld] = make_double2(u1 - 0.5, u2 - 0.5);
+}
+
+// max |G_ij - delta_ij| of an n x n matrix (single CTA)
+__global__ void k_orth_err(const double2 *G, int n, double *out) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (long idx = threadIdx.x; idx < (long)n * n; idx += blockDim.x) {
+    const int i = (int)(idx % n), j = (int)(idx / n);
+    const double2 g = G[idx];
+    const double re = g.x - (i == j ? 1.0 : 0.0);
+    m = fmax(m, sqrt(re * re + g.y * g.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r = fmax(r, sh[q]);
+    *out = r;
+  }
+}
+
+pw_status alloc(void **p, size_t bytes, size_t *acc) {
+  if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); *p = nullptr; return PW_ERR_OOM; }
+  *acc += bytes;
+  return PW_OK;
+}
+
+const double2 kOne = {1.0, 0.0}, kZero = {0.0, 0.0};
+
+// run H on ncols columns with the solver's precision
+pw_status solver_apply_H(pw_solver *s, const double2 *x, double2 *hx, int ncols) {
+  pw_cell *c = s->cell;
+  const int saved = c->precision;
+  c->precision = s->precision;
+  pw_status r = pw_apply_H(c, x, s->npw, ncols, hx, s->st);
+  c->precision = saved;
+  return r;
+}
+
+pw_status gemm(pw_solver *s, char oa, char ob, int m, int n, int k, const double2 *A, int lda,
+               const double2 *B, int ldb, double2 beta, double2 *C, int ldc) {
+  const size_t need = pw_zgemm_ws_elems(m, n, k);
+  if (need > s->gws_elems) {
+    size_t cur = s->gws_elems * 16;
+    PW_TRY(pw_ensure((void **)&s->gws, &cur, need * 16));
+    s->gws_elems = cur / 16;
+  }
+  return pw_zgemm(oa, ob, m, n, k, kOne, A, lda, B, ldb, beta, C, ldc, s->gws, s->gws_elems, s->st);
+}
+
+// Rayleigh-Ritz on the first ns columns of (S, HS) -> theta, C (ns x nb, ld 3nb).
+// Events ev[3] / ev[4] bracket the Gram products.
+pw_status subspace_rr(pw_solver *s, int ns, int *chol_ok) {
+  const int ldg = 3 * s->nb;
+  cudaEventRecord(s->ev[3], s->st);
+  PW_TRY(gemm(s, 'C', 'N', ns, ns, s->npw, s->S, s->npw, s->S, s->npw, kZero, s->G, ldg));
+  PW_TRY(gemm(s, 'C', 'N', ns, ns, s->npw, s->S, s->npw, s->HS, s->npw, kZero, s->A, ldg));
+  cudaEventRecord(s->ev[4], s->st);
+  return pw_rayleigh_ritz(&s->dws, ns, s->nb, s->G, ldg, s->A, ldg, s->theta, s->C, ldg, chol_ok, s->st);
+}
+
+// residual statistics of the current block to the host
+pw_status refresh_stats(pw_solver *s, std::vector<double> &st_h) {
+  pw_count_launch();
+  k_stats<<<s->nb, 256, 0, s->st>>>(s->S, s->HS, s->npw, s->npw, s->lam, s->cell->d_kin, s->stats, s->nb);
+  PW_TRY(pw_check_launch("stats"));
+  st_h.resize(3 * (size_t)s->nb);
+  PW_CUDA(cudaMemcpyAsync(st_h.data(), s->stats, st_h.size() * 8, cudaMemcpyDeviceToHost, s->st));
+  PW_CUDA(cudaMemcpyAsync(s->lam_h.data(), s->lam, s->nb * 8, cudaMemcpyDeviceToHost, s->st));
+  PW_CUDA(cudaStreamSynchronize(s->st));
+  for (int j = 0; j < s->nb; ++j) {
+    s->resid_h[j] = sqrt(st_h[j]);
+    if (!isfinite(s->resid_h[j]) || !isfinite(s->lam_h[j])) return PW_ERR_NUMERIC;
+  }
+  return PW_OK;
+}
+
+}  // namespace
+
+extern "C" void pw_solver_destroy(pw_solver *s) {
+  if (!s) return;
+  void *ptrs[] = {s->S, s->S2, s->HS, s->HS2, s->P, s->HP, s->G, s->A, s->C, s->lam, s->theta,
+                  s->stats, s->act, s->gws};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : s->ev)
+    if (e) cudaEventDestroy(e);
+  pw_dense_free(&s->dws);
+  delete s;
+}
+
+extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, void *stream,
+                                      pw_solver **out) {
+  if (!out) return PW_ERR_ARG;
+  *out = nullptr;
+  if (!cell || !o || o->nbands < 1 || 3 * o->nbands > cell->npw || !(o->tol >= 0.0) ||
+      (o->precision != PW_FP64 && o->precision != PW_MIXED))
+    return PW_ERR_ARG;
+  pw_solver *s = new pw_solver();
+  s->cell = cell;
+  s->nb = o->nbands;
+  s->npw = cell->npw;
+  s->tol = o->tol;
+  s->maxit = o->maxit;
+  s->precision = o->precision;
+  s->st = (cudaStream_t)stream;
+  const int nb = s->nb, npw = s->npw, n3 = 3 * nb;
+  const size_t blk3 = (size_t)npw * n3 * 16, blk = (size_t)npw * nb * 16;
+  size_t acc = 0;
+  pw_status r = PW_OK;
+  if ((r = alloc((void **)&s->S, blk3, &acc)) || (r = alloc((void **)&s->S2, blk3, &acc)) ||
+      (r = alloc((void **)&s->HS, blk3, &acc)) || (r = alloc((void **)&s->HS2, blk3, &acc)) ||
+      (r = alloc((void **)&s->P, blk, &acc)) || (r = alloc((void **)&s->HP, blk, &acc)) ||
+      (r = alloc((void **)&s->G, (size_t)n3 * n3 * 16, &acc)) ||
+      (r = alloc((void **)&s->A, (size_t)n3 * n3 * 16, &acc)) ||
+      (r = alloc((void **)&s->C, (size_t)n3 * nb * 16, &acc)) ||
+      (r = alloc((void **)&s->lam, nb * 8, &acc)) || (r = alloc((void **)&s->theta, nb * 8, &acc)) ||
+      (r = alloc((void **)&s->stats, 3 * (size_t)nb * 8, &acc)) ||
+      (r = alloc((void **)&s->act, nb * 4, &acc)) || (r = pw_dense_alloc(&s->dws, n3, nb))) {
+    pw_solver_destroy(s);
+    return r;
+  }
+  s->bytes = acc + s->dws.bytes;
+  for (cudaEvent_t &e : s->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { pw_solver_destroy(s); return PW_ERR_CUDA; }
+  s->active.assign(nb, 1);
+  s->lam_h.assign(nb, 0.0);
+  s->resid_h.assign(nb, 0.0);
+  // start block X0 in S[:, 0:nb]
+  if (o->x0) {
+    if (cudaMemcpyAsync(s->S, o->x0, blk, cudaMemcpyHostToDevice, s->st) != cudaSuccess) {
+      pw_solver_destroy(s); return PW_ERR_CUDA;
+    }
+  } else {
+    pw_count_launch();
+    k_random_block<<<(unsigned)(((long)npw * nb + 255) / 256), 256, 0, s->st>>>(
+        s->S, npw, npw, nb, o->seed, 5ull * (uint64_t)cell->natom);
+  }
+  // H X0, then Cholesky-QR + Rayleigh-Ritz on span(X0)
+  int ok = 1;
+  if ((r = solver_apply_H(s, s->S, s->HS, nb)) || (r = subspace_rr(s, nb, &ok))) {
+    pw_solver_destroy(s); return r;
+  }
+  if (!ok) { pw_solver_destroy(s); return PW_ERR_CHOL; }
+  if ((r = gemm(s, 'N', 'N', npw, nb, nb, s->S, npw, s->C, n3, kZero, s->S2, npw)) ||
+      (r = gemm(s, 'N', 'N', npw, nb, nb, s->HS, npw, s->C, n3, kZero, s->HS2, npw))) {
+    pw_solver_destroy(s); return r;
+  }
+  std::swap(s->S, s->S2);
+  std::swap(s->HS, s->HS2);
+  cudaMemcpyAsync(s->lam, s->theta, nb * 8, cudaMemcpyDeviceToDevice, s->st);
+  if (cudaStreamSynchronize(s->st) != cudaSuccess) { pw_solver_destroy(s); return PW_ERR_CUDA; }
+  *out = s;
+  return PW_OK;
+}
+
+extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_report *rep) {
+  if (!cell || !s || cell != s->cell) return PW_ERR_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  const int nb = s->nb, npw = s->npw, n3 = 3 * nb;
+  std::vector<double> st_h;
+  PW_TRY(refresh_stats(s, st_h));
+  double rmax = 0.0;
+  std::vector<int> act;
+  for (int j = 0; j < nb; ++j) {
+    rmax = fmax(rmax, s->resid_h[j]);
+    s->active[j] = s->active[j] && (s->resid_h[j] > s->tol);
+    if (s->active[j]) act.push_back(j);
+  }
+  const int k = (int)act.size();
+  if (rep) {
+    memset(rep, 0, sizeof *rep);
+    rep->iter = s->iter;
+    rep->nactive = k;
+    rep->max_resid = rmax;
+  }
+  if (k == 0) return PW_OK;
+  cudaEventRecord(s->ev[0], s->st);
+  PW_CUDA(cudaMemcpyAsync(s->act, act.data(), k * 4, cudaMemcpyHostToDevice, s->st));
+  double2 *W = s->S + (size_t)nb * npw, *HW = s->HS + (size_t)nb * npw;
+  pw_count_launch();
+  k_precond<<<(unsigned)(((long)npw * k + 255) / 256), 256, 0, s->st>>>(
+      s->S, s->HS, npw, npw, s->lam, cell->d_kin, s->stats, nb, s->act, k, W);
+  PW_TRY(pw_check_launch("precond"));
+  cudaEventRecord(s->ev[1], s->st);
+  PW_TRY(solver_apply_H(s, W, HW, k));
+  cudaEventRecord(s->ev[2], s->st);
+  int ns = nb + k;
+  if (s->haveP) {
+    pw_count_launch();
+    k_gather_cols<<<(unsigned)(((long)npw * k + 255) / 256), 256, 0, s->st>>>(
+        s->P, npw, npw, s->act, k, s->S + (size_t)(nb + k) * npw);
+    pw_count_launch();
+    k_gather_cols<<<(unsigned)(((long)npw * k + 255) / 256), 256, 0, s->st>>>(
+        s->HP, npw, npw, s->act, k, s->HS + (size_t)(nb + k) * npw);
+    PW_TRY(pw_check_launch("gather P"));
+    ns = nb + 2 * k;
+  }
+  int ok = 1;
+  PW_TRY(subspace_rr(s, ns, &ok));
+  int dropped = 0;
+  if (!ok && s->haveP) {
+    ns = nb + k;
+    dropped = 1;
+    PW_TRY(pw_rayleigh_ritz(&s->dws, ns, nb, s->G, n3, s->A, n3, s->theta, s->C, n3, &ok, s->st));
+  }
+  if (!ok) return PW_ERR_CHOL;
+  cudaEventRecord(s->ev[5], s->st);
+  // X' = S C, HX' = HS C, P' = S[:, nb:ns] C[nb:ns], HP' likewise
+  PW_TRY(gemm(s, 'N', 'N', npw, nb, ns, s->S, npw, s->C, n3, kZero, s->S2, npw));
+  PW_TRY(gemm(s, 'N', 'N', npw, nb, ns, s->HS, npw, s->C, n3, kZero, s->HS2, npw));
+  PW_TRY(gemm(s, 'N', 'N', npw, nb, ns - nb, s->S + (size_t)nb * npw, npw, s->C + nb, n3, kZero, s->P, npw));
+  PW_TRY(gemm(s, 'N', 'N', npw, nb, ns - nb, s->HS + (size_t)nb * npw, npw, s->C + nb, n3, kZero, s->HP, npw));
+  cudaEventRecord(s->ev[6], s->st);
+  std::swap(s->S, s->S2);
+  std::swap(s->HS, s->HS2);
+  PW_CUDA(cudaMemcpyAsync(s->lam, s->theta, nb * 8, cudaMemcpyDeviceToDevice, s->st));
+  PW_CUDA(cudaStreamSynchronize(s->st));
+  s->haveP = true;
+  s->iter++;
+  s->dropped += dropped;
+  if (rep) {
+    rep->iter = s->iter;
+    rep->dropped_p = dropped;
+    rep->nsub = ns;
+    rep->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    float t[6] = {0, 0, 0, 0, 0, 0};
+    cudaEventElapsedTime(&t[0], s->ev[0], s->ev[1]);
+    cudaEventElapsedTime(&t[1], s->ev[1], s->ev[2]);
+    cudaEventElapsedTime(&t[2], s->ev[3], s->ev[4]);
+    cudaEventElapsedTime(&t[3], s->ev[4], s->ev[5]);
+    cudaEventElapsedTime(&t[4], s->ev[5], s->ev[6]);
+    rep->ms_resid = t[0];
+    rep->ms_hpsi = t[1];
+    rep->ms_gram = t[2];
+    rep->ms_rr = t[3];
+    rep->ms_rot = t[4];
+  }
+  return PW_OK;
+}
+
+extern "C" pw_status pw_solver_eigs(pw_solver *s, double *eig, double *resid) {
+  if (!s) return PW_ERR_ARG;
+  std::vector<double> st_h;
+  PW_TRY(refresh_stats(s, st_h));
+  if (eig) memcpy(eig, s->lam_h.data(), s->nb * 8);
+  if (resid) memcpy(resid, s->resid_h.data(), s->nb * 8);
+  return PW_OK;
+}
+
+extern "C" pw_status pw_solver_block(pw_solver *s, void *psi, int ld) {
+  if (!s || !psi || ld < s->npw) return PW_ERR_ARG;
+  PW_CUDA(cudaMemcpy2DAsync(psi, (size_t)ld * 16, s->S, (size_t)s->npw * 16, (size_t)s->npw * 16,
+                            s->nb, cudaMemcpyDeviceToDevice, s->st));
+  PW_CUDA(cudaStreamSynchronize(s->st));
+  return PW_OK;
+}
+
+extern "C" pw_status pw_eigsolve(pw_cell *cell, const pw_solve_opts *o, double *eig, void *psi_out,
+                                 int ld, pw_solve_report *rep, void *stream) {
+  if (!cell || !o || !eig || (psi_out && ld < cell->npw)) return PW_ERR_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  pw_solver *s = nullptr;
+  PW_TRY(pw_solver_create(cell, o, stream, &s));
+  pw_status r = PW_OK;
+  std::vector<double> st_h;
+  bool conv = false;
+  for (;;) {
+    if ((r = refresh_stats(s, st_h)) != PW_OK) break;
+    double rmax = 0.0;
+    for (int j = 0; j < s->nb; ++j) rmax = fmax(rmax, s->resid_h[j]);
+    if (rmax <= s->tol) { conv = true; break; }
+    if (s->iter >= s->maxit) break;
+    if ((r = pw_subspace_step(cell, s, nullptr)) != PW_OK) break;
+  }
+  if (r == PW_OK || r == PW_ERR_CHOL) {
+    memcpy(eig, s->lam_h.data(), s->nb * 8);
+    if (psi_out) pw_solver_block(s, psi_out, ld);
+  }
+  if (rep) {
+    rep->iters = s->iter;
+    double rmax = 0.0;
+    for (int j = 0; j < s->nb; ++j) rmax = fmax(rmax, s->resid_h[j]);
+    rep->max_resid = rmax;
+    rep->device_bytes = s->bytes;
+    // orthonormality of the final block, FP64
+    double oe = -1.0;
+    if (gemm(s, 'C', 'N', s->nb, s->nb, s->npw, s->S, s->npw, s->S, s->npw, kZero, s->G, s->nb) == PW_OK) {
+      pw_count_launch();
+      k_orth_err<<<1, 1024, 0, s->st>>>(s->G, s->nb, s->theta);
+      cudaMemcpyAsync(&oe, s->theta, 8, cudaMemcpyDeviceToHost, s->st);
+      cudaStreamSynchronize(s->st);
+    }
+    rep->orth_err = oe;
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  pw_solver_destroy(s);
+  if (r != PW_OK) return r;
+  return conv ? PW_OK : PW_ERR_NOCONV;
+}

@@ -23,6 +23,8 @@
   } while (0)
 
 void pw_last_cuda_error(cudaError_t e, const char *file, int line);
+// count of kernel launches issued by the library (diagnostics; see pw_kernel_launches)
+void pw_count_launch();
 pw_status pw_check_launch(const char *what);
 
 // --------------------------------------------------------------------------
@@ -83,7 +85,12 @@ struct pw_cell {
   double2 *d_B = nullptr; size_t B_elems = 0;   // nproj x nb projections
   double2 *d_gemm_ws = nullptr; size_t gemm_ws_elems = 0;
   size_t bytes = 0;
-  // mixed-precision operand store for beta (split BF16), built on first use
+  // mixed-precision operands (split FP16), built on first use: beta as rows
+  // over G (for beta^H psi) and as rows over projectors (for beta (D B))
+  struct pw_tc_operand *op_beta_rows = nullptr, *op_beta_t = nullptr;
+  struct pw_tc_operand *op_psi = nullptr, *op_db = nullptr;
+  float *d_rmax = nullptr;
+  int *d_tc_err = nullptr;
   void *d_beta_split = nullptr; size_t beta_split_bytes = 0;
 };
 

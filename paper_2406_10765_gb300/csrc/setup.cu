@@ -14,8 +14,15 @@
 #include <vector>
 
 #include "pw_internal.cuh"
+#include "tc_gemm.cuh"
+
+#include <atomic>
 
 static thread_local char g_err[256];
+static std::atomic<unsigned long long> g_launches{0};
+
+void pw_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+extern "C" uint64_t pw_kernel_launches(void) { return g_launches.load(); }
 
 void pw_last_cuda_error(cudaError_t e, const char *file, int line) {
   snprintf(g_err, sizeof g_err, "%s at %s:%d", cudaGetErrorString(e), file, line);
@@ -142,6 +149,11 @@ __global__ void k_beta(double2 *beta, const int *mvec, const double2 *phx, const
 // --------------------------------------------------------------------------
 extern "C" void pw_destroy_cell(pw_cell *c) {
   if (!c) return;
+  pw_tc_operand **ops[] = {&c->op_beta_rows, &c->op_beta_t, &c->op_psi, &c->op_db};
+  for (pw_tc_operand **o : ops)
+    if (*o) { pw_tc_operand_free(*o); delete *o; *o = nullptr; }
+  if (c->d_rmax) cudaFree(c->d_rmax);
+  if (c->d_tc_err) cudaFree(c->d_tc_err);
   void *ptrs[] = {c->d_gcol, c->d_gz, c->d_colstart, c->d_colxy, c->d_kin, c->d_V, c->d_Vf,
                   c->d_beta, c->d_D, c->d_z, c->d_B, c->d_gemm_ws, c->d_beta_split,
                   c->ax[0].tw64, c->ax[0].tw32, c->ax[1].tw64, c->ax[1].tw32,
@@ -291,6 +303,7 @@ extern "C" pw_status pw_setup_cell(const pw_cell_desc *d, void *stream, pw_cell 
           (s = upload((void **)&ddep, d->vdepth, (size_t)d->natom * 8, &tmp)) != PW_OK) {
         pw_destroy_cell(c); return s;
       }
+      pw_count_launch();
       k_vloc<<<(unsigned)((ng + 255) / 256), 256, 0, st>>>(c->d_V, c->d_Vf, dfx, dfy, dfz, ddep,
                                                          d->natom, Nx, Ny, Nz);
       s = pw_check_launch("k_vloc");
@@ -333,6 +346,7 @@ extern "C" pw_status pw_setup_cell(const pw_cell_desc *d, void *stream, pw_cell 
     double np = sqrt(16.0 * pow(M_PI, 1.5) * rp * rp * rp * rp * rp);
     double omega = L[0] * L[1] * L[2];
     dim3 grid((c->npw + 127) / 128, d->natom);
+    pw_count_launch();
     k_beta<<<grid, 128, 0, st>>>(c->d_beta, dm, dpx, dpy, dpz, M[0], M[1], M[2], c->npw,
                                  d->natom, twopi / L[0], twopi / L[1], twopi / L[2], ns, np,
                                  rp * rp, 1.0 / sqrt(omega));

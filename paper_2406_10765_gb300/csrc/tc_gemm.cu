@@ -1,0 +1,569 @@
+// Split-FP16 tensor-core GEMM for the mixed-precision path (tcgen05 + TMA,
+// sm_103a).  These are the dense contractions of the step: the projector
+// products of Sec. III-A and the subspace products S^H S, S^H (H S) and the
+// rotations of Sec. II-B.
+//
+// Real core:  D[m][n] = sum_k sum_{(s,t) in pairs} A_s[m][k] B_t[n][k]
+//   A_s, B_t: FP16 slices of scaled operands, K-major, rows padded, K a
+//   multiple of 64; x * 2^e_row = hi + lo with hi = fp16(x 2^e), lo =
+//   fp16(x 2^e - hi), |x 2^e| < 2^14.  Pairs (hi,hi), (hi,lo), (lo,hi) keep
+//   ~22 significant bits of every product; accumulation is FP32 in TMEM.
+//   Complex products use interleaved rows (re-row, im-row) so one real GEMM
+//   yields the complex result; the epilogue removes the row scales in FP64.
+//
+// Kernel: one 128 x 256 output tile per CTA; warp 0 = TMA producer, warp 1 =
+// MMA issuer (one thread), warps 2-5 = epilogue (tcgen05.ld from TMEM).
+// Two shared-memory stages of (A_hi, A_lo, B_hi, B_lo) = 96 KB each, 128-byte
+// swizzle.  Every mbarrier wait is bounded (~1 s of clock); on timeout the
+// CTA records an error, still frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "pw_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int A_TILE = BM * BK * 2;          // 16 KB
+constexpr int B_TILE = BN * BK * 2;          // 32 KB
+constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;
+constexpr int NSTAGE = 2;
+constexpr int SMEM_BYTES = NSTAGE * STAGE + 1024 + 256;
+constexpr int TMEM_COLS = 256;
+constexpr long long WAIT_CYCLES = 2000000000ll;   // ~1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                          // swizzle: 128B
+  return d;
+}
+
+// instruction descriptor, kind::f16: FP16 A and B, FP32 D, both K-major, M=128, N=256
+__host__ __device__ constexpr uint32_t idesc_f16() {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Epilogue destinations (complex128 output, column-major, ldc):
+//  ROWPAIR: real row r = 2i + c  ->  C[i + n ldc].{re,im}[c]   (A^H B products)
+//  COLPAIR: real col n = 2j + c  ->  C[r + j ldc].{re,im}[c]   (A B products)
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              int a_slice_rows, int b_slice_rows, int m, int n, int kblocks, int mtiles,
+              int ntiles, const float *__restrict__ inv_sa, const float *__restrict__ inv_sb,
+              double2 *__restrict__ C, int ldc, int mode, int accumulate, int herm_skip,
+              int *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(smem + NSTAGE * STAGE);
+  uint64_t *empty = full + NSTAGE;
+  uint64_t *accf = empty + NSTAGE;
+  uint32_t *tmem_slot = (uint32_t *)(accf + 1);
+  __shared__ int s_fail;
+
+  const int tile = blockIdx.x;
+  const int mt = tile / ntiles, nt = tile % ntiles;
+  if (mt >= mtiles) return;
+  const int m0 = mt * BM, n0 = nt * BN;
+  // Hermitian products: skip tiles strictly below the diagonal (rows are
+  // interleaved re/im pairs of output row i = r / 2)
+  if (herm_skip && n0 + BN - 1 < m0 / 2) return;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(accf, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int kb = 0; kb < kblocks; ++kb) {
+      const int s = kb % NSTAGE;
+      const uint32_t u = kb / NSTAGE;
+      if (!mbar_wait(&empty[s], (u & 1) ^ 1)) { atomicOr(err, 1); s_fail = 1; break; }
+      unsigned char *st = smem + s * STAGE;
+      mbar_expect_tx(&full[s], STAGE);
+      const int x = kb * BK;
+      tma_load_2d(st, &mapA, &full[s], x, m0);
+      tma_load_2d(st + A_TILE, &mapA, &full[s], x, a_slice_rows + m0);
+      tma_load_2d(st + 2 * A_TILE, &mapB, &full[s], x, n0);
+      tma_load_2d(st + 2 * A_TILE + B_TILE, &mapB, &full[s], x, b_slice_rows + n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t idesc = idesc_f16();
+    bool ok = true;
+    for (int kb = 0; kb < kblocks; ++kb) {
+      const int s = kb % NSTAGE;
+      const uint32_t u = kb / NSTAGE;
+      if (!mbar_wait(&full[s], u & 1)) { atomicOr(err, 2); s_fail = 1; ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(smem + s * STAGE);
+      const uint32_t a1 = a0 + A_TILE;
+      const uint32_t b0 = a0 + 2 * A_TILE;
+      const uint32_t b1 = b0 + B_TILE;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t off = kk * 32;
+        mma_f16(tmem, smem_desc(a0 + off), smem_desc(b0 + off), idesc, (kb | kk) != 0);
+        mma_f16(tmem, smem_desc(a0 + off), smem_desc(b1 + off), idesc, 1);
+        mma_f16(tmem, smem_desc(a1 + off), smem_desc(b0 + off), idesc, 1);
+      }
+      mma_commit(&empty[s]);
+    }
+    (void)ok;
+    mma_commit(accf);
+  } else if (warp >= 2) {
+    // ---------------- epilogue
+    const int q = warp & 3;                      // TMEM lane quarter this warp may read
+    const bool got = mbar_wait(accf, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!got) atomicOr(err, 4);
+    const int r = m0 + q * 32 + lane;            // output (real) row of this thread
+    if (got) {
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + c0, v);
+        if (r >= m) continue;
+        const double sa = inv_sa[r];
+        if (mode == 0) {                         // ROWPAIR
+          const int i = r >> 1, c = r & 1;
+#pragma unroll 4
+          for (int t = 0; t < 32; ++t) {
+            const int col = n0 + c0 + t;
+            if (col >= n) break;
+            double *dst = (double *)&C[i + (long)col * ldc] + c;
+            const double val = (double)v[t] * sa * (double)inv_sb[col];
+            *dst = accumulate ? *dst + val : val;
+          }
+        } else {                                 // COLPAIR
+#pragma unroll 4
+          for (int t = 0; t < 32; t += 2) {
+            const int col = n0 + c0 + t;
+            if (col >= n) break;
+            double2 *dst = &C[r + (long)(col >> 1) * ldc];
+            const double re = (double)v[t] * sa * (double)inv_sb[col];
+            const double im = (double)v[t + 1] * sa * (double)inv_sb[col + 1];
+            if (accumulate) { double2 o = *dst; o.x += re; o.y += im; *dst = o; }
+            else *dst = make_double2(re, im);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// -------------------------------------------------------------- splits ----
+__device__ __forceinline__ float warp_maxf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ float block_maxf(float v) {
+  __shared__ float sh[32];
+  v = warp_maxf(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = 0.0f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, sh[w]);
+  __syncthreads();
+  return r;
+}
+
+// power-of-two scale s with max * s in [2^13, 2^14)  (s = 1 for an all-zero row)
+__device__ __forceinline__ double pow2_scale(double mx, float *inv) {
+  if (!(mx > 0.0)) { *inv = 1.0f; return 1.0; }
+  int e;
+  frexp(mx, &e);                 // mx = f 2^e, f in [0.5, 1)
+  const int sh = 14 - e;         // mx 2^sh in [2^13, 2^14)
+  *inv = ldexpf(1.0f, -sh);
+  return ldexp(1.0, sh);
+}
+
+__device__ __forceinline__ void split2(double x, __half &hi, __half &lo) {
+  hi = __double2half(x);
+  lo = __double2half(x - (double)__half2float(hi));
+}
+
+// Rows from columns: for each column c of X (npw x ncols, ld), real rows
+//   conj=0:  row c       = (re, im) interleaved over g
+//   conj=1:  row 2c      = (re, im),   row 2c + 1 = (-im, re)
+// out: slices [2][rows_total][kpad] (hi then lo), inv scale per row.
+__global__ void __launch_bounds__(256) k_split_rows(const double2 *__restrict__ X, int ld, int npw,
+                                                    int ncols, int conj, int kpad, int rows_total,
+                                                    __half *__restrict__ out,
+                                                    float *__restrict__ inv_scale,
+                                                    const double *__restrict__ colscale) {
+  const int c = blockIdx.x;
+  const double2 *x = X + (long)c * ld;
+  const double cs = colscale ? colscale[c] : 1.0;
+  float mx = 0.0f;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x)
+    mx = fmaxf(mx, (float)fmax(fabs(x[g].x * cs), fabs(x[g].y * cs)));
+  mx = block_maxf(mx);
+  float inv;
+  const double s = pow2_scale((double)mx * 1.0000001, &inv) * cs;
+  const long slice = (long)rows_total * kpad;
+  const int r0 = conj ? 2 * c : c;
+  if (threadIdx.x == 0) { inv_scale[r0] = inv; if (conj) inv_scale[r0 + 1] = inv; }
+  __half *o0 = out + (long)r0 * kpad;
+  for (int g = threadIdx.x; g < kpad / 2; g += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    if (g < npw) { re = x[g].x * s; im = x[g].y * s; }
+    __half h, l;
+    split2(re, h, l); o0[2 * g] = h; o0[slice + 2 * g] = l;
+    split2(im, h, l); o0[2 * g + 1] = h; o0[slice + 2 * g + 1] = l;
+    if (conj) {
+      __half *o1 = o0 + kpad;
+      split2(-im, h, l); o1[2 * g] = h; o1[slice + 2 * g] = l;
+      split2(re, h, l); o1[2 * g + 1] = h; o1[slice + 2 * g + 1] = l;
+    }
+  }
+}
+
+// Transposed rows: for each g of X (npw x ncols), row g = (re, im) over the
+// columns t (K = 2 ncols).  Per-row scale from the row maximum.
+__global__ void __launch_bounds__(256) k_rowmax(const double2 *__restrict__ X, int ld, int npw,
+                                                int ncols, float *__restrict__ rmax) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= npw) return;
+  float m = 0.0f;
+  for (int t = 0; t < ncols; ++t) {
+    const double2 v = X[g + (long)t * ld];
+    m = fmaxf(m, (float)fmax(fabs(v.x), fabs(v.y)));
+  }
+  rmax[g] = m;
+}
+
+__global__ void __launch_bounds__(256) k_split_trans(const double2 *__restrict__ X, int ld, int npw,
+                                                     int ncols, int kpad, int rows_total,
+                                                     const float *__restrict__ rmax,
+                                                     __half *__restrict__ out,
+                                                     float *__restrict__ inv_scale) {
+  // tile: 32 rows (g) x 64 columns (t); read coalesced along g, write along t
+  __shared__ double2 tileS[64][33];
+  const int g0 = blockIdx.x * 32, t0 = blockIdx.y * 64;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;    // 32 x 8
+  for (int tt = ty; tt < 64; tt += 8) {
+    const int g = g0 + tx, t = t0 + tt;
+    double2 v = make_double2(0.0, 0.0);
+    if (g < npw && t < ncols) v = X[g + (long)t * ld];
+    tileS[tt][tx] = v;
+  }
+  __syncthreads();
+  const long slice = (long)rows_total * kpad;
+  for (int gg = ty; gg < 32; gg += 8) {
+    const int g = g0 + gg;
+    if (g >= npw) continue;
+    float inv;
+    const double s = pow2_scale((double)rmax[g] * 1.0000001, &inv);
+    if (blockIdx.y == 0 && tx == 0) inv_scale[g] = inv;
+    __half *o = out + (long)g * kpad;
+    for (int tt = tx; tt < 64; tt += 32) {
+      const int t = t0 + tt;
+      if (2 * t >= kpad) continue;
+      const double2 v = tileS[tt][gg];
+      __half h, l;
+      split2(v.x * s, h, l); o[2 * t] = h; o[slice + 2 * t] = l;
+      split2(v.y * s, h, l); o[2 * t + 1] = h; o[slice + 2 * t + 1] = l;
+    }
+  }
+}
+
+// Coefficient rows for A B products: for column j of Cm (kdim x ncols, ld):
+//   row 2j = (re, -im) over t,  row 2j + 1 = (im, re)
+// optional per-row (t) real factor d[t] applied first.
+__global__ void __launch_bounds__(256) k_split_coef(const double2 *__restrict__ Cm, int ld, int kdim,
+                                                    int ncols, const double *__restrict__ d,
+                                                    int kpad, int rows_total,
+                                                    __half *__restrict__ out,
+                                                    float *__restrict__ inv_scale) {
+  const int j = blockIdx.x;
+  const double2 *x = Cm + (long)j * ld;
+  float mx = 0.0f;
+  for (int t = threadIdx.x; t < kdim; t += blockDim.x) {
+    const double f = d ? d[t] : 1.0;
+    mx = fmaxf(mx, (float)fmax(fabs(x[t].x * f), fabs(x[t].y * f)));
+  }
+  mx = block_maxf(mx);
+  float inv;
+  const double s = pow2_scale((double)mx * 1.0000001, &inv);
+  if (threadIdx.x == 0) { inv_scale[2 * j] = inv; inv_scale[2 * j + 1] = inv; }
+  const long slice = (long)rows_total * kpad;
+  __half *o0 = out + (long)(2 * j) * kpad, *o1 = o0 + kpad;
+  for (int t = threadIdx.x; t < kpad / 2; t += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    if (t < kdim) { const double f = d ? d[t] * s : s; re = x[t].x * f; im = x[t].y * f; }
+    __half h, l;
+    split2(re, h, l); o0[2 * t] = h; o0[slice + 2 * t] = l;
+    split2(-im, h, l); o0[2 * t + 1] = h; o0[slice + 2 * t + 1] = l;
+    split2(im, h, l); o1[2 * t] = h; o1[slice + 2 * t] = l;
+    split2(re, h, l); o1[2 * t + 1] = h; o1[slice + 2 * t + 1] = l;
+  }
+}
+
+// lower triangle <- conj(upper) for an n x n complex matrix (ld)
+__global__ void k_mirror_lower(double2 *G, int ld, int n) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
+  if (i >= n || j >= n || i <= j) return;
+  const double2 u = G[j + (long)i * ld];
+  G[i + (long)j * ld] = make_double2(u.x, -u.y);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap *map, const void *base, int kpad, int rows_total, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows_total};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host ----
+
+int pw_tc_kpad(int kreal) { return (kreal + BK - 1) / BK * BK; }
+
+pw_status pw_tc_split_rows(const double2 *X, int ld, int npw, int ncols, int conj, const double *colscale,
+                           pw_tc_operand *op, cudaStream_t st) {
+  if (op->rows_total < (conj ? 2 : 1) * ncols || op->kpad < 2 * npw) return PW_ERR_ARG;
+  pw_count_launch();
+  k_split_rows<<<ncols, 256, 0, st>>>(X, ld, npw, ncols, conj, op->kpad, op->rows_total, op->data,
+                                      op->inv_scale, colscale);
+  return pw_check_launch("split_rows");
+}
+
+pw_status pw_tc_split_trans(const double2 *X, int ld, int npw, int ncols, float *rmax_ws,
+                            pw_tc_operand *op, cudaStream_t st) {
+  if (op->rows_total < npw || op->kpad < 2 * ncols) return PW_ERR_ARG;
+  pw_count_launch();
+  k_rowmax<<<(npw + 255) / 256, 256, 0, st>>>(X, ld, npw, ncols, rmax_ws);
+  pw_count_launch();
+  k_split_trans<<<dim3((npw + 31) / 32, (op->kpad / 2 + 63) / 64), 256, 0, st>>>(
+      X, ld, npw, ncols, op->kpad, op->rows_total, rmax_ws, op->data, op->inv_scale);
+  return pw_check_launch("split_trans");
+}
+
+pw_status pw_tc_split_coef(const double2 *Cm, int ld, int kdim, int ncols, const double *d,
+                           pw_tc_operand *op, cudaStream_t st) {
+  if (op->rows_total < 2 * ncols || op->kpad < 2 * kdim) return PW_ERR_ARG;
+  pw_count_launch();
+  k_split_coef<<<ncols, 256, 0, st>>>(Cm, ld, kdim, ncols, d, op->kpad, op->rows_total, op->data,
+                                      op->inv_scale);
+  return pw_check_launch("split_coef");
+}
+
+pw_status pw_tc_gemm(const pw_tc_operand *A, int m, const pw_tc_operand *B, int n, double2 *C, int ldc,
+                     int mode, int accumulate, int herm, int *d_err, cudaStream_t st) {
+  if (A->kpad != B->kpad || m > A->rows_total || n > B->rows_total || m <= 0 || n <= 0) return PW_ERR_ARG;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A->data, A->kpad, 2 * A->rows_total, BM) ||
+      !make_map(&mb, B->data, B->kpad, 2 * B->rows_total, BN))
+    return PW_ERR_CUDA;
+  static bool attr = false;
+  if (!attr) {
+    PW_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr = true;
+  }
+  const int mtiles = (m + BM - 1) / BM, ntiles = (n + BN - 1) / BN;
+  pw_count_launch();
+  k_tc_gemm<<<mtiles * ntiles, 192, SMEM_BYTES, st>>>(ma, mb, A->rows_total, B->rows_total, m, n,
+                                                      A->kpad / BK, mtiles, ntiles, A->inv_scale,
+                                                      B->inv_scale, C, ldc, mode, accumulate, herm,
+                                                      d_err);
+  PW_TRY(pw_check_launch("tc_gemm"));
+  if (herm) {
+    const int ni = m / 2;
+    pw_count_launch();
+    k_mirror_lower<<<dim3((ni + 31) / 32, (ni + 31) / 32), dim3(32, 32), 0, st>>>(C, ldc, ni);
+    PW_TRY(pw_check_launch("mirror"));
+  }
+  return PW_OK;
+}
+
+pw_status pw_tc_operand_alloc(pw_tc_operand *op, int rows, int kreal) {
+  const int kpad = pw_tc_kpad(kreal);
+  const int rows_pad = (rows + 255) / 256 * 256;
+  const size_t bytes = (size_t)2 * rows_pad * kpad * sizeof(__half);
+  if (op->data && op->cap_bytes >= bytes && op->scale_cap >= rows_pad) {
+    op->rows_total = rows_pad;
+    op->kpad = kpad;
+    return PW_OK;
+  }
+  pw_tc_operand_free(op);
+  if (cudaMalloc(&op->data, bytes) != cudaSuccess ||
+      cudaMalloc(&op->inv_scale, (size_t)rows_pad * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    pw_tc_operand_free(op);
+    return PW_ERR_OOM;
+  }
+  // padded rows and K must read as zeros
+  cudaMemset(op->data, 0, bytes);
+  cudaMemset(op->inv_scale, 0, (size_t)rows_pad * sizeof(float));
+  op->cap_bytes = bytes;
+  op->scale_cap = rows_pad;
+  op->rows_total = rows_pad;
+  op->kpad = kpad;
+  return PW_OK;
+}
+
+void pw_tc_operand_free(pw_tc_operand *op) {
+  if (op->data) cudaFree(op->data);
+  if (op->inv_scale) cudaFree(op->inv_scale);
+  *op = pw_tc_operand();
+}
+
+extern "C" pw_status pw_zgemm_tc(char opA, int m, int n, int k, const void *A, int lda, const void *B,
+                                 int ldb, double beta, void *C, int ldc, void *stream) {
+  if ((opA != 'C' && opA != 'N') || m < 1 || n < 1 || k < 1 || !A || !B || !C ||
+      (beta != 0.0 && beta != 1.0) || ldc < m)
+    return PW_ERR_ARG;
+  if (opA == 'C' ? (lda < k || ldb < k) : (lda < m || ldb < k)) return PW_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  pw_tc_operand a, b;
+  int *err = nullptr;
+  float *rmax = nullptr;
+  pw_status r = PW_OK;
+  const double2 *Ad = (const double2 *)A, *Bd = (const double2 *)B;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return PW_ERR_OOM; }
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (opA == 'C') {
+    if ((r = pw_tc_operand_alloc(&a, 2 * m, 2 * k)) == PW_OK &&
+        (r = pw_tc_operand_alloc(&b, n, 2 * k)) == PW_OK &&
+        (r = pw_tc_split_rows(Ad, lda, k, m, 1, nullptr, &a, st)) == PW_OK &&
+        (r = pw_tc_split_rows(Bd, ldb, k, n, 0, nullptr, &b, st)) == PW_OK)
+      r = pw_tc_gemm(&a, 2 * m, &b, n, (double2 *)C, ldc, 0, beta != 0.0, 0, err, st);
+  } else {
+    if (cudaMalloc(&rmax, (size_t)m * sizeof(float)) != cudaSuccess) { cudaGetLastError(); r = PW_ERR_OOM; }
+    if (r == PW_OK && (r = pw_tc_operand_alloc(&a, m, 2 * k)) == PW_OK &&
+        (r = pw_tc_operand_alloc(&b, 2 * n, 2 * k)) == PW_OK &&
+        (r = pw_tc_split_trans(Ad, lda, m, k, rmax, &a, st)) == PW_OK &&
+        (r = pw_tc_split_coef(Bd, ldb, k, n, nullptr, &b, st)) == PW_OK)
+      r = pw_tc_gemm(&a, m, &b, 2 * n, (double2 *)C, ldc, 1, beta != 0.0, 0, err, st);
+  }
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    r = PW_ERR_CUDA;
+  if (r == PW_OK && herr) r = PW_ERR_TIMEOUT;
+  cudaFree(err);
+  if (rmax) cudaFree(rmax);
+  pw_tc_operand_free(&a);
+  pw_tc_operand_free(&b);
+  return r;
+}

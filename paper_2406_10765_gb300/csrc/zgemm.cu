@@ -136,6 +136,7 @@ pw_status pw_zgemm(char opA, char opB, int m, int n, int k, double2 alpha, const
     // C = beta C
     if (beta.x == 1.0 && beta.y == 0.0) return PW_OK;
     // reuse the reduce kernel with zero partial sums
+    pw_count_launch();
     k_zgemm_reduce<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, st>>>(m, n, 0, alpha, ws, beta, C, ldc);
     return pw_check_launch("zgemm k=0");
   }
@@ -146,6 +147,7 @@ pw_status pw_zgemm(char opA, char opB, int m, int n, int k, double2 alpha, const
   splits = (k + kchunk - 1) / kchunk;
   dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN, splits);
 #define L(a, b) k_zgemm<a, b><<<grid, 256, 0, st>>>(m, n, k, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, ws)
+  pw_count_launch();
   if (opA == 'N' && opB == 'N') L('N', 'N');
   else if (opA == 'C' && opB == 'N') L('C', 'N');
   else if (opA == 'N' && opB == 'C') L('N', 'C');
@@ -153,7 +155,10 @@ pw_status pw_zgemm(char opA, char opB, int m, int n, int k, double2 alpha, const
   else return PW_ERR_ARG;
 #undef L
   if (splits > 1)
-    k_zgemm_reduce<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, st>>>(m, n, splits, alpha, ws,
-                                                                        beta, C, ldc);
+    {
+      pw_count_launch();
+      k_zgemm_reduce<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, st>>>(m, n, splits, alpha, ws,
+                                                                          beta, C, ldc);
+    }
   return pw_check_launch("zgemm");
 }

@@ -1,0 +1,52 @@
+"""FP64 GPU Hermitian eigensolver (the small dense eigensolve of the
+Rayleigh-Ritz step, Syevd in Sec. III-D) against LAPACK."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _herm(n, seed, kind="rand"):
+    rng = np.random.default_rng(seed)
+    if kind == "rand":
+        M = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        return M + M.conj().T
+    if kind == "degenerate":    # eigenvalues with multiplicity, random unitary
+        w = np.repeat(np.arange(n // 4 + 1, dtype=float), 4)[:n]
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+        return (Q * w) @ Q.conj().T
+    if kind == "diag":
+        return np.diag(rng.standard_normal(n)).astype(complex)
+    if kind == "cluster":
+        w = np.sort(np.concatenate([np.full(n // 2, 1.0) + 1e-12 * rng.standard_normal(n // 2),
+                                    rng.standard_normal(n - n // 2)]))
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+        return (Q * w) @ Q.conj().T
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("n,nb,kind", [(1, 1, "rand"), (2, 1, "rand"), (3, 3, "rand"),
+                                       (33, 11, "rand"), (72, 24, "rand"), (130, 40, "degenerate"),
+                                       (97, 30, "diag"), (200, 64, "cluster"), (515, 170, "rand")])
+def test_heev_matches_lapack(n, nb, kind):
+    import paper_2406_10765_gb300 as pw
+    A = _herm(n, n + 7, kind)
+    w, Y = pw.pw_heev(torch.from_numpy(A).cuda(), nb)
+    torch.cuda.synchronize()
+    w = w.cpu().numpy()
+    Y = Y.cpu().numpy()
+    ref = np.linalg.eigvalsh(A)
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(w - ref).max() < 1e-13 * scale * max(1, n) ** 0.5
+    # eigenvectors: residual and orthonormality (unique only up to degenerate subspaces)
+    assert np.abs(A @ Y - Y * w[:nb]).max() < 1e-12 * scale
+    assert np.abs(Y.conj().T @ Y - np.eye(nb)).max() < 1e-12
+
+
+def test_heev_argument_errors():
+    from paper_2406_10765_gb300 import binding as B
+    st = B._stream(None)
+    import ctypes as ct
+    assert B._heev(0, 1, ct.c_void_p(1), ct.c_void_p(1), ct.c_void_p(1), st) == B.PW_ERR_ARG
+    assert B._heev(4, 5, ct.c_void_p(1), ct.c_void_p(1), ct.c_void_p(1), st) == B.PW_ERR_ARG

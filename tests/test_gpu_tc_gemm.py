@@ -1,0 +1,48 @@
+"""Split-FP16 tcgen05 GEMM (mixed-precision contractions) against an FP64
+reference product of the same operands."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _cm(x):
+    """host complex -> column-major CUDA tensor"""
+    return torch.from_numpy(np.ascontiguousarray(x.T)).cuda().T
+
+
+def _rand(shape, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    return scale * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (64, 256, 512), (100, 37, 1000), (300, 300, 2000)])
+def test_tc_gemm_AhB(m, n, k):
+    import paper_2406_10765_gb300 as pw
+    A = _rand((k, m), 1, 1e-2)
+    B = _rand((k, n), 2, 3.0)
+    C = pw.pw_zgemm_tc("C", _cm(A), _cm(B)).cpu().numpy()
+    ref = A.conj().T @ B
+    bound = np.sqrt(k) * np.abs(A).max() * np.abs(B).max()
+    assert np.abs(C - ref).max() < 2e-6 * bound
+
+
+@pytest.mark.parametrize("m,n,k", [(129, 5, 40), (1000, 64, 300), (257, 130, 1200)])
+def test_tc_gemm_AB_accumulate(m, n, k):
+    import paper_2406_10765_gb300 as pw
+    A = _rand((m, k), 3, 0.5)
+    B = _rand((k, n), 4, 2.0)
+    C0 = _rand((m, n), 5)
+    C = pw.pw_zgemm_tc("N", _cm(A), _cm(B), C=_cm(C0).clone(), beta=1.0).cpu().numpy()
+    ref = C0 + A @ B
+    bound = np.sqrt(k) * np.abs(A).max() * np.abs(B).max()
+    assert np.abs(C - ref).max() < 2e-6 * bound
+
+
+def test_tc_gemm_gram_hermitian():
+    import paper_2406_10765_gb300 as pw
+    S = _rand((5000, 200), 6, 0.01)
+    G = pw.pw_zgemm_tc("C", _cm(S), _cm(S)).cpu().numpy()
+    ref = S.conj().T @ S
+    assert np.abs(G - ref).max() < 1e-6 * np.abs(ref).max()
