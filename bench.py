@@ -56,8 +56,9 @@ def step_flops(npw, nb, ns, k, nproj, grid):
     n3 = grid[0] * grid[1] * grid[2]
     fft = 2 * 5.0 * n3 * math.log2(n3) * k          # one inverse + one forward 3-D FFT per band
     proj = 2 * 8.0 * npw * nproj * k                # beta^H W and beta (D B)
-    gram = 2 * 8.0 * npw * ns * ns                  # S^H S and S^H (H S), full products
-    rot = 2 * 8.0 * npw * nb * ns + 2 * 8.0 * npw * nb * (ns - nb)
+    gram = 2 * 4.0 * npw * ns * ns                  # S^H S and S^H (H S), Hermitian halves
+    # P' = [W P] C_WP and H P' (ns - nb), then X' = X C_X + P' and H X' (nb)
+    rot = 2 * 8.0 * npw * nb * (ns - nb) + 2 * 8.0 * npw * nb * nb
     return dict(fft=fft, proj=proj, gram=gram, rot=rot)
 
 
@@ -248,6 +249,8 @@ def run_gpu(args):
     # roofline of the dominant stage, from the solver's CUDA events
     stage = {k: sum(getattr(r, "ms_" + k) for r in reps) / len(reps)
              for k in ["resid", "hpsi", "gram", "rr", "rot"]}
+    rr_part = {nm: sum(r.ms_rr_part[i] for r in reps) / len(reps)
+               for i, nm in enumerate(["chol_inv", "transform", "tridiag", "dc", "backtransform"])}
     ns = reps[-1].nsub
     k_act = reps[-1].nactive
     fl = step_flops(cell.npw, nb, ns, k_act, cell.nproj, cell.grid)
@@ -260,6 +263,12 @@ def run_gpu(args):
         flops = fl["fft"] + fl["proj"]
         t_ms = stage["hpsi"]
         kern = "H W (FFT kernels + projector k_zgemm)"
+    elif dom == "rr":
+        n = ns
+        flops = (8 * n ** 3 / 3 + 4 * n ** 3 / 3 + 16 * n ** 3 + 16 * n ** 3 / 3 + 4 * n ** 3 / 3
+                 + 8.0 * n * n * nb * 2)
+        t_ms = stage["rr"]
+        kern = "FP64 Rayleigh-Ritz (Cholesky, L^-1, L^-1 A L^-H, Householder, D&C, back-transform)"
     else:
         flops = None
         t_ms = stage[dom]
@@ -271,7 +280,9 @@ def run_gpu(args):
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": None, "kernel": kern,
                 "peak_source": "nominal FP64 rate 1.25 TFLOP/s (measured DFMA 1.20)",
-                "stage_ms": stage}
+                "stage_ms": stage, "rr_ms": rr_part}
+    if roof is None:
+        roof = {"bound": None, "kernel": kern, "stage_ms": stage}
 
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -282,7 +293,8 @@ def run_gpu(args):
                       "nbands": nb, "nproj": cell.nproj, "nsub": ns, "precision": args.precision,
                       "l2": "inputs larger than L2 (S blocks of several GB)",
                       "parallelism": f"replicas x{world}"},
-           "roofline": roof, "gpu_launches": launches, "clocks": clk}
+           "roofline": roof, "gpu_launches": launches, "launches_before_timed": launches0,
+           "clocks": clk}
     pw.pw_solver_destroy(solver)
 
     if not args.no_e2e:

@@ -125,6 +125,9 @@ typedef struct {
   double ms_gram;       /* S^H S and S^H (H S) */
   double ms_rr;         /* Cholesky, L^-1, eigensolve, coefficients (FP64) */
   double ms_rot;        /* rotations X', H X', P', H P' */
+  /* inside ms_rr: scale + Cholesky + L^-1 | L^-1 A L^-H | Householder
+   * tridiagonalisation | divide and conquer | back-transform + coefficients */
+  double ms_rr_part[5];
 } pw_step_report;
 
 typedef struct {
@@ -149,6 +152,12 @@ pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *opts, void *strea
  * PW_ERR_NUMERIC, PW_ERR_CUDA. */
 pw_status pw_subspace_step(pw_cell *cell, pw_solver *solver, pw_step_report *rep);
 
+/* FP64 Rayleigh-Ritz refinement of the current block: H X, X^H X and
+ * X^H (H X) in FP64, FP64 Cholesky and eigensolve, FP64 rotation.  Used to
+ * finish mixed-precision solves (FP64 overlap, eigenvalues, residual norms
+ * and orthonormality).  Drops P.  Synchronises the solver's stream. */
+pw_status pw_solver_polish(pw_solver *solver);
+
 /* Current Ritz values (host, nb) and residual norms of the current block
  * (host, nb; computed in FP64).  Either pointer may be NULL. */
 pw_status pw_solver_eigs(pw_solver *solver, double *eig, double *resid);
@@ -159,7 +168,9 @@ pw_status pw_solver_block(pw_solver *solver, void *psi, int ld);
 void pw_solver_destroy(pw_solver *solver);
 
 /* Runs LOBPCG to max residual <= tol or maxit steps.  eig: host nb doubles
- * (required); psi_out: device complex128 npw x nb (ld) or NULL.  Returns
+ * (required); psi_out: device complex128 npw x nb (ld) or NULL.  With
+ * opts->precision == PW_MIXED the converged block is finished by
+ * pw_solver_polish (FP64) and the reported residuals are FP64.  Returns
  * PW_ERR_NOCONV with eig / psi_out filled if maxit is reached. */
 pw_status pw_eigsolve(pw_cell *cell, const pw_solve_opts *opts, double *eig, void *psi_out,
                       int ld, pw_solve_report *rep, void *stream);

@@ -51,7 +51,8 @@ class pw_step_report(ct.Structure):
     _fields_ = [("iter", ct.c_int), ("nactive", ct.c_int), ("dropped_p", ct.c_int),
                 ("nsub", ct.c_int), ("max_resid", ct.c_double), ("ms", ct.c_double),
                 ("ms_resid", ct.c_double), ("ms_hpsi", ct.c_double), ("ms_gram", ct.c_double),
-                ("ms_rr", ct.c_double), ("ms_rot", ct.c_double)]
+                ("ms_rr", ct.c_double), ("ms_rot", ct.c_double),
+                ("ms_rr_part", ct.c_double * 5)]
 
 
 class pw_solve_report(ct.Structure):
@@ -244,6 +245,13 @@ def pw_subspace_step(cell, solver):
     r = pw_step_report()
     _check(_sstep(cell, solver, ct.byref(r)), "pw_subspace_step")
     return r
+
+
+_spolish = _sig("pw_solver_polish", ct.c_int, [_vp])
+
+
+def pw_solver_polish(solver):
+    _check(_spolish(solver), "pw_solver_polish")
 
 
 def pw_solver_eigs(solver, nbands):

@@ -97,6 +97,15 @@ __global__ void k_scale_herm(const double2 *M, int ld, int n, const double *d, d
   out[i + (long)j * n] = make_double2(s * (a.x + b.x), s * (a.y - b.y));
 }
 
+// lower triangle <- conj(upper), diagonal made real (n x n, ld n)
+__global__ void k_mirror_upper_to_lower(double2 *M, int n) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
+  if (i >= n || j >= n || i < j) return;
+  if (i == j) { M[i + (long)i * n].y = 0.0; return; }
+  const double2 u = M[j + (long)i * n];
+  M[i + (long)j * n] = make_double2(u.x, -u.y);
+}
+
 // in-place Hermitian average of an n x n matrix (ld n)
 __global__ void k_hermitize(double2 *M, int n) {
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
@@ -230,29 +239,60 @@ __global__ void k_scale_rows_real(double2 *C, int ld, int n, int nb, const doubl
 }
 
 // ======================================================================
-// Householder tridiagonalisation (lower, unblocked), complex Hermitian
+// Householder tridiagonalisation, complex Hermitian (lower triangle)
 // ======================================================================
 
-// reflector from column k: v (stored in place below the diagonal), tau[k], e[k], d[k]
-__global__ void k_house(double2 *A, int n, int k, double *d, double *e, double2 *tau) {
+// ----------------------------------------------------------------------
+// Fused lower-triangle tridiagonalisation.  Step k keeps the rank-2 update
+// of step k-1 pending: k_house_lazy applies it to column k and builds the
+// reflector; k_her2_hemv applies it to the lower triangle of the trailing
+// block and, in the same pass, forms the partial products of
+// p = A22 v_k (each off-diagonal element serves its row and, conjugated, its
+// column); k_hemv_finish sums the partials and forms w.  One read and one
+// write of half the trailing matrix per step.
+// ----------------------------------------------------------------------
+constexpr int TT = 32;
+
+// alpha of step k-1: -1/2 tau (p^H v), from the per-block partial dots
+__device__ __forceinline__ double2 prev_alpha(const double2 *dotpart, int ndot, double2 t) {
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = 0; b < ndot; ++b) s = cadd(s, dotpart[b]);
+  return cmul(make_double2(-0.5 * t.x, -0.5 * t.y), s);
+}
+
+__global__ void k_house_lazy(double2 *A, int n, int k, const double2 *pprev, const double2 *dotpart,
+                             int ndot, int has_prev, double *d, double *e, double2 *tau) {
   __shared__ double sh[32];
+  double2 *col = A + (long)k * n;
+  if (has_prev) {
+    const double2 *vp = A + k + (long)(k - 1) * n;     // v_{k-1}[r - k], rows r >= k
+    const double2 al = prev_alpha(dotpart, ndot, tau[k - 1]);
+    // w_{k-1} = p_{k-1} + alpha v_{k-1}
+    const double2 w0 = cadd(pprev[0], al);
+    for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
+      const double2 vr = vp[r - k], wr = cadd(pprev[r - k], cmul(al, vr));
+      // A_rk -= v_r conj(w_0) + w_r conj(v_0), v_0 = 1
+      const double2 t = cmul(vr, make_double2(w0.x, -w0.y));
+      col[r].x -= t.x + wr.x;
+      col[r].y -= t.y + wr.y;
+    }
+    __syncthreads();
+  }
   const int m = n - k - 1;
-  double2 *x = A + (k + 1) + (long)k * n;
+  double2 *x = col + k + 1;
   double s = 0.0;
   for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += x[i].x * x[i].x + x[i].y * x[i].y;
   const double xn2 = block_sum(s, sh);
   const double2 alpha = x[0];
   double beta;
   double2 tk, scal;
-  const bool identity = (xn2 == 0.0 && alpha.y == 0.0);
-  if (identity) {
+  if (xn2 == 0.0 && alpha.y == 0.0) {
     beta = alpha.x;
     tk = make_double2(0.0, 0.0);
     scal = make_double2(0.0, 0.0);
   } else {
     beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2), alpha.x);
     tk = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-    // scal = 1 / (alpha - beta)
     const double2 den = make_double2(alpha.x - beta, alpha.y);
     const double q = 1.0 / (den.x * den.x + den.y * den.y);
     scal = make_double2(den.x * q, -den.y * q);
@@ -260,66 +300,122 @@ __global__ void k_house(double2 *A, int n, int k, double *d, double *e, double2 
   __syncthreads();
   for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] = cmul(x[i], scal);
   if (threadIdx.x == 0) {
+    d[k] = col[k].x;
     x[0] = make_double2(1.0, 0.0);
     tau[k] = tk;
     e[k] = beta;
-    d[k] = A[k + (long)k * n].x;
   }
 }
 
-constexpr int HV_ROWS = 128, HV_COLS = 128;
-
-// partial p = A22 v over a column chunk
-__global__ void k_hemv(const double2 *A, int n, int k, double2 *part, int nmax) {
-  const int m = n - k - 1;
-  const int i = blockIdx.x * HV_ROWS + threadIdx.x;
-  const int c0 = blockIdx.y * HV_COLS, c1 = min(m, c0 + HV_COLS);
-  if (i >= m) return;
-  const double2 *v = A + (k + 1) + (long)k * n;
-  const double2 *Ai = A + (k + 1 + i) + (long)(k + 1) * n;
-  double2 acc = make_double2(0.0, 0.0);
-  for (int j = c0; j < c1; ++j) acc = cadd(acc, cmul(Ai[(long)j * n], v[j]));
-  part[(long)blockIdx.y * nmax + i] = acc;
+// one CTA per lower tile (I >= J) of the trailing block (rows/cols >= k+1)
+__global__ void __launch_bounds__(256) k_her2_hemv(double2 *A, int n, int k, const double2 *pprev,
+                                                   const double2 *dotpart, int ndot,
+                                                   const double2 *tau, int has_prev, double2 *part,
+                                                   int nmax) {
+  __shared__ double2 colacc[8][TT];
+  __shared__ double2 s_al;
+  const int t = blockIdx.x;
+  int I = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((I + 1) * (I + 2) / 2 <= t) ++I;
+  while (I * (I + 1) / 2 > t) --I;
+  const int J = t - I * (I + 1) / 2;
+  const int m = n - k - 1, o = k + 1;
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;   // 8 warps x 4 rows
+  const int c = o + TT * J + lane;                            // this lane's column
+  const double2 *vk = A + o + (long)k * n;                    // v_k[x], x = row - o
+  const double2 *vp = A + k + (long)(k - 1) * n;              // v_{k-1}[x], x = row - k
+  if (threadIdx.x == 0 && has_prev) s_al = prev_alpha(dotpart, ndot, tau[k - 1]);
+  __syncthreads();
+  const double2 al = has_prev ? s_al : make_double2(0.0, 0.0);
+  const bool cin = c < n;
+  double2 vc = make_double2(0.0, 0.0), vpc = vc, wpc = vc;
+  if (cin) {
+    vc = vk[c - o];
+    if (has_prev) { vpc = vp[c - k]; wpc = cadd(pprev[c - k], cmul(al, vpc)); }
+  }
+  double2 cacc = make_double2(0.0, 0.0);
+  for (int q = 0; q < 4; ++q) {
+    const int r = o + TT * I + wq * 4 + q;
+    const bool rin = r < n;
+    const bool use = rin && cin && (I != J || c <= r);
+    double2 a = make_double2(0.0, 0.0);
+    if (use) {
+      double2 *ap = A + r + (long)c * n;
+      a = *ap;
+      if (has_prev) {
+        const double2 vr = vp[r - k], wr = cadd(pprev[r - k], cmul(al, vr));
+        // a -= v_r conj(w_c) + w_r conj(v_c)
+        a.x -= (vr.x * wpc.x + vr.y * wpc.y) + (wr.x * vpc.x + wr.y * vpc.y);
+        a.y -= (vr.y * wpc.x - vr.x * wpc.y) + (wr.y * vpc.x - wr.x * vpc.y);
+        *ap = a;
+      }
+    }
+    // row part: sum_c a_rc v_c
+    double2 rp = cmul(a, vc);
+    for (int off = 16; off > 0; off >>= 1) {
+      rp.x += __shfl_xor_sync(0xffffffffu, rp.x, off);
+      rp.y += __shfl_xor_sync(0xffffffffu, rp.y, off);
+    }
+    // column part (strictly below the diagonal): conj(a_rc) v_r
+    if (use && (I != J || c < r)) cacc = cadd(cacc, cmulc(a, vk[r - o]));
+    if (lane == 0 && rin) {
+      // diagonal tiles also collect the column parts below (added after the loop)
+      part[(long)J * nmax + (r - o)] = rp;
+    }
+  }
+  colacc[wq][lane] = cacc;
+  __syncthreads();
+  if (threadIdx.x < TT) {
+    const int cc = o + TT * J + threadIdx.x;
+    if (cc < n) {
+      double2 s = colacc[0][threadIdx.x];
+      for (int w = 1; w < 8; ++w) s = cadd(s, colacc[w][threadIdx.x]);
+      if (I != J) {
+        part[(long)I * nmax + (cc - o)] = s;
+      } else {
+        // same slot as the row part of the diagonal tile: add
+        double2 *pp = &part[(long)J * nmax + (cc - o)];
+        *pp = cadd(*pp, s);
+      }
+    }
+  }
+  (void)m;
 }
 
-// p = tau sum(part); w = p - 1/2 tau (p^H v) v
-__global__ void k_hemv_fin(const double2 *A, int n, int k, const double2 *part, int nchunk,
-                           int nmax, const double2 *tau, double2 *p, double2 *w) {
+// p = tau sum_c part[c] (one thread per row) and per-block partial dots
+// p^H v; w = p + alpha v is formed by the next step's kernels
+__global__ void __launch_bounds__(256) k_hemv_rows(const double2 *A, int n, int k, const double2 *part,
+                                                   int nT, int nmax, const double2 *tau, double2 *p,
+                                                   double2 *dotpart) {
   __shared__ double sh[32];
-  const int m = n - k - 1;
-  const double2 *v = A + (k + 1) + (long)k * n;
+  const int m = n - k - 1, o = k + 1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const double2 t = tau[k];
   double dr = 0.0, di = 0.0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+  if (i < m) {
     double2 s = make_double2(0.0, 0.0);
-    for (int c = 0; c < nchunk; ++c) s = cadd(s, part[(long)c * nmax + i]);
+    for (int c = 0; c < nT; ++c) s = cadd(s, part[(long)c * nmax + i]);
     s = cmul(t, s);
     p[i] = s;
-    const double2 pv = cmulc(s, v[i]);   // conj(p_i) v_i
-    dr += pv.x;
-    di += pv.y;
+    const double2 pv = cmulc(s, A[o + i + (long)k * n]);
+    dr = pv.x;
+    di = pv.y;
   }
   dr = block_sum(dr, sh);
   di = block_sum(di, sh);
-  // alpha = -1/2 tau (p^H v)
-  const double2 al = cmul(make_double2(-0.5 * t.x, -0.5 * t.y), make_double2(dr, di));
-  for (int i = threadIdx.x; i < m; i += blockDim.x) w[i] = cadd(p[i], cmul(al, v[i]));
+  if (threadIdx.x == 0) dotpart[blockIdx.x] = make_double2(dr, di);
 }
 
-// A22 -= v w^H + w v^H
-__global__ void k_her2(double2 *A, int n, int k, const double2 *w) {
-  const int m = n - k - 1;
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y;
-  if (i >= m || j >= m) return;
-  const double2 *v = A + (k + 1) + (long)k * n;
-  const double2 vi = v[i], vj = v[j], wi = w[i], wj = w[j];
-  double2 &a = A[(k + 1 + i) + (long)(k + 1 + j) * n];
-  // v_i conj(w_j) + w_i conj(v_j)
-  a.x -= (vi.x * wj.x + vi.y * wj.y) + (wi.x * vj.x + wi.y * vj.y);
-  a.y -= (vi.y * wj.x - vi.x * wj.y) + (wi.y * vj.x - wi.x * vj.y);
+// last diagonal after the final pending update (v_{n-2} = 1, w_{n-2} = w[0])
+__global__ void k_last_diag_lazy(const double2 *A, int n, const double2 *pprev, const double2 *dotpart,
+                                 int ndot, const double2 *tau, int has_prev, double *d) {
+  double a = A[(n - 1) + (long)(n - 1) * n].x;
+  if (has_prev) {
+    const double2 w0 = cadd(pprev[0], prev_alpha(dotpart, ndot, tau[n - 2]));   // v = 1
+    a -= 2.0 * w0.x;
+  }
+  d[n - 1] = a;
 }
-
-__global__ void k_last_diag(const double2 *A, int n, double *d) { d[n - 1] = A[(n - 1) + (long)(n - 1) * n].x; }
 
 // ======================================================================
 // divide and conquer on the symmetric tridiagonal (d, e)
@@ -735,7 +831,7 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
             get((void **)&ws->e, nmax * 8) && get((void **)&ws->lam, nmax * 8) &&
             get((void **)&ws->tau, nmax * 16) && get((void **)&ws->p, nmax * 16) &&
             get((void **)&ws->w, nmax * 16) &&
-            get((void **)&ws->part, (size_t)((nmax + HV_COLS - 1) / HV_COLS) * nmax * 16) &&
+            get((void **)&ws->part, (size_t)((nmax + TT - 1) / TT) * nmax * 16) &&
             get((void **)&ws->Z, n2 * 8) && get((void **)&ws->W, n2 * 8) && get((void **)&ws->U, n2 * 8);
   double **dbl[] = {&ws->Ds, &ws->zs, &ws->DK, &ws->zK, &ws->tauK, &ws->zh, &ws->lamK, &ws->dD, &ws->lnew};
   for (double **q : dbl) ok = ok && get((void **)q, nmax * 8);
@@ -747,6 +843,8 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
   ws->gemm_ws_elems = std::max(pw_zgemm_ws_elems(nmax, nmax, nmax), pw_zgemm_ws_elems(nmax, nbmax, nmax));
   if (ok && ws->gemm_ws_elems) ok = get((void **)&ws->gemm_ws, ws->gemm_ws_elems * 16);
   if (!ok) { pw_dense_free(ws); return PW_ERR_OOM; }
+  for (cudaEvent_t &e : ws->ev)
+    if (!e && cudaEventCreate(&e) != cudaSuccess) { pw_dense_free(ws); return PW_ERR_CUDA; }
   ws->nmax = nmax;
   ws->nbmax = nbmax;
   ws->bytes = total;
@@ -761,7 +859,16 @@ void pw_dense_free(pw_dense_ws *ws) {
                   ws->orig, ws->dcol, ws->src, ws->nodes, ws->knode, ws->rhonode, ws->gemm_ws};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  for (cudaEvent_t e : ws->ev)
+    if (e) cudaEventDestroy(e);
   *ws = pw_dense_ws();
+}
+
+void pw_dense_stage_ms(pw_dense_ws *ws, float out[5]) {
+  for (int i = 0; i < 5; ++i) {
+    out[i] = 0.0f;
+    if (ws->ev[i] && ws->ev[i + 1]) cudaEventElapsedTime(&out[i], ws->ev[i], ws->ev[i + 1]);
+  }
 }
 
 // ======================================================================
@@ -770,26 +877,29 @@ void pw_dense_free(pw_dense_ws *ws) {
 pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam, double2 *Y,
                          cudaStream_t st) {
   if (n <= 0 || nb <= 0 || nb > n || n > ws->nmax || nb > ws->nbmax) return PW_ERR_ARG;
-  // 1. Householder tridiagonalisation
-  const int nchunk_max = (n + HV_COLS - 1) / HV_COLS;
+  // 1. Householder tridiagonalisation (lower triangle, lazy rank-2 updates)
+  if (ws->ev[2]) cudaEventRecord(ws->ev[2], st);
+  double2 *dotpart = ws->w;     // per-block partial dots of the previous step
+  int ndot = 0;
   for (int k = 0; k + 1 < n; ++k) {
     const int m = n - k - 1;
+    const int has_prev = k > 0;
     pw_count_launch();
-    k_house<<<1, 256, 0, st>>>(A, n, k, ws->d, ws->e, ws->tau);
-    const int nch = (m + HV_COLS - 1) / HV_COLS;
+    k_house_lazy<<<1, 256, 0, st>>>(A, n, k, ws->p, dotpart, ndot, has_prev, ws->d, ws->e, ws->tau);
+    const int nT = (m + TT - 1) / TT;
     pw_count_launch();
-    k_hemv<<<dim3((m + HV_ROWS - 1) / HV_ROWS, nch), HV_ROWS, 0, st>>>(A, n, k, ws->part, ws->nmax);
+    k_her2_hemv<<<nT * (nT + 1) / 2, 256, 0, st>>>(A, n, k, ws->p, dotpart, ndot, ws->tau, has_prev,
+                                                   ws->part, ws->nmax);
+    ndot = (m + 255) / 256;
     pw_count_launch();
-    k_hemv_fin<<<1, 256, 0, st>>>(A, n, k, ws->part, nch, ws->nmax, ws->tau, ws->p, ws->w);
-    pw_count_launch();
-    k_her2<<<dim3((m + 31) / 32, (m + 7) / 8), dim3(32, 8), 0, st>>>(A, n, k, ws->w);
+    k_hemv_rows<<<ndot, 256, 0, st>>>(A, n, k, ws->part, nT, ws->nmax, ws->tau, ws->p, dotpart);
   }
-  (void)nchunk_max;
   pw_count_launch();
-  k_last_diag<<<1, 1, 0, st>>>(A, n, ws->d);
+  k_last_diag_lazy<<<1, 1, 0, st>>>(A, n, ws->p, dotpart, ndot, ws->tau, n > 1, ws->d);
   PW_TRY(pw_check_launch("tridiag"));
 
   // 2. divide and conquer
+  if (ws->ev[3]) cudaEventRecord(ws->ev[3], st);
   if (ws->tree_n != n) build_tree(ws, n);
   DcArrays a{lam, ws->Z, ws->W, ws->U, ws->Ds, ws->zs, ws->DK, ws->zK, ws->tauK, ws->zh,
              ws->lamK, ws->dD, ws->lnew, ws->perm, ws->colK, ws->orig, ws->dcol, ws->src,
@@ -824,6 +934,7 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
   PW_TRY(pw_check_launch("divide and conquer"));
 
   // 3. back-transformation of the wanted columns
+  if (ws->ev[4]) cudaEventRecord(ws->ev[4], st);
   pw_count_launch();
   k_bt_init<<<(unsigned)(((long)n * nb + 255) / 256), 256, 0, st>>>(ws->Z, n, nb, Y);
   for (int k = n - 2; k >= 0; --k)
@@ -848,9 +959,10 @@ pw_status cholesky(pw_dense_ws *ws, double2 *A, int n, cudaStream_t st) {
     if (rest > 0) {
       pw_count_launch();
       k_trsm_rows<<<(rest + 127) / 128, 128, 0, st>>>(A, n, j0, b);
-      PW_TRY(pw_zgemm('N', 'C', rest, rest, b, mone, A + (j0 + b) + (long)j0 * n, n,
-                      A + (j0 + b) + (long)j0 * n, n, one, A + (j0 + b) + (long)(j0 + b) * n, n,
-                      ws->gemm_ws, ws->gemm_ws_elems, st));
+      // A22 -= L21 L21^H: Hermitian, so only upper tiles are formed, then mirrored
+      PW_TRY(pw_zgemm_ex('N', 'C', rest, rest, b, mone, A + (j0 + b) + (long)j0 * n, n,
+                         A + (j0 + b) + (long)j0 * n, n, one, A + (j0 + b) + (long)(j0 + b) * n, n,
+                         ws->gemm_ws, ws->gemm_ws_elems, st, 1));
     }
   }
   pw_count_launch();
@@ -892,9 +1004,10 @@ pw_status trinv(pw_dense_ws *ws, const double2 *L, double2 *X, int n, cudaStream
 
 pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, int ldg,
                            const double2 *A, int lda, double *theta, double2 *C, int ldc,
-                           int *chol_ok, cudaStream_t st) {
+                           int *chol_ok, cudaStream_t st, double piv_tol) {
   if (n > ws->nmax || nb > ws->nbmax || nb > n) return PW_ERR_ARG;
   *chol_ok = 1;
+  cudaEventRecord(ws->ev[0], st);
   PW_CUDA(cudaMemsetAsync(ws->flag, 0, 16, st));
   pw_count_launch();
   k_diag_scale<<<(n + 127) / 128, 128, 0, st>>>(G, ldg, n, ws->dscale, ws->flag);
@@ -906,20 +1019,30 @@ pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, int
   PW_TRY(pw_check_launch("scale"));
   PW_TRY(cholesky(ws, ws->G, n, st));
   pw_count_launch();
-  k_chol_check<<<1, 256, 0, st>>>(ws->piv, n, 1e-14, ws->flag);
+  k_chol_check<<<1, 256, 0, st>>>(ws->piv, n, piv_tol, ws->flag);
   int flag = 0;
   PW_CUDA(cudaMemcpyAsync(&flag, ws->flag, 4, cudaMemcpyDeviceToHost, st));
   PW_CUDA(cudaStreamSynchronize(st));
   if (flag) { *chol_ok = 0; return PW_OK; }
   PW_TRY(trinv(ws, ws->G, ws->Linv, n, st));
+  cudaEventRecord(ws->ev[1], st);
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
-  // At = Linv As Linv^H
-  PW_TRY(pw_zgemm('N', 'N', n, n, n, one, ws->Linv, n, ws->A, n, zero, ws->T, n, ws->gemm_ws,
-                  ws->gemm_ws_elems, st));
-  PW_TRY(pw_zgemm('N', 'C', n, n, n, one, ws->T, n, ws->Linv, n, zero, ws->A, n, ws->gemm_ws,
-                  ws->gemm_ws_elems, st));
+  // At = Linv As Linv^H, using the triangle of Linv: row block I of T = Linv As
+  // needs columns < I_end of Linv; column block J of At = T Linv^H needs
+  // rows < J_end of T and, At being Hermitian, only its rows <= J_end
+  constexpr int TB = 256;
+  for (int i0 = 0; i0 < n; i0 += TB) {
+    const int ib = std::min(TB, n - i0), kend = i0 + ib;
+    PW_TRY(pw_zgemm('N', 'N', ib, n, kend, one, ws->Linv + i0, n, ws->A, n, zero, ws->T + i0, n,
+                    ws->gemm_ws, ws->gemm_ws_elems, st));
+  }
+  for (int j0 = 0; j0 < n; j0 += TB) {
+    const int jb = std::min(TB, n - j0), kend = j0 + jb;
+    PW_TRY(pw_zgemm('N', 'C', kend, jb, kend, one, ws->T, n, ws->Linv + j0, n, zero,
+                    ws->A + (long)j0 * n, n, ws->gemm_ws, ws->gemm_ws_elems, st));
+  }
   pw_count_launch();
-  k_hermitize<<<g2, b2, 0, st>>>(ws->A, n);
+  k_mirror_upper_to_lower<<<g2, b2, 0, st>>>(ws->A, n);
   PW_TRY(pw_heev_lowest(ws, n, nb, ws->A, ws->lam, ws->Y, st));
   PW_CUDA(cudaMemcpyAsync(theta, ws->lam, nb * 8, cudaMemcpyDeviceToDevice, st));
   // C = d o (Linv^H Y)
@@ -927,6 +1050,7 @@ pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, int
                   ws->gemm_ws_elems, st));
   pw_count_launch();
   k_scale_rows_real<<<(unsigned)(((long)n * nb + 255) / 256), 256, 0, st>>>(C, ldc, n, nb, ws->dscale);
+  cudaEventRecord(ws->ev[5], st);
   return pw_check_launch("rayleigh_ritz");
 }
 

@@ -29,7 +29,15 @@ struct pw_dense_ws {
   std::vector<int> level_off;             // offset of each level in `nodes` (in triples)
   int max_level_nodes = 0;
   size_t bytes = 0;
+  // sub-stage timing of the last Rayleigh-Ritz: events at the boundaries of
+  // scale+Cholesky+L^-1 | L^-1 A L^-H | tridiagonal | divide & conquer |
+  // back-transform + coefficients
+  cudaEvent_t ev[6] = {};
+  float ms[5] = {0, 0, 0, 0, 0};
 };
+
+// elapsed times of the last pw_rayleigh_ritz (after its stream synchronised)
+void pw_dense_stage_ms(pw_dense_ws *ws, float out[5]);
 
 pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax);
 void pw_dense_free(pw_dense_ws *ws);
@@ -37,10 +45,10 @@ void pw_dense_free(pw_dense_ws *ws);
 // Lowest nb Ritz pairs of the pencil (A, G), both n x n Hermitian (device,
 // leading dims ldg, lda).  theta: device nb doubles; C: device n x nb (ldc)
 // coefficients.  *chol_ok (host) = 0 on a Cholesky breakdown (a pivot of the
-// Jacobi-scaled Gram <= 1e-14 times the largest).  Synchronises `st`.
+// Jacobi-scaled Gram <= piv_tol times the largest).  Synchronises `st`.
 pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, int ldg,
                            const double2 *A, int lda, double *theta, double2 *C, int ldc,
-                           int *chol_ok, cudaStream_t st);
+                           int *chol_ok, cudaStream_t st, double piv_tol = 1e-14);
 
 // Hermitian eigensolver: lowest nb eigenpairs of the n x n matrix A (device,
 // destroyed).  lam: device n doubles (all eigenvalues, ascending); Y: device

@@ -24,6 +24,7 @@
 
 #include "dense.cuh"
 #include "pw_internal.cuh"
+#include "tc_gemm.cuh"
 
 struct pw_solver {
   pw_cell *cell = nullptr;
@@ -42,6 +43,16 @@ struct pw_solver {
   pw_dense_ws dws;
   size_t bytes = 0;
   cudaEvent_t ev[8] = {};    // stage boundaries of the last step
+  // mixed precision: split-FP16 operands of S, H S and the coefficients
+  pw_tc_operand opSA, opSB, opHSB, opST, opHST, opC, opCP;
+  float *rmax = nullptr;
+  int *d_err = nullptr;
+  double2 *Cz = nullptr;
+  // mixed precision applies H to the whole basis [X W P] every step instead of
+  // carrying H X and H P through the rotations (their split-precision errors
+  // would be amplified by ill-conditioned coefficients near convergence)
+  bool fresh_h = false;
+  bool hx_valid = true;    // HS[:, 0:nb] == H X for the current X
 };
 
 namespace {
@@ -106,6 +117,24 @@ __global__ void k_precond(const double2 *X, const double2 *HX, int ld, int npw, 
   const double2 xv = X[g + (long)j * ld], h = HX[g + (long)j * ld];
   const double l = lam[j];
   W[g + (long)a * ld] = make_double2(K * (h.x - l * xv.x), K * (h.y - l * xv.y));
+}
+
+// scale each column of X (and of HX, if given) to unit 2-norm of X's column;
+// zero columns are left unchanged
+__global__ void __launch_bounds__(256) k_normalize_cols(double2 *X, double2 *HX, int ld, int npw) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x;
+  double2 *x = X + (long)j * ld;
+  double s2 = 0.0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) s2 += x[g].x * x[g].x + x[g].y * x[g].y;
+  s2 = bsum(s2, sh);
+  if (!(s2 > 0.0)) return;
+  const double f = 1.0 / sqrt(s2);
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) { x[g].x *= f; x[g].y *= f; }
+  if (HX) {
+    double2 *h = HX + (long)j * ld;
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) { h[g].x *= f; h[g].y *= f; }
+  }
 }
 
 // dst[:, a] = src[:, act[a]]
@@ -185,19 +214,113 @@ pw_status gemm(pw_solver *s, char oa, char ob, int m, int n, int k, const double
   return pw_zgemm(oa, ob, m, n, k, kOne, A, lda, B, ldb, beta, C, ldc, s->gws, s->gws_elems, s->st);
 }
 
+// Cholesky pivot threshold of the Jacobi-scaled Gram: FP64 products are exact
+// to ~1e-16, the split-FP16 products to ~1e-8, so pivots below 1e-6 carry no
+// information in mixed precision.
+double piv_tol(const pw_solver *s) { return s->precision == PW_MIXED ? 1e-6 : 1e-14; }
+
 // Rayleigh-Ritz on the first ns columns of (S, HS) -> theta, C (ns x nb, ld 3nb).
 // Events ev[3] / ev[4] bracket the Gram products.
 pw_status subspace_rr(pw_solver *s, int ns, int *chol_ok) {
   const int ldg = 3 * s->nb;
   cudaEventRecord(s->ev[3], s->st);
-  PW_TRY(gemm(s, 'C', 'N', ns, ns, s->npw, s->S, s->npw, s->S, s->npw, kZero, s->G, ldg));
-  PW_TRY(gemm(s, 'C', 'N', ns, ns, s->npw, s->S, s->npw, s->HS, s->npw, kZero, s->A, ldg));
+  if (s->precision == PW_MIXED) {
+    // split-FP16 tensor-core products; upper triangles, mirrored (Hermitian)
+    const int npw = s->npw;
+    PW_TRY(pw_tc_operand_alloc(&s->opSA, 2 * ns, 2 * npw));
+    PW_TRY(pw_tc_operand_alloc(&s->opSB, ns, 2 * npw));
+    PW_TRY(pw_tc_operand_alloc(&s->opHSB, ns, 2 * npw));
+    PW_TRY(pw_tc_split_rows(s->S, npw, npw, ns, 1, nullptr, &s->opSA, s->st));
+    PW_TRY(pw_tc_split_rows(s->S, npw, npw, ns, 0, nullptr, &s->opSB, s->st));
+    PW_TRY(pw_tc_split_rows(s->HS, npw, npw, ns, 0, nullptr, &s->opHSB, s->st));
+    PW_TRY(pw_tc_gemm(&s->opSA, 2 * ns, &s->opSB, ns, s->G, ldg, 0, 0, 1, s->d_err, s->st));
+    PW_TRY(pw_tc_gemm(&s->opSA, 2 * ns, &s->opHSB, ns, s->A, ldg, 0, 0, 1, s->d_err, s->st));
+  } else {
+    // Hermitian products: upper-triangle tiles, mirrored
+    const size_t need = pw_zgemm_ws_elems(ns, ns, s->npw);
+    if (need > s->gws_elems) {
+      size_t cur = s->gws_elems * 16;
+      PW_TRY(pw_ensure((void **)&s->gws, &cur, need * 16));
+      s->gws_elems = cur / 16;
+    }
+    PW_TRY(pw_zgemm_herm(ns, s->npw, s->S, s->npw, s->S, s->npw, s->G, ldg, s->gws, s->gws_elems, s->st));
+    PW_TRY(pw_zgemm_herm(ns, s->npw, s->S, s->npw, s->HS, s->npw, s->A, ldg, s->gws, s->gws_elems, s->st));
+  }
   cudaEventRecord(s->ev[4], s->st);
-  return pw_rayleigh_ritz(&s->dws, ns, s->nb, s->G, ldg, s->A, ldg, s->theta, s->C, ldg, chol_ok, s->st);
+  return pw_rayleigh_ritz(&s->dws, ns, s->nb, s->G, ldg, s->A, ldg, s->theta, s->C, ldg, chol_ok, s->st,
+                          piv_tol(s));
+}
+
+__global__ void k_zero_top_rows(const double2 *C, int ld, int nrows_zero, int nrows, int ncols,
+                                double2 *out) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)nrows * ncols) return;
+  const int t = (int)(idx % nrows), j = (int)(idx / nrows);
+  out[t + (long)j * ld] = t < nrows_zero ? make_double2(0.0, 0.0) : C[t + (long)j * ld];
+}
+
+// X' = S C and H X' = HS C into S2, HS2; with_p: P' = S C_P, HP' = HS C_P
+// where C_P is C with its first nb rows zeroed (the [0, W, P] combination)
+pw_status rotate(pw_solver *s, int ns, bool with_p) {
+  const int npw = s->npw, nb = s->nb, n3 = 3 * nb;
+  if (s->precision == PW_MIXED) {
+    PW_TRY(pw_tc_operand_alloc(&s->opST, npw, 2 * ns));
+    PW_TRY(pw_tc_operand_alloc(&s->opHST, npw, 2 * ns));
+    PW_TRY(pw_tc_operand_alloc(&s->opC, 2 * nb, 2 * ns));
+    PW_TRY(pw_tc_split_trans(s->S, npw, npw, ns, s->rmax, &s->opST, s->st));
+    if (!s->fresh_h) PW_TRY(pw_tc_split_trans(s->HS, npw, npw, ns, s->rmax, &s->opHST, s->st));
+    PW_TRY(pw_tc_split_coef(s->C, n3, ns, nb, nullptr, &s->opC, s->st));
+    PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opC, 2 * nb, s->S2, npw, 1, 0, 0, s->d_err, s->st));
+    if (!s->fresh_h)
+      PW_TRY(pw_tc_gemm(&s->opHST, npw, &s->opC, 2 * nb, s->HS2, npw, 1, 0, 0, s->d_err, s->st));
+    if (with_p) {
+      pw_count_launch();
+      k_zero_top_rows<<<(unsigned)(((long)ns * nb + 255) / 256), 256, 0, s->st>>>(s->C, n3, nb, ns, nb, s->Cz);
+      PW_TRY(pw_check_launch("zero_top_rows"));
+      PW_TRY(pw_tc_operand_alloc(&s->opCP, 2 * nb, 2 * ns));
+      PW_TRY(pw_tc_split_coef(s->Cz, n3, ns, nb, nullptr, &s->opCP, s->st));
+      PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opCP, 2 * nb, s->P, npw, 1, 0, 0, s->d_err, s->st));
+      if (!s->fresh_h)
+        PW_TRY(pw_tc_gemm(&s->opHST, npw, &s->opCP, 2 * nb, s->HP, npw, 1, 0, 0, s->d_err, s->st));
+    }
+    return PW_OK;
+  }
+  if (with_p && ns > nb) {
+    // P' = [W P] C[nb:], then X' = X C[:nb] + P' (the W, P part is shared)
+    PW_TRY(gemm(s, 'N', 'N', npw, nb, ns - nb, s->S + (size_t)nb * npw, npw, s->C + nb, n3, kZero, s->P, npw));
+    PW_TRY(gemm(s, 'N', 'N', npw, nb, ns - nb, s->HS + (size_t)nb * npw, npw, s->C + nb, n3, kZero, s->HP, npw));
+    PW_CUDA(cudaMemcpyAsync(s->S2, s->P, (size_t)npw * nb * 16, cudaMemcpyDeviceToDevice, s->st));
+    PW_CUDA(cudaMemcpyAsync(s->HS2, s->HP, (size_t)npw * nb * 16, cudaMemcpyDeviceToDevice, s->st));
+    PW_TRY(gemm(s, 'N', 'N', npw, nb, nb, s->S, npw, s->C, n3, kOne, s->S2, npw));
+    PW_TRY(gemm(s, 'N', 'N', npw, nb, nb, s->HS, npw, s->C, n3, kOne, s->HS2, npw));
+    return PW_OK;
+  }
+  PW_TRY(gemm(s, 'N', 'N', npw, nb, ns, s->S, npw, s->C, n3, kZero, s->S2, npw));
+  PW_TRY(gemm(s, 'N', 'N', npw, nb, ns, s->HS, npw, s->C, n3, kZero, s->HS2, npw));
+  return PW_OK;
+}
+
+pw_status check_tc_err(pw_solver *s) {
+  if (s->precision != PW_MIXED) return PW_OK;
+  int e = 0;
+  PW_CUDA(cudaMemcpyAsync(&e, s->d_err, 4, cudaMemcpyDeviceToHost, s->st));
+  int ec = 0;
+  if (s->cell->d_tc_err) PW_CUDA(cudaMemcpyAsync(&ec, s->cell->d_tc_err, 4, cudaMemcpyDeviceToHost, s->st));
+  PW_CUDA(cudaStreamSynchronize(s->st));
+  return (e || ec) ? PW_ERR_TIMEOUT : PW_OK;
+}
+
+// make HS[:, 0:nb] = H X current (mixed precision recomputes it)
+pw_status ensure_hx(pw_solver *s) {
+  if (s->hx_valid) return PW_OK;
+  PW_TRY(solver_apply_H(s, s->S, s->HS, s->nb));
+  s->hx_valid = true;
+  return PW_OK;
 }
 
 // residual statistics of the current block to the host
 pw_status refresh_stats(pw_solver *s, std::vector<double> &st_h) {
+  PW_TRY(ensure_hx(s));
   pw_count_launch();
   k_stats<<<s->nb, 256, 0, s->st>>>(s->S, s->HS, s->npw, s->npw, s->lam, s->cell->d_kin, s->stats, s->nb);
   PW_TRY(pw_check_launch("stats"));
@@ -222,6 +345,11 @@ extern "C" void pw_solver_destroy(pw_solver *s) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : s->ev)
     if (e) cudaEventDestroy(e);
+  pw_tc_operand *ops[] = {&s->opSA, &s->opSB, &s->opHSB, &s->opST, &s->opHST, &s->opC, &s->opCP};
+  for (pw_tc_operand *o : ops) pw_tc_operand_free(o);
+  if (s->rmax) cudaFree(s->rmax);
+  if (s->d_err) cudaFree(s->d_err);
+  if (s->Cz) cudaFree(s->Cz);
   pw_dense_free(&s->dws);
   delete s;
 }
@@ -240,6 +368,7 @@ extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, voi
   s->tol = o->tol;
   s->maxit = o->maxit;
   s->precision = o->precision;
+  s->fresh_h = o->precision == PW_MIXED;
   s->st = (cudaStream_t)stream;
   const int nb = s->nb, npw = s->npw, n3 = 3 * nb;
   const size_t blk3 = (size_t)npw * n3 * 16, blk = (size_t)npw * nb * 16;
@@ -253,13 +382,16 @@ extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, voi
       (r = alloc((void **)&s->C, (size_t)n3 * nb * 16, &acc)) ||
       (r = alloc((void **)&s->lam, nb * 8, &acc)) || (r = alloc((void **)&s->theta, nb * 8, &acc)) ||
       (r = alloc((void **)&s->stats, 3 * (size_t)nb * 8, &acc)) ||
-      (r = alloc((void **)&s->act, nb * 4, &acc)) || (r = pw_dense_alloc(&s->dws, n3, nb))) {
+      (r = alloc((void **)&s->act, nb * 4, &acc)) || (r = alloc((void **)&s->rmax, (size_t)npw * 4, &acc)) ||
+      (r = alloc((void **)&s->d_err, 16, &acc)) ||
+      (r = alloc((void **)&s->Cz, (size_t)n3 * nb * 16, &acc)) || (r = pw_dense_alloc(&s->dws, n3, nb))) {
     pw_solver_destroy(s);
     return r;
   }
   s->bytes = acc + s->dws.bytes;
   for (cudaEvent_t &e : s->ev)
     if (cudaEventCreate(&e) != cudaSuccess) { pw_solver_destroy(s); return PW_ERR_CUDA; }
+  cudaMemsetAsync(s->d_err, 0, 16, s->st);
   s->active.assign(nb, 1);
   s->lam_h.assign(nb, 0.0);
   s->resid_h.assign(nb, 0.0);
@@ -279,12 +411,10 @@ extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, voi
     pw_solver_destroy(s); return r;
   }
   if (!ok) { pw_solver_destroy(s); return PW_ERR_CHOL; }
-  if ((r = gemm(s, 'N', 'N', npw, nb, nb, s->S, npw, s->C, n3, kZero, s->S2, npw)) ||
-      (r = gemm(s, 'N', 'N', npw, nb, nb, s->HS, npw, s->C, n3, kZero, s->HS2, npw))) {
-    pw_solver_destroy(s); return r;
-  }
+  if ((r = rotate(s, nb, false)) || (r = check_tc_err(s))) { pw_solver_destroy(s); return r; }
   std::swap(s->S, s->S2);
   std::swap(s->HS, s->HS2);
+  s->hx_valid = !s->fresh_h;
   cudaMemcpyAsync(s->lam, s->theta, nb * 8, cudaMemcpyDeviceToDevice, s->st);
   if (cudaStreamSynchronize(s->st) != cudaSuccess) { pw_solver_destroy(s); return PW_ERR_CUDA; }
   *out = s;
@@ -318,6 +448,10 @@ extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_repor
   pw_count_launch();
   k_precond<<<(unsigned)(((long)npw * k + 255) / 256), 256, 0, s->st>>>(
       s->S, s->HS, npw, npw, s->lam, cell->d_kin, s->stats, nb, s->act, k, W);
+  // unit columns: the Rayleigh-Ritz is invariant to column scaling, and the
+  // split-precision operands need W on the scale of X
+  pw_count_launch();
+  k_normalize_cols<<<k, 256, 0, s->st>>>(W, nullptr, npw, npw);
   PW_TRY(pw_check_launch("precond"));
   cudaEventRecord(s->ev[1], s->st);
   PW_TRY(solver_apply_H(s, W, HW, k));
@@ -327,9 +461,13 @@ extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_repor
     pw_count_launch();
     k_gather_cols<<<(unsigned)(((long)npw * k + 255) / 256), 256, 0, s->st>>>(
         s->P, npw, npw, s->act, k, s->S + (size_t)(nb + k) * npw);
-    pw_count_launch();
-    k_gather_cols<<<(unsigned)(((long)npw * k + 255) / 256), 256, 0, s->st>>>(
-        s->HP, npw, npw, s->act, k, s->HS + (size_t)(nb + k) * npw);
+    if (s->fresh_h) {
+      PW_TRY(solver_apply_H(s, s->S + (size_t)(nb + k) * npw, s->HS + (size_t)(nb + k) * npw, k));
+    } else {
+      pw_count_launch();
+      k_gather_cols<<<(unsigned)(((long)npw * k + 255) / 256), 256, 0, s->st>>>(
+          s->HP, npw, npw, s->act, k, s->HS + (size_t)(nb + k) * npw);
+    }
     PW_TRY(pw_check_launch("gather P"));
     ns = nb + 2 * k;
   }
@@ -339,20 +477,23 @@ extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_repor
   if (!ok && s->haveP) {
     ns = nb + k;
     dropped = 1;
-    PW_TRY(pw_rayleigh_ritz(&s->dws, ns, nb, s->G, n3, s->A, n3, s->theta, s->C, n3, &ok, s->st));
+    PW_TRY(pw_rayleigh_ritz(&s->dws, ns, nb, s->G, n3, s->A, n3, s->theta, s->C, n3, &ok, s->st,
+                            piv_tol(s)));
   }
   if (!ok) return PW_ERR_CHOL;
   cudaEventRecord(s->ev[5], s->st);
   // X' = S C, HX' = HS C, P' = S[:, nb:ns] C[nb:ns], HP' likewise
-  PW_TRY(gemm(s, 'N', 'N', npw, nb, ns, s->S, npw, s->C, n3, kZero, s->S2, npw));
-  PW_TRY(gemm(s, 'N', 'N', npw, nb, ns, s->HS, npw, s->C, n3, kZero, s->HS2, npw));
-  PW_TRY(gemm(s, 'N', 'N', npw, nb, ns - nb, s->S + (size_t)nb * npw, npw, s->C + nb, n3, kZero, s->P, npw));
-  PW_TRY(gemm(s, 'N', 'N', npw, nb, ns - nb, s->HS + (size_t)nb * npw, npw, s->C + nb, n3, kZero, s->HP, npw));
+  PW_TRY(rotate(s, ns, true));
+  pw_count_launch();
+  k_normalize_cols<<<nb, 256, 0, s->st>>>(s->P, s->HP, npw, npw);
+  PW_TRY(pw_check_launch("normalize P"));
   cudaEventRecord(s->ev[6], s->st);
   std::swap(s->S, s->S2);
   std::swap(s->HS, s->HS2);
+  s->hx_valid = !s->fresh_h;
   PW_CUDA(cudaMemcpyAsync(s->lam, s->theta, nb * 8, cudaMemcpyDeviceToDevice, s->st));
   PW_CUDA(cudaStreamSynchronize(s->st));
+  PW_TRY(check_tc_err(s));
   s->haveP = true;
   s->iter++;
   s->dropped += dropped;
@@ -372,13 +513,40 @@ extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_repor
     rep->ms_gram = t[2];
     rep->ms_rr = t[3];
     rep->ms_rot = t[4];
+    float part[5];
+    pw_dense_stage_ms(&s->dws, part);
+    for (int i = 0; i < 5; ++i) rep->ms_rr_part[i] = part[i];
   }
+  return PW_OK;
+}
+
+extern "C" pw_status pw_solver_polish(pw_solver *s) {
+  if (!s) return PW_ERR_ARG;
+  const int nb = s->nb, npw = s->npw, n3 = 3 * nb;
+  const int saved = s->precision;
+  s->precision = PW_FP64;
+  pw_status r = solver_apply_H(s, s->S, s->HS, nb);
+  int ok = 1;
+  if (r == PW_OK) r = subspace_rr(s, nb, &ok);
+  if (r == PW_OK && !ok) r = PW_ERR_CHOL;
+  if (r == PW_OK) r = rotate(s, nb, false);
+  s->precision = saved;
+  PW_TRY(r);
+  std::swap(s->S, s->S2);
+  std::swap(s->HS, s->HS2);
+  s->hx_valid = true;
+  PW_CUDA(cudaMemcpyAsync(s->lam, s->theta, nb * 8, cudaMemcpyDeviceToDevice, s->st));
+  PW_CUDA(cudaStreamSynchronize(s->st));
+  (void)npw; (void)n3;
+  // P no longer matches the rotated block
+  s->haveP = false;
   return PW_OK;
 }
 
 extern "C" pw_status pw_solver_eigs(pw_solver *s, double *eig, double *resid) {
   if (!s) return PW_ERR_ARG;
   std::vector<double> st_h;
+
   PW_TRY(refresh_stats(s, st_h));
   if (eig) memcpy(eig, s->lam_h.data(), s->nb * 8);
   if (resid) memcpy(resid, s->resid_h.data(), s->nb * 8);
@@ -408,7 +576,22 @@ extern "C" pw_status pw_eigsolve(pw_cell *cell, const pw_solve_opts *o, double *
     for (int j = 0; j < s->nb; ++j) rmax = fmax(rmax, s->resid_h[j]);
     if (rmax <= s->tol) { conv = true; break; }
     if (s->iter >= s->maxit) break;
-    if ((r = pw_subspace_step(cell, s, nullptr)) != PW_OK) break;
+    pw_step_report sr;
+    if ((r = pw_subspace_step(cell, s, &sr)) != PW_OK) break;
+    // every band locked: nothing left to iterate (a locked band whose residual
+    // drifted above tol leaves the solve unconverged)
+    if (sr.nactive == 0) break;
+  }
+  if (r == PW_OK && s->precision == PW_MIXED) {
+    // FP64 Rayleigh-Ritz on the converged block: FP64 overlap, eigensolve,
+    // residual norms and orthonormality
+    r = pw_solver_polish(s);
+    if (r == PW_OK) r = refresh_stats(s, st_h);
+    if (r == PW_OK) {
+      double rmax = 0.0;
+      for (int j = 0; j < s->nb; ++j) rmax = fmax(rmax, s->resid_h[j]);
+      conv = conv && rmax <= s->tol;
+    }
   }
   if (r == PW_OK || r == PW_ERR_CHOL) {
     memcpy(eig, s->lam_h.data(), s->nb * 8);

@@ -107,6 +107,14 @@ pw_status pw_zgemm(char opA, char opB, int m, int n, int k, double2 alpha, const
                    int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc,
                    double2 *ws, size_t ws_elems, cudaStream_t st);
 size_t pw_zgemm_ws_elems(int m, int n, int k);
+// herm = 1: C is Hermitian (A^H B with A == B up to H-symmetry); only the
+// upper-triangle tiles are computed, then mirrored
+pw_status pw_zgemm_ex(char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
+                      int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc,
+                      double2 *ws, size_t ws_elems, cudaStream_t st, int herm);
+// C (n x n) = A^H B, Hermitian result (upper tiles + mirror)
+pw_status pw_zgemm_herm(int n, int k, const double2 *A, int lda, const double2 *B, int ldb,
+                        double2 *C, int ldc, double2 *ws, size_t ws_elems, cudaStream_t st);
 
 // grow a device buffer
 pw_status pw_ensure(void **ptr, size_t *cur_bytes, size_t need_bytes);

@@ -11,30 +11,37 @@
 //   Complex products use interleaved rows (re-row, im-row) so one real GEMM
 //   yields the complex result; the epilogue removes the row scales in FP64.
 //
-// Kernel: one 128 x 256 output tile per CTA; warp 0 = TMA producer, warp 1 =
-// MMA issuer (one thread), warps 2-5 = epilogue (tcgen05.ld from TMEM).
-// Two shared-memory stages of (A_hi, A_lo, B_hi, B_lo) = 96 KB each, 128-byte
-// swizzle.  Every mbarrier wait is bounded (~1 s of clock); on timeout the
-// CTA records an error, still frees its TMEM and returns.
+// Kernel: one 128 x 128 output tile per CTA; warp 0 = TMA producer, warp 1 =
+// MMA issuer (one thread), warps 2-9 = epilogue (tcgen05.ld from TMEM).
+// Three shared-memory stages of (A_hi, A_lo, B_hi, B_lo) = 64 KB each,
+// 128-byte swizzle.  Each 64-wide K-block accumulates in a fresh TMEM buffer
+// (two buffers), folded by the epilogue into compensated FP32 sums.  Every
+// mbarrier wait is bounded (~1 s of clock); on timeout the CTA records an
+// error, still frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "pw_internal.cuh"
 #include "tc_gemm.cuh"
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int A_TILE = BM * BK * 2;          // 16 KB
-constexpr int B_TILE = BN * BK * 2;          // 32 KB
+constexpr int B_TILE = BN * BK * 2;          // 16 KB
 constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;
-constexpr int NSTAGE = 2;
+constexpr int NSTAGE = 3;
 constexpr int SMEM_BYTES = NSTAGE * STAGE + 1024 + 256;
-constexpr int TMEM_COLS = 256;
+constexpr int TMEM_COLS = 4 * BN;            // 2 accumulator buffers + compensation (+ spare)
+constexpr int CMP_COL = 2 * BN;              // TMEM column of the compensation terms
+constexpr int EPI_WARPS = 8;                 // 4 lane quarters x 2 column halves
+constexpr int EPI_COLS = BN / 2;
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr long long WAIT_CYCLES = 2000000000ll;   // ~1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -88,7 +95,7 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-// instruction descriptor, kind::f16: FP16 A and B, FP32 D, both K-major, M=128, N=256
+// instruction descriptor, kind::f16: FP16 A and B, FP32 D, both K-major, M=128, N=BN
 __host__ __device__ constexpr uint32_t idesc_f16() {
   return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
@@ -123,10 +130,46 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// error-free sum s + x = t + err, err accumulated into e
+__device__ __forceinline__ void two_sum_acc(float &s, float &e, float x) {
+  const float t = s + x;
+  const float z = t - s;
+  e += (s - (t - z)) + (x - z);
+  s = t;
+}
+
 // Epilogue destinations (complex128 output, column-major, ldc):
 //  ROWPAIR: real row r = 2i + c  ->  C[i + n ldc].{re,im}[c]   (A^H B products)
 //  COLPAIR: real col n = 2j + c  ->  C[r + j ldc].{re,im}[c]   (A B products)
-__global__ void __launch_bounds__(192, 1)
+//
+// Accumulation: every BK-wide K-block goes into a fresh TMEM accumulator
+// (double-buffered); epilogue warps fold each block into compensated
+// (two-sum) FP32 register sums, so the FP32 rounding of the tensor-core
+// accumulator covers only 12 MMAs.
+__global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               int a_slice_rows, int b_slice_rows, int m, int n, int kblocks, int mtiles,
               int ntiles, const float *__restrict__ inv_sa, const float *__restrict__ inv_sb,
@@ -136,9 +179,9 @@ __global__ void __launch_bounds__(192, 1)
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + NSTAGE * STAGE);
   uint64_t *empty = full + NSTAGE;
-  uint64_t *accf = empty + NSTAGE;
-  uint32_t *tmem_slot = (uint32_t *)(accf + 1);
-  __shared__ int s_fail;
+  uint64_t *accf = empty + NSTAGE;       // [2] accumulator ready
+  uint64_t *acce = accf + 2;             // [2] accumulator drained
+  uint32_t *tmem_slot = (uint32_t *)(acce + 2);
 
   const int tile = blockIdx.x;
   const int mt = tile / ntiles, nt = tile % ntiles;
@@ -151,8 +194,7 @@ __global__ void __launch_bounds__(192, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    mbar_init(accf, 1);
-    s_fail = 0;
+    for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], EPI_WARPS); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -166,76 +208,112 @@ __global__ void __launch_bounds__(192, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    for (int kb = 0; kb < kblocks; ++kb) {
-      const int s = kb % NSTAGE;
-      const uint32_t u = kb / NSTAGE;
-      if (!mbar_wait(&empty[s], (u & 1) ^ 1)) { atomicOr(err, 1); s_fail = 1; break; }
-      unsigned char *st = smem + s * STAGE;
-      mbar_expect_tx(&full[s], STAGE);
-      const int x = kb * BK;
-      tma_load_2d(st, &mapA, &full[s], x, m0);
-      tma_load_2d(st + A_TILE, &mapA, &full[s], x, a_slice_rows + m0);
-      tma_load_2d(st + 2 * A_TILE, &mapB, &full[s], x, n0);
-      tma_load_2d(st + 2 * A_TILE + B_TILE, &mapB, &full[s], x, b_slice_rows + n0);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int s = kb % NSTAGE;
+        const uint32_t u = kb / NSTAGE;
+        if (!mbar_wait(&empty[s], (u & 1) ^ 1)) { atomicOr(err, 1); break; }
+        unsigned char *st = smem + s * STAGE;
+        mbar_expect_tx(&full[s], STAGE);
+        const int x = kb * BK;
+        tma_load_2d(st, &mapA, &full[s], x, m0);
+        tma_load_2d(st + A_TILE, &mapA, &full[s], x, a_slice_rows + m0);
+        tma_load_2d(st + 2 * A_TILE, &mapB, &full[s], x, n0);
+        tma_load_2d(st + 2 * A_TILE + B_TILE, &mapB, &full[s], x, b_slice_rows + n0);
+      }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    const uint32_t idesc = idesc_f16();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer: one K-block per accumulator buffer
+      const uint32_t idesc = idesc_f16();
+      for (int kb = 0; kb < kblocks; ++kb) {
+        const int b = kb & 1;
+        const uint32_t ub = kb >> 1;
+        if (!mbar_wait(&acce[b], (ub & 1) ^ 1)) { atomicOr(err, 8); break; }
+        const int s = kb % NSTAGE;
+        const uint32_t u = kb / NSTAGE;
+        if (!mbar_wait(&full[s], u & 1)) { atomicOr(err, 2); break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(smem + s * STAGE);
+        const uint32_t a1 = a0 + A_TILE;
+        const uint32_t b0 = a0 + 2 * A_TILE;
+        const uint32_t b1 = b0 + B_TILE;
+        const uint32_t d = tmem + (uint32_t)(b * BN);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t off = kk * 32;
+          mma_f16(d, smem_desc(a0 + off), smem_desc(b0 + off), idesc, kk != 0);
+          mma_f16(d, smem_desc(a0 + off), smem_desc(b1 + off), idesc, 1);
+          mma_f16(d, smem_desc(a1 + off), smem_desc(b0 + off), idesc, 1);
+        }
+        mma_commit(&empty[s]);
+        mma_commit(&accf[b]);
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..9; lane quarter q, column half h.
+    // Running sums live in registers, their compensation terms in TMEM.
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const uint32_t lanes = (uint32_t)(q * 32) << 16;
+    const uint32_t cmp_base = tmem + lanes + (uint32_t)(CMP_COL + h * EPI_COLS);
+    float sum[EPI_COLS];
+#pragma unroll
+    for (int i = 0; i < EPI_COLS; ++i) sum[i] = 0.0f;
+    {
+      float z[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) z[i] = 0.0f;
+#pragma unroll
+      for (int c0 = 0; c0 < EPI_COLS; c0 += 32) tmem_st32(cmp_base + c0, z);
+    }
     bool ok = true;
     for (int kb = 0; kb < kblocks; ++kb) {
-      const int s = kb % NSTAGE;
-      const uint32_t u = kb / NSTAGE;
-      if (!mbar_wait(&full[s], u & 1)) { atomicOr(err, 2); s_fail = 1; ok = false; break; }
+      const int b = kb & 1;
+      const uint32_t ub = kb >> 1;
+      if (!mbar_wait(&accf[b], ub & 1)) { atomicOr(err, 4); ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(smem + s * STAGE);
-      const uint32_t a1 = a0 + A_TILE;
-      const uint32_t b0 = a0 + 2 * A_TILE;
-      const uint32_t b1 = b0 + B_TILE;
+      const uint32_t base = tmem + lanes + (uint32_t)(b * BN + h * EPI_COLS);
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint32_t off = kk * 32;
-        mma_f16(tmem, smem_desc(a0 + off), smem_desc(b0 + off), idesc, (kb | kk) != 0);
-        mma_f16(tmem, smem_desc(a0 + off), smem_desc(b1 + off), idesc, 1);
-        mma_f16(tmem, smem_desc(a1 + off), smem_desc(b0 + off), idesc, 1);
+      for (int c0 = 0; c0 < EPI_COLS; c0 += 32) {
+        float v[32], e[32];
+        tmem_ld32(base + c0, v);
+        tmem_ld32(cmp_base + c0, e);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) two_sum_acc(sum[c0 + i], e[i], v[i]);
+        tmem_st32(cmp_base + c0, e);
       }
-      mma_commit(&empty[s]);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
     }
-    (void)ok;
-    mma_commit(accf);
-  } else if (warp >= 2) {
-    // ---------------- epilogue
-    const int q = warp & 3;                      // TMEM lane quarter this warp may read
-    const bool got = mbar_wait(accf, 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!got) atomicOr(err, 4);
+    float cmp[EPI_COLS];
+#pragma unroll
+    for (int c0 = 0; c0 < EPI_COLS; c0 += 32) tmem_ld32(cmp_base + c0, cmp + c0);
     const int r = m0 + q * 32 + lane;            // output (real) row of this thread
-    if (got) {
-#pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + c0, v);
-        if (r >= m) continue;
-        const double sa = inv_sa[r];
-        if (mode == 0) {                         // ROWPAIR
-          const int i = r >> 1, c = r & 1;
-#pragma unroll 4
-          for (int t = 0; t < 32; ++t) {
-            const int col = n0 + c0 + t;
-            if (col >= n) break;
+    if (ok && r < m) {
+      const double sa = inv_sa[r];
+      const int cb = n0 + h * EPI_COLS;
+      if (mode == 0) {                         // ROWPAIR
+        const int i = r >> 1, c = r & 1;
+#pragma unroll
+        for (int t = 0; t < EPI_COLS; ++t) {
+          const int col = cb + t;
+          if (col < n) {
             double *dst = (double *)&C[i + (long)col * ldc] + c;
-            const double val = (double)v[t] * sa * (double)inv_sb[col];
+            const double val = ((double)sum[t] + (double)cmp[t]) * sa * (double)inv_sb[col];
             *dst = accumulate ? *dst + val : val;
           }
-        } else {                                 // COLPAIR
-#pragma unroll 4
-          for (int t = 0; t < 32; t += 2) {
-            const int col = n0 + c0 + t;
-            if (col >= n) break;
+        }
+      } else {                                 // COLPAIR
+#pragma unroll
+        for (int t = 0; t < EPI_COLS; t += 2) {
+          const int col = cb + t;
+          if (col < n) {
             double2 *dst = &C[r + (long)(col >> 1) * ldc];
-            const double re = (double)v[t] * sa * (double)inv_sb[col];
-            const double im = (double)v[t + 1] * sa * (double)inv_sb[col + 1];
+            const double re = ((double)sum[t] + (double)cmp[t]) * sa * (double)inv_sb[col];
+            const double im = ((double)sum[t + 1] + (double)cmp[t + 1]) * sa * (double)inv_sb[col + 1];
             if (accumulate) { double2 o = *dst; o.x += re; o.y += im; *dst = o; }
             else *dst = make_double2(re, im);
           }
@@ -410,14 +488,15 @@ __global__ void k_mirror_lower(double2 *G, int ld, int n) {
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
       fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
+  });
   return fn;
 }
 
@@ -475,14 +554,12 @@ pw_status pw_tc_gemm(const pw_tc_operand *A, int m, const pw_tc_operand *B, int 
   if (!make_map(&ma, A->data, A->kpad, 2 * A->rows_total, BM) ||
       !make_map(&mb, B->data, B->kpad, 2 * B->rows_total, BN))
     return PW_ERR_CUDA;
-  static bool attr = false;
-  if (!attr) {
-    PW_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
-  }
+  // per-device kernel attribute (set on every call: cheap, thread-safe, and
+  // correct on every device the caller uses)
+  PW_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   const int mtiles = (m + BM - 1) / BM, ntiles = (n + BN - 1) / BN;
   pw_count_launch();
-  k_tc_gemm<<<mtiles * ntiles, 192, SMEM_BYTES, st>>>(ma, mb, A->rows_total, B->rows_total, m, n,
+  k_tc_gemm<<<mtiles * ntiles, NTHREADS, SMEM_BYTES, st>>>(ma, mb, A->rows_total, B->rows_total, m, n,
                                                       A->kpad / BK, mtiles, ntiles, A->inv_scale,
                                                       B->inv_scale, C, ldc, mode, accumulate, herm,
                                                       d_err);
@@ -499,7 +576,7 @@ pw_status pw_tc_gemm(const pw_tc_operand *A, int m, const pw_tc_operand *B, int 
 pw_status pw_tc_operand_alloc(pw_tc_operand *op, int rows, int kreal) {
   const int kpad = pw_tc_kpad(kreal);
   const int rows_pad = (rows + 255) / 256 * 256;
-  const size_t bytes = (size_t)2 * rows_pad * kpad * sizeof(__half);
+  const size_t bytes = (size_t)2 * rows_pad * kpad * sizeof(__half);   // rows padded to 256
   if (op->data && op->cap_bytes >= bytes && op->scale_cap >= rows_pad) {
     op->rows_total = rows_pad;
     op->kpad = kpad;

@@ -23,7 +23,9 @@ __global__ void __launch_bounds__(256) k_zgemm(int m, int n, int k, int kchunk, 
                                                const double2 *__restrict__ A, int lda,
                                                const double2 *__restrict__ B, int ldb,
                                                double2 beta, double2 *__restrict__ C, int ldc,
-                                               double2 *__restrict__ ws) {
+                                               double2 *__restrict__ ws, int herm) {
+  // Hermitian products: tiles strictly below the diagonal are mirrored later
+  if (herm && blockIdx.y < blockIdx.x) return;
   __shared__ double2 As[BK][BM + 1];
   __shared__ double2 Bs[BK][BN + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -101,6 +103,14 @@ __global__ void __launch_bounds__(256) k_zgemm(int m, int n, int k, int kchunk, 
     }
 }
 
+// lower triangle <- conj(upper) (n x n, ld)
+__global__ void k_zmirror(double2 *C, int ldc, int n) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
+  if (i >= n || j >= n || i <= j) return;
+  const double2 u = C[j + (long)i * ldc];
+  C[i + (long)j * ldc] = make_double2(u.x, -u.y);
+}
+
 __global__ void k_zgemm_reduce(int m, int n, int splits, double2 alpha, const double2 *__restrict__ ws,
                                double2 beta, double2 *__restrict__ C, int ldc) {
   const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -128,9 +138,21 @@ size_t pw_zgemm_ws_elems(int m, int n, int k) {
   return s > 1 ? (size_t)s * m * n : 0;
 }
 
+pw_status pw_zgemm_herm(int n, int k, const double2 *A, int lda, const double2 *B, int ldb,
+                        double2 *C, int ldc, double2 *ws, size_t ws_elems, cudaStream_t st) {
+  return pw_zgemm_ex('C', 'N', n, n, k, make_double2(1.0, 0.0), A, lda, B, ldb,
+                     make_double2(0.0, 0.0), C, ldc, ws, ws_elems, st, 1);
+}
+
 pw_status pw_zgemm(char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A, int lda,
                    const double2 *B, int ldb, double2 beta, double2 *C, int ldc, double2 *ws,
                    size_t ws_elems, cudaStream_t st) {
+  return pw_zgemm_ex(opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, st, 0);
+}
+
+pw_status pw_zgemm_ex(char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A, int lda,
+                      const double2 *B, int ldb, double2 beta, double2 *C, int ldc, double2 *ws,
+                      size_t ws_elems, cudaStream_t st, int herm) {
   if (m <= 0 || n <= 0) return PW_OK;
   if (k <= 0) {
     // C = beta C
@@ -146,7 +168,7 @@ pw_status pw_zgemm(char opA, char opB, int m, int n, int k, double2 alpha, const
   kchunk = ((kchunk + BK - 1) / BK) * BK;
   splits = (k + kchunk - 1) / kchunk;
   dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN, splits);
-#define L(a, b) k_zgemm<a, b><<<grid, 256, 0, st>>>(m, n, k, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, ws)
+#define L(a, b) k_zgemm<a, b><<<grid, 256, 0, st>>>(m, n, k, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, ws, herm)
   pw_count_launch();
   if (opA == 'N' && opB == 'N') L('N', 'N');
   else if (opA == 'C' && opB == 'N') L('C', 'N');
@@ -160,5 +182,9 @@ pw_status pw_zgemm(char opA, char opB, int m, int n, int k, double2 alpha, const
       k_zgemm_reduce<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, st>>>(m, n, splits, alpha, ws,
                                                                           beta, C, ldc);
     }
+  if (herm) {
+    pw_count_launch();
+    k_zmirror<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 32), 0, st>>>(C, ldc, m);
+  }
   return pw_check_launch("zgemm");
 }

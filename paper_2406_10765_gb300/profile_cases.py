@@ -1,0 +1,78 @@
+"""Small, self-contained cases of the hot kernels for profiler captures.
+
+    python -m paper_2406_10765_gb300.profile_cases <case> [--reps N]
+
+Cases (each holds at most a few GB on the device and runs its kernels a few
+times after one warm-up):
+  step64      one FP64 LOBPCG step on the Si 64-atom cell (2x2x2, Ecut 10 Ha,
+              npw 13,056, 144 bands): k_zgemm, FFT kernels, Rayleigh-Ritz
+  step64mix   the same step in mixed precision (k_tc_gemm)
+  tcgemm      split-FP16 tensor-core A^H A, A: 104,415 x 1,152 complex
+  heev        FP64 Hermitian eigensolver, n = 1,152 (Householder, D&C)
+  hpsi512     FP64 H psi on 16 bands of the Si 512-atom cell (grid 96^3)
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case")
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args()
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2406_10765_gb300 as pw
+
+    torch.cuda.set_device(0)
+    if a.case in ("step64", "step64mix"):
+        prec = "mixed" if a.case == "step64mix" else "fp64"
+        ci = synth.cell_inputs("Si", 2, 0)
+        cell = pw.Cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], 10.0, precision=prec)
+        s = pw.pw_solver_create(cell.h, 144, tol=0.0, seed=0, precision=prec)
+        pw.pw_subspace_step(cell.h, s)
+        for _ in range(a.reps):
+            r = pw.pw_subspace_step(cell.h, s)
+        print(f"{a.case}: npw {cell.npw}, last step {r.ms:.1f} ms")
+        pw.pw_solver_destroy(s)
+    elif a.case == "tcgemm":
+        k, m = 104415, 1152
+        A = (torch.randn(m, k, dtype=torch.complex128, device="cuda") / k ** 0.5).T
+        for _ in range(a.reps + 1):
+            C = pw.pw_zgemm_tc("C", A, A)
+        torch.cuda.synchronize()
+        print("tcgemm done", float(C.abs().max()))
+    elif a.case == "heev":
+        n = 1152
+        rng = np.random.default_rng(0)
+        M = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        H = torch.from_numpy(M + M.conj().T).cuda()
+        for _ in range(a.reps + 1):
+            w, Y = pw.pw_heev(H, n // 3)
+        torch.cuda.synchronize()
+        print("heev done", float(w[0]))
+    elif a.case == "hpsi512":
+        ci = synth.cell_inputs("Si", 4, 0)
+        cell = pw.Cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], 10.0)
+        x = pw.new_block(cell.npw, 16)
+        x.copy_(torch.from_numpy(synth.draw_x0(0, 512, cell.npw, 16)))
+        y = pw.new_block(cell.npw, 16)
+        for _ in range(a.reps + 1):
+            pw.pw_apply_H(cell.h, x, y)
+        torch.cuda.synchronize()
+        print("hpsi512 done")
+    else:
+        raise SystemExit(f"unknown case {a.case}")
+
+
+if __name__ == "__main__":
+    main()

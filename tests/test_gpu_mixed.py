@@ -1,0 +1,67 @@
+"""Mixed-precision path (FP32 FFTs, split-FP16 tensor-core contractions, FP64
+Cholesky / eigensolve / residual norms) against the FP64 oracle at the stated
+tolerances: |d eps| <= 1e-6 Ha, residual <= 1e-5, ||X^H X - I|| <= 1e-10."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import pw_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_util import cells, to_dev, rel  # noqa: E402
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.mark.parametrize("species,ecut,nb,gold", [("Si", 10.0, 24, "si8_ecut10_seed0_eigs.txt"),
+                                                  ("C", 8.0, 18, "c8_ecut8_seed0_eigs.txt")])
+def test_mixed_eigsolve_tolerances(species, ecut, nb, gold):
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells(species, 1, ecut)
+    ref = np.loadtxt(os.path.join(GOLD, gold))[:nb]
+    psi = pw.new_block(lib.npw, nb)
+    # the split-precision residual floor is ~1e-6; the stated targets are
+    # |d eps| <= 1e-6 Ha, residual <= 1e-5, ||X^H X - I|| <= 1e-10
+    eig, rep, st = pw.pw_eigsolve(lib.h, nb, tol=5e-6, maxit=300, seed=0, precision="mixed",
+                                  psi_out=psi)
+    assert np.abs(eig - ref).max() <= 1e-6
+    assert rep.max_resid <= 1e-5
+    assert rep.orth_err <= 1e-10
+    # residual recomputed by the oracle from the returned block
+    X = psi.cpu().numpy()
+    R = O.apply_H(orc, X) - X * eig[None, :]
+    assert np.sqrt((np.abs(R) ** 2).sum(axis=0)).max() <= 1e-5
+
+
+def test_mixed_step_tracks_fp64_step():
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 1, 10.0)
+    nb = 24
+    x0 = synth.draw_x0(0, 8, orc.npw, nb)
+    a = pw.pw_solver_create(lib.h, nb, tol=0.0, x0=x0, precision="fp64")
+    b = pw.pw_solver_create(lib.h, nb, tol=0.0, x0=x0, precision="mixed")
+    for _ in range(3):
+        pw.pw_subspace_step(lib.h, a)
+        pw.pw_subspace_step(lib.h, b)
+    ea, _ = pw.pw_solver_eigs(a, nb)
+    eb, _ = pw.pw_solver_eigs(b, nb)
+    assert np.abs(ea - eb).max() < 1e-4
+    pw.pw_solver_destroy(a)
+    pw.pw_solver_destroy(b)
+
+
+def test_mixed_apply_h_si512_sampled():
+    lib, orc, _ = cells("Si", 4, 10.0, precision="mixed")
+    import paper_2406_10765_gb300 as pw
+    nb = 24
+    x = synth.draw_x0(1, 512, orc.npw, nb)
+    out = pw.new_block(lib.npw, nb)
+    pw.pw_apply_H(lib.h, to_dev(x), out)
+    got = out.cpu().numpy()
+    for j in [0, 23]:
+        ref = O.apply_H(orc, x[:, j:j + 1])[:, 0]
+        assert rel(got[:, j], ref) < 1e-5
