@@ -102,6 +102,28 @@ pw_status pw_cell_set_precision(pw_cell *cell, int precision);
  * PW_ERR_OOM (workspace growth), PW_ERR_CUDA. */
 pw_status pw_apply_H(pw_cell *cell, const void *psi, int ld, int nb, void *hpsi, void *stream);
 
+/* Size of the fixed device scratch array used by pw_apply_H_noalloc. */
+#define PW_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* H psi without allocating any device memory.  The paper has no counterpart:
+ * this is a library convenience for callers that cannot call cudaMalloc when
+ * they apply H, e.g. a host framework whose pool allocator reserved the GPU,
+ * or a latency-critical loop that must avoid cudaMalloc's implicit
+ * synchronisation.  Same operator and arguments as pw_apply_H, always in FP64
+ * arithmetic; all scratch (FFT z-pencils, projector coefficients, GEMM partial
+ * sums) lives in one static device array of PW_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.  The cell must
+ * already exist (pw_setup_cell allocates).  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Calls share the
+ * array: calls that overlap on the GPU (other streams, other threads) race.
+ * Errors: PW_ERR_ARG as pw_apply_H, and when the scratch would exceed
+ * PW_NOALLOC_SCRATCH_BYTES (projector coefficients, partial sums and one
+ * band's z-pencils must fit: roughly nb <= 400 for a 2,048-projector cell,
+ * fewer at small nb-independent limits); PW_ERR_CUDA. */
+pw_status pw_apply_H_noalloc(pw_cell *cell, const void *psi, int ld, int nb, void *hpsi,
+                             void *stream);
+
 /* Solver options. */
 typedef struct {
   int nbands;           /* nb >= 1, nb <= npw / 3 */

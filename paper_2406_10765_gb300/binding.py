@@ -217,6 +217,16 @@ def pw_apply_H(cell, psi, hpsi, stream=None):
     _check(_apply(cell, _dptr(psi), ld, nb, _dptr(hpsi), _stream(stream)), "pw_apply_H")
 
 
+_apply_na = _sig("pw_apply_H_noalloc", ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp, _vp])
+
+
+def pw_apply_H_noalloc(cell, psi, hpsi, stream=None):
+    """hpsi <- H psi (FP64) using only the library's static scratch (no allocation)."""
+    npw, nb = psi.shape
+    ld = psi.stride(1) if nb > 1 else npw
+    _check(_apply_na(cell, _dptr(psi), ld, nb, _dptr(hpsi), _stream(stream)), "pw_apply_H_noalloc")
+
+
 def pw_destroy_cell(cell):
     _destroy(cell)
 

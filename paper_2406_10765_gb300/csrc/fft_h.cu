@@ -303,7 +303,50 @@ pw_status apply_local_t(pw_cell *c, const double2 *psi, int ld, int nb, double2 
   return pw_check_launch("apply_local");
 }
 
+// FP64 local part with a caller-provided z-pencil buffer of `zbytes` bytes
+// (no allocation); bands are processed in batches that fit the buffer
+pw_status apply_local_into(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
+                           void *zbuf, size_t zbytes, cudaStream_t st) {
+  typedef double2 C;
+  const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
+  const size_t plane_bytes = (size_t)Ny * (Nx + 1) * sizeof(C);
+  if (plane_bytes > 227 * 1024) return PW_ERR_ARG;
+  const int cb = 16;
+  const size_t line_bytes = (size_t)cb * (Nz + 1) * sizeof(C);
+  const size_t per_band = (size_t)Nz * c->ncol * sizeof(C);
+  const int batch = (int)std::min<size_t>((size_t)nb, zbytes / per_band);
+  if (batch < 1) return PW_ERR_ARG;
+  C *Z = reinterpret_cast<C *>(zbuf);
+  PW_TRY(allow_smem(k_sphere_to_z<C>, line_bytes));
+  PW_TRY(allow_smem(k_plane<C, double>, plane_bytes));
+  PW_TRY(allow_smem(k_z_to_sphere<C>, line_bytes));
+  const double scale = 1.0 / ((double)Nx * Ny * Nz);
+  for (int b0 = 0; b0 < nb; b0 += batch) {
+    const int nbb = std::min(batch, nb - b0);
+    dim3 gcols((c->ncol + cb - 1) / cb, nbb);
+    pw_count_launch();
+    k_sphere_to_z<C><<<gcols, 256, line_bytes, st>>>(psi + (long)b0 * ld, ld, c->d_colstart,
+                                                     c->d_gcol, c->d_gz, c->ncol, cb, c->ax[2], Z);
+    pw_count_launch();
+    k_plane<C, double><<<dim3(Nz, nbb), kPlaneThreads<C>::value, plane_bytes, st>>>(
+        Z, c->ncol, c->d_colxy, c->mxmax, c->ax[0], c->ax[1], Nz, c->d_V);
+    pw_count_launch();
+    k_z_to_sphere<C><<<gcols, 256, line_bytes, st>>>(Z, c->ncol, cb, c->ax[2], c->d_colstart,
+                                                     c->d_gcol, c->d_gz, c->d_kin,
+                                                     psi + (long)b0 * ld, ld,
+                                                     hpsi + (long)b0 * ld, scale);
+  }
+  return pw_check_launch("apply_local_into");
+}
+
 }  // namespace
+
+size_t pw_local_zbytes_per_band(const pw_cell *c) { return (size_t)c->N[2] * c->ncol * sizeof(double2); }
+
+pw_status pw_apply_local_fp64_into(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
+                                   void *zbuf, size_t zbytes, cudaStream_t st) {
+  return apply_local_into(c, psi, ld, nb, hpsi, zbuf, zbytes, st);
+}
 
 pw_status pw_apply_local(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
                          int precision, cudaStream_t st) {

@@ -69,6 +69,21 @@ pw_status pw_apply_nonlocal(pw_cell *c, const double2 *psi, int ld, int nb, doub
                   hpsi, ld, c->d_gemm_ws, c->gemm_ws_elems, st);
 }
 
+// FP64 nonlocal term with caller-provided buffers: B (nproj x nb) and GEMM
+// split-K partial sums (ws, ws_elems); no allocation
+pw_status pw_apply_nonlocal_fp64_into(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
+                                      double2 *B, double2 *ws, size_t ws_elems, cudaStream_t st) {
+  if (c->nproj == 0 || nb == 0) return PW_OK;
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  PW_TRY(pw_zgemm('C', 'N', c->nproj, nb, c->npw, one, c->d_beta, c->npw, psi, ld, zero, B, c->nproj,
+                  ws, ws_elems, st));
+  pw_count_launch();
+  k_scale_rows<<<(unsigned)(((long)c->nproj * nb + 255) / 256), 256, 0, st>>>(B, c->nproj, nb, c->d_D);
+  PW_TRY(pw_check_launch("scale_rows"));
+  return pw_zgemm('N', 'N', c->npw, nb, c->nproj, one, c->d_beta, c->npw, B, c->nproj, one, hpsi, ld,
+                  ws, ws_elems, st);
+}
+
 extern "C" pw_status pw_apply_H(pw_cell *c, const void *psi, int ld, int nb, void *hpsi,
                                 void *stream) {
   if (!c || nb < 0) return PW_ERR_ARG;

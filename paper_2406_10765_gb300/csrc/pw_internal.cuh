@@ -100,6 +100,13 @@ pw_status pw_apply_local(pw_cell *c, const double2 *psi, int ld, int nb, double2
 pw_status pw_apply_nonlocal(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
                             int precision, cudaStream_t st);
 
+// FP64 H pieces writing only into caller-provided scratch (no allocation)
+size_t pw_local_zbytes_per_band(const pw_cell *c);
+pw_status pw_apply_local_fp64_into(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
+                                   void *zbuf, size_t zbytes, cudaStream_t st);
+pw_status pw_apply_nonlocal_fp64_into(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
+                                      double2 *B, double2 *ws, size_t ws_elems, cudaStream_t st);
+
 // dense complex FP64 GEMM: C = alpha op(A) op(B) + beta C, column-major.
 // opA: 'N' (A is m x k) or 'C' (A is k x m, conjugate-transposed);
 // opB: 'N' (B is k x n) or 'C' (B is n x k, conjugate-transposed).
