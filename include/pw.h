@@ -197,6 +197,54 @@ void pw_solver_destroy(pw_solver *solver);
 pw_status pw_eigsolve(pw_cell *cell, const pw_solve_opts *opts, double *eig, void *psi_out,
                       int ld, pw_solve_report *rep, void *stream);
 
+/* ---------------------------------------------------------------- serving
+ * A request is a fixed-potential eigensolve of a synthetic diamond supercell:
+ * Si (a = 10.26 bohr) or C (a = 6.74 bohr), n x n x n cubic cells (8 n^3
+ * atoms), Gaussian wells and KB projectors as in pw_cell_desc (widths 1.2
+ * bohr) with depths and D drawn from the request's SplitMix64 stream (depth
+ * a: draw a, d = -1 + 0.1 (2u - 1); D[a][k]: draw 8n^3 + 4a + k, 0.5 + u) and
+ * the random start block of pw_solve_opts.seed. */
+typedef struct {
+  int species;          /* 0 = Si, 1 = C */
+  int ncell;            /* n >= 1 */
+  double ecut;          /* Ha */
+  int nbands;
+  uint64_t seed;
+  double t_arrival;     /* seconds after pw_serve starts (times opts.time_scale) */
+  double tol;           /* 0 -> 1e-8 (FP64) or 5e-6 (mixed) */
+  int maxit;            /* 0 -> 300 */
+} pw_request;
+
+typedef struct {
+  double *eig;          /* caller-owned host buffer of nbands doubles (filled) */
+  int status;           /* pw_status of this request (PW_ERR_BUSY: larger than the budget) */
+  int iters, npw;
+  double max_resid, orth_err;
+  double t_admit, t_done, latency;   /* seconds; latency = t_done - arrival */
+  size_t hbm_bytes;     /* footprint used for admission */
+} pw_result;
+
+typedef struct {
+  int max_slots;        /* requests on the GPU at once (worker threads / streams) */
+  size_t hbm_budget;    /* bytes admitted at once; 0 -> 80% of free device memory */
+  int precision;        /* PW_FP64 or PW_MIXED */
+  double time_scale;    /* multiplies arrival times; 0 -> 1 */
+} pw_serve_opts;
+
+/* Device-memory footprint model used to admit a request (bytes). */
+size_t pw_request_footprint(const pw_request *req, int precision);
+
+/* Serves a stream of requests with continuous batching on the current
+ * device: a request is admitted at its arrival time once a slot is free and
+ * its footprint fits under the budget next to the requests already running;
+ * admitted requests run concurrently on their own streams, so their kernels
+ * overlap; results[i] receives the eigenvalues, status and timings of
+ * req[i].  Each request's result is independent of the mix (inputs from its
+ * seed, deterministic kernels).  Blocks until every request has finished.
+ * Errors: PW_ERR_ARG (bad options or request fields, NULL eig buffer),
+ * PW_ERR_CUDA; per-request failures are reported in results[i].status. */
+pw_status pw_serve(const pw_serve_opts *opts, const pw_request *req, int nreq, pw_result *results);
+
 /* FP64 Hermitian eigensolver used by the Rayleigh-Ritz step (the small dense
  * eigensolve, Syevd in Sec. III-D): Householder reduction to a real
  * tridiagonal, divide and conquer, back-transformation.  A: device complex128

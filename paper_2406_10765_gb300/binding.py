@@ -55,6 +55,24 @@ class pw_step_report(ct.Structure):
                 ("ms_rr_part", ct.c_double * 5)]
 
 
+class pw_request(ct.Structure):
+    _fields_ = [("species", ct.c_int), ("ncell", ct.c_int), ("ecut", ct.c_double),
+                ("nbands", ct.c_int), ("seed", ct.c_uint64), ("t_arrival", ct.c_double),
+                ("tol", ct.c_double), ("maxit", ct.c_int)]
+
+
+class pw_result(ct.Structure):
+    _fields_ = [("eig", ct.POINTER(ct.c_double)), ("status", ct.c_int), ("iters", ct.c_int),
+                ("npw", ct.c_int), ("max_resid", ct.c_double), ("orth_err", ct.c_double),
+                ("t_admit", ct.c_double), ("t_done", ct.c_double), ("latency", ct.c_double),
+                ("hbm_bytes", ct.c_size_t)]
+
+
+class pw_serve_opts(ct.Structure):
+    _fields_ = [("max_slots", ct.c_int), ("hbm_budget", ct.c_size_t), ("precision", ct.c_int),
+                ("time_scale", ct.c_double)]
+
+
 class pw_solve_report(ct.Structure):
     _fields_ = [("iters", ct.c_int), ("max_resid", ct.c_double), ("orth_err", ct.c_double),
                 ("seconds", ct.c_double), ("device_bytes", ct.c_size_t)]
@@ -140,6 +158,46 @@ _launches = _sig("pw_kernel_launches", ct.c_uint64, [])
 
 def pw_kernel_launches() -> int:
     return int(_launches())
+
+
+_serve = _sig("pw_serve", ct.c_int, [ct.POINTER(pw_serve_opts), ct.POINTER(pw_request), ct.c_int,
+                                      ct.POINTER(pw_result)])
+_footprint = _sig("pw_request_footprint", ct.c_size_t, [ct.POINTER(pw_request), ct.c_int])
+
+
+def _mkreq(r):
+    q = pw_request()
+    q.species = {"Si": 0, "C": 1, 0: 0, 1: 1}[r["species"]]
+    q.ncell, q.ecut, q.nbands = int(r["n"]), float(r["ecut"]), int(r["nbands"])
+    q.seed, q.t_arrival = int(r["seed"]), float(r.get("t_arrival", 0.0))
+    q.tol, q.maxit = float(r.get("tol", 0.0)), int(r.get("maxit", 0))
+    return q
+
+
+def pw_request_footprint(r, precision="fp64"):
+    return int(_footprint(ct.byref(_mkreq(r)), _PREC[precision]))
+
+
+def pw_serve(requests, max_slots=4, hbm_budget=0, precision="fp64", time_scale=1.0):
+    """Serve a list of request dicts (species, n, ecut, nbands, seed, t_arrival[, tol, maxit]).
+    Returns a list of dicts with eig (numpy), status, iters, timings."""
+    n = len(requests)
+    reqs = (pw_request * max(n, 1))(*[_mkreq(r) for r in requests])
+    eigs = [np.zeros(int(r["nbands"])) for r in requests]
+    res = (pw_result * max(n, 1))()
+    for i in range(n):
+        res[i].eig = eigs[i].ctypes.data_as(ct.POINTER(ct.c_double))
+    o = pw_serve_opts()
+    o.max_slots, o.hbm_budget, o.precision, o.time_scale = int(max_slots), int(hbm_budget), \
+        _PREC[precision], float(time_scale)
+    _check(_serve(ct.byref(o), reqs, n, res), "pw_serve")
+    out = []
+    for i in range(n):
+        r = res[i]
+        out.append(dict(eig=eigs[i], status=r.status, iters=r.iters, npw=r.npw,
+                        max_resid=r.max_resid, orth_err=r.orth_err, t_admit=r.t_admit,
+                        t_done=r.t_done, latency=r.latency, hbm_bytes=r.hbm_bytes))
+    return out
 
 
 def pw_strerror(status: int) -> str:

@@ -1,0 +1,61 @@
+"""pw_serve: continuous batching of fixed-potential eigensolves.  Each result
+must be the same alone and in the mix; admission refuses what does not fit;
+a bad request fails alone without disturbing the others."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import pw_oracle as O
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _requests():
+    reqs = synth.serving_requests(6, rate_per_s=20.0, seed=77)
+    for r in reqs:                       # keep the GPU test small: 8-atom cells
+        r["n"] = 1
+        r["nbands"] = 18
+    return reqs
+
+
+def test_serve_alone_equals_mix_and_oracle():
+    import paper_2406_10765_gb300 as pw
+    reqs = _requests()
+    mix = pw.pw_serve(reqs, max_slots=3, precision="fp64")
+    for r, m in zip(reqs, mix):
+        assert m["status"] == 0, m
+        alone = pw.pw_serve([dict(r, t_arrival=0.0)], max_slots=1, precision="fp64")[0]
+        assert np.array_equal(alone["eig"], m["eig"])
+        assert m["max_resid"] <= 1e-8
+    # the generated inputs are the seeded draws: dense diagonalisation agrees
+    r, m = reqs[0], mix[0]
+    ci = synth.cell_inputs(r["species"], 1, r["seed"])
+    cell = O.make_cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], r["ecut"])
+    w, _ = O.dense_eigs(cell, r["nbands"])
+    assert np.abs(m["eig"] - w).max() < 1e-10
+    assert all(x["latency"] >= 0 for x in mix)
+
+
+def test_serve_mixed_precision_close_to_fp64():
+    import paper_2406_10765_gb300 as pw
+    reqs = _requests()[:3]
+    a = pw.pw_serve(reqs, max_slots=3, precision="fp64")
+    b = pw.pw_serve(reqs, max_slots=3, precision="mixed")
+    for x, y in zip(a, b):
+        assert x["status"] == 0 and y["status"] == 0
+        assert np.abs(x["eig"] - y["eig"]).max() <= 1e-6
+        assert y["orth_err"] <= 1e-10
+
+
+def test_serve_admission_and_fault_isolation():
+    import paper_2406_10765_gb300 as pw
+    reqs = _requests()[:3]
+    # nothing fits a 1 MB budget: every request is refused, none runs
+    out = pw.pw_serve(reqs, max_slots=2, hbm_budget=1 << 20)
+    assert all(o["status"] == pw.PW_ERR_BUSY for o in out)
+    # an impossible band count fails on its own; the others are unaffected
+    bad = dict(reqs[1], nbands=5000)
+    out = pw.pw_serve([reqs[0], bad, reqs[2]], max_slots=3)
+    assert out[0]["status"] == 0 and out[2]["status"] == 0
+    assert out[1]["status"] == pw.PW_ERR_ARG
