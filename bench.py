@@ -41,14 +41,51 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
     ap.add_argument("--workload", default="si512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-rate", type=float, default=0.5)
     return ap.parse_args()
 
 
+def serve_sample(args):
+    """A bounded prefix of the seeded 2000-request serving stream (Si/C, n in
+    1..3, Ecut ~ U[8, 12], bands = 1.125 x occupied, Poisson arrivals), served
+    with continuous batching in mixed precision: solves/s and p50/p99 latency."""
+    import numpy as np
+    import synth
+    import paper_2406_10765_gb300 as pw
+    reqs = synth.serving_requests(2000, rate_per_s=args.serve_rate, seed=2024)[:args.serve_requests]
+    t0 = time.perf_counter()
+    out = pw.pw_serve(reqs, max_slots=4, precision="mixed")
+    wall = time.perf_counter() - t0
+    ok = [o for o in out if o["status"] in (0, -5)]
+    lat = np.array([o["latency"] for o in ok])
+    return {"metric": "served fixed-potential eigensolves", "solves_per_s": len(ok) / wall,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "requests": len(reqs), "completed": len(ok),
+            "converged": sum(o["status"] == 0 for o in out),
+            "max_resid": float(max(o["max_resid"] for o in ok)),
+            "arrival_rate_per_s": args.serve_rate, "slots": 4, "precision": "mixed",
+            "sample": f"first {len(reqs)} requests of the seeded 2000-request stream"}
+
+
 # ------------------------------------------------------------------ helpers --
+
+def reduce_timing(ms: float, steps: int, world: int, device=None):
+    """Replicas only: the slowest rank's time sets the job time; the value is
+    the steps all ranks completed divided by it.  Returns (max_ms, iters/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * steps / (ms / 1e3)
 
 def step_flops(npw, nb, ns, k, nproj, grid):
     """Algorithmic FLOPs of one step (complex products counted as 8 real flops)."""
@@ -240,11 +277,7 @@ def run_gpu(args):
     launches = pw.pw_kernel_launches() - launches0
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1e3)
+    ms, value = reduce_timing(ms, args.steps, world, device="cuda")
 
     # roofline of the dominant stage, from the solver's CUDA events
     stage = {k: sum(getattr(r, "ms_" + k) for r in reps) / len(reps)
@@ -287,7 +320,7 @@ def run_gpu(args):
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if args.precision == "fp64" else "f32/bf16-split+f64",
+           "dtype": "f64" if args.precision == "fp64" else "f16x2-split tensor + f32 FFT + f64 dense",
            "data": "synthetic",
            "config": {"workload": wl["name"], "npw": cell.npw, "grid": list(cell.grid),
                       "nbands": nb, "nproj": cell.nproj, "nsub": ns, "precision": args.precision,
@@ -296,6 +329,24 @@ def run_gpu(args):
            "roofline": roof, "gpu_launches": launches, "launches_before_timed": launches0,
            "clocks": clk}
     pw.pw_solver_destroy(solver)
+
+    if args.precision == "mixed" and not args.no_fp64:
+        # the same step in FP64 (one warm-up, one timed): the "mixed vs FP64" ratio
+        cell.set_precision("fp64")
+        s64 = pw.pw_solver_create(cell.h, nb, tol=0.0, seed=0, precision="fp64")
+        pw.pw_subspace_step(cell.h, s64)
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        pw.pw_subspace_step(cell.h, s64)
+        f1.record(stream)
+        barrier()
+        ms64 = f0.elapsed_time(f1)
+        pw.pw_solver_destroy(s64)
+        cell.set_precision("mixed")
+        out["fp64_comparison"] = {"iters_per_s": 1e3 / ms64, "ms_per_step": ms64,
+                                  "mixed_speedup": ms64 / (ms / args.steps)}
 
     if not args.no_e2e:
         # end to end through pw_eigsolve with host buffers: host start block in,
@@ -312,6 +363,8 @@ def run_gpu(args):
                       "d2h_bytes_per_step": eig.nbytes // max(1, rep.iters),
                       "note": "pw_eigsolve from a host start block: upload, H X0, initial "
                               "Rayleigh-Ritz, the steps, eigenvalues back to the host"}
+    if rank == 0 and not args.no_serve:
+        out["serving"] = serve_sample(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sec, note, parts = oracle_sample(wl)
         out["cpu_baseline"] = {"value": 1.0 / sec, "unit": "iters/s", "cores": cpu_cores(),

@@ -106,6 +106,14 @@ __global__ void k_mirror_upper_to_lower(double2 *M, int n) {
   M[i + (long)j * n] = make_double2(u.x, -u.y);
 }
 
+// out (ld n) = 0.5 (M + M^H) of an n x n matrix (ld)
+__global__ void k_copy_herm(const double2 *M, int ld, int n, double2 *out) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const double2 a = M[i + (long)j * ld], b = M[j + (long)i * ld];
+  out[i + (long)j * n] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+}
+
 // in-place Hermitian average of an n x n matrix (ld n)
 __global__ void k_hermitize(double2 *M, int n) {
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
@@ -260,17 +268,22 @@ __device__ __forceinline__ double2 prev_alpha(const double2 *dotpart, int ndot, 
   return cmul(make_double2(-0.5 * t.x, -0.5 * t.y), s);
 }
 
-__global__ void k_house_lazy(double2 *A, int n, int k, const double2 *pprev, const double2 *dotpart,
-                             int ndot, int has_prev, double *d, double *e, double2 *tau) {
-  __shared__ double sh[32];
+// one block: apply the pending update to column k and build reflector k.
+// p and the partial dots of step k-1 are read with L1-bypassing loads (they
+// may have been written by other blocks of the same kernel).
+__device__ void house_step(double2 *A, int n, int k, const double2 *pprev, const double2 *dotpart,
+                           int ndot, int has_prev, double *d, double *e, double2 *tau, double *sh) {
   double2 *col = A + (long)k * n;
   if (has_prev) {
     const double2 *vp = A + k + (long)(k - 1) * n;     // v_{k-1}[r - k], rows r >= k
-    const double2 al = prev_alpha(dotpart, ndot, tau[k - 1]);
+    double2 sdot = make_double2(0.0, 0.0);
+    for (int b = 0; b < ndot; ++b) sdot = cadd(sdot, __ldcg(&dotpart[b]));
+    const double2 tk1 = tau[k - 1];
+    const double2 al = cmul(make_double2(-0.5 * tk1.x, -0.5 * tk1.y), sdot);
     // w_{k-1} = p_{k-1} + alpha v_{k-1}
-    const double2 w0 = cadd(pprev[0], al);
+    const double2 w0 = cadd(__ldcg(&pprev[0]), al);
     for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
-      const double2 vr = vp[r - k], wr = cadd(pprev[r - k], cmul(al, vr));
+      const double2 vr = vp[r - k], wr = cadd(__ldcg(&pprev[r - k]), cmul(al, vr));
       // A_rk -= v_r conj(w_0) + w_r conj(v_0), v_0 = 1
       const double2 t = cmul(vr, make_double2(w0.x, -w0.y));
       col[r].x -= t.x + wr.x;
@@ -278,6 +291,7 @@ __global__ void k_house_lazy(double2 *A, int n, int k, const double2 *pprev, con
     }
     __syncthreads();
   }
+  __syncthreads();
   const int m = n - k - 1;
   double2 *x = col + k + 1;
   double s = 0.0;
@@ -307,39 +321,54 @@ __global__ void k_house_lazy(double2 *A, int n, int k, const double2 *pprev, con
   }
 }
 
-// one CTA per lower tile (I >= J) of the trailing block (rows/cols >= k+1)
+__global__ void k_house_lazy(double2 *A, int n, int k, const double2 *pprev, const double2 *dotpart,
+                             int ndot, int has_prev, double *d, double *e, double2 *tau) {
+  __shared__ double sh[32];
+  house_step(A, n, k, pprev, dotpart, ndot, has_prev, d, e, tau, sh);
+}
+
+// one CTA per lower tile (I >= J) of the trailing block (rows/cols >= k+1).
+// Phase 1: each thread updates 4 elements of the 32 x 32 tile and parks them
+// in shared memory.  Phase 2: threads 0-31 form the row sums sum_c a_rc v_c
+// (thread = row), threads 32-63 the column sums sum_r conj(a_rc) v_r (thread
+// = column), each a plain serial loop over the tile: no FP64 shuffle trees.
 __global__ void __launch_bounds__(256) k_her2_hemv(double2 *A, int n, int k, const double2 *pprev,
                                                    const double2 *dotpart, int ndot,
                                                    const double2 *tau, int has_prev, double2 *part,
                                                    int nmax) {
-  __shared__ double2 colacc[8][TT];
+  __shared__ double2 tile[TT][TT + 1];     // tile[row][col], zero outside the lower part
+  __shared__ double2 vrow[TT], vcol[TT], csum[TT];
   __shared__ double2 s_al;
   const int t = blockIdx.x;
   int I = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
   while ((I + 1) * (I + 2) / 2 <= t) ++I;
   while (I * (I + 1) / 2 > t) --I;
   const int J = t - I * (I + 1) / 2;
-  const int m = n - k - 1, o = k + 1;
-  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;   // 8 warps x 4 rows
-  const int c = o + TT * J + lane;                            // this lane's column
+  const int o = k + 1;
+  const int r0 = o + TT * I, c0 = o + TT * J;
   const double2 *vk = A + o + (long)k * n;                    // v_k[x], x = row - o
   const double2 *vp = A + k + (long)(k - 1) * n;              // v_{k-1}[x], x = row - k
   if (threadIdx.x == 0 && has_prev) s_al = prev_alpha(dotpart, ndot, tau[k - 1]);
+  if (threadIdx.x < TT) {
+    const int r = r0 + threadIdx.x, c = c0 + threadIdx.x;
+    vrow[threadIdx.x] = r < n ? vk[r - o] : make_double2(0.0, 0.0);
+    vcol[threadIdx.x] = c < n ? vk[c - o] : make_double2(0.0, 0.0);
+  }
   __syncthreads();
   const double2 al = has_prev ? s_al : make_double2(0.0, 0.0);
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  const int c = c0 + lane;
   const bool cin = c < n;
-  double2 vc = make_double2(0.0, 0.0), vpc = vc, wpc = vc;
-  if (cin) {
-    vc = vk[c - o];
-    if (has_prev) { vpc = vp[c - k]; wpc = cadd(pprev[c - k], cmul(al, vpc)); }
+  double2 vpc = make_double2(0.0, 0.0), wpc = vpc;
+  if (cin && has_prev) {
+    vpc = vp[c - k];
+    wpc = cadd(pprev[c - k], cmul(al, vpc));
   }
-  double2 cacc = make_double2(0.0, 0.0);
+#pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int r = o + TT * I + wq * 4 + q;
-    const bool rin = r < n;
-    const bool use = rin && cin && (I != J || c <= r);
+    const int rl = wq * 4 + q, r = r0 + rl;
     double2 a = make_double2(0.0, 0.0);
-    if (use) {
+    if (r < n && cin && (I != J || c <= r)) {
       double2 *ap = A + r + (long)c * n;
       a = *ap;
       if (has_prev) {
@@ -350,44 +379,47 @@ __global__ void __launch_bounds__(256) k_her2_hemv(double2 *A, int n, int k, con
         *ap = a;
       }
     }
-    // row part: sum_c a_rc v_c
-    double2 rp = cmul(a, vc);
-    for (int off = 16; off > 0; off >>= 1) {
-      rp.x += __shfl_xor_sync(0xffffffffu, rp.x, off);
-      rp.y += __shfl_xor_sync(0xffffffffu, rp.y, off);
-    }
-    // column part (strictly below the diagonal): conj(a_rc) v_r
-    if (use && (I != J || c < r)) cacc = cadd(cacc, cmulc(a, vk[r - o]));
-    if (lane == 0 && rin) {
-      // diagonal tiles also collect the column parts below (added after the loop)
-      part[(long)J * nmax + (r - o)] = rp;
-    }
+    tile[rl][lane] = a;
   }
-  colacc[wq][lane] = cacc;
   __syncthreads();
   if (threadIdx.x < TT) {
-    const int cc = o + TT * J + threadIdx.x;
-    if (cc < n) {
-      double2 s = colacc[0][threadIdx.x];
-      for (int w = 1; w < 8; ++w) s = cadd(s, colacc[w][threadIdx.x]);
-      if (I != J) {
-        part[(long)I * nmax + (cc - o)] = s;
-      } else {
-        // same slot as the row part of the diagonal tile: add
-        double2 *pp = &part[(long)J * nmax + (cc - o)];
-        *pp = cadd(*pp, s);
-      }
+    // row sums for row r (diagonal included)
+    const int rl = threadIdx.x, r = r0 + rl;
+    double2 s = make_double2(0.0, 0.0);
+#pragma unroll 8
+    for (int cl = 0; cl < TT; ++cl) s = cadd(s, cmul(tile[rl][cl], vcol[cl]));
+    if (r < n) {
+      if (I != J) part[(long)J * nmax + (r - o)] = s;
+      else tile[rl][TT] = s;                 // combined with the column sums below
     }
+  } else if (threadIdx.x < 2 * TT) {
+    // column sums for column c, strictly below the diagonal
+    const int cl = threadIdx.x - TT, cc = c0 + cl;
+    double2 s = make_double2(0.0, 0.0);
+#pragma unroll 8
+    for (int rl = 0; rl < TT; ++rl)
+      if (I != J || rl > cl) s = cadd(s, cmulc(tile[rl][cl], vrow[rl]));
+    if (cc < n && I != J) part[(long)I * nmax + (cc - o)] = s;
+    if (I == J) csum[cl] = s;                // park for the diagonal tile
   }
-  (void)m;
+  __syncthreads();
+  if (I == J && threadIdx.x < TT) {
+    const int rl = threadIdx.x, r = r0 + rl;
+    if (r < n) part[(long)J * nmax + (r - o)] = cadd(tile[rl][TT], csum[rl]);
+  }
 }
 
 // p = tau sum_c part[c] (one thread per row) and per-block partial dots
-// p^H v; w = p + alpha v is formed by the next step's kernels
-__global__ void __launch_bounds__(256) k_hemv_rows(const double2 *A, int n, int k, const double2 *part,
-                                                   int nT, int nmax, const double2 *tau, double2 *p,
-                                                   double2 *dotpart) {
+// p^H v; the block that finishes last then performs step k+1's column
+// update and reflector (or the last diagonal after the final step):
+// blocks publish p and their partial dots, fence, and take a ticket; no block
+// waits on another.
+__global__ void __launch_bounds__(256) k_hemv_rows_next(double2 *A, int n, int k, const double2 *part,
+                                                        int nT, int nmax, double2 *tau, double2 *p,
+                                                        double2 *dotpart, unsigned *ticket, double *d,
+                                                        double *e) {
   __shared__ double sh[32];
+  __shared__ unsigned s_ticket;
   const int m = n - k - 1, o = k + 1;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const double2 t = tau[k];
@@ -403,7 +435,27 @@ __global__ void __launch_bounds__(256) k_hemv_rows(const double2 *A, int n, int 
   }
   dr = block_sum(dr, sh);
   di = block_sum(di, sh);
-  if (threadIdx.x == 0) dotpart[blockIdx.x] = make_double2(dr, di);
+  if (threadIdx.x == 0) {
+    dotpart[blockIdx.x] = make_double2(dr, di);
+    __threadfence();
+    s_ticket = atomicAdd(ticket, 1u);
+  }
+  __syncthreads();
+  if (s_ticket != gridDim.x - 1) return;
+  // last block: every p and partial dot of step k is visible
+  __threadfence();
+  if (threadIdx.x == 0) *ticket = 0u;
+  const int ndot = gridDim.x;
+  if (k + 2 < n) {
+    house_step(A, n, k + 1, p, dotpart, ndot, 1, d, e, tau, sh);
+  } else if (threadIdx.x == 0) {
+    // k = n - 2: last diagonal after the final pending update (v = 1)
+    double2 sdot = make_double2(0.0, 0.0);
+    for (int b = 0; b < ndot; ++b) sdot = cadd(sdot, __ldcg(&dotpart[b]));
+    const double2 al = cmul(make_double2(-0.5 * t.x, -0.5 * t.y), sdot);
+    const double2 w0 = cadd(__ldcg(&p[0]), al);
+    d[n - 1] = A[(n - 1) + (long)(n - 1) * n].x - 2.0 * w0.x;
+  }
 }
 
 // last diagonal after the final pending update (v_{n-2} = 1, w_{n-2} = w[0])
@@ -762,24 +814,37 @@ __global__ void k_bt_init(const double *Z, int n, int nb, double2 *Y) {
   Y[idx] = make_double2(Z[idx], 0.0);
 }
 
-// y <- y - tau_k v (v^H y) for every column; one warp per column
-__global__ void k_bt_step(const double2 *A, int n, int k, const double2 *tau, double2 *Y, int nb) {
-  const int col = blockIdx.x * 4 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (col >= nb) return;
-  const int m = n - k - 1;
-  const double2 *v = A + (k + 1) + (long)k * n;
-  double2 *y = Y + (long)col * n + (k + 1);
-  double sr = 0.0, si = 0.0;
-  for (int i = lane; i < m; i += 32) {
-    const double2 p = cmulc(v[i], y[i]);
-    sr += p.x;
-    si += p.y;
+constexpr int BTB = 128;  // reflectors per compact-WY block
+
+// Vb (mb x b, ld mb) = reflectors j0..j0+b-1 with explicit zeros above their unit
+// entries; reflector j lives in A[j+1:, j] and Vb row q is matrix row j0+1+q
+__global__ void k_copy_panel(const double2 *A, int n, int j0, int b, double2 *Vb, int mb) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)mb * b) return;
+  const int q = (int)(idx % mb), c = (int)(idx / mb);
+  const int row = j0 + 1 + q, j = j0 + c;
+  Vb[idx] = row >= j + 1 ? A[row + (long)j * n] : make_double2(0.0, 0.0);
+}
+
+// T (b x b, upper, ld b): T_ii = tau_i; T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i],
+// G = Vb^H Vb.  One thread per row r; column i of T depends on columns < i.
+__global__ void k_build_T(const double2 *G, const double2 *tau, int j0, int b, double2 *T) {
+  const int r = threadIdx.x;
+  if (r < b)
+    for (int c = 0; c < b; ++c) T[r + (long)c * b] = make_double2(0.0, 0.0);
+  __syncthreads();
+  for (int i = 0; i < b; ++i) {
+    const double2 ti = tau[j0 + i];
+    if (r < i) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int c = r; c < i; ++c) s = cadd(s, cmul(T[r + (long)c * b], G[c + (long)i * b]));
+      const double2 v = cmul(ti, s);
+      T[r + (long)i * b] = make_double2(-v.x, -v.y);
+    } else if (r == i) {
+      T[r + (long)i * b] = ti;
+    }
+    __syncthreads();
   }
-  sr = warp_sum(sr);
-  si = warp_sum(si);
-  const double2 f = cmul(tau[k], make_double2(sr, si));
-  for (int i = lane; i < m; i += 32) y[i] = csub(y[i], cmul(f, v[i]));
 }
 
 void build_tree(pw_dense_ws *ws, int n) {
@@ -840,7 +905,13 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
   ok = ok && get((void **)&ws->nodes, (size_t)3 * nmax * 4 + 64) &&
        get((void **)&ws->knode, (size_t)nmax * 4 + 64) &&
        get((void **)&ws->rhonode, (size_t)nmax * 8 + 64);
+  ok = ok && get((void **)&ws->ticket, 64) && cudaMemset(ws->ticket, 0, 64) == cudaSuccess;
+  ok = ok && get((void **)&ws->Vb, (size_t)nmax * BTB * 16) && get((void **)&ws->Gv, BTB * BTB * 16) &&
+       get((void **)&ws->Tb, BTB * BTB * 16) && get((void **)&ws->Wk, (size_t)BTB * nbmax * 16) &&
+       get((void **)&ws->Wk2, (size_t)BTB * nbmax * 16);
   ws->gemm_ws_elems = std::max(pw_zgemm_ws_elems(nmax, nmax, nmax), pw_zgemm_ws_elems(nmax, nbmax, nmax));
+  ws->gemm_ws_elems = std::max(ws->gemm_ws_elems, pw_zgemm_ws_elems(BTB, nbmax, nmax));
+  ws->gemm_ws_elems = std::max(ws->gemm_ws_elems, pw_zgemm_ws_elems(BTB, BTB, nmax));
   if (ok && ws->gemm_ws_elems) ok = get((void **)&ws->gemm_ws, ws->gemm_ws_elems * 16);
   if (!ok) { pw_dense_free(ws); return PW_ERR_OOM; }
   for (cudaEvent_t &e : ws->ev)
@@ -856,7 +927,8 @@ void pw_dense_free(pw_dense_ws *ws) {
   void *ptrs[] = {ws->G, ws->A, ws->T, ws->Linv, ws->Y, ws->dscale, ws->piv, ws->flag, ws->d, ws->e,
                   ws->lam, ws->tau, ws->p, ws->w, ws->part, ws->Z, ws->W, ws->U, ws->Ds, ws->zs,
                   ws->DK, ws->zK, ws->tauK, ws->zh, ws->lamK, ws->dD, ws->lnew, ws->perm, ws->colK,
-                  ws->orig, ws->dcol, ws->src, ws->nodes, ws->knode, ws->rhonode, ws->gemm_ws};
+                  ws->orig, ws->dcol, ws->src, ws->nodes, ws->knode, ws->rhonode, ws->gemm_ws,
+                  ws->Vb, ws->Gv, ws->Tb, ws->Wk, ws->Wk2, ws->ticket};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : ws->ev)
@@ -880,22 +952,27 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
   // 1. Householder tridiagonalisation (lower triangle, lazy rank-2 updates)
   if (ws->ev[2]) cudaEventRecord(ws->ev[2], st);
   double2 *dotpart = ws->w;     // per-block partial dots of the previous step
+  if (n == 1) {
+    pw_count_launch();
+    k_last_diag_lazy<<<1, 1, 0, st>>>(A, n, ws->p, dotpart, 0, ws->tau, 0, ws->d);
+  } else {
+    pw_count_launch();
+    k_house_lazy<<<1, 256, 0, st>>>(A, n, 0, ws->p, dotpart, 0, 0, ws->d, ws->e, ws->tau);
+  }
   int ndot = 0;
   for (int k = 0; k + 1 < n; ++k) {
     const int m = n - k - 1;
     const int has_prev = k > 0;
-    pw_count_launch();
-    k_house_lazy<<<1, 256, 0, st>>>(A, n, k, ws->p, dotpart, ndot, has_prev, ws->d, ws->e, ws->tau);
     const int nT = (m + TT - 1) / TT;
     pw_count_launch();
     k_her2_hemv<<<nT * (nT + 1) / 2, 256, 0, st>>>(A, n, k, ws->p, dotpart, ndot, ws->tau, has_prev,
                                                    ws->part, ws->nmax);
     ndot = (m + 255) / 256;
+    // p, partial dots, then (last block) step k+1's reflector or the last diagonal
     pw_count_launch();
-    k_hemv_rows<<<ndot, 256, 0, st>>>(A, n, k, ws->part, nT, ws->nmax, ws->tau, ws->p, dotpart);
+    k_hemv_rows_next<<<ndot, 256, 0, st>>>(A, n, k, ws->part, nT, ws->nmax, ws->tau, ws->p, dotpart,
+                                           ws->ticket, ws->d, ws->e);
   }
-  pw_count_launch();
-  k_last_diag_lazy<<<1, 1, 0, st>>>(A, n, ws->p, dotpart, ndot, ws->tau, n > 1, ws->d);
   PW_TRY(pw_check_launch("tridiag"));
 
   // 2. divide and conquer
@@ -937,11 +1014,29 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
   if (ws->ev[4]) cudaEventRecord(ws->ev[4], st);
   pw_count_launch();
   k_bt_init<<<(unsigned)(((long)n * nb + 255) / 256), 256, 0, st>>>(ws->Z, n, nb, Y);
-  for (int k = n - 2; k >= 0; --k)
-    {
+  // Y = H_0 H_1 ... H_{n-2} Z, blocks of BTB reflectors from the last:
+  // H_j0 ... H_j1-1 = I - V T V^H  ->  Y[j0+1:, :] -= V (T (V^H Y[j0+1:, :]))
+  {
+    const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0),
+                  mone = make_double2(-1.0, 0.0);
+    for (int j1 = n - 1; j1 > 0;) {
+      const int j0 = std::max(0, j1 - BTB), b = j1 - j0, mb = n - j0 - 1;
       pw_count_launch();
-      k_bt_step<<<(nb + 3) / 4, 128, 0, st>>>(A, n, k, ws->tau, Y, nb);
+      k_copy_panel<<<(unsigned)(((long)mb * b + 255) / 256), 256, 0, st>>>(A, n, j0, b, ws->Vb, mb);
+      PW_TRY(pw_zgemm('C', 'N', b, b, mb, one, ws->Vb, mb, ws->Vb, mb, zero, ws->Gv, b, ws->gemm_ws,
+                      ws->gemm_ws_elems, st));
+      pw_count_launch();
+      k_build_T<<<1, BTB, 0, st>>>(ws->Gv, ws->tau, j0, b, ws->Tb);   // BTB <= 1024 threads
+      double2 *Yb = Y + (j0 + 1);
+      PW_TRY(pw_zgemm('C', 'N', b, nb, mb, one, ws->Vb, mb, Yb, n, zero, ws->Wk, b, ws->gemm_ws,
+                      ws->gemm_ws_elems, st));
+      PW_TRY(pw_zgemm('N', 'N', b, nb, b, one, ws->Tb, b, ws->Wk, b, zero, ws->Wk2, b, ws->gemm_ws,
+                      ws->gemm_ws_elems, st));
+      PW_TRY(pw_zgemm('N', 'N', mb, nb, b, mone, ws->Vb, mb, ws->Wk2, b, one, Yb, n, ws->gemm_ws,
+                      ws->gemm_ws_elems, st));
+      j1 = j0;
     }
+  }
   return pw_check_launch("back-transform");
 }
 
@@ -1063,4 +1158,60 @@ extern "C" pw_status pw_heev(int n, int nb, void *A, double *w, void *Y, void *s
   if (r == PW_OK && cudaStreamSynchronize(st) != cudaSuccess) r = PW_ERR_CUDA;
   pw_dense_free(&ws);
   return r;
+}
+
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz in two halves, for callers that orthonormalise the basis
+// themselves (the mixed path does S L^-H on the tensor cores)
+// ---------------------------------------------------------------------------
+namespace {
+// M = d o Linv^H   (M[i][j] = d_i conj(Linv[j][i]), upper triangular)
+__global__ void k_make_M(const double2 *Linv, int n, const double *d, double2 *M, int ldm) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const double2 l = Linv[j + (long)i * n];
+  M[i + (long)j * ldm] = i <= j ? make_double2(d[i] * l.x, -d[i] * l.y) : make_double2(0.0, 0.0);
+}
+}  // namespace
+
+pw_status pw_rr_factor(pw_dense_ws *ws, int n, const double2 *G, int ldg, double2 *M, int ldm,
+                       int *chol_ok, cudaStream_t st, double piv_tol) {
+  if (n > ws->nmax) return PW_ERR_ARG;
+  *chol_ok = 1;
+  cudaEventRecord(ws->ev[0], st);
+  PW_CUDA(cudaMemsetAsync(ws->flag, 0, 16, st));
+  pw_count_launch();
+  k_diag_scale<<<(n + 127) / 128, 128, 0, st>>>(G, ldg, n, ws->dscale, ws->flag);
+  const dim3 g2((n + 31) / 32, (n + 31) / 32), b2(32, 32);
+  pw_count_launch();
+  k_scale_herm<<<g2, b2, 0, st>>>(G, ldg, n, ws->dscale, ws->G);
+  PW_TRY(pw_check_launch("scale"));
+  PW_TRY(cholesky(ws, ws->G, n, st));
+  pw_count_launch();
+  k_chol_check<<<1, 256, 0, st>>>(ws->piv, n, piv_tol, ws->flag);
+  int flag = 0;
+  PW_CUDA(cudaMemcpyAsync(&flag, ws->flag, 4, cudaMemcpyDeviceToHost, st));
+  PW_CUDA(cudaStreamSynchronize(st));
+  if (flag) { *chol_ok = 0; return PW_OK; }
+  PW_TRY(trinv(ws, ws->G, ws->Linv, n, st));
+  pw_count_launch();
+  k_make_M<<<g2, b2, 0, st>>>(ws->Linv, n, ws->dscale, M, ldm);
+  cudaEventRecord(ws->ev[1], st);
+  return pw_check_launch("rr_factor");
+}
+
+pw_status pw_rr_finish(pw_dense_ws *ws, int n, int nb, const double2 *At, int lda, const double2 *M,
+                       int ldm, double *theta, double2 *C, int ldc, cudaStream_t st) {
+  if (n > ws->nmax || nb > ws->nbmax || nb > n) return PW_ERR_ARG;
+  // Hermitian order-n matrix into the workspace (ld n), eigensolve, C = M Y
+  pw_count_launch();
+  const dim3 g2((n + 31) / 32, (n + 31) / 32), b2(32, 32);
+  k_copy_herm<<<g2, b2, 0, st>>>(At, lda, n, ws->A);
+  PW_TRY(pw_heev_lowest(ws, n, nb, ws->A, ws->lam, ws->Y, st));
+  PW_CUDA(cudaMemcpyAsync(theta, ws->lam, nb * 8, cudaMemcpyDeviceToDevice, st));
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  PW_TRY(pw_zgemm('N', 'N', n, nb, n, one, M, ldm, ws->Y, n, zero, C, ldc, ws->gemm_ws,
+                  ws->gemm_ws_elems, st));
+  cudaEventRecord(ws->ev[5], st);
+  return pw_check_launch("rr_finish");
 }

@@ -23,6 +23,9 @@ struct pw_dense_ws {
   int *knode = nullptr;       // per node: nondeflated count
   double *rhonode = nullptr;
   double2 *gemm_ws = nullptr; size_t gemm_ws_elems = 0;
+  // blocked back-transformation: reflector panel, its Gram, T, two work blocks
+  double2 *Vb = nullptr, *Gv = nullptr, *Tb = nullptr, *Wk = nullptr, *Wk2 = nullptr;
+  unsigned *ticket = nullptr;   // last-block-done counter of the Householder steps
   // host side tree for the current n
   int tree_n = -1;
   std::vector<std::vector<int>> levels;   // per level: flat (lo, mid, hi) triples
@@ -49,6 +52,16 @@ void pw_dense_free(pw_dense_ws *ws);
 pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, int ldg,
                            const double2 *A, int lda, double *theta, double2 *C, int ldc,
                            int *chol_ok, cudaStream_t st, double piv_tol = 1e-14);
+
+// Rayleigh-Ritz in two halves.  pw_rr_factor: Jacobi scaling d and Cholesky
+// of G (same pivot test), L^-1, and M = d o L^-H (n x n upper triangular,
+// ld ldm); synchronises.  pw_rr_finish: eigensolve of the Hermitian matrix
+// At = M^H A M (given, ld lda), theta (nb), C = M Y (n x nb, ldc).  The
+// sub-stage events are recorded as for pw_rayleigh_ritz.
+pw_status pw_rr_factor(pw_dense_ws *ws, int n, const double2 *G, int ldg, double2 *M, int ldm,
+                       int *chol_ok, cudaStream_t st, double piv_tol);
+pw_status pw_rr_finish(pw_dense_ws *ws, int n, int nb, const double2 *At, int lda, const double2 *M,
+                       int ldm, double *theta, double2 *C, int ldc, cudaStream_t st);
 
 // Hermitian eigensolver: lowest nb eigenpairs of the n x n matrix A (device,
 // destroyed).  lam: device n doubles (all eigenvalues, ascending); Y: device

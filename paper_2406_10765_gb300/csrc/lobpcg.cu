@@ -44,7 +44,9 @@ struct pw_solver {
   size_t bytes = 0;
   cudaEvent_t ev[8] = {};    // stage boundaries of the last step
   // mixed precision: split-FP16 operands of S, H S and the coefficients
-  pw_tc_operand opSA, opSB, opHSB, opST, opHST, opC, opCP;
+  pw_tc_operand opSA, opSB, opHSB, opST, opHST, opC, opCP, opM;
+  double2 *Mx = nullptr;     // mixed: d o L^-H of the current Gram (3nb x 3nb)
+  bool st_split_valid = false;   // opST holds the split of the current S
   float *rmax = nullptr;
   int *d_err = nullptr;
   double2 *Cz = nullptr;
@@ -219,33 +221,54 @@ pw_status gemm(pw_solver *s, char oa, char ob, int m, int n, int k, const double
 // information in mixed precision.
 double piv_tol(const pw_solver *s) { return s->precision == PW_MIXED ? 1e-6 : 1e-14; }
 
+// Mixed precision: from the Gram in s->G (order ns), factor G in FP64
+// (scaling, Cholesky, L^-1, M = d L^-H), orthonormalise the basis on the
+// tensor cores (S~ = S M, H S~ = H S M into S2, HS2), form A~ = S~^H H S~
+// there too, and finish in FP64 (eigensolve, C = M Y).
+pw_status rr_mixed_from_gram(pw_solver *s, int ns, int *chol_ok) {
+  const int npw = s->npw, nb = s->nb, ldg = 3 * nb;
+  PW_TRY(pw_rr_factor(&s->dws, ns, s->G, ldg, s->Mx, ldg, chol_ok, s->st, piv_tol(s)));
+  if (!*chol_ok) return PW_OK;
+  PW_TRY(pw_tc_operand_alloc(&s->opST, npw, 2 * ns));
+  PW_TRY(pw_tc_operand_alloc(&s->opHST, npw, 2 * ns));
+  PW_TRY(pw_tc_operand_alloc(&s->opM, 2 * ns, 2 * ns));
+  PW_TRY(pw_tc_split_trans(s->S, npw, npw, ns, s->rmax, &s->opST, s->st));
+  s->st_split_valid = true;
+  PW_TRY(pw_tc_split_trans(s->HS, npw, npw, ns, s->rmax, &s->opHST, s->st));
+  PW_TRY(pw_tc_split_coef(s->Mx, ldg, ns, ns, nullptr, &s->opM, s->st));
+  PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opM, 2 * ns, s->S2, npw, 1, 0, 0, s->d_err, s->st));
+  PW_TRY(pw_tc_gemm(&s->opHST, npw, &s->opM, 2 * ns, s->HS2, npw, 1, 0, 0, s->d_err, s->st));
+  PW_TRY(pw_tc_split_rows(s->S2, npw, npw, ns, 1, nullptr, &s->opSA, s->st));
+  PW_TRY(pw_tc_split_rows(s->HS2, npw, npw, ns, 0, nullptr, &s->opHSB, s->st));
+  PW_TRY(pw_tc_gemm(&s->opSA, 2 * ns, &s->opHSB, ns, s->A, ldg, 0, 0, 1, s->d_err, s->st));
+  return pw_rr_finish(&s->dws, ns, nb, s->A, ldg, s->Mx, ldg, s->theta, s->C, ldg, s->st);
+}
+
 // Rayleigh-Ritz on the first ns columns of (S, HS) -> theta, C (ns x nb, ld 3nb).
 // Events ev[3] / ev[4] bracket the Gram products.
 pw_status subspace_rr(pw_solver *s, int ns, int *chol_ok) {
   const int ldg = 3 * s->nb;
   cudaEventRecord(s->ev[3], s->st);
   if (s->precision == PW_MIXED) {
-    // split-FP16 tensor-core products; upper triangles, mirrored (Hermitian)
     const int npw = s->npw;
     PW_TRY(pw_tc_operand_alloc(&s->opSA, 2 * ns, 2 * npw));
     PW_TRY(pw_tc_operand_alloc(&s->opSB, ns, 2 * npw));
     PW_TRY(pw_tc_operand_alloc(&s->opHSB, ns, 2 * npw));
     PW_TRY(pw_tc_split_rows(s->S, npw, npw, ns, 1, nullptr, &s->opSA, s->st));
     PW_TRY(pw_tc_split_rows(s->S, npw, npw, ns, 0, nullptr, &s->opSB, s->st));
-    PW_TRY(pw_tc_split_rows(s->HS, npw, npw, ns, 0, nullptr, &s->opHSB, s->st));
     PW_TRY(pw_tc_gemm(&s->opSA, 2 * ns, &s->opSB, ns, s->G, ldg, 0, 0, 1, s->d_err, s->st));
-    PW_TRY(pw_tc_gemm(&s->opSA, 2 * ns, &s->opHSB, ns, s->A, ldg, 0, 0, 1, s->d_err, s->st));
-  } else {
-    // Hermitian products: upper-triangle tiles, mirrored
-    const size_t need = pw_zgemm_ws_elems(ns, ns, s->npw);
-    if (need > s->gws_elems) {
-      size_t cur = s->gws_elems * 16;
-      PW_TRY(pw_ensure((void **)&s->gws, &cur, need * 16));
-      s->gws_elems = cur / 16;
-    }
-    PW_TRY(pw_zgemm_herm(ns, s->npw, s->S, s->npw, s->S, s->npw, s->G, ldg, s->gws, s->gws_elems, s->st));
-    PW_TRY(pw_zgemm_herm(ns, s->npw, s->S, s->npw, s->HS, s->npw, s->A, ldg, s->gws, s->gws_elems, s->st));
+    cudaEventRecord(s->ev[4], s->st);
+    return rr_mixed_from_gram(s, ns, chol_ok);
   }
+  // Hermitian products: upper-triangle tiles, mirrored
+  const size_t need = pw_zgemm_ws_elems(ns, ns, s->npw);
+  if (need > s->gws_elems) {
+    size_t cur = s->gws_elems * 16;
+    PW_TRY(pw_ensure((void **)&s->gws, &cur, need * 16));
+    s->gws_elems = cur / 16;
+  }
+  PW_TRY(pw_zgemm_herm(ns, s->npw, s->S, s->npw, s->S, s->npw, s->G, ldg, s->gws, s->gws_elems, s->st));
+  PW_TRY(pw_zgemm_herm(ns, s->npw, s->S, s->npw, s->HS, s->npw, s->A, ldg, s->gws, s->gws_elems, s->st));
   cudaEventRecord(s->ev[4], s->st);
   return pw_rayleigh_ritz(&s->dws, ns, s->nb, s->G, ldg, s->A, ldg, s->theta, s->C, ldg, chol_ok, s->st,
                           piv_tol(s));
@@ -267,7 +290,8 @@ pw_status rotate(pw_solver *s, int ns, bool with_p) {
     PW_TRY(pw_tc_operand_alloc(&s->opST, npw, 2 * ns));
     PW_TRY(pw_tc_operand_alloc(&s->opHST, npw, 2 * ns));
     PW_TRY(pw_tc_operand_alloc(&s->opC, 2 * nb, 2 * ns));
-    PW_TRY(pw_tc_split_trans(s->S, npw, npw, ns, s->rmax, &s->opST, s->st));
+    if (!s->st_split_valid || s->opST.kpad != pw_tc_kpad(2 * ns))
+      PW_TRY(pw_tc_split_trans(s->S, npw, npw, ns, s->rmax, &s->opST, s->st));
     if (!s->fresh_h) PW_TRY(pw_tc_split_trans(s->HS, npw, npw, ns, s->rmax, &s->opHST, s->st));
     PW_TRY(pw_tc_split_coef(s->C, n3, ns, nb, nullptr, &s->opC, s->st));
     PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opC, 2 * nb, s->S2, npw, 1, 0, 0, s->d_err, s->st));
@@ -345,7 +369,9 @@ extern "C" void pw_solver_destroy(pw_solver *s) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : s->ev)
     if (e) cudaEventDestroy(e);
-  pw_tc_operand *ops[] = {&s->opSA, &s->opSB, &s->opHSB, &s->opST, &s->opHST, &s->opC, &s->opCP};
+  pw_tc_operand *ops[] = {&s->opSA, &s->opSB, &s->opHSB, &s->opST, &s->opHST, &s->opC, &s->opCP,
+                          &s->opM};
+  if (s->Mx) cudaFree(s->Mx);
   for (pw_tc_operand *o : ops) pw_tc_operand_free(o);
   if (s->rmax) cudaFree(s->rmax);
   if (s->d_err) cudaFree(s->d_err);
@@ -388,6 +414,10 @@ extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, voi
     pw_solver_destroy(s);
     return r;
   }
+  if (s->precision == PW_MIXED && (r = alloc((void **)&s->Mx, (size_t)n3 * n3 * 16, &acc))) {
+    pw_solver_destroy(s);
+    return r;
+  }
   s->bytes = acc + s->dws.bytes;
   for (cudaEvent_t &e : s->ev)
     if (cudaEventCreate(&e) != cudaSuccess) { pw_solver_destroy(s); return PW_ERR_CUDA; }
@@ -415,6 +445,7 @@ extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, voi
   std::swap(s->S, s->S2);
   std::swap(s->HS, s->HS2);
   s->hx_valid = !s->fresh_h;
+  s->st_split_valid = false;
   cudaMemcpyAsync(s->lam, s->theta, nb * 8, cudaMemcpyDeviceToDevice, s->st);
   if (cudaStreamSynchronize(s->st) != cudaSuccess) { pw_solver_destroy(s); return PW_ERR_CUDA; }
   *out = s;
@@ -477,8 +508,12 @@ extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_repor
   if (!ok && s->haveP) {
     ns = nb + k;
     dropped = 1;
-    PW_TRY(pw_rayleigh_ritz(&s->dws, ns, nb, s->G, n3, s->A, n3, s->theta, s->C, n3, &ok, s->st,
-                            piv_tol(s)));
+    if (s->precision == PW_MIXED) {
+      PW_TRY(rr_mixed_from_gram(s, ns, &ok));
+    } else {
+      PW_TRY(pw_rayleigh_ritz(&s->dws, ns, nb, s->G, n3, s->A, n3, s->theta, s->C, n3, &ok, s->st,
+                              piv_tol(s)));
+    }
   }
   if (!ok) return PW_ERR_CHOL;
   cudaEventRecord(s->ev[5], s->st);
@@ -491,6 +526,7 @@ extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_repor
   std::swap(s->S, s->S2);
   std::swap(s->HS, s->HS2);
   s->hx_valid = !s->fresh_h;
+  s->st_split_valid = false;
   PW_CUDA(cudaMemcpyAsync(s->lam, s->theta, nb * 8, cudaMemcpyDeviceToDevice, s->st));
   PW_CUDA(cudaStreamSynchronize(s->st));
   PW_TRY(check_tc_err(s));

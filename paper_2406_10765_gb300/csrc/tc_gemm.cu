@@ -41,6 +41,10 @@ constexpr int TMEM_COLS = 4 * BN;            // 2 accumulator buffers + compensa
 constexpr int CMP_COL = 2 * BN;              // TMEM column of the compensation terms
 constexpr int EPI_WARPS = 8;                 // 4 lane quarters x 2 column halves
 constexpr int EPI_COLS = BN / 2;
+// K blocks per TMEM accumulator buffer (K = 128): the tensor-core FP32
+// accumulation rounds toward zero, so longer chunks bias positive sums
+// (~2.5e-8 relative per MMA); two blocks keep the bias below ~1e-6
+constexpr int CHUNK_KB = 2;
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
 constexpr long long WAIT_CYCLES = 2000000000ll;   // ~1 s
 
@@ -226,29 +230,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---------------- MMA issuer: one K-block per accumulator buffer
+      // ---------------- MMA issuer: CHUNK_KB K-blocks per accumulator buffer
       const uint32_t idesc = idesc_f16();
-      for (int kb = 0; kb < kblocks; ++kb) {
-        const int b = kb & 1;
-        const uint32_t ub = kb >> 1;
+      const int nchunk = (kblocks + CHUNK_KB - 1) / CHUNK_KB;
+      bool ok = true;
+      for (int ch = 0; ch < nchunk && ok; ++ch) {
+        const int b = ch & 1;
+        const uint32_t ub = ch >> 1;
         if (!mbar_wait(&acce[b], (ub & 1) ^ 1)) { atomicOr(err, 8); break; }
-        const int s = kb % NSTAGE;
-        const uint32_t u = kb / NSTAGE;
-        if (!mbar_wait(&full[s], u & 1)) { atomicOr(err, 2); break; }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(smem + s * STAGE);
-        const uint32_t a1 = a0 + A_TILE;
-        const uint32_t b0 = a0 + 2 * A_TILE;
-        const uint32_t b1 = b0 + B_TILE;
         const uint32_t d = tmem + (uint32_t)(b * BN);
+        const int kb1 = min(kblocks, (ch + 1) * CHUNK_KB);
+        for (int kb = ch * CHUNK_KB; kb < kb1; ++kb) {
+          const int s = kb % NSTAGE;
+          const uint32_t u = kb / NSTAGE;
+          if (!mbar_wait(&full[s], u & 1)) { atomicOr(err, 2); ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(smem + s * STAGE);
+          const uint32_t a1 = a0 + A_TILE;
+          const uint32_t b0 = a0 + 2 * A_TILE;
+          const uint32_t b1 = b0 + B_TILE;
+          const bool first = kb == ch * CHUNK_KB;
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint32_t off = kk * 32;
-          mma_f16(d, smem_desc(a0 + off), smem_desc(b0 + off), idesc, kk != 0);
-          mma_f16(d, smem_desc(a0 + off), smem_desc(b1 + off), idesc, 1);
-          mma_f16(d, smem_desc(a1 + off), smem_desc(b0 + off), idesc, 1);
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint32_t off = kk * 32;
+            mma_f16(d, smem_desc(a0 + off), smem_desc(b0 + off), idesc, !(first && kk == 0));
+            mma_f16(d, smem_desc(a0 + off), smem_desc(b1 + off), idesc, 1);
+            mma_f16(d, smem_desc(a1 + off), smem_desc(b0 + off), idesc, 1);
+          }
+          mma_commit(&empty[s]);
         }
-        mma_commit(&empty[s]);
         mma_commit(&accf[b]);
       }
     }
@@ -269,9 +279,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int c0 = 0; c0 < EPI_COLS; c0 += 32) tmem_st32(cmp_base + c0, z);
     }
     bool ok = true;
-    for (int kb = 0; kb < kblocks; ++kb) {
-      const int b = kb & 1;
-      const uint32_t ub = kb >> 1;
+    const int nchunk = (kblocks + CHUNK_KB - 1) / CHUNK_KB;
+    for (int ch = 0; ch < nchunk; ++ch) {
+      const int b = ch & 1;
+      const uint32_t ub = ch >> 1;
       if (!mbar_wait(&accf[b], ub & 1)) { atomicOr(err, 4); ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t base = tmem + lanes + (uint32_t)(b * BN + h * EPI_COLS);

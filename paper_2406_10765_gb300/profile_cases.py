@@ -41,8 +41,11 @@ def main():
         s = pw.pw_solver_create(cell.h, 144, tol=0.0, seed=0, precision=prec)
         pw.pw_subspace_step(cell.h, s)
         for _ in range(a.reps):
+            l0 = pw.pw_kernel_launches()
             r = pw.pw_subspace_step(cell.h, s)
-        print(f"{a.case}: npw {cell.npw}, last step {r.ms:.1f} ms")
+            l1 = pw.pw_kernel_launches()
+        print(f"{a.case}: npw {cell.npw}, last step {r.ms:.1f} ms, launches before it {l0}, "
+              f"in it {l1 - l0}")
         pw.pw_solver_destroy(s)
     elif a.case == "tcgemm":
         k, m = 104415, 1152
