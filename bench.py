@@ -69,6 +69,8 @@ def serve_sample(args):
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "requests": len(reqs), "completed": len(ok),
             "converged": sum(o["status"] == 0 for o in out),
+            "status_counts": {str(k): sum(o["status"] == k for o in out)
+                              for k in sorted(set(o["status"] for o in out))},
             "max_resid": float(max(o["max_resid"] for o in ok)),
             "arrival_rate_per_s": args.serve_rate, "slots": 4, "precision": "mixed",
             "sample": f"first {len(reqs)} requests of the seeded 2000-request stream"}

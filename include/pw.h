@@ -153,7 +153,8 @@ typedef struct {
 } pw_step_report;
 
 typedef struct {
-  int iters;
+  int iters;            /* LOBPCG steps taken (all precisions) */
+  int fp64_iters;       /* of which FP64 refinement steps after a mixed solve */
   double max_resid;     /* final max residual norm (FP64) */
   double orth_err;      /* max |X^H X - I| of the final block (FP64) */
   double seconds;
@@ -191,9 +192,10 @@ void pw_solver_destroy(pw_solver *solver);
 
 /* Runs LOBPCG to max residual <= tol or maxit steps.  eig: host nb doubles
  * (required); psi_out: device complex128 npw x nb (ld) or NULL.  With
- * opts->precision == PW_MIXED the converged block is finished by
- * pw_solver_polish (FP64) and the reported residuals are FP64.  Returns
- * PW_ERR_NOCONV with eig / psi_out filled if maxit is reached. */
+ * opts->precision == PW_MIXED the block converged in mixed precision is
+ * finished by pw_solver_polish (FP64); bands still above tol then continue in
+ * FP64 (rep->fp64_iters) within maxit, and the reported residuals are FP64.
+ * Returns PW_ERR_NOCONV with eig / psi_out filled if maxit is reached. */
 pw_status pw_eigsolve(pw_cell *cell, const pw_solve_opts *opts, double *eig, void *psi_out,
                       int ld, pw_solve_report *rep, void *stream);
 

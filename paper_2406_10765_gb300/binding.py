@@ -74,7 +74,7 @@ class pw_serve_opts(ct.Structure):
 
 
 class pw_solve_report(ct.Structure):
-    _fields_ = [("iters", ct.c_int), ("max_resid", ct.c_double), ("orth_err", ct.c_double),
+    _fields_ = [("iters", ct.c_int), ("fp64_iters", ct.c_int), ("max_resid", ct.c_double), ("orth_err", ct.c_double),
                 ("seconds", ct.c_double), ("device_bytes", ct.c_size_t)]
 
 

@@ -905,7 +905,7 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
   ok = ok && get((void **)&ws->nodes, (size_t)3 * nmax * 4 + 64) &&
        get((void **)&ws->knode, (size_t)nmax * 4 + 64) &&
        get((void **)&ws->rhonode, (size_t)nmax * 8 + 64);
-  ok = ok && get((void **)&ws->ticket, 64) && cudaMemset(ws->ticket, 0, 64) == cudaSuccess;
+  ok = ok && get((void **)&ws->ticket, 64);
   ok = ok && get((void **)&ws->Vb, (size_t)nmax * BTB * 16) && get((void **)&ws->Gv, BTB * BTB * 16) &&
        get((void **)&ws->Tb, BTB * BTB * 16) && get((void **)&ws->Wk, (size_t)BTB * nbmax * 16) &&
        get((void **)&ws->Wk2, (size_t)BTB * nbmax * 16);
@@ -952,6 +952,7 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
   // 1. Householder tridiagonalisation (lower triangle, lazy rank-2 updates)
   if (ws->ev[2]) cudaEventRecord(ws->ev[2], st);
   double2 *dotpart = ws->w;     // per-block partial dots of the previous step
+  PW_CUDA(cudaMemsetAsync(ws->ticket, 0, sizeof(unsigned), st));
   if (n == 1) {
     pw_count_launch();
     k_last_diag_lazy<<<1, 1, 0, st>>>(A, n, ws->p, dotpart, 0, ws->tau, 0, ws->d);

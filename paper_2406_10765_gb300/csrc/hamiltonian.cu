@@ -31,13 +31,13 @@ static pw_status nonlocal_tc(pw_cell *c, const double2 *psi, int ld, int nb, dou
     cur = 0;
     PW_TRY(pw_ensure((void **)&c->d_rmax, &cur, (size_t)c->npw * sizeof(float)));
     PW_CUDA(cudaMemsetAsync(c->d_tc_err, 0, 16, st));
-    PW_TRY(pw_tc_operand_alloc(c->op_beta_rows, 2 * c->nproj, 2 * c->npw));
-    PW_TRY(pw_tc_operand_alloc(c->op_beta_t, c->npw, 2 * c->nproj));
+    PW_TRY(pw_tc_operand_alloc(c->op_beta_rows, 2 * c->nproj, 2 * c->npw, st));
+    PW_TRY(pw_tc_operand_alloc(c->op_beta_t, c->npw, 2 * c->nproj, st));
     PW_TRY(pw_tc_split_rows(c->d_beta, c->npw, c->npw, c->nproj, 1, nullptr, c->op_beta_rows, st));
     PW_TRY(pw_tc_split_trans(c->d_beta, c->npw, c->npw, c->nproj, c->d_rmax, c->op_beta_t, st));
   }
-  PW_TRY(pw_tc_operand_alloc(c->op_psi, nb, 2 * c->npw));
-  PW_TRY(pw_tc_operand_alloc(c->op_db, 2 * nb, 2 * c->nproj));
+  PW_TRY(pw_tc_operand_alloc(c->op_psi, nb, 2 * c->npw, st));
+  PW_TRY(pw_tc_operand_alloc(c->op_db, 2 * nb, 2 * c->nproj, st));
   PW_TRY(pw_tc_split_rows(psi, ld, c->npw, nb, 0, nullptr, c->op_psi, st));
   // B = beta^H psi  (nproj x nb)
   PW_TRY(pw_tc_gemm(c->op_beta_rows, 2 * c->nproj, c->op_psi, nb, c->d_B, c->nproj, 0, 0, 0,

@@ -229,9 +229,9 @@ pw_status rr_mixed_from_gram(pw_solver *s, int ns, int *chol_ok) {
   const int npw = s->npw, nb = s->nb, ldg = 3 * nb;
   PW_TRY(pw_rr_factor(&s->dws, ns, s->G, ldg, s->Mx, ldg, chol_ok, s->st, piv_tol(s)));
   if (!*chol_ok) return PW_OK;
-  PW_TRY(pw_tc_operand_alloc(&s->opST, npw, 2 * ns));
-  PW_TRY(pw_tc_operand_alloc(&s->opHST, npw, 2 * ns));
-  PW_TRY(pw_tc_operand_alloc(&s->opM, 2 * ns, 2 * ns));
+  PW_TRY(pw_tc_operand_alloc(&s->opST, npw, 2 * ns, s->st));
+  PW_TRY(pw_tc_operand_alloc(&s->opHST, npw, 2 * ns, s->st));
+  PW_TRY(pw_tc_operand_alloc(&s->opM, 2 * ns, 2 * ns, s->st));
   PW_TRY(pw_tc_split_trans(s->S, npw, npw, ns, s->rmax, &s->opST, s->st));
   s->st_split_valid = true;
   PW_TRY(pw_tc_split_trans(s->HS, npw, npw, ns, s->rmax, &s->opHST, s->st));
@@ -251,9 +251,9 @@ pw_status subspace_rr(pw_solver *s, int ns, int *chol_ok) {
   cudaEventRecord(s->ev[3], s->st);
   if (s->precision == PW_MIXED) {
     const int npw = s->npw;
-    PW_TRY(pw_tc_operand_alloc(&s->opSA, 2 * ns, 2 * npw));
-    PW_TRY(pw_tc_operand_alloc(&s->opSB, ns, 2 * npw));
-    PW_TRY(pw_tc_operand_alloc(&s->opHSB, ns, 2 * npw));
+    PW_TRY(pw_tc_operand_alloc(&s->opSA, 2 * ns, 2 * npw, s->st));
+    PW_TRY(pw_tc_operand_alloc(&s->opSB, ns, 2 * npw, s->st));
+    PW_TRY(pw_tc_operand_alloc(&s->opHSB, ns, 2 * npw, s->st));
     PW_TRY(pw_tc_split_rows(s->S, npw, npw, ns, 1, nullptr, &s->opSA, s->st));
     PW_TRY(pw_tc_split_rows(s->S, npw, npw, ns, 0, nullptr, &s->opSB, s->st));
     PW_TRY(pw_tc_gemm(&s->opSA, 2 * ns, &s->opSB, ns, s->G, ldg, 0, 0, 1, s->d_err, s->st));
@@ -287,9 +287,9 @@ __global__ void k_zero_top_rows(const double2 *C, int ld, int nrows_zero, int nr
 pw_status rotate(pw_solver *s, int ns, bool with_p) {
   const int npw = s->npw, nb = s->nb, n3 = 3 * nb;
   if (s->precision == PW_MIXED) {
-    PW_TRY(pw_tc_operand_alloc(&s->opST, npw, 2 * ns));
-    PW_TRY(pw_tc_operand_alloc(&s->opHST, npw, 2 * ns));
-    PW_TRY(pw_tc_operand_alloc(&s->opC, 2 * nb, 2 * ns));
+    PW_TRY(pw_tc_operand_alloc(&s->opST, npw, 2 * ns, s->st));
+    PW_TRY(pw_tc_operand_alloc(&s->opHST, npw, 2 * ns, s->st));
+    PW_TRY(pw_tc_operand_alloc(&s->opC, 2 * nb, 2 * ns, s->st));
     if (!s->st_split_valid || s->opST.kpad != pw_tc_kpad(2 * ns))
       PW_TRY(pw_tc_split_trans(s->S, npw, npw, ns, s->rmax, &s->opST, s->st));
     if (!s->fresh_h) PW_TRY(pw_tc_split_trans(s->HS, npw, npw, ns, s->rmax, &s->opHST, s->st));
@@ -301,7 +301,7 @@ pw_status rotate(pw_solver *s, int ns, bool with_p) {
       pw_count_launch();
       k_zero_top_rows<<<(unsigned)(((long)ns * nb + 255) / 256), 256, 0, s->st>>>(s->C, n3, nb, ns, nb, s->Cz);
       PW_TRY(pw_check_launch("zero_top_rows"));
-      PW_TRY(pw_tc_operand_alloc(&s->opCP, 2 * nb, 2 * ns));
+      PW_TRY(pw_tc_operand_alloc(&s->opCP, 2 * nb, 2 * ns, s->st));
       PW_TRY(pw_tc_split_coef(s->Cz, n3, ns, nb, nullptr, &s->opCP, s->st));
       PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opCP, 2 * nb, s->P, npw, 1, 0, 0, s->d_err, s->st));
       if (!s->fresh_h)
@@ -618,16 +618,33 @@ extern "C" pw_status pw_eigsolve(pw_cell *cell, const pw_solve_opts *o, double *
     // drifted above tol leaves the solve unconverged)
     if (sr.nactive == 0) break;
   }
+  int fp64_iters = 0;
   if (r == PW_OK && s->precision == PW_MIXED) {
     // FP64 Rayleigh-Ritz on the converged block: FP64 overlap, eigensolve,
     // residual norms and orthonormality
     r = pw_solver_polish(s);
     if (r == PW_OK) r = refresh_stats(s, st_h);
-    if (r == PW_OK) {
-      double rmax = 0.0;
-      for (int j = 0; j < s->nb; ++j) rmax = fmax(rmax, s->resid_h[j]);
-      conv = conv && rmax <= s->tol;
+    double rmax = 0.0;
+    for (int j = 0; j < s->nb; ++j) rmax = fmax(rmax, s->resid_h[j]);
+    if (r == PW_OK && rmax > s->tol && s->iter < s->maxit) {
+      // bands the split-precision floor left above tol: continue in FP64 from
+      // the polished block (P was dropped by the polish; H X is FP64)
+      s->precision = PW_FP64;
+      s->fresh_h = false;
+      for (int j = 0; j < s->nb; ++j) s->active[j] = s->resid_h[j] > s->tol;
+      for (;;) {
+        if ((r = refresh_stats(s, st_h)) != PW_OK) break;
+        rmax = 0.0;
+        for (int j = 0; j < s->nb; ++j) rmax = fmax(rmax, s->resid_h[j]);
+        if (rmax <= s->tol || s->iter >= s->maxit) break;
+        pw_step_report sr;
+        if ((r = pw_subspace_step(cell, s, &sr)) != PW_OK) break;
+        ++fp64_iters;
+        if (sr.nactive == 0) break;
+      }
+      s->precision = PW_MIXED;
     }
+    if (r == PW_OK) conv = rmax <= s->tol;
   }
   if (r == PW_OK || r == PW_ERR_CHOL) {
     memcpy(eig, s->lam_h.data(), s->nb * 8);
@@ -648,6 +665,7 @@ extern "C" pw_status pw_eigsolve(pw_cell *cell, const pw_solve_opts *o, double *
       cudaStreamSynchronize(s->st);
     }
     rep->orth_err = oe;
+    rep->fp64_iters = fp64_iters;
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   pw_solver_destroy(s);

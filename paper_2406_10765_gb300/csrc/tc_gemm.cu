@@ -584,7 +584,7 @@ pw_status pw_tc_gemm(const pw_tc_operand *A, int m, const pw_tc_operand *B, int 
   return PW_OK;
 }
 
-pw_status pw_tc_operand_alloc(pw_tc_operand *op, int rows, int kreal) {
+pw_status pw_tc_operand_alloc(pw_tc_operand *op, int rows, int kreal, cudaStream_t st) {
   const int kpad = pw_tc_kpad(kreal);
   const int rows_pad = (rows + 255) / 256 * 256;
   const size_t bytes = (size_t)2 * rows_pad * kpad * sizeof(__half);   // rows padded to 256
@@ -600,9 +600,10 @@ pw_status pw_tc_operand_alloc(pw_tc_operand *op, int rows, int kreal) {
     pw_tc_operand_free(op);
     return PW_ERR_OOM;
   }
-  // padded rows and K must read as zeros
-  cudaMemset(op->data, 0, bytes);
-  cudaMemset(op->inv_scale, 0, (size_t)rows_pad * sizeof(float));
+  // padded rows and K must read as zeros: cleared on the caller's stream so
+  // the clearing is ordered before the kernels that fill the operand
+  PW_CUDA(cudaMemsetAsync(op->data, 0, bytes, st));
+  PW_CUDA(cudaMemsetAsync(op->inv_scale, 0, (size_t)rows_pad * sizeof(float), st));
   op->cap_bytes = bytes;
   op->scale_cap = rows_pad;
   op->rows_total = rows_pad;
@@ -631,15 +632,15 @@ extern "C" pw_status pw_zgemm_tc(char opA, int m, int n, int k, const void *A, i
   if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return PW_ERR_OOM; }
   cudaMemsetAsync(err, 0, sizeof(int), st);
   if (opA == 'C') {
-    if ((r = pw_tc_operand_alloc(&a, 2 * m, 2 * k)) == PW_OK &&
-        (r = pw_tc_operand_alloc(&b, n, 2 * k)) == PW_OK &&
+    if ((r = pw_tc_operand_alloc(&a, 2 * m, 2 * k, st)) == PW_OK &&
+        (r = pw_tc_operand_alloc(&b, n, 2 * k, st)) == PW_OK &&
         (r = pw_tc_split_rows(Ad, lda, k, m, 1, nullptr, &a, st)) == PW_OK &&
         (r = pw_tc_split_rows(Bd, ldb, k, n, 0, nullptr, &b, st)) == PW_OK)
       r = pw_tc_gemm(&a, 2 * m, &b, n, (double2 *)C, ldc, 0, beta != 0.0, 0, err, st);
   } else {
     if (cudaMalloc(&rmax, (size_t)m * sizeof(float)) != cudaSuccess) { cudaGetLastError(); r = PW_ERR_OOM; }
-    if (r == PW_OK && (r = pw_tc_operand_alloc(&a, m, 2 * k)) == PW_OK &&
-        (r = pw_tc_operand_alloc(&b, 2 * n, 2 * k)) == PW_OK &&
+    if (r == PW_OK && (r = pw_tc_operand_alloc(&a, m, 2 * k, st)) == PW_OK &&
+        (r = pw_tc_operand_alloc(&b, 2 * n, 2 * k, st)) == PW_OK &&
         (r = pw_tc_split_trans(Ad, lda, m, k, rmax, &a, st)) == PW_OK &&
         (r = pw_tc_split_coef(Bd, ldb, k, n, nullptr, &b, st)) == PW_OK)
       r = pw_tc_gemm(&a, m, &b, 2 * n, (double2 *)C, ldc, 1, beta != 0.0, 0, err, st);

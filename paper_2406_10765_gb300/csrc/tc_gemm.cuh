@@ -15,7 +15,8 @@ struct pw_tc_operand {
 };
 
 int pw_tc_kpad(int kreal);
-pw_status pw_tc_operand_alloc(pw_tc_operand *op, int rows, int kreal);
+// (re)allocates when larger; new storage is cleared on `st`
+pw_status pw_tc_operand_alloc(pw_tc_operand *op, int rows, int kreal, cudaStream_t st);
 void pw_tc_operand_free(pw_tc_operand *op);
 
 // rows from the columns of X (npw x ncols): conj=0 -> ncols rows (re, im);

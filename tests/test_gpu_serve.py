@@ -59,3 +59,18 @@ def test_serve_admission_and_fault_isolation():
     out = pw.pw_serve([reqs[0], bad, reqs[2]], max_slots=3)
     assert out[0]["status"] == 0 and out[2]["status"] == 0
     assert out[1]["status"] == pw.PW_ERR_ARG
+
+
+def test_serve_mixed_concurrent_equals_alone():
+    # larger cells, all four slots busy: concurrency must not change a result
+    import paper_2406_10765_gb300 as pw
+    reqs = synth.serving_requests(2000, rate_per_s=50.0, seed=2024)[:6]
+    for r in reqs:
+        r["n"] = min(r["n"], 2)
+        r["nbands"] = round(1.125 * 2 * 8 * r["n"] ** 3)
+    mix = pw.pw_serve(reqs, max_slots=4, precision="mixed")
+    for r, m in zip(reqs, mix):
+        alone = pw.pw_serve([dict(r, t_arrival=0.0)], max_slots=1, precision="mixed")[0]
+        assert m["status"] == alone["status"]
+        assert np.array_equal(alone["eig"], m["eig"])
+        assert m["status"] == 0 and m["max_resid"] <= 5e-6
