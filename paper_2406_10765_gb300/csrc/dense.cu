@@ -114,17 +114,6 @@ __global__ void k_copy_herm(const double2 *M, int ld, int n, double2 *out) {
   out[i + (long)j * n] = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
 }
 
-// in-place Hermitian average of an n x n matrix (ld n)
-__global__ void k_hermitize(double2 *M, int n) {
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
-  if (i >= n || j >= n || i < j) return;
-  if (i == j) { M[i + (long)i * n].y = 0.0; return; }
-  double2 a = M[i + (long)j * n], b = M[j + (long)i * n];
-  const double2 h = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
-  M[i + (long)j * n] = h;
-  M[j + (long)i * n] = make_double2(h.x, -h.y);
-}
-
 constexpr int CB = 32;   // Cholesky / inverse block
 
 // unblocked Cholesky of the diagonal block at j0 (size b <= 32), in place
@@ -251,53 +240,128 @@ __global__ void k_scale_rows_real(double2 *C, int ld, int n, int nb, const doubl
 // ======================================================================
 
 // ----------------------------------------------------------------------
-// Fused lower-triangle tridiagonalisation.  Step k keeps the rank-2 update
-// of step k-1 pending: k_house_lazy applies it to column k and builds the
-// reflector; k_her2_hemv applies it to the lower triangle of the trailing
-// block and, in the same pass, forms the partial products of
-// p = A22 v_k (each off-diagonal element serves its row and, conjugated, its
-// column); k_hemv_finish sums the partials and forms w.  One read and one
-// write of half the trailing matrix per step.
+// Blocked Householder reduction (panels of TPB columns, lower triangle).
+// Inside a panel the trailing matrix is not updated: column c first receives
+// the panel's previous rank-2 updates, A22 v is a pure Hermitian product of
+// the not-yet-updated lower triangle, corrected by V (W^H v) + W (V^H v);
+// after the panel, A22 -= V W^H + W V^H is one rank-2 TPB GEMM on the lower
+// tiles.  Panel buffer P = [V | W | V] (ld n), so [V W] and [W V] are both
+// column ranges of it.
+//
+// Per column c (panel index i) three kernels:
+//   k_pcol   finish W[:, i-1], update column c, norm partials; the block that
+//            finishes last forms beta, tau and the scale s of the reflector
+//            (v = x s below its unit head) -- scalars only;
+//   k_phemv  lower-tile partial products of A22 v (v formed on the fly from
+//            x and s), the dots W^H v and V^H v, and the V columns of v;
+//   k_prows  sum the partials, subtract the corrections, p = tau y, store v
+//            in place of x and the partial dots p^H v.
+// FP64 runs at about two FMAs per clock per SM on this part, so the products
+// are written as four FMAs per complex multiply-add.
 // ----------------------------------------------------------------------
 constexpr int TT = 32;
+constexpr int TPB = 32;
+constexpr int PCOL_THREADS = 128;
 
-// alpha of step k-1: -1/2 tau (p^H v), from the per-block partial dots
-__device__ __forceinline__ double2 prev_alpha(const double2 *dotpart, int ndot, double2 t) {
-  double2 s = make_double2(0.0, 0.0);
-  for (int b = 0; b < ndot; ++b) s = cadd(s, dotpart[b]);
-  return cmul(make_double2(-0.5 * t.x, -0.5 * t.y), s);
+// s += a b and s += conj(a) b, four FMAs each
+__device__ __forceinline__ void cmac(double2 &s, double2 a, double2 b) {
+  s.x = fma(a.x, b.x, s.x);
+  s.x = fma(-a.y, b.y, s.x);
+  s.y = fma(a.x, b.y, s.y);
+  s.y = fma(a.y, b.x, s.y);
+}
+__device__ __forceinline__ void cmacc(double2 &s, double2 a, double2 b) {
+  s.x = fma(a.x, b.x, s.x);
+  s.x = fma(a.y, b.y, s.x);
+  s.y = fma(a.x, b.y, s.y);
+  s.y = fma(-a.y, b.x, s.y);
 }
 
-// one block: apply the pending update to column k and build reflector k.
-// p and the partial dots of step k-1 are read with L1-bypassing loads (they
-// may have been written by other blocks of the same kernel).
-__device__ void house_step(double2 *A, int n, int k, const double2 *pprev, const double2 *dotpart,
-                           int ndot, int has_prev, double *d, double *e, double2 *tau, double *sh) {
-  double2 *col = A + (long)k * n;
-  if (has_prev) {
-    const double2 *vp = A + k + (long)(k - 1) * n;     // v_{k-1}[r - k], rows r >= k
-    double2 sdot = make_double2(0.0, 0.0);
-    for (int b = 0; b < ndot; ++b) sdot = cadd(sdot, __ldcg(&dotpart[b]));
-    const double2 tk1 = tau[k - 1];
-    const double2 al = cmul(make_double2(-0.5 * tk1.x, -0.5 * tk1.y), sdot);
-    // w_{k-1} = p_{k-1} + alpha v_{k-1}
-    const double2 w0 = cadd(__ldcg(&pprev[0]), al);
-    for (int r = k + threadIdx.x; r < n; r += blockDim.x) {
-      const double2 vr = vp[r - k], wr = cadd(__ldcg(&pprev[r - k]), cmul(al, vr));
-      // A_rk -= v_r conj(w_0) + w_r conj(v_0), v_0 = 1
-      const double2 t = cmul(vr, make_double2(w0.x, -w0.y));
-      col[r].x -= t.x + wr.x;
-      col[r].y -= t.y + wr.y;
-    }
-    __syncthreads();
+// alpha = -1/2 tau (p^H v) from the per-block partial dots (block-wide sum)
+__device__ double2 panel_alpha(const double2 *dotpart, int ndot, double2 t, double *sh) {
+  double sr = 0.0, si = 0.0;
+  for (int q = threadIdx.x; q < ndot; q += blockDim.x) {
+    const double2 v = __ldcg(&dotpart[q]);
+    sr += v.x;
+    si += v.y;
+  }
+  sr = block_sum(sr, sh);
+  si = block_sum(si, sh);
+  return cmul(make_double2(-0.5 * t.x, -0.5 * t.y), make_double2(sr, si));
+}
+
+// v_c entry x (x = row - (c+1)) from the stored column and the scale
+__device__ __forceinline__ double2 refl_entry(const double2 *xcol, int x, double2 scal) {
+  return x == 0 ? make_double2(1.0, 0.0) : cmul(xcol[x], scal);
+}
+
+// 32 rows per block; the four warps split the panel's previous updates
+// (q = warp mod 4) so that the FP64 work lands on all four SM sub-partitions
+__global__ void __launch_bounds__(PCOL_THREADS) k_pcol(double2 *A, int n, int c, int i, double2 *P, int b,
+                                                       const double2 *p, const double2 *dotpart, int ndot,
+                                                       double2 *tau, double *d, double *e, double *nrm_part,
+                                                       double2 *hscal, unsigned *ticket) {
+  __shared__ double sh[32];
+  __shared__ unsigned s_ticket;
+  __shared__ double2 s_vc[TPB], s_wc[TPB], s_u[4][33];
+  double2 *V = P, *W = P + (long)b * n;
+  double2 al = make_double2(0.0, 0.0);
+  if (i > 0) al = panel_alpha(dotpart, ndot, tau[c - 1], sh);
+  if (threadIdx.x < i) {
+    const int q = threadIdx.x;
+    s_vc[q] = V[c + (long)q * n];
+    // W[c, i-1] = p_{c-1}[0] + alpha v_{c-1}[row c], the head of v_{c-1} being 1
+    s_wc[q] = (q == i - 1) ? cadd(__ldcg(&p[0]), al) : W[c + (long)q * n];
   }
   __syncthreads();
-  const int m = n - k - 1;
-  double2 *x = col + k + 1;
-  double s = 0.0;
-  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) s += x[i].x * x[i].x + x[i].y * x[i].y;
-  const double xn2 = block_sum(s, sh);
-  const double2 alpha = x[0];
+  const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int r = c + blockIdx.x * 32 + rl;
+  if (i > 0) {
+    double2 u = make_double2(0.0, 0.0);   // sum_q v_rq conj(w_cq) + w_rq conj(v_cq), q = g mod 4
+    if (r < n) {
+      for (int q = g; q < i; q += 4) {
+        const double2 vq = V[r + (long)q * n];
+        double2 wq;
+        if (q == i - 1) {
+          wq = __ldcg(&p[r - c]);
+          cmac(wq, al, vq);
+          W[r + (long)q * n] = wq;
+        } else {
+          wq = W[r + (long)q * n];
+        }
+        cmacc(u, s_wc[q], vq);
+        cmacc(u, s_vc[q], wq);
+      }
+    }
+    s_u[g][rl] = u;
+    __syncthreads();
+  }
+  if (g != 0) return;
+  double nrm = 0.0;
+  if (r < n) {
+    double2 a = A[r + (long)c * n];
+    if (i > 0) {
+      a = csub(a, cadd(cadd(s_u[0][rl], s_u[1][rl]), cadd(s_u[2][rl], s_u[3][rl])));
+      A[r + (long)c * n] = a;
+    }
+    if (r > c + 1) nrm = a.x * a.x + a.y * a.y;
+  }
+  nrm = warp_sum(nrm);
+  if (rl == 0) {
+    nrm_part[blockIdx.x] = nrm;
+    __threadfence();
+    s_ticket = atomicAdd(ticket, 1u);
+  }
+  __syncwarp();
+  if (s_ticket != gridDim.x - 1) return;
+  __threadfence();
+  // last block: reflector scalars from x = A[c+1:, c]
+  double xn2 = 0.0;
+  for (int q = rl; q < (int)gridDim.x; q += 32) xn2 += __ldcg(&nrm_part[q]);
+  xn2 = warp_sum(xn2);
+  if (rl != 0) return;
+  *ticket = 0u;
+  const double2 alpha = __ldcg(&A[(c + 1) + (long)c * n]);
   double beta;
   double2 tk, scal;
   if (xn2 == 0.0 && alpha.y == 0.0) {
@@ -308,165 +372,155 @@ __device__ void house_step(double2 *A, int n, int k, const double2 *pprev, const
     beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2), alpha.x);
     tk = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
     const double2 den = make_double2(alpha.x - beta, alpha.y);
-    const double q = 1.0 / (den.x * den.x + den.y * den.y);
-    scal = make_double2(den.x * q, -den.y * q);
+    const double qq = 1.0 / (den.x * den.x + den.y * den.y);
+    scal = make_double2(den.x * qq, -den.y * qq);
   }
-  __syncthreads();
-  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] = cmul(x[i], scal);
-  if (threadIdx.x == 0) {
-    d[k] = col[k].x;
-    x[0] = make_double2(1.0, 0.0);
-    tau[k] = tk;
-    e[k] = beta;
-  }
+  d[c] = __ldcg(&A[c + (long)c * n]).x;
+  tau[c] = tk;
+  e[c] = beta;
+  *hscal = scal;
 }
 
-__global__ void k_house_lazy(double2 *A, int n, int k, const double2 *pprev, const double2 *dotpart,
-                             int ndot, int has_prev, double *d, double *e, double2 *tau) {
+// y = A22 v as lower-tile partials (A22 = rows/cols >= c+1, not yet updated
+// by this panel); 2i extra blocks: u[2q] = W[:, q]^H v, u[2q+1] = V[:, q]^H v;
+// nwr more blocks write v into V[:, i] and its copy
+__global__ void __launch_bounds__(256) k_phemv(const double2 *A, int n, int c, int i, double2 *P, int b,
+                                               int ntiles, double2 *part, int nmax, double2 *ucorr,
+                                               const double2 *hscal) {
+  __shared__ double2 tile[TT][TT + 1];
+  __shared__ double2 vrow[TT], vcol[TT], rpart[4][TT + 1], cpart[4][TT + 1];
   __shared__ double sh[32];
-  house_step(A, n, k, pprev, dotpart, ndot, has_prev, d, e, tau, sh);
-}
-
-// one CTA per lower tile (I >= J) of the trailing block (rows/cols >= k+1).
-// Phase 1: each thread updates 4 elements of the 32 x 32 tile and parks them
-// in shared memory.  Phase 2: threads 0-31 form the row sums sum_c a_rc v_c
-// (thread = row), threads 32-63 the column sums sum_r conj(a_rc) v_r (thread
-// = column), each a plain serial loop over the tile: no FP64 shuffle trees.
-__global__ void __launch_bounds__(256) k_her2_hemv(double2 *A, int n, int k, const double2 *pprev,
-                                                   const double2 *dotpart, int ndot,
-                                                   const double2 *tau, int has_prev, double2 *part,
-                                                   int nmax) {
-  __shared__ double2 tile[TT][TT + 1];     // tile[row][col], zero outside the lower part
-  __shared__ double2 vrow[TT], vcol[TT], csum[TT];
-  __shared__ double2 s_al;
-  const int t = blockIdx.x;
-  int I = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  const int o = c + 1, m = n - o;
+  const double2 *xk = A + o + (long)c * n;   // x of column c, x[0] at row o
+  const double2 scal = *hscal;
+  const int blk = blockIdx.x;
+  if (blk >= ntiles + 2 * i) {   // writer blocks
+    const int x = (blk - ntiles - 2 * i) * blockDim.x + threadIdx.x;
+    if (x < m) {
+      const double2 v = refl_entry(xk, x, scal);
+      P[o + x + (long)i * n] = v;
+      P[o + x + (long)(2 * b + i) * n] = v;
+    }
+    return;
+  }
+  if (blk >= ntiles) {
+    const int q2 = blk - ntiles, q = q2 >> 1;
+    const double2 *col = P + (long)((q2 & 1) ? q : b + q) * n;   // odd: V[:, q], even: W[:, q]
+    double2 s = make_double2(0.0, 0.0);
+    for (int x = threadIdx.x; x < m; x += blockDim.x) cmacc(s, col[o + x], refl_entry(xk, x, scal));
+    s.x = block_sum(s.x, sh);
+    s.y = block_sum(s.y, sh);
+    if (threadIdx.x == 0) ucorr[q2] = s;
+    return;
+  }
+  const int t = blk;
+  // tile (I, J) of the lower triangle; FP32 estimate (FP64 is scarce), fixed up exactly
+  int I = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
   while ((I + 1) * (I + 2) / 2 <= t) ++I;
   while (I * (I + 1) / 2 > t) --I;
   const int J = t - I * (I + 1) / 2;
-  const int o = k + 1;
-  const int r0 = o + TT * I, c0 = o + TT * J;
-  const double2 *vk = A + o + (long)k * n;                    // v_k[x], x = row - o
-  const double2 *vp = A + k + (long)(k - 1) * n;              // v_{k-1}[x], x = row - k
-  if (threadIdx.x == 0 && has_prev) s_al = prev_alpha(dotpart, ndot, tau[k - 1]);
+  const int x0 = TT * I, y0 = TT * J;   // tile rows x0.., columns y0.. (offsets from o)
   if (threadIdx.x < TT) {
-    const int r = r0 + threadIdx.x, c = c0 + threadIdx.x;
-    vrow[threadIdx.x] = r < n ? vk[r - o] : make_double2(0.0, 0.0);
-    vcol[threadIdx.x] = c < n ? vk[c - o] : make_double2(0.0, 0.0);
+    const int xr = x0 + threadIdx.x, yc = y0 + threadIdx.x;
+    vrow[threadIdx.x] = xr < m ? refl_entry(xk, xr, scal) : make_double2(0.0, 0.0);
+    vcol[threadIdx.x] = yc < m ? refl_entry(xk, yc, scal) : make_double2(0.0, 0.0);
   }
-  __syncthreads();
-  const double2 al = has_prev ? s_al : make_double2(0.0, 0.0);
   const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-  const int c = c0 + lane;
-  const bool cin = c < n;
-  double2 vpc = make_double2(0.0, 0.0), wpc = vpc;
-  if (cin && has_prev) {
-    vpc = vp[c - k];
-    wpc = cadd(pprev[c - k], cmul(al, vpc));
-  }
+  const int yc = y0 + lane;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int rl = wq * 4 + q, r = r0 + rl;
+    const int rl = wq * 4 + q, xr = x0 + rl;
     double2 a = make_double2(0.0, 0.0);
-    if (r < n && cin && (I != J || c <= r)) {
-      double2 *ap = A + r + (long)c * n;
-      a = *ap;
-      if (has_prev) {
-        const double2 vr = vp[r - k], wr = cadd(pprev[r - k], cmul(al, vr));
-        // a -= v_r conj(w_c) + w_r conj(v_c)
-        a.x -= (vr.x * wpc.x + vr.y * wpc.y) + (wr.x * vpc.x + wr.y * vpc.y);
-        a.y -= (vr.y * wpc.x - vr.x * wpc.y) + (wr.y * vpc.x - wr.x * vpc.y);
-        *ap = a;
-      }
-    }
+    if (xr < m && yc < m && (I != J || yc <= xr)) a = A[(o + xr) + (long)(o + yc) * n];
     tile[rl][lane] = a;
   }
   __syncthreads();
-  if (threadIdx.x < TT) {
-    // row sums for row r (diagonal included)
-    const int rl = threadIdx.x, r = r0 + rl;
+  // warps 0-3: quarter row sums A v; warps 4-7: quarter column sums A^H v
+  // (strictly below the diagonal in a diagonal tile)
+  {
+    const int k = (threadIdx.x >> 5) & 3, l = threadIdx.x & 31;
     double2 s = make_double2(0.0, 0.0);
-#pragma unroll 8
-    for (int cl = 0; cl < TT; ++cl) s = cadd(s, cmul(tile[rl][cl], vcol[cl]));
-    if (r < n) {
-      if (I != J) part[(long)J * nmax + (r - o)] = s;
-      else tile[rl][TT] = s;                 // combined with the column sums below
+    if (threadIdx.x < 128) {
+#pragma unroll
+      for (int cl = 8 * k; cl < 8 * k + 8; ++cl) cmac(s, tile[l][cl], vcol[cl]);
+      rpart[k][l] = s;
+    } else {
+#pragma unroll
+      for (int rr = 8 * k; rr < 8 * k + 8; ++rr)
+        if (I != J || rr > l) cmacc(s, tile[rr][l], vrow[rr]);
+      cpart[k][l] = s;
     }
-  } else if (threadIdx.x < 2 * TT) {
-    // column sums for column c, strictly below the diagonal
-    const int cl = threadIdx.x - TT, cc = c0 + cl;
-    double2 s = make_double2(0.0, 0.0);
-#pragma unroll 8
-    for (int rl = 0; rl < TT; ++rl)
-      if (I != J || rl > cl) s = cadd(s, cmulc(tile[rl][cl], vrow[rl]));
-    if (cc < n && I != J) part[(long)I * nmax + (cc - o)] = s;
-    if (I == J) csum[cl] = s;                // park for the diagonal tile
   }
   __syncthreads();
-  if (I == J && threadIdx.x < TT) {
-    const int rl = threadIdx.x, r = r0 + rl;
-    if (r < n) part[(long)J * nmax + (r - o)] = cadd(tile[rl][TT], csum[rl]);
+  if (threadIdx.x < TT) {
+    const int l = threadIdx.x;
+    const double2 rs = cadd(cadd(rpart[0][l], rpart[1][l]), cadd(rpart[2][l], rpart[3][l]));
+    const double2 cs = cadd(cadd(cpart[0][l], cpart[1][l]), cadd(cpart[2][l], cpart[3][l]));
+    if (I != J) {
+      if (x0 + l < m) part[(long)J * nmax + x0 + l] = rs;
+      if (y0 + l < m) part[(long)I * nmax + y0 + l] = cs;
+    } else if (x0 + l < m) {
+      part[(long)J * nmax + x0 + l] = cadd(rs, cs);
+    }
   }
 }
 
-// p = tau sum_c part[c] (one thread per row) and per-block partial dots
-// p^H v; the block that finishes last then performs step k+1's column
-// update and reflector (or the last diagonal after the final step):
-// blocks publish p and their partial dots, fence, and take a ticket; no block
-// waits on another.
-__global__ void __launch_bounds__(256) k_hemv_rows_next(double2 *A, int n, int k, const double2 *part,
-                                                        int nT, int nmax, double2 *tau, double2 *p,
-                                                        double2 *dotpart, unsigned *ticket, double *d,
-                                                        double *e) {
+// 32 rows per block, 8 thread groups over the partial slots and corrections:
+// y = sum of partials - V[:, <i] u_W - W[:, <i] u_V, p = tau_c y, v stored in
+// place of x, partial dots p^H v
+__global__ void __launch_bounds__(256) k_prows(double2 *A, int n, int c, int i, const double2 *P, int b,
+                                               const double2 *part, int nT, int nmax, const double2 *ucorr,
+                                               const double2 *tau, const double2 *hscal, double2 *p,
+                                               double2 *dotpart) {
+  __shared__ double2 red[8][33];
+  const int o = c + 1, m = n - o;
+  const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int x = blockIdx.x * 32 + rl;
+  double2 y = make_double2(0.0, 0.0);
+  if (x < m) {
+    for (int s = g; s < nT; s += 8) y = cadd(y, part[(long)s * nmax + x]);
+    for (int q = g; q < i; q += 8) {
+      const double2 uw = ucorr[2 * q], uv = ucorr[2 * q + 1];
+      cmac(y, P[o + x + (long)q * n], make_double2(-uw.x, -uw.y));         // - V[r,q] (W^H v)_q
+      cmac(y, P[o + x + (long)(b + q) * n], make_double2(-uv.x, -uv.y));   // - W[r,q] (V^H v)_q
+    }
+  }
+  red[g][rl] = y;
+  __syncthreads();
+  if (g != 0) return;
+  double2 pv = make_double2(0.0, 0.0);
+  if (x < m) {
+#pragma unroll
+    for (int q = 1; q < 8; ++q) y = cadd(y, red[q][rl]);
+    const double2 pr = cmul(tau[c], y);
+    p[x] = pr;
+    double2 *xc = A + o + (long)c * n;
+    const double2 v = refl_entry(xc, x, *hscal);
+    xc[x] = v;
+    cmacc(pv, pr, v);
+  }
+  pv.x = warp_sum(pv.x);
+  pv.y = warp_sum(pv.y);
+  if (rl == 0) dotpart[blockIdx.x] = pv;
+}
+
+// W[:, i] = p + alpha v for the panel's last column (rows >= c+1)
+__global__ void __launch_bounds__(256) k_pfinal(const double2 *A, int n, int c, int i, double2 *P, int b,
+                                                const double2 *p, const double2 *dotpart, int ndot,
+                                                const double2 *tau) {
   __shared__ double sh[32];
-  __shared__ unsigned s_ticket;
-  const int m = n - k - 1, o = k + 1;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const double2 t = tau[k];
-  double dr = 0.0, di = 0.0;
-  if (i < m) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int c = 0; c < nT; ++c) s = cadd(s, part[(long)c * nmax + i]);
-    s = cmul(t, s);
-    p[i] = s;
-    const double2 pv = cmulc(s, A[o + i + (long)k * n]);
-    dr = pv.x;
-    di = pv.y;
-  }
-  dr = block_sum(dr, sh);
-  di = block_sum(di, sh);
-  if (threadIdx.x == 0) {
-    dotpart[blockIdx.x] = make_double2(dr, di);
-    __threadfence();
-    s_ticket = atomicAdd(ticket, 1u);
-  }
-  __syncthreads();
-  if (s_ticket != gridDim.x - 1) return;
-  // last block: every p and partial dot of step k is visible
-  __threadfence();
-  if (threadIdx.x == 0) *ticket = 0u;
-  const int ndot = gridDim.x;
-  if (k + 2 < n) {
-    house_step(A, n, k + 1, p, dotpart, ndot, 1, d, e, tau, sh);
-  } else if (threadIdx.x == 0) {
-    // k = n - 2: last diagonal after the final pending update (v = 1)
-    double2 sdot = make_double2(0.0, 0.0);
-    for (int b = 0; b < ndot; ++b) sdot = cadd(sdot, __ldcg(&dotpart[b]));
-    const double2 al = cmul(make_double2(-0.5 * t.x, -0.5 * t.y), sdot);
-    const double2 w0 = cadd(__ldcg(&p[0]), al);
-    d[n - 1] = A[(n - 1) + (long)(n - 1) * n].x - 2.0 * w0.x;
+  const double2 al = panel_alpha(dotpart, ndot, tau[c], sh);
+  const int o = c + 1;
+  const int r = o + blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) {
+    double2 w = p[r - o];
+    cmac(w, al, A[r + (long)c * n]);
+    P[r + (long)(b + i) * n] = w;
   }
 }
 
-// last diagonal after the final pending update (v_{n-2} = 1, w_{n-2} = w[0])
-__global__ void k_last_diag_lazy(const double2 *A, int n, const double2 *pprev, const double2 *dotpart,
-                                 int ndot, const double2 *tau, int has_prev, double *d) {
-  double a = A[(n - 1) + (long)(n - 1) * n].x;
-  if (has_prev) {
-    const double2 w0 = cadd(pprev[0], prev_alpha(dotpart, ndot, tau[n - 2]));   // v = 1
-    a -= 2.0 * w0.x;
-  }
-  d[n - 1] = a;
+__global__ void k_last_diag_plain(const double2 *A, int n, double *d) {
+  d[n - 1] = A[(n - 1) + (long)(n - 1) * n].x;
 }
 
 // ======================================================================
@@ -827,24 +881,53 @@ __global__ void k_copy_panel(const double2 *A, int n, int j0, int b, double2 *Vb
 }
 
 // T (b x b, upper, ld b): T_ii = tau_i; T[0:i, i] = -tau_i T[0:i, 0:i] G[0:i, i],
-// G = Vb^H Vb.  One thread per row r; column i of T depends on columns < i.
-__global__ void k_build_T(const double2 *G, const double2 *tau, int j0, int b, double2 *T) {
-  const int r = threadIdx.x;
-  if (r < b)
-    for (int c = 0; c < b; ++c) T[r + (long)c * b] = make_double2(0.0, 0.0);
-  __syncthreads();
-  for (int i = 0; i < b; ++i) {
-    const double2 ti = tau[j0 + i];
-    if (r < i) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int c = r; c < i; ++c) s = cadd(s, cmul(T[r + (long)c * b], G[c + (long)i * b]));
-      const double2 v = cmul(ti, s);
-      T[r + (long)i * b] = make_double2(-v.x, -v.y);
-    } else if (r == i) {
-      T[r + (long)i * b] = ti;
+// G = Vb^H Vb.  Row r of T depends only on itself (T[r, i] = -tau_i
+// sum_{m=r}^{i-1} T[r, m] G[m, i]), so each warp owns one row: the lanes split
+// the sum, the row is kept in shared memory, and the next column of G is
+// fetched while the current one is reduced.
+constexpr int BT_WARPS = 4;
+__global__ void __launch_bounds__(32 * BT_WARPS) k_build_T(const double2 *G, const double2 *tau, int j0, int b,
+                                                           double2 *T) {
+  __shared__ double2 trow[BT_WARPS][BTB];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = blockIdx.x * BT_WARPS + w;
+  if (r >= b) return;
+  double2 *tr = trow[w];
+  constexpr int KMAX = BTB / 32;
+  double2 gnext[KMAX];
+  auto fetch = [&](int col) {
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      const int m = r + lane + 32 * k;
+      gnext[k] = (col < b && m < col) ? G[m + (long)col * b] : make_double2(0.0, 0.0);
     }
-    __syncthreads();
+  };
+  if (lane == 0) tr[r] = tau[j0 + r];
+  fetch(r + 1);
+  __syncwarp();
+  for (int c = r + 1; c < b; ++c) {
+    double2 g[KMAX];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) g[k] = gnext[k];
+    fetch(c + 1);
+    double2 s = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      const int m = r + lane + 32 * k;
+      if (m < c) cmac(s, tr[m], g[k]);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+    }
+    if (lane == 0) {
+      const double2 t = cmul(tau[j0 + c], s);
+      tr[c] = make_double2(-t.x, -t.y);
+    }
+    __syncwarp();
   }
+  for (int c = lane; c < b; c += 32) T[r + (long)c * b] = c >= r ? tr[c] : make_double2(0.0, 0.0);
 }
 
 void build_tree(pw_dense_ws *ws, int n) {
@@ -905,7 +988,9 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
   ok = ok && get((void **)&ws->nodes, (size_t)3 * nmax * 4 + 64) &&
        get((void **)&ws->knode, (size_t)nmax * 4 + 64) &&
        get((void **)&ws->rhonode, (size_t)nmax * 8 + 64);
-  ok = ok && get((void **)&ws->ticket, 64);
+  ok = ok && get((void **)&ws->ticket, 64) && get((void **)&ws->panel, (size_t)nmax * 3 * TPB * 16) &&
+       get((void **)&ws->ucorr, 2 * TPB * 16) && get((void **)&ws->hscal, 16) &&
+       get((void **)&ws->nrm_part, (size_t)(nmax / 32 + 2) * 8);
   ok = ok && get((void **)&ws->Vb, (size_t)nmax * BTB * 16) && get((void **)&ws->Gv, BTB * BTB * 16) &&
        get((void **)&ws->Tb, BTB * BTB * 16) && get((void **)&ws->Wk, (size_t)BTB * nbmax * 16) &&
        get((void **)&ws->Wk2, (size_t)BTB * nbmax * 16);
@@ -928,7 +1013,8 @@ void pw_dense_free(pw_dense_ws *ws) {
                   ws->lam, ws->tau, ws->p, ws->w, ws->part, ws->Z, ws->W, ws->U, ws->Ds, ws->zs,
                   ws->DK, ws->zK, ws->tauK, ws->zh, ws->lamK, ws->dD, ws->lnew, ws->perm, ws->colK,
                   ws->orig, ws->dcol, ws->src, ws->nodes, ws->knode, ws->rhonode, ws->gemm_ws,
-                  ws->Vb, ws->Gv, ws->Tb, ws->Wk, ws->Wk2, ws->ticket};
+                  ws->Vb, ws->Gv, ws->Tb, ws->Wk, ws->Wk2, ws->ticket, ws->panel, ws->ucorr,
+                  ws->hscal, ws->nrm_part};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : ws->ev)
@@ -949,30 +1035,42 @@ void pw_dense_stage_ms(pw_dense_ws *ws, float out[5]) {
 pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam, double2 *Y,
                          cudaStream_t st) {
   if (n <= 0 || nb <= 0 || nb > n || n > ws->nmax || nb > ws->nbmax) return PW_ERR_ARG;
-  // 1. Householder tridiagonalisation (lower triangle, lazy rank-2 updates)
+  // 1. Householder tridiagonalisation: panels of TPB columns (lower triangle)
   if (ws->ev[2]) cudaEventRecord(ws->ev[2], st);
-  double2 *dotpart = ws->w;     // per-block partial dots of the previous step
   PW_CUDA(cudaMemsetAsync(ws->ticket, 0, sizeof(unsigned), st));
-  if (n == 1) {
+  {
+    const double2 mone = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
+    double2 *dotpart = ws->w;
+    for (int j0 = 0; j0 + 1 < n; j0 += TPB) {
+      const int b = std::min(TPB, n - 1 - j0);
+      PW_CUDA(cudaMemsetAsync(ws->panel, 0, (size_t)n * 3 * b * sizeof(double2), st));
+      int ndot = 0;
+      for (int i = 0; i < b; ++i) {
+        const int c = j0 + i, m = n - c - 1;
+        pw_count_launch();
+        k_pcol<<<(n - c + 31) / 32, PCOL_THREADS, 0, st>>>(
+            A, n, c, i, ws->panel, b, ws->p, dotpart, ndot, ws->tau, ws->d, ws->e, ws->nrm_part, ws->hscal,
+            ws->ticket);
+        const int nT = (m + TT - 1) / TT, ntiles = nT * (nT + 1) / 2, nwr = (m + 255) / 256;
+        pw_count_launch();
+        k_phemv<<<ntiles + 2 * i + nwr, 256, 0, st>>>(A, n, c, i, ws->panel, b, ntiles, ws->part, ws->nmax,
+                                                      ws->ucorr, ws->hscal);
+        ndot = (m + 31) / 32;
+        pw_count_launch();
+        k_prows<<<ndot, 256, 0, st>>>(A, n, c, i, ws->panel, b, ws->part, nT, ws->nmax, ws->ucorr, ws->tau,
+                                      ws->hscal, ws->p, dotpart);
+      }
+      const int cl = j0 + b - 1, ml = n - cl - 1;
+      pw_count_launch();
+      k_pfinal<<<(ml + 255) / 256, 256, 0, st>>>(A, n, cl, b - 1, ws->panel, b, ws->p, dotpart, ndot,
+                                                 ws->tau);
+      const int t = j0 + b, m2 = n - t;
+      if (m2 > 0)
+        PW_TRY(pw_zgemm_ex('N', 'C', m2, m2, 2 * b, mone, ws->panel + t, n, ws->panel + (long)b * n + t,
+                           n, one, A + t + (long)t * n, n, ws->gemm_ws, ws->gemm_ws_elems, st, 2));
+    }
     pw_count_launch();
-    k_last_diag_lazy<<<1, 1, 0, st>>>(A, n, ws->p, dotpart, 0, ws->tau, 0, ws->d);
-  } else {
-    pw_count_launch();
-    k_house_lazy<<<1, 256, 0, st>>>(A, n, 0, ws->p, dotpart, 0, 0, ws->d, ws->e, ws->tau);
-  }
-  int ndot = 0;
-  for (int k = 0; k + 1 < n; ++k) {
-    const int m = n - k - 1;
-    const int has_prev = k > 0;
-    const int nT = (m + TT - 1) / TT;
-    pw_count_launch();
-    k_her2_hemv<<<nT * (nT + 1) / 2, 256, 0, st>>>(A, n, k, ws->p, dotpart, ndot, ws->tau, has_prev,
-                                                   ws->part, ws->nmax);
-    ndot = (m + 255) / 256;
-    // p, partial dots, then (last block) step k+1's reflector or the last diagonal
-    pw_count_launch();
-    k_hemv_rows_next<<<ndot, 256, 0, st>>>(A, n, k, ws->part, nT, ws->nmax, ws->tau, ws->p, dotpart,
-                                           ws->ticket, ws->d, ws->e);
+    k_last_diag_plain<<<1, 1, 0, st>>>(A, n, ws->d);
   }
   PW_TRY(pw_check_launch("tridiag"));
 
@@ -1027,7 +1125,7 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
       PW_TRY(pw_zgemm('C', 'N', b, b, mb, one, ws->Vb, mb, ws->Vb, mb, zero, ws->Gv, b, ws->gemm_ws,
                       ws->gemm_ws_elems, st));
       pw_count_launch();
-      k_build_T<<<1, BTB, 0, st>>>(ws->Gv, ws->tau, j0, b, ws->Tb);   // BTB <= 1024 threads
+      k_build_T<<<(b + BT_WARPS - 1) / BT_WARPS, 32 * BT_WARPS, 0, st>>>(ws->Gv, ws->tau, j0, b, ws->Tb);
       double2 *Yb = Y + (j0 + 1);
       PW_TRY(pw_zgemm('C', 'N', b, nb, mb, one, ws->Vb, mb, Yb, n, zero, ws->Wk, b, ws->gemm_ws,
                       ws->gemm_ws_elems, st));
@@ -1055,10 +1153,11 @@ pw_status cholesky(pw_dense_ws *ws, double2 *A, int n, cudaStream_t st) {
     if (rest > 0) {
       pw_count_launch();
       k_trsm_rows<<<(rest + 127) / 128, 128, 0, st>>>(A, n, j0, b);
-      // A22 -= L21 L21^H: Hermitian, so only upper tiles are formed, then mirrored
+      // A22 -= L21 L21^H on the lower tiles only (the factorisation reads the
+      // lower triangle; the upper one is cleared at the end)
       PW_TRY(pw_zgemm_ex('N', 'C', rest, rest, b, mone, A + (j0 + b) + (long)j0 * n, n,
                          A + (j0 + b) + (long)j0 * n, n, one, A + (j0 + b) + (long)(j0 + b) * n, n,
-                         ws->gemm_ws, ws->gemm_ws_elems, st, 1));
+                         ws->gemm_ws, ws->gemm_ws_elems, st, 2));
     }
   }
   pw_count_launch();
@@ -1141,9 +1240,9 @@ pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, int
   k_mirror_upper_to_lower<<<g2, b2, 0, st>>>(ws->A, n);
   PW_TRY(pw_heev_lowest(ws, n, nb, ws->A, ws->lam, ws->Y, st));
   PW_CUDA(cudaMemcpyAsync(theta, ws->lam, nb * 8, cudaMemcpyDeviceToDevice, st));
-  // C = d o (Linv^H Y)
-  PW_TRY(pw_zgemm('C', 'N', n, nb, n, one, ws->Linv, n, ws->Y, n, zero, C, ldc, ws->gemm_ws,
-                  ws->gemm_ws_elems, st));
+  // C = d o (Linv^H Y); Linv^H is upper triangular
+  PW_TRY(pw_zgemm_ex('C', 'N', n, nb, n, one, ws->Linv, n, ws->Y, n, zero, C, ldc, ws->gemm_ws,
+                     ws->gemm_ws_elems, st, 3));
   pw_count_launch();
   k_scale_rows_real<<<(unsigned)(((long)n * nb + 255) / 256), 256, 0, st>>>(C, ldc, n, nb, ws->dscale);
   cudaEventRecord(ws->ev[5], st);
@@ -1211,8 +1310,9 @@ pw_status pw_rr_finish(pw_dense_ws *ws, int n, int nb, const double2 *At, int ld
   PW_TRY(pw_heev_lowest(ws, n, nb, ws->A, ws->lam, ws->Y, st));
   PW_CUDA(cudaMemcpyAsync(theta, ws->lam, nb * 8, cudaMemcpyDeviceToDevice, st));
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
-  PW_TRY(pw_zgemm('N', 'N', n, nb, n, one, M, ldm, ws->Y, n, zero, C, ldc, ws->gemm_ws,
-                  ws->gemm_ws_elems, st));
+  // M is upper triangular: each row tile skips the zero part of its K range
+  PW_TRY(pw_zgemm_ex('N', 'N', n, nb, n, one, M, ldm, ws->Y, n, zero, C, ldc, ws->gemm_ws,
+                     ws->gemm_ws_elems, st, 3));
   cudaEventRecord(ws->ev[5], st);
   return pw_check_launch("rr_finish");
 }

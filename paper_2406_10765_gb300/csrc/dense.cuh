@@ -26,6 +26,10 @@ struct pw_dense_ws {
   // blocked back-transformation: reflector panel, its Gram, T, two work blocks
   double2 *Vb = nullptr, *Gv = nullptr, *Tb = nullptr, *Wk = nullptr, *Wk2 = nullptr;
   unsigned *ticket = nullptr;   // last-block-done counter of the Householder steps
+  // blocked Householder reduction: panel [V | W | V] (nmax x 3*32), partial
+  // norms of a column, the panel correction dots
+  double2 *panel = nullptr, *ucorr = nullptr, *hscal = nullptr;
+  double *nrm_part = nullptr;
   // host side tree for the current n
   int tree_n = -1;
   std::vector<std::vector<int>> levels;   // per level: flat (lo, mid, hi) triples

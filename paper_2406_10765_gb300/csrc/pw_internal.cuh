@@ -115,7 +115,10 @@ pw_status pw_zgemm(char opA, char opB, int m, int n, int k, double2 alpha, const
                    double2 *ws, size_t ws_elems, cudaStream_t st);
 size_t pw_zgemm_ws_elems(int m, int n, int k);
 // herm = 1: C is Hermitian (A^H B with A == B up to H-symmetry); only the
-// upper-triangle tiles are computed, then mirrored
+// upper-triangle tiles are computed, then mirrored.  herm = 2: only the tiles
+// on and below the diagonal are computed (the caller keeps a lower triangle).
+// herm = 3: op(A) is upper triangular (explicit zeros below the diagonal), so
+// each row tile skips the K range left of its first row.
 pw_status pw_zgemm_ex(char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
                       int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc,
                       double2 *ws, size_t ws_elems, cudaStream_t st, int herm);

@@ -25,20 +25,24 @@ __global__ void __launch_bounds__(256) k_zgemm(int m, int n, int k, int kchunk, 
                                                double2 beta, double2 *__restrict__ C, int ldc,
                                                double2 *__restrict__ ws, int herm) {
   // Hermitian products: tiles strictly below the diagonal are mirrored later
-  if (herm && blockIdx.y < blockIdx.x) return;
+  // herm 1: upper-triangle tiles (mirrored later); herm 2: lower-triangle tiles only
+  if (herm == 1 && blockIdx.y < blockIdx.x) return;
+  if (herm == 2 && blockIdx.y > blockIdx.x) return;
   __shared__ double2 As[BK][BM + 1];
   __shared__ double2 Bs[BK][BN + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int kb = blockIdx.z * kchunk;
   const int ke = min(k, kb + kchunk);
+  // herm 3: op(A) upper triangular, so rows m0.. need K from m0 on only
+  const int ks = herm == 3 ? max(kb, m0 - m0 % BK) : kb;
   double2 acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
 
-  for (int k0 = kb; k0 < ke; k0 += BK) {
+  for (int k0 = ks; k0 < ke; k0 += BK) {
     // A tile: op(A)(mm, kk), 64 x 8 = 512 elements, 2 per thread
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -112,10 +116,13 @@ __global__ void k_zmirror(double2 *C, int ldc, int n) {
 }
 
 __global__ void k_zgemm_reduce(int m, int n, int splits, double2 alpha, const double2 *__restrict__ ws,
-                               double2 beta, double2 *__restrict__ C, int ldc) {
+                               double2 beta, double2 *__restrict__ C, int ldc, int herm) {
   const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (idx >= (long)m * n) return;
   const int gm = (int)(idx % m), gn = (int)(idx / m);
+  // same tile selection as k_zgemm (the skipped tiles have no partial sums)
+  if (herm == 1 && gn / BN < gm / BM) return;
+  if (herm == 2 && gn / BN > gm / BM) return;
   double2 s = make_double2(0.0, 0.0);
   for (int z = 0; z < splits; ++z) s = cadd(s, ws[(long)z * m * n + idx]);
   double2 r = cmul(alpha, s);
@@ -126,7 +133,8 @@ __global__ void k_zgemm_reduce(int m, int n, int splits, double2 alpha, const do
 int choose_splits(int m, int n, int k) {
   const long tiles = (long)((m + BM - 1) / BM) * ((n + BN - 1) / BN);
   long s = (2 * 152 + tiles - 1) / tiles;
-  s = std::min<long>(s, std::max(1, k / 512));
+  // K chunks of at least 128, or of 32 when the tiles alone leave half the SMs idle
+  s = std::min<long>(s, std::max(1, k / (tiles < 76 ? 32 : 128)));
   s = std::min<long>(s, 64);
   return (int)std::max<long>(1, s);
 }
@@ -159,7 +167,8 @@ pw_status pw_zgemm_ex(char opA, char opB, int m, int n, int k, double2 alpha, co
     if (beta.x == 1.0 && beta.y == 0.0) return PW_OK;
     // reuse the reduce kernel with zero partial sums
     pw_count_launch();
-    k_zgemm_reduce<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, st>>>(m, n, 0, alpha, ws, beta, C, ldc);
+    k_zgemm_reduce<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, st>>>(m, n, 0, alpha, ws, beta, C, ldc,
+                                                                          0);
     return pw_check_launch("zgemm k=0");
   }
   int splits = choose_splits(m, n, k);
@@ -180,9 +189,9 @@ pw_status pw_zgemm_ex(char opA, char opB, int m, int n, int k, double2 alpha, co
     {
       pw_count_launch();
       k_zgemm_reduce<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, st>>>(m, n, splits, alpha, ws,
-                                                                          beta, C, ldc);
+                                                                          beta, C, ldc, herm);
     }
-  if (herm) {
+  if (herm == 1) {
     pw_count_launch();
     k_zmirror<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 32), 0, st>>>(C, ldc, m);
   }

@@ -8,7 +8,8 @@ times after one warm-up):
               npw 13,056, 144 bands): k_zgemm, FFT kernels, Rayleigh-Ritz
   step64mix   the same step in mixed precision (k_tc_gemm)
   tcgemm      split-FP16 tensor-core A^H A, A: 104,415 x 1,152 complex
-  heev        FP64 Hermitian eigensolver, n = 1,152 (Householder, D&C)
+  heev        FP64 Hermitian eigensolver, n = 1,152 (Householder, D&C);
+              --n 3456 gives the Si-512 Rayleigh-Ritz order
   hpsi512     FP64 H psi on 16 bands of the Si 512-atom cell (grid 96^3)
 """
 from __future__ import annotations
@@ -26,6 +27,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("case")
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--n", type=int, default=1152, help="order of the heev case")
     a = ap.parse_args()
     import numpy as np
     import torch
@@ -55,7 +57,7 @@ def main():
         torch.cuda.synchronize()
         print("tcgemm done", float(C.abs().max()))
     elif a.case == "heev":
-        n = 1152
+        n = a.n
         rng = np.random.default_rng(0)
         M = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
         H = torch.from_numpy(M + M.conj().T).cuda()
