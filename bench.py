@@ -89,12 +89,14 @@ def reduce_timing(ms: float, steps: int, world: int, device=None):
         ms = float(t.item())
     return ms, world * steps / (ms / 1e3)
 
-def step_flops(npw, nb, ns, k, nproj, grid):
-    """Algorithmic FLOPs of one step (complex products counted as 8 real flops)."""
+def step_flops(npw, nb, ns, k, nproj, grid, hcols=None):
+    """Algorithmic FLOPs of one step (complex products counted as 8 real flops);
+    hcols: columns H is applied to (k, or nb + 2k when H X and H P are fresh)."""
     import math
+    hcols = k if hcols is None else hcols
     n3 = grid[0] * grid[1] * grid[2]
-    fft = 2 * 5.0 * n3 * math.log2(n3) * k          # one inverse + one forward 3-D FFT per band
-    proj = 2 * 8.0 * npw * nproj * k                # beta^H W and beta (D B)
+    fft = 2 * 5.0 * n3 * math.log2(n3) * hcols      # one inverse + one forward 3-D FFT per column
+    proj = 2 * 8.0 * npw * nproj * hcols            # beta^H W and beta (D B)
     gram = 2 * 4.0 * npw * ns * ns                  # S^H S and S^H (H S), Hermitian halves
     # P' = [W P] C_WP and H P' (ns - nb), then X' = X C_X + P' and H X' (nb)
     rot = 2 * 8.0 * npw * nb * (ns - nb) + 2 * 8.0 * npw * nb * nb
@@ -345,8 +347,9 @@ def run_gpu(args):
                for i, nm in enumerate(["chol_inv", "transform", "tridiag", "dc", "backtransform"])}
     ns = reps[-1].nsub
     k_act = reps[-1].nactive
-    fl = step_flops(cell.npw, nb, ns, k_act, cell.nproj, cell.grid)
+    fl = step_flops(cell.npw, nb, ns, k_act, cell.nproj, cell.grid, reps[-1].hpsi_cols)
     roof = roofline(stage, rr_part, fl, ns, nb, args.precision)
+    roof["hpsi_cols"] = reps[-1].hpsi_cols
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -143,13 +143,16 @@ typedef struct {
   double ms;            /* wall time of the step (host clock, synchronised) */
   /* device time per stage (CUDA events on the solver's stream), ms: */
   double ms_resid;      /* residual norms + preconditioner */
-  double ms_hpsi;       /* H W (FFT local part + projector contractions) */
+  double ms_hpsi;       /* every H application of the step (FFT local part +
+                           projector contractions): H W, and in mixed precision
+                           also H X and H P, which are recomputed each step */
   double ms_gram;       /* S^H S and S^H (H S) */
   double ms_rr;         /* Cholesky, L^-1, eigensolve, coefficients (FP64) */
   double ms_rot;        /* rotations X', H X', P', H P' */
   /* inside ms_rr: scale + Cholesky + L^-1 | L^-1 A L^-H | Householder
    * tridiagonalisation | divide and conquer | back-transform + coefficients */
   double ms_rr_part[5];
+  int hpsi_cols;        /* columns H was applied to in the step */
 } pw_step_report;
 
 typedef struct {

@@ -52,7 +52,7 @@ class pw_step_report(ct.Structure):
                 ("nsub", ct.c_int), ("max_resid", ct.c_double), ("ms", ct.c_double),
                 ("ms_resid", ct.c_double), ("ms_hpsi", ct.c_double), ("ms_gram", ct.c_double),
                 ("ms_rr", ct.c_double), ("ms_rot", ct.c_double),
-                ("ms_rr_part", ct.c_double * 5)]
+                ("ms_rr_part", ct.c_double * 5), ("hpsi_cols", ct.c_int)]
 
 
 class pw_request(ct.Structure):

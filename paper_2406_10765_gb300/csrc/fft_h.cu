@@ -285,8 +285,14 @@ pw_status apply_local_t(pw_cell *c, const double2 *psi, int ld, int nb, double2 
   PW_TRY(allow_smem(k_plane<C, T>, plane_bytes));
   PW_TRY(allow_smem(k_z_to_sphere<C>, line_bytes));
   const double scale = 1.0 / ((double)Nx * Ny * Nz);
+  constexpr int fp32 = sizeof(C) == sizeof(float2);
+  const bool reg = pw_fft_reg_supported(c, fp32);
   for (int b0 = 0; b0 < nb; b0 += batch) {
     const int nbb = std::min(batch, nb - b0);
+    if (reg) {
+      PW_TRY(pw_fft_reg_batch(c, psi + (long)b0 * ld, ld, nbb, hpsi + (long)b0 * ld, Z, fp32, scale, st));
+      continue;
+    }
     dim3 gcols((c->ncol + cb - 1) / cb, nbb);
     pw_count_launch();
     k_sphere_to_z<C><<<gcols, 256, line_bytes, st>>>(psi + (long)b0 * ld, ld, c->d_colstart,
@@ -321,8 +327,13 @@ pw_status apply_local_into(pw_cell *c, const double2 *psi, int ld, int nb, doubl
   PW_TRY(allow_smem(k_plane<C, double>, plane_bytes));
   PW_TRY(allow_smem(k_z_to_sphere<C>, line_bytes));
   const double scale = 1.0 / ((double)Nx * Ny * Nz);
+  const bool reg = pw_fft_reg_supported(c, 0);
   for (int b0 = 0; b0 < nb; b0 += batch) {
     const int nbb = std::min(batch, nb - b0);
+    if (reg) {
+      PW_TRY(pw_fft_reg_batch(c, psi + (long)b0 * ld, ld, nbb, hpsi + (long)b0 * ld, Z, 0, scale, st));
+      continue;
+    }
     dim3 gcols((c->ncol + cb - 1) / cb, nbb);
     pw_count_launch();
     k_sphere_to_z<C><<<gcols, 256, line_bytes, st>>>(psi + (long)b0 * ld, ld, c->d_colstart,

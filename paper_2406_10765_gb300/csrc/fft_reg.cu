@@ -1,0 +1,403 @@
+// Register-resident line FFTs for the local part of H psi (Sec. II-B), used
+// when every grid dimension is N = L * R with L = 2^min(a, 5) lanes and
+// R = N / L <= 16 values per lane (N = 2^a 3^b).
+//
+// A line x[0..N) is held by a group of L lanes, lane l owning x[l + L r],
+// r < R.  With n = l + L r and k = k2 + R k1:
+//   1. in-lane DFT of length R over r            -> Y[l][k2]
+//   2. twiddle Y[l][k2] *= w_N^(l k2)
+//   3. DFT of length L across the lanes for each k2 (radix-2 decimation in
+//      frequency with warp shuffles), which leaves X[k2 + R k1] in lane
+//      bitrev(k1).
+// Each pass loads a line from shared memory in the strided order above and
+// stores the result at its natural position, so a whole 1-D transform is one
+// shared-memory read and one write, with no block barrier inside it.
+//
+// The kernels mirror the generic Stockham path (k_sphere_to_z, k_plane,
+// k_z_to_sphere): same data layout, same sign and scaling conventions.
+#include "pw_internal.cuh"
+
+namespace {
+
+constexpr int log2c(int x) { return x <= 1 ? 0 : 1 + log2c(x / 2); }
+
+template <typename C> __device__ __forceinline__ C czero_r() { C r; r.x = 0; r.y = 0; return r; }
+template <typename C> __device__ __forceinline__ C conj_if(C w, bool inv) {
+  if (inv) w.y = -w.y;
+  return w;
+}
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return v;
+}
+__device__ __forceinline__ double2 shfl_xor2(double2 v, int m) {
+  v.x = __shfl_xor_sync(0xffffffffu, v.x, m);
+  v.y = __shfl_xor_sync(0xffffffffu, v.y, m);
+  return v;
+}
+
+// ---- in-lane DFTs: y_q = sum_p x_p exp(s 2 pi i p q / R), s = -1 forward, +1 inverse
+template <typename C, int R, int N> struct LaneDFT;
+
+template <typename C, int N> struct LaneDFT<C, 1, N> {
+  static __device__ __forceinline__ void run(C (&)[1], const C *, bool) {}
+};
+template <typename C, int N> struct LaneDFT<C, 2, N> {
+  static __device__ __forceinline__ void run(C (&v)[2], const C *, bool) {
+    const C a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  }
+};
+template <typename C, int N> struct LaneDFT<C, 3, N> {
+  static __device__ __forceinline__ void run(C (&v)[3], const C *, bool inv) {
+    typedef decltype(v[0].x) T;
+    const T h = (T)0.86602540378443864676;   // sqrt(3)/2
+    const C a = v[0], s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+    C m, t;
+    m.x = a.x - (T)0.5 * s.x;
+    m.y = a.y - (T)0.5 * s.y;
+    if (inv) { t.x = -h * d.y; t.y = h * d.x; } else { t.x = h * d.y; t.y = -h * d.x; }
+    v[0] = cadd(a, s);
+    v[1] = cadd(m, t);
+    v[2] = csub(m, t);
+  }
+};
+template <typename C, int N> struct LaneDFT<C, 4, N> {
+  static __device__ __forceinline__ void run(C (&v)[4], const C *, bool inv) {
+    const C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const C s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+    C jd;   // -i d13 (forward) or +i d13 (inverse)
+    if (inv) { jd.x = -d13.y; jd.y = d13.x; } else { jd.x = d13.y; jd.y = -d13.x; }
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, jd);
+    v[3] = csub(d02, jd);
+  }
+};
+// composite R = P Q: index r = p + P q, output k = kq + Q kp; tw holds w_N^m
+template <typename C, int R, int N> struct LaneDFT {
+  static constexpr int P = (R % 4 == 0) ? 4 : (R % 2 == 0) ? 2 : 3;
+  static constexpr int Q = R / P;
+  static __device__ __forceinline__ void run(C (&v)[R], const C *tw, bool inv) {
+    C t[P][Q];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      C u[Q];
+#pragma unroll
+      for (int q = 0; q < Q; ++q) u[q] = v[p + P * q];
+      LaneDFT<C, Q, N>::run(u, tw, inv);
+#pragma unroll
+      for (int kq = 0; kq < Q; ++kq) {
+        C x = u[kq];
+        if (p > 0 && kq > 0) x = cmul(x, conj_if(tw[p * kq * (N / R)], inv));
+        t[p][kq] = x;
+      }
+    }
+#pragma unroll
+    for (int kq = 0; kq < Q; ++kq) {
+      C u[P];
+#pragma unroll
+      for (int p = 0; p < P; ++p) u[p] = t[p][kq];
+      LaneDFT<C, P, N>::run(u, tw, inv);
+#pragma unroll
+      for (int kp = 0; kp < P; ++kp) v[kq + Q * kp] = u[kp];
+    }
+  }
+};
+
+// per-lane twiddles of a line: w_N^(l k2) and the shuffle-stage factors
+template <typename C, int L, int R> struct LineTw {
+  static constexpr int N = L * R, LG = log2c(L);
+  C lt[R > 1 ? R - 1 : 1];
+  C st[LG > 0 ? LG : 1];
+  __device__ __forceinline__ void init(const C *tw, int l) {
+#pragma unroll
+    for (int k2 = 1; k2 < R; ++k2) lt[k2 - 1] = tw[l * k2];
+    int s = 0;
+#pragma unroll
+    for (int h = L / 2; h >= 1; h >>= 1, ++s) st[s] = tw[(l & (h - 1)) * (N / (2 * h))];
+  }
+  // natural index of register k2 of lane l after line_fft
+  __device__ __forceinline__ int out_index(int k2, int l) const {
+    if (LG == 0) return k2;
+    return k2 + R * (int)(__brev((unsigned)l) >> (32 - LG));
+  }
+};
+
+template <typename C, int L, int R>
+__device__ __forceinline__ void line_fft(C (&v)[R], const LineTw<C, L, R> &t, const C *tw, int l,
+                                         bool inv) {
+  LaneDFT<C, R, L * R>::run(v, tw, inv);
+#pragma unroll
+  for (int k2 = 1; k2 < R; ++k2) v[k2] = cmul(v[k2], conj_if(t.lt[k2 - 1], inv));
+  int s = 0;
+#pragma unroll
+  for (int h = L / 2; h >= 1; h >>= 1, ++s) {
+    const C w = conj_if(t.st[s], inv);
+    const bool upper = (l & h) != 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const C p = shfl_xor2(v[r], h);
+      v[r] = upper ? cmul(csub(p, v[r]), w) : cadd(v[r], p);
+    }
+  }
+}
+
+template <typename C> __device__ __forceinline__ C from64r(double2 a);
+template <> __device__ __forceinline__ double2 from64r<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 from64r<float2>(double2 a) {
+  return make_float2((float)a.x, (float)a.y);
+}
+
+constexpr int ZCB = 16;          // z-lines per block in K1 / K3
+constexpr int ZTHREADS = 256;
+template <typename C> struct RegPlaneThreads { static constexpr int value = 512; };
+template <> struct RegPlaneThreads<double2> { static constexpr int value = 256; };
+
+// FFT of `nlines` lines held in shared memory (line i at buf + i * ls, element
+// e at e * es), all warps of the block; lines are processed G = 32 / L at a
+// time per warp, every lane taking part in the shuffles
+template <typename C, int L, int R>
+__device__ __forceinline__ void fft_lines_reg(C *buf, int nlines, int ls, int es, const C *tw,
+                                              const LineTw<C, L, R> &t, bool inv) {
+  constexpr int G = 32 / L;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gid = lane / L, l = lane % L;
+  for (int base = warp * G; base < nlines; base += nw * G) {
+    const int line = base + gid;
+    const bool act = line < nlines;
+    C *p = buf + (long)(act ? line : 0) * ls;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = act ? p[(l + L * r) * es] : czero_r<C>();
+    line_fft<C, L, R>(v, t, tw, l, inv);
+    if (act) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) p[t.out_index(r, l) * es] = v[r];
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------- K1 ----
+template <typename C, int L, int R>
+__global__ void __launch_bounds__(ZTHREADS) k_sphere_to_z_reg(const double2 *__restrict__ psi, int ld,
+                                                              const int *__restrict__ colstart,
+                                                              const int *__restrict__ gcol,
+                                                              const int *__restrict__ gz, int ncol,
+                                                              const C *__restrict__ twz,
+                                                              C *__restrict__ Z) {
+  constexpr int Nz = L * R, ls = Nz + 1;
+  __shared__ C lines[ZCB * ls];
+  const int c0 = blockIdx.x * ZCB;
+  const int nc = min(ZCB, ncol - c0);
+  const int b = blockIdx.y;
+  const double2 *p = psi + (long)b * ld;
+  LineTw<C, L, R> t;
+  t.init(twz, (threadIdx.x & 31) % L);
+  for (int i = threadIdx.x; i < nc * ls; i += blockDim.x) lines[i] = czero_r<C>();
+  __syncthreads();
+  const int g0 = colstart[c0], g1 = colstart[c0 + nc];
+  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x)
+    lines[(gcol[g] - c0) * ls + gz[g]] = from64r<C>(p[g]);
+  __syncthreads();
+  fft_lines_reg<C, L, R>(lines, nc, ls, 1, twz, t, true);
+  __syncthreads();
+  C *Zb = Z + (long)b * Nz * ncol;
+  for (int i = threadIdx.x; i < nc * Nz; i += blockDim.x) {
+    const int z = i / nc, cl = i % nc;
+    Zb[(long)z * ncol + c0 + cl] = lines[cl * ls + z];
+  }
+}
+
+// ---------------------------------------------------------------- K2 ----
+template <typename C, typename T, int L, int R>
+__global__ void __launch_bounds__(RegPlaneThreads<C>::value) k_plane_reg(C *__restrict__ Z, int ncol,
+                                                                         const int *__restrict__ colxy,
+                                                                         int mxmax, const C *__restrict__ twx,
+                                                                         int Nz, const T *__restrict__ V) {
+  constexpr int N = L * R, pxs = N + 1, G = 32 / L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *P = reinterpret_cast<C *>(smem_raw);
+  const int z = blockIdx.x, b = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gid = lane / L, l = lane % L;
+  LineTw<C, L, R> t;
+  t.init(twx, l);
+  C *Zp = Z + ((long)b * Nz + z) * ncol;
+  for (int i = threadIdx.x; i < N * pxs; i += blockDim.x) P[i] = czero_r<C>();
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    const int xy = colxy[c];
+    P[(xy / N) * pxs + (xy % N)] = Zp[c];
+  }
+  __syncthreads();
+  // inverse FFT along y on the x-columns that meet the sphere (x in [-mxmax, mxmax])
+  const int nxe = 2 * mxmax + 1;
+  for (int base = warp * G; base < nxe; base += nw * G) {
+    const int xi = base + gid;
+    const bool act = xi < nxe;
+    int x = xi - mxmax;
+    if (x < 0) x += N;
+    C *col = P + (act ? x : 0);
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = act ? col[(l + L * r) * pxs] : czero_r<C>();
+    line_fft<C, L, R>(v, t, twx, l, true);
+    if (act) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) col[t.out_index(r, l) * pxs] = v[r];
+    }
+  }
+  __syncthreads();
+  // each row: inverse FFT along x, V(r), forward FFT along x
+  const T *Vz = V + (long)z * N * N;
+  for (int base = warp * G; base < N; base += nw * G) {
+    const int y = base + gid;
+    const bool act = y < N;
+    C *row = P + (long)(act ? y : 0) * pxs;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = act ? row[l + L * r] : czero_r<C>();
+    line_fft<C, L, R>(v, t, twx, l, true);
+    if (act) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int x = t.out_index(r, l);
+        const T vv = Vz[(long)y * N + x];
+        C e = v[r];
+        e.x *= vv;
+        e.y *= vv;
+        row[x] = e;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = act ? row[l + L * r] : czero_r<C>();
+    line_fft<C, L, R>(v, t, twx, l, false);
+    if (act) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) row[t.out_index(r, l)] = v[r];
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // forward FFT along y on the same x-columns
+  for (int base = warp * G; base < nxe; base += nw * G) {
+    const int xi = base + gid;
+    const bool act = xi < nxe;
+    int x = xi - mxmax;
+    if (x < 0) x += N;
+    C *col = P + (act ? x : 0);
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = act ? col[(l + L * r) * pxs] : czero_r<C>();
+    line_fft<C, L, R>(v, t, twx, l, false);
+    if (act) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) col[t.out_index(r, l) * pxs] = v[r];
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    const int xy = colxy[c];
+    Zp[c] = P[(xy / N) * pxs + (xy % N)];
+  }
+}
+
+// ---------------------------------------------------------------- K3 ----
+template <typename C, int L, int R>
+__global__ void __launch_bounds__(ZTHREADS) k_z_to_sphere_reg(const C *__restrict__ Z, int ncol,
+                                                              const C *__restrict__ twz,
+                                                              const int *__restrict__ colstart,
+                                                              const int *__restrict__ gcol,
+                                                              const int *__restrict__ gz,
+                                                              const double *__restrict__ kin,
+                                                              const double2 *__restrict__ psi, int ld,
+                                                              double2 *__restrict__ hpsi, double scale) {
+  constexpr int Nz = L * R, ls = Nz + 1;
+  __shared__ C lines[ZCB * ls];
+  const int c0 = blockIdx.x * ZCB;
+  const int nc = min(ZCB, ncol - c0);
+  const int b = blockIdx.y;
+  LineTw<C, L, R> t;
+  t.init(twz, (threadIdx.x & 31) % L);
+  const C *Zb = Z + (long)b * Nz * ncol;
+  for (int i = threadIdx.x; i < nc * Nz; i += blockDim.x) {
+    const int z = i / nc, cl = i % nc;
+    lines[cl * ls + z] = Zb[(long)z * ncol + c0 + cl];
+  }
+  __syncthreads();
+  fft_lines_reg<C, L, R>(lines, nc, ls, 1, twz, t, false);
+  __syncthreads();
+  const int g0 = colstart[c0], g1 = colstart[c0 + nc];
+  const double2 *p = psi + (long)b * ld;
+  double2 *h = hpsi + (long)b * ld;
+  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+    const C v = lines[(gcol[g] - c0) * ls + gz[g]];
+    const double k = kin[g];
+    const double2 x = p[g];
+    h[g] = make_double2(k * x.x + scale * (double)v.x, k * x.y + scale * (double)v.y);
+  }
+}
+
+template <typename C> __host__ __device__ inline const C *twtab(const pw_fft_axis &a);
+template <> inline const double2 *twtab<double2>(const pw_fft_axis &a) { return a.tw64; }
+template <> inline const float2 *twtab<float2>(const pw_fft_axis &a) { return a.tw32; }
+
+template <typename C, typename T, int L, int R>
+pw_status run_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hpsi, C *Z, const T *V,
+                    double scale, cudaStream_t st) {
+  constexpr int N = L * R;
+  const size_t plane_bytes = (size_t)N * (N + 1) * sizeof(C);
+  if (plane_bytes > 227 * 1024) return PW_ERR_ARG;
+  if (plane_bytes > 48 * 1024)
+    PW_CUDA(cudaFuncSetAttribute(k_plane_reg<C, T, L, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)plane_bytes));
+  const dim3 gcols((c->ncol + ZCB - 1) / ZCB, nbb);
+  pw_count_launch();
+  k_sphere_to_z_reg<C, L, R><<<gcols, ZTHREADS, 0, st>>>(psi, ld, c->d_colstart, c->d_gcol, c->d_gz,
+                                                         c->ncol, twtab<C>(c->ax[2]), Z);
+  pw_count_launch();
+  k_plane_reg<C, T, L, R><<<dim3(N, nbb), RegPlaneThreads<C>::value, plane_bytes, st>>>(
+      Z, c->ncol, c->d_colxy, c->mxmax, twtab<C>(c->ax[0]), N, V);
+  pw_count_launch();
+  k_z_to_sphere_reg<C, L, R><<<gcols, ZTHREADS, 0, st>>>(Z, c->ncol, twtab<C>(c->ax[2]), c->d_colstart,
+                                                         c->d_gcol, c->d_gz, c->d_kin, psi, ld, hpsi,
+                                                         scale);
+  return pw_check_launch("local part (register FFT)");
+}
+
+// grid sizes with a register FFT: N -> (L, R)
+#define PW_REG_SIZES(X) X(16, 16, 1) X(24, 8, 3) X(32, 32, 1) X(36, 4, 9) X(48, 16, 3) \
+                        X(64, 32, 2) X(72, 8, 9) X(96, 32, 3) X(128, 32, 4) X(144, 16, 9)
+
+}  // namespace
+
+bool pw_fft_reg_supported(const pw_cell *c, int fp32) {
+  const int n = c->N[0];
+  if (c->N[1] != n || c->N[2] != n) return false;
+  if ((size_t)n * (n + 1) * (fp32 ? 8 : 16) > 227 * 1024) return false;   // plane in shared memory
+  // the y-columns that meet the sphere must not wrap onto each other
+  if (2 * c->mxmax + 1 > n) return false;
+#define PW_CASE(NN, LL, RR) if (n == NN) return true;
+  PW_REG_SIZES(PW_CASE)
+#undef PW_CASE
+  return false;
+}
+
+pw_status pw_fft_reg_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hpsi, void *Z,
+                           int fp32, double scale, cudaStream_t st) {
+  const int n = c->N[0];
+#define PW_CASE(NN, LL, RR)                                                                          \
+  if (n == NN) {                                                                                     \
+    if (fp32)                                                                                        \
+      return run_batch<float2, float, LL, RR>(c, psi, ld, nbb, hpsi, (float2 *)Z, c->d_Vf, scale, st); \
+    return run_batch<double2, double, LL, RR>(c, psi, ld, nbb, hpsi, (double2 *)Z, c->d_V, scale, st); \
+  }
+  PW_REG_SIZES(PW_CASE)
+#undef PW_CASE
+  return PW_ERR_ARG;
+}

@@ -42,7 +42,8 @@ struct pw_solver {
   int iter = 0, dropped = 0;
   pw_dense_ws dws;
   size_t bytes = 0;
-  cudaEvent_t ev[8] = {};    // stage boundaries of the last step
+  cudaEvent_t ev[12] = {};   // stage boundaries of the last step (7-10: H X and H P)
+  int hx_applied = 0;        // H X was recomputed in the last refresh
   // mixed precision: split-FP16 operands of S, H S and the coefficients
   pw_tc_operand opSA, opSB, opHSB, opST, opHST, opC, opCP, opM;
   double2 *Mx = nullptr;     // mixed: d o L^-H of the current Gram (3nb x 3nb)
@@ -336,9 +337,13 @@ pw_status check_tc_err(pw_solver *s) {
 
 // make HS[:, 0:nb] = H X current (mixed precision recomputes it)
 pw_status ensure_hx(pw_solver *s) {
+  s->hx_applied = 0;
   if (s->hx_valid) return PW_OK;
+  cudaEventRecord(s->ev[7], s->st);
   PW_TRY(solver_apply_H(s, s->S, s->HS, s->nb));
+  cudaEventRecord(s->ev[8], s->st);
   s->hx_valid = true;
+  s->hx_applied = 1;
   return PW_OK;
 }
 
@@ -487,13 +492,16 @@ extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_repor
   cudaEventRecord(s->ev[1], s->st);
   PW_TRY(solver_apply_H(s, W, HW, k));
   cudaEventRecord(s->ev[2], s->st);
-  int ns = nb + k;
+  int ns = nb + k, hp_applied = 0;
   if (s->haveP) {
     pw_count_launch();
     k_gather_cols<<<(unsigned)(((long)npw * k + 255) / 256), 256, 0, s->st>>>(
         s->P, npw, npw, s->act, k, s->S + (size_t)(nb + k) * npw);
     if (s->fresh_h) {
+      cudaEventRecord(s->ev[9], s->st);
       PW_TRY(solver_apply_H(s, s->S + (size_t)(nb + k) * npw, s->HS + (size_t)(nb + k) * npw, k));
+      cudaEventRecord(s->ev[10], s->st);
+      hp_applied = 1;
     } else {
       pw_count_launch();
       k_gather_cols<<<(unsigned)(((long)npw * k + 255) / 256), 256, 0, s->st>>>(
@@ -545,7 +553,11 @@ extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_repor
     cudaEventElapsedTime(&t[3], s->ev[4], s->ev[5]);
     cudaEventElapsedTime(&t[4], s->ev[5], s->ev[6]);
     rep->ms_resid = t[0];
-    rep->ms_hpsi = t[1];
+    float thx = 0.f, thp = 0.f;
+    if (s->hx_applied) cudaEventElapsedTime(&thx, s->ev[7], s->ev[8]);
+    if (hp_applied) cudaEventElapsedTime(&thp, s->ev[9], s->ev[10]);
+    rep->ms_hpsi = t[1] + thx + thp;
+    rep->hpsi_cols = k + (s->hx_applied ? nb : 0) + (hp_applied ? k : 0);
     rep->ms_gram = t[2];
     rep->ms_rr = t[3];
     rep->ms_rot = t[4];

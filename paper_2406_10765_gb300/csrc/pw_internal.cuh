@@ -102,6 +102,11 @@ pw_status pw_apply_nonlocal(pw_cell *c, const double2 *psi, int ld, int nb, doub
 
 // FP64 H pieces writing only into caller-provided scratch (no allocation)
 size_t pw_local_zbytes_per_band(const pw_cell *c);
+// register-resident line FFTs for cubic grids of supported sizes (one batch
+// of nbb bands through K1-K3 into the z-pencil buffer Z)
+bool pw_fft_reg_supported(const pw_cell *c, int fp32);
+pw_status pw_fft_reg_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hpsi, void *Z,
+                           int fp32, double scale, cudaStream_t st);
 pw_status pw_apply_local_fp64_into(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
                                    void *zbuf, size_t zbytes, cudaStream_t st);
 pw_status pw_apply_nonlocal_fp64_into(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,

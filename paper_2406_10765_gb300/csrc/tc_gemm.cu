@@ -173,6 +173,35 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &e, float x) {
 // (double-buffered); epilogue warps fold each block into compensated
 // (two-sum) FP32 register sums, so the FP32 rounding of the tensor-core
 // accumulator covers only 12 MMAs.
+// Epilogue conversions on integer bits (FP64 issues at about two operations
+// per clock per SM on this part).
+// float -> double, exact; float subnormals (far below anything the FP16
+// slices produce) flush to zero
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  const unsigned long long ed = e == 0xFFu ? 0x7FFull : (unsigned long long)(e + 896u);
+  return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+// exponent k of a power-of-two row scale 2^k held as a float; a zero (or
+// subnormal) scale gives a large negative k, so the product flushes to zero
+__device__ __forceinline__ int pow2_exp(float s) {
+  const int e = (int)((__float_as_uint(s) >> 23) & 0xFFu);
+  return e == 0 ? -4096 : e - 127;
+}
+// x 2^k by exponent arithmetic; results below the normal range become zero
+__device__ __forceinline__ double scale_pow2(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return __longlong_as_double(b & (long long)0x8000000000000000ull);
+  const int en = ex + k;
+  if (en <= 0) return __longlong_as_double(b & (long long)0x8000000000000000ull);
+  if (en >= 0x7FF) return __longlong_as_double((b & (long long)0x8000000000000000ull) | 0x7FF0000000000000ll);
+  return __longlong_as_double(b + ((long long)k << 52));
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               int a_slice_rows, int b_slice_rows, int m, int n, int kblocks, int mtiles,
@@ -304,7 +333,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int c0 = 0; c0 < EPI_COLS; c0 += 32) tmem_ld32(cmp_base + c0, cmp + c0);
     const int r = m0 + q * 32 + lane;            // output (real) row of this thread
     if (ok && r < m) {
-      const double sa = inv_sa[r];
+      // value = (sum + cmp) 2^(ka + kb): one FP64 add, the rest on integer bits
+      const int ka = pow2_exp(inv_sa[r]);
       const int cb = n0 + h * EPI_COLS;
       if (mode == 0) {                         // ROWPAIR
         const int i = r >> 1, c = r & 1;
@@ -313,7 +343,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int col = cb + t;
           if (col < n) {
             double *dst = (double *)&C[i + (long)col * ldc] + c;
-            const double val = ((double)sum[t] + (double)cmp[t]) * sa * (double)inv_sb[col];
+            const double val = scale_pow2(f2d_bits(sum[t]) + f2d_bits(cmp[t]), ka + pow2_exp(inv_sb[col]));
             *dst = accumulate ? *dst + val : val;
           }
         }
@@ -323,8 +353,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int col = cb + t;
           if (col < n) {
             double2 *dst = &C[r + (long)(col >> 1) * ldc];
-            const double re = ((double)sum[t] + (double)cmp[t]) * sa * (double)inv_sb[col];
-            const double im = ((double)sum[t + 1] + (double)cmp[t + 1]) * sa * (double)inv_sb[col + 1];
+            const double re = scale_pow2(f2d_bits(sum[t]) + f2d_bits(cmp[t]), ka + pow2_exp(inv_sb[col]));
+            const double im =
+                scale_pow2(f2d_bits(sum[t + 1]) + f2d_bits(cmp[t + 1]), ka + pow2_exp(inv_sb[col + 1]));
             if (accumulate) { double2 o = *dst; o.x += re; o.y += im; *dst = o; }
             else *dst = make_double2(re, im);
           }
@@ -357,19 +388,68 @@ __device__ float block_maxf(float v) {
   return r;
 }
 
-// power-of-two scale s with max * s in [2^13, 2^14)  (s = 1 for an all-zero row)
-__device__ __forceinline__ double pow2_scale(double mx, float *inv) {
-  if (!(mx > 0.0)) { *inv = 1.0f; return 1.0; }
-  int e;
-  frexp(mx, &e);                 // mx = f 2^e, f in [0.5, 1)
-  const int sh = 14 - e;         // mx 2^sh in [2^13, 2^14)
-  *inv = ldexpf(1.0f, -sh);
-  return ldexp(1.0, sh);
+// The splits below run on integer and FP32 arithmetic only: FP64 issues at
+// about two operations per clock per SM on this part, which made the split
+// kernels FP64-bound at several times their memory time.
+
+// |x| as ordered integer bits (for non-negative doubles the integer order is
+// the numeric order)
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 
-__device__ __forceinline__ void split2(double x, __half &hi, __half &lo) {
-  hi = __double2half(x);
-  lo = __double2half(x - (double)__half2float(hi));
+// x 2^sh rounded to the nearest float, ties to even, from the bit pattern;
+// magnitudes below the smallest normal float become a signed zero (they are
+// far below what the two FP16 slices can hold after the row scaling)
+__device__ __forceinline__ float d2f_pow2(double x, int sh) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return __uint_as_float(sign);
+  e += sh - 1023 + 127;
+  unsigned m = (unsigned)((b >> 29) & 0x7FFFFFu);      // top 23 of the 52 fraction bits
+  const unsigned rest = (unsigned)(b & 0x1FFFFFFFu);    // the 29 dropped bits
+  if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) {
+    if (++m == 0x800000u) { m = 0; ++e; }
+  }
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | m);
+}
+
+// hi = fp16(x), lo = fp16(x - hi); x - hi is exact in FP32
+__device__ __forceinline__ void split2f(float x, __half &hi, __half &lo) {
+  hi = __float2half_rn(x);
+  lo = __float2half_rn(x - __half2float(hi));
+}
+
+__device__ __forceinline__ unsigned long long warp_maxu(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+__device__ unsigned long long block_maxu(unsigned long long v) {
+  __shared__ unsigned long long shm[32];
+  v = warp_maxu(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  unsigned long long r = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = shm[w] > r ? shm[w] : r;
+  __syncthreads();
+  return r;
+}
+
+// exponent sh of the power-of-two row scale 2^sh (max 2^sh in [2^13, 2^14))
+__device__ __forceinline__ int pow2_shift(double mx, float *inv) {
+  if (!(mx > 0.0)) { *inv = 1.0f; return 0; }
+  int e;
+  frexp(mx, &e);
+  const int sh = 14 - e;
+  *inv = ldexpf(1.0f, -sh);
+  return sh;
 }
 
 // Rows from columns: for each column c of X (npw x ncols, ld), real rows
@@ -384,26 +464,35 @@ __global__ void __launch_bounds__(256) k_split_rows(const double2 *__restrict__ 
   const int c = blockIdx.x;
   const double2 *x = X + (long)c * ld;
   const double cs = colscale ? colscale[c] : 1.0;
-  float mx = 0.0f;
-  for (int g = threadIdx.x; g < npw; g += blockDim.x)
-    mx = fmaxf(mx, (float)fmax(fabs(x[g].x * cs), fabs(x[g].y * cs)));
-  mx = block_maxf(mx);
+  unsigned long long mb = 0;
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    const double2 v = x[g];
+    const unsigned long long a = abs_bits(v.x), b = abs_bits(v.y);
+    const unsigned long long t = a > b ? a : b;
+    mb = t > mb ? t : mb;
+  }
+  mb = block_maxu(mb);
   float inv;
-  const double s = pow2_scale((double)mx * 1.0000001, &inv) * cs;
+  const int sh = pow2_shift(__longlong_as_double((long long)mb) * fabs(cs) * 1.0000001, &inv);
   const long slice = (long)rows_total * kpad;
   const int r0 = conj ? 2 * c : c;
   if (threadIdx.x == 0) { inv_scale[r0] = inv; if (conj) inv_scale[r0 + 1] = inv; }
   __half *o0 = out + (long)r0 * kpad;
   for (int g = threadIdx.x; g < kpad / 2; g += blockDim.x) {
-    double re = 0.0, im = 0.0;
-    if (g < npw) { re = x[g].x * s; im = x[g].y * s; }
+    float re = 0.0f, im = 0.0f;
+    if (g < npw) {
+      double2 v = x[g];
+      if (colscale) { v.x *= cs; v.y *= cs; }
+      re = d2f_pow2(v.x, sh);
+      im = d2f_pow2(v.y, sh);
+    }
     __half h, l;
-    split2(re, h, l); o0[2 * g] = h; o0[slice + 2 * g] = l;
-    split2(im, h, l); o0[2 * g + 1] = h; o0[slice + 2 * g + 1] = l;
+    split2f(re, h, l); o0[2 * g] = h; o0[slice + 2 * g] = l;
+    split2f(im, h, l); o0[2 * g + 1] = h; o0[slice + 2 * g + 1] = l;
     if (conj) {
       __half *o1 = o0 + kpad;
-      split2(-im, h, l); o1[2 * g] = h; o1[slice + 2 * g] = l;
-      split2(re, h, l); o1[2 * g + 1] = h; o1[slice + 2 * g + 1] = l;
+      split2f(-im, h, l); o1[2 * g] = h; o1[slice + 2 * g] = l;
+      split2f(re, h, l); o1[2 * g + 1] = h; o1[slice + 2 * g + 1] = l;
     }
   }
 }
@@ -414,12 +503,18 @@ __global__ void __launch_bounds__(256) k_rowmax(const double2 *__restrict__ X, i
                                                 int ncols, float *__restrict__ rmax) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= npw) return;
-  float m = 0.0f;
+  unsigned long long m = 0;
   for (int t = 0; t < ncols; ++t) {
     const double2 v = X[g + (long)t * ld];
-    m = fmaxf(m, (float)fmax(fabs(v.x), fabs(v.y)));
+    const unsigned long long a = abs_bits(v.x), b = abs_bits(v.y);
+    const unsigned long long u = a > b ? a : b;
+    m = u > m ? u : m;
   }
-  rmax[g] = m;
+  // rounded up to a float so that the scale never undercounts the maximum
+  const double md = __longlong_as_double((long long)m);
+  float mf = d2f_pow2(md, 0);
+  if ((double)mf < md) mf = __uint_as_float(__float_as_uint(mf) + 1u);
+  rmax[g] = mf;
 }
 
 __global__ void __launch_bounds__(256) k_split_trans(const double2 *__restrict__ X, int ld, int npw,
@@ -443,7 +538,7 @@ __global__ void __launch_bounds__(256) k_split_trans(const double2 *__restrict__
     const int g = g0 + gg;
     if (g >= npw) continue;
     float inv;
-    const double s = pow2_scale((double)rmax[g] * 1.0000001, &inv);
+    const int sh = pow2_shift((double)rmax[g] * 1.0000001, &inv);
     if (blockIdx.y == 0 && tx == 0) inv_scale[g] = inv;
     __half *o = out + (long)g * kpad;
     for (int tt = tx; tt < 64; tt += 32) {
@@ -451,8 +546,8 @@ __global__ void __launch_bounds__(256) k_split_trans(const double2 *__restrict__
       if (2 * t >= kpad) continue;
       const double2 v = tileS[tt][gg];
       __half h, l;
-      split2(v.x * s, h, l); o[2 * t] = h; o[slice + 2 * t] = l;
-      split2(v.y * s, h, l); o[2 * t + 1] = h; o[slice + 2 * t + 1] = l;
+      split2f(d2f_pow2(v.x, sh), h, l); o[2 * t] = h; o[slice + 2 * t] = l;
+      split2f(d2f_pow2(v.y, sh), h, l); o[2 * t + 1] = h; o[slice + 2 * t + 1] = l;
     }
   }
 }
@@ -467,25 +562,33 @@ __global__ void __launch_bounds__(256) k_split_coef(const double2 *__restrict__ 
                                                     float *__restrict__ inv_scale) {
   const int j = blockIdx.x;
   const double2 *x = Cm + (long)j * ld;
-  float mx = 0.0f;
+  unsigned long long mb = 0;
   for (int t = threadIdx.x; t < kdim; t += blockDim.x) {
-    const double f = d ? d[t] : 1.0;
-    mx = fmaxf(mx, (float)fmax(fabs(x[t].x * f), fabs(x[t].y * f)));
+    double2 v = x[t];
+    if (d) { v.x *= d[t]; v.y *= d[t]; }
+    const unsigned long long a = abs_bits(v.x), b = abs_bits(v.y);
+    const unsigned long long u = a > b ? a : b;
+    mb = u > mb ? u : mb;
   }
-  mx = block_maxf(mx);
+  mb = block_maxu(mb);
   float inv;
-  const double s = pow2_scale((double)mx * 1.0000001, &inv);
+  const int sh = pow2_shift(__longlong_as_double((long long)mb) * 1.0000001, &inv);
   if (threadIdx.x == 0) { inv_scale[2 * j] = inv; inv_scale[2 * j + 1] = inv; }
   const long slice = (long)rows_total * kpad;
   __half *o0 = out + (long)(2 * j) * kpad, *o1 = o0 + kpad;
   for (int t = threadIdx.x; t < kpad / 2; t += blockDim.x) {
-    double re = 0.0, im = 0.0;
-    if (t < kdim) { const double f = d ? d[t] * s : s; re = x[t].x * f; im = x[t].y * f; }
+    float re = 0.0f, im = 0.0f;
+    if (t < kdim) {
+      double2 v = x[t];
+      if (d) { v.x *= d[t]; v.y *= d[t]; }
+      re = d2f_pow2(v.x, sh);
+      im = d2f_pow2(v.y, sh);
+    }
     __half h, l;
-    split2(re, h, l); o0[2 * t] = h; o0[slice + 2 * t] = l;
-    split2(-im, h, l); o0[2 * t + 1] = h; o0[slice + 2 * t + 1] = l;
-    split2(im, h, l); o1[2 * t] = h; o1[slice + 2 * t] = l;
-    split2(re, h, l); o1[2 * t + 1] = h; o1[slice + 2 * t + 1] = l;
+    split2f(re, h, l); o0[2 * t] = h; o0[slice + 2 * t] = l;
+    split2f(-im, h, l); o0[2 * t + 1] = h; o0[slice + 2 * t + 1] = l;
+    split2f(im, h, l); o1[2 * t] = h; o1[slice + 2 * t] = l;
+    split2f(re, h, l); o1[2 * t + 1] = h; o1[slice + 2 * t + 1] = l;
   }
 }
 

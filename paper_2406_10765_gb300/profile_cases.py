@@ -11,6 +11,7 @@ times after one warm-up):
   heev        FP64 Hermitian eigensolver, n = 1,152 (Householder, D&C);
               --n 3456 gives the Si-512 Rayleigh-Ritz order
   hpsi512     FP64 H psi on 16 bands of the Si 512-atom cell (grid 96^3)
+  hpsi512mix  mixed-precision H psi on --nb bands (default 1152) of the same cell
 """
 from __future__ import annotations
 
@@ -28,6 +29,7 @@ def main():
     ap.add_argument("case")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--n", type=int, default=1152, help="order of the heev case")
+    ap.add_argument("--nb", type=int, default=1152, help="bands of the hpsi512mix case")
     a = ap.parse_args()
     import numpy as np
     import torch
@@ -75,6 +77,16 @@ def main():
             pw.pw_apply_H(cell.h, x, y)
         torch.cuda.synchronize()
         print("hpsi512 done")
+    elif a.case == "hpsi512mix":
+        ci = synth.cell_inputs("Si", 4, 0)
+        cell = pw.Cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], 10.0, precision="mixed")
+        x = pw.new_block(cell.npw, a.nb)
+        x.copy_(torch.from_numpy(synth.draw_x0(0, 512, cell.npw, a.nb)))
+        y = pw.new_block(cell.npw, a.nb)
+        for _ in range(a.reps + 1):
+            pw.pw_apply_H(cell.h, x, y)
+        torch.cuda.synchronize()
+        print("hpsi512mix done")
     else:
         raise SystemExit(f"unknown case {a.case}")
 
