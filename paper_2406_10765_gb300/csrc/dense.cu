@@ -548,6 +548,7 @@ struct DcArrays {
   int *perm, *colK, *orig, *dcol, *src, *defl;
   int *knode;
   double *rhonode;
+  int *ctype, *qL, *qR, *kLR, *kneed;
 };
 
 // sort, z-vector, deflation and compaction for one node per CTA
@@ -574,6 +575,7 @@ __global__ void __launch_bounds__(256) k_dc_deflate(const int *nodes, int n, con
   }
   __syncthreads();
   double dmax = 0.0;
+  for (int c = lo + threadIdx.x; c < hi; c += blockDim.x) a.ctype[c] = c < mid ? 0 : 1;
   for (int p = threadIdx.x; p < size; p += blockDim.x) {
     const int li = a.perm[lo + p];
     const double Dv = a.lam[lo + li];
@@ -606,6 +608,7 @@ __global__ void __launch_bounds__(256) k_dc_deflate(const int *nodes, int n, con
             s_rot = 1;
             s_cj = lo + a.perm[lo + j];
             s_ci = lo + a.perm[lo + p];
+            if (a.ctype[s_cj] != a.ctype[s_ci]) a.ctype[s_cj] = a.ctype[s_ci] = 2;
             s_c = c;
             s_s = s;
             a.Ds[lo + j] = c * c * Dj + s * s * Dp;
@@ -646,6 +649,16 @@ __global__ void __launch_bounds__(256) k_dc_deflate(const int *nodes, int n, con
       }
     }
     a.knode[node] = rho2 > 0.0 ? t : 0;
+    // root columns the upper rows need (types 0, 2) and the lower rows (2, 1)
+    int nl = 0, nr = 0;
+    for (int q2 = 0; q2 < t; ++q2) {
+      const int ty = a.ctype[a.colK[lo + q2]];
+      if (ty != 1) a.qL[lo + nl++] = q2;
+      if (ty != 0) a.qR[lo + nr++] = q2;
+    }
+    a.kLR[2 * node] = nl;
+    a.kLR[2 * node + 1] = nr;
+    a.kneed[node] = 0;
     if (!(rho2 > 0.0)) {   // no coupling: everything deflates
       for (int p = 0; p < size; ++p) {
         a.dD[lo + p] = a.Ds[lo + p];
@@ -776,25 +789,34 @@ __global__ void __launch_bounds__(256) k_dc_vectors(const int *nodes, int n, DcA
   for (int i = lane; i < k; i += 32) Ucol[i] = inv * a.zh[lo + i] / ((D[i] - Do) - tau);
 }
 
-// W[rows, lo + t] = Z[rows, colK] U[:, t]  (node rows lo..hi-1)
+// W[rows, lo + t] = Z[rows, colK] U[:, t]  (node rows lo..hi-1).  Z is block
+// diagonal apart from the columns a deflating rotation mixed, so row tiles of
+// the upper half run over the root columns qL only, those of the lower half
+// over qR; only the roots t < kneed are formed.
 __global__ void __launch_bounds__(256) k_dc_gemm(const int *nodes, int n, DcArrays a) {
   const int node = blockIdx.z;
-  const int lo = nodes[3 * node], hi = nodes[3 * node + 2];
-  const int rows = hi - lo, k = a.knode[node];
-  const int r0 = blockIdx.x * 64, t0 = blockIdx.y * 64;
-  if (r0 >= rows || t0 >= k) return;
+  const int lo = nodes[3 * node], mid = nodes[3 * node + 1], hi = nodes[3 * node + 2];
+  const int tl = (mid - lo + 63) / 64;
+  const bool upper = (int)blockIdx.x < tl;
+  const int rbeg = upper ? lo + (int)blockIdx.x * 64 : mid + ((int)blockIdx.x - tl) * 64;
+  const int rend = upper ? mid : hi;
+  const int kneed = a.kneed[node];
+  const int t0 = blockIdx.y * 64;
+  if (rbeg >= rend || t0 >= kneed) return;
+  const int *ql = upper ? a.qL + lo : a.qR + lo;
+  const int kq = a.kLR[2 * node + (upper ? 0 : 1)];
   __shared__ double As[16][65], Bs[16][65];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   double acc[4][4] = {};
-  for (int k0 = 0; k0 < k; k0 += 16) {
+  for (int k0 = 0; k0 < kq; k0 += 16) {
     for (int e = threadIdx.x; e < 1024; e += 256) {
       const int r = e & 63, kk = e >> 6;
       double v = 0.0;
-      if (r0 + r < rows && k0 + kk < k) v = a.Z[(lo + r0 + r) + (long)a.colK[lo + k0 + kk] * n];
+      if (rbeg + r < rend && k0 + kk < kq) v = a.Z[(rbeg + r) + (long)a.colK[lo + ql[k0 + kk]] * n];
       As[kk][r] = v;
       const int kb = e & 15, tt = e >> 4;
       double u = 0.0;
-      if (k0 + kb < k && t0 + tt < k) u = a.U[(lo + k0 + kb) + (long)(lo + t0 + tt) * n];
+      if (k0 + kb < kq && t0 + tt < kneed) u = a.U[(lo + ql[k0 + kb]) + (long)(lo + t0 + tt) * n];
       Bs[kb][tt] = u;
     }
     __syncthreads();
@@ -814,13 +836,14 @@ __global__ void __launch_bounds__(256) k_dc_gemm(const int *nodes, int n, DcArra
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const int row = r0 + tx + 16 * q, t = t0 + ty + 16 * r;
-      if (row < rows && t < k) a.W[(lo + row) + (long)(lo + t) * n] = acc[q][r];
+      const int row = rbeg + tx + 16 * q, t = t0 + ty + 16 * r;
+      if (row < rend && t < kneed) a.W[row + (long)(lo + t) * n] = acc[q][r];
     }
 }
 
-// final order: rank of each (value, source index) among the node's eigenvalues
-__global__ void k_dc_rank(const int *nodes, DcArrays a) {
+// final order: rank of each (value, source index) among the node's eigenvalues;
+// kneed = roots among the `keep` lowest (the roots are in increasing order)
+__global__ void k_dc_rank(const int *nodes, DcArrays a, int keep) {
   const int node = blockIdx.y;
   const int lo = nodes[3 * node], hi = nodes[3 * node + 2];
   const int size = hi - lo, k = a.knode[node];
@@ -834,6 +857,7 @@ __global__ void k_dc_rank(const int *nodes, DcArrays a) {
   }
   a.lnew[lo + rank] = v;
   a.src[lo + rank] = lo + e;     // W column: roots at lo..lo+k-1, deflated copied after them
+  if (e < k && rank < keep) atomicMax(&a.kneed[node], e + 1);
 }
 
 // copy deflated columns of Z into W after the roots' columns
@@ -848,15 +872,16 @@ __global__ void k_dc_copy_defl(const int *nodes, int n, DcArrays a) {
   for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) dst[r] = src[r];
 }
 
-__global__ void k_dc_write(const int *nodes, int n, DcArrays a) {
+__global__ void k_dc_write(const int *nodes, int n, DcArrays a, int keep) {
   const int node = blockIdx.y;
   const int lo = nodes[3 * node], hi = nodes[3 * node + 2];
   const int p = blockIdx.x;
   if (p >= hi - lo) return;
+  if (threadIdx.x == 0) a.lam[lo + p] = a.lnew[lo + p];
+  if (p >= keep) return;   // every eigenvalue, only the kept vectors
   const double *src = a.W + (long)a.src[lo + p] * n;
   double *dst = a.Z + (long)(lo + p) * n;
   for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) dst[r] = src[r];
-  if (threadIdx.x == 0) a.lam[lo + p] = a.lnew[lo + p];
 }
 
 // ======================================================================
@@ -987,7 +1012,9 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
   for (int **q : ints) ok = ok && get((void **)q, nmax * 4);
   ok = ok && get((void **)&ws->nodes, (size_t)3 * nmax * 4 + 64) &&
        get((void **)&ws->knode, (size_t)nmax * 4 + 64) &&
-       get((void **)&ws->rhonode, (size_t)nmax * 8 + 64);
+       get((void **)&ws->rhonode, (size_t)nmax * 8 + 64) && get((void **)&ws->ctype, (size_t)nmax * 4) &&
+       get((void **)&ws->qL, (size_t)nmax * 4) && get((void **)&ws->qR, (size_t)nmax * 4) &&
+       get((void **)&ws->kLR, (size_t)nmax * 8 + 64) && get((void **)&ws->kneed, (size_t)nmax * 4 + 64);
   ok = ok && get((void **)&ws->ticket, 64) && get((void **)&ws->panel, (size_t)nmax * 3 * TPB * 16) &&
        get((void **)&ws->ucorr, 2 * TPB * 16) && get((void **)&ws->hscal, 16) &&
        get((void **)&ws->nrm_part, (size_t)(nmax / 32 + 2) * 8);
@@ -1012,7 +1039,8 @@ void pw_dense_free(pw_dense_ws *ws) {
   void *ptrs[] = {ws->G, ws->A, ws->T, ws->Linv, ws->Y, ws->dscale, ws->piv, ws->flag, ws->d, ws->e,
                   ws->lam, ws->tau, ws->p, ws->w, ws->part, ws->Z, ws->W, ws->U, ws->Ds, ws->zs,
                   ws->DK, ws->zK, ws->tauK, ws->zh, ws->lamK, ws->dD, ws->lnew, ws->perm, ws->colK,
-                  ws->orig, ws->dcol, ws->src, ws->nodes, ws->knode, ws->rhonode, ws->gemm_ws,
+                  ws->orig, ws->dcol, ws->src, ws->nodes, ws->knode, ws->rhonode, ws->ctype, ws->qL, ws->qR,
+                  ws->kLR, ws->kneed, ws->gemm_ws,
                   ws->Vb, ws->Gv, ws->Tb, ws->Wk, ws->Wk2, ws->ticket, ws->panel, ws->ucorr,
                   ws->hscal, ws->nrm_part};
   for (void *p : ptrs)
@@ -1079,7 +1107,8 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
   if (ws->tree_n != n) build_tree(ws, n);
   DcArrays a{lam, ws->Z, ws->W, ws->U, ws->Ds, ws->zs, ws->DK, ws->zK, ws->tauK, ws->zh,
              ws->lamK, ws->dD, ws->lnew, ws->perm, ws->colK, ws->orig, ws->dcol, ws->src,
-             (int *)ws->p /* defl scratch: n ints fit in n double2 */, ws->knode, ws->rhonode};
+             (int *)ws->p /* defl scratch: n ints fit in n double2 */, ws->knode, ws->rhonode,
+             ws->ctype, ws->qL, ws->qR, ws->kLR, ws->kneed};
   pw_count_launch();
   k_dc_init<<<(n + 255) / 256, 256, 0, st>>>(ws->d, ws->e, n, lam, ws->Z);
   pw_count_launch();
@@ -1098,14 +1127,16 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
     k_dc_zhat<<<gw, 256, 0, st>>>(nodes, a);
     pw_count_launch();
     k_dc_vectors<<<gw, 256, 0, st>>>(nodes, n, a);
+    // the root merge keeps only the nb lowest eigenpairs
+    const int keep = l == 0 ? nb : n;
     pw_count_launch();
-    k_dc_gemm<<<dim3((maxsize + 63) / 64, (maxsize + 63) / 64, nn), 256, 0, st>>>(nodes, n, a);
+    k_dc_rank<<<dim3((maxsize + 127) / 128, nn), 128, 0, st>>>(nodes, a, keep);
     pw_count_launch();
-    k_dc_rank<<<dim3((maxsize + 127) / 128, nn), 128, 0, st>>>(nodes, a);
+    k_dc_gemm<<<dim3((maxsize + 63) / 64 + 1, (maxsize + 63) / 64, nn), 256, 0, st>>>(nodes, n, a);
     pw_count_launch();
     k_dc_copy_defl<<<dim3(maxsize, nn), 128, 0, st>>>(nodes, n, a);
     pw_count_launch();
-    k_dc_write<<<dim3(maxsize, nn), 128, 0, st>>>(nodes, n, a);
+    k_dc_write<<<dim3(maxsize, nn), 128, 0, st>>>(nodes, n, a, keep);
   }
   PW_TRY(pw_check_launch("divide and conquer"));
 

@@ -21,6 +21,10 @@ struct pw_dense_ws {
   int *perm = nullptr, *colK = nullptr, *orig = nullptr, *dcol = nullptr, *src = nullptr;
   int *nodes = nullptr;       // per-level node tables (lo, mid, hi) for nmax
   int *knode = nullptr;       // per node: nondeflated count
+  // per column: which half of the node it is nonzero in (0 upper, 1 lower,
+  // 2 both after a deflating rotation); per node: the root columns each half
+  // of the merge product needs, their counts and the roots the caller keeps
+  int *ctype = nullptr, *qL = nullptr, *qR = nullptr, *kLR = nullptr, *kneed = nullptr;
   double *rhonode = nullptr;
   double2 *gemm_ws = nullptr; size_t gemm_ws_elems = 0;
   // blocked back-transformation: reflector panel, its Gram, T, two work blocks
