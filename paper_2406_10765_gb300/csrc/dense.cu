@@ -117,7 +117,8 @@ __global__ void k_copy_herm(const double2 *M, int ld, int n, double2 *out) {
 constexpr int CB = 32;   // Cholesky / inverse block
 
 // unblocked Cholesky of the diagonal block at j0 (size b <= 32), in place
-__global__ void k_potf2(double2 *A, int n, int j0, int b, double *piv, int *flag) {
+// Li (b x b, ld CB) = L11^-1 as well, for the row solves of the panel below
+__global__ void k_potf2(double2 *A, int n, int j0, int b, double *piv, int *flag, double2 *Li) {
   __shared__ double2 L[CB][CB + 1];
   __shared__ int bad;
   const int t = threadIdx.x;
@@ -154,30 +155,60 @@ __global__ void k_potf2(double2 *A, int n, int j0, int b, double *piv, int *flag
     if (i >= j) A[(j0 + i) + (long)(j0 + j) * n] = L[i][j];
   }
   if (t == 0 && bad) atomicOr(flag, 2);
+  // column j of L11^-1 by forward substitution
+  if (t < b) {
+    const int j = t;
+    double2 x[CB];
+#pragma unroll
+    for (int i = 0; i < CB; ++i) x[i] = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int i = 0; i < CB; ++i) {
+      if (i >= b || i < j) continue;
+      double2 s = (i == j) ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int l = 0; l < CB; ++l)
+        if (l >= j && l < i) s = csub(s, cmul(L[i][l], x[l]));
+      const double inv = 1.0 / L[i][i].x;
+      x[i] = make_double2(s.x * inv, s.y * inv);
+    }
+#pragma unroll
+    for (int i = 0; i < CB; ++i)
+      if (i < b) Li[i + j * CB] = x[i];
+  }
 }
 
-// rows i >= j0 + b:  A[i, j0:j0+b] <- A[i, j0:j0+b] L11^-H
-__global__ void k_trsm_rows(double2 *A, int n, int j0, int b) {
-  __shared__ double2 L[CB][CB + 1];
+// rows i >= j0 + b:  A[i, j0:j0+b] <- A[i, j0:j0+b] L11^-H, as products with
+// the inverse Li = L11^-1 from k_potf2: x_c = sum_{l <= c} a_l conj(Li[c][l]).
+// 16 rows per block, thread (row r, r + 8; column c), so every SM gets work.
+constexpr int TRSM_ROWS = 16;
+__global__ void __launch_bounds__(256) k_trsm_inv(double2 *A, int n, int j0, int b, const double2 *Li) {
+  __shared__ double2 Ls[CB][CB + 1], As[TRSM_ROWS][CB + 1];
+  const int r0 = j0 + b + blockIdx.x * TRSM_ROWS;
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int i = e % b, j = e / b;
-    L[i][j] = A[(j0 + i) + (long)(j0 + j) * n];
+    Ls[i][j] = Li[i + j * CB];
+  }
+  for (int e = threadIdx.x; e < TRSM_ROWS * b; e += blockDim.x) {
+    const int rr = e % TRSM_ROWS, c = e / TRSM_ROWS, i = r0 + rr;
+    As[rr][c] = i < n ? A[i + (long)(j0 + c) * n] : make_double2(0.0, 0.0);
   }
   __syncthreads();
-  const int i = j0 + b + blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double2 x[CB];
-  for (int c = 0; c < b; ++c) {
-    double2 a = A[i + (long)(j0 + c) * n];
-    for (int l = 0; l < c; ++l) {
-      // a -= x_l * conj(L[c][l])
-      const double2 lc = L[c][l];
-      a.x -= x[l].x * lc.x + x[l].y * lc.y;
-      a.y -= x[l].y * lc.x - x[l].x * lc.y;
+  const int c = threadIdx.x & 31, rq = threadIdx.x >> 5;
+  if (c >= b) return;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int rr = rq + 8 * h, i = r0 + rr;
+    if (i >= n) continue;
+    double2 x = make_double2(0.0, 0.0);
+    for (int l = 0; l <= c; ++l) {
+      const double2 a = As[rr][l], li = Ls[c][l];
+      // x += a conj(li)
+      x.x = fma(a.x, li.x, x.x);
+      x.x = fma(a.y, li.y, x.x);
+      x.y = fma(a.y, li.x, x.y);
+      x.y = fma(-a.x, li.y, x.y);
     }
-    const double inv = 1.0 / L[c][c].x;
-    x[c] = make_double2(a.x * inv, a.y * inv);
-    A[i + (long)(j0 + c) * n] = x[c];
+    A[i + (long)(j0 + c) * n] = x;
   }
 }
 
@@ -1016,7 +1047,7 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
        get((void **)&ws->qL, (size_t)nmax * 4) && get((void **)&ws->qR, (size_t)nmax * 4) &&
        get((void **)&ws->kLR, (size_t)nmax * 8 + 64) && get((void **)&ws->kneed, (size_t)nmax * 4 + 64);
   ok = ok && get((void **)&ws->ticket, 64) && get((void **)&ws->panel, (size_t)nmax * 3 * TPB * 16) &&
-       get((void **)&ws->ucorr, 2 * TPB * 16) && get((void **)&ws->hscal, 16) &&
+       get((void **)&ws->ucorr, 2 * TPB * 16) && get((void **)&ws->hscal, 16) && get((void **)&ws->Li, CB * CB * 16) &&
        get((void **)&ws->nrm_part, (size_t)(nmax / 32 + 2) * 8);
   ok = ok && get((void **)&ws->Vb, (size_t)nmax * BTB * 16) && get((void **)&ws->Gv, BTB * BTB * 16) &&
        get((void **)&ws->Tb, BTB * BTB * 16) && get((void **)&ws->Wk, (size_t)BTB * nbmax * 16) &&
@@ -1042,7 +1073,7 @@ void pw_dense_free(pw_dense_ws *ws) {
                   ws->orig, ws->dcol, ws->src, ws->nodes, ws->knode, ws->rhonode, ws->ctype, ws->qL, ws->qR,
                   ws->kLR, ws->kneed, ws->gemm_ws,
                   ws->Vb, ws->Gv, ws->Tb, ws->Wk, ws->Wk2, ws->ticket, ws->panel, ws->ucorr,
-                  ws->hscal, ws->nrm_part};
+                  ws->hscal, ws->nrm_part, ws->Li};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : ws->ev)
@@ -1179,11 +1210,11 @@ pw_status cholesky(pw_dense_ws *ws, double2 *A, int n, cudaStream_t st) {
   for (int j0 = 0; j0 < n; j0 += CB) {
     const int b = std::min(CB, n - j0);
     pw_count_launch();
-    k_potf2<<<1, 256, 0, st>>>(A, n, j0, b, ws->piv, ws->flag);
+    k_potf2<<<1, 256, 0, st>>>(A, n, j0, b, ws->piv, ws->flag, ws->Li);
     const int rest = n - j0 - b;
     if (rest > 0) {
       pw_count_launch();
-      k_trsm_rows<<<(rest + 127) / 128, 128, 0, st>>>(A, n, j0, b);
+      k_trsm_inv<<<(rest + TRSM_ROWS - 1) / TRSM_ROWS, 256, 0, st>>>(A, n, j0, b, ws->Li);
       // A22 -= L21 L21^H on the lower tiles only (the factorisation reads the
       // lower triangle; the upper one is cleared at the end)
       PW_TRY(pw_zgemm_ex('N', 'C', rest, rest, b, mone, A + (j0 + b) + (long)j0 * n, n,
@@ -1209,19 +1240,30 @@ pw_status trinv(pw_dense_ws *ws, const double2 *L, double2 *X, int n, cudaStream
   k_trinv_small<<<(unsigned)lo.size(), 32, 0, st>>>(L, X, n, dlo, dsz);
   PW_TRY(pw_check_launch("trinv_small"));
   // combine: [L11 0; L21 L22]^-1 = [X11 0; -X22 L21 X11, X22], bottom-up over
-  // block widths 32, 64, 128, ...
+  // block widths 32, 64, 128, ...; the pairs of one width go in one batched
+  // launch, and the triangular X11, X22 bound each tile's K range
   const double2 one = make_double2(1.0, 0.0), mone = make_double2(-1.0, 0.0),
                 zero = make_double2(0.0, 0.0);
+  const long dstep = (long)n + 1;
   for (int w = CB; w < n; w *= 2) {
-    for (int off = 0; off + w < n; off += 2 * w) {
-      const int h1 = w, h2 = std::min(w, n - off - w);
-      // T = L21 X11  (h2 x h1)
-      double2 *T = ws->T;
-      PW_TRY(pw_zgemm('N', 'N', h2, h1, h1, one, L + (off + h1) + (long)off * n, n,
-                      X + off + (long)off * n, n, zero, T, h2, ws->gemm_ws, ws->gemm_ws_elems, st));
-      // X21 = -X22 T
-      PW_TRY(pw_zgemm('N', 'N', h2, h1, h2, mone, X + (off + h1) + (long)(off + h1) * n, n, T, h2,
-                      zero, X + (off + h1) + (long)off * n, n, ws->gemm_ws, ws->gemm_ws_elems, st));
+    const int full = n / (2 * w);            // pairs of two complete w-blocks
+    double2 *T = ws->T;
+    if (full > 0) {
+      const long s2 = 2 * (long)w * dstep;   // from one pair's corner to the next
+      // T_p = L21 X11 (w x w, ld w)
+      PW_TRY(pw_zgemm_batched('N', 'N', w, w, w, one, L + w, n, s2, X, n, s2, zero, T, w, (long)w * w,
+                              full, st, 4));
+      // X21 = -X22 T_p
+      PW_TRY(pw_zgemm_batched('N', 'N', w, w, w, mone, X + w * dstep, n, s2, T, w, (long)w * w, zero,
+                              X + w, n, s2, full, st, 5));
+    }
+    const int off = full * 2 * w;
+    if (off + w < n) {                       // a last pair with a shorter second block
+      const int h1 = w, h2 = n - off - w;
+      PW_TRY(pw_zgemm_ex('N', 'N', h2, h1, h1, one, L + (off + h1) + (long)off * n, n, X + off * dstep, n,
+                         zero, T, h2, ws->gemm_ws, ws->gemm_ws_elems, st, 4));
+      PW_TRY(pw_zgemm_ex('N', 'N', h2, h1, h2, mone, X + (off + h1) * dstep, n, T, h2, zero,
+                         X + (off + h1) + (long)off * n, n, ws->gemm_ws, ws->gemm_ws_elems, st, 5));
     }
   }
   return PW_OK;

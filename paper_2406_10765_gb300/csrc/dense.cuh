@@ -33,6 +33,7 @@ struct pw_dense_ws {
   // blocked Householder reduction: panel [V | W | V] (nmax x 3*32), partial
   // norms of a column, the panel correction dots
   double2 *panel = nullptr, *ucorr = nullptr, *hscal = nullptr;
+  double2 *Li = nullptr;      // inverse of the current Cholesky diagonal block (CB x CB)
   double *nrm_part = nullptr;
   // host side tree for the current n
   int tree_n = -1;

@@ -106,17 +106,26 @@ __global__ void __launch_bounds__(256) k_stats(const double2 *X, const double2 *
 }
 
 // W[:, a] = K(kin / E_kin(j)) (HX_j - lam_j X_j), j = act[a]
+// f32k: the preconditioner factor in FP32 (mixed precision; it only shapes the
+// search direction, and FP64 divisions are scarce on this part)
 __global__ void k_precond(const double2 *X, const double2 *HX, int ld, int npw, const double *lam,
                           const double *kin, const double *stats, int nb, const int *act, int k,
-                          double2 *W) {
+                          double2 *W, int f32k) {
   const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (idx >= (long)npw * k) return;
   const int g = (int)(idx % npw), a = (int)(idx / npw);
   const int j = act[a];
-  const double ek = stats[nb + j] / stats[2 * nb + j];
-  const double x = kin[g] / ek;
-  const double p = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
-  const double K = p / (p + 16.0 * x * x * x * x);
+  double K;
+  if (f32k) {
+    const float x = (float)kin[g] * ((float)stats[2 * nb + j] / (float)stats[nb + j]);
+    const float p = 27.0f + x * (18.0f + x * (12.0f + 8.0f * x));
+    K = (double)(p / (p + 16.0f * x * x * x * x));
+  } else {
+    const double ek = stats[nb + j] / stats[2 * nb + j];
+    const double x = kin[g] / ek;
+    const double p = 27.0 + x * (18.0 + x * (12.0 + 8.0 * x));
+    K = p / (p + 16.0 * x * x * x * x);
+  }
   const double2 xv = X[g + (long)j * ld], h = HX[g + (long)j * ld];
   const double l = lam[j];
   W[g + (long)a * ld] = make_double2(K * (h.x - l * xv.x), K * (h.y - l * xv.y));
@@ -483,7 +492,7 @@ extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_repor
   double2 *W = s->S + (size_t)nb * npw, *HW = s->HS + (size_t)nb * npw;
   pw_count_launch();
   k_precond<<<(unsigned)(((long)npw * k + 255) / 256), 256, 0, s->st>>>(
-      s->S, s->HS, npw, npw, s->lam, cell->d_kin, s->stats, nb, s->act, k, W);
+      s->S, s->HS, npw, npw, s->lam, cell->d_kin, s->stats, nb, s->act, k, W, s->precision == PW_MIXED);
   // unit columns: the Rayleigh-Ritz is invariant to column scaling, and the
   // split-precision operands need W on the scale of X
   pw_count_launch();

@@ -123,10 +123,17 @@ size_t pw_zgemm_ws_elems(int m, int n, int k);
 // upper-triangle tiles are computed, then mirrored.  herm = 2: only the tiles
 // on and below the diagonal are computed (the caller keeps a lower triangle).
 // herm = 3: op(A) is upper triangular (explicit zeros below the diagonal), so
-// each row tile skips the K range left of its first row.
+// each row tile skips the K range left of its first row; herm = 4: op(B) is
+// lower triangular (column tiles skip K below their first column); herm = 5:
+// op(A) is lower triangular (row tiles stop K after their last row).
 pw_status pw_zgemm_ex(char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
                       int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc,
                       double2 *ws, size_t ws_elems, cudaStream_t st, int herm);
+// batch independent products, operand i at A + i sA, B + i sB, C + i sC
+// (element strides); mode as herm above except 1 (no mirror pass)
+pw_status pw_zgemm_batched(char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
+                           int lda, long sA, const double2 *B, int ldb, long sB, double2 beta,
+                           double2 *C, int ldc, long sC, int batch, cudaStream_t st, int mode);
 // C (n x n) = A^H B, Hermitian result (upper tiles + mirror)
 pw_status pw_zgemm_herm(int n, int k, const double2 *A, int lda, const double2 *B, int ldb,
                         double2 *C, int ldc, double2 *ws, size_t ws_elems, cudaStream_t st);

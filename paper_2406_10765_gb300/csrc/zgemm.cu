@@ -23,26 +23,38 @@ __global__ void __launch_bounds__(256) k_zgemm(int m, int n, int k, int kchunk, 
                                                const double2 *__restrict__ A, int lda,
                                                const double2 *__restrict__ B, int ldb,
                                                double2 beta, double2 *__restrict__ C, int ldc,
-                                               double2 *__restrict__ ws, int herm) {
-  // Hermitian products: tiles strictly below the diagonal are mirrored later
+                                               double2 *__restrict__ ws, int herm, long sA, long sB,
+                                               long sC) {
   // herm 1: upper-triangle tiles (mirrored later); herm 2: lower-triangle tiles only
   if (herm == 1 && blockIdx.y < blockIdx.x) return;
   if (herm == 2 && blockIdx.y > blockIdx.x) return;
+  // batched: blockIdx.z picks the problem (operands at multiples of the strides)
+  const bool batched = (sA | sB | sC) != 0;
+  if (batched) {
+    A += blockIdx.z * sA;
+    B += blockIdx.z * sB;
+    C += blockIdx.z * sC;
+  }
   __shared__ double2 As[BK][BM + 1];
   __shared__ double2 Bs[BK][BN + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int kb = blockIdx.z * kchunk;
-  const int ke = min(k, kb + kchunk);
-  // herm 3: op(A) upper triangular, so rows m0.. need K from m0 on only
-  const int ks = herm == 3 ? max(kb, m0 - m0 % BK) : kb;
+  const int kb = batched ? 0 : blockIdx.z * kchunk;
+  const int ke = batched ? k : min(k, kb + kchunk);
+  // triangular operands (explicit zeros) bound the K range of a tile:
+  // herm 3: op(A) upper, rows m0.. need K >= m0; herm 4: op(B) lower,
+  // columns n0.. need K >= n0; herm 5: op(A) lower, rows < m0 + BM need K < m0 + BM
+  int ks = kb, kl = ke;
+  if (herm == 3) ks = max(kb, m0 - m0 % BK);
+  if (herm == 4) ks = max(kb, n0 - n0 % BK);
+  if (herm == 5) kl = min(ke, m0 + BM);
   double2 acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
 
-  for (int k0 = ks; k0 < ke; k0 += BK) {
+  for (int k0 = ks; k0 < kl; k0 += BK) {
     // A tile: op(A)(mm, kk), 64 x 8 = 512 elements, 2 per thread
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -90,7 +102,7 @@ __global__ void __launch_bounds__(256) k_zgemm(int m, int n, int k, int kchunk, 
     }
     __syncthreads();
   }
-  const bool split = gridDim.z > 1;
+  const bool split = !batched && gridDim.z > 1;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -177,7 +189,8 @@ pw_status pw_zgemm_ex(char opA, char opB, int m, int n, int k, double2 alpha, co
   kchunk = ((kchunk + BK - 1) / BK) * BK;
   splits = (k + kchunk - 1) / kchunk;
   dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN, splits);
-#define L(a, b) k_zgemm<a, b><<<grid, 256, 0, st>>>(m, n, k, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, ws, herm)
+#define L(a, b) k_zgemm<a, b><<<grid, 256, 0, st>>>(m, n, k, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, ws, herm, \
+                                                   0L, 0L, 0L)
   pw_count_launch();
   if (opA == 'N' && opB == 'N') L('N', 'N');
   else if (opA == 'C' && opB == 'N') L('C', 'N');
@@ -196,4 +209,22 @@ pw_status pw_zgemm_ex(char opA, char opB, int m, int n, int k, double2 alpha, co
     k_zmirror<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 32), 0, st>>>(C, ldc, m);
   }
   return pw_check_launch("zgemm");
+}
+
+pw_status pw_zgemm_batched(char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
+                           int lda, long sA, const double2 *B, int ldb, long sB, double2 beta,
+                           double2 *C, int ldc, long sC, int batch, cudaStream_t st, int mode) {
+  if (m <= 0 || n <= 0 || batch <= 0) return PW_OK;
+  if (k <= 0 || (sA | sB | sC) == 0 || mode == 1) return PW_ERR_ARG;
+  dim3 grid((m + BM - 1) / BM, (n + BN - 1) / BN, batch);
+#define L(a, b) k_zgemm<a, b><<<grid, 256, 0, st>>>(m, n, k, k, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, \
+                                                   mode, sA, sB, sC)
+  pw_count_launch();
+  if (opA == 'N' && opB == 'N') L('N', 'N');
+  else if (opA == 'C' && opB == 'N') L('C', 'N');
+  else if (opA == 'N' && opB == 'C') L('N', 'C');
+  else if (opA == 'C' && opB == 'C') L('C', 'C');
+  else return PW_ERR_ARG;
+#undef L
+  return pw_check_launch("zgemm batched");
 }
