@@ -292,6 +292,29 @@ __global__ void k_scale_rows_real(double2 *C, int ld, int n, int nb, const doubl
 // ----------------------------------------------------------------------
 constexpr int TT = 32;
 constexpr int TPB = 32;
+
+// The per-column kernels are chained with programmatic dependent launch: a
+// kernel may start while its predecessor finishes, waits (griddepcontrol.wait)
+// before it reads anything the predecessor wrote, and only then lets its own
+// successor launch.  So before its wait a kernel may read data written two or
+// more launches back (k_phemv loads its tile of the trailing matrix there).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
 constexpr int PCOL_THREADS = 128;
 
 // s += a b and s += conj(a) b, four FMAs each
@@ -335,6 +358,8 @@ __global__ void __launch_bounds__(PCOL_THREADS) k_pcol(double2 *A, int n, int c,
   __shared__ double sh[32];
   __shared__ unsigned s_ticket;
   __shared__ double2 s_vc[TPB], s_wc[TPB], s_u[4][33];
+  pdl_wait();
+  pdl_trigger();
   double2 *V = P, *W = P + (long)b * n;
   double2 al = make_double2(0.0, 0.0);
   if (i > 0) al = panel_alpha(dotpart, ndot, tau[c - 1], sh);
@@ -423,8 +448,31 @@ __global__ void __launch_bounds__(256) k_phemv(const double2 *A, int n, int c, i
   __shared__ double sh[32];
   const int o = c + 1, m = n - o;
   const double2 *xk = A + o + (long)c * n;   // x of column c, x[0] at row o
-  const double2 scal = *hscal;
   const int blk = blockIdx.x;
+  int I = 0, J = 0, x0 = 0, y0 = 0;
+  if (blk < ntiles) {
+    // tile (I, J) of the lower triangle; FP32 estimate (FP64 is scarce), fixed up exactly
+    const int t = blk;
+    I = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    while (I * (I + 1) / 2 > t) --I;
+    J = t - I * (I + 1) / 2;
+    x0 = TT * I;
+    y0 = TT * J;   // tile rows x0.., columns y0.. (offsets from o)
+    // the trailing matrix was last written before the predecessor's wait: load it now
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int yc = y0 + lane;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int rl = wq * 4 + q, xr = x0 + rl;
+      double2 a = make_double2(0.0, 0.0);
+      if (xr < m && yc < m && (I != J || yc <= xr)) a = A[(o + xr) + (long)(o + yc) * n];
+      tile[rl][lane] = a;
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
+  const double2 scal = *hscal;
   if (blk >= ntiles + 2 * i) {   // writer blocks
     const int x = (blk - ntiles - 2 * i) * blockDim.x + threadIdx.x;
     if (x < m) {
@@ -444,26 +492,10 @@ __global__ void __launch_bounds__(256) k_phemv(const double2 *A, int n, int c, i
     if (threadIdx.x == 0) ucorr[q2] = s;
     return;
   }
-  const int t = blk;
-  // tile (I, J) of the lower triangle; FP32 estimate (FP64 is scarce), fixed up exactly
-  int I = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-  while ((I + 1) * (I + 2) / 2 <= t) ++I;
-  while (I * (I + 1) / 2 > t) --I;
-  const int J = t - I * (I + 1) / 2;
-  const int x0 = TT * I, y0 = TT * J;   // tile rows x0.., columns y0.. (offsets from o)
   if (threadIdx.x < TT) {
     const int xr = x0 + threadIdx.x, yc = y0 + threadIdx.x;
     vrow[threadIdx.x] = xr < m ? refl_entry(xk, xr, scal) : make_double2(0.0, 0.0);
     vcol[threadIdx.x] = yc < m ? refl_entry(xk, yc, scal) : make_double2(0.0, 0.0);
-  }
-  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-  const int yc = y0 + lane;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int rl = wq * 4 + q, xr = x0 + rl;
-    double2 a = make_double2(0.0, 0.0);
-    if (xr < m && yc < m && (I != J || yc <= xr)) a = A[(o + xr) + (long)(o + yc) * n];
-    tile[rl][lane] = a;
   }
   __syncthreads();
   // warps 0-3: quarter row sums A v; warps 4-7: quarter column sums A^H v
@@ -504,6 +536,8 @@ __global__ void __launch_bounds__(256) k_prows(double2 *A, int n, int c, int i, 
                                                const double2 *tau, const double2 *hscal, double2 *p,
                                                double2 *dotpart) {
   __shared__ double2 red[8][33];
+  pdl_wait();
+  pdl_trigger();
   const int o = c + 1, m = n - o;
   const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int x = blockIdx.x * 32 + rl;
@@ -540,6 +574,8 @@ __global__ void __launch_bounds__(256) k_pfinal(const double2 *A, int n, int c, 
                                                 const double2 *p, const double2 *dotpart, int ndot,
                                                 const double2 *tau) {
   __shared__ double sh[32];
+  pdl_wait();
+  pdl_trigger();
   const double2 al = panel_alpha(dotpart, ndot, tau[c], sh);
   const int o = c + 1;
   const int r = o + blockIdx.x * blockDim.x + threadIdx.x;
@@ -1107,22 +1143,23 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
       for (int i = 0; i < b; ++i) {
         const int c = j0 + i, m = n - c - 1;
         pw_count_launch();
-        k_pcol<<<(n - c + 31) / 32, PCOL_THREADS, 0, st>>>(
-            A, n, c, i, ws->panel, b, ws->p, dotpart, ndot, ws->tau, ws->d, ws->e, ws->nrm_part, ws->hscal,
-            ws->ticket);
+        PW_CUDA(launch_pdl(k_pcol, (n - c + 31) / 32, PCOL_THREADS, st, A, n, c, i, ws->panel, b,
+                           (const double2 *)ws->p, (const double2 *)dotpart, ndot, ws->tau, ws->d, ws->e,
+                           ws->nrm_part, ws->hscal, ws->ticket));
         const int nT = (m + TT - 1) / TT, ntiles = nT * (nT + 1) / 2, nwr = (m + 255) / 256;
         pw_count_launch();
-        k_phemv<<<ntiles + 2 * i + nwr, 256, 0, st>>>(A, n, c, i, ws->panel, b, ntiles, ws->part, ws->nmax,
-                                                      ws->ucorr, ws->hscal);
+        PW_CUDA(launch_pdl(k_phemv, ntiles + 2 * i + nwr, 256, st, (const double2 *)A, n, c, i, ws->panel,
+                           b, ntiles, ws->part, ws->nmax, ws->ucorr, (const double2 *)ws->hscal));
         ndot = (m + 31) / 32;
         pw_count_launch();
-        k_prows<<<ndot, 256, 0, st>>>(A, n, c, i, ws->panel, b, ws->part, nT, ws->nmax, ws->ucorr, ws->tau,
-                                      ws->hscal, ws->p, dotpart);
+        PW_CUDA(launch_pdl(k_prows, ndot, 256, st, A, n, c, i, (const double2 *)ws->panel, b,
+                           (const double2 *)ws->part, nT, ws->nmax, (const double2 *)ws->ucorr,
+                           (const double2 *)ws->tau, (const double2 *)ws->hscal, ws->p, dotpart));
       }
       const int cl = j0 + b - 1, ml = n - cl - 1;
       pw_count_launch();
-      k_pfinal<<<(ml + 255) / 256, 256, 0, st>>>(A, n, cl, b - 1, ws->panel, b, ws->p, dotpart, ndot,
-                                                 ws->tau);
+      PW_CUDA(launch_pdl(k_pfinal, (ml + 255) / 256, 256, st, (const double2 *)A, n, cl, b - 1, ws->panel, b,
+                         (const double2 *)ws->p, (const double2 *)dotpart, ndot, (const double2 *)ws->tau));
       const int t = j0 + b, m2 = n - t;
       if (m2 > 0)
         PW_TRY(pw_zgemm_ex('N', 'C', m2, m2, 2 * b, mone, ws->panel + t, n, ws->panel + (long)b * n + t,
