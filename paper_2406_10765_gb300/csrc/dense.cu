@@ -155,25 +155,32 @@ __global__ void k_potf2(double2 *A, int n, int j0, int b, double *piv, int *flag
     if (i >= j) A[(j0 + i) + (long)(j0 + j) * n] = L[i][j];
   }
   if (t == 0 && bad) atomicOr(flag, 2);
-  // column j of L11^-1 by forward substitution
-  if (t < b) {
-    const int j = t;
-    double2 x[CB];
-#pragma unroll
-    for (int i = 0; i < CB; ++i) x[i] = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int i = 0; i < CB; ++i) {
-      if (i >= b || i < j) continue;
-      double2 s = (i == j) ? make_double2(1.0, 0.0) : make_double2(0.0, 0.0);
-#pragma unroll
-      for (int l = 0; l < CB; ++l)
-        if (l >= j && l < i) s = csub(s, cmul(L[i][l], x[l]));
-      const double inv = 1.0 / L[i][i].x;
-      x[i] = make_double2(s.x * inv, s.y * inv);
+  // L11^-1 by row elimination of [L11 | I]: step l scales row l by 1/L_ll and
+  // removes L_il (i > l) from the rows below; only the original L entries are
+  // read, and each step's updates are spread over the whole block
+  __shared__ double2 X[CB][CB + 1];
+  for (int e = t; e < b * b; e += blockDim.x) {
+    const int i = e % b, j = e / b;
+    X[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int l = 0; l < b; ++l) {
+    if (t <= l) {
+      const double inv = 1.0 / L[l][l].x;
+      X[l][t].x *= inv;
+      X[l][t].y *= inv;
     }
-#pragma unroll
-    for (int i = 0; i < CB; ++i)
-      if (i < b) Li[i + j * CB] = x[i];
+    __syncthreads();
+    const int cnt = (b - 1 - l) * (l + 1);
+    for (int e = t; e < cnt; e += blockDim.x) {
+      const int i = l + 1 + e / (l + 1), j = e % (l + 1);
+      X[i][j] = csub(X[i][j], cmul(L[i][l], X[l][j]));
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < b * b; e += blockDim.x) {
+    const int i = e % b, j = e / b;
+    Li[i + j * CB] = X[i][j];
   }
 }
 
