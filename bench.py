@@ -32,6 +32,9 @@ WORKLOADS = {
                 name="Si-8 (diamond cell, a=10.26 bohr), Gamma, Ecut=10 Ha"),
 }
 E2E_TOL, E2E_MAXIT = 5e-6, 20
+# DRAM bytes (read + write) of one instance of a sub-stage, from one ncu
+# capture of the same kernels: (stage, n, nb) -> (bytes, summary)
+NCU_TRAFFIC = {("tridiag", 3456, 1152): (131.1e9, "profiles/householder_tridiag_n3456.md")}
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of the part (no FP64 tensor path)
 METRIC = "Si-512 eigensolver iters/s"
 
@@ -140,8 +143,10 @@ def roofline(stage, rr_part, fl, n, nb, precision):
     peaks = measured_peaks()
     if dom in fp64:
         ach = fp64[dom] / (t_ms * 1e-3) / 1e12
+        tr = NCU_TRAFFIC.get((dom, n, nb)) if not mixed or dom != "transform" else None
         roof.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                    frac=ach / FP64_PEAK_TFLOPS, traffic=None,
+                    frac=ach / FP64_PEAK_TFLOPS, traffic=tr[0] if tr else None,
+                    traffic_source=tr[1] if tr else None,
                     peak_source="nominal FP64 rate: 152 SMs x 2.07 GHz x 2 DFMA/clk (measured DFMA 1.20)")
     elif dom in ("gram", "rot"):
         ach = fl[dom] / (t_ms * 1e-3) / 1e12
