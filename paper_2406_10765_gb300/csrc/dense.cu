@@ -775,10 +775,11 @@ __global__ void __launch_bounds__(256) k_dc_roots(const int *nodes, DcArrays a) 
   for (int it = 0; it < 100; ++it) {
     double psi = 0.0, dpsi = 0.0, phi = 0.0, dphi = 0.0;
     for (int i = lane; i < k; i += 32) {
-      const double diff = (D[i] - Do) - tau;
-      const double term = z[i] * z[i] / diff;
-      if (i <= t) { psi += term; dpsi += term / diff; }
-      else { phi += term; dphi += term / diff; }
+      // one reciprocal per term (FP64 divisions are the costly part here)
+      const double r = __drcp_rn((D[i] - Do) - tau);
+      const double term = z[i] * z[i] * r;
+      if (i <= t) { psi += term; dpsi = fma(term, r, dpsi); }
+      else { phi += term; dphi = fma(term, r, dphi); }
     }
     psi = rho * warp_sum(psi);
     dpsi = rho * warp_sum(dpsi);
@@ -1415,6 +1416,23 @@ pw_status pw_rr_factor(pw_dense_ws *ws, int n, const double2 *G, int ldg, double
   k_make_M<<<g2, b2, 0, st>>>(ws->Linv, n, ws->dscale, M, ldm);
   cudaEventRecord(ws->ev[1], st);
   return pw_check_launch("rr_factor");
+}
+
+pw_status pw_rr_finish_tall(pw_dense_ws *ws, int n, int nb, const double2 *At, int lda, const double2 *M,
+                            int ldm, double *theta, double2 *Cp, int ldc, cudaStream_t st) {
+  if (n > ws->nmax || nb > ws->nbmax || nb > n) return PW_ERR_ARG;
+  pw_count_launch();
+  const dim3 g2((n + 31) / 32, (n + 31) / 32), b2(32, 32);
+  k_copy_herm<<<g2, b2, 0, st>>>(At, lda, n, ws->A);
+  PW_TRY(pw_heev_lowest(ws, n, nb, ws->A, ws->lam, ws->Y, st));
+  PW_CUDA(cudaMemcpyAsync(theta, ws->lam, nb * 8, cudaMemcpyDeviceToDevice, st));
+  PW_CUDA(cudaMemset2DAsync(Cp, (size_t)ldc * 16, 0, (size_t)nb * 16, nb, st));
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  if (n > nb)
+    PW_TRY(pw_zgemm_ex('N', 'N', n - nb, nb, n - nb, one, M + nb + (long)nb * ldm, ldm, ws->Y + nb, n,
+                       zero, Cp + nb, ldc, ws->gemm_ws, ws->gemm_ws_elems, st, 3));
+  cudaEventRecord(ws->ev[5], st);
+  return pw_check_launch("rr_finish_tall");
 }
 
 pw_status pw_rr_finish(pw_dense_ws *ws, int n, int nb, const double2 *At, int lda, const double2 *M,

@@ -71,6 +71,12 @@ pw_status pw_rr_factor(pw_dense_ws *ws, int n, const double2 *G, int ldg, double
                        int *chol_ok, cudaStream_t st, double piv_tol);
 pw_status pw_rr_finish(pw_dense_ws *ws, int n, int nb, const double2 *At, int lda, const double2 *M,
                        int ldm, double *theta, double2 *C, int ldc, cudaStream_t st);
+// Variant for callers that hold the orthonormalised basis S~ = S M: leaves
+// the eigenvectors Y (n x nb, ld n) in ws->Y for X' = S~ Y and forms only
+// the rows nb..n-1 of C = M Y (= M[nb:, nb:] Y[nb:], M upper triangular) in
+// Cp, whose rows 0..nb-1 are set to zero: P' = S Cp.
+pw_status pw_rr_finish_tall(pw_dense_ws *ws, int n, int nb, const double2 *At, int lda, const double2 *M,
+                            int ldm, double *theta, double2 *Cp, int ldc, cudaStream_t st);
 
 // Hermitian eigensolver: lowest nb eigenpairs of the n x n matrix A (device,
 // destroyed).  lam: device n doubles (all eigenvalues, ascending); Y: device

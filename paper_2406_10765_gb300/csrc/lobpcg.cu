@@ -55,6 +55,9 @@ struct pw_solver {
   // carrying H X and H P through the rotations (their split-precision errors
   // would be amplified by ill-conditioned coefficients near convergence)
   bool fresh_h = false;
+  // mixed precision with fresh H: the Rayleigh-Ritz left Y in the dense
+  // workspace and S~ = S M in S2, and the rotation writes X' = S~ Y to HS2
+  bool ytilde = false, x_in_hs2 = false;
   bool hx_valid = true;    // HS[:, 0:nb] == H X for the current X
 };
 
@@ -251,6 +254,11 @@ pw_status rr_mixed_from_gram(pw_solver *s, int ns, int *chol_ok) {
   PW_TRY(pw_tc_split_rows(s->S2, npw, npw, ns, 1, nullptr, &s->opSA, s->st));
   PW_TRY(pw_tc_split_rows(s->HS2, npw, npw, ns, 0, nullptr, &s->opHSB, s->st));
   PW_TRY(pw_tc_gemm(&s->opSA, 2 * ns, &s->opHSB, ns, s->A, ldg, 0, 0, 1, s->d_err, s->st));
+  if (s->fresh_h) {
+    // X' = S~ Y on the tensor cores; only the P part of C = M Y in FP64
+    s->ytilde = true;
+    return pw_rr_finish_tall(&s->dws, ns, nb, s->A, ldg, s->Mx, ldg, s->theta, s->C, ldg, s->st);
+  }
   return pw_rr_finish(&s->dws, ns, nb, s->A, ldg, s->Mx, ldg, s->theta, s->C, ldg, s->st);
 }
 
@@ -292,10 +300,39 @@ __global__ void k_zero_top_rows(const double2 *C, int ld, int nrows_zero, int nr
   out[t + (long)j * ld] = t < nrows_zero ? make_double2(0.0, 0.0) : C[t + (long)j * ld];
 }
 
+// after a rotation the new block becomes S (and HS): X' sits in S2 (H X' in
+// HS2), or, after the tensor-core S~ Y rotation, in HS2
+void swap_rotated(pw_solver *s) {
+  if (s->x_in_hs2) {
+    std::swap(s->S, s->HS2);
+    s->x_in_hs2 = false;
+  } else {
+    std::swap(s->S, s->S2);
+    std::swap(s->HS, s->HS2);
+  }
+}
+
 // X' = S C and H X' = HS C into S2, HS2; with_p: P' = S C_P, HP' = HS C_P
 // where C_P is C with its first nb rows zeroed (the [0, W, P] combination)
 pw_status rotate(pw_solver *s, int ns, bool with_p) {
   const int npw = s->npw, nb = s->nb, n3 = 3 * nb;
+  if (s->precision == PW_MIXED && s->ytilde) {
+    s->ytilde = false;
+    PW_TRY(pw_tc_operand_alloc(&s->opC, 2 * nb, 2 * ns, s->st));
+    if (with_p) {
+      // P' = S C_P, C_P = C with its first nb rows zero (opST: the split of S)
+      PW_TRY(pw_tc_operand_alloc(&s->opCP, 2 * nb, 2 * ns, s->st));
+      PW_TRY(pw_tc_split_coef(s->C, n3, ns, nb, nullptr, &s->opCP, s->st));
+      PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opCP, 2 * nb, s->P, npw, 1, 0, 0, s->d_err, s->st));
+    }
+    // X' = S~ Y into HS2 (H S~ is no longer needed), S~ re-split over opST
+    PW_TRY(pw_tc_split_trans(s->S2, npw, npw, ns, s->rmax, &s->opST, s->st));
+    s->st_split_valid = false;
+    PW_TRY(pw_tc_split_coef(s->dws.Y, ns, ns, nb, nullptr, &s->opC, s->st));
+    PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opC, 2 * nb, s->HS2, npw, 1, 0, 0, s->d_err, s->st));
+    s->x_in_hs2 = true;
+    return PW_OK;
+  }
   if (s->precision == PW_MIXED) {
     PW_TRY(pw_tc_operand_alloc(&s->opST, npw, 2 * ns, s->st));
     PW_TRY(pw_tc_operand_alloc(&s->opHST, npw, 2 * ns, s->st));
@@ -456,8 +493,7 @@ extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, voi
   }
   if (!ok) { pw_solver_destroy(s); return PW_ERR_CHOL; }
   if ((r = rotate(s, nb, false)) || (r = check_tc_err(s))) { pw_solver_destroy(s); return r; }
-  std::swap(s->S, s->S2);
-  std::swap(s->HS, s->HS2);
+  swap_rotated(s);
   s->hx_valid = !s->fresh_h;
   s->st_split_valid = false;
   cudaMemcpyAsync(s->lam, s->theta, nb * 8, cudaMemcpyDeviceToDevice, s->st);
@@ -540,8 +576,7 @@ extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_repor
   k_normalize_cols<<<nb, 256, 0, s->st>>>(s->P, s->HP, npw, npw);
   PW_TRY(pw_check_launch("normalize P"));
   cudaEventRecord(s->ev[6], s->st);
-  std::swap(s->S, s->S2);
-  std::swap(s->HS, s->HS2);
+  swap_rotated(s);
   s->hx_valid = !s->fresh_h;
   s->st_split_valid = false;
   PW_CUDA(cudaMemcpyAsync(s->lam, s->theta, nb * 8, cudaMemcpyDeviceToDevice, s->st));
@@ -589,8 +624,7 @@ extern "C" pw_status pw_solver_polish(pw_solver *s) {
   if (r == PW_OK) r = rotate(s, nb, false);
   s->precision = saved;
   PW_TRY(r);
-  std::swap(s->S, s->S2);
-  std::swap(s->HS, s->HS2);
+  swap_rotated(s);
   s->hx_valid = true;
   PW_CUDA(cudaMemcpyAsync(s->lam, s->theta, nb * 8, cudaMemcpyDeviceToDevice, s->st));
   PW_CUDA(cudaStreamSynchronize(s->st));
