@@ -249,8 +249,9 @@ pw_status rr_mixed_from_gram(pw_solver *s, int ns, int *chol_ok) {
   s->st_split_valid = true;
   PW_TRY(pw_tc_split_trans(s->HS, npw, npw, ns, s->rmax, &s->opHST, s->st));
   PW_TRY(pw_tc_split_coef(s->Mx, ldg, ns, ns, nullptr, &s->opM, s->st));
-  PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opM, 2 * ns, s->S2, npw, 1, 0, 0, s->d_err, s->st));
-  PW_TRY(pw_tc_gemm(&s->opHST, npw, &s->opM, 2 * ns, s->HS2, npw, 1, 0, 0, s->d_err, s->st));
+  // M is upper triangular: output columns j need K rows t <= j only
+  PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opM, 2 * ns, s->S2, npw, 1, 0, 0, s->d_err, s->st, 0, 1));
+  PW_TRY(pw_tc_gemm(&s->opHST, npw, &s->opM, 2 * ns, s->HS2, npw, 1, 0, 0, s->d_err, s->st, 0, 1));
   PW_TRY(pw_tc_split_rows(s->S2, npw, npw, ns, 1, nullptr, &s->opSA, s->st));
   PW_TRY(pw_tc_split_rows(s->HS2, npw, npw, ns, 0, nullptr, &s->opHSB, s->st));
   PW_TRY(pw_tc_gemm(&s->opSA, 2 * ns, &s->opHSB, ns, s->A, ldg, 0, 0, 1, s->d_err, s->st));
@@ -323,7 +324,9 @@ pw_status rotate(pw_solver *s, int ns, bool with_p) {
       // P' = S C_P, C_P = C with its first nb rows zero (opST: the split of S)
       PW_TRY(pw_tc_operand_alloc(&s->opCP, 2 * nb, 2 * ns, s->st));
       PW_TRY(pw_tc_split_coef(s->C, n3, ns, nb, nullptr, &s->opCP, s->st));
-      PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opCP, 2 * nb, s->P, npw, 1, 0, 0, s->d_err, s->st));
+      // the first nb coefficient rows are zero: skip their K blocks
+      PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opCP, 2 * nb, s->P, npw, 1, 0, 0, s->d_err, s->st,
+                        (2 * nb) / 64));
     }
     // X' = S~ Y into HS2 (H S~ is no longer needed), S~ re-split over opST
     PW_TRY(pw_tc_split_trans(s->S2, npw, npw, ns, s->rmax, &s->opST, s->st));

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               int a_slice_rows, int b_slice_rows, int m, int n, int kblocks, int mtiles,
               int ntiles, const float *__restrict__ inv_sa, const float *__restrict__ inv_sb,
               double2 *__restrict__ C, int ldc, int mode, int accumulate, int herm_skip,
-              int *__restrict__ err) {
+              int kb_lo, int tri_b, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + NSTAGE * STAGE);
@@ -223,6 +223,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   // Hermitian products: skip tiles strictly below the diagonal (rows are
   // interleaved re/im pairs of output row i = r / 2)
   if (herm_skip && n0 + BN - 1 < m0 / 2) return;
+  // K blocks of this tile: kb_lo.. (B zero below), and with tri_b (B rows
+  // from an upper-triangular coefficient matrix) only K < n0 + BN is nonzero
+  const int kb_beg = kb_lo;
+  const int kb_end = tri_b ? min(kblocks, (n0 + BN + BK - 1) / BK) : kblocks;
+  const int nkb = max(0, kb_end - kb_beg);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -244,13 +249,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      for (int kb = 0; kb < kblocks; ++kb) {
-        const int s = kb % NSTAGE;
-        const uint32_t u = kb / NSTAGE;
+      for (int i = 0; i < nkb; ++i) {
+        const int s = i % NSTAGE;
+        const uint32_t u = i / NSTAGE;
         if (!mbar_wait(&empty[s], (u & 1) ^ 1)) { atomicOr(err, 1); break; }
         unsigned char *st = smem + s * STAGE;
         mbar_expect_tx(&full[s], STAGE);
-        const int x = kb * BK;
+        const int x = (kb_beg + i) * BK;
         tma_load_2d(st, &mapA, &full[s], x, m0);
         tma_load_2d(st + A_TILE, &mapA, &full[s], x, a_slice_rows + m0);
         tma_load_2d(st + 2 * A_TILE, &mapB, &full[s], x, n0);
@@ -261,14 +266,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       // ---------------- MMA issuer: CHUNK_KB K-blocks per accumulator buffer
       const uint32_t idesc = idesc_f16();
-      const int nchunk = (kblocks + CHUNK_KB - 1) / CHUNK_KB;
+      const int nchunk = (nkb + CHUNK_KB - 1) / CHUNK_KB;
       bool ok = true;
       for (int ch = 0; ch < nchunk && ok; ++ch) {
         const int b = ch & 1;
         const uint32_t ub = ch >> 1;
         if (!mbar_wait(&acce[b], (ub & 1) ^ 1)) { atomicOr(err, 8); break; }
         const uint32_t d = tmem + (uint32_t)(b * BN);
-        const int kb1 = min(kblocks, (ch + 1) * CHUNK_KB);
+        const int kb1 = min(nkb, (ch + 1) * CHUNK_KB);
         for (int kb = ch * CHUNK_KB; kb < kb1; ++kb) {
           const int s = kb % NSTAGE;
           const uint32_t u = kb / NSTAGE;
@@ -308,7 +313,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int c0 = 0; c0 < EPI_COLS; c0 += 32) tmem_st32(cmp_base + c0, z);
     }
     bool ok = true;
-    const int nchunk = (kblocks + CHUNK_KB - 1) / CHUNK_KB;
+    const int nchunk = (nkb + CHUNK_KB - 1) / CHUNK_KB;
     for (int ch = 0; ch < nchunk; ++ch) {
       const int b = ch & 1;
       const uint32_t ub = ch >> 1;
@@ -662,8 +667,9 @@ pw_status pw_tc_split_coef(const double2 *Cm, int ld, int kdim, int ncols, const
 }
 
 pw_status pw_tc_gemm(const pw_tc_operand *A, int m, const pw_tc_operand *B, int n, double2 *C, int ldc,
-                     int mode, int accumulate, int herm, int *d_err, cudaStream_t st) {
+                     int mode, int accumulate, int herm, int *d_err, cudaStream_t st, int kb_lo, int tri_b) {
   if (A->kpad != B->kpad || m > A->rows_total || n > B->rows_total || m <= 0 || n <= 0) return PW_ERR_ARG;
+  if (kb_lo < 0 || kb_lo > A->kpad / BK) return PW_ERR_ARG;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A->data, A->kpad, 2 * A->rows_total, BM) ||
       !make_map(&mb, B->data, B->kpad, 2 * B->rows_total, BN))
@@ -676,7 +682,7 @@ pw_status pw_tc_gemm(const pw_tc_operand *A, int m, const pw_tc_operand *B, int 
   k_tc_gemm<<<mtiles * ntiles, NTHREADS, SMEM_BYTES, st>>>(ma, mb, A->rows_total, B->rows_total, m, n,
                                                       A->kpad / BK, mtiles, ntiles, A->inv_scale,
                                                       B->inv_scale, C, ldc, mode, accumulate, herm,
-                                                      d_err);
+                                                      kb_lo, tri_b, d_err);
   PW_TRY(pw_check_launch("tc_gemm"));
   if (herm) {
     const int ni = m / 2;

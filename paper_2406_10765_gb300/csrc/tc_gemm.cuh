@@ -36,5 +36,10 @@ pw_status pw_tc_split_coef(const double2 *Cm, int ld, int kdim, int ncols, const
 // mode 0 (rows pair re/im: A^H B products) or 1 (columns pair: A B products);
 // accumulate: add to C; herm: compute the upper triangle only and mirror it.
 // d_err: device int, OR-ed with a nonzero code if a bounded wait ran out.
+// kb_lo: the first kb_lo 64-wide K blocks of B are zero (skipped); tri_b: B's
+// rows come from an upper-triangular coefficient matrix (split_coef of M with
+// M[t][j] = 0 for t > j), so an output tile of real columns n0.. stops at K
+// block (n0 + 128) / 64.
 pw_status pw_tc_gemm(const pw_tc_operand *A, int m, const pw_tc_operand *B, int n, double2 *C,
-                     int ldc, int mode, int accumulate, int herm, int *d_err, cudaStream_t st);
+                     int ldc, int mode, int accumulate, int herm, int *d_err, cudaStream_t st,
+                     int kb_lo = 0, int tri_b = 0);
