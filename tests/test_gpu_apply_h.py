@@ -104,3 +104,21 @@ def test_apply_h_argument_errors():
     assert B._apply(lib.h, B._dptr(x), orc.npw, 0, B._dptr(y), st) == 0
     assert B._apply(lib.h, B._dptr(x), orc.npw - 1, 2, B._dptr(y), st) == B.PW_ERR_ARG
     assert B._apply(lib.h, ct.c_void_p(), orc.npw, 2, B._dptr(y), st) == B.PW_ERR_ARG
+
+
+# every grid size with a register line-FFT kernel (and the Stockham fallback
+# at 54 and 81): H psi on the Si 8-atom cell on an explicit grid against the
+# oracle on the same grid; FP64 where the FP64 plane fits in shared memory
+@pytest.mark.parametrize("N", [16, 24, 32, 36, 48, 54, 64, 72, 81, 96, 128, 144])
+def test_apply_h_grid_sizes(N):
+    ecut = 4.0 if N < 24 else 8.0
+    x = None
+    for prec, tol in (("fp64", 1e-12), ("mixed", 1e-5)):
+        if prec == "fp64" and N * (N + 1) * 16 > 227 * 1024:
+            continue
+        lib, orc, _ = cells("Si", 1, ecut, grid=(N, N, N), precision=prec)
+        assert lib.grid == (N, N, N) and lib.npw == orc.npw
+        if x is None:
+            x = synth.draw_x0(7, 8, orc.npw, 3)
+            ref = O.apply_H(orc, x)
+        assert rel(_run(lib, x), ref) < tol, (N, prec)
