@@ -197,8 +197,9 @@ void pw_solver_destroy(pw_solver *solver);
  * (required); psi_out: device complex128 npw x nb (ld) or NULL.  With
  * opts->precision == PW_MIXED the block converged in mixed precision is
  * finished by pw_solver_polish (FP64); bands still above tol then continue in
- * FP64 (rep->fp64_iters) within maxit, and the reported residuals are FP64.
- * Returns PW_ERR_NOCONV with eig / psi_out filled if maxit is reached. */
+ * FP64 (rep->fp64_iters, at most 8 steps) within maxit, and the reported
+ * residuals are FP64.  Returns PW_ERR_NOCONV with eig / psi_out filled if
+ * maxit (or the FP64 step limit) is reached. */
 pw_status pw_eigsolve(pw_cell *cell, const pw_solve_opts *opts, double *eig, void *psi_out,
                       int ld, pw_solve_report *rep, void *stream);
 

@@ -655,6 +655,11 @@ extern "C" pw_status pw_solver_block(pw_solver *s, void *psi, int ld) {
   return PW_OK;
 }
 
+// FP64 steps after a mixed solve: the split-precision floor leaves a few
+// bands just above tol, which one or two FP64 steps finish; more than this
+// means the mixed solve did not converge and FP64 (~20x slower) would not help
+constexpr int kMaxFp64Refine = 8;
+
 extern "C" pw_status pw_eigsolve(pw_cell *cell, const pw_solve_opts *o, double *eig, void *psi_out,
                                  int ld, pw_solve_report *rep, void *stream) {
   if (!cell || !o || !eig || (psi_out && ld < cell->npw)) return PW_ERR_ARG;
@@ -694,7 +699,7 @@ extern "C" pw_status pw_eigsolve(pw_cell *cell, const pw_solve_opts *o, double *
         if ((r = refresh_stats(s, st_h)) != PW_OK) break;
         rmax = 0.0;
         for (int j = 0; j < s->nb; ++j) rmax = fmax(rmax, s->resid_h[j]);
-        if (rmax <= s->tol || s->iter >= s->maxit) break;
+        if (rmax <= s->tol || s->iter >= s->maxit || fp64_iters >= kMaxFp64Refine) break;
         pw_step_report sr;
         if ((r = pw_subspace_step(cell, s, &sr)) != PW_OK) break;
         ++fp64_iters;
