@@ -251,6 +251,21 @@ size_t pw_request_footprint(const pw_request *req, int precision);
  * PW_ERR_CUDA; per-request failures are reported in results[i].status. */
 pw_status pw_serve(const pw_serve_opts *opts, const pw_request *req, int nreq, pw_result *results);
 
+/* Electron density of a block of bands on the cell's FFT grid, the quantity
+ * the self-consistent loop of Sec. II-A forms from the converged
+ * wavefunctions: rho(r_j) = sum_b occ_b |psi_b(r_j)|^2 with psi_b(r_j) =
+ * sum_G c_bG exp(i G.r_j), r_j = L j / N (no normalisation factor).
+ * psi: device complex128 npw x nb, leading dimension ld >= npw, sphere order
+ * of pw_cell_info.  occ: device nb doubles, or NULL for all ones.  rho:
+ * device N0*N1*N2 doubles, x fastest: rho[(jz*N1 + jy)*N0 + jx]; overwritten.
+ * Uses the cell's precision for the FFTs (FP32 in mixed mode) and sums in
+ * FP64 across band groups; the result is independent of scheduling.  Shares
+ * the cell's FFT workspace with pw_apply_H (no concurrent calls on one cell).
+ * Asynchronous on `stream`.  Errors: PW_ERR_ARG (nb < 0, ld < npw, NULL
+ * pointer, a grid whose plane exceeds shared memory), PW_ERR_OOM, PW_ERR_CUDA. */
+pw_status pw_density(pw_cell *cell, const void *psi, int ld, int nb, const double *occ, double *rho,
+                     void *stream);
+
 /* FP64 Hermitian eigensolver used by the Rayleigh-Ritz step (the small dense
  * eigensolve, Syevd in Sec. III-D): Householder reduction to a real
  * tridiagonal, divide and conquer, back-transformation.  A: device complex128

@@ -276,6 +276,23 @@ def pw_apply_H(cell, psi, hpsi, stream=None):
 
 
 _apply_na = _sig("pw_apply_H_noalloc", ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp, _vp])
+_density = _sig("pw_density", ct.c_int, [_vp, _vp, ct.c_int, ct.c_int, _vp, _vp, _vp])
+
+
+def pw_density(cell, psi, occ=None, rho=None, stream=None):
+    """rho(r) = sum_b occ_b |psi_b(r)|^2 on the cell's grid; psi: CUDA complex128
+    (npw, nb) column-major; occ: CUDA float64 (nb,) or None; returns rho as a
+    CUDA float64 tensor of shape (N2, N1, N0) (x fastest)."""
+    import torch
+    npw, nb = psi.shape
+    ld = psi.stride(1) if nb > 1 else npw
+    assert psi.stride(0) == 1 and psi.is_cuda
+    grid = pw_cell_info(cell)[1]
+    if rho is None:
+        rho = torch.empty((grid[2], grid[1], grid[0]), dtype=torch.float64, device=psi.device)
+    optr = _dptr(occ) if occ is not None else ct.c_void_p()
+    _check(_density(cell, _dptr(psi), ld, nb, optr, _dptr(rho), _stream(stream)), "pw_density")
+    return rho
 
 
 def pw_apply_H_noalloc(cell, psi, hpsi, stream=None):

@@ -262,6 +262,59 @@ __global__ void __launch_bounds__(256) k_z_to_sphere(const C *__restrict__ Z, in
   }
 }
 
+// ------------------------------------------------------------ density ----
+// Stockham counterpart of k_density_reg (grids without a register FFT):
+// inverse y and x FFTs of each band's plane, acc += w |psi(r)|^2 in fixed
+// per-thread points (at most DENS_ACC per thread).
+constexpr int DENS_ACC = 32;
+template <typename C>
+__global__ void __launch_bounds__(kPlaneThreads<C>::value) k_density_plane(const C *__restrict__ Z, int ncol,
+                                                                           const int *__restrict__ colxy,
+                                                                           int mxmax, pw_fft_axis ax, pw_fft_axis ay,
+                                                                           int Nz, int nbb,
+                                                                           const double *__restrict__ occ,
+                                                                           double *__restrict__ part) {
+  typedef decltype(Z[0].x) T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *P = reinterpret_cast<C *>(smem_raw);
+  const int Nx = ax.n, Ny = ay.n, pxs = Nx + 1, np = Nx * Ny;
+  const int z = blockIdx.x, grp = blockIdx.y, ngroups = gridDim.y;
+  T acc[DENS_ACC];
+#pragma unroll
+  for (int k = 0; k < DENS_ACC; ++k) acc[k] = 0;
+  const int nxe = 2 * mxmax + 1;
+  LineMap ycols{1, pxs, mxmax, Nx};
+  LineMap xrows{pxs, 1, 0, 1 << 30};
+  for (int j = grp; j < nbb; j += ngroups) {
+    const T w = occ ? (T)occ[j] : (T)1;
+    const C *Zp = Z + ((long)j * Nz + z) * ncol;
+    for (int i = threadIdx.x; i < Ny * pxs; i += blockDim.x) P[i] = czero<C>();
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+      const int xy = colxy[c];
+      P[(xy / Nx) * pxs + (xy % Nx)] = Zp[c];
+    }
+    __syncthreads();
+    fft_lines<C>(P, nxe, ycols, ay, true);
+    fft_lines<C>(P, Ny, xrows, ax, true);
+#pragma unroll
+    for (int k = 0; k < DENS_ACC; ++k) {
+      const int i = threadIdx.x + k * blockDim.x;
+      if (i < np) {
+        const C e = P[(i / Nx) * pxs + (i % Nx)];
+        acc[k] += w * (e.x * e.x + e.y * e.y);
+      }
+    }
+    __syncthreads();
+  }
+  double *out = part + ((long)grp * Nz + z) * np;
+#pragma unroll
+  for (int k = 0; k < DENS_ACC; ++k) {
+    const int i = threadIdx.x + k * blockDim.x;
+    if (i < np) out[i] = (double)acc[k];
+  }
+}
+
 template <typename K> static pw_status allow_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024)
     PW_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -350,6 +403,26 @@ pw_status apply_local_into(pw_cell *c, const double2 *psi, int ld, int nb, doubl
   return pw_check_launch("apply_local_into");
 }
 
+template <typename C>
+pw_status density_batch_t(pw_cell *c, const double2 *psi, int ld, int nbb, C *Z, const double *occ,
+                          int ngroups, double *part, cudaStream_t st) {
+  const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
+  const size_t plane_bytes = (size_t)Ny * (Nx + 1) * sizeof(C);
+  if (plane_bytes > 227 * 1024 || (long)Nx * Ny > (long)DENS_ACC * kPlaneThreads<C>::value) return PW_ERR_ARG;
+  const int cb = 16;
+  const size_t line_bytes = (size_t)cb * (Nz + 1) * sizeof(C);
+  PW_TRY(allow_smem(k_sphere_to_z<C>, line_bytes));
+  PW_TRY(allow_smem(k_density_plane<C>, plane_bytes));
+  dim3 gcols((c->ncol + cb - 1) / cb, nbb);
+  pw_count_launch();
+  k_sphere_to_z<C><<<gcols, 256, line_bytes, st>>>(psi, ld, c->d_colstart, c->d_gcol, c->d_gz, c->ncol, cb,
+                                                   c->ax[2], Z);
+  pw_count_launch();
+  k_density_plane<C><<<dim3(Nz, ngroups), kPlaneThreads<C>::value, plane_bytes, st>>>(
+      Z, c->ncol, c->d_colxy, c->mxmax, c->ax[0], c->ax[1], Nz, nbb, occ, part);
+  return pw_check_launch("density");
+}
+
 }  // namespace
 
 size_t pw_local_zbytes_per_band(const pw_cell *c) { return (size_t)c->N[2] * c->ncol * sizeof(double2); }
@@ -363,4 +436,10 @@ pw_status pw_apply_local(pw_cell *c, const double2 *psi, int ld, int nb, double2
                          int precision, cudaStream_t st) {
   if (precision == PW_MIXED) return apply_local_t<float2, float>(c, psi, ld, nb, hpsi, c->d_Vf, st);
   return apply_local_t<double2, double>(c, psi, ld, nb, hpsi, c->d_V, st);
+}
+
+pw_status pw_fft_density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, int fp32,
+                               const double *occ, int ngroups, double *part, cudaStream_t st) {
+  if (fp32) return density_batch_t<float2>(c, psi, ld, nbb, (float2 *)Z, occ, ngroups, part, st);
+  return density_batch_t<double2>(c, psi, ld, nbb, (double2 *)Z, occ, ngroups, part, st);
 }

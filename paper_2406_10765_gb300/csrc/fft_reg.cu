@@ -370,6 +370,109 @@ pw_status run_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hp
   return pw_check_launch("local part (register FFT)");
 }
 
+// ------------------------------------------------------------ density ----
+// Per z-plane and band group: psi_j(r) of the plane by inverse FFTs along y
+// and x (as in K2), then acc += w_j |psi_j(r)|^2.  Each thread owns fixed
+// plane points, so the sum over the group's bands runs in a fixed order in
+// registers; part[g][z][y][x] holds each group's sum.
+template <typename C, int L, int R>
+__global__ void __launch_bounds__(RegPlaneThreads<C>::value) k_density_reg(const C *__restrict__ Z, int ncol,
+                                                                           const int *__restrict__ colxy,
+                                                                           int mxmax, const C *__restrict__ twx,
+                                                                           int nbb, const double *__restrict__ occ,
+                                                                           double *__restrict__ part) {
+  typedef decltype(Z[0].x) T;
+  constexpr int N = L * R, pxs = N + 1, G = 32 / L;
+  constexpr int NT = RegPlaneThreads<C>::value;
+  constexpr int ACC = (N * N + NT - 1) / NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C *P = reinterpret_cast<C *>(smem_raw);
+  const int z = blockIdx.x, grp = blockIdx.y, ngroups = gridDim.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gid = lane / L, l = lane % L;
+  LineTw<C, L, R> t;
+  t.init(twx, l);
+  T acc[ACC];
+#pragma unroll
+  for (int k = 0; k < ACC; ++k) acc[k] = 0;
+  const int nxe = 2 * mxmax + 1;
+  for (int j = grp; j < nbb; j += ngroups) {
+    const T w = occ ? (T)occ[j] : (T)1;
+    const C *Zp = Z + ((long)j * N + z) * ncol;
+    for (int i = threadIdx.x; i < N * pxs; i += blockDim.x) P[i] = czero_r<C>();
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+      const int xy = colxy[c];
+      P[(xy / N) * pxs + (xy % N)] = Zp[c];
+    }
+    __syncthreads();
+    for (int base = warp * G; base < nxe; base += nw * G) {
+      const int xi = base + gid;
+      const bool act = xi < nxe;
+      int x = xi - mxmax;
+      if (x < 0) x += N;
+      C *col = P + (act ? x : 0);
+      C v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = act ? col[(l + L * r) * pxs] : czero_r<C>();
+      line_fft<C, L, R>(v, t, twx, l, true);
+      if (act) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) col[t.out_index(r, l) * pxs] = v[r];
+      }
+    }
+    __syncthreads();
+    for (int base = warp * G; base < N; base += nw * G) {
+      const int y = base + gid;
+      const bool act = y < N;
+      C *row = P + (long)(act ? y : 0) * pxs;
+      C v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = act ? row[l + L * r] : czero_r<C>();
+      line_fft<C, L, R>(v, t, twx, l, true);
+      if (act) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) row[t.out_index(r, l)] = v[r];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ACC; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < N * N) {
+        const C e = P[(i / N) * pxs + (i % N)];
+        acc[k] += w * (e.x * e.x + e.y * e.y);
+      }
+    }
+    __syncthreads();
+  }
+  double *out = part + ((long)grp * N + z) * N * N;
+#pragma unroll
+  for (int k = 0; k < ACC; ++k) {
+    const int i = threadIdx.x + k * NT;
+    if (i < N * N) out[i] = (double)acc[k];
+  }
+}
+
+template <typename C, int L, int R>
+pw_status density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, C *Z, const double *occ, int ngroups,
+                        double *part, cudaStream_t st) {
+  constexpr int N = L * R;
+  const size_t plane_bytes = (size_t)N * (N + 1) * sizeof(C);
+  if (plane_bytes > 227 * 1024) return PW_ERR_ARG;
+  if (plane_bytes > 48 * 1024)
+    PW_CUDA(cudaFuncSetAttribute(k_density_reg<C, L, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)plane_bytes));
+  const dim3 gcols((c->ncol + ZCB - 1) / ZCB, nbb);
+  pw_count_launch();
+  k_sphere_to_z_reg<C, L, R><<<gcols, ZTHREADS, 0, st>>>(psi, ld, c->d_colstart, c->d_gcol, c->d_gz,
+                                                         c->ncol, twtab<C>(c->ax[2]), Z);
+  pw_count_launch();
+  k_density_reg<C, L, R><<<dim3(N, ngroups), RegPlaneThreads<C>::value, plane_bytes, st>>>(
+      Z, c->ncol, c->d_colxy, c->mxmax, twtab<C>(c->ax[0]), nbb, occ, part);
+  return pw_check_launch("density (register FFT)");
+}
+
 // grid sizes with a register FFT: N -> (L, R)
 #define PW_REG_SIZES(X) X(16, 16, 1) X(24, 8, 3) X(32, 32, 1) X(36, 4, 9) X(48, 16, 3) \
                         X(64, 32, 2) X(72, 8, 9) X(96, 32, 3) X(128, 32, 4) X(144, 16, 9)
@@ -396,6 +499,19 @@ pw_status pw_fft_reg_batch(pw_cell *c, const double2 *psi, int ld, int nbb, doub
     if (fp32)                                                                                        \
       return run_batch<float2, float, LL, RR>(c, psi, ld, nbb, hpsi, (float2 *)Z, c->d_Vf, scale, st); \
     return run_batch<double2, double, LL, RR>(c, psi, ld, nbb, hpsi, (double2 *)Z, c->d_V, scale, st); \
+  }
+  PW_REG_SIZES(PW_CASE)
+#undef PW_CASE
+  return PW_ERR_ARG;
+}
+
+pw_status pw_fft_reg_density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, int fp32,
+                                   const double *occ, int ngroups, double *part, cudaStream_t st) {
+  const int n = c->N[0];
+#define PW_CASE(NN, LL, RR)                                                                          \
+  if (n == NN) {                                                                                     \
+    if (fp32) return density_batch<float2, LL, RR>(c, psi, ld, nbb, (float2 *)Z, occ, ngroups, part, st); \
+    return density_batch<double2, LL, RR>(c, psi, ld, nbb, (double2 *)Z, occ, ngroups, part, st);   \
   }
   PW_REG_SIZES(PW_CASE)
 #undef PW_CASE

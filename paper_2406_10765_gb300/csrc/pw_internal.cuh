@@ -82,6 +82,7 @@ struct pw_cell {
   pw_fft_axis ax[3];
   // apply_H workspace (grown on demand)
   void *d_z = nullptr; size_t z_bytes = 0;
+  double *d_dpart = nullptr; size_t dpart_bytes = 0;   // density partial sums
   double2 *d_B = nullptr; size_t B_elems = 0;   // nproj x nb projections
   double2 *d_gemm_ws = nullptr; size_t gemm_ws_elems = 0;
   size_t bytes = 0;
@@ -105,6 +106,13 @@ size_t pw_local_zbytes_per_band(const pw_cell *c);
 // register-resident line FFTs for cubic grids of supported sizes (one batch
 // of nbb bands through K1-K3 into the z-pencil buffer Z)
 bool pw_fft_reg_supported(const pw_cell *c, int fp32);
+// density of one batch of bands: z-pencils into Z, then per (z-plane, band
+// group) the inverse plane FFTs and sum_j occ[j] |psi_j(r)|^2 into
+// part[group][z][y][x]; register FFT or Stockham passes
+pw_status pw_fft_reg_density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, int fp32,
+                                   const double *occ, int ngroups, double *part, cudaStream_t st);
+pw_status pw_fft_density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, int fp32,
+                               const double *occ, int ngroups, double *part, cudaStream_t st);
 pw_status pw_fft_reg_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hpsi, void *Z,
                            int fp32, double scale, cudaStream_t st);
 pw_status pw_apply_local_fp64_into(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
