@@ -387,3 +387,59 @@ def density(cell: Cell, X: np.ndarray, occ: np.ndarray | None = None) -> np.ndar
     psi = to_real_space(cell, X)
     w = np.ones(X.shape[1]) if occ is None else occ
     return np.einsum("xyzb,b->xyz", np.abs(psi) ** 2, w)
+
+
+# --------------------------------------------------------------------------
+# Self-consistent field with a model V_Hxc (the outer loop of Sec. II-A; the
+# paper fixes no exchange-correlation functional, so the model is Hartree
+# plus Slater/Dirac exchange)
+# --------------------------------------------------------------------------
+
+def grid_gvectors(Ls, Ns) -> np.ndarray:
+    """|G|^2 on the full FFT grid, G = 2 pi k / L with k the signed index
+    (0 .. N/2, then negative), array [kx, ky, kz]."""
+    ks = [np.fft.fftfreq(Ns[a]) * Ns[a] for a in range(3)]
+    g = [TWO_PI * ks[a] / Ls[a] for a in range(3)]
+    return g[0][:, None, None] ** 2 + g[1][None, :, None] ** 2 + g[2][None, None, :] ** 2
+
+
+def hartree_potential(Ls, Ns, n: np.ndarray) -> np.ndarray:
+    """Periodic solution of lap V_H = -4 pi (n - <n>): V_H(r_j) = sum_{G != 0}
+    4 pi n~(G) / |G|^2 exp(i G.r_j), n~ the grid Fourier coefficients."""
+    nt = np.fft.fftn(n) / n.size
+    g2 = grid_gvectors(Ls, Ns)
+    vt = np.zeros_like(nt)
+    nz = g2 > 0
+    vt[nz] = 4.0 * math.pi * nt[nz] / g2[nz]
+    return np.real(np.fft.ifftn(vt) * n.size)
+
+
+def slater_exchange(n: np.ndarray) -> np.ndarray:
+    """Dirac/Slater exchange potential v_x = -(3 n / pi)^(1/3) (n >= 0)."""
+    return -np.cbrt(3.0 * np.maximum(n, 0.0) / math.pi)
+
+
+def electron_density(cell: Cell, X: np.ndarray, occ: np.ndarray) -> np.ndarray:
+    """n(r_j) = Omega^-1 sum_b occ_b |psi_b(r_j)|^2 (unit-norm coefficient
+    columns), so sum_j n_j Omega / N^3 = sum_b occ_b."""
+    return density(cell, X, occ) / float(np.prod(cell.Ls))
+
+
+def scf(cell0: Cell, nocc: int, fill: float = 2.0, mix: float = 0.3, niter: int = 8,
+        hxc_scale: float = 1.0):
+    """Linear density mixing: n_in <- (1 - mix) n_in + mix n_out, starting
+    from n_in = 0.  Iteration k: V = V_loc + hxc_scale (V_H + v_x)[n_in], the
+    lowest nocc eigenpairs of the dense H (LAPACK), n_out from them with
+    occupation `fill`.  Returns per iteration (eigenvalues, n_in, n_out)."""
+    n_in = np.zeros(cell0.Ns)
+    hist = []
+    occ = np.full(nocc, fill)
+    for _ in range(niter):
+        V = cell0.V + hxc_scale * (hartree_potential(cell0.Ls, cell0.Ns, n_in) + slater_exchange(n_in))
+        cell = Cell(Ls=cell0.Ls, Ns=cell0.Ns, ecut=cell0.ecut, m=cell0.m, kin=cell0.kin, V=V,
+                    beta=cell0.beta, D=cell0.D)
+        w, X = dense_eigs(cell, nocc)
+        n_out = electron_density(cell, X, occ)
+        hist.append((w, n_in.copy(), n_out))
+        n_in = (1.0 - mix) * n_in + mix * n_out
+    return hist

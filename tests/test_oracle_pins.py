@@ -331,3 +331,61 @@ def test_free_electron_golden_table():
     n2 = (m ** 2).sum(axis=1)
     for s, g in rows:
         assert (n2 == s).sum() == g
+
+
+# ---- model V_Hxc and the SCF loop -------------------------------------------
+
+def test_hartree_single_mode_closed_form():
+    # n = A cos(G.r) with G = 2 pi (2, -1, 3) / L: V_H = 4 pi A cos(G.r) / |G|^2
+    Ls = np.array([7.0, 8.0, 9.0])
+    Ns = (16, 18, 24)
+    k = np.array([2, -1, 3])
+    G = 2 * np.pi * k / Ls
+    r = [Ls[a] * np.arange(Ns[a]) / Ns[a] for a in range(3)]
+    phase = G[0] * r[0][:, None, None] + G[1] * r[1][None, :, None] + G[2] * r[2][None, None, :]
+    n = 0.37 * np.cos(phase) + 0.05                   # the constant has no potential
+    V = O.hartree_potential(Ls, Ns, n)
+    ref = 4 * np.pi * 0.37 * np.cos(phase) / (G @ G)
+    assert np.abs(V - ref).max() < 1e-12
+
+
+def test_hartree_superposition_and_zero_mean():
+    rng = np.random.default_rng(0)
+    Ls, Ns = np.array([6.0, 6.0, 6.0]), (12, 12, 12)
+    a, b = rng.random(Ns), rng.random(Ns)
+    Va, Vb = O.hartree_potential(Ls, Ns, a), O.hartree_potential(Ls, Ns, b)
+    assert np.abs(O.hartree_potential(Ls, Ns, 2 * a - b) - (2 * Va - Vb)).max() < 1e-12
+    assert abs(Va.mean()) < 1e-13
+
+
+def test_slater_exchange_uniform_gas():
+    # Dirac exchange potential of the uniform gas at r_s = 2: n = 3 / (4 pi r_s^3),
+    # v_x = -(3 n / pi)^(1/3) = -(9 / (4 pi^2))^(1/3) / r_s
+    rs = 2.0
+    n = np.full((2, 2, 2), 3.0 / (4 * np.pi * rs ** 3))
+    ref = -((9.0 / (4.0 * np.pi ** 2)) ** (1.0 / 3.0)) / rs
+    assert np.abs(O.slater_exchange(n) - ref).max() < 1e-15
+
+
+def test_scf_reduces_to_fixed_potential_and_counts_electrons():
+    ci = synth.cell_inputs("Si", 1, 0)
+    cell = O.make_cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], 6.0)
+    # no V_Hxc: every iteration is the fixed-potential eigenproblem
+    h = O.scf(cell, 8, niter=2, hxc_scale=0.0)
+    w0, _ = O.dense_eigs(cell, 8)
+    assert np.abs(h[1][0] - w0).max() < 1e-12
+    # electron count: sum_j n_j Omega / N^3 = 2 x 8
+    n_out = h[0][2]
+    assert abs(n_out.sum() * np.prod(cell.Ls) / n_out.size - 16.0) < 1e-10
+
+
+def test_scf_mixing_converges_to_a_fixed_point():
+    # the synthetic wells give a gapped model insulator with 8 doubly
+    # occupied bands (gap 0.21 Ha for C-8); linear mixing contracts to the
+    # self-consistent density
+    ci = synth.cell_inputs("C", 1, 0)
+    cell = O.make_cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], 8.0)
+    h = O.scf(cell, 8, mix=0.5, niter=16)
+    d = [np.abs(n_out - n_in).max() for _, n_in, n_out in h]
+    assert d[-1] < 1e-4 * d[0]
+    assert all(d[k + 2] < d[k] for k in range(len(d) - 2))
