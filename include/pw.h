@@ -130,7 +130,8 @@ typedef struct {
   double tol;           /* residual-norm tolerance (bands below it are locked) */
   int maxit;            /* maximum LOBPCG steps for pw_eigsolve */
   uint64_t seed;        /* SplitMix64 stream of the random start when x0 == NULL */
-  const void *x0;       /* optional host complex128 npw x nbands start (ld = npw) */
+  const void *x0;       /* optional complex128 npw x nbands start (ld = npw), host
+                           or device memory */
   int precision;        /* PW_FP64 or PW_MIXED */
 } pw_solve_opts;
 
@@ -265,6 +266,54 @@ pw_status pw_serve(const pw_serve_opts *opts, const pw_request *req, int nreq, p
  * pointer, a grid whose plane exceeds shared memory), PW_ERR_OOM, PW_ERR_CUDA. */
 pw_status pw_density(pw_cell *cell, const void *psi, int ld, int nb, const double *occ, double *rho,
                      void *stream);
+
+/* Model exchange-correlation step of the self-consistent loop of Sec. II-A
+ * (the paper fixes no functional): v(r) = V_H(r) + v_x(r) from an electron
+ * density n(r), with V_H the periodic solution of lap V_H = -4 pi (n - <n>)
+ * (V_H(G) = 4 pi n(G) / |G|^2, G = 2 pi k / L, V_H(0) = 0) and the
+ * Slater/Dirac exchange v_x = -(3 n / pi)^(1/3).  n, v: device N0*N1*N2
+ * doubles, x fastest ([z][y][x], as rho of pw_density); n is not changed.
+ * FP64.  Asynchronous on `stream`.  Errors: PW_ERR_ARG (NULL pointer),
+ * PW_ERR_OOM, PW_ERR_CUDA. */
+pw_status pw_hxc_potential(pw_cell *cell, const double *n, double *v, void *stream);
+
+/* Local potential of the cell becomes V_loc + v_hxc (device N0*N1*N2
+ * doubles, [z][y][x]; copied), in both the FP64 and FP32 copies used by
+ * pw_apply_H; v_hxc == NULL restores the cell's own V_loc.  Asynchronous on
+ * `stream`.  Errors: PW_ERR_ARG, PW_ERR_OOM, PW_ERR_CUDA. */
+pw_status pw_cell_set_hxc(pw_cell *cell, const double *v_hxc, void *stream);
+
+typedef struct {
+  int nbands;           /* bands solved for (>= nocc) */
+  int nocc;             /* occupied bands */
+  double fill;          /* occupation of each occupied band (2 for spin pairs) */
+  double mix;           /* linear density mixing, 0 < mix <= 1 */
+  int maxiter;          /* SCF iterations at most */
+  double tol;           /* stop when max_r |n_out - n_in| <= tol */
+  double eig_tol;       /* pw_eigsolve tolerance of each iteration */
+  int eig_maxit;        /* pw_eigsolve step limit of each iteration */
+  uint64_t seed;        /* random start block of the first iteration */
+  int precision;        /* PW_FP64 | PW_MIXED (eigensolves and FFTs) */
+} pw_scf_opts;
+
+typedef struct {
+  int iters;            /* SCF iterations taken */
+  int eig_iters;        /* LOBPCG steps over all iterations */
+  double max_dn;        /* max |n_out - n_in| of the last iteration */
+} pw_scf_report;
+
+/* Self-consistent field loop with the model V_Hxc of pw_hxc_potential:
+ * starting from n_in = 0, iteration k sets V = V_loc + V_Hxc[n_in]
+ * (pw_cell_set_hxc), solves for the lowest nbands eigenpairs (pw_eigsolve,
+ * started from the previous iteration's block), forms
+ * n_out = Omega^-1 sum_{b < nocc} fill |psi_b|^2 (pw_density) and mixes
+ * n_in <- (1 - mix) n_in + mix n_out, until max |n_out - n_in| <= tol or
+ * maxiter.  eig: host nbands doubles (last iteration).  n_out: device
+ * N0*N1*N2 doubles or NULL (last output density).  The cell keeps the last
+ * V = V_loc + V_Hxc[n_in].  Synchronises `stream`.  Returns PW_ERR_NOCONV
+ * (results filled) if maxiter is reached; errors as pw_eigsolve. */
+pw_status pw_scf(pw_cell *cell, const pw_scf_opts *opts, double *eig, double *n_out, pw_scf_report *rep,
+                 void *stream);
 
 /* FP64 Hermitian eigensolver used by the Rayleigh-Ritz step (the small dense
  * eigensolve, Syevd in Sec. III-D): Householder reduction to a real

@@ -399,3 +399,58 @@ class Cell:
             self.close()
         except Exception:
             pass
+
+
+_hxc = _sig("pw_hxc_potential", ct.c_int, [_vp, _vp, _vp, _vp])
+_set_hxc = _sig("pw_cell_set_hxc", ct.c_int, [_vp, _vp, _vp])
+
+
+class pw_scf_opts(ct.Structure):
+    _fields_ = [("nbands", ct.c_int), ("nocc", ct.c_int), ("fill", ct.c_double), ("mix", ct.c_double),
+                ("maxiter", ct.c_int), ("tol", ct.c_double), ("eig_tol", ct.c_double),
+                ("eig_maxit", ct.c_int), ("seed", ct.c_uint64), ("precision", ct.c_int)]
+
+
+class pw_scf_report(ct.Structure):
+    _fields_ = [("iters", ct.c_int), ("eig_iters", ct.c_int), ("max_dn", ct.c_double)]
+
+
+_scf = _sig("pw_scf", ct.c_int, [_vp, ct.POINTER(pw_scf_opts), ct.POINTER(ct.c_double), _vp,
+                                  ct.POINTER(pw_scf_report), _vp])
+
+
+def _grid_tensor(cell, device="cuda"):
+    import torch
+    g = pw_cell_info(cell)[1]
+    return torch.empty((g[2], g[1], g[0]), dtype=torch.float64, device=device)
+
+
+def pw_hxc_potential(cell, n, v=None, stream=None):
+    """Model V_H + v_x of a density n (CUDA float64 grid tensor, (N2, N1, N0))."""
+    if v is None:
+        v = _grid_tensor(cell, n.device)
+    _check(_hxc(cell, _dptr(n), _dptr(v), _stream(stream)), "pw_hxc_potential")
+    return v
+
+
+def pw_cell_set_hxc(cell, v=None, stream=None):
+    """Local potential becomes V_loc + v (None restores V_loc)."""
+    _check(_set_hxc(cell, _dptr(v) if v is not None else ct.c_void_p(), _stream(stream)), "pw_cell_set_hxc")
+
+
+def pw_scf(cell, nbands, nocc, fill=2.0, mix=0.5, maxiter=30, tol=1e-6, eig_tol=1e-10, eig_maxit=200,
+           seed=0, precision="fp64", stream=None, raise_noconv=True):
+    """Linear-mixing SCF with the model V_Hxc; returns (eig (numpy), n_out (CUDA grid
+    tensor), report, status)."""
+    o = pw_scf_opts()
+    o.nbands, o.nocc, o.fill, o.mix = int(nbands), int(nocc), float(fill), float(mix)
+    o.maxiter, o.tol, o.eig_tol, o.eig_maxit = int(maxiter), float(tol), float(eig_tol), int(eig_maxit)
+    o.seed, o.precision = int(seed), _PREC[precision]
+    eig = np.zeros(nbands)
+    n_out = _grid_tensor(cell)
+    rep = pw_scf_report()
+    st = _scf(cell, ct.byref(o), eig.ctypes.data_as(ct.POINTER(ct.c_double)), _dptr(n_out), ct.byref(rep),
+              _stream(stream))
+    if st != PW_OK and (st != PW_ERR_NOCONV or raise_noconv):
+        raise PwError(st, "pw_scf")
+    return eig, n_out, rep, st

@@ -315,6 +315,44 @@ __global__ void __launch_bounds__(kPlaneThreads<C>::value) k_density_plane(const
   }
 }
 
+// ------------------------------------------------------ full-grid FFT ----
+// One axis of a 3-D transform of a complex grid g[(z N1 + y) N0 + x]
+// (x fastest): each block gathers 16 lines of the axis into shared memory,
+// runs the Stockham passes in place and writes them back.  Unscaled; sign -1
+// forward, +1 inverse.
+constexpr int GL = 16;
+__global__ void __launch_bounds__(256) k_grid_fft_axis(double2 *__restrict__ g, int N0, int N1, int N2,
+                                                       int axis, pw_fft_axis ax, int inv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *lines = reinterpret_cast<double2 *>(smem_raw);
+  const int n = ax.n, ls = n + 1;
+  const long nlines = (long)N0 * N1 * N2 / n;
+  const long l0 = (long)blockIdx.x * GL;
+  const int nl = (int)min((long)GL, nlines - l0);
+  // line q -> (first element, stride)
+  auto base = [&](long q, long *stride) -> long {
+    if (axis == 0) { *stride = 1; return q * N0; }
+    if (axis == 1) { *stride = N0; const long z = q / N0, x = q % N0; return z * (long)N0 * N1 + x; }
+    *stride = (long)N0 * N1;
+    return q;                                            // q = y N0 + x
+  };
+  for (int i = threadIdx.x; i < nl * n; i += blockDim.x) {
+    const int e = i / nl, q = i % nl;                    // consecutive threads: consecutive lines
+    long st;
+    const long b = base(l0 + q, &st);
+    lines[q * ls + e] = g[b + e * st];
+  }
+  __syncthreads();
+  LineMap lm{ls, 1, 0, 1 << 30};
+  fft_lines<double2>(lines, nl, lm, ax, inv != 0);
+  for (int i = threadIdx.x; i < nl * n; i += blockDim.x) {
+    const int e = i / nl, q = i % nl;
+    long st;
+    const long b = base(l0 + q, &st);
+    g[b + e * st] = lines[q * ls + e];
+  }
+}
+
 template <typename K> static pw_status allow_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024)
     PW_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -442,4 +480,18 @@ pw_status pw_fft_density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, 
                                const double *occ, int ngroups, double *part, cudaStream_t st) {
   if (fp32) return density_batch_t<float2>(c, psi, ld, nbb, (float2 *)Z, occ, ngroups, part, st);
   return density_batch_t<double2>(c, psi, ld, nbb, (double2 *)Z, occ, ngroups, part, st);
+}
+
+pw_status pw_grid_fft(pw_cell *c, double2 *g, int inverse, cudaStream_t st) {
+  const long npts = (long)c->N[0] * c->N[1] * c->N[2];
+  for (int a = 0; a < 3; ++a) {
+    const int n = c->N[a];
+    const size_t bytes = (size_t)GL * (n + 1) * sizeof(double2);
+    PW_TRY(allow_smem(k_grid_fft_axis, bytes));
+    const long nlines = npts / n;
+    pw_count_launch();
+    k_grid_fft_axis<<<(unsigned)((nlines + GL - 1) / GL), 256, bytes, st>>>(g, c->N[0], c->N[1], c->N[2], a,
+                                                                          c->ax[a], inverse);
+  }
+  return pw_check_launch("grid fft");
 }

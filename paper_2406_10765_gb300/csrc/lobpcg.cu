@@ -481,7 +481,8 @@ extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, voi
   s->resid_h.assign(nb, 0.0);
   // start block X0 in S[:, 0:nb]
   if (o->x0) {
-    if (cudaMemcpyAsync(s->S, o->x0, blk, cudaMemcpyHostToDevice, s->st) != cudaSuccess) {
+    // host or device memory (unified addressing decides the direction)
+    if (cudaMemcpyAsync(s->S, o->x0, blk, cudaMemcpyDefault, s->st) != cudaSuccess) {
       pw_solver_destroy(s); return PW_ERR_CUDA;
     }
   } else {

@@ -83,6 +83,8 @@ struct pw_cell {
   // apply_H workspace (grown on demand)
   void *d_z = nullptr; size_t z_bytes = 0;
   double *d_dpart = nullptr; size_t dpart_bytes = 0;   // density partial sums
+  double *d_V0 = nullptr;                              // the cell's own V_loc while another V is set
+  double2 *d_grid = nullptr; size_t grid_bytes = 0;    // full-grid FFT scratch
   double2 *d_B = nullptr; size_t B_elems = 0;   // nproj x nb projections
   double2 *d_gemm_ws = nullptr; size_t gemm_ws_elems = 0;
   size_t bytes = 0;
@@ -111,6 +113,9 @@ bool pw_fft_reg_supported(const pw_cell *c, int fp32);
 // part[group][z][y][x]; register FFT or Stockham passes
 pw_status pw_fft_reg_density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, int fp32,
                                    const double *occ, int ngroups, double *part, cudaStream_t st);
+// unscaled 3-D FFT of a complex grid g[(z N1 + y) N0 + x] in place (sign -1
+// forward, +1 inverse)
+pw_status pw_grid_fft(pw_cell *c, double2 *g, int inverse, cudaStream_t st);
 pw_status pw_fft_density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, int fp32,
                                const double *occ, int ngroups, double *part, cudaStream_t st);
 pw_status pw_fft_reg_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hpsi, void *Z,

@@ -155,7 +155,7 @@ extern "C" void pw_destroy_cell(pw_cell *c) {
   if (c->d_rmax) cudaFree(c->d_rmax);
   if (c->d_tc_err) cudaFree(c->d_tc_err);
   void *ptrs[] = {c->d_gcol, c->d_gz, c->d_colstart, c->d_colxy, c->d_kin, c->d_V, c->d_Vf,
-                  c->d_beta, c->d_D, c->d_z, c->d_dpart, c->d_B, c->d_gemm_ws, c->d_beta_split,
+                  c->d_beta, c->d_D, c->d_z, c->d_dpart, c->d_V0, c->d_grid, c->d_B, c->d_gemm_ws, c->d_beta_split,
                   c->ax[0].tw64, c->ax[0].tw32, c->ax[1].tw64, c->ax[1].tw32,
                   c->ax[2].tw64, c->ax[2].tw32};
   for (void *p : ptrs)

@@ -377,22 +377,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // -------------------------------------------------------------- splits ----
-__device__ __forceinline__ float warp_maxf(float v) {
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ float block_maxf(float v) {
-  __shared__ float sh[32];
-  v = warp_maxf(v);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float r = 0.0f;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, sh[w]);
-  __syncthreads();
-  return r;
-}
-
 // The splits below run on integer and FP32 arithmetic only: FP64 issues at
 // about two operations per clock per SM on this part, which made the split
 // kernels FP64-bound at several times their memory time.
