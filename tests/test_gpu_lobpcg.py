@@ -110,3 +110,24 @@ def test_solver_argument_errors():
     assert e.value.status == pw.PW_ERR_ARG
     with pytest.raises(pw.PwError):
         pw.pw_solver_create(lib.h, 0)
+
+
+def test_lobpcg_steps_match_oracle_si64():
+    # 64-atom cell (npw 13,133, grid 48^3, 144 bands): a Rayleigh-Ritz order
+    # of 432 spans 13.5 Householder panels, four divide-and-conquer levels
+    # and many GEMM tiles with ragged edges
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 2, 10.0)
+    assert lib.grid == (48, 48, 48) and lib.npw == orc.npw
+    nb = 144
+    x0 = synth.draw_x0(0, 64, orc.npw, nb)
+    st = O.lobpcg_init(orc, x0)
+    s = pw.pw_solver_create(lib.h, nb, tol=0.0, x0=x0)
+    for it in range(2):
+        st = O.lobpcg_step(orc, st)
+        rep = pw.pw_subspace_step(lib.h, s)
+        assert rep.nsub == 3 * nb or it == 0
+        e, r = pw.pw_solver_eigs(s, nb)
+        assert np.abs(e - st.lam).max() < 1e-9, (it, np.abs(e - st.lam).max())
+        assert abs(rep.max_resid - st.resid.max()) < 1e-8 * max(1.0, st.resid.max())
+    pw.pw_solver_destroy(s)

@@ -65,3 +65,22 @@ def test_mixed_apply_h_si512_sampled():
     for j in [0, 23]:
         ref = O.apply_H(orc, x[:, j:j + 1])[:, 0]
         assert rel(got[:, j], ref) < 1e-5
+
+
+def test_mixed_steps_track_oracle_si64():
+    # mixed precision on the 64-atom cell (Rayleigh-Ritz order 432; the
+    # tensor-core products span many 128 x 128 tiles with ragged edges):
+    # the Ritz values stay within the split-precision error of the oracle's
+    # FP64 steps from the same start block
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 2, 10.0, precision="mixed")
+    nb = 144
+    x0 = synth.draw_x0(0, 64, orc.npw, nb)
+    st = O.lobpcg_init(orc, x0)
+    s = pw.pw_solver_create(lib.h, nb, tol=0.0, x0=x0, precision="mixed")
+    for _ in range(3):
+        st = O.lobpcg_step(orc, st)
+        pw.pw_subspace_step(lib.h, s)
+    e, _ = pw.pw_solver_eigs(s, nb)
+    assert np.abs(e - st.lam).max() < 1e-4
+    pw.pw_solver_destroy(s)
