@@ -625,27 +625,62 @@ struct DcArrays {
   int *ctype, *qL, *qR, *kLR, *kneed;
 };
 
-// sort, z-vector, deflation and compaction for one node per CTA
+// exclusive prefix over the block of per-thread counts (blockDim <= 256);
+// returns this thread's offset, *total the sum
+__device__ int block_excl_scan(int v, int *s_scan, int *total) {
+  __syncthreads();
+  s_scan[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const int c = s_scan[t];
+      s_scan[t] = acc;
+      acc += c;
+    }
+    s_scan[blockDim.x] = acc;
+  }
+  __syncthreads();
+  *total = s_scan[blockDim.x];
+  return s_scan[threadIdx.x];
+}
+
+// sort, z-vector, deflation and compaction for one node per CTA.  The merge
+// of the two sorted halves places each value by its rank in the other half
+// (ties: left first); the deflation scan (each decision depends on the
+// previous surviving index) runs on one thread over the node's arrays and
+// records its rotations, which the block then applies in order; the
+// compactions are block-wide prefix sums.
 __global__ void __launch_bounds__(256) k_dc_deflate(const int *nodes, int n, const double *e,
                                                     DcArrays a) {
   __shared__ double sh[32];
-  __shared__ int s_rot, s_cj, s_ci, s_prev;
-  __shared__ double s_c, s_s;
+  __shared__ int s_scan[257];
+  __shared__ int s_nrot;
   const int node = blockIdx.x;
   const int lo = nodes[3 * node], mid = nodes[3 * node + 1], hi = nodes[3 * node + 2];
   const int size = hi - lo, m1 = mid - lo;
   const double beta = e[mid - 1];
   const double rho = fabs(beta), sgn = beta >= 0.0 ? 1.0 : -1.0;
-  if (threadIdx.x == 0) {    // merge of the two sorted halves (ties: left first)
-    int i = 0, j = m1;
-    for (int p = 0; p < size; ++p) {
-      int take;
-      if (i >= m1) take = j++;
-      else if (j >= size) take = i++;
-      else if (a.lam[lo + j] < a.lam[lo + i]) take = j++;
-      else take = i++;
-      a.perm[lo + p] = take;
+  // 1. merge: left value -> its index + #(right < v); right -> index + #(left <= v)
+  for (int p = threadIdx.x; p < size; p += blockDim.x) {
+    const double v = a.lam[lo + p];
+    int out;
+    if (p < m1) {
+      int l = 0, r = size - m1;
+      while (l < r) {
+        const int mm = (l + r) >> 1;
+        if (a.lam[lo + m1 + mm] < v) l = mm + 1; else r = mm;
+      }
+      out = p + l;
+    } else {
+      int l = 0, r = m1;
+      while (l < r) {
+        const int mm = (l + r) >> 1;
+        if (a.lam[lo + mm] <= v) l = mm + 1; else r = mm;
+      }
+      out = (p - m1) + l;
     }
+    a.perm[lo + out] = p;
   }
   __syncthreads();
   double dmax = 0.0;
@@ -663,82 +698,98 @@ __global__ void __launch_bounds__(256) k_dc_deflate(const int *nodes, int n, con
   dmax = block_max(dmax, sh);
   const double rho2 = 2.0 * rho;
   const double tol = 8.0 * kEps * fmax(dmax, rho2);
-  if (threadIdx.x == 0) s_prev = -1;
-  __syncthreads();
-  for (int p = 0; p < size; ++p) {
-    if (threadIdx.x == 0) {
-      s_rot = 0;
+  // 2. deflation scan; rotation list in this node's own columns of W (W is
+  // rewritten by k_dc_gemm later in the level)
+  double *rot = a.W + (long)lo * n;
+  if (threadIdx.x == 0) {
+    int prev = -1, nrot = 0;
+    for (int p = 0; p < size; ++p) {
       const double zp = a.zs[lo + p];
-      if (rho2 * fabs(zp) <= tol) {
-        a.defl[lo + p] = 1;
-      } else {
-        if (s_prev >= 0) {
-          const int j = s_prev;
-          const double zj = a.zs[lo + j];
-          const double r = hypot(zp, zj);
-          const double c = zp / r, s = -zj / r;
-          const double Dj = a.Ds[lo + j], Dp = a.Ds[lo + p];
-          if (fabs(c * s * (Dp - Dj)) <= tol) {
-            s_rot = 1;
-            s_cj = lo + a.perm[lo + j];
-            s_ci = lo + a.perm[lo + p];
-            if (a.ctype[s_cj] != a.ctype[s_ci]) a.ctype[s_cj] = a.ctype[s_ci] = 2;
-            s_c = c;
-            s_s = s;
-            a.Ds[lo + j] = c * c * Dj + s * s * Dp;
-            a.Ds[lo + p] = s * s * Dj + c * c * Dp;
-            a.zs[lo + j] = 0.0;
-            a.zs[lo + p] = r;
-            a.defl[lo + j] = 1;
-          }
+      if (rho2 * fabs(zp) <= tol) { a.defl[lo + p] = 1; continue; }
+      if (prev >= 0) {
+        const int j = prev;
+        const double zj = a.zs[lo + j];
+        const double r = hypot(zp, zj);
+        const double c = zp / r, s = -zj / r;
+        const double Dj = a.Ds[lo + j], Dp = a.Ds[lo + p];
+        if (fabs(c * s * (Dp - Dj)) <= tol) {
+          const int cj = lo + a.perm[lo + j], ci = lo + a.perm[lo + p];
+          if (a.ctype[cj] != a.ctype[ci]) a.ctype[cj] = a.ctype[ci] = 2;
+          rot[4 * nrot] = cj;
+          rot[4 * nrot + 1] = ci;
+          rot[4 * nrot + 2] = c;
+          rot[4 * nrot + 3] = s;
+          ++nrot;
+          a.Ds[lo + j] = c * c * Dj + s * s * Dp;
+          a.Ds[lo + p] = s * s * Dj + c * c * Dp;
+          a.zs[lo + j] = 0.0;
+          a.zs[lo + p] = r;
+          a.defl[lo + j] = 1;
         }
-        s_prev = p;
       }
+      prev = p;
     }
-    __syncthreads();
-    if (s_rot) {
-      const double c = s_c, s = s_s;
-      double *Qj = a.Z + (long)s_cj * n, *Qi = a.Z + (long)s_ci * n;
-      for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
-        const double qj = Qj[r], qi = Qi[r];
-        Qj[r] = c * qj + s * qi;
-        Qi[r] = -s * qj + c * qi;
-      }
+    s_nrot = nrot;
+  }
+  __syncthreads();
+  const int nrot = s_nrot;
+  for (int k = 0; k < nrot; ++k) {           // in order: a column may take part in two
+    const int cj = (int)rot[4 * k], ci = (int)rot[4 * k + 1];
+    const double c = rot[4 * k + 2], s = rot[4 * k + 3];
+    double *Qj = a.Z + (long)cj * n, *Qi = a.Z + (long)ci * n;
+    for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
+      const double qj = Qj[r], qi = Qi[r];
+      Qj[r] = c * qj + s * qi;
+      Qi[r] = -s * qj + c * qi;
     }
     __syncthreads();
   }
+  // 3. compaction: survivors -> (DK, zK, colK), deflated -> (dD, dcol), in order
+  const bool all_defl = !(rho2 > 0.0);   // no coupling: everything deflates
+  const int chunk = (size + blockDim.x - 1) / blockDim.x;
+  const int p0 = min(size, (int)threadIdx.x * chunk), p1 = min(size, p0 + chunk);
+  int cnt = 0;
+  for (int p = p0; p < p1; ++p) cnt += (!all_defl && !a.defl[lo + p]);
+  int k_total;
+  int t = block_excl_scan(cnt, s_scan, &k_total);
+  int q = p0 - t;
+  for (int p = p0; p < p1; ++p) {
+    const int col = lo + a.perm[lo + p];
+    if (!all_defl && !a.defl[lo + p]) {
+      a.DK[lo + t] = a.Ds[lo + p];
+      a.zK[lo + t] = a.zs[lo + p];
+      a.colK[lo + t] = col;
+      ++t;
+    } else {
+      a.dD[lo + q] = a.Ds[lo + p];
+      a.dcol[lo + q] = col;
+      ++q;
+    }
+  }
+  __syncthreads();
+  // root columns the upper rows need (types 0, 2) and the lower rows (2, 1)
+  const int kk = k_total;
+  const int c0 = min(kk, (int)threadIdx.x * ((kk + blockDim.x - 1) / blockDim.x));
+  const int c1 = min(kk, c0 + (kk + blockDim.x - 1) / blockDim.x);
+  int nl = 0, nr = 0;
+  for (int q2 = c0; q2 < c1; ++q2) {
+    const int ty = a.ctype[a.colK[lo + q2]];
+    nl += ty != 1;
+    nr += ty != 0;
+  }
+  int nl_total, nr_total;
+  int ol = block_excl_scan(nl, s_scan, &nl_total);
+  int orr = block_excl_scan(nr, s_scan, &nr_total);
+  for (int q2 = c0; q2 < c1; ++q2) {
+    const int ty = a.ctype[a.colK[lo + q2]];
+    if (ty != 1) a.qL[lo + ol++] = q2;
+    if (ty != 0) a.qR[lo + orr++] = q2;
+  }
   if (threadIdx.x == 0) {
-    int t = 0, q = 0;
-    for (int p = 0; p < size; ++p) {
-      const int col = lo + a.perm[lo + p];
-      if (!a.defl[lo + p]) {
-        a.DK[lo + t] = a.Ds[lo + p];
-        a.zK[lo + t] = a.zs[lo + p];
-        a.colK[lo + t] = col;
-        ++t;
-      } else {
-        a.dD[lo + q] = a.Ds[lo + p];
-        a.dcol[lo + q] = col;
-        ++q;
-      }
-    }
-    a.knode[node] = rho2 > 0.0 ? t : 0;
-    // root columns the upper rows need (types 0, 2) and the lower rows (2, 1)
-    int nl = 0, nr = 0;
-    for (int q2 = 0; q2 < t; ++q2) {
-      const int ty = a.ctype[a.colK[lo + q2]];
-      if (ty != 1) a.qL[lo + nl++] = q2;
-      if (ty != 0) a.qR[lo + nr++] = q2;
-    }
-    a.kLR[2 * node] = nl;
-    a.kLR[2 * node + 1] = nr;
+    a.knode[node] = kk;
+    a.kLR[2 * node] = nl_total;
+    a.kLR[2 * node + 1] = nr_total;
     a.kneed[node] = 0;
-    if (!(rho2 > 0.0)) {   // no coupling: everything deflates
-      for (int p = 0; p < size; ++p) {
-        a.dD[lo + p] = a.Ds[lo + p];
-        a.dcol[lo + p] = lo + a.perm[lo + p];
-      }
-    }
     a.rhonode[node] = rho2;
   }
 }
