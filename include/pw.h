@@ -102,6 +102,16 @@ pw_status pw_cell_set_precision(pw_cell *cell, int precision);
  * PW_ERR_OOM (workspace growth), PW_ERR_CUDA. */
 pw_status pw_apply_H(pw_cell *cell, const void *psi, int ld, int nb, void *hpsi, void *stream);
 
+/* Projector storage of a cell.  onthefly = 0 (default): beta (npw x 4 natom
+ * complex128, and in mixed precision its split-FP16 copies) stays resident.
+ * onthefly = 1: beta is freed and pw_apply_H regenerates it in chunks of
+ * atoms (at most 256 MB of beta at a time) from the plane-wave indices and
+ * per-axis structure-factor tables: the same operator (Sec. III-A), FP64
+ * values, the projection summed chunk by chunk.  Trades the resident
+ * projector memory for one projector evaluation per H psi.  Synchronises
+ * `stream`.  Errors: PW_ERR_ARG, PW_ERR_OOM (switching back), PW_ERR_CUDA. */
+pw_status pw_cell_set_projectors(pw_cell *cell, int onthefly, void *stream);
+
 /* Size of the fixed device scratch array used by pw_apply_H_noalloc. */
 #define PW_NOALLOC_SCRATCH_BYTES (16u << 20)
 
@@ -117,7 +127,8 @@ pw_status pw_apply_H(pw_cell *cell, const void *psi, int ld, int nb, void *hpsi,
  * looks up the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  Calls share the
  * array: calls that overlap on the GPU (other streams, other threads) race.
- * Errors: PW_ERR_ARG as pw_apply_H, and when the scratch would exceed
+ * Errors: PW_ERR_ARG as pw_apply_H, for a cell that generates its
+ * projectors on the fly (pw_cell_set_projectors), and when the scratch would exceed
  * PW_NOALLOC_SCRATCH_BYTES (projector coefficients, partial sums and one
  * band's z-pencils must fit: roughly nb <= 400 for a 2,048-projector cell,
  * fewer at small nb-independent limits); PW_ERR_CUDA. */

@@ -454,3 +454,11 @@ def pw_scf(cell, nbands, nocc, fill=2.0, mix=0.5, maxiter=30, tol=1e-6, eig_tol=
     if st != PW_OK and (st != PW_ERR_NOCONV or raise_noconv):
         raise PwError(st, "pw_scf")
     return eig, n_out, rep, st
+
+
+_setproj = _sig("pw_cell_set_projectors", ct.c_int, [_vp, ct.c_int, _vp])
+
+
+def pw_cell_set_projectors(cell, onthefly, stream=None):
+    """Projectors resident (False) or regenerated in atom chunks per H psi (True)."""
+    _check(_setproj(cell, 1 if onthefly else 0, _stream(stream)), "pw_cell_set_projectors")

@@ -5,6 +5,8 @@
 // resident, so the per-atom loop becomes two dense contractions over all
 // projectors at once:  B = beta^H psi  (nproj x nb), B <- D o B,
 // H psi += beta B.
+#include <algorithm>
+
 #include "pw_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -47,6 +49,68 @@ static pw_status nonlocal_tc(pw_cell *c, const double2 *psi, int ld, int nb, dou
   return pw_tc_gemm(c->op_beta_t, c->npw, c->op_db, 2 * nb, hpsi, ld, 1, 1, 0, c->d_tc_err, st);
 }
 
+// Projectors generated on the fly: atoms in chunks whose beta columns fit a
+// bounded buffer; each chunk's contribution beta_c (D_c o beta_c^H psi) is
+// added to hpsi in chunk order.  The same arithmetic as the stored-beta path
+// per projector (FP64 GEMMs, or split-FP16 tensor-core products of the
+// chunk), with beta regenerated each call instead of kept resident.
+constexpr size_t BCHUNK_BYTES = 256u << 20;
+static pw_status nonlocal_onthefly(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
+                                   int precision, cudaStream_t st) {
+  const int npw = c->npw;
+  const int ca = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->natom,
+                                                            BCHUNK_BYTES / ((size_t)npw * 4 * sizeof(double2))));
+  const int npc = 4 * ca;
+  PW_TRY(pw_ensure((void **)&c->d_bchunk, &c->bchunk_bytes, (size_t)npw * npc * sizeof(double2)));
+  const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+  const bool mixed = precision == PW_MIXED;
+  if (mixed) {
+    if (!c->op_bc_rows) {
+      c->op_bc_rows = new pw_tc_operand();
+      c->op_bc_t = new pw_tc_operand();
+      c->op_psi = c->op_psi ? c->op_psi : new pw_tc_operand();
+      c->op_db = c->op_db ? c->op_db : new pw_tc_operand();
+      size_t cur = 0;
+      if (!c->d_tc_err) {
+        PW_TRY(pw_ensure((void **)&c->d_tc_err, &cur, 16));
+        PW_CUDA(cudaMemsetAsync(c->d_tc_err, 0, 16, st));
+      }
+      cur = 0;
+      if (!c->d_rmax) PW_TRY(pw_ensure((void **)&c->d_rmax, &cur, (size_t)npw * sizeof(float)));
+    }
+    PW_TRY(pw_tc_operand_alloc(c->op_psi, nb, 2 * npw, st));
+    PW_TRY(pw_tc_split_rows(psi, ld, npw, nb, 0, nullptr, c->op_psi, st));
+  } else {
+    size_t ws = std::max(pw_zgemm_ws_elems(npc, nb, npw), pw_zgemm_ws_elems(npw, nb, npc));
+    size_t wcur = c->gemm_ws_elems * sizeof(double2);
+    PW_TRY(pw_ensure((void **)&c->d_gemm_ws, &wcur, ws * sizeof(double2)));
+    c->gemm_ws_elems = wcur / sizeof(double2);
+  }
+  for (int a0 = 0; a0 < c->natom; a0 += ca) {
+    const int na = std::min(ca, c->natom - a0), np = 4 * na;
+    PW_TRY(pw_beta_chunk(c, a0, na, c->d_bchunk, st));
+    if (mixed) {
+      PW_TRY(pw_tc_operand_alloc(c->op_bc_rows, 2 * np, 2 * npw, st));
+      PW_TRY(pw_tc_operand_alloc(c->op_bc_t, npw, 2 * np, st));
+      PW_TRY(pw_tc_operand_alloc(c->op_db, 2 * nb, 2 * np, st));
+      PW_TRY(pw_tc_split_rows(c->d_bchunk, npw, npw, np, 1, nullptr, c->op_bc_rows, st));
+      PW_TRY(pw_tc_split_trans(c->d_bchunk, npw, npw, np, c->d_rmax, c->op_bc_t, st));
+      PW_TRY(pw_tc_gemm(c->op_bc_rows, 2 * np, c->op_psi, nb, c->d_B, np, 0, 0, 0, c->d_tc_err, st));
+      PW_TRY(pw_tc_split_coef(c->d_B, np, np, nb, c->d_D + 4 * a0, c->op_db, st));
+      PW_TRY(pw_tc_gemm(c->op_bc_t, npw, c->op_db, 2 * nb, hpsi, ld, 1, 1, 0, c->d_tc_err, st));
+    } else {
+      PW_TRY(pw_zgemm('C', 'N', np, nb, npw, one, c->d_bchunk, npw, psi, ld, zero, c->d_B, np,
+                      c->d_gemm_ws, c->gemm_ws_elems, st));
+      pw_count_launch();
+      k_scale_rows<<<(unsigned)(((long)np * nb + 255) / 256), 256, 0, st>>>(c->d_B, np, nb, c->d_D + 4 * a0);
+      PW_TRY(pw_check_launch("scale_rows"));
+      PW_TRY(pw_zgemm('N', 'N', npw, nb, np, one, c->d_bchunk, npw, c->d_B, np, one, hpsi, ld, c->d_gemm_ws,
+                      c->gemm_ws_elems, st));
+    }
+  }
+  return PW_OK;
+}
+
 pw_status pw_apply_nonlocal(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
                             int precision, cudaStream_t st) {
   if (c->nproj == 0 || nb == 0) return PW_OK;
@@ -54,6 +118,7 @@ pw_status pw_apply_nonlocal(pw_cell *c, const double2 *psi, int ld, int nb, doub
   size_t cur = c->B_elems * sizeof(double2);
   PW_TRY(pw_ensure((void **)&c->d_B, &cur, need));
   c->B_elems = cur / sizeof(double2);
+  if (c->proj_onthefly) return nonlocal_onthefly(c, psi, ld, nb, hpsi, precision, st);
   if (precision == PW_MIXED) return nonlocal_tc(c, psi, ld, nb, hpsi, st);
   size_t ws = std::max(pw_zgemm_ws_elems(c->nproj, nb, c->npw), pw_zgemm_ws_elems(c->npw, nb, c->nproj));
   size_t wcur = c->gemm_ws_elems * sizeof(double2);
@@ -74,6 +139,7 @@ pw_status pw_apply_nonlocal(pw_cell *c, const double2 *psi, int ld, int nb, doub
 pw_status pw_apply_nonlocal_fp64_into(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
                                       double2 *B, double2 *ws, size_t ws_elems, cudaStream_t st) {
   if (c->nproj == 0 || nb == 0) return PW_OK;
+  if (!c->d_beta) return PW_ERR_ARG;   // projectors generated on the fly: not without allocation
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
   PW_TRY(pw_zgemm('C', 'N', c->nproj, nb, c->npw, one, c->d_beta, c->npw, psi, ld, zero, B, c->nproj,
                   ws, ws_elems, st));

@@ -49,6 +49,7 @@ extern "C" pw_status pw_apply_H_noalloc(pw_cell *c, const void *psi, int ld, int
   if (!c || nb < 0) return PW_ERR_ARG;
   if (nb == 0) return PW_OK;
   if (!psi || !hpsi || ld < c->npw) return PW_ERR_ARG;
+  if (c->proj_onthefly) return PW_ERR_ARG;   // regenerating beta needs a buffer
   // carve the scratch: projector coefficients B, GEMM partial sums, z-pencils
   const size_t b_bytes = round_up((size_t)c->nproj * nb * sizeof(double2));
   const size_t ws_elems = std::max(pw_zgemm_ws_elems(c->nproj, nb, c->npw),

@@ -77,7 +77,16 @@ struct pw_cell {
   double *d_kin = nullptr;    // npw: 1/2 |G|^2
   double *d_V = nullptr;      // Nz*Ny*Nx real potential, index (z*Ny + y)*Nx + x
   float *d_Vf = nullptr;
-  double2 *d_beta = nullptr;  // npw x nproj (ld = npw)
+  double2 *d_beta = nullptr;  // npw x nproj (ld = npw); NULL while generated on the fly
+  // projector generation: plane-wave indices and per-axis phase tables
+  // exp(-i 2 pi m tau_a / L), kept for regenerating beta (chunks or whole)
+  int *d_m = nullptr;
+  double2 *d_ph[3] = {nullptr, nullptr, nullptr};
+  int Mext[3] = {0, 0, 0};
+  double proj_ns = 0, proj_np = 0;
+  int proj_onthefly = 0;      // 1: beta generated per chunk of atoms in each H psi
+  double2 *d_bchunk = nullptr; size_t bchunk_bytes = 0;
+  struct pw_tc_operand *op_bc_rows = nullptr, *op_bc_t = nullptr;
   double *d_D = nullptr;      // nproj
   pw_fft_axis ax[3];
   // apply_H workspace (grown on demand)
@@ -96,6 +105,9 @@ struct pw_cell {
   int *d_tc_err = nullptr;
   void *d_beta_split = nullptr; size_t beta_split_bytes = 0;
 };
+
+// beta columns 4 a0 .. 4 (a0 + na) - 1 into out (npw x 4 na, ld npw)
+pw_status pw_beta_chunk(pw_cell *c, int a0, int na, double2 *out, cudaStream_t st);
 
 // apply_H pieces
 pw_status pw_apply_local(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,

@@ -123,19 +123,20 @@ __global__ void k_vloc(double *V, float *Vf, const double *fx, const double *fy,
 // exp(-i G.tau_a) is the product of three per-axis phases from host tables
 // ph[axis][a][m + M_axis].
 __global__ void k_beta(double2 *beta, const int *mvec, const double2 *phx, const double2 *phy,
-                       const double2 *phz, int Mx, int My, int Mz, int npw, int natom,
+                       const double2 *phz, int Mx, int My, int Mz, int npw, int natom, int a0,
                        double gx, double gy, double gz, double ns, double np, double rp2,
                        double inv_sqrt_omega) {
+  // atom a0 + blockIdx.y into columns 4 blockIdx.y .. (chunks of atoms)
   int g = blockIdx.x * blockDim.x + threadIdx.x;
-  int a = blockIdx.y;
-  if (g >= npw || a >= natom) return;
+  int al = blockIdx.y, a = a0 + al;
+  if (g >= npw || al >= natom) return;
   int mx = mvec[3 * g], my = mvec[3 * g + 1], mz = mvec[3 * g + 2];
   double Gx = gx * mx, Gy = gy * my, Gz = gz * mz;
   double g2 = Gx * Gx + Gy * Gy + Gz * Gz;
   double rad = exp(-0.5 * g2 * rp2) * inv_sqrt_omega;
   double2 p = cmul(cmul(phx[(long)a * (2 * Mx + 1) + mx + Mx], phy[(long)a * (2 * My + 1) + my + My]),
                    phz[(long)a * (2 * Mz + 1) + mz + Mz]);
-  double2 *col = beta + (long)(4 * a) * npw + g;
+  double2 *col = beta + (long)(4 * al) * npw + g;
   col[0] = make_double2(ns * rad * p.x, ns * rad * p.y);
   // (-i) * G_k * rad * p  ->  (G_k rad) * (p.y, -p.x)
   double f = np * rad;
@@ -144,18 +145,33 @@ __global__ void k_beta(double2 *beta, const int *mvec, const double2 *phx, const
   col[(long)3 * npw] = make_double2(f * Gz * p.y, -f * Gz * p.x);
 }
 
+pw_status pw_beta_chunk(pw_cell *c, int a0, int na, double2 *out, cudaStream_t st) {
+  if (na <= 0) return PW_OK;
+  const double twopi = 2.0 * M_PI;
+  const double omega = c->L[0] * c->L[1] * c->L[2];
+  dim3 grid((c->npw + 127) / 128, na);
+  pw_count_launch();
+  k_beta<<<grid, 128, 0, st>>>(out, c->d_m, c->d_ph[0], c->d_ph[1], c->d_ph[2], c->Mext[0], c->Mext[1],
+                               c->Mext[2], c->npw, na, a0, twopi / c->L[0], twopi / c->L[1],
+                               twopi / c->L[2], c->proj_ns, c->proj_np, c->pwidth * c->pwidth,
+                               1.0 / sqrt(omega));
+  return pw_check_launch("k_beta");
+}
+
 // --------------------------------------------------------------------------
 // entry points
 // --------------------------------------------------------------------------
 extern "C" void pw_destroy_cell(pw_cell *c) {
   if (!c) return;
-  pw_tc_operand **ops[] = {&c->op_beta_rows, &c->op_beta_t, &c->op_psi, &c->op_db};
+  pw_tc_operand **ops[] = {&c->op_beta_rows, &c->op_beta_t, &c->op_psi, &c->op_db, &c->op_bc_rows,
+                           &c->op_bc_t};
   for (pw_tc_operand **o : ops)
     if (*o) { pw_tc_operand_free(*o); delete *o; *o = nullptr; }
   if (c->d_rmax) cudaFree(c->d_rmax);
   if (c->d_tc_err) cudaFree(c->d_tc_err);
   void *ptrs[] = {c->d_gcol, c->d_gz, c->d_colstart, c->d_colxy, c->d_kin, c->d_V, c->d_Vf,
                   c->d_beta, c->d_D, c->d_z, c->d_dpart, c->d_V0, c->d_grid, c->d_B, c->d_gemm_ws, c->d_beta_split,
+                  c->d_m, c->d_ph[0], c->d_ph[1], c->d_ph[2], c->d_bchunk,
                   c->ax[0].tw64, c->ax[0].tw32, c->ax[1].tw64, c->ax[1].tw32,
                   c->ax[2].tw64, c->ax[2].tw32};
   for (void *p : ptrs)
@@ -332,27 +348,22 @@ extern "C" pw_status pw_setup_cell(const pw_cell_desc *d, void *stream, pw_cell 
           ph[ax][(size_t)a * w + m + M[ax]] = make_double2(cos(th), -sin(th));
         }
     }
-    int *dm;
-    double2 *dpx, *dpy, *dpz;
+    // tables stay with the cell (projector regeneration); uploaded straight
+    // into it, so a failure part-way is released by pw_destroy_cell
     size_t tmp = 0;
-    if ((s = upload((void **)&dm, c->m_host.data(), c->m_host.size() * 4, &tmp)) != PW_OK ||
-        (s = upload((void **)&dpx, ph[0].data(), ph[0].size() * 16, &tmp)) != PW_OK ||
-        (s = upload((void **)&dpy, ph[1].data(), ph[1].size() * 16, &tmp)) != PW_OK ||
-        (s = upload((void **)&dpz, ph[2].data(), ph[2].size() * 16, &tmp)) != PW_OK) {
+    if ((s = upload((void **)&c->d_m, c->m_host.data(), c->m_host.size() * 4, &tmp)) != PW_OK ||
+        (s = upload((void **)&c->d_ph[0], ph[0].data(), ph[0].size() * 16, &tmp)) != PW_OK ||
+        (s = upload((void **)&c->d_ph[1], ph[1].data(), ph[1].size() * 16, &tmp)) != PW_OK ||
+        (s = upload((void **)&c->d_ph[2], ph[2].data(), ph[2].size() * 16, &tmp)) != PW_OK) {
       pw_destroy_cell(c); return s;
     }
     double rp = d->pwidth;
-    double ns = sqrt(8.0 * pow(M_PI, 1.5) * rp * rp * rp);
-    double np = sqrt(16.0 * pow(M_PI, 1.5) * rp * rp * rp * rp * rp);
-    double omega = L[0] * L[1] * L[2];
-    dim3 grid((c->npw + 127) / 128, d->natom);
-    pw_count_launch();
-    k_beta<<<grid, 128, 0, st>>>(c->d_beta, dm, dpx, dpy, dpz, M[0], M[1], M[2], c->npw,
-                                 d->natom, twopi / L[0], twopi / L[1], twopi / L[2], ns, np,
-                                 rp * rp, 1.0 / sqrt(omega));
-    s = pw_check_launch("k_beta");
+    c->proj_ns = sqrt(8.0 * pow(M_PI, 1.5) * rp * rp * rp);
+    c->proj_np = sqrt(16.0 * pow(M_PI, 1.5) * rp * rp * rp * rp * rp);
+    for (int ax = 0; ax < 3; ++ax) c->Mext[ax] = M[ax];
+    acc += tmp;
+    s = pw_beta_chunk(c, 0, d->natom, c->d_beta, st);
     cudaStreamSynchronize(st);
-    cudaFree(dm); cudaFree(dpx); cudaFree(dpy); cudaFree(dpz);
     if (s != PW_OK) { pw_destroy_cell(c); return s; }
   }
 #undef UP
@@ -381,5 +392,34 @@ extern "C" pw_status pw_cell_sizes(const pw_cell *c, int *nproj, size_t *bytes) 
 extern "C" pw_status pw_cell_set_precision(pw_cell *c, int p) {
   if (!c || (p != PW_FP64 && p != PW_MIXED)) return PW_ERR_ARG;
   c->precision = p;
+  return PW_OK;
+}
+
+extern "C" pw_status pw_cell_set_projectors(pw_cell *c, int onthefly, void *stream) {
+  if (!c || (onthefly != 0 && onthefly != 1)) return PW_ERR_ARG;
+  if (c->natom == 0 || onthefly == c->proj_onthefly) return PW_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  PW_CUDA(cudaStreamSynchronize(st));
+  // the stored split operands of beta go either way (rebuilt on first use)
+  pw_tc_operand **ops[] = {&c->op_beta_rows, &c->op_beta_t};
+  for (pw_tc_operand **o : ops)
+    if (*o) { pw_tc_operand_free(*o); delete *o; *o = nullptr; }
+  if (onthefly) {
+    cudaFree(c->d_beta);
+    c->d_beta = nullptr;
+    c->proj_onthefly = 1;
+    return PW_OK;
+  }
+  if (cudaMalloc(&c->d_beta, (size_t)c->npw * c->nproj * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    c->d_beta = nullptr;
+    return PW_ERR_OOM;
+  }
+  PW_TRY(pw_beta_chunk(c, 0, c->natom, c->d_beta, st));
+  PW_CUDA(cudaStreamSynchronize(st));
+  cudaFree(c->d_bchunk);
+  c->d_bchunk = nullptr;
+  c->bchunk_bytes = 0;
+  c->proj_onthefly = 0;
   return PW_OK;
 }

@@ -14,6 +14,8 @@ times after one warm-up):
               --n 3456 gives the Si-512 Rayleigh-Ritz order
   hpsi512     FP64 H psi on 16 bands of the Si 512-atom cell (grid 96^3)
   hpsi512mix  mixed-precision H psi on --nb bands (default 1152) of the same cell
+  projmodes   H psi of the Si-512 cell with resident and with on-the-fly
+              projectors: mixed on 1,152 bands, FP64 on 64 (CUDA-event times)
 """
 from __future__ import annotations
 
@@ -92,6 +94,25 @@ def main():
             pw.pw_apply_H(cell.h, x, y)
         torch.cuda.synchronize()
         print("hpsi512mix done")
+    elif a.case == "projmodes":
+        ci = synth.cell_inputs("Si", 4, 0)
+        for prec, nb in (("mixed", 1152), ("fp64", 64)):
+            cell = pw.Cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], 10.0, precision=prec)
+            x = pw.new_block(cell.npw, nb)
+            x.copy_(torch.from_numpy(synth.draw_x0(0, 512, cell.npw, nb)))
+            y = pw.new_block(cell.npw, nb)
+            for mode in (False, True):
+                pw.pw_cell_set_projectors(cell.h, mode)
+                pw.pw_apply_H(cell.h, x, y)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(a.reps):
+                    pw.pw_apply_H(cell.h, x, y)
+                e1.record()
+                torch.cuda.synchronize()
+                print(f"projmodes {prec} nb={nb} {'on-the-fly' if mode else 'resident'}: "
+                      f"{e0.elapsed_time(e1) / a.reps:.1f} ms per H psi")
+            cell.close()
     else:
         raise SystemExit(f"unknown case {a.case}")
 

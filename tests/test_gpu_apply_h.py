@@ -122,3 +122,26 @@ def test_apply_h_grid_sizes(N):
             x = synth.draw_x0(7, 8, orc.npw, 3)
             ref = O.apply_H(orc, x)
         assert rel(_run(lib, x), ref) < tol, (N, prec)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_projectors_on_the_fly(prec, tol):
+    # beta regenerated in atom chunks (the 512-atom cell needs several 256 MB
+    # chunks) gives the same H psi as the resident projectors and the oracle
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 4, 10.0, precision=prec)
+    x = synth.draw_x0(21, 512, orc.npw, 12)
+    stored = _run(lib, x)
+    pw.pw_cell_set_projectors(lib.h, True)
+    otf = _run(lib, x)
+    for j in (0, 11):
+        ref = O.apply_H(orc, x[:, j:j + 1])[:, 0]
+        assert rel(otf[:, j], ref) < tol
+    assert rel(otf, stored) < (1e-13 if prec == "fp64" else 1e-6)
+    # no-allocation entry refuses a cell without resident projectors
+    from paper_2406_10765_gb300 import binding as B
+    psi = to_dev(x[:, :2])
+    out = torch.empty_like(psi)
+    assert B._apply_na(lib.h, B._dptr(psi), orc.npw, 2, B._dptr(out), B._stream(None)) == B.PW_ERR_ARG
+    pw.pw_cell_set_projectors(lib.h, False)
+    assert rel(_run(lib, x), stored) < (1e-15 if prec == "fp64" else 1e-12)
