@@ -49,11 +49,10 @@ static pw_status nonlocal_tc(pw_cell *c, const double2 *psi, int ld, int nb, dou
   return pw_tc_gemm(c->op_beta_t, c->npw, c->op_db, 2 * nb, hpsi, ld, 1, 1, 0, c->d_tc_err, st);
 }
 
-// Projectors generated on the fly: atoms in chunks whose beta columns fit a
-// bounded buffer; each chunk's contribution beta_c (D_c o beta_c^H psi) is
-// added to hpsi in chunk order.  The same arithmetic as the stored-beta path
-// per projector (FP64 GEMMs, or split-FP16 tensor-core products of the
-// chunk), with beta regenerated each call instead of kept resident.
+// Projectors generated on the fly into a bounded buffer instead of kept
+// resident.  FP64: chunks of atoms, each adding beta_c (D_c o beta_c^H psi).
+// Mixed: chunks of plane waves, so every tensor-core product keeps all
+// projectors (B accumulated over chunks in FP64, then hpsi_c += beta_c (D B)).
 constexpr size_t BCHUNK_BYTES = 256u << 20;
 static pw_status nonlocal_onthefly(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
                                    int precision, cudaStream_t st) {
@@ -61,15 +60,18 @@ static pw_status nonlocal_onthefly(pw_cell *c, const double2 *psi, int ld, int n
   const int ca = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->natom,
                                                             BCHUNK_BYTES / ((size_t)npw * 4 * sizeof(double2))));
   const int npc = 4 * ca;
-  PW_TRY(pw_ensure((void **)&c->d_bchunk, &c->bchunk_bytes, (size_t)npw * npc * sizeof(double2)));
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
-  const bool mixed = precision == PW_MIXED;
-  if (mixed) {
+  if (precision == PW_MIXED) {
+    // mixed: chunks of plane waves (every projector in each chunk keeps the
+    // tensor-core products wide), beta generated in FP32 twice per call
+    const int np = c->nproj;
+    const int gc = (int)std::max<size_t>(64, std::min<size_t>((size_t)npw, BCHUNK_BYTES / ((size_t)np * sizeof(double2))));
+    PW_TRY(pw_ensure((void **)&c->d_bchunk, &c->bchunk_bytes, (size_t)gc * np * sizeof(double2)));
     if (!c->op_bc_rows) {
       c->op_bc_rows = new pw_tc_operand();
       c->op_bc_t = new pw_tc_operand();
-      c->op_psi = c->op_psi ? c->op_psi : new pw_tc_operand();
-      c->op_db = c->op_db ? c->op_db : new pw_tc_operand();
+      c->op_psi_c = new pw_tc_operand();
+      if (!c->op_db) c->op_db = new pw_tc_operand();
       size_t cur = 0;
       if (!c->d_tc_err) {
         PW_TRY(pw_ensure((void **)&c->d_tc_err, &cur, 16));
@@ -78,9 +80,31 @@ static pw_status nonlocal_onthefly(pw_cell *c, const double2 *psi, int ld, int n
       cur = 0;
       if (!c->d_rmax) PW_TRY(pw_ensure((void **)&c->d_rmax, &cur, (size_t)npw * sizeof(float)));
     }
-    PW_TRY(pw_tc_operand_alloc(c->op_psi, nb, 2 * npw, st));
-    PW_TRY(pw_tc_split_rows(psi, ld, npw, nb, 0, nullptr, c->op_psi, st));
-  } else {
+    // B = sum over chunks of beta_c^H psi_c (FP64 accumulation)
+    for (int g0 = 0; g0 < npw; g0 += gc) {
+      const int ng = std::min(gc, npw - g0);
+      PW_TRY(pw_beta_rows_f32(c, g0, ng, c->d_bchunk, st));
+      PW_TRY(pw_tc_operand_alloc(c->op_bc_rows, 2 * np, 2 * ng, st));
+      PW_TRY(pw_tc_operand_alloc(c->op_psi_c, nb, 2 * ng, st));
+      PW_TRY(pw_tc_split_rows(c->d_bchunk, ng, ng, np, 1, nullptr, c->op_bc_rows, st));
+      PW_TRY(pw_tc_split_rows(psi + g0, ld, ng, nb, 0, nullptr, c->op_psi_c, st));
+      PW_TRY(pw_tc_gemm(c->op_bc_rows, 2 * np, c->op_psi_c, nb, c->d_B, np, 0, g0 > 0, 0, c->d_tc_err, st));
+    }
+    // hpsi_c += beta_c (D o B)
+    PW_TRY(pw_tc_operand_alloc(c->op_db, 2 * nb, 2 * np, st));
+    PW_TRY(pw_tc_split_coef(c->d_B, np, np, nb, c->d_D, c->op_db, st));
+    for (int g0 = 0; g0 < npw; g0 += gc) {
+      const int ng = std::min(gc, npw - g0);
+      PW_TRY(pw_beta_rows_f32(c, g0, ng, c->d_bchunk, st));
+      PW_TRY(pw_tc_operand_alloc(c->op_bc_t, ng, 2 * np, st));
+      PW_TRY(pw_tc_split_trans(c->d_bchunk, ng, ng, np, c->d_rmax, c->op_bc_t, st));
+      PW_TRY(pw_tc_gemm(c->op_bc_t, ng, c->op_db, 2 * nb, hpsi + g0, ld, 1, 1, 0, c->d_tc_err, st));
+    }
+    return PW_OK;
+  }
+  // FP64: chunks of atoms, beta generated in FP64 (the operator of the resident path)
+  PW_TRY(pw_ensure((void **)&c->d_bchunk, &c->bchunk_bytes, (size_t)npw * npc * sizeof(double2)));
+  {
     size_t ws = std::max(pw_zgemm_ws_elems(npc, nb, npw), pw_zgemm_ws_elems(npw, nb, npc));
     size_t wcur = c->gemm_ws_elems * sizeof(double2);
     PW_TRY(pw_ensure((void **)&c->d_gemm_ws, &wcur, ws * sizeof(double2)));
@@ -89,24 +113,13 @@ static pw_status nonlocal_onthefly(pw_cell *c, const double2 *psi, int ld, int n
   for (int a0 = 0; a0 < c->natom; a0 += ca) {
     const int na = std::min(ca, c->natom - a0), np = 4 * na;
     PW_TRY(pw_beta_chunk(c, a0, na, c->d_bchunk, st));
-    if (mixed) {
-      PW_TRY(pw_tc_operand_alloc(c->op_bc_rows, 2 * np, 2 * npw, st));
-      PW_TRY(pw_tc_operand_alloc(c->op_bc_t, npw, 2 * np, st));
-      PW_TRY(pw_tc_operand_alloc(c->op_db, 2 * nb, 2 * np, st));
-      PW_TRY(pw_tc_split_rows(c->d_bchunk, npw, npw, np, 1, nullptr, c->op_bc_rows, st));
-      PW_TRY(pw_tc_split_trans(c->d_bchunk, npw, npw, np, c->d_rmax, c->op_bc_t, st));
-      PW_TRY(pw_tc_gemm(c->op_bc_rows, 2 * np, c->op_psi, nb, c->d_B, np, 0, 0, 0, c->d_tc_err, st));
-      PW_TRY(pw_tc_split_coef(c->d_B, np, np, nb, c->d_D + 4 * a0, c->op_db, st));
-      PW_TRY(pw_tc_gemm(c->op_bc_t, npw, c->op_db, 2 * nb, hpsi, ld, 1, 1, 0, c->d_tc_err, st));
-    } else {
-      PW_TRY(pw_zgemm('C', 'N', np, nb, npw, one, c->d_bchunk, npw, psi, ld, zero, c->d_B, np,
-                      c->d_gemm_ws, c->gemm_ws_elems, st));
-      pw_count_launch();
-      k_scale_rows<<<(unsigned)(((long)np * nb + 255) / 256), 256, 0, st>>>(c->d_B, np, nb, c->d_D + 4 * a0);
-      PW_TRY(pw_check_launch("scale_rows"));
-      PW_TRY(pw_zgemm('N', 'N', npw, nb, np, one, c->d_bchunk, npw, c->d_B, np, one, hpsi, ld, c->d_gemm_ws,
-                      c->gemm_ws_elems, st));
-    }
+    PW_TRY(pw_zgemm('C', 'N', np, nb, npw, one, c->d_bchunk, npw, psi, ld, zero, c->d_B, np,
+                    c->d_gemm_ws, c->gemm_ws_elems, st));
+    pw_count_launch();
+    k_scale_rows<<<(unsigned)(((long)np * nb + 255) / 256), 256, 0, st>>>(c->d_B, np, nb, c->d_D + 4 * a0);
+    PW_TRY(pw_check_launch("scale_rows"));
+    PW_TRY(pw_zgemm('N', 'N', npw, nb, np, one, c->d_bchunk, npw, c->d_B, np, one, hpsi, ld, c->d_gemm_ws,
+                    c->gemm_ws_elems, st));
   }
   return PW_OK;
 }

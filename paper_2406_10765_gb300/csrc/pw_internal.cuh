@@ -86,7 +86,7 @@ struct pw_cell {
   double proj_ns = 0, proj_np = 0;
   int proj_onthefly = 0;      // 1: beta generated per chunk of atoms in each H psi
   double2 *d_bchunk = nullptr; size_t bchunk_bytes = 0;
-  struct pw_tc_operand *op_bc_rows = nullptr, *op_bc_t = nullptr;
+  struct pw_tc_operand *op_bc_rows = nullptr, *op_bc_t = nullptr, *op_psi_c = nullptr;
   double *d_D = nullptr;      // nproj
   pw_fft_axis ax[3];
   // apply_H workspace (grown on demand)
@@ -108,6 +108,8 @@ struct pw_cell {
 
 // beta columns 4 a0 .. 4 (a0 + na) - 1 into out (npw x 4 na, ld npw)
 pw_status pw_beta_chunk(pw_cell *c, int a0, int na, double2 *out, cudaStream_t st);
+// beta rows g0 .. g0+ng-1 of every projector, FP32 arithmetic, into out (ng x nproj, ld ng)
+pw_status pw_beta_rows_f32(pw_cell *c, int g0, int ng, double2 *out, cudaStream_t st);
 
 // apply_H pieces
 pw_status pw_apply_local(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,

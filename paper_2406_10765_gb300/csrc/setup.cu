@@ -145,6 +145,47 @@ __global__ void k_beta(double2 *beta, const int *mvec, const double2 *phx, const
   col[(long)3 * npw] = make_double2(f * Gz * p.y, -f * Gz * p.x);
 }
 
+// beta rows g0 .. g0 + ng - 1 for all projectors, in FP32 arithmetic
+// (for the split-FP16 products, which keep ~22 bits): out[(g - g0) + p ng]
+__global__ void k_beta_rows_f32(double2 *out, const int *mvec, const double2 *phx, const double2 *phy,
+                                const double2 *phz, int Mx, int My, int Mz, int g0, int ng, int natom,
+                                float gx, float gy, float gz, float ns, float np, float rp2,
+                                float inv_sqrt_omega) {
+  const int gl = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (gl >= ng || a >= natom) return;
+  const int g = g0 + gl;
+  const int mx = mvec[3 * g], my = mvec[3 * g + 1], mz = mvec[3 * g + 2];
+  const float Gx = gx * mx, Gy = gy * my, Gz = gz * mz;
+  const float g2 = Gx * Gx + Gy * Gy + Gz * Gz;
+  const float rad = expf(-0.5f * g2 * rp2) * inv_sqrt_omega;
+  const double2 px = phx[(long)a * (2 * Mx + 1) + mx + Mx], py = phy[(long)a * (2 * My + 1) + my + My],
+                pz = phz[(long)a * (2 * Mz + 1) + mz + Mz];
+  const float2 qx = make_float2((float)px.x, (float)px.y), qy = make_float2((float)py.x, (float)py.y),
+               qz = make_float2((float)pz.x, (float)pz.y);
+  const float2 p = cmul(cmul(qx, qy), qz);
+  double2 *col = out + (long)(4 * a) * ng + gl;
+  col[0] = make_double2(ns * rad * p.x, ns * rad * p.y);
+  const float f = np * rad;
+  col[(long)ng] = make_double2(f * Gx * p.y, -f * Gx * p.x);
+  col[(long)2 * ng] = make_double2(f * Gy * p.y, -f * Gy * p.x);
+  col[(long)3 * ng] = make_double2(f * Gz * p.y, -f * Gz * p.x);
+}
+
+pw_status pw_beta_rows_f32(pw_cell *c, int g0, int ng, double2 *out, cudaStream_t st) {
+  if (ng <= 0) return PW_OK;
+  const double twopi = 2.0 * M_PI;
+  const double omega = c->L[0] * c->L[1] * c->L[2];
+  dim3 grid((ng + 127) / 128, c->natom);
+  pw_count_launch();
+  k_beta_rows_f32<<<grid, 128, 0, st>>>(out, c->d_m, c->d_ph[0], c->d_ph[1], c->d_ph[2], c->Mext[0],
+                                        c->Mext[1], c->Mext[2], g0, ng, c->natom, (float)(twopi / c->L[0]),
+                                        (float)(twopi / c->L[1]), (float)(twopi / c->L[2]), (float)c->proj_ns,
+                                        (float)c->proj_np, (float)(c->pwidth * c->pwidth),
+                                        (float)(1.0 / sqrt(omega)));
+  return pw_check_launch("k_beta_rows_f32");
+}
+
 pw_status pw_beta_chunk(pw_cell *c, int a0, int na, double2 *out, cudaStream_t st) {
   if (na <= 0) return PW_OK;
   const double twopi = 2.0 * M_PI;
@@ -164,7 +205,7 @@ pw_status pw_beta_chunk(pw_cell *c, int a0, int na, double2 *out, cudaStream_t s
 extern "C" void pw_destroy_cell(pw_cell *c) {
   if (!c) return;
   pw_tc_operand **ops[] = {&c->op_beta_rows, &c->op_beta_t, &c->op_psi, &c->op_db, &c->op_bc_rows,
-                           &c->op_bc_t};
+                           &c->op_bc_t, &c->op_psi_c};
   for (pw_tc_operand **o : ops)
     if (*o) { pw_tc_operand_free(*o); delete *o; *o = nullptr; }
   if (c->d_rmax) cudaFree(c->d_rmax);
