@@ -145,3 +145,29 @@ def test_projectors_on_the_fly(prec, tol):
     assert B._apply_na(lib.h, B._dptr(psi), orc.npw, 2, B._dptr(out), B._stream(None)) == B.PW_ERR_ARG
     pw.pw_cell_set_projectors(lib.h, False)
     assert rel(_run(lib, x), stored) < (1e-15 if prec == "fp64" else 1e-12)
+
+
+def test_apply_h_si1728_mixed_sampled():
+    # the 1,728-atom cell (npw 251,967, grid 128^3, 6,912 projectors) in mixed
+    # precision with projectors generated on the fly, on sampled bands against
+    # the oracle's operator (its projectors formed 64 atoms at a time)
+    import paper_2406_10765_gb300 as pw
+    ci = synth.cell_inputs("Si", 6, 0)
+    lib = pw.Cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], 8.0, precision="mixed")
+    assert lib.npw == 251967 and lib.grid == (128, 128, 128)
+    pw.pw_cell_set_projectors(lib.h, True)
+    x = synth.draw_x0(0, 1728, lib.npw, 3)
+    got = _run(lib, x)
+    Ls = np.full(3, float(ci["L"]) if np.ndim(ci["L"]) == 0 else ci["L"][0])
+    m = O.sphere(8.0, Ls)
+    assert np.array_equal(lib.m, m)
+    Ns = (128, 128, 128)
+    V = O.vloc_grid(Ls, Ns, ci["tau"], ci["depth"], 1.2)
+    orc = O.Cell(Ls=Ls, Ns=Ns, ecut=8.0, m=m, kin=O.kinetic(m, Ls), V=V,
+                 beta=np.zeros((m.shape[0], 0), complex), D=np.zeros(0))
+    ref = orc.kin[:, None] * x + O.apply_local(orc, x)
+    D = np.asarray(ci["dkb"], float).reshape(-1)
+    for a0 in range(0, len(ci["tau"]), 64):
+        b = O.projectors(m, Ls, ci["tau"][a0:a0 + 64], 1.2)
+        ref += b @ (D[4 * a0:4 * a0 + b.shape[1], None] * (b.conj().T @ x))
+    assert rel(got, ref) < 1e-5
