@@ -144,6 +144,10 @@ typedef struct {
   const void *x0;       /* optional complex128 npw x nbands start (ld = npw), host
                            or device memory */
   int precision;        /* PW_FP64 or PW_MIXED */
+  int chunk_rows;       /* PW_MIXED: plane-wave rows per chunk of the tall
+                           split-FP16 products (Gram, S M, rotations); 0 picks
+                           chunks whose split operands stay under ~8 GB.  Bounds
+                           the solver's scratch; results agree to rounding. */
 } pw_solve_opts;
 
 typedef struct {

@@ -48,6 +48,7 @@ struct pw_solver {
   pw_tc_operand opSA, opSB, opHSB, opST, opHST, opC, opCP, opM;
   double2 *Mx = nullptr;     // mixed: d o L^-H of the current Gram (3nb x 3nb)
   bool st_split_valid = false;   // opST holds the split of the current S
+  int chunk_rows = 0;            // rows per chunk of the tall split products (0: automatic)
   float *rmax = nullptr;
   int *d_err = nullptr;
   double2 *Cz = nullptr;
@@ -234,6 +235,53 @@ pw_status gemm(pw_solver *s, char oa, char ob, int m, int n, int k, const double
 // information in mixed precision.
 double piv_tol(const pw_solver *s) { return s->precision == PW_MIXED ? 1e-6 : 1e-14; }
 
+// Plane-wave rows per chunk of the tall split-FP16 operands: the largest
+// chunk operand (2 ns rows x 2 ng K, two FP16 slices) stays under ~8 GB, so
+// the 1,728-atom cell fits in HBM; smaller cells take one chunk.
+int tall_chunk(const pw_solver *s, int ns) {
+  if (s->chunk_rows > 0) return std::min(s->chunk_rows, s->npw);
+  const size_t cap = (size_t)8 << 30;
+  size_t ng = cap / ((size_t)2 * ns * 2 * 2 * 2);
+  ng = std::max<size_t>(1024, ng / 64 * 64);
+  return (int)std::min<size_t>(ng, (size_t)s->npw);
+}
+
+// C (ns x ns, ld ldc, Hermitian) = X^H Y over the plane-wave rows, chunk by
+// chunk, accumulated in FP64 (opSA, opSB as scratch)
+pw_status tall_gram(pw_solver *s, const double2 *X, const double2 *Y, int ns, double2 *C, int ldc) {
+  const int npw = s->npw, gc = tall_chunk(s, ns);
+  for (int g0 = 0; g0 < npw; g0 += gc) {
+    const int ng = std::min(gc, npw - g0);
+    PW_TRY(pw_tc_operand_alloc(&s->opSA, 2 * ns, 2 * ng, s->st));
+    PW_TRY(pw_tc_operand_alloc(&s->opSB, ns, 2 * ng, s->st));
+    PW_TRY(pw_tc_split_rows(X + g0, npw, ng, ns, 1, nullptr, &s->opSA, s->st));
+    PW_TRY(pw_tc_split_rows(Y + g0, npw, ng, ns, 0, nullptr, &s->opSB, s->st));
+    PW_TRY(pw_tc_gemm(&s->opSA, 2 * ns, &s->opSB, ns, C, ldc, 0, g0 > 0, 1, s->d_err, s->st));
+  }
+  return PW_OK;
+}
+
+// out (npw rows, ld npw) = X (npw x ns) times the split coefficients coef,
+// row chunk by row chunk; X's rows are split into op (skipped when op already
+// holds the split of all of X).  coef2 (optional): out2 = X coef2 from the
+// same split chunk.
+pw_status tall_times_coef(pw_solver *s, const double2 *X, int ns, pw_tc_operand *op, bool presplit,
+                          const pw_tc_operand *coef, int ncols2, double2 *out, int kb_lo, int tri,
+                          const pw_tc_operand *coef2 = nullptr, double2 *out2 = nullptr, int kb_lo2 = 0) {
+  const int npw = s->npw, gc = tall_chunk(s, ns);
+  for (int g0 = 0; g0 < npw; g0 += gc) {
+    const int ng = std::min(gc, npw - g0);
+    if (!(presplit && gc >= npw)) {
+      PW_TRY(pw_tc_operand_alloc(op, ng, 2 * ns, s->st));
+      PW_TRY(pw_tc_split_trans(X + g0, npw, ng, ns, s->rmax, op, s->st));
+    }
+    PW_TRY(pw_tc_gemm(op, ng, coef, ncols2, out + g0, npw, 1, 0, 0, s->d_err, s->st, kb_lo, tri));
+    if (coef2)
+      PW_TRY(pw_tc_gemm(op, ng, coef2, ncols2, out2 + g0, npw, 1, 0, 0, s->d_err, s->st, kb_lo2));
+  }
+  return PW_OK;
+}
+
 // Mixed precision: from the Gram in s->G (order ns), factor G in FP64
 // (scaling, Cholesky, L^-1, M = d L^-H), orthonormalise the basis on the
 // tensor cores (S~ = S M, H S~ = H S M into S2, HS2), form A~ = S~^H H S~
@@ -242,19 +290,14 @@ pw_status rr_mixed_from_gram(pw_solver *s, int ns, int *chol_ok) {
   const int npw = s->npw, nb = s->nb, ldg = 3 * nb;
   PW_TRY(pw_rr_factor(&s->dws, ns, s->G, ldg, s->Mx, ldg, chol_ok, s->st, piv_tol(s)));
   if (!*chol_ok) return PW_OK;
-  PW_TRY(pw_tc_operand_alloc(&s->opST, npw, 2 * ns, s->st));
-  PW_TRY(pw_tc_operand_alloc(&s->opHST, npw, 2 * ns, s->st));
   PW_TRY(pw_tc_operand_alloc(&s->opM, 2 * ns, 2 * ns, s->st));
-  PW_TRY(pw_tc_split_trans(s->S, npw, npw, ns, s->rmax, &s->opST, s->st));
-  s->st_split_valid = true;
-  PW_TRY(pw_tc_split_trans(s->HS, npw, npw, ns, s->rmax, &s->opHST, s->st));
   PW_TRY(pw_tc_split_coef(s->Mx, ldg, ns, ns, nullptr, &s->opM, s->st));
-  // M is upper triangular: output columns j need K rows t <= j only
-  PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opM, 2 * ns, s->S2, npw, 1, 0, 0, s->d_err, s->st, 0, 1));
-  PW_TRY(pw_tc_gemm(&s->opHST, npw, &s->opM, 2 * ns, s->HS2, npw, 1, 0, 0, s->d_err, s->st, 0, 1));
-  PW_TRY(pw_tc_split_rows(s->S2, npw, npw, ns, 1, nullptr, &s->opSA, s->st));
-  PW_TRY(pw_tc_split_rows(s->HS2, npw, npw, ns, 0, nullptr, &s->opHSB, s->st));
-  PW_TRY(pw_tc_gemm(&s->opSA, 2 * ns, &s->opHSB, ns, s->A, ldg, 0, 0, 1, s->d_err, s->st));
+  // S~ = S M, H S~ = HS M; M is upper triangular: output columns j need K rows t <= j only
+  PW_TRY(tall_times_coef(s, s->S, ns, &s->opST, false, &s->opM, 2 * ns, s->S2, 0, 1));
+  s->st_split_valid = tall_chunk(s, ns) >= npw;   // opST holds the split of all of S
+  PW_TRY(tall_times_coef(s, s->HS, ns, &s->opHST, false, &s->opM, 2 * ns, s->HS2, 0, 1));
+  // A~ = S~^H (H S~)
+  PW_TRY(tall_gram(s, s->S2, s->HS2, ns, s->A, ldg));
   if (s->fresh_h) {
     // X' = S~ Y on the tensor cores; only the P part of C = M Y in FP64
     s->ytilde = true;
@@ -269,13 +312,7 @@ pw_status subspace_rr(pw_solver *s, int ns, int *chol_ok) {
   const int ldg = 3 * s->nb;
   cudaEventRecord(s->ev[3], s->st);
   if (s->precision == PW_MIXED) {
-    const int npw = s->npw;
-    PW_TRY(pw_tc_operand_alloc(&s->opSA, 2 * ns, 2 * npw, s->st));
-    PW_TRY(pw_tc_operand_alloc(&s->opSB, ns, 2 * npw, s->st));
-    PW_TRY(pw_tc_operand_alloc(&s->opHSB, ns, 2 * npw, s->st));
-    PW_TRY(pw_tc_split_rows(s->S, npw, npw, ns, 1, nullptr, &s->opSA, s->st));
-    PW_TRY(pw_tc_split_rows(s->S, npw, npw, ns, 0, nullptr, &s->opSB, s->st));
-    PW_TRY(pw_tc_gemm(&s->opSA, 2 * ns, &s->opSB, ns, s->G, ldg, 0, 0, 1, s->d_err, s->st));
+    PW_TRY(tall_gram(s, s->S, s->S, ns, s->G, ldg));
     cudaEventRecord(s->ev[4], s->st);
     return rr_mixed_from_gram(s, ns, chol_ok);
   }
@@ -321,42 +358,36 @@ pw_status rotate(pw_solver *s, int ns, bool with_p) {
     s->ytilde = false;
     PW_TRY(pw_tc_operand_alloc(&s->opC, 2 * nb, 2 * ns, s->st));
     if (with_p) {
-      // P' = S C_P, C_P = C with its first nb rows zero (opST: the split of S)
+      // P' = S C_P, C_P = C with its first nb rows zero (opST may still hold
+      // the split of S); the first nb coefficient rows are zero: skip their K blocks
       PW_TRY(pw_tc_operand_alloc(&s->opCP, 2 * nb, 2 * ns, s->st));
       PW_TRY(pw_tc_split_coef(s->C, n3, ns, nb, nullptr, &s->opCP, s->st));
-      // the first nb coefficient rows are zero: skip their K blocks
-      PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opCP, 2 * nb, s->P, npw, 1, 0, 0, s->d_err, s->st,
-                        (2 * nb) / 64));
+      PW_TRY(tall_times_coef(s, s->S, ns, &s->opST, s->st_split_valid, &s->opCP, 2 * nb, s->P,
+                             (2 * nb) / 64, 0));
     }
-    // X' = S~ Y into HS2 (H S~ is no longer needed), S~ re-split over opST
-    PW_TRY(pw_tc_split_trans(s->S2, npw, npw, ns, s->rmax, &s->opST, s->st));
-    s->st_split_valid = false;
+    // X' = S~ Y into HS2 (H S~ is no longer needed)
     PW_TRY(pw_tc_split_coef(s->dws.Y, ns, ns, nb, nullptr, &s->opC, s->st));
-    PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opC, 2 * nb, s->HS2, npw, 1, 0, 0, s->d_err, s->st));
+    PW_TRY(tall_times_coef(s, s->S2, ns, &s->opST, false, &s->opC, 2 * nb, s->HS2, 0, 0));
+    s->st_split_valid = false;
     s->x_in_hs2 = true;
     return PW_OK;
   }
   if (s->precision == PW_MIXED) {
-    PW_TRY(pw_tc_operand_alloc(&s->opST, npw, 2 * ns, s->st));
-    PW_TRY(pw_tc_operand_alloc(&s->opHST, npw, 2 * ns, s->st));
     PW_TRY(pw_tc_operand_alloc(&s->opC, 2 * nb, 2 * ns, s->st));
-    if (!s->st_split_valid || s->opST.kpad != pw_tc_kpad(2 * ns))
-      PW_TRY(pw_tc_split_trans(s->S, npw, npw, ns, s->rmax, &s->opST, s->st));
-    if (!s->fresh_h) PW_TRY(pw_tc_split_trans(s->HS, npw, npw, ns, s->rmax, &s->opHST, s->st));
     PW_TRY(pw_tc_split_coef(s->C, n3, ns, nb, nullptr, &s->opC, s->st));
-    PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opC, 2 * nb, s->S2, npw, 1, 0, 0, s->d_err, s->st));
-    if (!s->fresh_h)
-      PW_TRY(pw_tc_gemm(&s->opHST, npw, &s->opC, 2 * nb, s->HS2, npw, 1, 0, 0, s->d_err, s->st));
+    const pw_tc_operand *cp = nullptr;
     if (with_p) {
       pw_count_launch();
       k_zero_top_rows<<<(unsigned)(((long)ns * nb + 255) / 256), 256, 0, s->st>>>(s->C, n3, nb, ns, nb, s->Cz);
       PW_TRY(pw_check_launch("zero_top_rows"));
       PW_TRY(pw_tc_operand_alloc(&s->opCP, 2 * nb, 2 * ns, s->st));
       PW_TRY(pw_tc_split_coef(s->Cz, n3, ns, nb, nullptr, &s->opCP, s->st));
-      PW_TRY(pw_tc_gemm(&s->opST, npw, &s->opCP, 2 * nb, s->P, npw, 1, 0, 0, s->d_err, s->st));
-      if (!s->fresh_h)
-        PW_TRY(pw_tc_gemm(&s->opHST, npw, &s->opCP, 2 * nb, s->HP, npw, 1, 0, 0, s->d_err, s->st));
+      cp = &s->opCP;
     }
+    const bool pre = s->st_split_valid && s->opST.kpad == pw_tc_kpad(2 * ns);
+    PW_TRY(tall_times_coef(s, s->S, ns, &s->opST, pre, &s->opC, 2 * nb, s->S2, 0, 0, cp, s->P));
+    if (!s->fresh_h)
+      PW_TRY(tall_times_coef(s, s->HS, ns, &s->opHST, false, &s->opC, 2 * nb, s->HS2, 0, 0, cp, s->HP));
     return PW_OK;
   }
   if (with_p && ns > nb) {
@@ -439,7 +470,7 @@ extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, voi
   if (!out) return PW_ERR_ARG;
   *out = nullptr;
   if (!cell || !o || o->nbands < 1 || 3 * o->nbands > cell->npw || !(o->tol >= 0.0) ||
-      (o->precision != PW_FP64 && o->precision != PW_MIXED))
+      (o->precision != PW_FP64 && o->precision != PW_MIXED) || o->chunk_rows < 0)
     return PW_ERR_ARG;
   pw_solver *s = new pw_solver();
   s->cell = cell;
@@ -449,6 +480,7 @@ extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, voi
   s->maxit = o->maxit;
   s->precision = o->precision;
   s->fresh_h = o->precision == PW_MIXED;
+  s->chunk_rows = o->chunk_rows;
   s->st = (cudaStream_t)stream;
   const int nb = s->nb, npw = s->npw, n3 = 3 * nb;
   const size_t blk3 = (size_t)npw * n3 * 16, blk = (size_t)npw * nb * 16;

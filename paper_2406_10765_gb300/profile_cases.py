@@ -16,6 +16,11 @@ times after one warm-up):
   hpsi512mix  mixed-precision H psi on --nb bands (default 1152) of the same cell
   projmodes   H psi of the Si-512 cell with resident and with on-the-fly
               projectors: mixed on 1,152 bands, FP64 on 64 (CUDA-event times)
+  step1728mix the 1,728-atom cell (Ecut 8 Ha, grid 128^3, npw 251,967, 6,912
+              projectors generated on the fly), 3,840 bands in mixed
+              precision: solver creation and --reps LOBPCG steps with stage
+              times, device memory in use, and the Rayleigh-Ritz property
+              that no Ritz value rises.  Holds ~250 GB: not a profiler case.
 """
 from __future__ import annotations
 
@@ -57,6 +62,29 @@ def main():
             l1 = pw.pw_kernel_launches()
         print(f"{a.case}: npw {cell.npw}, last step {r.ms:.1f} ms, launches before it {l0}, "
               f"in it {l1 - l0}")
+        pw.pw_solver_destroy(s)
+    elif a.case == "step1728mix":
+        import time
+        ci = synth.cell_inputs("Si", 6, 0)
+        cell = pw.Cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], 8.0, precision="mixed")
+        pw.pw_cell_set_projectors(cell.h, True)
+        nb = 3840
+        t0 = time.time()
+        s = pw.pw_solver_create(cell.h, nb, tol=0.0, seed=0, precision="mixed")
+        free, total = torch.cuda.mem_get_info()
+        e0, r0 = pw.pw_solver_eigs(s, nb)
+        print(f"step1728mix: npw {cell.npw}, grid {cell.grid}, create {time.time() - t0:.1f} s, "
+              f"device in use {(total - free) / 2**30:.1f} GiB of {total / 2**30:.1f}")
+        print(f"  start: theta [{e0[0]:.6f}, {e0[-1]:.6f}], max resid {r0.max():.3e}")
+        for it in range(max(1, a.reps)):
+            r = pw.pw_subspace_step(cell.h, s)
+            e1, r1 = pw.pw_solver_eigs(s, nb)
+            print(f"  step {it + 1}: {r.ms:.0f} ms (resid {r.ms_resid:.0f}, hpsi {r.ms_hpsi:.0f} on "
+                  f"{r.hpsi_cols} cols, gram {r.ms_gram:.0f}, rr {r.ms_rr:.0f} "
+                  f"[{', '.join(f'{v:.0f}' for v in r.ms_rr_part)}], rot {r.ms_rot:.0f}), nsub {r.nsub}")
+            print(f"    theta [{e1[0]:.6f}, {e1[-1]:.6f}], max rise {np.max(e1 - e0):.3e}, "
+                  f"max resid {r1.max():.3e}, finite {bool(np.isfinite(e1).all())}")
+            e0 = e1
         pw.pw_solver_destroy(s)
     elif a.case == "tcgemm":
         k, m = 104415, 1152

@@ -84,3 +84,42 @@ def test_mixed_steps_track_oracle_si64():
     e, _ = pw.pw_solver_eigs(s, nb)
     assert np.abs(e - st.lam).max() < 1e-4
     pw.pw_solver_destroy(s)
+
+
+def test_mixed_chunked_tall_products_si64():
+    # the tall split-FP16 products (Gram, S M, A~, rotations) taken over
+    # plane-wave chunks of 1,000 rows (a ragged last chunk) follow the
+    # single-chunk solver and the oracle's FP64 steps
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 2, 10.0, precision="mixed")
+    nb = 144
+    x0 = synth.draw_x0(0, 64, orc.npw, nb)
+    assert orc.npw % 1000 != 0 and orc.npw > 5000
+    st = O.lobpcg_init(orc, x0)
+    a = pw.pw_solver_create(lib.h, nb, tol=0.0, x0=x0, precision="mixed")
+    b = pw.pw_solver_create(lib.h, nb, tol=0.0, x0=x0, precision="mixed", chunk_rows=1000)
+    for _ in range(3):
+        st = O.lobpcg_step(orc, st)
+        pw.pw_subspace_step(lib.h, a)
+        pw.pw_subspace_step(lib.h, b)
+    ea, _ = pw.pw_solver_eigs(a, nb)
+    eb, rb = pw.pw_solver_eigs(b, nb)
+    assert np.abs(eb - ea).max() < 1e-6
+    assert np.abs(eb - st.lam).max() < 1e-4
+    assert np.isfinite(rb).all()
+    pw.pw_solver_destroy(a)
+    pw.pw_solver_destroy(b)
+
+
+def test_mixed_chunked_eigsolve_si8():
+    # a full mixed solve with chunks of 250 plane-wave rows meets the same
+    # targets against the stored FP64 eigenvalues
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 1, 10.0)
+    nb = 24
+    ref = np.loadtxt(os.path.join(GOLD, "si8_ecut10_seed0_eigs.txt"))[:nb]
+    eig, rep, st = pw.pw_eigsolve(lib.h, nb, tol=5e-6, maxit=300, seed=0, precision="mixed",
+                                  chunk_rows=250)
+    assert np.abs(eig - ref).max() <= 1e-6
+    assert rep.max_resid <= 1e-5
+    assert rep.orth_err <= 1e-10
