@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--e2e-maxit", type=int, default=None,
                     help="step limit of the end-to-end solve (default 200: a full solve)")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default FFT plan and K split instead of the autotuner's")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-rate", type=float, default=0.5)
     return ap.parse_args()
@@ -323,6 +325,17 @@ def run_gpu(args):
     cell = pw.Cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], wl["ecut"], precision=args.precision)
     nb = wl["nb"]
     stream = torch.cuda.current_stream()
+    tune = None
+    if not args.no_autotune:
+        # untimed set-up: the FFT plan of this cell, then per-shape K splits of
+        # the tensor-core products on their first call (solver creation and
+        # the first warm-up step)
+        fr = pw.pw_cell_autotune_fft(cell.h, min(nb, 256), precision=args.precision)
+        pw.pw_autotune_gemm(1)
+        tune = {"fft": {"L": fr.best.L, "R": fr.best.R, "batch_mib": fr.best.batch_bytes >> 20,
+                        "ms_best": fr.ms_best, "ms_default": fr.ms_default,
+                        "default": [fr.dflt.L, fr.dflt.R, fr.dflt.batch_bytes >> 20],
+                        "candidates": fr.ncand, "bands": min(nb, 256)}}
     solver = pw.pw_solver_create(cell.h, nb, tol=0.0, seed=0, precision=args.precision)
     for _ in range(args.warmup):
         pw.pw_subspace_step(cell.h, solver)
@@ -369,6 +382,11 @@ def run_gpu(args):
                       "parallelism": f"replicas x{world}"},
            "roofline": roof, "gpu_launches": launches, "launches_before_timed": launches0,
            "clocks": clk}
+    if tune is not None:
+        lines = [ln for ln in pw.pw_autotune_gemm_table().splitlines() if ln]
+        tune["gemm_shapes_tuned"] = len(lines)
+        tune["gemm_split_gt1"] = [ln for ln in lines if "split=1 " not in ln]
+        out["config"]["autotune"] = tune
     pw.pw_solver_destroy(solver)
 
     if args.precision == "mixed" and not args.no_fp64:

@@ -354,6 +354,66 @@ pw_status pw_heev(int n, int nb, void *A, double *w, void *Y, void *stream);
 pw_status pw_zgemm_tc(char opA, int m, int n, int k, const void *A, int lda, const void *B,
                       int ldb, double beta, void *C, int ldc, void *stream);
 
+/* ---- Autotuner: the plan and tile-shape choices of the hot kernels ----
+ * Sec. III-D picks, for each execution step, the process count that runs it
+ * fastest among the candidates that fit in memory.  On one GPU the matching
+ * choices are how a step's work is cut into kernel work units: the
+ * factorisation of the FFT lines and the band batch of the local part of
+ * H psi, and the K extent of the tensor-core GEMM tiles. */
+
+/* A plan for the local part of H psi: register line FFTs with N = L R per
+ * axis (L lanes, R values per lane), or L = R = 0 for the Stockham passes in
+ * shared memory; batch_bytes: z-pencil bytes per batch of bands (0: 64 MiB). */
+typedef struct {
+  int L, R;
+  size_t batch_bytes;
+} pw_fft_plan;
+
+/* Register line-FFT plans compiled for grid size n: writes up to `max` of
+ * them to `plans` (may be NULL) and returns how many exist (0: the grid size
+ * runs on the Stockham passes only). */
+int pw_fft_plans(int n, pw_fft_plan *plans, int max);
+
+/* The cell's plan for one precision (PW_FP64, or PW_MIXED for its FP32
+ * FFTs).  Set: L = R = 0 selects the Stockham passes.  Results agree to
+ * rounding across plans.  Errors: PW_ERR_ARG (NULL, unknown precision, or an
+ * (L, R) that is not a plan for the cell's cubic grid, or whose plane does
+ * not fit in shared memory in that precision). */
+pw_status pw_cell_set_fft_plan(pw_cell *cell, int precision, const pw_fft_plan *plan);
+pw_status pw_cell_get_fft_plan(const pw_cell *cell, int precision, pw_fft_plan *plan);
+
+typedef struct {
+  int ncand;            /* candidates timed */
+  pw_fft_plan best;     /* the fastest, now set on the cell */
+  pw_fft_plan dflt;     /* the default plan */
+  double ms_best;       /* local part of H psi on nb bands with `best` (CUDA events, best of 3) */
+  double ms_default;    /* the same with the default plan */
+} pw_fft_tune_report;
+
+/* Times the local part of H psi (FFT, V_loc, kinetic) on nb scratch bands
+ * for every register plan that fits the cell's grid and for the Stockham
+ * passes, each with z-pencil batches of 32, 64 and 128 MiB, and sets the
+ * fastest on the cell for that precision.  Allocates and frees 2 npw nb
+ * complex128 of scratch; synchronises `stream`.  Errors: PW_ERR_ARG (nb < 1,
+ * precision), PW_ERR_OOM, PW_ERR_CUDA. */
+pw_status pw_cell_autotune_fft(pw_cell *cell, int nb, int precision, void *stream,
+                               pw_fft_tune_report *rep);
+
+/* K split of the split-FP16 tensor-core GEMMs (tiles of 128 x 128 x K/s,
+ * partial sums reduced in FP64 in a fixed order), process-wide:
+ *   mode 0: s = 1 for every product (the default; clears the table);
+ *   mode 1: each new product shape with fewer than 608 output tiles is timed
+ *           on its first call at s = 1, 2, 3, 4, 8, 16 (within limits: at
+ *           least 4 K blocks per part, partial sums <= 256 MiB) on a scratch
+ *           output, and the fastest s is kept for that shape (not under
+ *           stream capture; the first call synchronises its stream);
+ *   mode 2: s = `split` wherever those limits allow it.
+ * Results agree to rounding across splits.  Errors: PW_ERR_ARG. */
+pw_status pw_autotune_gemm(int mode, int split);
+/* The tuned shapes as text, one line each ("m= n= kblocks= ... split= ms1= ms="),
+ * into buf (len bytes, NUL-terminated, truncated); returns the number of shapes. */
+int pw_autotune_gemm_table(char *buf, size_t len);
+
 /* Number of CUDA kernel launches the library has issued in this process
  * (all devices, all threads); a diagnostic counter for launch accounting. */
 uint64_t pw_kernel_launches(void);

@@ -464,3 +464,60 @@ _setproj = _sig("pw_cell_set_projectors", ct.c_int, [_vp, ct.c_int, _vp])
 def pw_cell_set_projectors(cell, onthefly, stream=None):
     """Projectors resident (False) or regenerated in atom chunks per H psi (True)."""
     _check(_setproj(cell, 1 if onthefly else 0, _stream(stream)), "pw_cell_set_projectors")
+
+
+# ---------------------------------------------------------------- autotuner --
+class pw_fft_plan(ct.Structure):
+    _fields_ = [("L", ct.c_int), ("R", ct.c_int), ("batch_bytes", ct.c_size_t)]
+
+
+class pw_fft_tune_report(ct.Structure):
+    _fields_ = [("ncand", ct.c_int), ("best", pw_fft_plan), ("dflt", pw_fft_plan),
+                ("ms_best", ct.c_double), ("ms_default", ct.c_double)]
+
+
+_fft_plans = _sig("pw_fft_plans", ct.c_int, [ct.c_int, ct.POINTER(pw_fft_plan), ct.c_int])
+_set_fft_plan = _sig("pw_cell_set_fft_plan", ct.c_int, [_vp, ct.c_int, ct.POINTER(pw_fft_plan)])
+_get_fft_plan = _sig("pw_cell_get_fft_plan", ct.c_int, [_vp, ct.c_int, ct.POINTER(pw_fft_plan)])
+_tune_fft = _sig("pw_cell_autotune_fft", ct.c_int, [_vp, ct.c_int, ct.c_int, _vp,
+                                                     ct.POINTER(pw_fft_tune_report)])
+_tune_gemm = _sig("pw_autotune_gemm", ct.c_int, [ct.c_int, ct.c_int])
+_tune_table = _sig("pw_autotune_gemm_table", ct.c_int, [ct.c_char_p, ct.c_size_t])
+
+
+def pw_fft_plans(n):
+    """Register line-FFT plans (L, R) compiled for grid size n."""
+    k = _fft_plans(int(n), None, 0)
+    arr = (pw_fft_plan * max(k, 1))()
+    _fft_plans(int(n), arr, k)
+    return [(arr[i].L, arr[i].R) for i in range(k)]
+
+
+def pw_cell_set_fft_plan(cell, L, R, batch_bytes=0, precision="fp64"):
+    """Set the cell's FFT plan (L = R = 0: Stockham passes)."""
+    p = pw_fft_plan(int(L), int(R), int(batch_bytes))
+    _check(_set_fft_plan(cell, _PREC[precision], ct.byref(p)), "pw_cell_set_fft_plan")
+
+
+def pw_cell_get_fft_plan(cell, precision="fp64"):
+    p = pw_fft_plan()
+    _check(_get_fft_plan(cell, _PREC[precision], ct.byref(p)), "pw_cell_get_fft_plan")
+    return (p.L, p.R, p.batch_bytes)
+
+
+def pw_cell_autotune_fft(cell, nb, precision="fp64", stream=None):
+    r = pw_fft_tune_report()
+    _check(_tune_fft(cell, int(nb), _PREC[precision], _stream(stream), ct.byref(r)), "pw_cell_autotune_fft")
+    return r
+
+
+def pw_autotune_gemm(mode, split=1):
+    """K split of the tensor-core GEMMs: 0 fixed (s = 1), 1 tuned per shape, 2 forced `split`."""
+    _check(_tune_gemm(int(mode), int(split)), "pw_autotune_gemm")
+
+
+def pw_autotune_gemm_table():
+    n = _tune_table(None, 0)
+    buf = ct.create_string_buffer(256 * (n + 1) + 1)
+    _tune_table(buf, len(buf))
+    return buf.value.decode()

@@ -35,19 +35,20 @@ extern "C" pw_status pw_density(pw_cell *c, const void *psi, int ld, int nb, con
   const int fp32 = c->precision == PW_MIXED;
   const size_t csize = fp32 ? sizeof(float2) : sizeof(double2);
   const size_t per_band = (size_t)c->N[2] * c->ncol * csize;
-  // z-pencils of an L2-sized batch of bands (~64 MB)
-  const int batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, (64u << 20) / per_band));
+  // z-pencils of an L2-sized batch of bands (the cell's batch size, default ~64 MB)
+  const int batch =
+      (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, pw_cell_fft_batch_bytes(c, fp32) / per_band));
   PW_TRY(pw_ensure(&c->d_z, &c->z_bytes, per_band * batch));
   // enough (z-plane, group) blocks for two per SM
   const int ngroups = std::max(1, std::min(8, (2 * 152 + c->N[2] - 1) / c->N[2]));
   PW_TRY(pw_ensure((void **)&c->d_dpart, &c->dpart_bytes, (size_t)ngroups * npts * sizeof(double)));
-  const bool reg = pw_fft_reg_supported(c, fp32);
+  const pw_reg_plan *reg = pw_reg_plan_at(pw_cell_fft_plan(c, fp32));
   for (int b0 = 0; b0 < nb; b0 += batch) {
     const int nbb = std::min(batch, nb - b0);
     const double2 *p = (const double2 *)psi + (long)b0 * ld;
     const double *w = occ ? occ + b0 : nullptr;
     const int g = std::min(ngroups, nbb);
-    if (reg) PW_TRY(pw_fft_reg_density_batch(c, p, ld, nbb, c->d_z, fp32, w, g, c->d_dpart, st));
+    if (reg) PW_TRY((fp32 ? reg->dens32 : reg->dens64)(c, p, ld, nbb, c->d_z, w, g, c->d_dpart, st));
     else PW_TRY(pw_fft_density_batch(c, p, ld, nbb, c->d_z, fp32, w, g, c->d_dpart, st));
     pw_count_launch();
     k_density_reduce<<<(unsigned)((npts + 255) / 256), 256, 0, st>>>(c->d_dpart, g, npts, b0 > 0, rho);

@@ -368,20 +368,21 @@ pw_status apply_local_t(pw_cell *c, const double2 *psi, int ld, int nb, double2 
   const int cb = 16;
   const size_t line_bytes = (size_t)cb * (Nz + 1) * sizeof(C);
   const size_t per_band = (size_t)Nz * c->ncol * sizeof(C);
-  // batch of bands whose z-pencils stay L2-resident (~64 MB)
-  int batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, (64u << 20) / per_band));
+  constexpr int fp32 = sizeof(C) == sizeof(float2);
+  // batch of bands whose z-pencils stay L2-resident (default ~64 MB)
+  int batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, pw_cell_fft_batch_bytes(c, fp32) / per_band));
   PW_TRY(pw_ensure(&c->d_z, &c->z_bytes, per_band * batch));
   C *Z = reinterpret_cast<C *>(c->d_z);
   PW_TRY(allow_smem(k_sphere_to_z<C>, line_bytes));
   PW_TRY(allow_smem(k_plane<C, T>, plane_bytes));
   PW_TRY(allow_smem(k_z_to_sphere<C>, line_bytes));
   const double scale = 1.0 / ((double)Nx * Ny * Nz);
-  constexpr int fp32 = sizeof(C) == sizeof(float2);
-  const bool reg = pw_fft_reg_supported(c, fp32);
+  const pw_reg_plan *reg = pw_reg_plan_at(pw_cell_fft_plan(c, fp32));
   for (int b0 = 0; b0 < nb; b0 += batch) {
     const int nbb = std::min(batch, nb - b0);
     if (reg) {
-      PW_TRY(pw_fft_reg_batch(c, psi + (long)b0 * ld, ld, nbb, hpsi + (long)b0 * ld, Z, fp32, scale, st));
+      PW_TRY((fp32 ? reg->run32 : reg->run64)(c, psi + (long)b0 * ld, ld, nbb, hpsi + (long)b0 * ld, Z, scale,
+                                              st));
       continue;
     }
     dim3 gcols((c->ncol + cb - 1) / cb, nbb);
@@ -418,11 +419,11 @@ pw_status apply_local_into(pw_cell *c, const double2 *psi, int ld, int nb, doubl
   PW_TRY(allow_smem(k_plane<C, double>, plane_bytes));
   PW_TRY(allow_smem(k_z_to_sphere<C>, line_bytes));
   const double scale = 1.0 / ((double)Nx * Ny * Nz);
-  const bool reg = pw_fft_reg_supported(c, 0);
+  const pw_reg_plan *reg = pw_reg_plan_at(pw_cell_fft_plan(c, 0));
   for (int b0 = 0; b0 < nb; b0 += batch) {
     const int nbb = std::min(batch, nb - b0);
     if (reg) {
-      PW_TRY(pw_fft_reg_batch(c, psi + (long)b0 * ld, ld, nbb, hpsi + (long)b0 * ld, Z, 0, scale, st));
+      PW_TRY(reg->run64(c, psi + (long)b0 * ld, ld, nbb, hpsi + (long)b0 * ld, Z, scale, st));
       continue;
     }
     dim3 gcols((c->ncol + cb - 1) / cb, nbb);

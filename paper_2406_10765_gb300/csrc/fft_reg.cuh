@@ -15,6 +15,13 @@
 //
 // The kernels mirror the generic Stockham path (k_sphere_to_z, k_plane,
 // k_z_to_sphere): same data layout, same sign and scaling conventions.
+//
+// A plan is one factorisation N = L R; several plans exist per grid size
+// (fewer lanes: fewer shuffle stages, longer in-lane DFTs) and the cell picks
+// one (default: the first listed, or the autotuner's choice).  Each
+// fft_reg_*.cu instantiates the kernels of a few plans, so the translation
+// units compile in parallel.
+#pragma once
 #include "pw_internal.cuh"
 
 namespace {
@@ -473,47 +480,29 @@ pw_status density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, C *Z, c
   return pw_check_launch("density (register FFT)");
 }
 
-// grid sizes with a register FFT: N -> (L, R)
-#define PW_REG_SIZES(X) X(16, 16, 1) X(24, 8, 3) X(32, 32, 1) X(36, 4, 9) X(48, 16, 3) \
-                        X(64, 32, 2) X(72, 8, 9) X(96, 32, 3) X(128, 32, 4) X(144, 16, 9)
+// entry points of one plan, as stored in the plan tables
+template <int L, int R>
+pw_status reg_run64(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hpsi, void *Z, double scale,
+                    cudaStream_t st) {
+  return run_batch<double2, double, L, R>(c, psi, ld, nbb, hpsi, (double2 *)Z, c->d_V, scale, st);
+}
+template <int L, int R>
+pw_status reg_run32(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hpsi, void *Z, double scale,
+                    cudaStream_t st) {
+  return run_batch<float2, float, L, R>(c, psi, ld, nbb, hpsi, (float2 *)Z, c->d_Vf, scale, st);
+}
+template <int L, int R>
+pw_status reg_dens64(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, const double *occ, int ngroups,
+                     double *part, cudaStream_t st) {
+  return density_batch<double2, L, R>(c, psi, ld, nbb, (double2 *)Z, occ, ngroups, part, st);
+}
+template <int L, int R>
+pw_status reg_dens32(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, const double *occ, int ngroups,
+                     double *part, cudaStream_t st) {
+  return density_batch<float2, L, R>(c, psi, ld, nbb, (float2 *)Z, occ, ngroups, part, st);
+}
 
 }  // namespace
 
-bool pw_fft_reg_supported(const pw_cell *c, int fp32) {
-  const int n = c->N[0];
-  if (c->N[1] != n || c->N[2] != n) return false;
-  if ((size_t)n * (n + 1) * (fp32 ? 8 : 16) > 227 * 1024) return false;   // plane in shared memory
-  // the y-columns that meet the sphere must not wrap onto each other
-  if (2 * c->mxmax + 1 > n) return false;
-#define PW_CASE(NN, LL, RR) if (n == NN) return true;
-  PW_REG_SIZES(PW_CASE)
-#undef PW_CASE
-  return false;
-}
-
-pw_status pw_fft_reg_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hpsi, void *Z,
-                           int fp32, double scale, cudaStream_t st) {
-  const int n = c->N[0];
-#define PW_CASE(NN, LL, RR)                                                                          \
-  if (n == NN) {                                                                                     \
-    if (fp32)                                                                                        \
-      return run_batch<float2, float, LL, RR>(c, psi, ld, nbb, hpsi, (float2 *)Z, c->d_Vf, scale, st); \
-    return run_batch<double2, double, LL, RR>(c, psi, ld, nbb, hpsi, (double2 *)Z, c->d_V, scale, st); \
-  }
-  PW_REG_SIZES(PW_CASE)
-#undef PW_CASE
-  return PW_ERR_ARG;
-}
-
-pw_status pw_fft_reg_density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, int fp32,
-                                   const double *occ, int ngroups, double *part, cudaStream_t st) {
-  const int n = c->N[0];
-#define PW_CASE(NN, LL, RR)                                                                          \
-  if (n == NN) {                                                                                     \
-    if (fp32) return density_batch<float2, LL, RR>(c, psi, ld, nbb, (float2 *)Z, occ, ngroups, part, st); \
-    return density_batch<double2, LL, RR>(c, psi, ld, nbb, (double2 *)Z, occ, ngroups, part, st);   \
-  }
-  PW_REG_SIZES(PW_CASE)
-#undef PW_CASE
-  return PW_ERR_ARG;
-}
+#define PW_REG_PLAN(LL, RR) \
+  { (LL) * (RR), LL, RR, reg_run64<LL, RR>, reg_run32<LL, RR>, reg_dens64<LL, RR>, reg_dens32<LL, RR> }

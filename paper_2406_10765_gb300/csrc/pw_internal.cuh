@@ -91,6 +91,10 @@ struct pw_cell {
   pw_fft_axis ax[3];
   // apply_H workspace (grown on demand)
   void *d_z = nullptr; size_t z_bytes = 0;
+  // FFT plan per precision ([0] FP64, [1] FP32): register line-FFT plan index,
+  // -1 for the Stockham passes, -2 for the default; z-pencil batch bytes (0: default)
+  int fft_plan[2] = {-2, -2};
+  size_t fft_batch[2] = {0, 0};
   double *d_dpart = nullptr; size_t dpart_bytes = 0;   // density partial sums
   double *d_V0 = nullptr;                              // the cell's own V_loc while another V is set
   double2 *d_grid = nullptr; size_t grid_bytes = 0;    // full-grid FFT scratch
@@ -119,21 +123,33 @@ pw_status pw_apply_nonlocal(pw_cell *c, const double2 *psi, int ld, int nb, doub
 
 // FP64 H pieces writing only into caller-provided scratch (no allocation)
 size_t pw_local_zbytes_per_band(const pw_cell *c);
-// register-resident line FFTs for cubic grids of supported sizes (one batch
-// of nbb bands through K1-K3 into the z-pencil buffer Z)
-bool pw_fft_reg_supported(const pw_cell *c, int fp32);
-// density of one batch of bands: z-pencils into Z, then per (z-plane, band
-// group) the inverse plane FFTs and sum_j occ[j] |psi_j(r)|^2 into
-// part[group][z][y][x]; register FFT or Stockham passes
-pw_status pw_fft_reg_density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, int fp32,
-                                   const double *occ, int ngroups, double *part, cudaStream_t st);
+// Register line-FFT plans for cubic grids N = L R (fft_reg_*.cu).  run*: one
+// batch of nbb bands through K1-K3 via the z-pencil buffer Z; dens*: the
+// density of one batch (z-pencils into Z, then per (z-plane, band group) the
+// inverse plane FFTs and sum_j occ[j] |psi_j(r)|^2 into part[group][z][y][x]).
+struct pw_reg_plan {
+  int N, L, R;
+  pw_status (*run64)(pw_cell *, const double2 *, int, int, double2 *, void *, double, cudaStream_t);
+  pw_status (*run32)(pw_cell *, const double2 *, int, int, double2 *, void *, double, cudaStream_t);
+  pw_status (*dens64)(pw_cell *, const double2 *, int, int, void *, const double *, int, double *,
+                      cudaStream_t);
+  pw_status (*dens32)(pw_cell *, const double2 *, int, int, void *, const double *, int, double *,
+                      cudaStream_t);
+};
+int pw_reg_plan_count();
+const pw_reg_plan *pw_reg_plan_at(int i);
+// plan i can run this cell's grid in this precision (cubic grid of size N,
+// plane in shared memory, sphere columns that do not wrap)
+bool pw_reg_plan_fits(const pw_cell *c, int i, int fp32);
+// the cell's FFT plan for a precision (resolving the default): a plan index,
+// or -1 for the Stockham passes; and its z-pencil batch size in bytes
+int pw_cell_fft_plan(const pw_cell *c, int fp32);
+size_t pw_cell_fft_batch_bytes(const pw_cell *c, int fp32);
 // unscaled 3-D FFT of a complex grid g[(z N1 + y) N0 + x] in place (sign -1
 // forward, +1 inverse)
 pw_status pw_grid_fft(pw_cell *c, double2 *g, int inverse, cudaStream_t st);
 pw_status pw_fft_density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, int fp32,
                                const double *occ, int ngroups, double *part, cudaStream_t st);
-pw_status pw_fft_reg_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hpsi, void *Z,
-                           int fp32, double scale, cudaStream_t st);
 pw_status pw_apply_local_fp64_into(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
                                    void *zbuf, size_t zbytes, cudaStream_t st);
 pw_status pw_apply_nonlocal_fp64_into(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,

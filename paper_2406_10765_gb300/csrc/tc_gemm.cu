@@ -11,7 +11,9 @@
 //   Complex products use interleaved rows (re-row, im-row) so one real GEMM
 //   yields the complex result; the epilogue removes the row scales in FP64.
 //
-// Kernel: one 128 x 128 output tile per CTA; warp 0 = TMA producer, warp 1 =
+// Kernel: one 128 x 128 output tile per CTA (and, with a K split, one of
+// gridDim.y equal K ranges of it, partial sums reduced in FP64 by a second
+// kernel in a fixed order); warp 0 = TMA producer, warp 1 =
 // MMA issuer (one thread), warps 2-9 = epilogue (tcgen05.ld from TMEM).
 // Three shared-memory stages of (A_hi, A_lo, B_hi, B_lo) = 64 KB each,
 // 128-byte swizzle.  Each 64-wide K-block accumulates in a fresh TMEM buffer
@@ -24,7 +26,10 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <string>
+#include <tuple>
 
 #include "pw_internal.cuh"
 #include "tc_gemm.cuh"
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               int a_slice_rows, int b_slice_rows, int m, int n, int kblocks, int mtiles,
               int ntiles, const float *__restrict__ inv_sa, const float *__restrict__ inv_sb,
               double2 *__restrict__ C, int ldc, int mode, int accumulate, int herm_skip,
-              int kb_lo, int tri_b, int *__restrict__ err) {
+              int kb_lo, int tri_b, double *__restrict__ part, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + NSTAGE * STAGE);
@@ -225,9 +230,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (herm_skip && n0 + BN - 1 < m0 / 2) return;
   // K blocks of this tile: kb_lo.. (B zero below), and with tri_b (B rows
   // from an upper-triangular coefficient matrix) only K < n0 + BN is nonzero
-  const int kb_beg = kb_lo;
   const int kb_end = tri_b ? min(kblocks, (n0 + BN + BK - 1) / BK) : kblocks;
-  const int nkb = max(0, kb_end - kb_beg);
+  const int ntot = max(0, kb_end - kb_lo);
+  // K split: part z of gridDim.y takes an equal share of the tile's K blocks
+  const int per = (ntot + (int)gridDim.y - 1) / (int)gridDim.y;
+  const int z0 = min(ntot, (int)blockIdx.y * per), z1 = min(ntot, z0 + per);
+  const int kb_beg = kb_lo + z0;
+  const int nkb = z1 - z0;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -337,7 +346,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
     for (int c0 = 0; c0 < EPI_COLS; c0 += 32) tmem_ld32(cmp_base + c0, cmp + c0);
     const int r = m0 + q * 32 + lane;            // output (real) row of this thread
-    if (ok && r < m) {
+    if (ok && r < m && part) {
+      // K split: this part's sums, real layout part[z][col][r], scaled
+      const int ka = pow2_exp(inv_sa[r]);
+      const int cb = n0 + h * EPI_COLS;
+      double *pz = part + (long)blockIdx.y * n * m;
+#pragma unroll
+      for (int t = 0; t < EPI_COLS; ++t) {
+        const int col = cb + t;
+        if (col < n)
+          pz[(long)col * m + r] = scale_pow2(f2d_bits(sum[t]) + f2d_bits(cmp[t]), ka + pow2_exp(inv_sb[col]));
+      }
+    } else if (ok && r < m) {
       // value = (sum + cmp) 2^(ka + kb): one FP64 add, the rest on integer bits
       const int ka = pow2_exp(inv_sa[r]);
       const int cb = n0 + h * EPI_COLS;
@@ -581,6 +601,21 @@ __global__ void __launch_bounds__(256) k_split_coef(const double2 *__restrict__ 
   }
 }
 
+// sum of the K-split parts (in part order) into C, same destinations and
+// tile selection as the single-part epilogue
+__global__ void k_tc_reduce(const double *__restrict__ part, int splits, int m, int n,
+                            double2 *__restrict__ C, int ldc, int mode, int accumulate, int herm_skip) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)m * n) return;
+  const int r = (int)(idx % m), col = (int)(idx / m);
+  if (herm_skip && (col / BN) * BN + BN - 1 < ((r / BM) * BM) / 2) return;
+  double s = 0.0;
+  for (int z = 0; z < splits; ++z) s += part[(long)z * m * n + idx];
+  double *dst = mode == 0 ? (double *)&C[(r >> 1) + (long)col * ldc] + (r & 1)
+                          : (double *)&C[r + (long)(col >> 1) * ldc] + (col & 1);
+  *dst = accumulate ? *dst + s : s;
+}
+
 // lower triangle <- conj(upper) for an n x n complex matrix (ld)
 __global__ void k_mirror_lower(double2 *G, int ld, int n) {
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
@@ -650,6 +685,150 @@ pw_status pw_tc_split_coef(const double2 *Cm, int ld, int kdim, int ncols, const
   return pw_check_launch("split_coef");
 }
 
+// ------------------------------------------------------- K-split tuning ----
+// A product shape with few output tiles and long K leaves SMs idle; splitting
+// K over gridDim.y fills them at the cost of an FP64 partial-sum pass.  The
+// split is a tile-shape choice (128 x 128 x K/s): fixed at 1, forced, or
+// picked per shape by timing the candidates on first use (the autotuner).
+namespace {
+
+constexpr int kWaveTiles = 4 * 152;                 // shapes with fewer tiles are tuned
+constexpr size_t kPartBytesMax = (size_t)256 << 20; // partial sums of one product
+
+struct GemmKey {
+  int m, n, kblocks, kb_lo, tri_b, herm, mode;
+  bool operator<(const GemmKey &o) const {
+    return std::tie(m, n, kblocks, kb_lo, tri_b, herm, mode) <
+           std::tie(o.m, o.n, o.kblocks, o.kb_lo, o.tri_b, o.herm, o.mode);
+  }
+};
+struct GemmChoice {
+  int split;
+  float ms_one, ms_best;   // timed at split 1 and at the chosen split
+};
+
+std::mutex g_tune_mu;
+int g_tune_mode = 0, g_tune_split = 1;
+std::map<GemmKey, GemmChoice> g_tune_table;
+
+// largest split worth trying: at least 4 K blocks per part, bounded partial sums
+int max_split(const GemmKey &k) {
+  const int ntot = k.kblocks - k.kb_lo;
+  int s = std::min(16, std::max(1, ntot / 4));
+  while (s > 1 && (size_t)s * k.m * k.n * sizeof(double) > kPartBytesMax) --s;
+  return s;
+}
+
+void pool_keep(cudaStream_t) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> g(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = kPartBytesMax;   // keep partial-sum buffers between calls
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  done[dev] = true;
+}
+
+pw_status launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const pw_tc_operand *A,
+                      const pw_tc_operand *B, int m, int n, double2 *C, int ldc, int mode, int accumulate,
+                      int herm, int *d_err, cudaStream_t st, int kb_lo, int tri_b, int split) {
+  const int mtiles = (m + BM - 1) / BM, ntiles = (n + BN - 1) / BN;
+  double *part = nullptr;
+  if (split > 1) {
+    pool_keep(st);
+    PW_CUDA(cudaMallocAsync((void **)&part, (size_t)split * m * n * sizeof(double), st));
+  }
+  pw_count_launch();
+  k_tc_gemm<<<dim3(mtiles * ntiles, split), NTHREADS, SMEM_BYTES, st>>>(
+      ma, mb, A->rows_total, B->rows_total, m, n, A->kpad / BK, mtiles, ntiles, A->inv_scale, B->inv_scale, C,
+      ldc, mode, accumulate, herm, kb_lo, tri_b, part, d_err);
+  PW_TRY(pw_check_launch("tc_gemm"));
+  if (split > 1) {
+    pw_count_launch();
+    k_tc_reduce<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, st>>>(part, split, m, n, C, ldc, mode,
+                                                                        accumulate, herm);
+    PW_TRY(pw_check_launch("tc_gemm reduce"));
+    PW_CUDA(cudaFreeAsync(part, st));
+  }
+  if (herm) {
+    const int ni = m / 2;
+    pw_count_launch();
+    k_mirror_lower<<<dim3((ni + 31) / 32, (ni + 31) / 32), dim3(32, 32), 0, st>>>(C, ldc, ni);
+    PW_TRY(pw_check_launch("mirror"));
+  }
+  return PW_OK;
+}
+
+// times every candidate split on a scratch output; returns the fastest
+pw_status tune_split(const GemmKey &key, const CUtensorMap &ma, const CUtensorMap &mb, const pw_tc_operand *A,
+                     const pw_tc_operand *B, int *d_err, cudaStream_t st, GemmChoice *out) {
+  const int m = key.m, n = key.n;
+  const int ldc = key.mode == 0 ? (m + 1) / 2 : m;
+  const size_t cols = key.mode == 0 ? (size_t)n : (size_t)(n + 1) / 2;
+  double2 *Cs = nullptr;
+  PW_CUDA(cudaMallocAsync((void **)&Cs, (size_t)ldc * cols * sizeof(double2), st));
+  cudaEvent_t e0, e1;
+  PW_CUDA(cudaEventCreate(&e0));
+  PW_CUDA(cudaEventCreate(&e1));
+  pw_status r = PW_OK;
+  GemmChoice best{1, 0.0f, 0.0f};
+  const int smax = max_split(key);
+  for (int s = 1; s <= smax && r == PW_OK; s = s < 4 ? s + 1 : s * 2) {
+    float ms = 1e30f;
+    for (int rep = 0; rep < 3 && r == PW_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      r = launch_gemm(ma, mb, A, B, m, n, Cs, ldc, key.mode, 0, key.herm, d_err, st, key.kb_lo, key.tri_b, s);
+      cudaEventRecord(e1, st);
+      float t = 0.0f;
+      if (r == PW_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess &&
+          rep > 0)
+        ms = std::min(ms, t);
+    }
+    if (s == 1) best = GemmChoice{1, ms, ms};
+    else if (ms < best.ms_best) { best.split = s; best.ms_best = ms; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(Cs, st);
+  if (r == PW_OK) *out = best;
+  return r;
+}
+
+}  // namespace
+
+extern "C" pw_status pw_autotune_gemm(int mode, int split) {
+  if (mode < 0 || mode > 2 || (mode == 2 && split < 1)) return PW_ERR_ARG;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune_mode = mode;
+  g_tune_split = mode == 2 ? split : 1;
+  if (mode == 0) g_tune_table.clear();
+  return PW_OK;
+}
+
+extern "C" int pw_autotune_gemm_table(char *buf, size_t len) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  std::string s;
+  for (const auto &kv : g_tune_table) {
+    const GemmKey &k = kv.first;
+    char line[256];
+    snprintf(line, sizeof line, "m=%d n=%d kblocks=%d kb_lo=%d tri_b=%d herm=%d mode=%d split=%d ms1=%.4f ms=%.4f\n",
+             k.m, k.n, k.kblocks, k.kb_lo, k.tri_b, k.herm, k.mode, kv.second.split, kv.second.ms_one,
+             kv.second.ms_best);
+    s += line;
+  }
+  if (buf && len) {
+    const size_t c = std::min(len - 1, s.size());
+    memcpy(buf, s.data(), c);
+    buf[c] = 0;
+  }
+  return (int)g_tune_table.size();
+}
+
 pw_status pw_tc_gemm(const pw_tc_operand *A, int m, const pw_tc_operand *B, int n, double2 *C, int ldc,
                      int mode, int accumulate, int herm, int *d_err, cudaStream_t st, int kb_lo, int tri_b) {
   if (A->kpad != B->kpad || m > A->rows_total || n > B->rows_total || m <= 0 || n <= 0) return PW_ERR_ARG;
@@ -661,20 +840,31 @@ pw_status pw_tc_gemm(const pw_tc_operand *A, int m, const pw_tc_operand *B, int 
   // per-device kernel attribute (set on every call: cheap, thread-safe, and
   // correct on every device the caller uses)
   PW_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  const int mtiles = (m + BM - 1) / BM, ntiles = (n + BN - 1) / BN;
-  pw_count_launch();
-  k_tc_gemm<<<mtiles * ntiles, NTHREADS, SMEM_BYTES, st>>>(ma, mb, A->rows_total, B->rows_total, m, n,
-                                                      A->kpad / BK, mtiles, ntiles, A->inv_scale,
-                                                      B->inv_scale, C, ldc, mode, accumulate, herm,
-                                                      kb_lo, tri_b, d_err);
-  PW_TRY(pw_check_launch("tc_gemm"));
-  if (herm) {
-    const int ni = m / 2;
-    pw_count_launch();
-    k_mirror_lower<<<dim3((ni + 31) / 32, (ni + 31) / 32), dim3(32, 32), 0, st>>>(C, ldc, ni);
-    PW_TRY(pw_check_launch("mirror"));
+  const GemmKey key{m, n, A->kpad / BK, kb_lo, tri_b, herm, mode};
+  const int tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+  int split = 1, tmode;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    tmode = g_tune_mode;
+    if (tmode == 2) split = g_tune_split;
+    if (tmode == 1) {
+      auto it = g_tune_table.find(key);
+      if (it != g_tune_table.end()) { split = it->second.split; tmode = 0; }
+    }
   }
-  return PW_OK;
+  if (tmode == 1) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (tiles < kWaveTiles && max_split(key) > 1 && cs == cudaStreamCaptureStatusNone) {
+      GemmChoice ch;
+      PW_TRY(tune_split(key, ma, mb, A, B, d_err, st, &ch));
+      split = ch.split;
+      std::lock_guard<std::mutex> g(g_tune_mu);
+      g_tune_table[key] = ch;
+    }
+  }
+  split = std::max(1, std::min(split, max_split(key)));
+  return launch_gemm(ma, mb, A, B, m, n, C, ldc, mode, accumulate, herm, d_err, st, kb_lo, tri_b, split);
 }
 
 pw_status pw_tc_operand_alloc(pw_tc_operand *op, int rows, int kreal, cudaStream_t st) {

@@ -38,3 +38,22 @@ def test_strerror_without_gpu():
     import paper_2406_10765_gb300 as pw
     assert pw.pw_strerror(0) == "ok"
     assert "positive definite" in pw.pw_strerror(-4)
+
+
+def test_autotuner_host_entry_points_without_gpu():
+    # the plan table and the GEMM tuning switch need no device
+    import paper_2406_10765_gb300 as pw
+    for n in (16, 24, 32, 36, 48, 64, 72, 96, 128, 144):
+        plans = pw.pw_fft_plans(n)
+        assert plans, n
+        assert len(set(plans)) == len(plans)
+        for L, R in plans:
+            assert L * R == n and L & (L - 1) == 0 and 1 <= L <= 32 and R <= 18
+    assert pw.pw_fft_plans(27) == [] and pw.pw_fft_plans(0) == []
+    with pytest.raises(pw.PwError):
+        pw.pw_autotune_gemm(3)
+    with pytest.raises(pw.PwError):
+        pw.pw_autotune_gemm(2, 0)
+    pw.pw_autotune_gemm(2, 4)
+    pw.pw_autotune_gemm(0)
+    assert pw.pw_autotune_gemm_table() == ""

@@ -124,6 +124,50 @@ def test_apply_h_grid_sizes(N):
         assert rel(_run(lib, x), ref) < tol, (N, prec)
 
 
+# every FFT plan of every register grid size (each factorisation N = L R,
+# and the Stockham passes where the plane fits), one band per batch and the
+# default batch, against the oracle on the same grid
+@pytest.mark.parametrize("N", [16, 24, 32, 36, 48, 64, 72, 96, 128, 144])
+def test_apply_h_every_fft_plan(N):
+    import paper_2406_10765_gb300 as pw
+    ecut = 4.0 if N < 24 else 8.0
+    plans = pw.pw_fft_plans(N)
+    assert plans and all(L * R == N and L & (L - 1) == 0 and L <= 32 for L, R in plans)
+    x = None
+    for prec, tol, csize in (("fp64", 1e-12, 16), ("mixed", 1e-5, 8)):
+        lib, orc, _ = cells("Si", 1, ecut, grid=(N, N, N), precision=prec)
+        if N * (N + 1) * csize > 227 * 1024:
+            # the plane does not fit in shared memory in this precision
+            with pytest.raises(pw.PwError):
+                pw.pw_cell_set_fft_plan(lib.h, *plans[0], precision=prec)
+            continue
+        if x is None:
+            x = synth.draw_x0(7, 8, orc.npw, 3)
+            ref = O.apply_H(orc, x)
+        assert pw.pw_cell_get_fft_plan(lib.h, prec)[:2] == plans[0]
+        for L, R in plans + [(0, 0)]:
+            for batch in (1, 0):
+                pw.pw_cell_set_fft_plan(lib.h, L, R, batch, precision=prec)
+                assert pw.pw_cell_get_fft_plan(lib.h, prec)[:2] == (L, R)
+                assert rel(_run(lib, x), ref) < tol, (N, prec, L, R, batch)
+    with pytest.raises(pw.PwError):
+        pw.pw_cell_set_fft_plan(lib.h, 3, N // 3 + 1, precision="mixed")
+
+
+def test_fft_autotune_si64():
+    # the autotuner times every candidate plan of the 64-atom cell (grid 48)
+    # and leaves the fastest set; H psi still matches the oracle
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 2, 10.0, precision="mixed")
+    r = pw.pw_cell_autotune_fft(lib.h, 64, precision="mixed")
+    ncand_min = len(pw.pw_fft_plans(lib.grid[0])) + 1
+    assert r.ncand >= ncand_min
+    assert 0 < r.ms_best <= r.ms_default
+    assert pw.pw_cell_get_fft_plan(lib.h, "mixed") == (r.best.L, r.best.R, r.best.batch_bytes)
+    x = synth.draw_x0(3, 64, orc.npw, 4)
+    assert rel(_run(lib, x), O.apply_H(orc, x)) < 1e-5
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
 def test_projectors_on_the_fly(prec, tol):
     # beta regenerated in atom chunks (the 512-atom cell needs several 256 MB

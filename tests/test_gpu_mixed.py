@@ -123,3 +123,25 @@ def test_mixed_chunked_eigsolve_si8():
     assert np.abs(eig - ref).max() <= 1e-6
     assert rep.max_resid <= 1e-5
     assert rep.orth_err <= 1e-10
+
+
+def test_mixed_steps_with_k_split():
+    # every tensor-core product of the step with its K range cut in three
+    # (including the triangular and zero-block K bounds of S M and P') tracks
+    # the oracle's FP64 steps as the single-part products do
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 2, 10.0, precision="mixed")
+    nb = 144
+    x0 = synth.draw_x0(0, 64, orc.npw, nb)
+    st = O.lobpcg_init(orc, x0)
+    try:
+        pw.pw_autotune_gemm(2, 3)
+        s = pw.pw_solver_create(lib.h, nb, tol=0.0, x0=x0, precision="mixed")
+        for _ in range(3):
+            st = O.lobpcg_step(orc, st)
+            pw.pw_subspace_step(lib.h, s)
+        e, _ = pw.pw_solver_eigs(s, nb)
+        pw.pw_solver_destroy(s)
+    finally:
+        pw.pw_autotune_gemm(0)
+    assert np.abs(e - st.lam).max() < 1e-4
