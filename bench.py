@@ -69,7 +69,7 @@ def serve_sample(args):
     import paper_2406_10765_gb300 as pw
     reqs = synth.serving_requests(2000, rate_per_s=args.serve_rate, seed=2024)[:args.serve_requests]
     t0 = time.perf_counter()
-    out = pw.pw_serve(reqs, max_slots=4, precision="mixed")
+    out = pw.pw_serve(reqs, max_slots=4, precision="mixed", autotune=not args.no_autotune)
     wall = time.perf_counter() - t0
     ok = [o for o in out if o["status"] in (0, -5)]
     lat = np.array([o["latency"] for o in ok])
@@ -81,6 +81,7 @@ def serve_sample(args):
                               for k in sorted(set(o["status"] for o in out))},
             "max_resid": float(max(o["max_resid"] for o in ok)),
             "arrival_rate_per_s": args.serve_rate, "slots": 4, "precision": "mixed",
+            "autotune": not args.no_autotune,
             "sample": f"first {len(reqs)} requests of the seeded 2000-request stream"}
 
 

@@ -251,6 +251,10 @@ typedef struct {
   size_t hbm_budget;    /* bytes admitted at once; 0 -> 80% of free device memory */
   int precision;        /* PW_FP64 or PW_MIXED */
   double time_scale;    /* multiplies arrival times; 0 -> 1 */
+  int autotune;         /* 1: the first request of each grid size tunes the FFT
+                           plan (pw_cell_autotune_fft on its bands) and later
+                           requests of that grid reuse it; the tensor-core K
+                           splits follow pw_autotune_gemm's process-wide mode */
 } pw_serve_opts;
 
 /* Device-memory footprint model used to admit a request (bytes). */
@@ -402,15 +406,17 @@ pw_status pw_cell_autotune_fft(pw_cell *cell, int nb, int precision, void *strea
 /* K split of the split-FP16 tensor-core GEMMs (tiles of 128 x 128 x K/s,
  * partial sums reduced in FP64 in a fixed order), process-wide:
  *   mode 0: s = 1 for every product (the default; clears the table);
- *   mode 1: each new product shape with fewer than 608 output tiles is timed
- *           on its first call at s = 1, 2, 3, 4, 8, 16 (within limits: at
- *           least 4 K blocks per part, partial sums <= 256 MiB) on a scratch
- *           output, and the fastest s is kept for that shape (not under
- *           stream capture; the first call synchronises its stream);
+ *   mode 1: each new product shape class (output tiles, K blocks rounded up
+ *           to a power of two, K bounds, layout) with fewer than 608 output
+ *           tiles is timed on its first call at s = 1, 2, 3, 4, 8, 16 (within
+ *           limits: at least 4 K blocks per part, partial sums <= 256 MiB) on
+ *           a scratch output, and the fastest s is kept for the class (not
+ *           under stream capture; that call synchronises its stream);
  *   mode 2: s = `split` wherever those limits allow it.
  * Results agree to rounding across splits.  Errors: PW_ERR_ARG. */
 pw_status pw_autotune_gemm(int mode, int split);
-/* The tuned shapes as text, one line each ("m= n= kblocks= ... split= ms1= ms="),
+/* The tuned shape classes as text, one line each ("mtiles= ntiles= kblocks<= ...
+ * split= ms1= ms="),
  * into buf (len bytes, NUL-terminated, truncated); returns the number of shapes. */
 int pw_autotune_gemm_table(char *buf, size_t len);
 

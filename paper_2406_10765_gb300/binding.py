@@ -71,7 +71,7 @@ class pw_result(ct.Structure):
 
 class pw_serve_opts(ct.Structure):
     _fields_ = [("max_slots", ct.c_int), ("hbm_budget", ct.c_size_t), ("precision", ct.c_int),
-                ("time_scale", ct.c_double)]
+                ("time_scale", ct.c_double), ("autotune", ct.c_int)]
 
 
 class pw_solve_report(ct.Structure):
@@ -179,7 +179,7 @@ def pw_request_footprint(r, precision="fp64"):
     return int(_footprint(ct.byref(_mkreq(r)), _PREC[precision]))
 
 
-def pw_serve(requests, max_slots=4, hbm_budget=0, precision="fp64", time_scale=1.0):
+def pw_serve(requests, max_slots=4, hbm_budget=0, precision="fp64", time_scale=1.0, autotune=False):
     """Serve a list of request dicts (species, n, ecut, nbands, seed, t_arrival[, tol, maxit]).
     Returns a list of dicts with eig (numpy), status, iters, timings."""
     n = len(requests)
@@ -191,6 +191,7 @@ def pw_serve(requests, max_slots=4, hbm_budget=0, precision="fp64", time_scale=1
     o = pw_serve_opts()
     o.max_slots, o.hbm_budget, o.precision, o.time_scale = int(max_slots), int(hbm_budget), \
         _PREC[precision], float(time_scale)
+    o.autotune = 1 if autotune else 0
     _check(_serve(ct.byref(o), reqs, n, res), "pw_serve")
     out = []
     for i in range(n):

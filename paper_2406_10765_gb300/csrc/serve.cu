@@ -15,10 +15,12 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -116,6 +118,10 @@ struct Server {
   int running = 0;
   bool closing = false;
   std::chrono::steady_clock::time_point t0;
+  // FFT plans tuned per grid (N0, N1, N2); a grid being tuned is marked with
+  // L = -1 and later requests use the default plan meanwhile
+  std::mutex plan_mu;
+  std::map<std::array<int, 3>, pw_fft_plan> plans;
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
@@ -146,6 +152,31 @@ void run_one(Server &sv, int i, int device) {
   d.precision = sv.opts->precision;
   pw_cell *cell = nullptr;
   s = pw_setup_cell(&d, st, &cell);
+  if (s == PW_OK && sv.opts->autotune) {
+    const std::array<int, 3> g{cell->N[0], cell->N[1], cell->N[2]};
+    bool tune = false, have = false;
+    pw_fft_plan p{};
+    {
+      std::lock_guard<std::mutex> lk(sv.plan_mu);
+      auto it = sv.plans.find(g);
+      if (it == sv.plans.end()) {
+        sv.plans[g] = pw_fft_plan{-1, 0, 0};
+        tune = true;
+      } else if (it->second.L >= 0) {
+        p = it->second;
+        have = true;
+      }
+    }
+    if (tune) {
+      pw_fft_tune_report tr;
+      s = pw_cell_autotune_fft(cell, r.nbands, sv.opts->precision, st, &tr);
+      std::lock_guard<std::mutex> lk(sv.plan_mu);
+      if (s == PW_OK) sv.plans[g] = tr.best;
+      else sv.plans.erase(g);
+    } else if (have) {
+      s = pw_cell_set_fft_plan(cell, sv.opts->precision, &p);
+    }
+  }
   pw_solve_report rep;
   memset(&rep, 0, sizeof rep);
   if (s == PW_OK) {

@@ -695,13 +695,20 @@ namespace {
 constexpr int kWaveTiles = 4 * 152;                 // shapes with fewer tiles are tuned
 constexpr size_t kPartBytesMax = (size_t)256 << 20; // partial sums of one product
 
+// shape class of a product: output tiles, K blocks rounded up to a power of
+// two (cells of nearby sizes share a choice), the K bounds and the layout
 struct GemmKey {
-  int m, n, kblocks, kb_lo, tri_b, herm, mode;
+  int mtiles, ntiles, kclass, kb_lo, tri_b, herm, mode;
   bool operator<(const GemmKey &o) const {
-    return std::tie(m, n, kblocks, kb_lo, tri_b, herm, mode) <
-           std::tie(o.m, o.n, o.kblocks, o.kb_lo, o.tri_b, o.herm, o.mode);
+    return std::tie(mtiles, ntiles, kclass, kb_lo, tri_b, herm, mode) <
+           std::tie(o.mtiles, o.ntiles, o.kclass, o.kb_lo, o.tri_b, o.herm, o.mode);
   }
 };
+GemmKey make_key(int m, int n, int kblocks, int kb_lo, int tri_b, int herm, int mode) {
+  int kc = 1;
+  while (kc < kblocks - kb_lo) kc *= 2;
+  return GemmKey{(m + BM - 1) / BM, (n + BN - 1) / BN, kc, kb_lo, tri_b, herm, mode};
+}
 struct GemmChoice {
   int split;
   float ms_one, ms_best;   // timed at split 1 and at the chosen split
@@ -712,10 +719,10 @@ int g_tune_mode = 0, g_tune_split = 1;
 std::map<GemmKey, GemmChoice> g_tune_table;
 
 // largest split worth trying: at least 4 K blocks per part, bounded partial sums
-int max_split(const GemmKey &k) {
-  const int ntot = k.kblocks - k.kb_lo;
+int max_split(int m, int n, int kblocks, int kb_lo) {
+  const int ntot = kblocks - kb_lo;
   int s = std::min(16, std::max(1, ntot / 4));
-  while (s > 1 && (size_t)s * k.m * k.n * sizeof(double) > kPartBytesMax) --s;
+  while (s > 1 && (size_t)s * m * n * sizeof(double) > kPartBytesMax) --s;
   return s;
 }
 
@@ -765,9 +772,9 @@ pw_status launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const pw_tc_
 }
 
 // times every candidate split on a scratch output; returns the fastest
-pw_status tune_split(const GemmKey &key, const CUtensorMap &ma, const CUtensorMap &mb, const pw_tc_operand *A,
-                     const pw_tc_operand *B, int *d_err, cudaStream_t st, GemmChoice *out) {
-  const int m = key.m, n = key.n;
+pw_status tune_split(const GemmKey &key, int m, int n, int smax, const CUtensorMap &ma, const CUtensorMap &mb,
+                     const pw_tc_operand *A, const pw_tc_operand *B, int *d_err, cudaStream_t st,
+                     GemmChoice *out) {
   const int ldc = key.mode == 0 ? (m + 1) / 2 : m;
   const size_t cols = key.mode == 0 ? (size_t)n : (size_t)(n + 1) / 2;
   double2 *Cs = nullptr;
@@ -777,7 +784,6 @@ pw_status tune_split(const GemmKey &key, const CUtensorMap &ma, const CUtensorMa
   PW_CUDA(cudaEventCreate(&e1));
   pw_status r = PW_OK;
   GemmChoice best{1, 0.0f, 0.0f};
-  const int smax = max_split(key);
   for (int s = 1; s <= smax && r == PW_OK; s = s < 4 ? s + 1 : s * 2) {
     float ms = 1e30f;
     for (int rep = 0; rep < 3 && r == PW_OK; ++rep) {
@@ -816,8 +822,9 @@ extern "C" int pw_autotune_gemm_table(char *buf, size_t len) {
   for (const auto &kv : g_tune_table) {
     const GemmKey &k = kv.first;
     char line[256];
-    snprintf(line, sizeof line, "m=%d n=%d kblocks=%d kb_lo=%d tri_b=%d herm=%d mode=%d split=%d ms1=%.4f ms=%.4f\n",
-             k.m, k.n, k.kblocks, k.kb_lo, k.tri_b, k.herm, k.mode, kv.second.split, kv.second.ms_one,
+    snprintf(line, sizeof line,
+             "mtiles=%d ntiles=%d kblocks<=%d kb_lo=%d tri_b=%d herm=%d mode=%d split=%d ms1=%.4f ms=%.4f\n",
+             k.mtiles, k.ntiles, k.kclass, k.kb_lo, k.tri_b, k.herm, k.mode, kv.second.split, kv.second.ms_one,
              kv.second.ms_best);
     s += line;
   }
@@ -840,8 +847,9 @@ pw_status pw_tc_gemm(const pw_tc_operand *A, int m, const pw_tc_operand *B, int 
   // per-device kernel attribute (set on every call: cheap, thread-safe, and
   // correct on every device the caller uses)
   PW_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-  const GemmKey key{m, n, A->kpad / BK, kb_lo, tri_b, herm, mode};
-  const int tiles = ((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+  const GemmKey key = make_key(m, n, A->kpad / BK, kb_lo, tri_b, herm, mode);
+  const int tiles = key.mtiles * key.ntiles;
+  const int smax = max_split(m, n, A->kpad / BK, kb_lo);
   int split = 1, tmode;
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
@@ -855,15 +863,15 @@ pw_status pw_tc_gemm(const pw_tc_operand *A, int m, const pw_tc_operand *B, int 
   if (tmode == 1) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cs);
-    if (tiles < kWaveTiles && max_split(key) > 1 && cs == cudaStreamCaptureStatusNone) {
+    if (tiles < kWaveTiles && smax > 1 && cs == cudaStreamCaptureStatusNone) {
       GemmChoice ch;
-      PW_TRY(tune_split(key, ma, mb, A, B, d_err, st, &ch));
+      PW_TRY(tune_split(key, m, n, smax, ma, mb, A, B, d_err, st, &ch));
       split = ch.split;
       std::lock_guard<std::mutex> g(g_tune_mu);
       g_tune_table[key] = ch;
     }
   }
-  split = std::max(1, std::min(split, max_split(key)));
+  split = std::max(1, std::min(split, smax));
   return launch_gemm(ma, mb, A, B, m, n, C, ldc, mode, accumulate, herm, d_err, st, kb_lo, tri_b, split);
 }
 

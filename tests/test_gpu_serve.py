@@ -74,3 +74,24 @@ def test_serve_mixed_concurrent_equals_alone():
         assert m["status"] == alone["status"]
         assert np.array_equal(alone["eig"], m["eig"])
         assert m["status"] == 0 and m["max_resid"] <= 5e-6
+
+
+def test_serve_autotuned_plans_within_tolerance():
+    # with the autotuner on (FFT plan per grid size, K splits per shape class)
+    # the served eigenvalues stay within the mixed-precision tolerance of the
+    # untuned run, and every request still converges
+    import paper_2406_10765_gb300 as pw
+    reqs = synth.serving_requests(2000, rate_per_s=50.0, seed=2024)[:6]
+    for r in reqs:
+        r["n"] = min(r["n"], 2)
+        r["nbands"] = round(1.125 * 2 * 8 * r["n"] ** 3)
+    base = pw.pw_serve(reqs, max_slots=4, precision="mixed")
+    try:
+        pw.pw_autotune_gemm(1)
+        tuned = pw.pw_serve(reqs, max_slots=4, precision="mixed", autotune=True)
+    finally:
+        pw.pw_autotune_gemm(0)
+    for a, b in zip(base, tuned):
+        assert a["status"] == 0 and b["status"] == 0, (a["status"], b["status"])
+        assert np.abs(a["eig"] - b["eig"]).max() <= 2e-6
+        assert b["max_resid"] <= 5e-6 and b["orth_err"] <= 1e-10
