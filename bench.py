@@ -333,9 +333,10 @@ def run_gpu(args):
         # the first warm-up step)
         fr = pw.pw_cell_autotune_fft(cell.h, min(nb, 256), precision=args.precision)
         pw.pw_autotune_gemm(1)
-        tune = {"fft": {"L": fr.best.L, "R": fr.best.R, "batch_mib": fr.best.batch_bytes >> 20,
+        tune = {"fft": {"L": fr.best.L, "R": fr.best.R, "compact": fr.best.compact,
+                        "batch_mib": fr.best.batch_bytes >> 20,
                         "ms_best": fr.ms_best, "ms_default": fr.ms_default,
-                        "default": [fr.dflt.L, fr.dflt.R, fr.dflt.batch_bytes >> 20],
+                        "default": [fr.dflt.L, fr.dflt.R, fr.dflt.compact, fr.dflt.batch_bytes >> 20],
                         "candidates": fr.ncand, "bands": min(nb, 256)}}
     solver = pw.pw_solver_create(cell.h, nb, tol=0.0, seed=0, precision=args.precision)
     for _ in range(args.warmup):

@@ -367,9 +367,13 @@ pw_status pw_zgemm_tc(char opA, int m, int n, int k, const void *A, int lda, con
 
 /* A plan for the local part of H psi: register line FFTs with N = L R per
  * axis (L lanes, R values per lane), or L = R = 0 for the Stockham passes in
- * shared memory; batch_bytes: z-pencil bytes per batch of bands (0: 64 MiB). */
+ * shared memory; compact = 1 keeps only the x-columns that meet the sphere
+ * in shared memory (register plans only: smaller planes, e.g. the FP64 plane
+ * at N = 128, more blocks per SM); batch_bytes: z-pencil bytes per batch of
+ * bands (0: 64 MiB). */
 typedef struct {
   int L, R;
+  int compact;
   size_t batch_bytes;
 } pw_fft_plan;
 
@@ -381,8 +385,8 @@ int pw_fft_plans(int n, pw_fft_plan *plans, int max);
 /* The cell's plan for one precision (PW_FP64, or PW_MIXED for its FP32
  * FFTs).  Set: L = R = 0 selects the Stockham passes.  Results agree to
  * rounding across plans.  Errors: PW_ERR_ARG (NULL, unknown precision, or an
- * (L, R) that is not a plan for the cell's cubic grid, or whose plane does
- * not fit in shared memory in that precision). */
+ * (L, R, compact) that is not a plan for the cell's cubic grid, or whose
+ * plane does not fit in shared memory in that precision). */
 pw_status pw_cell_set_fft_plan(pw_cell *cell, int precision, const pw_fft_plan *plan);
 pw_status pw_cell_get_fft_plan(const pw_cell *cell, int precision, pw_fft_plan *plan);
 
@@ -395,8 +399,8 @@ typedef struct {
 } pw_fft_tune_report;
 
 /* Times the local part of H psi (FFT, V_loc, kinetic) on nb scratch bands
- * for every register plan that fits the cell's grid and for the Stockham
- * passes, each with z-pencil batches of 32, 64 and 128 MiB, and sets the
+ * for every register plan that fits the cell's grid (full and compact plane)
+ * and for the Stockham passes, each with z-pencil batches of 32, 64 and 128 MiB, and sets the
  * fastest on the cell for that precision.  Allocates and frees 2 npw nb
  * complex128 of scratch; synchronises `stream`.  Errors: PW_ERR_ARG (nb < 1,
  * precision), PW_ERR_OOM, PW_ERR_CUDA. */

@@ -469,7 +469,7 @@ def pw_cell_set_projectors(cell, onthefly, stream=None):
 
 # ---------------------------------------------------------------- autotuner --
 class pw_fft_plan(ct.Structure):
-    _fields_ = [("L", ct.c_int), ("R", ct.c_int), ("batch_bytes", ct.c_size_t)]
+    _fields_ = [("L", ct.c_int), ("R", ct.c_int), ("compact", ct.c_int), ("batch_bytes", ct.c_size_t)]
 
 
 class pw_fft_tune_report(ct.Structure):
@@ -494,16 +494,16 @@ def pw_fft_plans(n):
     return [(arr[i].L, arr[i].R) for i in range(k)]
 
 
-def pw_cell_set_fft_plan(cell, L, R, batch_bytes=0, precision="fp64"):
-    """Set the cell's FFT plan (L = R = 0: Stockham passes)."""
-    p = pw_fft_plan(int(L), int(R), int(batch_bytes))
+def pw_cell_set_fft_plan(cell, L, R, batch_bytes=0, precision="fp64", compact=False):
+    """Set the cell's FFT plan (L = R = 0: Stockham passes; compact: sphere x-columns only)."""
+    p = pw_fft_plan(int(L), int(R), 1 if compact else 0, int(batch_bytes))
     _check(_set_fft_plan(cell, _PREC[precision], ct.byref(p)), "pw_cell_set_fft_plan")
 
 
 def pw_cell_get_fft_plan(cell, precision="fp64"):
     p = pw_fft_plan()
     _check(_get_fft_plan(cell, _PREC[precision], ct.byref(p)), "pw_cell_get_fft_plan")
-    return (p.L, p.R, p.batch_bytes)
+    return (p.L, p.R, p.batch_bytes, bool(p.compact))
 
 
 def pw_cell_autotune_fft(cell, nb, precision="fp64", stream=None):

@@ -363,26 +363,30 @@ template <typename C, typename T>
 pw_status apply_local_t(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
                         const T *V, cudaStream_t st) {
   const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
+  constexpr int fp32 = sizeof(C) == sizeof(float2);
+  const pw_reg_plan *reg = pw_reg_plan_at(pw_cell_fft_plan(c, fp32));
+  const int cp = pw_cell_fft_compact(c, fp32);
+  // the Stockham passes hold the whole x-y plane in shared memory
   const size_t plane_bytes = (size_t)Ny * (Nx + 1) * sizeof(C);
-  if (plane_bytes > 227 * 1024) return PW_ERR_ARG;
+  if (!reg && plane_bytes > 227 * 1024) return PW_ERR_ARG;
   const int cb = 16;
   const size_t line_bytes = (size_t)cb * (Nz + 1) * sizeof(C);
   const size_t per_band = (size_t)Nz * c->ncol * sizeof(C);
-  constexpr int fp32 = sizeof(C) == sizeof(float2);
   // batch of bands whose z-pencils stay L2-resident (default ~64 MB)
   int batch = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, pw_cell_fft_batch_bytes(c, fp32) / per_band));
   PW_TRY(pw_ensure(&c->d_z, &c->z_bytes, per_band * batch));
   C *Z = reinterpret_cast<C *>(c->d_z);
-  PW_TRY(allow_smem(k_sphere_to_z<C>, line_bytes));
-  PW_TRY(allow_smem(k_plane<C, T>, plane_bytes));
-  PW_TRY(allow_smem(k_z_to_sphere<C>, line_bytes));
+  if (!reg) {
+    PW_TRY(allow_smem(k_sphere_to_z<C>, line_bytes));
+    PW_TRY(allow_smem(k_plane<C, T>, plane_bytes));
+    PW_TRY(allow_smem(k_z_to_sphere<C>, line_bytes));
+  }
   const double scale = 1.0 / ((double)Nx * Ny * Nz);
-  const pw_reg_plan *reg = pw_reg_plan_at(pw_cell_fft_plan(c, fp32));
   for (int b0 = 0; b0 < nb; b0 += batch) {
     const int nbb = std::min(batch, nb - b0);
     if (reg) {
-      PW_TRY((fp32 ? reg->run32 : reg->run64)(c, psi + (long)b0 * ld, ld, nbb, hpsi + (long)b0 * ld, Z, scale,
-                                              st));
+      PW_TRY((fp32 ? reg->run32[cp] : reg->run64[cp])(c, psi + (long)b0 * ld, ld, nbb, hpsi + (long)b0 * ld, Z,
+                                                      scale, st));
       continue;
     }
     dim3 gcols((c->ncol + cb - 1) / cb, nbb);
@@ -407,23 +411,26 @@ pw_status apply_local_into(pw_cell *c, const double2 *psi, int ld, int nb, doubl
                            void *zbuf, size_t zbytes, cudaStream_t st) {
   typedef double2 C;
   const int Nx = c->N[0], Ny = c->N[1], Nz = c->N[2];
+  const pw_reg_plan *reg = pw_reg_plan_at(pw_cell_fft_plan(c, 0));
+  const int cp = pw_cell_fft_compact(c, 0);
   const size_t plane_bytes = (size_t)Ny * (Nx + 1) * sizeof(C);
-  if (plane_bytes > 227 * 1024) return PW_ERR_ARG;
+  if (!reg && plane_bytes > 227 * 1024) return PW_ERR_ARG;
   const int cb = 16;
   const size_t line_bytes = (size_t)cb * (Nz + 1) * sizeof(C);
   const size_t per_band = (size_t)Nz * c->ncol * sizeof(C);
   const int batch = (int)std::min<size_t>((size_t)nb, zbytes / per_band);
   if (batch < 1) return PW_ERR_ARG;
   C *Z = reinterpret_cast<C *>(zbuf);
-  PW_TRY(allow_smem(k_sphere_to_z<C>, line_bytes));
-  PW_TRY(allow_smem(k_plane<C, double>, plane_bytes));
-  PW_TRY(allow_smem(k_z_to_sphere<C>, line_bytes));
+  if (!reg) {
+    PW_TRY(allow_smem(k_sphere_to_z<C>, line_bytes));
+    PW_TRY(allow_smem(k_plane<C, double>, plane_bytes));
+    PW_TRY(allow_smem(k_z_to_sphere<C>, line_bytes));
+  }
   const double scale = 1.0 / ((double)Nx * Ny * Nz);
-  const pw_reg_plan *reg = pw_reg_plan_at(pw_cell_fft_plan(c, 0));
   for (int b0 = 0; b0 < nb; b0 += batch) {
     const int nbb = std::min(batch, nb - b0);
     if (reg) {
-      PW_TRY(reg->run64(c, psi + (long)b0 * ld, ld, nbb, hpsi + (long)b0 * ld, Z, scale, st));
+      PW_TRY(reg->run64[cp](c, psi + (long)b0 * ld, ld, nbb, hpsi + (long)b0 * ld, Z, scale, st));
       continue;
     }
     dim3 gcols((c->ncol + cb - 1) / cb, nbb);

@@ -35,24 +35,42 @@ const pw_reg_plan *pw_reg_plan_at(int i) {
   return nullptr;
 }
 
-bool pw_reg_plan_fits(const pw_cell *c, int i, int fp32) {
+bool pw_reg_plan_fits(const pw_cell *c, int i, int fp32, int compact) {
   const pw_reg_plan *p = pw_reg_plan_at(i);
   if (!p) return false;
   const int n = c->N[0];
   if (c->N[1] != n || c->N[2] != n || p->N != n) return false;
-  if ((size_t)n * (n + 1) * (fp32 ? 8 : 16) > 227 * 1024) return false;   // plane in shared memory
   // the y-columns that meet the sphere must not wrap onto each other
-  return 2 * c->mxmax + 1 <= n;
+  if (2 * c->mxmax + 1 > n) return false;
+  return p->smem(c, fp32, compact) <= 227 * 1024;   // plane in shared memory
 }
+
+namespace {
+// default: the first plan listed for the grid size with the full plane,
+// else the first with the compact plane; (-1, 0) for the Stockham passes
+void default_plan(const pw_cell *c, int fp32, int *plan, int *compact) {
+  const int np = pw_reg_plan_count();
+  for (int cp = 0; cp < 2; ++cp)
+    for (int i = 0; i < np; ++i)
+      if (pw_reg_plan_fits(c, i, fp32, cp)) { *plan = i; *compact = cp; return; }
+  *plan = -1;
+  *compact = 0;
+}
+}  // namespace
 
 int pw_cell_fft_plan(const pw_cell *c, int fp32) {
   const int chosen = c->fft_plan[fp32 ? 1 : 0];
   if (chosen >= -1) return chosen;
-  // default: the first plan listed for the grid size
-  const int np = pw_reg_plan_count();
-  for (int i = 0; i < np; ++i)
-    if (pw_reg_plan_fits(c, i, fp32)) return i;
-  return -1;
+  int p, cp;
+  default_plan(c, fp32, &p, &cp);
+  return p;
+}
+
+int pw_cell_fft_compact(const pw_cell *c, int fp32) {
+  if (c->fft_plan[fp32 ? 1 : 0] >= -1) return c->fft_compact[fp32 ? 1 : 0];
+  int p, cp;
+  default_plan(c, fp32, &p, &cp);
+  return cp;
 }
 
 size_t pw_cell_fft_batch_bytes(const pw_cell *c, int fp32) {

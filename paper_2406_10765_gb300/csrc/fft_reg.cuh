@@ -220,42 +220,63 @@ __global__ void __launch_bounds__(ZTHREADS) k_sphere_to_z_reg(const double2 *__r
 }
 
 // ---------------------------------------------------------------- K2 ----
-template <typename C, typename T, int L, int R>
+// Plane layouts in shared memory: full, the N x N plane with row stride N + 1;
+// compact (CP), only the x-columns that meet the sphere (x in [-mxmax,
+// mxmax], column x + mxmax) with an odd row stride, plus one N-point row
+// buffer per line group of each warp for the x transforms.  After the y
+// transforms the other x-columns are zero, and after the x transforms only
+// the sphere's x-columns are read again, so the compact plane holds
+// everything the pass needs (an FP64 plane of 128 x 85 instead of 128 x 129).
+__host__ __device__ inline int compact_stride(int mxmax) { return (2 * mxmax + 1) | 1; }
+template <typename C, int L, int R>
+__host__ __device__ inline size_t plane_smem_bytes(int mxmax, bool cp, int nthreads) {
+  constexpr int N = L * R;
+  if (!cp) return (size_t)N * (N + 1) * sizeof(C);
+  return ((size_t)N * compact_stride(mxmax) + (size_t)(nthreads / 32) * (32 / L) * N) * sizeof(C);
+}
+
+template <typename C, typename T, int L, int R, bool CP>
 __global__ void __launch_bounds__(RegPlaneThreads<C>::value) k_plane_reg(C *__restrict__ Z, int ncol,
                                                                          const int *__restrict__ colxy,
                                                                          int mxmax, const C *__restrict__ twx,
                                                                          int Nz, const T *__restrict__ V) {
-  constexpr int N = L * R, pxs = N + 1, G = 32 / L;
+  constexpr int N = L * R, G = 32 / L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *P = reinterpret_cast<C *>(smem_raw);
   const int z = blockIdx.x, b = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int gid = lane / L, l = lane % L;
+  const int nxe = 2 * mxmax + 1;
+  const int ps = CP ? compact_stride(mxmax) : N + 1;
+  // plane column of x in [0, N): the x index itself, or its place in the
+  // compact sphere extent (valid for x <= mxmax or x >= N - mxmax)
+  auto pcol = [&](int x) { return CP ? (x <= mxmax ? x + mxmax : x - N + mxmax) : x; };
+  auto in_ext = [&](int x) { return !CP || x <= mxmax || x >= N - mxmax; };
+  C *rowbuf = P + (long)N * ps + (long)(warp * G + gid) * N;   // compact only
   LineTw<C, L, R> t;
   t.init(twx, l);
   C *Zp = Z + ((long)b * Nz + z) * ncol;
-  for (int i = threadIdx.x; i < N * pxs; i += blockDim.x) P[i] = czero_r<C>();
+  for (int i = threadIdx.x; i < N * ps; i += blockDim.x) P[i] = czero_r<C>();
   __syncthreads();
   for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
     const int xy = colxy[c];
-    P[(xy / N) * pxs + (xy % N)] = Zp[c];
+    P[(xy / N) * ps + pcol(xy % N)] = Zp[c];
   }
   __syncthreads();
   // inverse FFT along y on the x-columns that meet the sphere (x in [-mxmax, mxmax])
-  const int nxe = 2 * mxmax + 1;
   for (int base = warp * G; base < nxe; base += nw * G) {
     const int xi = base + gid;
     const bool act = xi < nxe;
     int x = xi - mxmax;
     if (x < 0) x += N;
-    C *col = P + (act ? x : 0);
+    C *col = P + (act ? pcol(x) : 0);
     C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = act ? col[(l + L * r) * pxs] : czero_r<C>();
+    for (int r = 0; r < R; ++r) v[r] = act ? col[(l + L * r) * ps] : czero_r<C>();
     line_fft<C, L, R>(v, t, twx, l, true);
     if (act) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) col[t.out_index(r, l) * pxs] = v[r];
+      for (int r = 0; r < R; ++r) col[t.out_index(r, l) * ps] = v[r];
     }
   }
   __syncthreads();
@@ -264,10 +285,14 @@ __global__ void __launch_bounds__(RegPlaneThreads<C>::value) k_plane_reg(C *__re
   for (int base = warp * G; base < N; base += nw * G) {
     const int y = base + gid;
     const bool act = y < N;
-    C *row = P + (long)(act ? y : 0) * pxs;
+    C *row = P + (long)(act ? y : 0) * ps;
+    C *mid = CP ? rowbuf : row;               // the row between the two transforms, natural x order
     C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = act ? row[l + L * r] : czero_r<C>();
+    for (int r = 0; r < R; ++r) {
+      const int x = l + L * r;
+      v[r] = act && in_ext(x) ? row[pcol(x)] : czero_r<C>();
+    }
     line_fft<C, L, R>(v, t, twx, l, true);
     if (act) {
 #pragma unroll
@@ -277,16 +302,19 @@ __global__ void __launch_bounds__(RegPlaneThreads<C>::value) k_plane_reg(C *__re
         C e = v[r];
         e.x *= vv;
         e.y *= vv;
-        row[x] = e;
+        mid[x] = e;
       }
     }
     __syncwarp();
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = act ? row[l + L * r] : czero_r<C>();
+    for (int r = 0; r < R; ++r) v[r] = act ? mid[l + L * r] : czero_r<C>();
     line_fft<C, L, R>(v, t, twx, l, false);
     if (act) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) row[t.out_index(r, l)] = v[r];
+      for (int r = 0; r < R; ++r) {
+        const int x = t.out_index(r, l);
+        if (in_ext(x)) row[pcol(x)] = v[r];
+      }
     }
     __syncwarp();
   }
@@ -297,20 +325,20 @@ __global__ void __launch_bounds__(RegPlaneThreads<C>::value) k_plane_reg(C *__re
     const bool act = xi < nxe;
     int x = xi - mxmax;
     if (x < 0) x += N;
-    C *col = P + (act ? x : 0);
+    C *col = P + (act ? pcol(x) : 0);
     C v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = act ? col[(l + L * r) * pxs] : czero_r<C>();
+    for (int r = 0; r < R; ++r) v[r] = act ? col[(l + L * r) * ps] : czero_r<C>();
     line_fft<C, L, R>(v, t, twx, l, false);
     if (act) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) col[t.out_index(r, l) * pxs] = v[r];
+      for (int r = 0; r < R; ++r) col[t.out_index(r, l) * ps] = v[r];
     }
   }
   __syncthreads();
   for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
     const int xy = colxy[c];
-    Zp[c] = P[(xy / N) * pxs + (xy % N)];
+    Zp[c] = P[(xy / N) * ps + pcol(xy % N)];
   }
 }
 
@@ -354,21 +382,22 @@ template <typename C> __host__ __device__ inline const C *twtab(const pw_fft_axi
 template <> inline const double2 *twtab<double2>(const pw_fft_axis &a) { return a.tw64; }
 template <> inline const float2 *twtab<float2>(const pw_fft_axis &a) { return a.tw32; }
 
-template <typename C, typename T, int L, int R>
+template <typename C, typename T, int L, int R, bool CP>
 pw_status run_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hpsi, C *Z, const T *V,
                     double scale, cudaStream_t st) {
   constexpr int N = L * R;
-  const size_t plane_bytes = (size_t)N * (N + 1) * sizeof(C);
+  if (2 * c->mxmax + 1 > N) return PW_ERR_ARG;
+  const size_t plane_bytes = plane_smem_bytes<C, L, R>(c->mxmax, CP, RegPlaneThreads<C>::value);
   if (plane_bytes > 227 * 1024) return PW_ERR_ARG;
   if (plane_bytes > 48 * 1024)
-    PW_CUDA(cudaFuncSetAttribute(k_plane_reg<C, T, L, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    PW_CUDA(cudaFuncSetAttribute(k_plane_reg<C, T, L, R, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)plane_bytes));
   const dim3 gcols((c->ncol + ZCB - 1) / ZCB, nbb);
   pw_count_launch();
   k_sphere_to_z_reg<C, L, R><<<gcols, ZTHREADS, 0, st>>>(psi, ld, c->d_colstart, c->d_gcol, c->d_gz,
                                                          c->ncol, twtab<C>(c->ax[2]), Z);
   pw_count_launch();
-  k_plane_reg<C, T, L, R><<<dim3(N, nbb), RegPlaneThreads<C>::value, plane_bytes, st>>>(
+  k_plane_reg<C, T, L, R, CP><<<dim3(N, nbb), RegPlaneThreads<C>::value, plane_bytes, st>>>(
       Z, c->ncol, c->d_colxy, c->mxmax, twtab<C>(c->ax[0]), N, V);
   pw_count_launch();
   k_z_to_sphere_reg<C, L, R><<<gcols, ZTHREADS, 0, st>>>(Z, c->ncol, twtab<C>(c->ax[2]), c->d_colstart,
@@ -481,15 +510,21 @@ pw_status density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, C *Z, c
 }
 
 // entry points of one plan, as stored in the plan tables
-template <int L, int R>
+template <int L, int R, bool CP>
 pw_status reg_run64(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hpsi, void *Z, double scale,
                     cudaStream_t st) {
-  return run_batch<double2, double, L, R>(c, psi, ld, nbb, hpsi, (double2 *)Z, c->d_V, scale, st);
+  return run_batch<double2, double, L, R, CP>(c, psi, ld, nbb, hpsi, (double2 *)Z, c->d_V, scale, st);
 }
-template <int L, int R>
+template <int L, int R, bool CP>
 pw_status reg_run32(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hpsi, void *Z, double scale,
                     cudaStream_t st) {
-  return run_batch<float2, float, L, R>(c, psi, ld, nbb, hpsi, (float2 *)Z, c->d_Vf, scale, st);
+  return run_batch<float2, float, L, R, CP>(c, psi, ld, nbb, hpsi, (float2 *)Z, c->d_Vf, scale, st);
+}
+// shared memory of the plane kernel for a cell (full or compact layout)
+template <int L, int R>
+size_t reg_smem(const pw_cell *c, int fp32, int compact) {
+  return fp32 ? plane_smem_bytes<float2, L, R>(c->mxmax, compact != 0, RegPlaneThreads<float2>::value)
+              : plane_smem_bytes<double2, L, R>(c->mxmax, compact != 0, RegPlaneThreads<double2>::value);
 }
 template <int L, int R>
 pw_status reg_dens64(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, const double *occ, int ngroups,
@@ -504,5 +539,7 @@ pw_status reg_dens32(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, c
 
 }  // namespace
 
-#define PW_REG_PLAN(LL, RR) \
-  { (LL) * (RR), LL, RR, reg_run64<LL, RR>, reg_run32<LL, RR>, reg_dens64<LL, RR>, reg_dens32<LL, RR> }
+#define PW_REG_PLAN(LL, RR)                                                                           \
+  { (LL) * (RR), LL, RR, {reg_run64<LL, RR, false>, reg_run64<LL, RR, true>},                          \
+    {reg_run32<LL, RR, false>, reg_run32<LL, RR, true>}, reg_dens64<LL, RR>, reg_dens32<LL, RR>,         \
+    reg_smem<LL, RR> }

@@ -94,6 +94,7 @@ struct pw_cell {
   // FFT plan per precision ([0] FP64, [1] FP32): register line-FFT plan index,
   // -1 for the Stockham passes, -2 for the default; z-pencil batch bytes (0: default)
   int fft_plan[2] = {-2, -2};
+  int fft_compact[2] = {0, 0};
   size_t fft_batch[2] = {0, 0};
   double *d_dpart = nullptr; size_t dpart_bytes = 0;   // density partial sums
   double *d_V0 = nullptr;                              // the cell's own V_loc while another V is set
@@ -127,23 +128,28 @@ size_t pw_local_zbytes_per_band(const pw_cell *c);
 // batch of nbb bands through K1-K3 via the z-pencil buffer Z; dens*: the
 // density of one batch (z-pencils into Z, then per (z-plane, band group) the
 // inverse plane FFTs and sum_j occ[j] |psi_j(r)|^2 into part[group][z][y][x]).
+// run*[compact]: plane kernel with the full N x N plane (0) or only the
+// sphere's x-columns (1) in shared memory; smem: its shared-memory bytes.
+typedef pw_status (*pw_reg_run_fn)(pw_cell *, const double2 *, int, int, double2 *, void *, double,
+                                   cudaStream_t);
 struct pw_reg_plan {
   int N, L, R;
-  pw_status (*run64)(pw_cell *, const double2 *, int, int, double2 *, void *, double, cudaStream_t);
-  pw_status (*run32)(pw_cell *, const double2 *, int, int, double2 *, void *, double, cudaStream_t);
+  pw_reg_run_fn run64[2], run32[2];
   pw_status (*dens64)(pw_cell *, const double2 *, int, int, void *, const double *, int, double *,
                       cudaStream_t);
   pw_status (*dens32)(pw_cell *, const double2 *, int, int, void *, const double *, int, double *,
                       cudaStream_t);
+  size_t (*smem)(const pw_cell *, int fp32, int compact);
 };
 int pw_reg_plan_count();
 const pw_reg_plan *pw_reg_plan_at(int i);
-// plan i can run this cell's grid in this precision (cubic grid of size N,
-// plane in shared memory, sphere columns that do not wrap)
-bool pw_reg_plan_fits(const pw_cell *c, int i, int fp32);
+// plan i can run this cell's grid in this precision and plane layout (cubic
+// grid of size N, plane in shared memory, sphere columns that do not wrap)
+bool pw_reg_plan_fits(const pw_cell *c, int i, int fp32, int compact);
 // the cell's FFT plan for a precision (resolving the default): a plan index,
-// or -1 for the Stockham passes; and its z-pencil batch size in bytes
+// or -1 for the Stockham passes; its plane layout; its z-pencil batch bytes
 int pw_cell_fft_plan(const pw_cell *c, int fp32);
+int pw_cell_fft_compact(const pw_cell *c, int fp32);
 size_t pw_cell_fft_batch_bytes(const pw_cell *c, int fp32);
 // unscaled 3-D FFT of a complex grid g[(z N1 + y) N0 + x] in place (sign -1
 // forward, +1 inverse)

@@ -24,11 +24,11 @@ __global__ void k_fill_scratch(double2 *x, long n) {
   x[i] = make_double2(re, im);
 }
 
-int plan_index(const pw_cell *c, int L, int R, int fp32) {
+int plan_index(const pw_cell *c, int L, int R, int fp32, int compact) {
   const int np = pw_reg_plan_count();
   for (int i = 0; i < np; ++i) {
     const pw_reg_plan *p = pw_reg_plan_at(i);
-    if (p->L == L && p->R == R && pw_reg_plan_fits(c, i, fp32)) return i;
+    if (p->L == L && p->R == R && pw_reg_plan_fits(c, i, fp32, compact)) return i;
   }
   return -2;
 }
@@ -37,6 +37,7 @@ void describe(const pw_cell *c, int fp32, pw_fft_plan *out) {
   const pw_reg_plan *p = pw_reg_plan_at(pw_cell_fft_plan(c, fp32));
   out->L = p ? p->L : 0;
   out->R = p ? p->R : 0;
+  out->compact = p ? pw_cell_fft_compact(c, fp32) : 0;
   out->batch_bytes = pw_cell_fft_batch_bytes(c, fp32);
 }
 
@@ -48,7 +49,7 @@ extern "C" int pw_fft_plans(int n, pw_fft_plan *plans, int max) {
   for (int i = 0; i < np; ++i) {
     const pw_reg_plan *p = pw_reg_plan_at(i);
     if (p->N != n) continue;
-    if (plans && k < max) plans[k] = pw_fft_plan{p->L, p->R, 0};
+    if (plans && k < max) plans[k] = pw_fft_plan{p->L, p->R, 0, 0};
     ++k;
   }
   return k;
@@ -58,11 +59,16 @@ extern "C" pw_status pw_cell_set_fft_plan(pw_cell *c, int precision, const pw_ff
   if (!c || !plan || (precision != PW_FP64 && precision != PW_MIXED)) return PW_ERR_ARG;
   const int fp32 = precision == PW_MIXED;
   int idx = -1;
+  if (plan->compact != 0 && plan->compact != 1) return PW_ERR_ARG;
   if (plan->L != 0 || plan->R != 0) {
-    idx = plan_index(c, plan->L, plan->R, fp32);
+    idx = plan_index(c, plan->L, plan->R, fp32, plan->compact);
     if (idx < 0) return PW_ERR_ARG;
+  } else {
+    // the Stockham passes: full plane only
+    if (plan->compact || (size_t)c->N[1] * (c->N[0] + 1) * (fp32 ? 8 : 16) > 227 * 1024) return PW_ERR_ARG;
   }
   c->fft_plan[fp32] = idx;
+  c->fft_compact[fp32] = idx >= 0 ? plan->compact : 0;
   c->fft_batch[fp32] = plan->batch_bytes;
   return PW_OK;
 }
@@ -80,24 +86,26 @@ extern "C" pw_status pw_cell_autotune_fft(pw_cell *c, int nb, int precision, voi
   const int fp32 = precision == PW_MIXED;
   const int npw = c->npw;
   const size_t per_band = (size_t)c->N[2] * c->ncol * (fp32 ? sizeof(float2) : sizeof(double2));
-  // candidates: every fitting register plan, the Stockham passes; three batch sizes
-  std::vector<int> plans;
+  // candidates: every fitting register plan in both plane layouts, the
+  // Stockham passes; three batch sizes
+  std::vector<std::pair<int, int>> plans;
   const int np = pw_reg_plan_count();
-  for (int i = 0; i < np; ++i)
-    if (pw_reg_plan_fits(c, i, fp32)) plans.push_back(i);
+  for (int cp = 0; cp < 2; ++cp)
+    for (int i = 0; i < np; ++i)
+      if (pw_reg_plan_fits(c, i, fp32, cp)) plans.push_back({i, cp});
   // the Stockham passes hold one x-y plane in shared memory
   if ((size_t)c->N[1] * (c->N[0] + 1) * (fp32 ? sizeof(float2) : sizeof(double2)) <= 227 * 1024)
-    plans.push_back(-1);
+    plans.push_back({-1, 0});
   if (plans.empty()) return PW_ERR_ARG;
   const size_t batches[3] = {(size_t)32 << 20, (size_t)64 << 20, (size_t)128 << 20};
 
-  const int saved_plan = c->fft_plan[fp32];
+  const int saved_plan = c->fft_plan[fp32], saved_cp = c->fft_compact[fp32];
   const size_t saved_batch = c->fft_batch[fp32];
   pw_fft_tune_report r{};
   c->fft_plan[fp32] = -2;
   c->fft_batch[fp32] = 0;
   describe(c, fp32, &r.dflt);
-  const int dflt_idx = pw_cell_fft_plan(c, fp32);
+  const int dflt_idx = pw_cell_fft_plan(c, fp32), dflt_cp = pw_cell_fft_compact(c, fp32);
   const size_t dflt_batch = pw_cell_fft_batch_bytes(c, fp32);
   const int dflt_nbatch = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, dflt_batch / per_band));
 
@@ -117,7 +125,7 @@ extern "C" pw_status pw_cell_autotune_fft(pw_cell *c, int nb, int precision, voi
     s = pw_check_launch("autotune fill");
   }
   double best = 1e300;
-  int best_plan = dflt_idx;
+  int best_plan = dflt_idx, best_cp = dflt_cp;
   size_t best_batch = dflt_batch;
   for (int pi = 0; pi < (int)plans.size() && s == PW_OK; ++pi) {
     int last_batch = -1;
@@ -126,7 +134,8 @@ extern "C" pw_status pw_cell_autotune_fft(pw_cell *c, int nb, int precision, voi
       const int nbatch = (int)std::max<size_t>(1, std::min<size_t>((size_t)nb, batches[bi] / per_band));
       if (nbatch == last_batch) continue;
       last_batch = nbatch;
-      c->fft_plan[fp32] = plans[pi];
+      c->fft_plan[fp32] = plans[pi].first;
+      c->fft_compact[fp32] = plans[pi].second;
       c->fft_batch[fp32] = batches[bi];
       double ms = 1e300;
       for (int rep_i = 0; rep_i < 4 && s == PW_OK; ++rep_i) {
@@ -141,9 +150,14 @@ extern "C" pw_status pw_cell_autotune_fft(pw_cell *c, int nb, int precision, voi
       }
       if (s != PW_OK) break;
       ++r.ncand;
-      const bool is_default = plans[pi] == dflt_idx && nbatch == dflt_nbatch;
+      const bool is_default = plans[pi].first == dflt_idx && plans[pi].second == dflt_cp && nbatch == dflt_nbatch;
       if (is_default) r.ms_default = ms;
-      if (ms < best) { best = ms; best_plan = plans[pi]; best_batch = batches[bi]; }
+      if (ms < best) {
+        best = ms;
+        best_plan = plans[pi].first;
+        best_cp = plans[pi].second;
+        best_batch = batches[bi];
+      }
     }
   }
   if (e0) cudaEventDestroy(e0);
@@ -152,10 +166,12 @@ extern "C" pw_status pw_cell_autotune_fft(pw_cell *c, int nb, int precision, voi
   if (hpsi) cudaFree(hpsi);
   if (s != PW_OK) {
     c->fft_plan[fp32] = saved_plan;
+    c->fft_compact[fp32] = saved_cp;
     c->fft_batch[fp32] = saved_batch;
     return s;
   }
   c->fft_plan[fp32] = best_plan;
+  c->fft_compact[fp32] = best_cp;
   c->fft_batch[fp32] = best_batch;
   describe(c, fp32, &r.best);
   r.ms_best = best;

@@ -124,9 +124,10 @@ def test_apply_h_grid_sizes(N):
         assert rel(_run(lib, x), ref) < tol, (N, prec)
 
 
-# every FFT plan of every register grid size (each factorisation N = L R,
-# and the Stockham passes where the plane fits), one band per batch and the
-# default batch, against the oracle on the same grid
+# every FFT plan of every register grid size (each factorisation N = L R
+# with the full and the compact plane, and the Stockham passes where the full
+# plane fits), one band per batch and the default batch, against the oracle
+# on the same grid; FP64 at 128 and 144 runs on compact planes only
 @pytest.mark.parametrize("N", [16, 24, 32, 36, 48, 64, 72, 96, 128, 144])
 def test_apply_h_every_fft_plan(N):
     import paper_2406_10765_gb300 as pw
@@ -136,22 +137,31 @@ def test_apply_h_every_fft_plan(N):
     x = None
     for prec, tol, csize in (("fp64", 1e-12, 16), ("mixed", 1e-5, 8)):
         lib, orc, _ = cells("Si", 1, ecut, grid=(N, N, N), precision=prec)
-        if N * (N + 1) * csize > 227 * 1024:
-            # the plane does not fit in shared memory in this precision
-            with pytest.raises(pw.PwError):
-                pw.pw_cell_set_fft_plan(lib.h, *plans[0], precision=prec)
-            continue
         if x is None:
             x = synth.draw_x0(7, 8, orc.npw, 3)
             ref = O.apply_H(orc, x)
-        assert pw.pw_cell_get_fft_plan(lib.h, prec)[:2] == plans[0]
-        for L, R in plans + [(0, 0)]:
+        full_fits = N * (N + 1) * csize <= 227 * 1024
+        assert pw.pw_cell_get_fft_plan(lib.h, prec)[0:2] == plans[0]
+        assert pw.pw_cell_get_fft_plan(lib.h, prec)[3] == (not full_fits)
+        cands = [(L, R, cp) for L, R in plans for cp in (False, True) if full_fits or cp]
+        if full_fits:
+            cands.append((0, 0, False))
+        else:
+            # the full plane does not fit in shared memory in this precision
+            with pytest.raises(pw.PwError):
+                pw.pw_cell_set_fft_plan(lib.h, *plans[0], precision=prec)
+            with pytest.raises(pw.PwError):
+                pw.pw_cell_set_fft_plan(lib.h, 0, 0, precision=prec)
+        for L, R, cp in cands:
             for batch in (1, 0):
-                pw.pw_cell_set_fft_plan(lib.h, L, R, batch, precision=prec)
-                assert pw.pw_cell_get_fft_plan(lib.h, prec)[:2] == (L, R)
-                assert rel(_run(lib, x), ref) < tol, (N, prec, L, R, batch)
+                pw.pw_cell_set_fft_plan(lib.h, L, R, batch, precision=prec, compact=cp)
+                got = pw.pw_cell_get_fft_plan(lib.h, prec)
+                assert got[:2] == (L, R) and got[3] == cp
+                assert rel(_run(lib, x), ref) < tol, (N, prec, L, R, cp, batch)
     with pytest.raises(pw.PwError):
         pw.pw_cell_set_fft_plan(lib.h, 3, N // 3 + 1, precision="mixed")
+    with pytest.raises(pw.PwError):
+        pw.pw_cell_set_fft_plan(lib.h, 0, 0, precision="mixed", compact=True)
 
 
 def test_fft_autotune_si64():
@@ -160,10 +170,11 @@ def test_fft_autotune_si64():
     import paper_2406_10765_gb300 as pw
     lib, orc, _ = cells("Si", 2, 10.0, precision="mixed")
     r = pw.pw_cell_autotune_fft(lib.h, 64, precision="mixed")
-    ncand_min = len(pw.pw_fft_plans(lib.grid[0])) + 1
+    ncand_min = 2 * len(pw.pw_fft_plans(lib.grid[0])) + 1
     assert r.ncand >= ncand_min
     assert 0 < r.ms_best <= r.ms_default
-    assert pw.pw_cell_get_fft_plan(lib.h, "mixed") == (r.best.L, r.best.R, r.best.batch_bytes)
+    assert pw.pw_cell_get_fft_plan(lib.h, "mixed") == (r.best.L, r.best.R, r.best.batch_bytes,
+                                                      bool(r.best.compact))
     x = synth.draw_x0(3, 64, orc.npw, 4)
     assert rel(_run(lib, x), O.apply_H(orc, x)) < 1e-5
 
@@ -191,17 +202,23 @@ def test_projectors_on_the_fly(prec, tol):
     assert rel(_run(lib, x), stored) < (1e-15 if prec == "fp64" else 1e-12)
 
 
-def test_apply_h_si1728_mixed_sampled():
-    # the 1,728-atom cell (npw 251,967, grid 128^3, 6,912 projectors) in mixed
-    # precision with projectors generated on the fly, on sampled bands against
-    # the oracle's operator (its projectors formed 64 atoms at a time)
+def test_apply_h_si1728_sampled():
+    # the 1,728-atom cell (npw 251,967, grid 128^3, 6,912 projectors) with
+    # projectors generated on the fly, on sampled bands against the oracle's
+    # operator (its projectors formed 64 atoms at a time): mixed precision,
+    # and FP64 on the compact x-y plane (the full FP64 plane does not fit in
+    # shared memory at 128^2)
     import paper_2406_10765_gb300 as pw
     ci = synth.cell_inputs("Si", 6, 0)
-    lib = pw.Cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], 8.0, precision="mixed")
-    assert lib.npw == 251967 and lib.grid == (128, 128, 128)
-    pw.pw_cell_set_projectors(lib.h, True)
-    x = synth.draw_x0(0, 1728, lib.npw, 3)
-    got = _run(lib, x)
+    x = synth.draw_x0(0, 1728, 251967, 3)
+    got = {}
+    for prec in ("mixed", "fp64"):
+        lib = pw.Cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], 8.0, precision=prec)
+        assert lib.npw == 251967 and lib.grid == (128, 128, 128)
+        pw.pw_cell_set_projectors(lib.h, True)
+        if prec == "fp64":
+            assert pw.pw_cell_get_fft_plan(lib.h, "fp64")[3]      # compact plane
+        got[prec] = _run(lib, x)
     Ls = np.full(3, float(ci["L"]) if np.ndim(ci["L"]) == 0 else ci["L"][0])
     m = O.sphere(8.0, Ls)
     assert np.array_equal(lib.m, m)
@@ -214,4 +231,5 @@ def test_apply_h_si1728_mixed_sampled():
     for a0 in range(0, len(ci["tau"]), 64):
         b = O.projectors(m, Ls, ci["tau"][a0:a0 + 64], 1.2)
         ref += b @ (D[4 * a0:4 * a0 + b.shape[1], None] * (b.conj().T @ x))
-    assert rel(got, ref) < 1e-5
+    assert rel(got["mixed"], ref) < 1e-5
+    assert rel(got["fp64"], ref) < 1e-12
