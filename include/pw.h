@@ -419,7 +419,7 @@ pw_status pw_cell_autotune_fft(pw_cell *cell, int nb, int precision, void *strea
  *   mode 2: s = `split` wherever those limits allow it.
  * Results agree to rounding across splits.  Errors: PW_ERR_ARG. */
 pw_status pw_autotune_gemm(int mode, int split);
-/* The tuned shape classes as text, one line each ("mtiles= ntiles= kblocks<= ...
+/* The tuned shape classes as text, one line each ("mtiles= ntiles= k<= k_lo= ...
  * split= ms1= ms="),
  * into buf (len bytes, NUL-terminated, truncated); returns the number of shapes. */
 int pw_autotune_gemm_table(char *buf, size_t len);

@@ -139,6 +139,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// two 32-column TMEM loads (accumulator and compensation) under one wait
+__device__ __forceinline__ void tmem_ld32x2(uint32_t ta, uint32_t tb, float *va, float *vb) {
+  uint32_t a[32], b[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(a[16]), "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]), "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31]),
+        "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]), "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15]), "=r"(b[16]), "=r"(b[17]), "=r"(b[18]), "=r"(b[19]), "=r"(b[20]), "=r"(b[21]), "=r"(b[22]), "=r"(b[23]), "=r"(b[24]), "=r"(b[25]), "=r"(b[26]), "=r"(b[27]), "=r"(b[28]), "=r"(b[29]), "=r"(b[30]), "=r"(b[31])
+      : "r"(ta), "r"(tb)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    va[i] = __uint_as_float(a[i]);
+    vb[i] = __uint_as_float(b[i]);
+  }
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -332,8 +350,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
       for (int c0 = 0; c0 < EPI_COLS; c0 += 32) {
         float v[32], e[32];
-        tmem_ld32(base + c0, v);
-        tmem_ld32(cmp_base + c0, e);
+        tmem_ld32x2(base + c0, cmp_base + c0, v, e);
 #pragma unroll
         for (int i = 0; i < 32; ++i) two_sum_acc(sum[c0 + i], e[i], v[i]);
         tmem_st32(cmp_base + c0, e);
@@ -823,8 +840,8 @@ extern "C" int pw_autotune_gemm_table(char *buf, size_t len) {
     const GemmKey &k = kv.first;
     char line[256];
     snprintf(line, sizeof line,
-             "mtiles=%d ntiles=%d kblocks<=%d kb_lo=%d tri_b=%d herm=%d mode=%d split=%d ms1=%.4f ms=%.4f\n",
-             k.mtiles, k.ntiles, k.kclass, k.kb_lo, k.tri_b, k.herm, k.mode, kv.second.split, kv.second.ms_one,
+             "mtiles=%d ntiles=%d k<=%d k_lo=%d tri_b=%d herm=%d mode=%d split=%d ms1=%.4f ms=%.4f\n",
+             k.mtiles, k.ntiles, k.kclass * BK, k.kb_lo * BK, k.tri_b, k.herm, k.mode, kv.second.split, kv.second.ms_one,
              kv.second.ms_best);
     s += line;
   }
