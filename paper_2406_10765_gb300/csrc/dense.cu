@@ -365,32 +365,53 @@ __global__ void __launch_bounds__(PCOL_THREADS) k_pcol(double2 *A, int n, int c,
   __shared__ double sh[32];
   __shared__ unsigned s_ticket;
   __shared__ double2 s_vc[TPB], s_wc[TPB], s_u[4][33];
-  pdl_wait();
-  pdl_trigger();
   double2 *V = P, *W = P + (long)b * n;
-  double2 al = make_double2(0.0, 0.0);
-  if (i > 0) al = panel_alpha(dotpart, ndot, tau[c - 1], sh);
-  if (threadIdx.x < i) {
-    const int q = threadIdx.x;
-    s_vc[q] = V[c + (long)q * n];
-    // W[c, i-1] = p_{c-1}[0] + alpha v_{c-1}[row c], the head of v_{c-1} being 1
-    s_wc[q] = (q == i - 1) ? cadd(__ldcg(&p[0]), al) : W[c + (long)q * n];
-  }
-  __syncthreads();
   const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int r = c + blockIdx.x * 32 + rl;
+  // Before the wait: what the panel's earlier columns wrote two or more
+  // launches back — V[:, q < i], W[:, q < i-1] and, for i > 0, column c of A
+  // (last written by the previous panel's update).  p and the dots (and from
+  // them W[:, i-1]) come from the predecessor.
+  constexpr int QMAX = (TPB + 3) / 4;
+  double2 vq_r[QMAX], wq_r[QMAX];
+  double2 a = make_double2(0.0, 0.0);
+  if (i > 0) {
+    if (threadIdx.x < i) {
+      const int q = threadIdx.x;
+      s_vc[q] = V[c + (long)q * n];
+      if (q < i - 1) s_wc[q] = W[c + (long)q * n];
+    }
+#pragma unroll
+    for (int t = 0; t < QMAX; ++t) {
+      const int q = g + 4 * t;
+      const bool ok = r < n && q < i;
+      vq_r[t] = ok ? V[r + (long)q * n] : make_double2(0.0, 0.0);
+      wq_r[t] = ok && q < i - 1 ? W[r + (long)q * n] : make_double2(0.0, 0.0);
+    }
+    if (g == 0 && r < n) a = A[r + (long)c * n];
+  }
+  pdl_wait();
+  pdl_trigger();
+  double2 al = make_double2(0.0, 0.0);
+  if (i > 0) {
+    al = panel_alpha(dotpart, ndot, tau[c - 1], sh);
+    // W[c, i-1] = p_{c-1}[0] + alpha v_{c-1}[row c], the head of v_{c-1} being 1
+    if (threadIdx.x == 0) s_wc[i - 1] = cadd(__ldcg(&p[0]), al);
+  }
+  __syncthreads();
   if (i > 0) {
     double2 u = make_double2(0.0, 0.0);   // sum_q v_rq conj(w_cq) + w_rq conj(v_cq), q = g mod 4
     if (r < n) {
-      for (int q = g; q < i; q += 4) {
-        const double2 vq = V[r + (long)q * n];
-        double2 wq;
+#pragma unroll
+      for (int t = 0; t < QMAX; ++t) {
+        const int q = g + 4 * t;
+        if (q >= i) break;
+        const double2 vq = vq_r[t];
+        double2 wq = wq_r[t];
         if (q == i - 1) {
           wq = __ldcg(&p[r - c]);
           cmac(wq, al, vq);
           W[r + (long)q * n] = wq;
-        } else {
-          wq = W[r + (long)q * n];
         }
         cmacc(u, s_wc[q], vq);
         cmacc(u, s_vc[q], wq);
@@ -402,7 +423,7 @@ __global__ void __launch_bounds__(PCOL_THREADS) k_pcol(double2 *A, int n, int c,
   if (g != 0) return;
   double nrm = 0.0;
   if (r < n) {
-    double2 a = A[r + (long)c * n];
+    if (i == 0) a = A[r + (long)c * n];
     if (i > 0) {
       a = csub(a, cadd(cadd(s_u[0][rl], s_u[1][rl]), cadd(s_u[2][rl], s_u[3][rl])));
       A[r + (long)c * n] = a;
@@ -543,18 +564,33 @@ __global__ void __launch_bounds__(256) k_prows(double2 *A, int n, int c, int i, 
                                                const double2 *tau, const double2 *hscal, double2 *p,
                                                double2 *dotpart) {
   __shared__ double2 red[8][33];
-  pdl_wait();
-  pdl_trigger();
   const int o = c + 1, m = n - o;
   const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int x = blockIdx.x * 32 + rl;
+  // Before the wait: the panel columns V[:, q < i], W[:, q < i] (written two
+  // or more launches back); the partial products and corrections come from
+  // the predecessor.
+  constexpr int QMAX = (TPB + 7) / 8;
+  double2 vq_r[QMAX], wq_r[QMAX];
+#pragma unroll
+  for (int t = 0; t < QMAX; ++t) {
+    const int q = g + 8 * t;
+    const bool ok = x < m && q < i;
+    vq_r[t] = ok ? P[o + x + (long)q * n] : make_double2(0.0, 0.0);
+    wq_r[t] = ok ? P[o + x + (long)(b + q) * n] : make_double2(0.0, 0.0);
+  }
+  pdl_wait();
+  pdl_trigger();
   double2 y = make_double2(0.0, 0.0);
   if (x < m) {
     for (int s = g; s < nT; s += 8) y = cadd(y, part[(long)s * nmax + x]);
-    for (int q = g; q < i; q += 8) {
+#pragma unroll
+    for (int t = 0; t < QMAX; ++t) {
+      const int q = g + 8 * t;
+      if (q >= i) break;
       const double2 uw = ucorr[2 * q], uv = ucorr[2 * q + 1];
-      cmac(y, P[o + x + (long)q * n], make_double2(-uw.x, -uw.y));         // - V[r,q] (W^H v)_q
-      cmac(y, P[o + x + (long)(b + q) * n], make_double2(-uv.x, -uv.y));   // - W[r,q] (V^H v)_q
+      cmac(y, vq_r[t], make_double2(-uw.x, -uw.y));   // - V[r,q] (W^H v)_q
+      cmac(y, wq_r[t], make_double2(-uv.x, -uv.y));   // - W[r,q] (V^H v)_q
     }
   }
   red[g][rl] = y;

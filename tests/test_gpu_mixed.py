@@ -145,3 +145,38 @@ def test_mixed_steps_with_k_split():
     finally:
         pw.pw_autotune_gemm(0)
     assert np.abs(e - st.lam).max() < 1e-4
+
+
+def test_mixed_steps_si512_full_size_sampled():
+    # the timed configuration of the benchmark (Si-512, 1,152 bands, mixed,
+    # steps with nsub 2,304 then 3,456): no Ritz value rises; on sampled bands
+    # the Rayleigh quotient and residual norm of the returned vectors under
+    # the oracle's FP64 operator equal the solver's Ritz values and residual
+    # norms, and the sampled block is orthonormal
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 4, 10.0, precision="mixed")
+    nb = 1152
+    s = pw.pw_solver_create(lib.h, nb, tol=0.0, seed=0, precision="mixed")
+    e_prev, _ = pw.pw_solver_eigs(s, nb)
+    nsubs = []
+    for _ in range(2):
+        rep = pw.pw_subspace_step(lib.h, s)
+        nsubs.append(rep.nsub)
+        e, resid = pw.pw_solver_eigs(s, nb)
+        assert np.all(e <= e_prev + 1e-9)
+        e_prev = e
+    assert nsubs == [2 * nb, 3 * nb]
+    X = pw.new_block(lib.npw, nb)
+    pw.pw_solver_block(s, X)
+    pw.pw_solver_destroy(s)
+    cols = [0, 1, 575, nb - 1]
+    xs = X[:, cols].cpu().numpy()
+    hx = O.apply_H(orc, xs)
+    for k, j in enumerate(cols):
+        x, h = xs[:, k], hx[:, k]
+        rho = np.vdot(x, h).real / np.vdot(x, x).real
+        assert abs(rho - e[j]) < 1e-5, (j, rho, e[j])
+        r = np.linalg.norm(h - e[j] * x)
+        assert abs(r - resid[j]) < 1e-5 * max(1.0, r), (j, r, resid[j])
+    g = xs.conj().T @ xs
+    assert np.abs(g - np.eye(len(cols))).max() < 1e-5
