@@ -294,6 +294,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // ---------------- MMA issuer: CHUNK_KB K-blocks per accumulator buffer
       const uint32_t idesc = idesc_f16();
       const int nchunk = (nkb + CHUNK_KB - 1) / CHUNK_KB;
+      // operand descriptors of every stage, formed once; a K step of 16
+      // (32 bytes) adds 2 to the start-address field
+      uint64_t dA0[NSTAGE], dA1[NSTAGE], dB0[NSTAGE], dB1[NSTAGE];
+#pragma unroll
+      for (int s = 0; s < NSTAGE; ++s) {
+        const uint32_t a0 = smem_u32(smem + s * STAGE);
+        dA0[s] = smem_desc(a0);
+        dA1[s] = smem_desc(a0 + A_TILE);
+        dB0[s] = smem_desc(a0 + 2 * A_TILE);
+        dB1[s] = smem_desc(a0 + 2 * A_TILE + B_TILE);
+      }
       bool ok = true;
       for (int ch = 0; ch < nchunk && ok; ++ch) {
         const int b = ch & 1;
@@ -306,17 +317,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const uint32_t u = kb / NSTAGE;
           if (!mbar_wait(&full[s], u & 1)) { atomicOr(err, 2); ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a0 = smem_u32(smem + s * STAGE);
-          const uint32_t a1 = a0 + A_TILE;
-          const uint32_t b0 = a0 + 2 * A_TILE;
-          const uint32_t b1 = b0 + B_TILE;
+          uint64_t a0, a1, b0, b1;
+          // stage s of a runtime index: select among the precomputed descriptors
+#pragma unroll
+          for (int t = 0; t < NSTAGE; ++t)
+            if (t == s) { a0 = dA0[t]; a1 = dA1[t]; b0 = dB0[t]; b1 = dB1[t]; }
           const bool first = kb == ch * CHUNK_KB;
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint32_t off = kk * 32;
-            mma_f16(d, smem_desc(a0 + off), smem_desc(b0 + off), idesc, !(first && kk == 0));
-            mma_f16(d, smem_desc(a0 + off), smem_desc(b1 + off), idesc, 1);
-            mma_f16(d, smem_desc(a1 + off), smem_desc(b0 + off), idesc, 1);
+            const uint64_t o = 2 * kk;
+            mma_f16(d, a0 + o, b0 + o, idesc, !(first && kk == 0));
+            mma_f16(d, a0 + o, b1 + o, idesc, 1);
+            mma_f16(d, a1 + o, b0 + o, idesc, 1);
           }
           mma_commit(&empty[s]);
         }
