@@ -337,7 +337,8 @@ def run_gpu(args):
                         "batch_mib": fr.best.batch_bytes >> 20,
                         "ms_best": fr.ms_best, "ms_default": fr.ms_default,
                         "default": [fr.dflt.L, fr.dflt.R, fr.dflt.compact, fr.dflt.batch_bytes >> 20],
-                        "candidates": fr.ncand, "bands": min(nb, 256)}}
+                        "candidates": fr.ncand, "bands": min(nb, 256),
+                        "timed": [ln for ln in pw.pw_cell_fft_tune_log(cell.h).splitlines() if ln]}}
     solver = pw.pw_solver_create(cell.h, nb, tol=0.0, seed=0, precision=args.precision)
     for _ in range(args.warmup):
         pw.pw_subspace_step(cell.h, solver)

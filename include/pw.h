@@ -406,6 +406,11 @@ typedef struct {
  * precision), PW_ERR_OOM, PW_ERR_CUDA. */
 pw_status pw_cell_autotune_fft(pw_cell *cell, int nb, int precision, void *stream,
                                pw_fft_tune_report *rep);
+/* The candidates and times of the cell's last pw_cell_autotune_fft, one line
+ * each ("L= R= compact= batch_mib= bands_per_batch= ms="), into buf (len
+ * bytes, NUL-terminated, truncated); returns the full text length (0 if the
+ * cell was never tuned). */
+int pw_cell_fft_tune_log(const pw_cell *cell, char *buf, size_t len);
 
 /* K split of the split-FP16 tensor-core GEMMs (tiles of 128 x 128 x K/s,
  * partial sums reduced in FP64 in a fixed order), process-wide:

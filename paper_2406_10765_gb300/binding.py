@@ -483,6 +483,7 @@ _get_fft_plan = _sig("pw_cell_get_fft_plan", ct.c_int, [_vp, ct.c_int, ct.POINTE
 _tune_fft = _sig("pw_cell_autotune_fft", ct.c_int, [_vp, ct.c_int, ct.c_int, _vp,
                                                      ct.POINTER(pw_fft_tune_report)])
 _tune_gemm = _sig("pw_autotune_gemm", ct.c_int, [ct.c_int, ct.c_int])
+_tune_log = _sig("pw_cell_fft_tune_log", ct.c_int, [_vp, ct.c_char_p, ct.c_size_t])
 _tune_table = _sig("pw_autotune_gemm_table", ct.c_int, [ct.c_char_p, ct.c_size_t])
 
 
@@ -521,4 +522,12 @@ def pw_autotune_gemm_table():
     n = _tune_table(None, 0)
     buf = ct.create_string_buffer(256 * (n + 1) + 1)
     _tune_table(buf, len(buf))
+    return buf.value.decode()
+
+
+def pw_cell_fft_tune_log(cell):
+    """Candidates and times of the cell's last FFT tuning (text, one line each)."""
+    n = _tune_log(cell, None, 0)
+    buf = ct.create_string_buffer(n + 1)
+    _tune_log(cell, buf, len(buf))
     return buf.value.decode()

@@ -1,6 +1,6 @@
 // Register-resident line FFTs for the local part of H psi (Sec. II-B), used
-// when every grid dimension is N = L * R with L = 2^min(a, 5) lanes and
-// R = N / L <= 16 values per lane (N = 2^a 3^b).
+// when every grid dimension is N = L * R with L a power of two up to 32 lanes
+// and R = N / L <= 18 values per lane (N = 2^a 3^b).
 //
 // A line x[0..N) is held by a group of L lanes, lane l owning x[l + L r],
 // r < R.  With n = l + L r and k = k2 + R k1:
@@ -160,8 +160,10 @@ template <> __device__ __forceinline__ float2 from64r<float2>(double2 a) {
 
 constexpr int ZCB = 16;          // z-lines per block in K1 / K3
 constexpr int ZTHREADS = 256;
-template <typename C> struct RegPlaneThreads { static constexpr int value = 512; };
-template <> struct RegPlaneThreads<double2> { static constexpr int value = 256; };
+// threads of the plane kernels: 512 for FP32 lines of up to 9 values per
+// lane; 256 (twice the registers per thread) for longer FP32 lines and FP64
+template <typename C, int R> struct RegPlaneThreads { static constexpr int value = R >= 12 ? 256 : 512; };
+template <int R> struct RegPlaneThreads<double2, R> { static constexpr int value = 256; };
 
 // FFT of `nlines` lines held in shared memory (line i at buf + i * ls, element
 // e at e * es), all warps of the block; lines are processed G = 32 / L at a
@@ -236,7 +238,7 @@ __host__ __device__ inline size_t plane_smem_bytes(int mxmax, bool cp, int nthre
 }
 
 template <typename C, typename T, int L, int R, bool CP>
-__global__ void __launch_bounds__(RegPlaneThreads<C>::value) k_plane_reg(C *__restrict__ Z, int ncol,
+__global__ void __launch_bounds__(RegPlaneThreads<C, R>::value) k_plane_reg(C *__restrict__ Z, int ncol,
                                                                          const int *__restrict__ colxy,
                                                                          int mxmax, const C *__restrict__ twx,
                                                                          int Nz, const T *__restrict__ V) {
@@ -387,7 +389,7 @@ pw_status run_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hp
                     double scale, cudaStream_t st) {
   constexpr int N = L * R;
   if (2 * c->mxmax + 1 > N) return PW_ERR_ARG;
-  const size_t plane_bytes = plane_smem_bytes<C, L, R>(c->mxmax, CP, RegPlaneThreads<C>::value);
+  const size_t plane_bytes = plane_smem_bytes<C, L, R>(c->mxmax, CP, RegPlaneThreads<C, R>::value);
   if (plane_bytes > 227 * 1024) return PW_ERR_ARG;
   if (plane_bytes > 48 * 1024)
     PW_CUDA(cudaFuncSetAttribute(k_plane_reg<C, T, L, R, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -397,7 +399,7 @@ pw_status run_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hp
   k_sphere_to_z_reg<C, L, R><<<gcols, ZTHREADS, 0, st>>>(psi, ld, c->d_colstart, c->d_gcol, c->d_gz,
                                                          c->ncol, twtab<C>(c->ax[2]), Z);
   pw_count_launch();
-  k_plane_reg<C, T, L, R, CP><<<dim3(N, nbb), RegPlaneThreads<C>::value, plane_bytes, st>>>(
+  k_plane_reg<C, T, L, R, CP><<<dim3(N, nbb), RegPlaneThreads<C, R>::value, plane_bytes, st>>>(
       Z, c->ncol, c->d_colxy, c->mxmax, twtab<C>(c->ax[0]), N, V);
   pw_count_launch();
   k_z_to_sphere_reg<C, L, R><<<gcols, ZTHREADS, 0, st>>>(Z, c->ncol, twtab<C>(c->ax[2]), c->d_colstart,
@@ -412,14 +414,14 @@ pw_status run_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hp
 // plane points, so the sum over the group's bands runs in a fixed order in
 // registers; part[g][z][y][x] holds each group's sum.
 template <typename C, int L, int R>
-__global__ void __launch_bounds__(RegPlaneThreads<C>::value) k_density_reg(const C *__restrict__ Z, int ncol,
+__global__ void __launch_bounds__(RegPlaneThreads<C, R>::value) k_density_reg(const C *__restrict__ Z, int ncol,
                                                                            const int *__restrict__ colxy,
                                                                            int mxmax, const C *__restrict__ twx,
                                                                            int nbb, const double *__restrict__ occ,
                                                                            double *__restrict__ part) {
   typedef decltype(Z[0].x) T;
   constexpr int N = L * R, pxs = N + 1, G = 32 / L;
-  constexpr int NT = RegPlaneThreads<C>::value;
+  constexpr int NT = RegPlaneThreads<C, R>::value;
   constexpr int ACC = (N * N + NT - 1) / NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C *P = reinterpret_cast<C *>(smem_raw);
@@ -504,7 +506,7 @@ pw_status density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, C *Z, c
   k_sphere_to_z_reg<C, L, R><<<gcols, ZTHREADS, 0, st>>>(psi, ld, c->d_colstart, c->d_gcol, c->d_gz,
                                                          c->ncol, twtab<C>(c->ax[2]), Z);
   pw_count_launch();
-  k_density_reg<C, L, R><<<dim3(N, ngroups), RegPlaneThreads<C>::value, plane_bytes, st>>>(
+  k_density_reg<C, L, R><<<dim3(N, ngroups), RegPlaneThreads<C, R>::value, plane_bytes, st>>>(
       Z, c->ncol, c->d_colxy, c->mxmax, twtab<C>(c->ax[0]), nbb, occ, part);
   return pw_check_launch("density (register FFT)");
 }
@@ -523,8 +525,8 @@ pw_status reg_run32(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hp
 // shared memory of the plane kernel for a cell (full or compact layout)
 template <int L, int R>
 size_t reg_smem(const pw_cell *c, int fp32, int compact) {
-  return fp32 ? plane_smem_bytes<float2, L, R>(c->mxmax, compact != 0, RegPlaneThreads<float2>::value)
-              : plane_smem_bytes<double2, L, R>(c->mxmax, compact != 0, RegPlaneThreads<double2>::value);
+  return fp32 ? plane_smem_bytes<float2, L, R>(c->mxmax, compact != 0, RegPlaneThreads<float2, R>::value)
+              : plane_smem_bytes<double2, L, R>(c->mxmax, compact != 0, RegPlaneThreads<double2, R>::value);
 }
 template <int L, int R>
 pw_status reg_dens64(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, const double *occ, int ngroups,

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string>
 #include <vector>
 
 #include "pw.h"
@@ -96,6 +97,7 @@ struct pw_cell {
   int fft_plan[2] = {-2, -2};
   int fft_compact[2] = {0, 0};
   size_t fft_batch[2] = {0, 0};
+  std::string fft_tune_log;   // candidates and times of the last FFT tuning
   double *d_dpart = nullptr; size_t dpart_bytes = 0;   // density partial sums
   double *d_V0 = nullptr;                              // the cell's own V_loc while another V is set
   double2 *d_grid = nullptr; size_t grid_bytes = 0;    // full-grid FFT scratch

@@ -3,7 +3,11 @@
 // here the candidates are the register line-FFT factorisations N = L R of
 // the cell's grid, the Stockham passes, and the band batch of the z-pencils).
 // The K split of the tensor-core GEMMs is tuned in tc_gemm.cu.
+#include <stdio.h>
+#include <string.h>
+
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "pw_internal.cuh"
@@ -124,6 +128,7 @@ extern "C" pw_status pw_cell_autotune_fft(pw_cell *c, int nb, int precision, voi
     k_fill_scratch<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(psi, n);
     s = pw_check_launch("autotune fill");
   }
+  std::string log;
   double best = 1e300;
   int best_plan = dflt_idx, best_cp = dflt_cp;
   size_t best_batch = dflt_batch;
@@ -150,6 +155,13 @@ extern "C" pw_status pw_cell_autotune_fft(pw_cell *c, int nb, int precision, voi
       }
       if (s != PW_OK) break;
       ++r.ncand;
+      {
+        const pw_reg_plan *rp = pw_reg_plan_at(plans[pi].first);
+        char line[160];
+        snprintf(line, sizeof line, "L=%d R=%d compact=%d batch_mib=%zu bands_per_batch=%d ms=%.4f\n",
+                 rp ? rp->L : 0, rp ? rp->R : 0, plans[pi].second, batches[bi] >> 20, nbatch, ms);
+        log += line;
+      }
       const bool is_default = plans[pi].first == dflt_idx && plans[pi].second == dflt_cp && nbatch == dflt_nbatch;
       if (is_default) r.ms_default = ms;
       if (ms < best) {
@@ -173,8 +185,20 @@ extern "C" pw_status pw_cell_autotune_fft(pw_cell *c, int nb, int precision, voi
   c->fft_plan[fp32] = best_plan;
   c->fft_compact[fp32] = best_cp;
   c->fft_batch[fp32] = best_batch;
+  c->fft_tune_log = log;
   describe(c, fp32, &r.best);
   r.ms_best = best;
   if (rep) *rep = r;
   return PW_OK;
+}
+
+extern "C" int pw_cell_fft_tune_log(const pw_cell *c, char *buf, size_t len) {
+  if (!c) return 0;
+  const std::string &s = c->fft_tune_log;
+  if (buf && len) {
+    const size_t n = std::min(len - 1, s.size());
+    memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
+  return (int)s.size();
 }
