@@ -34,7 +34,12 @@ WORKLOADS = {
 E2E_TOL, E2E_MAXIT = 5e-6, 200      # a full solve (Si-512 converges in ~120 steps)
 # DRAM bytes (read + write) of one instance of a sub-stage, from one ncu
 # capture of the same kernels: (stage, n, nb) -> (bytes, summary)
-NCU_TRAFFIC = {("tridiag", 3456, 1152): (131.1e9, "profiles/householder_tridiag_n3456.md")}
+# DRAM bytes per stage from an ncu capture of the same kernels, when the
+# kernels have not changed since (else traffic is null with a note)
+NCU_TRAFFIC = {}
+NCU_TRAFFIC_STALE = {("tridiag", 3456, 1152): (
+    "profiles/householder_tridiag_n3456.md measured 131.1 GB per reduction before k_pcol and k_prows "
+    "began loading earlier panel columns ahead of their dependency wait; not re-captured since")}
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of the part (no FP64 tensor path)
 METRIC = "Si-512 eigensolver iters/s"
 
@@ -149,9 +154,10 @@ def roofline(stage, rr_part, fl, n, nb, precision):
     if dom in fp64:
         ach = fp64[dom] / (t_ms * 1e-3) / 1e12
         tr = NCU_TRAFFIC.get((dom, n, nb)) if not mixed or dom != "transform" else None
+        stale = NCU_TRAFFIC_STALE.get((dom, n, nb))
         roof.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
                     frac=ach / FP64_PEAK_TFLOPS, traffic=tr[0] if tr else None,
-                    traffic_source=tr[1] if tr else None,
+                    traffic_source=tr[1] if tr else stale,
                     peak_source="nominal FP64 rate: 152 SMs x 2.07 GHz x 2 DFMA/clk (measured DFMA 1.20)")
     elif dom in ("gram", "rot"):
         ach = fl[dom] / (t_ms * 1e-3) / 1e12
