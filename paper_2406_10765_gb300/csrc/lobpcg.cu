@@ -45,7 +45,7 @@ struct pw_solver {
   cudaEvent_t ev[12] = {};   // stage boundaries of the last step (7-10: H X and H P)
   int hx_applied = 0;        // H X was recomputed in the last refresh
   // mixed precision: split-FP16 operands of S, H S and the coefficients
-  pw_tc_operand opSA, opSB, opHSB, opST, opHST, opC, opCP, opM;
+  pw_tc_operand opSA, opSB, opST, opHST, opC, opCP, opM;
   double2 *Mx = nullptr;     // mixed: d o L^-H of the current Gram (3nb x 3nb)
   bool st_split_valid = false;   // opST holds the split of the current S
   int chunk_rows = 0;            // rows per chunk of the tall split products (0: automatic)
@@ -454,7 +454,7 @@ extern "C" void pw_solver_destroy(pw_solver *s) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : s->ev)
     if (e) cudaEventDestroy(e);
-  pw_tc_operand *ops[] = {&s->opSA, &s->opSB, &s->opHSB, &s->opST, &s->opHST, &s->opC, &s->opCP,
+  pw_tc_operand *ops[] = {&s->opSA, &s->opSB, &s->opST, &s->opHST, &s->opC, &s->opCP,
                           &s->opM};
   if (s->Mx) cudaFree(s->Mx);
   for (pw_tc_operand *o : ops) pw_tc_operand_free(o);

@@ -755,7 +755,8 @@ int max_split(int m, int n, int kblocks, int kb_lo) {
   return s;
 }
 
-void pool_keep(cudaStream_t) {
+// keep freed partial-sum buffers in the device's stream-ordered pool
+void pool_keep() {
   static std::mutex mu;
   static bool done[64] = {};
   int dev = 0;
@@ -776,7 +777,7 @@ pw_status launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const pw_tc_
   const int mtiles = (m + BM - 1) / BM, ntiles = (n + BN - 1) / BN;
   double *part = nullptr;
   if (split > 1) {
-    pool_keep(st);
+    pool_keep();
     PW_CUDA(cudaMallocAsync((void **)&part, (size_t)split * m * n * sizeof(double), st));
   }
   pw_count_launch();
