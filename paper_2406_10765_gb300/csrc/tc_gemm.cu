@@ -784,14 +784,17 @@ pw_status launch_gemm(const CUtensorMap &ma, const CUtensorMap &mb, const pw_tc_
   k_tc_gemm<<<dim3(mtiles * ntiles, split), NTHREADS, SMEM_BYTES, st>>>(
       ma, mb, A->rows_total, B->rows_total, m, n, A->kpad / BK, mtiles, ntiles, A->inv_scale, B->inv_scale, C,
       ldc, mode, accumulate, herm, kb_lo, tri_b, part, d_err);
-  PW_TRY(pw_check_launch("tc_gemm"));
+  pw_status r = pw_check_launch("tc_gemm");
   if (split > 1) {
-    pw_count_launch();
-    k_tc_reduce<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, st>>>(part, split, m, n, C, ldc, mode,
-                                                                        accumulate, herm);
-    PW_TRY(pw_check_launch("tc_gemm reduce"));
-    PW_CUDA(cudaFreeAsync(part, st));
+    if (r == PW_OK) {
+      pw_count_launch();
+      k_tc_reduce<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, st>>>(part, split, m, n, C, ldc, mode,
+                                                                          accumulate, herm);
+      r = pw_check_launch("tc_gemm reduce");
+    }
+    cudaFreeAsync(part, st);
   }
+  PW_TRY(r);
   if (herm) {
     const int ni = m / 2;
     pw_count_launch();
@@ -816,17 +819,26 @@ pw_status tune_split(const GemmKey &key, int m, int n, int smax, const CUtensorM
   GemmChoice best{1, 0.0f, 0.0f};
   for (int s = 1; s <= smax && r == PW_OK; s = s < 4 ? s + 1 : s * 2) {
     float ms = 1e30f;
-    for (int rep = 0; rep < 3 && r == PW_OK; ++rep) {
+    pw_status rs = PW_OK;
+    for (int rep = 0; rep < 3 && rs == PW_OK; ++rep) {
       cudaEventRecord(e0, st);
-      r = launch_gemm(ma, mb, A, B, m, n, Cs, ldc, key.mode, 0, key.herm, d_err, st, key.kb_lo, key.tri_b, s);
+      rs = launch_gemm(ma, mb, A, B, m, n, Cs, ldc, key.mode, 0, key.herm, d_err, st, key.kb_lo, key.tri_b, s);
       cudaEventRecord(e1, st);
       float t = 0.0f;
-      if (r == PW_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess &&
+      if (rs == PW_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess &&
           rep > 0)
         ms = std::min(ms, t);
     }
-    if (s == 1) best = GemmChoice{1, ms, ms};
-    else if (ms < best.ms_best) { best.split = s; best.ms_best = ms; }
+    if (s == 1) {
+      r = rs;   // the single-part product must run
+      best = GemmChoice{1, ms, ms};
+    } else if (rs != PW_OK) {
+      cudaGetLastError();   // e.g. no room for the partial sums: stop at the splits that ran
+      break;
+    } else if (ms < best.ms_best) {
+      best.split = s;
+      best.ms_best = ms;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
