@@ -429,6 +429,14 @@ pw_status pw_autotune_gemm(int mode, int split);
  * into buf (len bytes, NUL-terminated, truncated); returns the number of shapes. */
 int pw_autotune_gemm_table(char *buf, size_t len);
 
+/* Failure-detection self-test: one kernel waits, with the bounded wait of
+ * the tensor-core GEMM pipeline and a limit of `cycles` SM clocks (1 ..
+ * ~2e9), on a shared-memory barrier that nothing arrives on.  Returns
+ * PW_ERR_TIMEOUT when the wait gave up and reported as designed (the
+ * expected result; the context stays usable), PW_ERR_NUMERIC if it did not,
+ * PW_ERR_ARG, PW_ERR_CUDA.  Synchronises `stream`. */
+pw_status pw_selftest_bounded_wait(long long cycles, void *stream);
+
 /* Number of CUDA kernel launches the library has issued in this process
  * (all devices, all threads); a diagnostic counter for launch accounting. */
 uint64_t pw_kernel_launches(void);

@@ -531,3 +531,11 @@ def pw_cell_fft_tune_log(cell):
     buf = ct.create_string_buffer(n + 1)
     _tune_log(cell, buf, len(buf))
     return buf.value.decode()
+
+
+_selftest_wait = _sig("pw_selftest_bounded_wait", ct.c_int, [ct.c_longlong, _vp])
+
+
+def pw_selftest_bounded_wait(cycles, stream=None):
+    """Status of the bounded-wait self-test (PW_ERR_TIMEOUT is the expected result)."""
+    return int(_selftest_wait(int(cycles), _stream(stream)))

@@ -75,13 +75,16 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// bounded wait: false after `limit` clocks without the phase completing
+__device__ __forceinline__ bool mbar_wait_limit(uint64_t *bar, uint32_t parity, long long limit) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try(bar, parity))
-    if (clock64() - t0 > WAIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  return mbar_wait_limit(bar, parity, WAIT_CYCLES);
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
@@ -630,6 +633,19 @@ __global__ void __launch_bounds__(256) k_split_coef(const double2 *__restrict__ 
   }
 }
 
+// The bounded wait of the GEMM pipeline on a barrier that nothing arrives
+// on: it must give up after `limit` clocks and report, leaving the context
+// usable (failure detection without a fault or a hang).
+__global__ void k_wait_selftest(long long limit, int *err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_limit(&bar, 0, limit)) atomicOr(err, 16);
+}
+
 // sum of the K-split parts (in part order) into C, same destinations and
 // tile selection as the single-part epilogue
 __global__ void k_tc_reduce(const double *__restrict__ part, int splits, int m, int n,
@@ -988,4 +1004,24 @@ extern "C" pw_status pw_zgemm_tc(char opA, int m, int n, int k, const void *A, i
   pw_tc_operand_free(&a);
   pw_tc_operand_free(&b);
   return r;
+}
+
+extern "C" pw_status pw_selftest_bounded_wait(long long cycles, void *stream) {
+  if (cycles < 1 || cycles > WAIT_CYCLES) return PW_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int *d_err = nullptr, herr = 0;
+  PW_CUDA(cudaMalloc(&d_err, sizeof(int)));
+  pw_status r = PW_OK;
+  if (cudaMemsetAsync(d_err, 0, sizeof(int), st) != cudaSuccess) r = PW_ERR_CUDA;
+  if (r == PW_OK) {
+    pw_count_launch();
+    k_wait_selftest<<<1, 32, 0, st>>>(cycles, d_err);
+    r = pw_check_launch("wait selftest");
+  }
+  if (r == PW_OK && (cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                     cudaStreamSynchronize(st) != cudaSuccess))
+    r = PW_ERR_CUDA;
+  cudaFree(d_err);
+  if (r != PW_OK) return r;
+  return herr ? PW_ERR_TIMEOUT : PW_ERR_NUMERIC;   // the wait must have run out
 }

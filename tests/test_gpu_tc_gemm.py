@@ -94,3 +94,17 @@ def test_tc_gemm_autotuned_split():
     finally:
         pw.pw_autotune_gemm(0)
     assert pw.pw_autotune_gemm_table() == ""
+
+
+def test_bounded_wait_reports_and_context_survives():
+    # the pipeline's bounded wait on a barrier nothing arrives on gives up
+    # after the limit and reports (no fault, no hang); the context stays
+    # usable for the next product
+    import paper_2406_10765_gb300 as pw
+    assert pw.pw_selftest_bounded_wait(2_000_000) == pw.PW_ERR_TIMEOUT
+    assert pw.pw_selftest_bounded_wait(0) == pw.PW_ERR_ARG
+    A = _rand((500, 40), 31, 0.1)
+    B = _rand((500, 30), 32, 1.0)
+    C = pw.pw_zgemm_tc("C", _cm(A), _cm(B)).cpu().numpy()
+    bound = np.sqrt(500) * np.abs(A).max() * np.abs(B).max()
+    assert np.abs(C - A.conj().T @ B).max() < 2e-6 * bound
