@@ -140,7 +140,7 @@ def roofline(stage, rr_part, fl, n, nb, precision):
     if not mixed:
         fp64["transform"] = 8.0 * n ** 3
     names = {"tridiag": "Householder reduction (k_pcol, k_phemv, k_prows + rank-64 k_zgemm)",
-             "chol_inv": "Cholesky + triangular inverse (k_potf2, k_trsm_rows, k_zgemm)",
+             "chol_inv": "Cholesky + triangular inverse (k_potf2, k_trsm_inv, k_trinv_small, k_zgemm)",
              "backtransform": "compact-WY back-transformation (k_build_T + k_zgemm)",
              "transform": "L^-1 A L^-H", "dc": "divide and conquer (k_dc_*)",
              "gram": "S^H S, S^H HS", "rot": "rotations", "hpsi": "H W (FFT kernels + projectors)",
