@@ -400,8 +400,8 @@ typedef struct {
 
 /* Times the local part of H psi (FFT, V_loc, kinetic) on nb scratch bands
  * for every register plan that fits the cell's grid (full and compact plane)
- * and for the Stockham passes, each with z-pencil batches of 32, 64 and 128 MiB, and sets the
- * fastest on the cell for that precision.  Allocates and frees 2 npw nb
+ * and for the Stockham passes, each with z-pencil batches of 32, 64 and
+ * 128 MiB, and sets the fastest on the cell for that precision.  Allocates and frees 2 npw nb
  * complex128 of scratch; synchronises `stream`.  Errors: PW_ERR_ARG (nb < 1,
  * precision), PW_ERR_OOM, PW_ERR_CUDA. */
 pw_status pw_cell_autotune_fft(pw_cell *cell, int nb, int precision, void *stream,
@@ -418,15 +418,15 @@ int pw_cell_fft_tune_log(const pw_cell *cell, char *buf, size_t len);
  *   mode 1: each new product shape class (output tiles, K blocks rounded up
  *           to a power of two, K bounds, layout) with fewer than 608 output
  *           tiles is timed on its first call at s = 1, 2, 3, 4, 8, 16 (within
- *           limits: at least 4 K blocks per part, partial sums <= 256 MiB) on
+ *           limits: K >= 256 per part, partial sums <= 256 MiB) on
  *           a scratch output, and the fastest s is kept for the class (not
  *           under stream capture; that call synchronises its stream);
  *   mode 2: s = `split` wherever those limits allow it.
  * Results agree to rounding across splits.  Errors: PW_ERR_ARG. */
 pw_status pw_autotune_gemm(int mode, int split);
-/* The tuned shape classes as text, one line each ("mtiles= ntiles= k<= k_lo= ...
- * split= ms1= ms="),
- * into buf (len bytes, NUL-terminated, truncated); returns the number of shapes. */
+/* The tuned shape classes as text, one line each ("mtiles= ntiles= k<= k_lo=
+ * ... split= ms1= ms="), into buf (len bytes, NUL-terminated, truncated);
+ * returns the number of shapes. */
 int pw_autotune_gemm_table(char *buf, size_t len);
 
 /* Failure-detection self-test: one kernel waits, with the bounded wait of
