@@ -428,6 +428,11 @@ pw_status pw_autotune_gemm(int mode, int split);
  * ... split= ms1= ms="), into buf (len bytes, NUL-terminated, truncated);
  * returns the number of shapes. */
 int pw_autotune_gemm_table(char *buf, size_t len);
+/* Adds shape classes in the text format of pw_autotune_gemm_table (a table
+ * saved by an earlier process), so mode 1 uses them without timing again.
+ * Returns the number of lines added, or -1 (nothing after the first bad
+ * line is added) for a malformed line.  Host only: no device work. */
+int pw_autotune_gemm_load(const char *text);
 
 /* Failure-detection self-test: one kernel waits, with the bounded wait of
  * the tensor-core GEMM pipeline and a limit of `cycles` SM clocks (1 ..

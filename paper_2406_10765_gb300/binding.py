@@ -485,6 +485,7 @@ _tune_fft = _sig("pw_cell_autotune_fft", ct.c_int, [_vp, ct.c_int, ct.c_int, _vp
 _tune_gemm = _sig("pw_autotune_gemm", ct.c_int, [ct.c_int, ct.c_int])
 _tune_log = _sig("pw_cell_fft_tune_log", ct.c_int, [_vp, ct.c_char_p, ct.c_size_t])
 _tune_table = _sig("pw_autotune_gemm_table", ct.c_int, [ct.c_char_p, ct.c_size_t])
+_tune_load = _sig("pw_autotune_gemm_load", ct.c_int, [ct.c_char_p])
 
 
 def pw_fft_plans(n):
@@ -539,3 +540,11 @@ _selftest_wait = _sig("pw_selftest_bounded_wait", ct.c_int, [ct.c_longlong, _vp]
 def pw_selftest_bounded_wait(cycles, stream=None):
     """Status of the bounded-wait self-test (PW_ERR_TIMEOUT is the expected result)."""
     return int(_selftest_wait(int(cycles), _stream(stream)))
+
+
+def pw_autotune_gemm_load(text):
+    """Add K-split choices saved from pw_autotune_gemm_table; returns the lines added."""
+    n = _tune_load(text.encode())
+    if n < 0:
+        raise PwError(PW_ERR_ARG, "pw_autotune_gemm_load")
+    return n

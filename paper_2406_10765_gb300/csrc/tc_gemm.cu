@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 #include <map>
@@ -892,6 +893,31 @@ extern "C" int pw_autotune_gemm_table(char *buf, size_t len) {
     buf[c] = 0;
   }
   return (int)g_tune_table.size();
+}
+
+extern "C" int pw_autotune_gemm_load(const char *text) {
+  if (!text) return -1;
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  int added = 0;
+  const char *p = text;
+  while (*p) {
+    const char *e = strchr(p, '\n');
+    const std::string line(p, e ? (size_t)(e - p) : strlen(p));
+    p = e ? e + 1 : p + line.size();
+    if (line.empty()) continue;
+    GemmKey k{};
+    int kmax = 0, klo = 0, split = 0;
+    float ms1 = 0.0f, ms = 0.0f;
+    if (sscanf(line.c_str(), "mtiles=%d ntiles=%d k<=%d k_lo=%d tri_b=%d herm=%d mode=%d split=%d ms1=%f ms=%f",
+               &k.mtiles, &k.ntiles, &kmax, &klo, &k.tri_b, &k.herm, &k.mode, &split, &ms1, &ms) != 10 ||
+        k.mtiles < 1 || k.ntiles < 1 || kmax < BK || kmax % BK || klo < 0 || klo % BK || split < 1 || split > 16)
+      return -1;
+    k.kclass = kmax / BK;
+    k.kb_lo = klo / BK;
+    g_tune_table[k] = GemmChoice{split, ms1, ms};
+    ++added;
+  }
+  return added;
 }
 
 pw_status pw_tc_gemm(const pw_tc_operand *A, int m, const pw_tc_operand *B, int n, double2 *C, int ldc,

@@ -57,3 +57,18 @@ def test_autotuner_host_entry_points_without_gpu():
     pw.pw_autotune_gemm(2, 4)
     pw.pw_autotune_gemm(0)
     assert pw.pw_autotune_gemm_table() == ""
+
+
+def test_gemm_tuning_table_round_trip_without_gpu():
+    # a saved K-split table loads back into the process-wide table unchanged
+    import paper_2406_10765_gb300 as pw
+    pw.pw_autotune_gemm(0)
+    saved = ("mtiles=18 ntiles=9 k<=262144 k_lo=0 tri_b=0 herm=1 mode=0 split=8 ms1=2.6580 ms=1.7670\n"
+             "mtiles=2 ntiles=18 k<=4096 k_lo=128 tri_b=1 herm=0 mode=1 split=3 ms1=0.5000 ms=0.2500\n")
+    assert pw.pw_autotune_gemm_load(saved) == 2
+    table = pw.pw_autotune_gemm_table()
+    assert sorted(table.splitlines()) == sorted(saved.splitlines())
+    with pytest.raises(pw.PwError):
+        pw.pw_autotune_gemm_load("mtiles=1 ntiles=1 k<=100 k_lo=0 tri_b=0 herm=0 mode=0 split=2 ms1=1 ms=1\n")
+    pw.pw_autotune_gemm(0)
+    assert pw.pw_autotune_gemm_table() == ""
