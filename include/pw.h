@@ -91,8 +91,9 @@ pw_status pw_cell_info(const pw_cell *cell, int *npw, int grid[3], const int **m
 pw_status pw_cell_sizes(const pw_cell *cell, int *nproj, size_t *device_bytes);
 
 /* Selects the arithmetic of later pw_apply_H calls on this cell: PW_FP64, or
- * PW_MIXED (FP32 FFTs and split-BF16 tensor-core projector contractions,
- * FP64 kinetic term and FP64 accumulation of the result). */
+ * PW_MIXED (FP32 FFTs and split-FP16 tensor-core projector contractions --
+ * two FP16 slices per row-scaled operand, the reading of "split-BF16" that
+ * keeps 22 bits -- FP64 kinetic term and FP64 accumulation of the result). */
 pw_status pw_cell_set_precision(pw_cell *cell, int precision);
 
 /* hpsi = H psi for nb bands (Sec. II-A Eq. 1; FFT local term per Sec. II-B,
@@ -206,6 +207,21 @@ pw_status pw_solver_eigs(pw_solver *solver, double *eig, double *resid);
 
 /* Copies the current block X (device complex128 npw x nb, leading dim ld). */
 pw_status pw_solver_block(pw_solver *solver, void *psi, int ld);
+
+/* Search directions of Knyazev's method (the block P of the LOBPCG step,
+ * Sec. II-A names LOBPCG as an inner eigensolver).  pw_solver_set_p replaces
+ * P by the nb columns of p (complex128 npw x nb, leading dimension ld >= npw,
+ * host or device memory; columns are normalised, and in FP64 the matching
+ * H P is formed); the next pw_subspace_step then uses S = [X, W, P].  With
+ * pw_solver_get_p (copies P into p, same layout; *have_p = 1 once a step or
+ * set_p has defined it, may be NULL) and pw_solver_block, a solve can be saved
+ * and resumed: pw_solver_create with x0 = the saved block, then set_p.  A P
+ * that makes the overlap singular (for example columns inside span(X)) is
+ * dropped by the next step's Cholesky pivot test (pw_step_report.dropped_p).
+ * Both synchronise the solver's stream.  Errors: PW_ERR_ARG (NULL, ld < npw),
+ * PW_ERR_OOM, PW_ERR_CUDA. */
+pw_status pw_solver_set_p(pw_solver *solver, const void *p, int ld);
+pw_status pw_solver_get_p(pw_solver *solver, void *p, int ld, int *have_p);
 
 void pw_solver_destroy(pw_solver *solver);
 
@@ -358,6 +374,27 @@ pw_status pw_heev(int n, int nb, void *A, double *w, void *Y, void *stream);
 pw_status pw_zgemm_tc(char opA, int m, int n, int k, const void *A, int lda, const void *B,
                       int ldb, double beta, void *C, int ldc, void *stream);
 
+/* Complex FP64 matrix product on the FP16 tensor cores, FP64-accurate: the
+ * dense products of the Rayleigh-Ritz solve (Syevd, Sec. III-D, and the
+ * Cholesky and back-transformation around it) without the FP64 pipe.  Each
+ * real row of op(A) and each real column of op(B) is scaled by a power of
+ * two and written exactly as 8 integer slices of 7 bits (FP16 values); the
+ * slice products whose weights reach 2^-63 are accumulated exactly (FP32
+ * tensor-core sums over 64-wide K chunks are integers below 2^22) into a
+ * 64-bit fixed-point sum and converted to FP64 once.  Error per entry at
+ * most ~2K 2^-55 max_k |op(A)_ik| max_k |op(B)_kj|, within the FP64 product
+ * bound for rows without large internal range.
+ *   C (m x n) = alpha op(A) op(B) + beta C,  op in {'N', 'C'}:
+ *   op(A) = A (m x k, lda >= m) or A^H (A k x m, lda >= k);
+ *   op(B) = B (k x n, ldb >= k) or B^H (B n x k, ldb >= n).
+ * All device complex128, column-major; alpha, beta: host pointers to
+ * (re, im).  Allocates and frees its slice buffers; synchronises `stream`.
+ * Errors: PW_ERR_ARG (bad op, sizes, leading dimensions, NULL), PW_ERR_OOM,
+ * PW_ERR_CUDA, PW_ERR_TIMEOUT (a bounded device wait ran out). */
+pw_status pw_zgemm_f64tc(char opA, char opB, int m, int n, int k, const double *alpha, const void *A,
+                         int lda, const void *B, int ldb, const double *beta, void *C, int ldc,
+                         void *stream);
+
 /* ---- Autotuner: the plan and tile-shape choices of the hot kernels ----
  * Sec. III-D picks, for each execution step, the process count that runs it
  * fastest among the candidates that fit in memory.  On one GPU the matching
@@ -430,8 +467,9 @@ pw_status pw_autotune_gemm(int mode, int split);
 int pw_autotune_gemm_table(char *buf, size_t len);
 /* Adds shape classes in the text format of pw_autotune_gemm_table (a table
  * saved by an earlier process), so mode 1 uses them without timing again.
- * Returns the number of lines added, or -1 (nothing after the first bad
- * line is added) for a malformed line.  Host only: no device work. */
+ * Returns the number of lines added, or -1 for a malformed line, in which
+ * case nothing from `text` is added (the table is unchanged).  Host only: no
+ * device work. */
 int pw_autotune_gemm_load(const char *text);
 
 /* Failure-detection self-test: one kernel waits, with the bounded wait of

@@ -154,6 +154,29 @@ def pw_zgemm_tc(opA, A, B, C=None, beta=0.0, stream=None):
     return C
 
 
+_zgemm_f64tc = _sig("pw_zgemm_f64tc", ct.c_int, [ct.c_char, ct.c_char, ct.c_int, ct.c_int, ct.c_int,
+                                                  ct.POINTER(ct.c_double), _vp, ct.c_int, _vp, ct.c_int,
+                                                  ct.POINTER(ct.c_double), _vp, ct.c_int, _vp])
+
+
+def pw_zgemm_f64tc(opA, opB, A, B, C=None, alpha=1.0, beta=0.0, stream=None):
+    """C = alpha op(A) op(B) + beta C, FP64-accurate on the FP16 tensor cores.
+    A, B, C: column-major CUDA complex128 tensors (stride(0) == 1)."""
+    import torch
+    m, k = (A.shape if opA == "N" else A.shape[::-1])
+    n = B.shape[1] if opB == "N" else B.shape[0]
+    if C is None:
+        C = torch.zeros((n, m), dtype=torch.complex128, device=A.device).T
+    for t in (A, B, C):
+        assert t.stride(0) == 1
+    a = (ct.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+    b = (ct.c_double * 2)(complex(beta).real, complex(beta).imag)
+    ld = lambda t: max(t.stride(1), t.shape[0], 1)
+    _check(_zgemm_f64tc(opA.encode(), opB.encode(), m, n, k, a, _dptr(A), ld(A), _dptr(B), ld(B), b,
+                        _dptr(C), ld(C), _stream(stream)), "pw_zgemm_f64tc")
+    return C
+
+
 _launches = _sig("pw_kernel_launches", ct.c_uint64, [])
 
 
@@ -352,6 +375,28 @@ def pw_solver_eigs(solver, nbands):
 
 def pw_solver_block(solver, out):
     _check(_sblock(solver, _dptr(out), out.shape[0]), "pw_solver_block")
+
+
+_sset_p = _sig("pw_solver_set_p", ct.c_int, [_vp, _vp, ct.c_int])
+_sget_p = _sig("pw_solver_get_p", ct.c_int, [_vp, _vp, ct.c_int, ct.POINTER(ct.c_int)])
+
+
+def pw_solver_set_p(solver, p):
+    """Replace the search directions P by p (CUDA complex128 (npw, nb), column-major,
+    or a host numpy array)."""
+    if isinstance(p, np.ndarray):
+        keep = np.asfortranarray(p, dtype=np.complex128)
+        _check(_sset_p(solver, ct.c_void_p(keep.ctypes.data), keep.shape[0]), "pw_solver_set_p")
+        return
+    assert p.stride(0) == 1
+    _check(_sset_p(solver, _dptr(p), p.stride(1) if p.shape[1] > 1 else p.shape[0]), "pw_solver_set_p")
+
+
+def pw_solver_get_p(solver, out):
+    """Copy P into out (CUDA complex128 (npw, nb), column-major); returns whether P is defined."""
+    have = ct.c_int()
+    _check(_sget_p(solver, _dptr(out), out.shape[0], ct.byref(have)), "pw_solver_get_p")
+    return bool(have.value)
 
 
 def pw_solver_destroy(solver):

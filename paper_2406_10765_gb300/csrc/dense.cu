@@ -84,6 +84,9 @@ __global__ void k_diag_scale(const double2 *G, int ld, int n, double *dscale, in
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double g = G[i + (long)i * ld].x;
+  // a diagonal entry sum_g |s_g|^2 is finite for any finite basis column, so a
+  // NaN / Inf here means NaN / Inf in the basis (or in its split operands)
+  if (!isfinite(g)) atomicOr(flag, 8);
   if (!(g > 0.0)) { atomicOr(flag, 1); dscale[i] = 0.0; return; }
   dscale[i] = 1.0 / sqrt(g);
 }
@@ -224,7 +227,9 @@ __global__ void k_zero_upper(double2 *A, int n) {
   if (i < n && j < n && i < j) A[i + (long)j * n] = make_double2(0.0, 0.0);
 }
 
-// flag |= 4 if min pivot <= tol * max pivot (or a pivot is not finite)
+// flag |= 4 if min pivot <= tol * max pivot or a pivot is not finite (a tiny
+// pivot can overflow the columns after it, so a non-finite pivot is a
+// breakdown, not evidence of NaN / Inf input: k_diag_scale reports those)
 __global__ void k_chol_check(const double *piv, int n, double tol, int *flag) {
   __shared__ double sh[32];
   double mn = 1e300, mx = 0.0;
@@ -1423,6 +1428,7 @@ pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, int
   int flag = 0;
   PW_CUDA(cudaMemcpyAsync(&flag, ws->flag, 4, cudaMemcpyDeviceToHost, st));
   PW_CUDA(cudaStreamSynchronize(st));
+  if (flag & 8) return PW_ERR_NUMERIC;
   if (flag) { *chol_ok = 0; return PW_OK; }
   PW_TRY(trinv(ws, ws->G, ws->Linv, n, st));
   cudaEventRecord(ws->ev[1], st);
@@ -1497,6 +1503,7 @@ pw_status pw_rr_factor(pw_dense_ws *ws, int n, const double2 *G, int ldg, double
   int flag = 0;
   PW_CUDA(cudaMemcpyAsync(&flag, ws->flag, 4, cudaMemcpyDeviceToHost, st));
   PW_CUDA(cudaStreamSynchronize(st));
+  if (flag & 8) return PW_ERR_NUMERIC;
   if (flag) { *chol_ok = 0; return PW_OK; }
   PW_TRY(trinv(ws, ws->G, ws->Linv, n, st));
   pw_count_launch();

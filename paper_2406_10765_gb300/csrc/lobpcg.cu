@@ -688,6 +688,32 @@ extern "C" pw_status pw_solver_block(pw_solver *s, void *psi, int ld) {
   return PW_OK;
 }
 
+extern "C" pw_status pw_solver_set_p(pw_solver *s, const void *p, int ld) {
+  if (!s || !p || ld < s->npw) return PW_ERR_ARG;
+  const int nb = s->nb, npw = s->npw;
+  // host or device memory (unified addressing decides the direction)
+  PW_CUDA(cudaMemcpy2DAsync(s->P, (size_t)npw * 16, p, (size_t)ld * 16, (size_t)npw * 16, nb,
+                            cudaMemcpyDefault, s->st));
+  // the FP64 step carries H P through the rotations, so form it here (in the
+  // solver's precision); the mixed step recomputes H P itself
+  if (!s->fresh_h) PW_TRY(solver_apply_H(s, s->P, s->HP, nb));
+  pw_count_launch();
+  k_normalize_cols<<<nb, 256, 0, s->st>>>(s->P, s->fresh_h ? nullptr : s->HP, npw, npw);
+  PW_TRY(pw_check_launch("set P"));
+  PW_CUDA(cudaStreamSynchronize(s->st));
+  s->haveP = true;
+  return PW_OK;
+}
+
+extern "C" pw_status pw_solver_get_p(pw_solver *s, void *p, int ld, int *have_p) {
+  if (!s || !p || ld < s->npw) return PW_ERR_ARG;
+  if (have_p) *have_p = s->haveP ? 1 : 0;
+  PW_CUDA(cudaMemcpy2DAsync(p, (size_t)ld * 16, s->P, (size_t)s->npw * 16, (size_t)s->npw * 16, s->nb,
+                            cudaMemcpyDefault, s->st));
+  PW_CUDA(cudaStreamSynchronize(s->st));
+  return PW_OK;
+}
+
 // FP64 steps after a mixed solve: the split-precision floor leaves a few
 // bands just above tol, which one or two FP64 steps finish; more than this
 // means the mixed solve did not converge and FP64 (~20x slower) would not help

@@ -51,9 +51,12 @@ extern "C" pw_status pw_apply_H_noalloc(pw_cell *c, const void *psi, int ld, int
   if (!psi || !hpsi || ld < c->npw) return PW_ERR_ARG;
   if (c->proj_onthefly) return PW_ERR_ARG;   // regenerating beta needs a buffer
   // carve the scratch: projector coefficients B, GEMM partial sums, z-pencils
-  const size_t b_bytes = round_up((size_t)c->nproj * nb * sizeof(double2));
-  const size_t ws_elems = std::max(pw_zgemm_ws_elems(c->nproj, nb, c->npw),
-                                   pw_zgemm_ws_elems(c->npw, nb, c->nproj));
+  // (a cell without atoms has no projectors and needs neither of the first two)
+  const bool nonlocal = c->nproj > 0;
+  const size_t b_bytes = nonlocal ? round_up((size_t)c->nproj * nb * sizeof(double2)) : 0;
+  const size_t ws_elems = nonlocal ? std::max(pw_zgemm_ws_elems(c->nproj, nb, c->npw),
+                                              pw_zgemm_ws_elems(c->npw, nb, c->nproj))
+                                   : 0;
   const size_t ws_bytes = round_up(ws_elems * sizeof(double2));
   const size_t z_one = pw_local_zbytes_per_band(c);
   if (b_bytes + ws_bytes + z_one > (size_t)PW_NOALLOC_SCRATCH_BYTES) return PW_ERR_ARG;
@@ -66,6 +69,7 @@ extern "C" pw_status pw_apply_H_noalloc(pw_cell *c, const void *psi, int ld, int
   const size_t zbytes = (size_t)PW_NOALLOC_SCRATCH_BYTES - b_bytes - ws_bytes;
   cudaStream_t st = (cudaStream_t)stream;
   PW_TRY(pw_apply_local_fp64_into(c, (const double2 *)psi, ld, nb, (double2 *)hpsi, zbuf, zbytes, st));
+  if (!nonlocal) return PW_OK;
   return pw_apply_nonlocal_fp64_into(c, (const double2 *)psi, ld, nb, (double2 *)hpsi, B, ws,
                                      ws_elems, st);
 }

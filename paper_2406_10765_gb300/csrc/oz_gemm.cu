@@ -1,0 +1,664 @@
+// FP64-accurate complex GEMM on the FP16 tensor cores (an Ozaki-type split
+// of each operand into short integer slices), for the dense products of the
+// Rayleigh-Ritz step -- the Cholesky and triangular-inverse updates, the
+// Householder panel updates and the back-transformation of the small
+// eigensolve (Syevd, Sec. III-D) -- which the FP64 pipe of this part runs at
+// only ~1.2 TFLOP/s.
+//
+// Arithmetic (C = op(A) op(B), complex, K = inner dimension):
+//   * Real form: row i of op(A) becomes one real row over K' = 2K,
+//     (re_k, im_k) interleaved; column j of op(B) becomes two real rows,
+//     (re, -im) and (im, re), so D[i][2j] = Re C_ij and D[i][2j+1] = Im C_ij.
+//   * Each real row r is scaled by a power of two 2^e_r so that its largest
+//     entry lies in [1/2, 1), and the scaled entry x is written exactly (to
+//     2^-56) as x = sum_{p=1..S} d_p 2^(-BETA p) with integer digits,
+//     |d_1| <= 2^BETA, |d_p| <= 2^(BETA-1), stored as FP16 (S = 8, BETA = 7).
+//   * The slice products d_p(a) d_q(b) with p + q = g are summed in one FP32
+//     tensor-memory accumulator per group g (g = 2..S+1; the pairs with
+//     p + q > S + 1 are below 2^-55 of the largest product and dropped).  Over
+//     a chunk of 64 real K every partial sum is an integer below 2^22, so the
+//     FP32 accumulation is exact whatever its rounding.
+//   * After each chunk the epilogue adds every group, shifted to a common
+//     binary point 2^-L, into a 64-bit integer per output (exact except for
+//     a rounding of the lowest groups below 2^-L), and at the end converts
+//     to FP64 and removes the row and column scales.
+// The error is at most ~K' 2^-55 max|a_i| max|b_j| per entry (the row and
+// column maxima), inside the usual FP64 bound K' u |a||b| for rows without
+// large internal dynamic range.
+//
+// Kernel: tile of 128 complex rows x 32 complex columns (128 x 64 real) per
+// CTA; warp 0 = TMA producer, warp 1 = MMA issuer (one thread), warps 2..9 =
+// epilogue.  Two shared-memory stages of 32 real K, each holding all S slices
+// of the A and B tiles (64-byte swizzle); eight 64-column FP32 accumulators
+// fill the 512 tensor-memory columns.  Every mbarrier wait is bounded; on
+// timeout the CTA records an error word, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "oz_gemm.cuh"
+#include "pw_internal.cuh"
+
+namespace {
+
+constexpr int S = PW_OZ_SLICES;       // slices per operand
+constexpr int BETA = 7;               // bits per slice
+constexpr int NG = S;                 // accumulator groups g = 2..S+1
+constexpr int BM = 128, BN = 64, BK = 32;   // real rows, real columns, real K per stage
+constexpr int A_T = BM * BK * 2;      // 8 KB per slice
+constexpr int B_T = BN * BK * 2;      // 4 KB per slice
+constexpr int STAGE = S * (A_T + B_T);   // 96 KB
+constexpr int NSTAGE = 2;
+constexpr int CHUNK_KB = 2;           // K blocks per exact accumulation chunk (64 real K)
+constexpr int SMEM_BYTES = NSTAGE * STAGE + 1024 + 512;
+constexpr int TMEM_COLS = 512;
+constexpr int EPI_WARPS = 8;
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
+constexpr long long WAIT_CYCLES = 2000000000ll;   // ~1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false after WAIT_CYCLES clocks without the phase completing
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 32
+// FP16), 8-row groups 512 B apart
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                   // descriptor version (sm_100 family)
+  d |= (uint64_t)4 << 61;                   // swizzle: 64B
+  return d;
+}
+// instruction descriptor, kind::f16: FP16 A and B, FP32 D, both K-major, M = 128, N = 64
+__host__ __device__ constexpr uint32_t idesc_oz() {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// x 2^k by exponent arithmetic (x finite); results below the normal range are zero
+__device__ __forceinline__ double scale_pow2(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return __longlong_as_double(b & (long long)0x8000000000000000ull);
+  const int en = ex + k;
+  if (en <= 0) return __longlong_as_double(b & (long long)0x8000000000000000ull);
+  if (en >= 0x7FF) return __longlong_as_double((b & (long long)0x8000000000000000ull) | 0x7FF0000000000000ll);
+  return __longlong_as_double(b + ((long long)k << 52));
+}
+
+// An FP32 accumulator value holding an integer |v| < 2^22, as an int: adding
+// 1.5 * 2^23 puts the integer into the low mantissa bits
+__device__ __forceinline__ int f2i_exact(uint32_t bits) {
+  const float v = __uint_as_float(bits) + 12582912.0f;
+  return __float_as_int(v) - 0x4B400000;
+}
+
+// v 2^sh into the 64-bit fixed-point sum (sh < 0: rounded to nearest)
+__device__ __forceinline__ long long shifted(int v, int sh) {
+  if (sh >= 0) return (long long)v << sh;
+  return ((long long)v + (1ll << (-sh - 1))) >> (-sh);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              int a_slice_rows, int b_slice_rows, int m, int n, int kblocks, int mtiles, int ntiles,
+              const int *__restrict__ ea, const int *__restrict__ eb, double2 alpha, double2 beta,
+              double2 *__restrict__ C, int ldc, int herm, double2 *__restrict__ part, int *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(smem + NSTAGE * STAGE);
+  uint64_t *empty = full + NSTAGE;
+  uint64_t *accf = empty + NSTAGE;     // [NG] group accumulator ready
+  uint64_t *acce = accf + NG;          // [NG] group accumulator drained
+  uint32_t *tmem_slot = (uint32_t *)(acce + NG);
+
+  const int tile = blockIdx.x;
+  const int mt = tile / ntiles, nt = tile % ntiles;
+  if (mt >= mtiles) return;
+  const int m0 = mt * BM;              // complex rows m0 .. m0 + 127
+  const int j0 = nt * (BN / 2);        // complex columns j0 .. j0 + 31
+  // Hermitian output, upper part (mirrored later): skip tiles strictly below
+  // the diagonal; lower part: tiles holding no element with j/64 <= i/64
+  if (herm == 1 && m0 > j0 + BN / 2 - 1) return;
+  if (herm == 2 && (j0 >> 6) > ((m0 + BM - 1) >> 6)) return;
+  // K range of the tile (real K blocks): triangular operands are zero outside
+  int kb_lo = 0, kb_hi = kblocks;
+  if (herm == 3) kb_lo = min(kblocks, (2 * m0) / BK);
+  if (herm == 4) kb_lo = min(kblocks, (2 * j0) / BK);
+  if (herm == 5) kb_hi = min(kblocks, (2 * (m0 + BM) + BK - 1) / BK);
+  // K split: part z of gridDim.y takes an equal share, in whole chunks
+  const int ntot = max(0, kb_hi - kb_lo);
+  const int nch = (ntot + CHUNK_KB - 1) / CHUNK_KB;
+  const int per = (nch + (int)gridDim.y - 1) / (int)gridDim.y;
+  const int c0 = min(nch, (int)blockIdx.y * per), c1 = min(nch, c0 + per);
+  const int kb_beg = kb_lo + c0 * CHUNK_KB;
+  const int nkb = max(0, min(kb_hi, kb_lo + c1 * CHUNK_KB) - kb_beg);
+  const int nchunk = (nkb + CHUNK_KB - 1) / CHUNK_KB;
+  // binary point of the fixed-point sum: |sum| <= K' (scaled entries < 1)
+  int lg = 0;
+  while ((1 << lg) < max(1, nkb * BK)) ++lg;
+  const int Lfix = min(56, 62 - lg);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int g = 0; g < NG; ++g) { mbar_init(&accf[g], 1); mbar_init(&acce[g], EPI_WARPS); }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer: all S slices of the A and B tiles per stage
+      for (int i = 0; i < nkb; ++i) {
+        const int s = i % NSTAGE;
+        const uint32_t u = i / NSTAGE;
+        if (!mbar_wait(&empty[s], (u & 1) ^ 1)) { atomicOr(err, 1); break; }
+        unsigned char *st = smem + s * STAGE;
+        mbar_expect_tx(&full[s], STAGE);
+        const int x = (kb_beg + i) * BK;
+#pragma unroll
+        for (int p = 0; p < S; ++p) {
+          tma_load_2d(st + p * A_T, &mapA, &full[s], x, p * a_slice_rows + m0);
+          tma_load_2d(st + S * A_T + p * B_T, &mapB, &full[s], x, p * b_slice_rows + 2 * j0);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      const uint32_t idesc = idesc_oz();
+      bool ok = true;
+      for (int i = 0; i < nkb && ok; ++i) {
+        const int s = i % NSTAGE;
+        const uint32_t u = i / NSTAGE;
+        const int ch = i / CHUNK_KB;
+        const bool first = (i % CHUNK_KB) == 0;
+        const bool last = (i % CHUNK_KB) == CHUNK_KB - 1 || i == nkb - 1;
+        if (!mbar_wait(&full[s], u & 1)) { atomicOr(err, 2); break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base = smem_u32(smem + s * STAGE);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+#pragma unroll
+          for (int g = 0; g < NG; ++g) {
+            const int d = g + 2;
+            if (first && kk == 0) {
+              // the epilogue has read this group's previous chunk
+              if (!mbar_wait(&acce[g], ((uint32_t)ch & 1) ^ 1)) { atomicOr(err, 8); ok = false; break; }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            const int plo = max(1, d - S), phi = min(S, d - 1);
+#pragma unroll
+            for (int p = plo; p <= phi; ++p) {
+              const int q = d - p;
+              const uint64_t da = smem_desc_sw64(base + (p - 1) * A_T) + 2 * kk;
+              const uint64_t db = smem_desc_sw64(base + S * A_T + (q - 1) * B_T) + 2 * kk;
+              mma_f16(tmem + (uint32_t)(g * BN), da, db, idesc, !(first && kk == 0 && p == plo));
+            }
+            if (last && kk == BK / 16 - 1) mma_commit(&accf[g]);
+          }
+          if (!ok) break;
+        }
+        mma_commit(&empty[s]);
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..9; lane quarter q, column half h
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const uint32_t lanes = (uint32_t)(q * 32) << 16;
+    long long acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0;
+    bool ok = true;
+    for (int ch = 0; ch < nchunk && ok; ++ch) {
+#pragma unroll 1
+      for (int g = 0; g < NG; ++g) {
+        if (!mbar_wait(&accf[g], (uint32_t)ch & 1)) { atomicOr(err, 4); ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t v[32];
+        tmem_ld32(tmem + lanes + (uint32_t)(g * BN + h * 32), v);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[g]);
+        const int sh = Lfix - BETA * (g + 2);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[i] += shifted(f2i_exact(v[i]), sh);
+      }
+    }
+    const int i = m0 + q * 32 + lane;              // complex output row
+    if (ok && i < m) {
+      const int jb = j0 + h * 16;                  // first complex column of this thread
+      const int ka = -Lfix - ea[i];
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int j = jb + t;
+        if (j >= n) continue;
+        if (herm == 2 && (j >> 6) > (i >> 6)) continue;
+        const int k = ka - eb[j];
+        const double re = scale_pow2((double)acc[2 * t], k);
+        const double im = scale_pow2((double)acc[2 * t + 1], k);
+        if (part) {
+          part[(long)blockIdx.y * m * n + i + (long)j * m] = make_double2(re, im);
+        } else {
+          double2 r = make_double2(alpha.x * re - alpha.y * im, alpha.x * im + alpha.y * re);
+          if (beta.x != 0.0 || beta.y != 0.0) {
+            const double2 c = C[i + (long)j * ldc];
+            r.x += beta.x * c.x - beta.y * c.y;
+            r.y += beta.x * c.y + beta.y * c.x;
+          }
+          C[i + (long)j * ldc] = r;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+// sum of the K-split parts (in part order), then alpha, beta; same element
+// selection as the single-part epilogue
+__global__ void k_oz_reduce(const double2 *__restrict__ part, int splits, int m, int n, double2 alpha,
+                            double2 beta, double2 *__restrict__ C, int ldc, int herm) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)m * n) return;
+  const int i = (int)(idx % m), j = (int)(idx / m);
+  const int m0 = (i / BM) * BM, j0 = (j / (BN / 2)) * (BN / 2);
+  if (herm == 1 && m0 > j0 + BN / 2 - 1) return;
+  if (herm == 2 && (j >> 6) > (i >> 6)) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int z = 0; z < splits; ++z) {
+    const double2 v = part[(long)z * m * n + idx];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  double2 r = make_double2(alpha.x * s.x - alpha.y * s.y, alpha.x * s.y + alpha.y * s.x);
+  if (beta.x != 0.0 || beta.y != 0.0) {
+    const double2 c = C[i + (long)j * ldc];
+    r.x += beta.x * c.x - beta.y * c.y;
+    r.y += beta.x * c.y + beta.y * c.x;
+  }
+  C[i + (long)j * ldc] = r;
+}
+
+// lower triangle <- conj(upper) (n x n, ld)
+__global__ void k_oz_mirror(double2 *C, int ldc, int n) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 32 + threadIdx.y;
+  if (i >= n || j >= n || i <= j) return;
+  const double2 u = C[j + (long)i * ldc];
+  C[i + (long)j * ldc] = make_double2(u.x, -u.y);
+}
+
+// ------------------------------------------------------------- slicing ----
+// |x| as ordered integer bits
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+// exponent e with max 2^e in [1/2, 1) from the bits of the row maximum
+__device__ __forceinline__ int row_exp(unsigned long long mb) {
+  const int ex = (int)(mb >> 52);
+  if (ex == 0) return 0;                 // zero (or subnormal) row: any scale works
+  return 1022 - ex;                      // max in [2^(ex-1023), 2^(ex-1022)) -> [1/2, 1)
+}
+// the S digits of x 2^e (|x 2^e| < 1), as FP16 integers: the fixed-point value
+// F = round(x 2^(e + 56)) is peeled from the top, BETA bits at a time, each
+// digit rounded to nearest (integer arithmetic only)
+__device__ __forceinline__ void digits(double x, int e, __half *out) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  long long F = 0;
+  if (ex != 0) {
+    const long long mant = (b & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;   // 53 bits
+    const int sa = ex - 1075 + e + 56;                                     // F = mant 2^sa
+    if (sa >= 0) F = mant << sa;
+    else if (sa > -64) F = (mant + (1ll << (-sa - 1))) >> (-sa);
+    if (b < 0) F = -F;
+  }
+#pragma unroll
+  for (int p = 1; p <= S; ++p) {
+    const int sh = 56 - BETA * p;
+    long long dgt;
+    if (sh > 0) {
+      dgt = (F + (1ll << (sh - 1))) >> sh;
+      F -= dgt << sh;
+    } else {
+      dgt = F;
+      F = 0;
+    }
+    out[p - 1] = __int2half_rn((int)dgt);
+  }
+}
+
+// Slices of the real rows of an operand.  The complex "row" r over k is
+//   contiguous:  v_kappa = X[kappa + r ld]      (a column of X)
+//   strided:     v_kappa = X[r + kappa ld]      (a row of X)
+// conjugated if conj.  bside = 0: one real row r = (re, im) over K' = 2k;
+// bside = 1: two real rows 2r = (re, -im), 2r + 1 = (im, re).
+// out: [S][rows_total][kpad] FP16, e: row exponents (one per complex row).
+__global__ void __launch_bounds__(256) k_oz_slice_contig(const double2 *__restrict__ X, int ld, int k, int conj,
+                                                         int bside, int kpad, int rows_total,
+                                                         __half *__restrict__ out, int *__restrict__ e) {
+  __shared__ unsigned long long shm[8];
+  const int r = blockIdx.x;
+  const double2 *x = X + (long)r * ld;
+  unsigned long long mb = 0;
+  for (int t = threadIdx.x; t < k; t += blockDim.x) {
+    const double2 v = x[t];
+    const unsigned long long a = abs_bits(v.x), c = abs_bits(v.y);
+    mb = max(mb, max(a, c));
+  }
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mb;
+  __syncthreads();
+  mb = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mb = max(mb, shm[w]);
+  const int ex = row_exp(mb);
+  if (threadIdx.x == 0) e[r] = ex;
+  const long slice = (long)rows_total * kpad;
+  for (int t = threadIdx.x; t < kpad / 2; t += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    if (t < k) {
+      const double2 v = x[t];
+      re = v.x;
+      im = conj ? -v.y : v.y;
+    }
+    __half dr[S], di[S];
+    digits(re, ex, dr);
+    digits(im, ex, di);
+    if (!bside) {
+      __half *o = out + (long)r * kpad + 2 * t;
+#pragma unroll
+      for (int p = 0; p < S; ++p) *(__half2 *)(o + p * slice) = __halves2half2(dr[p], di[p]);
+    } else {
+      __half *o0 = out + (long)(2 * r) * kpad + 2 * t, *o1 = o0 + kpad;
+#pragma unroll
+      for (int p = 0; p < S; ++p) {
+        *(__half2 *)(o0 + p * slice) = __halves2half2(dr[p], __hneg(di[p]));
+        *(__half2 *)(o1 + p * slice) = __halves2half2(di[p], dr[p]);
+      }
+    }
+  }
+}
+
+// row maxima of the strided rows (one thread per row, reads coalesced across rows)
+__global__ void k_oz_rowexp(const double2 *__restrict__ X, int ld, int nrows, int k, int *__restrict__ e) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  unsigned long long mb = 0;
+  for (int t = 0; t < k; ++t) {
+    const double2 v = X[r + (long)t * ld];
+    mb = max(mb, max(abs_bits(v.x), abs_bits(v.y)));
+  }
+  e[r] = row_exp(mb);
+}
+
+// strided rows: 32 rows x 64 K tile through shared memory (reads along r,
+// writes along K)
+__global__ void __launch_bounds__(256) k_oz_slice_strided(const double2 *__restrict__ X, int ld, int nrows, int k,
+                                                          int conj, int bside, int kpad, int rows_total,
+                                                          const int *__restrict__ e, __half *__restrict__ out) {
+  __shared__ double2 tileS[64][33];
+  const int r0 = blockIdx.x * 32, t0 = blockIdx.y * 64;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int tt = ty; tt < 64; tt += 8) {
+    const int r = r0 + tx, t = t0 + tt;
+    double2 v = make_double2(0.0, 0.0);
+    if (r < nrows && t < k) v = X[r + (long)t * ld];
+    if (conj) v.y = -v.y;
+    tileS[tt][tx] = v;
+  }
+  __syncthreads();
+  const long slice = (long)rows_total * kpad;
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int r = r0 + rr;
+    if (r >= nrows) continue;
+    const int ex = e[r];
+    for (int tt = tx; tt < 64; tt += 32) {
+      const int t = t0 + tt;
+      if (2 * t >= kpad) continue;
+      const double2 v = tileS[tt][rr];
+      __half dr[S], di[S];
+      digits(v.x, ex, dr);
+      digits(v.y, ex, di);
+      if (!bside) {
+        __half *o = out + (long)r * kpad + 2 * t;
+#pragma unroll
+        for (int p = 0; p < S; ++p) *(__half2 *)(o + p * slice) = __halves2half2(dr[p], di[p]);
+      } else {
+        __half *o0 = out + (long)(2 * r) * kpad + 2 * t, *o1 = o0 + kpad;
+#pragma unroll
+        for (int p = 0; p < S; ++p) {
+          *(__half2 *)(o0 + p * slice) = __halves2half2(dr[p], __hneg(di[p]));
+          *(__half2 *)(o1 + p * slice) = __halves2half2(di[p], dr[p]);
+        }
+      }
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap *map, const void *base, int kpad, long rows, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// slices of op(X)'s rows (bside 0) or of op(X)'s columns (bside 1):
+//   A side: op = 'N': rows of X (m x k) -> strided; op = 'C': columns of X (k x m) -> contiguous, conj
+//   B side: op = 'N': columns of X (k x n) -> contiguous; op = 'C': rows of X (n x k) -> strided, conj
+pw_status slice_operand(char op, int bside, const double2 *X, int ld, int nrows, int k, int kpad,
+                        int rows_total, __half *out, int *e, cudaStream_t st) {
+  const bool contig = bside ? op == 'N' : op == 'C';
+  const int conj = op == 'C';
+  if (contig) {
+    pw_count_launch();
+    k_oz_slice_contig<<<nrows, 256, 0, st>>>(X, ld, k, conj, bside, kpad, rows_total, out, e);
+  } else {
+    pw_count_launch();
+    k_oz_rowexp<<<(nrows + 255) / 256, 256, 0, st>>>(X, ld, nrows, k, e);
+    pw_count_launch();
+    k_oz_slice_strided<<<dim3((nrows + 31) / 32, (kpad / 2 + 63) / 64), 256, 0, st>>>(
+        X, ld, nrows, k, conj, bside, kpad, rows_total, e, out);
+  }
+  return pw_check_launch("oz slice");
+}
+
+int g_max_parts = 16;
+
+}  // namespace
+
+size_t pw_oz_ws_bytes(int m, int n, int k) {
+  const size_t kpad = ((size_t)2 * k + BK - 1) / BK * BK;
+  return (size_t)S * (m + 2 * (size_t)n) * kpad * 2 + ((size_t)m + n) * 4 + 4096;
+}
+
+void pw_oz_free(pw_oz_ws *w) {
+  if (w->buf) cudaFree(w->buf);
+  if (w->part) cudaFree(w->part);
+  if (w->err) cudaFree(w->err);
+  *w = pw_oz_ws();
+}
+
+pw_status pw_oz_check(pw_oz_ws *w, cudaStream_t st) {
+  if (!w->err) return PW_OK;
+  int e = 0;
+  PW_CUDA(cudaMemcpyAsync(&e, w->err, 4, cudaMemcpyDeviceToHost, st));
+  PW_CUDA(cudaStreamSynchronize(st));
+  return e ? PW_ERR_TIMEOUT : PW_OK;
+}
+
+pw_status pw_zgemm_oz(pw_oz_ws *w, char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
+                      int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc, cudaStream_t st,
+                      int herm) {
+  if ((opA != 'N' && opA != 'C') || (opB != 'N' && opB != 'C') || herm < 0 || herm > 5) return PW_ERR_ARG;
+  if (m <= 0 || n <= 0) return PW_OK;
+  if (k <= 0) return PW_ERR_ARG;
+  if (herm == 1 && m != n) return PW_ERR_ARG;
+  const int kpad = (2 * k + BK - 1) / BK * BK;
+  const int kblocks = kpad / BK;
+  // slice storage: A rows padded to the tile (the tensor map of the last
+  // slice then never reads another slice's rows), B rows likewise
+  const int arows = (m + BM - 1) / BM * BM, brows = (2 * n + BN - 1) / BN * BN;
+  const size_t abytes = (size_t)S * arows * kpad * 2, bbytes = (size_t)S * brows * kpad * 2;
+  const size_t need = abytes + bbytes + ((size_t)arows + brows) * 4 + 1024;
+  if (need > w->bytes) {
+    if (w->buf) cudaFree(w->buf);
+    w->buf = nullptr;
+    w->bytes = 0;
+    if (cudaMalloc(&w->buf, need) != cudaSuccess) { cudaGetLastError(); return PW_ERR_OOM; }
+    w->bytes = need;
+  }
+  if (!w->err) {
+    if (cudaMalloc((void **)&w->err, 16) != cudaSuccess) { cudaGetLastError(); return PW_ERR_OOM; }
+    PW_CUDA(cudaMemsetAsync(w->err, 0, 16, st));
+  }
+  unsigned char *p = (unsigned char *)w->buf;
+  __half *sa = (__half *)p, *sb = (__half *)(p + abytes);
+  int *ea = (int *)(p + abytes + bbytes), *eb = ea + arows;
+  PW_TRY(slice_operand(opA, 0, A, lda, m, k, kpad, arows, sa, ea, st));
+  PW_TRY(slice_operand(opB, 1, B, ldb, n, k, kpad, brows, sb, eb, st));
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, sa, kpad, (long)S * arows, BM) || !make_map(&mb, sb, kpad, (long)S * brows, BN))
+    return PW_ERR_CUDA;
+  PW_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  const int mtiles = arows / BM, ntiles = brows / BN, tiles = mtiles * ntiles;
+  // K split when the tiles alone leave SMs idle (chunks of >= 8 per part)
+  const int nch = (kblocks + CHUNK_KB - 1) / CHUNK_KB;
+  int parts = 1;
+  if (herm == 0 && tiles < 152) {
+    parts = std::min({(2 * 152 + tiles - 1) / tiles, std::max(1, nch / 8), g_max_parts});
+    const size_t pbytes = (size_t)parts * m * n * 16;
+    if (parts > 1 && pbytes > w->part_bytes) {
+      if (w->part) cudaFree(w->part);
+      w->part = nullptr;
+      w->part_bytes = 0;
+      if (cudaMalloc((void **)&w->part, pbytes) != cudaSuccess) { cudaGetLastError(); parts = 1; }
+      else w->part_bytes = pbytes;
+    }
+  }
+  pw_count_launch();
+  k_oz_gemm<<<dim3(tiles, parts), NTHREADS, SMEM_BYTES, st>>>(ma, mb, arows, brows, m, n, kblocks, mtiles,
+                                                              ntiles, ea, eb, alpha, beta, C, ldc, herm,
+                                                              parts > 1 ? w->part : nullptr, w->err);
+  PW_TRY(pw_check_launch("oz gemm"));
+  if (parts > 1) {
+    pw_count_launch();
+    k_oz_reduce<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, st>>>(w->part, parts, m, n, alpha, beta, C,
+                                                                        ldc, herm);
+    PW_TRY(pw_check_launch("oz reduce"));
+  }
+  if (herm == 1) {
+    pw_count_launch();
+    k_oz_mirror<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 32), 0, st>>>(C, ldc, m);
+    PW_TRY(pw_check_launch("oz mirror"));
+  }
+  return PW_OK;
+}
+
+extern "C" pw_status pw_zgemm_f64tc(char opA, char opB, int m, int n, int k, const double *alpha,
+                                    const void *A, int lda, const void *B, int ldb, const double *beta, void *C,
+                                    int ldc, void *stream) {
+  if (!alpha || !beta || m < 0 || n < 0 || k < 1 || !A || !B || !C) return PW_ERR_ARG;
+  if (ldc < m || lda < (opA == 'N' ? m : k) || ldb < (opB == 'N' ? k : n)) return PW_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  pw_oz_ws w;
+  pw_status r = pw_zgemm_oz(&w, opA, opB, m, n, k, make_double2(alpha[0], alpha[1]), (const double2 *)A, lda,
+                            (const double2 *)B, ldb, make_double2(beta[0], beta[1]), (double2 *)C, ldc, st, 0);
+  if (r == PW_OK) r = pw_oz_check(&w, st);
+  if (r == PW_OK && cudaStreamSynchronize(st) != cudaSuccess) r = PW_ERR_CUDA;
+  pw_oz_free(&w);
+  return r;
+}

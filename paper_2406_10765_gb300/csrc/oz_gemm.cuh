@@ -1,0 +1,29 @@
+// FP64-accurate complex GEMM on the FP16 tensor cores (integer-slice split of
+// both operands, exact slice products, 64-bit fixed-point accumulation).
+#pragma once
+#include "pw_internal.cuh"
+
+#define PW_OZ_SLICES 8
+
+// Workspace of the product (grown on demand, owned by the caller's object).
+struct pw_oz_ws {
+  void *buf = nullptr;        // operand slices and row exponents
+  size_t bytes = 0;
+  double2 *part = nullptr;    // K-split partial results
+  size_t part_bytes = 0;
+  int *err = nullptr;         // device error word (a bounded wait ran out)
+};
+
+// C = alpha op(A) op(B) + beta C, column-major complex128, op in {N, C};
+// herm as pw_zgemm_ex (0 plain, 1 Hermitian upper + mirror, 2 tiles with
+// j/64 <= i/64 only, 3 op(A) upper triangular, 4 op(B) lower triangular,
+// 5 op(A) lower triangular).  Error per entry <= ~2K 2^-55 max_k|op(A)_ik|
+// max_k|op(B)_kj|.  Asynchronous on st.
+pw_status pw_zgemm_oz(pw_oz_ws *w, char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
+                      int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc, cudaStream_t st,
+                      int herm);
+// device bytes of the slices of an m x n x k product (without K-split parts)
+size_t pw_oz_ws_bytes(int m, int n, int k);
+// PW_ERR_TIMEOUT if a bounded wait of an earlier product ran out (synchronises st)
+pw_status pw_oz_check(pw_oz_ws *w, cudaStream_t st);
+void pw_oz_free(pw_oz_ws *w);

@@ -897,7 +897,8 @@ extern "C" int pw_autotune_gemm_table(char *buf, size_t len) {
 
 extern "C" int pw_autotune_gemm_load(const char *text) {
   if (!text) return -1;
-  std::lock_guard<std::mutex> g(g_tune_mu);
+  // parse into a local table first: a dump with a bad line changes nothing
+  std::map<GemmKey, GemmChoice> parsed;
   int added = 0;
   const char *p = text;
   while (*p) {
@@ -914,9 +915,11 @@ extern "C" int pw_autotune_gemm_load(const char *text) {
       return -1;
     k.kclass = kmax / BK;
     k.kb_lo = klo / BK;
-    g_tune_table[k] = GemmChoice{split, ms1, ms};
+    parsed[k] = GemmChoice{split, ms1, ms};
     ++added;
   }
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  for (const auto &kv : parsed) g_tune_table[kv.first] = kv.second;
   return added;
 }
 

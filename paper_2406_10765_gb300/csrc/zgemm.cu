@@ -143,6 +143,7 @@ __global__ void k_zgemm_reduce(int m, int n, int splits, double2 alpha, const do
 }
 
 int choose_splits(int m, int n, int k) {
+  if (m <= 0 || n <= 0 || k <= 0) return 1;   // empty product: nothing to split
   const long tiles = (long)((m + BM - 1) / BM) * ((n + BN - 1) / BN);
   long s = (2 * 152 + tiles - 1) / tiles;
   // K chunks of at least 128, or of 32 when the tiles alone leave half the SMs idle

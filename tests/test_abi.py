@@ -70,5 +70,11 @@ def test_gemm_tuning_table_round_trip_without_gpu():
     assert sorted(table.splitlines()) == sorted(saved.splitlines())
     with pytest.raises(pw.PwError):
         pw.pw_autotune_gemm_load("mtiles=1 ntiles=1 k<=100 k_lo=0 tri_b=0 herm=0 mode=0 split=2 ms1=1 ms=1\n")
+    # a dump whose last line is malformed adds none of its good lines
+    bad = ("mtiles=5 ntiles=5 k<=4096 k_lo=0 tri_b=0 herm=0 mode=0 split=4 ms1=1.0000 ms=0.5000\n"
+           "mtiles=5 ntiles=6 k<=4096 k_lo=0 tri_b=0 herm=0 mode=0 split=99 ms1=1.0000 ms=0.5000\n")
+    with pytest.raises(pw.PwError):
+        pw.pw_autotune_gemm_load(bad)
+    assert sorted(pw.pw_autotune_gemm_table().splitlines()) == sorted(saved.splitlines())
     pw.pw_autotune_gemm(0)
     assert pw.pw_autotune_gemm_table() == ""

@@ -316,6 +316,75 @@ def test_rayleigh_ritz_breakdown_and_solution():
     assert np.abs(X.conj().T @ X - np.eye(4)).max() < 1e-12
 
 
+def _rr_pencil(S, HS, nb):
+    """Lowest nb eigenvalues of the pencil (S^H H S, S^H S) by scipy's
+    generalized Hermitian solver: a route that shares nothing with the
+    oracle's Jacobi scaling, Cholesky and triangular solves."""
+    import scipy.linalg as sla
+    A = S.conj().T @ HS
+    B = S.conj().T @ S
+    return sla.eigh(0.5 * (A + A.conj().T), 0.5 * (B + B.conj().T), eigvals_only=True)[:nb]
+
+
+def test_lobpcg_step_drops_p_on_breakdown():
+    """Cholesky breakdown inside the step (Knyazev's method with the pivot
+    reading): with P inside span(X) the Gram of [X, W, P] is singular, so the
+    step must retry on [X, W] alone.  Pinned against a generalized
+    eigensolve of that pencil, with W formed from the definition."""
+    cell, _ = _cell("Si", 1, 10.0)
+    nb = 6
+    st = O.lobpcg_init(cell, synth.draw_x0(3, 8, cell.npw, nb))
+    rng = np.random.default_rng(11)
+    Q = rng.standard_normal((nb, nb)) + 1j * rng.standard_normal((nb, nb))
+    st.P, st.HP = st.X @ Q, st.HX @ Q
+    nxt = O.lobpcg_step(cell, st)
+    assert nxt.dropped_p == 1
+    # W from its definition: R = H X - X Lambda, TPA on 1/2|G|^2 / E_kin
+    R = O.apply_H(cell, st.X) - st.X * st.lam[None, :]
+    ek = (cell.kin[:, None] * np.abs(st.X) ** 2).sum(0) / (np.abs(st.X) ** 2).sum(0)
+    x = cell.kin[:, None] / ek[None, :]
+    p = 27 + 18 * x + 12 * x ** 2 + 8 * x ** 3
+    W = p / (p + 16 * x ** 4) * R
+    S = np.hstack([st.X, W])
+    ref = _rr_pencil(S, O.apply_H(cell, S), nb)
+    assert np.abs(nxt.lam - ref).max() < 1e-10
+    # Ritz values of a larger space can only fall (Cauchy interlacing)
+    assert np.all(nxt.lam <= st.lam + 1e-12)
+    # the retried block is orthonormal and solves the projected problem
+    assert np.abs(nxt.X.conj().T @ nxt.X - np.eye(nb)).max() < 1e-12
+    Rn = O.apply_H(cell, nxt.X) - nxt.X * nxt.lam[None, :]
+    assert np.abs(S.conj().T @ Rn).max() < 1e-9 * np.abs(S).max() * np.abs(Rn).max() * cell.npw
+    # P' is the [0, W] part only: orthogonal complement test against span(X)
+    assert nxt.P.shape == (cell.npw, nb)
+
+
+def test_lobpcg_step_keeps_p_when_it_is_independent():
+    """The same state with a P outside span([X, W]) keeps P (no drop): the
+    step equals the generalized eigensolve of the full pencil [X, W, P]."""
+    cell, _ = _cell("Si", 1, 10.0)
+    nb = 6
+    st = O.lobpcg_init(cell, synth.draw_x0(3, 8, cell.npw, nb))
+    P = synth.draw_x0(5, 8, cell.npw, nb)
+    st.P, st.HP = P, O.apply_H(cell, P)
+    nxt = O.lobpcg_step(cell, st)
+    assert nxt.dropped_p == 0
+    R = st.HX - st.X * st.lam[None, :]
+    W = O.precondition(cell, st.X, R)
+    S = np.hstack([st.X, W, P])
+    ref = _rr_pencil(S, O.apply_H(cell, S), nb)
+    assert np.abs(nxt.lam - ref).max() < 1e-10
+
+
+def test_lobpcg_init_breakdown_on_dependent_start():
+    """A start block with two equal columns has a singular Gram: the initial
+    Cholesky QR reports a breakdown (the library's PW_ERR_CHOL)."""
+    cell, _ = _cell("C", 1, 8.0)
+    x0 = synth.draw_x0(2, 8, cell.npw, 4)
+    x0[:, 3] = x0[:, 1]
+    with pytest.raises(O.CholeskyBreakdown):
+        O.lobpcg_init(cell, x0)
+
+
 def test_density_sum_rule():
     cell, _ = _cell("C", 1, 8.0)
     w, v = O.dense_eigs(cell, 4)
