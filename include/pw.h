@@ -395,6 +395,13 @@ pw_status pw_zgemm_f64tc(char opA, char opB, int m, int n, int k, const double *
                          int lda, const void *B, int ldb, const double *beta, void *C, int ldc,
                          void *stream);
 
+/* Products of the FP64 Rayleigh-Ritz solve (Cholesky updates, triangular
+ * inverse, L^-1 A L^-H, Householder panel updates, back-transformation),
+ * process-wide: mode 1 (default) runs the large ones with the FP64-accurate
+ * tensor-core product of pw_zgemm_f64tc, mode 0 keeps every one on the FP64
+ * pipe.  Results agree to FP64 rounding.  Errors: PW_ERR_ARG. */
+pw_status pw_dense_products(int mode);
+
 /* ---- Autotuner: the plan and tile-shape choices of the hot kernels ----
  * Sec. III-D picks, for each execution step, the process count that runs it
  * fastest among the candidates that fit in memory.  On one GPU the matching

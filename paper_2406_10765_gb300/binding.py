@@ -177,6 +177,14 @@ def pw_zgemm_f64tc(opA, opB, A, B, C=None, alpha=1.0, beta=0.0, stream=None):
     return C
 
 
+_dense_products = _sig("pw_dense_products", ct.c_int, [ct.c_int])
+
+
+def pw_dense_products(mode):
+    """1: large products of the FP64 Rayleigh-Ritz on the tensor cores (FP64-accurate); 0: FP64 pipe."""
+    _check(_dense_products(int(mode)), "pw_dense_products")
+
+
 _launches = _sig("pw_kernel_launches", ct.c_uint64, [])
 
 

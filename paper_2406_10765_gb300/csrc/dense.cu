@@ -20,6 +20,8 @@
 #include <functional>
 #include <vector>
 
+#include <atomic>
+
 #include "dense.cuh"
 
 namespace {
@@ -1151,6 +1153,45 @@ void build_tree(pw_dense_ws *ws, int n) {
 }  // namespace
 
 // ======================================================================
+// products of the dense solve
+// ======================================================================
+namespace {
+std::atomic<int> g_dense_products{1};
+// complex multiply-adds below which the FP64 pipe is faster than slicing the
+// operands for the tensor cores
+constexpr double kOzMinMacs = 8.0 * (1 << 20);
+}  // namespace
+
+int pw_dense_products_mode() { return g_dense_products.load(); }
+
+extern "C" pw_status pw_dense_products(int mode) {
+  if (mode != 0 && mode != 1) return PW_ERR_ARG;
+  g_dense_products.store(mode);
+  return PW_OK;
+}
+
+pw_status pw_dense_gemm(pw_dense_ws *ws, char opA, char opB, int m, int n, int k, double2 alpha,
+                        const double2 *A, int lda, const double2 *B, int ldb, double2 beta, double2 *C,
+                        int ldc, cudaStream_t st, int herm) {
+  if (m <= 0 || n <= 0) return PW_OK;
+  if (k > 0 && g_dense_products.load() == 1 && (double)m * n * k >= kOzMinMacs) {
+    if (ws->oz.bytes == 0) {
+      // reserve the largest product of an order-nmax solve at once (the
+      // L^-1 A L^-H blocks and C = M Y), so later products reuse it
+      const size_t big = std::max(pw_oz_ws_bytes(256, ws->nmax, ws->nmax),
+                                  std::max(pw_oz_ws_bytes(ws->nmax, 256, ws->nmax),
+                                           pw_oz_ws_bytes(ws->nmax, ws->nbmax, ws->nmax)));
+      void *p = nullptr;
+      if (cudaMalloc(&p, big) == cudaSuccess) { ws->oz.buf = p; ws->oz.bytes = big; }
+      else cudaGetLastError();
+    }
+    return pw_zgemm_oz(&ws->oz, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, st, herm);
+  }
+  return pw_zgemm_ex(opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws->gemm_ws, ws->gemm_ws_elems,
+                     st, herm);
+}
+
+// ======================================================================
 // workspace
 // ======================================================================
 pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
@@ -1203,6 +1244,7 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
 }
 
 void pw_dense_free(pw_dense_ws *ws) {
+  pw_oz_free(&ws->oz);
   void *ptrs[] = {ws->G, ws->A, ws->T, ws->Linv, ws->Y, ws->dscale, ws->piv, ws->flag, ws->d, ws->e,
                   ws->lam, ws->tau, ws->p, ws->w, ws->part, ws->Z, ws->W, ws->U, ws->Ds, ws->zs,
                   ws->DK, ws->zK, ws->tauK, ws->zh, ws->lamK, ws->dD, ws->lnew, ws->perm, ws->colK,
@@ -1262,8 +1304,8 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
                          (const double2 *)ws->p, (const double2 *)dotpart, ndot, (const double2 *)ws->tau));
       const int t = j0 + b, m2 = n - t;
       if (m2 > 0)
-        PW_TRY(pw_zgemm_ex('N', 'C', m2, m2, 2 * b, mone, ws->panel + t, n, ws->panel + (long)b * n + t,
-                           n, one, A + t + (long)t * n, n, ws->gemm_ws, ws->gemm_ws_elems, st, 2));
+        PW_TRY(pw_dense_gemm(ws, 'N', 'C', m2, m2, 2 * b, mone, ws->panel + t, n, ws->panel + (long)b * n + t,
+                             n, one, A + t + (long)t * n, n, st, 2));
     }
     pw_count_launch();
     k_last_diag_plain<<<1, 1, 0, st>>>(A, n, ws->d);
@@ -1321,17 +1363,13 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
       const int j0 = std::max(0, j1 - BTB), b = j1 - j0, mb = n - j0 - 1;
       pw_count_launch();
       k_copy_panel<<<(unsigned)(((long)mb * b + 255) / 256), 256, 0, st>>>(A, n, j0, b, ws->Vb, mb);
-      PW_TRY(pw_zgemm('C', 'N', b, b, mb, one, ws->Vb, mb, ws->Vb, mb, zero, ws->Gv, b, ws->gemm_ws,
-                      ws->gemm_ws_elems, st));
+      PW_TRY(pw_dense_gemm(ws, 'C', 'N', b, b, mb, one, ws->Vb, mb, ws->Vb, mb, zero, ws->Gv, b, st));
       pw_count_launch();
       k_build_T<<<(b + BT_WARPS - 1) / BT_WARPS, 32 * BT_WARPS, 0, st>>>(ws->Gv, ws->tau, j0, b, ws->Tb);
       double2 *Yb = Y + (j0 + 1);
-      PW_TRY(pw_zgemm('C', 'N', b, nb, mb, one, ws->Vb, mb, Yb, n, zero, ws->Wk, b, ws->gemm_ws,
-                      ws->gemm_ws_elems, st));
-      PW_TRY(pw_zgemm('N', 'N', b, nb, b, one, ws->Tb, b, ws->Wk, b, zero, ws->Wk2, b, ws->gemm_ws,
-                      ws->gemm_ws_elems, st));
-      PW_TRY(pw_zgemm('N', 'N', mb, nb, b, mone, ws->Vb, mb, ws->Wk2, b, one, Yb, n, ws->gemm_ws,
-                      ws->gemm_ws_elems, st));
+      PW_TRY(pw_dense_gemm(ws, 'C', 'N', b, nb, mb, one, ws->Vb, mb, Yb, n, zero, ws->Wk, b, st));
+      PW_TRY(pw_dense_gemm(ws, 'N', 'N', b, nb, b, one, ws->Tb, b, ws->Wk, b, zero, ws->Wk2, b, st));
+      PW_TRY(pw_dense_gemm(ws, 'N', 'N', mb, nb, b, mone, ws->Vb, mb, ws->Wk2, b, one, Yb, n, st));
       j1 = j0;
     }
   }
@@ -1354,9 +1392,8 @@ pw_status cholesky(pw_dense_ws *ws, double2 *A, int n, cudaStream_t st) {
       k_trsm_inv<<<(rest + TRSM_ROWS - 1) / TRSM_ROWS, 256, 0, st>>>(A, n, j0, b, ws->Li);
       // A22 -= L21 L21^H on the lower tiles only (the factorisation reads the
       // lower triangle; the upper one is cleared at the end)
-      PW_TRY(pw_zgemm_ex('N', 'C', rest, rest, b, mone, A + (j0 + b) + (long)j0 * n, n,
-                         A + (j0 + b) + (long)j0 * n, n, one, A + (j0 + b) + (long)(j0 + b) * n, n,
-                         ws->gemm_ws, ws->gemm_ws_elems, st, 2));
+      PW_TRY(pw_dense_gemm(ws, 'N', 'C', rest, rest, b, mone, A + (j0 + b) + (long)j0 * n, n,
+                           A + (j0 + b) + (long)j0 * n, n, one, A + (j0 + b) + (long)(j0 + b) * n, n, st, 2));
     }
   }
   pw_count_launch();
@@ -1387,20 +1424,30 @@ pw_status trinv(pw_dense_ws *ws, const double2 *L, double2 *X, int n, cudaStream
     double2 *T = ws->T;
     if (full > 0) {
       const long s2 = 2 * (long)w * dstep;   // from one pair's corner to the next
-      // T_p = L21 X11 (w x w, ld w)
-      PW_TRY(pw_zgemm_batched('N', 'N', w, w, w, one, L + w, n, s2, X, n, s2, zero, T, w, (long)w * w,
-                              full, st, 4));
-      // X21 = -X22 T_p
-      PW_TRY(pw_zgemm_batched('N', 'N', w, w, w, mone, X + w * dstep, n, s2, T, w, (long)w * w, zero,
-                              X + w, n, s2, full, st, 5));
+      if (pw_dense_products_mode() == 1 && (double)w * w * w >= kOzMinMacs) {
+        // few large pairs: one tensor-core product each
+        for (int q = 0; q < full; ++q) {
+          PW_TRY(pw_dense_gemm(ws, 'N', 'N', w, w, w, one, L + w + q * s2, n, X + q * s2, n, zero,
+                               T + (long)q * w * w, w, st, 4));
+          PW_TRY(pw_dense_gemm(ws, 'N', 'N', w, w, w, mone, X + w * dstep + q * s2, n, T + (long)q * w * w, w,
+                               zero, X + w + q * s2, n, st, 5));
+        }
+      } else {
+        // T_p = L21 X11 (w x w, ld w)
+        PW_TRY(pw_zgemm_batched('N', 'N', w, w, w, one, L + w, n, s2, X, n, s2, zero, T, w, (long)w * w,
+                                full, st, 4));
+        // X21 = -X22 T_p
+        PW_TRY(pw_zgemm_batched('N', 'N', w, w, w, mone, X + w * dstep, n, s2, T, w, (long)w * w, zero,
+                                X + w, n, s2, full, st, 5));
+      }
     }
     const int off = full * 2 * w;
     if (off + w < n) {                       // a last pair with a shorter second block
       const int h1 = w, h2 = n - off - w;
-      PW_TRY(pw_zgemm_ex('N', 'N', h2, h1, h1, one, L + (off + h1) + (long)off * n, n, X + off * dstep, n,
-                         zero, T, h2, ws->gemm_ws, ws->gemm_ws_elems, st, 4));
-      PW_TRY(pw_zgemm_ex('N', 'N', h2, h1, h2, mone, X + (off + h1) * dstep, n, T, h2, zero,
-                         X + (off + h1) + (long)off * n, n, ws->gemm_ws, ws->gemm_ws_elems, st, 5));
+      PW_TRY(pw_dense_gemm(ws, 'N', 'N', h2, h1, h1, one, L + (off + h1) + (long)off * n, n, X + off * dstep,
+                           n, zero, T, h2, st, 4));
+      PW_TRY(pw_dense_gemm(ws, 'N', 'N', h2, h1, h2, mone, X + (off + h1) * dstep, n, T, h2, zero,
+                           X + (off + h1) + (long)off * n, n, st, 5));
     }
   }
   return PW_OK;
@@ -1439,21 +1486,19 @@ pw_status pw_rayleigh_ritz(pw_dense_ws *ws, int n, int nb, const double2 *G, int
   constexpr int TB = 256;
   for (int i0 = 0; i0 < n; i0 += TB) {
     const int ib = std::min(TB, n - i0), kend = i0 + ib;
-    PW_TRY(pw_zgemm('N', 'N', ib, n, kend, one, ws->Linv + i0, n, ws->A, n, zero, ws->T + i0, n,
-                    ws->gemm_ws, ws->gemm_ws_elems, st));
+    PW_TRY(pw_dense_gemm(ws, 'N', 'N', ib, n, kend, one, ws->Linv + i0, n, ws->A, n, zero, ws->T + i0, n, st));
   }
   for (int j0 = 0; j0 < n; j0 += TB) {
     const int jb = std::min(TB, n - j0), kend = j0 + jb;
-    PW_TRY(pw_zgemm('N', 'C', kend, jb, kend, one, ws->T, n, ws->Linv + j0, n, zero,
-                    ws->A + (long)j0 * n, n, ws->gemm_ws, ws->gemm_ws_elems, st));
+    PW_TRY(pw_dense_gemm(ws, 'N', 'C', kend, jb, kend, one, ws->T, n, ws->Linv + j0, n, zero,
+                         ws->A + (long)j0 * n, n, st));
   }
   pw_count_launch();
   k_mirror_upper_to_lower<<<g2, b2, 0, st>>>(ws->A, n);
   PW_TRY(pw_heev_lowest(ws, n, nb, ws->A, ws->lam, ws->Y, st));
   PW_CUDA(cudaMemcpyAsync(theta, ws->lam, nb * 8, cudaMemcpyDeviceToDevice, st));
   // C = d o (Linv^H Y); Linv^H is upper triangular
-  PW_TRY(pw_zgemm_ex('C', 'N', n, nb, n, one, ws->Linv, n, ws->Y, n, zero, C, ldc, ws->gemm_ws,
-                     ws->gemm_ws_elems, st, 3));
+  PW_TRY(pw_dense_gemm(ws, 'C', 'N', n, nb, n, one, ws->Linv, n, ws->Y, n, zero, C, ldc, st, 3));
   pw_count_launch();
   k_scale_rows_real<<<(unsigned)(((long)n * nb + 255) / 256), 256, 0, st>>>(C, ldc, n, nb, ws->dscale);
   cudaEventRecord(ws->ev[5], st);
@@ -1523,8 +1568,8 @@ pw_status pw_rr_finish_tall(pw_dense_ws *ws, int n, int nb, const double2 *At, i
   PW_CUDA(cudaMemset2DAsync(Cp, (size_t)ldc * 16, 0, (size_t)nb * 16, nb, st));
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
   if (n > nb)
-    PW_TRY(pw_zgemm_ex('N', 'N', n - nb, nb, n - nb, one, M + nb + (long)nb * ldm, ldm, ws->Y + nb, n,
-                       zero, Cp + nb, ldc, ws->gemm_ws, ws->gemm_ws_elems, st, 3));
+    PW_TRY(pw_dense_gemm(ws, 'N', 'N', n - nb, nb, n - nb, one, M + nb + (long)nb * ldm, ldm, ws->Y + nb, n,
+                         zero, Cp + nb, ldc, st, 3));
   cudaEventRecord(ws->ev[5], st);
   return pw_check_launch("rr_finish_tall");
 }
@@ -1540,8 +1585,7 @@ pw_status pw_rr_finish(pw_dense_ws *ws, int n, int nb, const double2 *At, int ld
   PW_CUDA(cudaMemcpyAsync(theta, ws->lam, nb * 8, cudaMemcpyDeviceToDevice, st));
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
   // M is upper triangular: each row tile skips the zero part of its K range
-  PW_TRY(pw_zgemm_ex('N', 'N', n, nb, n, one, M, ldm, ws->Y, n, zero, C, ldc, ws->gemm_ws,
-                     ws->gemm_ws_elems, st, 3));
+  PW_TRY(pw_dense_gemm(ws, 'N', 'N', n, nb, n, one, M, ldm, ws->Y, n, zero, C, ldc, st, 3));
   cudaEventRecord(ws->ev[5], st);
   return pw_check_launch("rr_finish");
 }

@@ -1,5 +1,6 @@
 // FP64 dense linear algebra of the Rayleigh-Ritz step, on the GPU.
 #pragma once
+#include "oz_gemm.cuh"
 #include "pw_internal.cuh"
 
 // Workspace for Rayleigh-Ritz problems up to order nmax with up to nbmax wanted pairs.
@@ -27,6 +28,7 @@ struct pw_dense_ws {
   int *ctype = nullptr, *qL = nullptr, *qR = nullptr, *kLR = nullptr, *kneed = nullptr;
   double *rhonode = nullptr;
   double2 *gemm_ws = nullptr; size_t gemm_ws_elems = 0;
+  pw_oz_ws oz;                // FP64-accurate tensor-core products (slices, partial sums)
   // blocked back-transformation: reflector panel, its Gram, T, two work blocks
   double2 *Vb = nullptr, *Gv = nullptr, *Tb = nullptr, *Wk = nullptr, *Wk2 = nullptr;
   unsigned *ticket = nullptr;   // last-block-done counter of the Householder steps
@@ -47,6 +49,14 @@ struct pw_dense_ws {
   cudaEvent_t ev[6] = {};
   float ms[5] = {0, 0, 0, 0, 0};
 };
+
+// Products of the dense solve: FP64-accurate tensor-core product
+// (pw_zgemm_oz) when the process-wide mode (pw_dense_products) is 1 and the
+// product is large enough to pay for its operand slicing, else the FP64 pipe.
+pw_status pw_dense_gemm(pw_dense_ws *ws, char opA, char opB, int m, int n, int k, double2 alpha,
+                        const double2 *A, int lda, const double2 *B, int ldb, double2 beta, double2 *C,
+                        int ldc, cudaStream_t st, int herm = 0);
+int pw_dense_products_mode();
 
 // elapsed times of the last pw_rayleigh_ritz (after its stream synchronised)
 void pw_dense_stage_ms(pw_dense_ws *ws, float out[5]);

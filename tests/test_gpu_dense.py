@@ -50,3 +50,26 @@ def test_heev_argument_errors():
     import ctypes as ct
     assert B._heev(0, 1, ct.c_void_p(1), ct.c_void_p(1), ct.c_void_p(1), st) == B.PW_ERR_ARG
     assert B._heev(4, 5, ct.c_void_p(1), ct.c_void_p(1), ct.c_void_p(1), st) == B.PW_ERR_ARG
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_heev_large_both_product_modes(mode):
+    # order 1,700: the panel updates, back-transformation and their K-split
+    # products run on the FP64-accurate tensor-core path (mode 1) or the FP64
+    # pipe (mode 0); both match LAPACK at the same tolerances
+    import paper_2406_10765_gb300 as pw
+    n, nb = 1700, 600
+    A = _herm(n, 17, "rand")
+    pw.pw_dense_products(mode)
+    try:
+        w, Y = pw.pw_heev(torch.from_numpy(A).cuda(), nb)
+        torch.cuda.synchronize()
+    finally:
+        pw.pw_dense_products(1)
+    w = w.cpu().numpy()
+    Y = Y.cpu().numpy()
+    ref = np.linalg.eigvalsh(A)
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(w - ref).max() < 1e-13 * scale * n ** 0.5
+    assert np.abs(A @ Y - Y * w[:nb]).max() < 1e-12 * scale
+    assert np.abs(Y.conj().T @ Y - np.eye(nb)).max() < 1e-12

@@ -131,3 +131,29 @@ def test_lobpcg_steps_match_oracle_si64():
         assert np.abs(e - st.lam).max() < 1e-9, (it, np.abs(e - st.lam).max())
         assert abs(rep.max_resid - st.resid.max()) < 1e-8 * max(1.0, st.resid.max())
     pw.pw_solver_destroy(s)
+
+
+def test_fp64_steps_same_in_both_product_modes():
+    # the Rayleigh-Ritz products on the FP64-accurate tensor-core path and on
+    # the FP64 pipe give the same FP64 steps (64-atom cell, order 432) and
+    # both follow the oracle
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 2, 10.0)
+    nb = 144
+    x0 = synth.draw_x0(0, 64, orc.npw, nb)
+    st = O.lobpcg_init(orc, x0)
+    eigs = []
+    for mode in (0, 1):
+        pw.pw_dense_products(mode)
+        try:
+            s = pw.pw_solver_create(lib.h, nb, tol=0.0, x0=x0)
+            for _ in range(2):
+                pw.pw_subspace_step(lib.h, s)
+            eigs.append(pw.pw_solver_eigs(s, nb)[0])
+            pw.pw_solver_destroy(s)
+        finally:
+            pw.pw_dense_products(1)
+    for _ in range(2):
+        st = O.lobpcg_step(orc, st)
+    assert np.abs(eigs[0] - eigs[1]).max() < 1e-11
+    assert np.abs(eigs[1] - st.lam).max() < 1e-9
