@@ -1155,26 +1155,13 @@ void build_tree(pw_dense_ws *ws, int n) {
 // ======================================================================
 // products of the dense solve
 // ======================================================================
-namespace {
-std::atomic<int> g_dense_products{1};
-// complex multiply-adds below which the FP64 pipe is faster than slicing the
-// operands for the tensor cores
-constexpr double kOzMinMacs = 8.0 * (1 << 20);
-}  // namespace
-
-int pw_dense_products_mode() { return g_dense_products.load(); }
-
-extern "C" pw_status pw_dense_products(int mode) {
-  if (mode != 0 && mode != 1) return PW_ERR_ARG;
-  g_dense_products.store(mode);
-  return PW_OK;
-}
+int pw_dense_products_mode() { return pw_f64_products_mode(); }
 
 pw_status pw_dense_gemm(pw_dense_ws *ws, char opA, char opB, int m, int n, int k, double2 alpha,
                         const double2 *A, int lda, const double2 *B, int ldb, double2 beta, double2 *C,
                         int ldc, cudaStream_t st, int herm) {
   if (m <= 0 || n <= 0) return PW_OK;
-  if (k > 0 && g_dense_products.load() == 1 && (double)m * n * k >= kOzMinMacs) {
+  if (pw_use_oz(m, n, k)) {
     if (ws->oz.bytes == 0) {
       // reserve the largest product of an order-nmax solve at once (the
       // L^-1 A L^-H blocks and C = M Y), so later products reuse it
@@ -1424,7 +1411,7 @@ pw_status trinv(pw_dense_ws *ws, const double2 *L, double2 *X, int n, cudaStream
     double2 *T = ws->T;
     if (full > 0) {
       const long s2 = 2 * (long)w * dstep;   // from one pair's corner to the next
-      if (pw_dense_products_mode() == 1 && (double)w * w * w >= kOzMinMacs) {
+      if (pw_use_oz(w, w, w)) {
         // few large pairs: one tensor-core product each
         for (int q = 0; q < full; ++q) {
           PW_TRY(pw_dense_gemm(ws, 'N', 'N', w, w, w, one, L + w + q * s2, n, X + q * s2, n, zero,

@@ -7,6 +7,7 @@
 // H psi += beta B.
 #include <algorithm>
 
+#include "oz_gemm.cuh"
 #include "pw_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -19,6 +20,12 @@ __global__ void k_scale_rows(double2 *B, int nproj, int nb, const double *D) {
   B[idx].y *= d;
 }
 }  // namespace
+
+// the cell's workspace of the FP64-accurate tensor-core products (made on first use)
+static pw_oz_ws *cell_oz(pw_cell *c) {
+  if (!c->oz) c->oz = new pw_oz_ws();
+  return c->oz;
+}
 
 // mixed precision: split-FP16 tensor-core products, FP64 accumulation into hpsi
 static pw_status nonlocal_tc(pw_cell *c, const double2 *psi, int ld, int nb, double2 *hpsi,
@@ -113,13 +120,13 @@ static pw_status nonlocal_onthefly(pw_cell *c, const double2 *psi, int ld, int n
   for (int a0 = 0; a0 < c->natom; a0 += ca) {
     const int na = std::min(ca, c->natom - a0), np = 4 * na;
     PW_TRY(pw_beta_chunk(c, a0, na, c->d_bchunk, st));
-    PW_TRY(pw_zgemm('C', 'N', np, nb, npw, one, c->d_bchunk, npw, psi, ld, zero, c->d_B, np,
-                    c->d_gemm_ws, c->gemm_ws_elems, st));
+    PW_TRY(pw_gemm64(cell_oz(c), 'C', 'N', np, nb, npw, one, c->d_bchunk, npw, psi, ld, zero, c->d_B, np,
+                     c->d_gemm_ws, c->gemm_ws_elems, st));
     pw_count_launch();
     k_scale_rows<<<(unsigned)(((long)np * nb + 255) / 256), 256, 0, st>>>(c->d_B, np, nb, c->d_D + 4 * a0);
     PW_TRY(pw_check_launch("scale_rows"));
-    PW_TRY(pw_zgemm('N', 'N', npw, nb, np, one, c->d_bchunk, npw, c->d_B, np, one, hpsi, ld, c->d_gemm_ws,
-                    c->gemm_ws_elems, st));
+    PW_TRY(pw_gemm64(cell_oz(c), 'N', 'N', npw, nb, np, one, c->d_bchunk, npw, c->d_B, np, one, hpsi, ld,
+                     c->d_gemm_ws, c->gemm_ws_elems, st));
   }
   return PW_OK;
 }
@@ -138,13 +145,13 @@ pw_status pw_apply_nonlocal(pw_cell *c, const double2 *psi, int ld, int nb, doub
   PW_TRY(pw_ensure((void **)&c->d_gemm_ws, &wcur, ws * sizeof(double2)));
   c->gemm_ws_elems = wcur / sizeof(double2);
   const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
-  PW_TRY(pw_zgemm('C', 'N', c->nproj, nb, c->npw, one, c->d_beta, c->npw, psi, ld, zero, c->d_B,
-                  c->nproj, c->d_gemm_ws, c->gemm_ws_elems, st));
+  PW_TRY(pw_gemm64(cell_oz(c), 'C', 'N', c->nproj, nb, c->npw, one, c->d_beta, c->npw, psi, ld, zero, c->d_B,
+                   c->nproj, c->d_gemm_ws, c->gemm_ws_elems, st));
   pw_count_launch();
   k_scale_rows<<<(unsigned)(((long)c->nproj * nb + 255) / 256), 256, 0, st>>>(c->d_B, c->nproj, nb, c->d_D);
   PW_TRY(pw_check_launch("scale_rows"));
-  return pw_zgemm('N', 'N', c->npw, nb, c->nproj, one, c->d_beta, c->npw, c->d_B, c->nproj, one,
-                  hpsi, ld, c->d_gemm_ws, c->gemm_ws_elems, st);
+  return pw_gemm64(cell_oz(c), 'N', 'N', c->npw, nb, c->nproj, one, c->d_beta, c->npw, c->d_B, c->nproj, one,
+                   hpsi, ld, c->d_gemm_ws, c->gemm_ws_elems, st);
 }
 
 // FP64 nonlocal term with caller-provided buffers: B (nproj x nb) and GEMM

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "dense.cuh"
+#include "oz_gemm.cuh"
 #include "pw_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -41,6 +42,7 @@ struct pw_solver {
   std::vector<double> lam_h, resid_h;
   int iter = 0, dropped = 0;
   pw_dense_ws dws;
+  pw_oz_ws oz;               // FP64-accurate tensor-core products of the tall FP64 blocks
   size_t bytes = 0;
   cudaEvent_t ev[12] = {};   // stage boundaries of the last step (7-10: H X and H P)
   int hx_applied = 0;        // H X was recomputed in the last refresh
@@ -227,7 +229,7 @@ pw_status gemm(pw_solver *s, char oa, char ob, int m, int n, int k, const double
     PW_TRY(pw_ensure((void **)&s->gws, &cur, need * 16));
     s->gws_elems = cur / 16;
   }
-  return pw_zgemm(oa, ob, m, n, k, kOne, A, lda, B, ldb, beta, C, ldc, s->gws, s->gws_elems, s->st);
+  return pw_gemm64(&s->oz, oa, ob, m, n, k, kOne, A, lda, B, ldb, beta, C, ldc, s->gws, s->gws_elems, s->st);
 }
 
 // Cholesky pivot threshold of the Jacobi-scaled Gram: FP64 products are exact
@@ -323,8 +325,10 @@ pw_status subspace_rr(pw_solver *s, int ns, int *chol_ok) {
     PW_TRY(pw_ensure((void **)&s->gws, &cur, need * 16));
     s->gws_elems = cur / 16;
   }
-  PW_TRY(pw_zgemm_herm(ns, s->npw, s->S, s->npw, s->S, s->npw, s->G, ldg, s->gws, s->gws_elems, s->st));
-  PW_TRY(pw_zgemm_herm(ns, s->npw, s->S, s->npw, s->HS, s->npw, s->A, ldg, s->gws, s->gws_elems, s->st));
+  PW_TRY(pw_gemm64(&s->oz, 'C', 'N', ns, ns, s->npw, kOne, s->S, s->npw, s->S, s->npw, kZero, s->G, ldg, s->gws,
+                   s->gws_elems, s->st, 1));
+  PW_TRY(pw_gemm64(&s->oz, 'C', 'N', ns, ns, s->npw, kOne, s->S, s->npw, s->HS, s->npw, kZero, s->A, ldg,
+                   s->gws, s->gws_elems, s->st, 1));
   cudaEventRecord(s->ev[4], s->st);
   return pw_rayleigh_ritz(&s->dws, ns, s->nb, s->G, ldg, s->A, ldg, s->theta, s->C, ldg, chol_ok, s->st,
                           piv_tol(s));
@@ -406,6 +410,8 @@ pw_status rotate(pw_solver *s, int ns, bool with_p) {
 }
 
 pw_status check_tc_err(pw_solver *s) {
+  PW_TRY(pw_oz_check(&s->oz, s->st));
+  PW_TRY(pw_oz_check(&s->dws.oz, s->st));
   if (s->precision != PW_MIXED) return PW_OK;
   int e = 0;
   PW_CUDA(cudaMemcpyAsync(&e, s->d_err, 4, cudaMemcpyDeviceToHost, s->st));
@@ -462,6 +468,7 @@ extern "C" void pw_solver_destroy(pw_solver *s) {
   if (s->d_err) cudaFree(s->d_err);
   if (s->Cz) cudaFree(s->Cz);
   pw_dense_free(&s->dws);
+  pw_oz_free(&s->oz);
   delete s;
 }
 

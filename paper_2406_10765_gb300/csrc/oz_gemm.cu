@@ -37,6 +37,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "oz_gemm.cuh"
@@ -165,7 +166,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               int a_slice_rows, int b_slice_rows, int m, int n, int kblocks, int mtiles, int ntiles,
               const int *__restrict__ ea, const int *__restrict__ eb, double2 alpha, double2 beta,
-              double2 *__restrict__ C, int ldc, int herm, double2 *__restrict__ part, int *__restrict__ err) {
+              double2 *__restrict__ C, int ldc, int herm, int ioff, int joff, double2 *__restrict__ part,
+              int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + NSTAGE * STAGE);
@@ -177,17 +179,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int tile = blockIdx.x;
   const int mt = tile / ntiles, nt = tile % ntiles;
   if (mt >= mtiles) return;
-  const int m0 = mt * BM;              // complex rows m0 .. m0 + 127
+  const int m0 = mt * BM;              // complex rows m0 .. m0 + 127 (of this block)
   const int j0 = nt * (BN / 2);        // complex columns j0 .. j0 + 31
+  const int gm0 = ioff + m0, gj0 = joff + j0;   // the same in the whole product
   // Hermitian output, upper part (mirrored later): skip tiles strictly below
   // the diagonal; lower part: tiles holding no element with j/64 <= i/64
-  if (herm == 1 && m0 > j0 + BN / 2 - 1) return;
-  if (herm == 2 && (j0 >> 6) > ((m0 + BM - 1) >> 6)) return;
+  if (herm == 1 && gm0 > gj0 + BN / 2 - 1) return;
+  if (herm == 2 && (gj0 >> 6) > ((gm0 + BM - 1) >> 6)) return;
   // K range of the tile (real K blocks): triangular operands are zero outside
   int kb_lo = 0, kb_hi = kblocks;
-  if (herm == 3) kb_lo = min(kblocks, (2 * m0) / BK);
-  if (herm == 4) kb_lo = min(kblocks, (2 * j0) / BK);
-  if (herm == 5) kb_hi = min(kblocks, (2 * (m0 + BM) + BK - 1) / BK);
+  if (herm == 3) kb_lo = min(kblocks, (2 * gm0) / BK);
+  if (herm == 4) kb_lo = min(kblocks, (2 * gj0) / BK);
+  if (herm == 5) kb_hi = min(kblocks, (2 * (gm0 + BM) + BK - 1) / BK);
   // K split: part z of gridDim.y takes an equal share, in whole chunks
   const int ntot = max(0, kb_hi - kb_lo);
   const int nch = (ntot + CHUNK_KB - 1) / CHUNK_KB;
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int t = 0; t < 16; ++t) {
         const int j = jb + t;
         if (j >= n) continue;
-        if (herm == 2 && (j >> 6) > (i >> 6)) continue;
+        if (herm == 2 && ((joff + j) >> 6) > ((ioff + i) >> 6)) continue;
         const int k = ka - eb[j];
         const double re = scale_pow2((double)acc[2 * t], k);
         const double im = scale_pow2((double)acc[2 * t + 1], k);
@@ -333,13 +336,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // sum of the K-split parts (in part order), then alpha, beta; same element
 // selection as the single-part epilogue
 __global__ void k_oz_reduce(const double2 *__restrict__ part, int splits, int m, int n, double2 alpha,
-                            double2 beta, double2 *__restrict__ C, int ldc, int herm) {
+                            double2 beta, double2 *__restrict__ C, int ldc) {
   const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (idx >= (long)m * n) return;
   const int i = (int)(idx % m), j = (int)(idx / m);
-  const int m0 = (i / BM) * BM, j0 = (j / (BN / 2)) * (BN / 2);
-  if (herm == 1 && m0 > j0 + BN / 2 - 1) return;
-  if (herm == 2 && (j >> 6) > (i >> 6)) return;
   double2 s = make_double2(0.0, 0.0);
   for (int z = 0; z < splits; ++z) {
     const double2 v = part[(long)z * m * n + idx];
@@ -580,18 +580,18 @@ pw_status pw_oz_check(pw_oz_ws *w, cudaStream_t st) {
   return e ? PW_ERR_TIMEOUT : PW_OK;
 }
 
-pw_status pw_zgemm_oz(pw_oz_ws *w, char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
-                      int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc, cudaStream_t st,
-                      int herm) {
-  if ((opA != 'N' && opA != 'C') || (opB != 'N' && opB != 'C') || herm < 0 || herm > 5) return PW_ERR_ARG;
-  if (m <= 0 || n <= 0) return PW_OK;
-  if (k <= 0) return PW_ERR_ARG;
-  if (herm == 1 && m != n) return PW_ERR_ARG;
+namespace {
+// One block of the product: rows [i0, i0 + mb) of op(A), columns [j0, j0 + nb)
+// of op(B), the whole K (given operand pointers already offset); herm
+// predicates use the global offsets.
+pw_status oz_block(pw_oz_ws *w, char opA, char opB, int mb, int nb, int k, double2 alpha, const double2 *A,
+                   int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc, cudaStream_t st,
+                   int herm, int ioff, int joff) {
   const int kpad = (2 * k + BK - 1) / BK * BK;
   const int kblocks = kpad / BK;
-  // slice storage: A rows padded to the tile (the tensor map of the last
-  // slice then never reads another slice's rows), B rows likewise
-  const int arows = (m + BM - 1) / BM * BM, brows = (2 * n + BN - 1) / BN * BN;
+  // slice storage: rows padded to the tile (the tensor map of the last slice
+  // then never reads another slice's rows)
+  const int arows = (mb + BM - 1) / BM * BM, brows = (2 * nb + BN - 1) / BN * BN;
   const size_t abytes = (size_t)S * arows * kpad * 2, bbytes = (size_t)S * brows * kpad * 2;
   const size_t need = abytes + bbytes + ((size_t)arows + brows) * 4 + 1024;
   if (need > w->bytes) {
@@ -608,19 +608,19 @@ pw_status pw_zgemm_oz(pw_oz_ws *w, char opA, char opB, int m, int n, int k, doub
   unsigned char *p = (unsigned char *)w->buf;
   __half *sa = (__half *)p, *sb = (__half *)(p + abytes);
   int *ea = (int *)(p + abytes + bbytes), *eb = ea + arows;
-  PW_TRY(slice_operand(opA, 0, A, lda, m, k, kpad, arows, sa, ea, st));
-  PW_TRY(slice_operand(opB, 1, B, ldb, n, k, kpad, brows, sb, eb, st));
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, sa, kpad, (long)S * arows, BM) || !make_map(&mb, sb, kpad, (long)S * brows, BN))
+  PW_TRY(slice_operand(opA, 0, A, lda, mb, k, kpad, arows, sa, ea, st));
+  PW_TRY(slice_operand(opB, 1, B, ldb, nb, k, kpad, brows, sb, eb, st));
+  CUtensorMap ma, mbm;
+  if (!make_map(&ma, sa, kpad, (long)S * arows, BM) || !make_map(&mbm, sb, kpad, (long)S * brows, BN))
     return PW_ERR_CUDA;
   PW_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   const int mtiles = arows / BM, ntiles = brows / BN, tiles = mtiles * ntiles;
-  // K split when the tiles alone leave SMs idle (chunks of >= 8 per part)
+  // K split when the tiles alone leave SMs idle (>= 8 chunks per part)
   const int nch = (kblocks + CHUNK_KB - 1) / CHUNK_KB;
   int parts = 1;
   if (herm == 0 && tiles < 152) {
     parts = std::min({(2 * 152 + tiles - 1) / tiles, std::max(1, nch / 8), g_max_parts});
-    const size_t pbytes = (size_t)parts * m * n * 16;
+    const size_t pbytes = (size_t)parts * mb * nb * 16;
     if (parts > 1 && pbytes > w->part_bytes) {
       if (w->part) cudaFree(w->part);
       w->part = nullptr;
@@ -630,15 +630,69 @@ pw_status pw_zgemm_oz(pw_oz_ws *w, char opA, char opB, int m, int n, int k, doub
     }
   }
   pw_count_launch();
-  k_oz_gemm<<<dim3(tiles, parts), NTHREADS, SMEM_BYTES, st>>>(ma, mb, arows, brows, m, n, kblocks, mtiles,
-                                                              ntiles, ea, eb, alpha, beta, C, ldc, herm,
-                                                              parts > 1 ? w->part : nullptr, w->err);
+  k_oz_gemm<<<dim3(tiles, parts), NTHREADS, SMEM_BYTES, st>>>(ma, mbm, arows, brows, mb, nb, kblocks, mtiles,
+                                                               ntiles, ea, eb, alpha, beta, C, ldc, herm, ioff,
+                                                               joff, parts > 1 ? w->part : nullptr, w->err);
   PW_TRY(pw_check_launch("oz gemm"));
   if (parts > 1) {
     pw_count_launch();
-    k_oz_reduce<<<(unsigned)(((long)m * n + 255) / 256), 256, 0, st>>>(w->part, parts, m, n, alpha, beta, C,
-                                                                        ldc, herm);
+    k_oz_reduce<<<(unsigned)(((long)mb * nb + 255) / 256), 256, 0, st>>>(w->part, parts, mb, nb, alpha, beta, C,
+                                                                          ldc);
     PW_TRY(pw_check_launch("oz reduce"));
+  }
+  return PW_OK;
+}
+
+// operand pointer of op(X) at (row r, K index t): op 'N' -> X[r + t ld],
+// op 'C' -> X[t + r ld]
+const double2 *at(const double2 *X, char op, int ld, long r, long t) {
+  return op == 'N' ? X + r + t * (long)ld : X + t + r * (long)ld;
+}
+}  // namespace
+
+pw_status pw_zgemm_oz(pw_oz_ws *w, char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
+                      int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc, cudaStream_t st,
+                      int herm) {
+  if ((opA != 'N' && opA != 'C') || (opB != 'N' && opB != 'C') || herm < 0 || herm > 5) return PW_ERR_ARG;
+  if (m <= 0 || n <= 0) return PW_OK;
+  if (k <= 0) return PW_ERR_ARG;
+  if (herm == 1 && m != n) return PW_ERR_ARG;
+  // Blocks of rows, columns and (for the modes whose predicates do not
+  // depend on K) K, so that the slices of one block stay under the cap; K
+  // blocks after the first accumulate into C (beta = 1).
+  const size_t cap = std::max(w->bytes, (size_t)PW_OZ_SLICE_CAP);
+  const double per_k = (double)S * 2 * 2;     // slice bytes per real row per complex K index
+  int kc = k, mc = m, nc = n;
+  auto bytes = [&]() { return per_k * ((double)mc + 2.0 * nc) * kc; };
+  auto shrink_k = [&]() {
+    if (herm <= 2)
+      while (kc > 512 && bytes() > (double)cap) kc = (kc + 1) / 2;
+  };
+  // K longest (Gram-type products): K blocks first; otherwise rows and
+  // columns first (K blocks cost a pass over C each)
+  if ((double)k > (double)m + 2.0 * n) shrink_k();
+  while (bytes() > (double)cap && (mc > BM || nc > BN / 2)) {
+    if ((double)mc >= 2.0 * nc && mc > BM) mc = ((mc + 1) / 2 + BM - 1) / BM * BM;
+    else if (nc > BN / 2) nc = ((nc + 1) / 2 + BN / 2 - 1) / (BN / 2) * (BN / 2);
+    else mc = ((mc + 1) / 2 + BM - 1) / BM * BM;
+  }
+  shrink_k();
+  const double2 one = make_double2(1.0, 0.0);
+  for (int k0 = 0; k0 < k; k0 += kc) {
+    const int kb = std::min(kc, k - k0);
+    const double2 bt = k0 == 0 ? beta : one;
+    for (int i0 = 0; i0 < m; i0 += mc) {
+      const int mb = std::min(mc, m - i0);
+      for (int j0 = 0; j0 < n; j0 += nc) {
+        const int nb = std::min(nc, n - j0);
+        // skip blocks the Hermitian modes leave alone
+        if (herm == 1 && i0 > j0 + nb - 1) continue;
+        if (herm == 2 && (j0 >> 6) > ((i0 + mb - 1) >> 6)) continue;
+        PW_TRY(oz_block(w, opA, opB, mb, nb, kb, alpha, at(A, opA, lda, i0, k0), lda,
+                        at(B, opB == 'N' ? 'C' : 'N', ldb, j0, k0), ldb, bt, C + i0 + (long)j0 * ldc, ldc, st,
+                        herm, i0, j0));
+      }
+    }
   }
   if (herm == 1) {
     pw_count_launch();
@@ -646,6 +700,33 @@ pw_status pw_zgemm_oz(pw_oz_ws *w, char opA, char opB, int m, int n, int k, doub
     PW_TRY(pw_check_launch("oz mirror"));
   }
   return PW_OK;
+}
+
+namespace {
+std::atomic<int> g_f64_products{1};
+// complex multiply-adds below which the FP64 pipe beats slicing the operands
+constexpr double kOzMinMacs = 8.0 * (1 << 20);
+}  // namespace
+
+int pw_f64_products_mode() { return g_f64_products.load(); }
+
+extern "C" pw_status pw_dense_products(int mode) {
+  if (mode != 0 && mode != 1) return PW_ERR_ARG;
+  g_f64_products.store(mode);
+  return PW_OK;
+}
+
+bool pw_use_oz(int m, int n, int k) {
+  return k > 0 && g_f64_products.load() == 1 && (double)m * n * k >= kOzMinMacs;
+}
+
+pw_status pw_gemm64(pw_oz_ws *w, char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
+                    int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc, double2 *ws,
+                    size_t ws_elems, cudaStream_t st, int herm) {
+  if (m <= 0 || n <= 0) return PW_OK;
+  if (w && pw_use_oz(m, n, k))
+    return pw_zgemm_oz(w, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, st, herm);
+  return pw_zgemm_ex(opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_elems, st, herm);
 }
 
 extern "C" pw_status pw_zgemm_f64tc(char opA, char opB, int m, int n, int k, const double *alpha,

@@ -4,6 +4,9 @@
 #include "pw_internal.cuh"
 
 #define PW_OZ_SLICES 8
+// slice bytes of one block of a product; larger products run in blocks of
+// rows, columns or K
+#define PW_OZ_SLICE_CAP ((size_t)2 << 30)
 
 // Workspace of the product (grown on demand, owned by the caller's object).
 struct pw_oz_ws {
@@ -22,6 +25,14 @@ struct pw_oz_ws {
 pw_status pw_zgemm_oz(pw_oz_ws *w, char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
                       int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc, cudaStream_t st,
                       int herm);
+// Dispatch of an FP64 product: the tensor-core path when the process-wide
+// mode (pw_dense_products) is 1, w is given and the product has at least
+// ~8M complex multiply-adds; else the FP64 pipe (pw_zgemm_ex with ws).
+pw_status pw_gemm64(pw_oz_ws *w, char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
+                    int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc, double2 *ws,
+                    size_t ws_elems, cudaStream_t st, int herm = 0);
+bool pw_use_oz(int m, int n, int k);
+int pw_f64_products_mode();
 // device bytes of the slices of an m x n x k product (without K-split parts)
 size_t pw_oz_ws_bytes(int m, int n, int k);
 // PW_ERR_TIMEOUT if a bounded wait of an earlier product ran out (synchronises st)

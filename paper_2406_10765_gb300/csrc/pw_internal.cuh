@@ -103,6 +103,7 @@ struct pw_cell {
   double2 *d_grid = nullptr; size_t grid_bytes = 0;    // full-grid FFT scratch
   double2 *d_B = nullptr; size_t B_elems = 0;   // nproj x nb projections
   double2 *d_gemm_ws = nullptr; size_t gemm_ws_elems = 0;
+  struct pw_oz_ws *oz = nullptr;   // FP64-accurate tensor-core products (FP64 projector terms)
   size_t bytes = 0;
   // mixed-precision operands (split FP16), built on first use: beta as rows
   // over G (for beta^H psi) and as rows over projectors (for beta (D B))

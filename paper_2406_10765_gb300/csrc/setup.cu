@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "oz_gemm.cuh"
 #include "pw_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -210,6 +211,7 @@ extern "C" void pw_destroy_cell(pw_cell *c) {
     if (*o) { pw_tc_operand_free(*o); delete *o; *o = nullptr; }
   if (c->d_rmax) cudaFree(c->d_rmax);
   if (c->d_tc_err) cudaFree(c->d_tc_err);
+  if (c->oz) { pw_oz_free(c->oz); delete c->oz; c->oz = nullptr; }
   void *ptrs[] = {c->d_gcol, c->d_gz, c->d_colstart, c->d_colxy, c->d_kin, c->d_V, c->d_Vf,
                   c->d_beta, c->d_D, c->d_z, c->d_dpart, c->d_V0, c->d_grid, c->d_B, c->d_gemm_ws, c->d_beta_split,
                   c->d_m, c->d_ph[0], c->d_ph[1], c->d_ph[2], c->d_bchunk,
