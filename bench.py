@@ -31,14 +31,17 @@ WORKLOADS = {
     "si8": dict(species="Si", n=1, ecut=10.0, nb=24,
                 name="Si-8 (diamond cell, a=10.26 bohr), Gamma, Ecut=10 Ha"),
 }
-E2E_TOL, E2E_MAXIT = 5e-6, 200      # a full solve (Si-512 converges in ~120 steps)
+E2E_STEPS = 20                      # e2e: full steps (tol 0, no locking) through pw_eigsolve
+SOLVE_TOL, SOLVE_MAXIT = 5e-6, 200  # time to solution (Si-512 mixed converges in ~120 steps)
+REF_TOL, REF_MAXIT = 5e-7, 80       # FP64 reference solve started from the mixed result
+DEPS_TARGET = 1e-6                  # |delta eps| of the metric, Ha
 # DRAM bytes (read + write) of one instance of a sub-stage, from one ncu
 # capture of the same kernels: (stage, n, nb) -> (bytes, summary)
 # DRAM bytes per stage from an ncu capture of the same kernels, when the
 # kernels have not changed since (else traffic is null with a note)
-NCU_TRAFFIC = {("tridiag", 3456, 1152): (131.1e9, "profiles/householder_tridiag_n3456.md")}
-NCU_TRAFFIC_STALE = {}
+NCU_TRAFFIC = {}
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of the part (no FP64 tensor path)
+FP32_PEAK_TFLOPS = 80.5     # nominal FP32 rate: 152 SMs x 128 lanes x 2 x 2.07 GHz
 METRIC = "Si-512 eigensolver iters/s"
 
 
@@ -53,8 +56,10 @@ def parse():
     ap.add_argument("--workload", default="si512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-maxit", type=int, default=None,
-                    help="step limit of the end-to-end solve (default 200: a full solve)")
+    ap.add_argument("--e2e-steps", type=int, default=E2E_STEPS,
+                    help="full steps of the end-to-end pw_eigsolve call")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the solve to tolerance and its FP64 reference (|delta eps|)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default FFT plan and K split instead of the autotuner's")
@@ -88,6 +93,55 @@ def serve_sample(args):
             "sample": f"first {len(reqs)} requests of the seeded 2000-request stream"}
 
 
+def accuracy_run(pw, torch, cell, nb, x0, barrier):
+    """The metric's accuracy condition: a mixed-precision solve to SOLVE_TOL
+    (step by step, Ritz values after every step), its FP64 polish, then an
+    FP64 solve to REF_TOL started from the mixed block as the reference.
+    Reports max |eps_mixed - eps_fp64| and the time and steps the mixed solve
+    took to bring every Ritz value within DEPS_TARGET of the reference."""
+    import numpy as np
+    barrier()
+    t0 = time.perf_counter()
+    s = pw.pw_solver_create(cell.h, nb, tol=SOLVE_TOL, x0=x0, precision="mixed")
+    hist, it = [], 0
+    while True:
+        e, r = pw.pw_solver_eigs(s, nb)
+        hist.append((time.perf_counter() - t0, it, e.copy()))
+        if r.max() <= SOLVE_TOL or it >= SOLVE_MAXIT:
+            break
+        rep = pw.pw_subspace_step(cell.h, s)
+        it += 1
+        if rep.nactive == 0:
+            break
+    pw.pw_solver_polish(s)
+    e_mix, r_mix = pw.pw_solver_eigs(s, nb)
+    t_mix = time.perf_counter() - t0
+    psi = pw.new_block(cell.npw, nb)
+    pw.pw_solver_block(s, psi)
+    pw.pw_solver_destroy(s)
+    cell.set_precision("fp64")
+    barrier()
+    t1 = time.perf_counter()
+    e_ref, rep64, st64 = pw.pw_eigsolve(cell.h, nb, tol=REF_TOL, maxit=REF_MAXIT, x0=psi, precision="fp64",
+                                        raise_noconv=False)
+    barrier()
+    t_ref = time.perf_counter() - t1
+    cell.set_precision("mixed")
+    reach = next(((t, k) for (t, k, e) in hist if np.abs(e - e_ref).max() <= DEPS_TARGET), None)
+    deps = float(np.abs(e_mix - e_ref).max())
+    return {"max_abs_deps": deps, "deps_target": DEPS_TARGET, "met": deps <= DEPS_TARGET,
+            "mixed_solve": {"tol": SOLVE_TOL, "steps": it, "seconds": t_mix, "max_resid_fp64": float(r_mix.max()),
+                            "solves_per_s": 1.0 / t_mix},
+            "reach_deps_target": {"seconds": reach[0], "steps": reach[1]} if reach else None,
+            "fp64_reference": {"tol": REF_TOL, "steps": rep64.iters, "seconds": t_ref,
+                               "max_resid": rep64.max_resid, "status": int(st64),
+                               "orth_err": rep64.orth_err},
+            "note": "mixed solve from the seeded start to max residual <= tol, then its FP64 Rayleigh-Ritz "
+                    "polish; reference: FP64 LOBPCG from the mixed block to max residual <= 5e-7 (each "
+                    "reference value within its residual of an exact eigenvalue); reach = first step whose "
+                    "Ritz values are all within the target of the reference"}
+
+
 # ------------------------------------------------------------------ helpers --
 
 def reduce_timing(ms: float, steps: int, world: int, device=None):
@@ -112,7 +166,7 @@ def step_flops(npw, nb, ns, k, nproj, grid, hcols=None):
     gram = 2 * 4.0 * npw * ns * ns                  # S^H S and S^H (H S), Hermitian halves
     # P' = [W P] C_WP and H P' (ns - nb), then X' = X C_X + P' and H X' (nb)
     rot = 2 * 8.0 * npw * nb * (ns - nb) + 2 * 8.0 * npw * nb * nb
-    return dict(fft=fft, proj=proj, gram=gram, rot=rot)
+    return dict(fft=fft, proj=proj, gram=gram, rot=rot, npw=npw)
 
 
 def measured_peaks():
@@ -123,56 +177,85 @@ def measured_peaks():
         return {}
 
 
-def roofline(stage, rr_part, fl, n, nb, precision):
-    """Roofline of the dominant sub-stage, timed by the solver's CUDA events.
+def roofline(stage, rr_part, fl, n, nb, precision, fft=None):
+    """Roofline of the dominant sub-stage, timed by the solver's CUDA events,
+    plus the per-stage fractions.
 
-    FP64 stages count their algorithmic flops with the usual complex counts
-    (Cholesky 4/3 n^3, triangular inverse 4/3 n^3, Householder reduction
-    16/3 n^3, back-transformation of nb vectors 8 n^2 nb, congruence
-    transform 8 n^3) against the nominal FP64 rate; tensor-core stages count
-    the complex product flops once (not the three split products) against
-    the measured sustained 16-bit tensor rate.
+    FP64-ALU work: the Householder reduction's Hermitian matrix-vector
+    products, sum_c 8 (n - c)^2 = 8 n^3 / 3 flop (its rank-64 panel updates,
+    the other 8 n^3 / 3, and every other product of the Rayleigh-Ritz solve
+    run on the FP64-accurate tensor-core path), against the nominal FP64 rate.
+    Tensor-core stages count the tensor flops they issue (split-FP16: three
+    slice products per real multiply-add) against the measured sustained
+    16-bit rate.  The FFT stage counts its algorithmic c64 bytes against the
+    measured HBM copy rate and its flops against the nominal FP32 rate.
     """
     mixed = precision == "mixed"
     parts = {k: v for k, v in stage.items() if k != "rr"}
     parts.update(rr_part)
-    fp64 = {"tridiag": 16 * n ** 3 / 3, "chol_inv": 8 * n ** 3 / 3, "backtransform": 8.0 * n * n * nb}
-    if not mixed:
-        fp64["transform"] = 8.0 * n ** 3
-    names = {"tridiag": "Householder reduction (k_pcol, k_phemv, k_prows + rank-64 k_zgemm)",
-             "chol_inv": "Cholesky + triangular inverse (k_potf2, k_trsm_inv, k_trinv_small, k_zgemm)",
-             "backtransform": "compact-WY back-transformation (k_build_T + k_zgemm)",
-             "transform": "L^-1 A L^-H", "dc": "divide and conquer (k_dc_*)",
-             "gram": "S^H S, S^H HS", "rot": "rotations", "hpsi": "H W (FFT kernels + projectors)",
-             "resid": "residuals"}
+    names = {"tridiag": "Householder reduction: k_phemv + k_pcol + k_prows (FP64 ALU), panel updates on "
+                        "the FP64-accurate tensor-core product",
+             "chol_inv": "Cholesky + triangular inverse (k_potf2, k_trsm_inv, k_trinv_small, k_oz_gemm)",
+             "backtransform": "compact-WY back-transformation (k_build_T + k_oz_gemm)",
+             "transform": "S~ = S M, H S~ = HS M, S~^H H S~ (k_tc_gemm)", "dc": "divide and conquer (k_dc_*)",
+             "gram": "S^H S (k_tc_gemm)", "rot": "rotations (k_tc_gemm)",
+             "hpsi": "H on [X W P] (FFT kernels + projector k_tc_gemm)", "resid": "residuals"}
     dom = max(parts, key=parts.get)
     t_ms = parts[dom]
     roof = {"bound": None, "kernel": names.get(dom, dom), "stage": dom, "ms": t_ms}
     peaks = measured_peaks()
-    if dom in fp64:
-        ach = fp64[dom] / (t_ms * 1e-3) / 1e12
-        tr = NCU_TRAFFIC.get((dom, n, nb)) if not mixed or dom != "transform" else None
-        stale = NCU_TRAFFIC_STALE.get((dom, n, nb))
-        roof.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                    frac=ach / FP64_PEAK_TFLOPS, traffic=tr[0] if tr else None,
-                    traffic_source=tr[1] if tr else stale,
-                    peak_source="nominal FP64 rate: 152 SMs x 2.07 GHz x 2 DFMA/clk (measured DFMA 1.20)")
-    elif dom in ("gram", "rot"):
-        ach = fl[dom] / (t_ms * 1e-3) / 1e12
-        if mixed and peaks.get("bf16_tflops_sustained"):
-            pk = peaks["bf16_tflops_sustained"]
-            roof.update(bound="tensor", achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk, traffic=None,
-                        peak_source="of measured: bf16 sustained (fp16 has the same nominal rate)")
-        else:
-            roof.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                        frac=ach / FP64_PEAK_TFLOPS, traffic=None, peak_source="nominal FP64 rate")
-    fl64 = sum(fp64.values())
-    ms64 = sum(rr_part[k] for k in fp64)
-    roof["rr_fp64"] = {"flops": fl64, "ms": ms64, "tflops": fl64 / (ms64 * 1e-3) / 1e12,
-                       "parts": sorted(fp64)}
+    tc_peak = peaks.get("bf16_tflops_sustained")
+    hbm = peaks.get("hbm_gbs")
+    hemv_flops = 8.0 * n ** 3 / 3
+    if dom == "tridiag":
+        ach = hemv_flops / (t_ms * 1e-3) / 1e12
+        roof.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=ach / FP64_PEAK_TFLOPS,
+                    traffic=NCU_TRAFFIC.get(("tridiag", n, nb)), algorithmic_flops=hemv_flops,
+                    peak_source="nominal FP64 rate: 152 SMs x 2.07 GHz x 2 DFMA/clk (measured DFMA 1.20); "
+                                "FP64 work counted: the Hermitian products, 8 n^3 / 3")
+    elif dom in ("gram", "rot", "transform") and mixed and tc_peak:
+        tfl = 3 * tc_flops(dom, fl, n, nb)
+        ach = tfl / (t_ms * 1e-3) / 1e12
+        roof.update(bound="tensor", achieved=ach, peak=tc_peak, unit="TFLOP/s", frac=ach / tc_peak, traffic=None,
+                    peak_source="of measured: bf16 sustained (fp16 has the same nominal rate)")
+    # per-stage figures
+    st = {}
+    if mixed and tc_peak:
+        for k in ("gram", "transform", "rot"):
+            if parts.get(k):
+                tfl = 3 * tc_flops(k, fl, n, nb)
+                a = tfl / (parts[k] * 1e-3) / 1e12
+                st["tc_gemm_" + k] = {"ms": parts[k], "tensor_tflops": a, "peak": tc_peak, "frac": a / tc_peak,
+                                      "unit": "TFLOP/s (split-FP16 slice products, of measured sustained)"}
+    if fft and hbm:
+        a = fft["bytes"] / (fft["ms"] * 1e-3) / 1e9
+        f = fft["flops"] / (fft["ms"] * 1e-3) / 1e12
+        st["fft"] = {"ms": fft["ms"], "bands": fft["bands"], "achieved_gbs": a, "hbm_peak_gbs": hbm,
+                     "frac_hbm": a / hbm, "tflops": f, "fp32_peak_tflops": FP32_PEAK_TFLOPS,
+                     "frac_fp32": f / FP32_PEAK_TFLOPS, "bytes": fft["bytes"], "source": fft["source"]}
+    if parts.get("tridiag"):
+        a = hemv_flops / (parts["tridiag"] * 1e-3) / 1e12
+        st["householder_fp64"] = {"ms": parts["tridiag"], "tflops": a, "peak": FP64_PEAK_TFLOPS,
+                                  "frac": a / FP64_PEAK_TFLOPS}
+    roof["stages"] = st
     roof["stage_ms"] = stage
     roof["rr_ms"] = rr_part
     return roof
+
+
+def tc_flops(stage, fl, n, nb):
+    """Complex-product flops (8 per complex multiply-add) of a tensor-core stage
+    of the mixed step: the Gram S^H S (Hermitian half), the transform
+    S M, H S M (triangular M: half) and S~^H H S~ (Hermitian half), the
+    rotations P' = S C_P and X' = S~ Y."""
+    npw = fl["npw"]
+    if stage == "gram":
+        return 4.0 * npw * n * n
+    if stage == "transform":
+        return 2 * 4.0 * npw * n * n + 4.0 * npw * n * n
+    if stage == "rot":
+        return 8.0 * npw * n * nb + 8.0 * npw * (n - nb) * nb
+    return 0.0
 
 
 class Clocks:
@@ -376,7 +459,23 @@ def run_gpu(args):
     ns = reps[-1].nsub
     k_act = reps[-1].nactive
     fl = step_flops(cell.npw, nb, ns, k_act, cell.nproj, cell.grid, reps[-1].hpsi_cols)
-    roof = roofline(stage, rr_part, fl, ns, nb, args.precision)
+    fft = None
+    if tune is not None:
+        # the local part of H psi (FFT kernels, V multiply, kinetic), timed by
+        # the autotuner with CUDA events on `bands` bands with the chosen plan
+        import math
+        N = cell.grid[0]
+        ncol = len({(int(a), int(b)) for a, b, _ in cell.m})
+        bands = tune["fft"]["bands"]
+        zb = ncol * N * 8                                   # FP32 z-pencils of one band
+        bpb = max(1, min(bands, (tune["fft"]["batch_mib"] << 20) // zb))
+        n3 = cell.grid[0] * cell.grid[1] * cell.grid[2]
+        per_band = 32.0 * cell.npw + 4.0 * zb + 4.0 * n3 / bpb
+        fft = {"ms": tune["fft"]["ms_best"], "bands": bands, "bytes": per_band * bands,
+               "flops": 2 * 5.0 * n3 * math.log2(n3) * bands,
+               "source": f"autotuner CUDA events, {bands} bands; bytes per band 32 npw (c128 sphere in and "
+                         f"out) + 4 x 8 Ncol N (c64 z-pencils, Ncol {ncol}) + 4 N^3 / {bpb} (FP32 V per batch)"}
+    roof = roofline(stage, rr_part, fl, ns, nb, args.precision, fft)
     roof["hpsi_cols"] = reps[-1].hpsi_cols
     out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -414,28 +513,29 @@ def run_gpu(args):
         out["fp64_comparison"] = {"iters_per_s": 1e3 / ms64, "ms_per_step": ms64,
                                   "mixed_speedup": ms64 / (ms / args.steps)}
 
+    x0h = torch.empty((nb, cell.npw), dtype=torch.complex128).pin_memory()
+    x0h.copy_(torch.from_numpy(np.ascontiguousarray(synth.draw_x0(0, len(ci["tau"]), cell.npw, nb).T)))
+    x0 = x0h.numpy().T          # Fortran-ordered view of the pinned buffer
     if not args.no_e2e:
-        # end to end through pw_eigsolve with host buffers: a pinned host start
-        # block in, host eigenvalues out; the solve runs to tol (at most
-        # E2E_MAXIT steps), then the FP64 polish of the block
-        x0h = torch.empty((nb, cell.npw), dtype=torch.complex128).pin_memory()
-        x0h.copy_(torch.from_numpy(np.ascontiguousarray(synth.draw_x0(0, len(ci["tau"]), cell.npw, nb).T)))
-        x0 = x0h.numpy().T          # Fortran-ordered view of the pinned buffer
+        # the step rate end to end through pw_eigsolve with host buffers: the
+        # pinned host start block in, H X0 and the initial Rayleigh-Ritz,
+        # e2e_steps full steps (tol 0: no band locks, the timed step's work),
+        # the FP64 polish, eigenvalues back to the host
         barrier()
         t0 = time.perf_counter()
-        maxit = args.e2e_maxit if args.e2e_maxit else E2E_MAXIT
-        eig, rep, st = pw.pw_eigsolve(cell.h, nb, tol=E2E_TOL, maxit=maxit, x0=x0,
+        eig, rep, st = pw.pw_eigsolve(cell.h, nb, tol=0.0, maxit=args.e2e_steps, x0=x0,
                                       precision=args.precision, raise_noconv=False)
         barrier()
         t1 = time.perf_counter() - t0
         out["e2e"] = {"value": rep.iters / t1, "unit": "iters/s",
                       "h2d_bytes_per_step": x0.nbytes // max(1, rep.iters),
                       "d2h_bytes_per_step": eig.nbytes // max(1, rep.iters),
-                      "iters": rep.iters, "fp64_iters": rep.fp64_iters, "seconds": t1,
-                      "max_resid": rep.max_resid, "status": int(st),
-                      "note": f"pw_eigsolve (tol {E2E_TOL:g}, at most {maxit} steps) from a pinned "
-                              "host start block: upload, H X0, initial Rayleigh-Ritz, the steps, "
-                              "FP64 polish, eigenvalues back to the host"}
+                      "iters": rep.iters, "seconds": t1, "status": int(st),
+                      "note": f"pw_eigsolve (tol 0, {args.e2e_steps} full steps) from a pinned host start "
+                              "block: upload, H X0, initial Rayleigh-Ritz, the steps, FP64 polish, "
+                              "eigenvalues back to the host"}
+    if rank == 0 and not args.no_accuracy and args.precision == "mixed":
+        out["accuracy"] = accuracy_run(pw, torch, cell, nb, x0, torch.cuda.synchronize)
     if rank == 0 and not args.no_serve:
         out["serving"] = serve_sample(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -345,7 +345,12 @@ def _opts(nbands, tol, maxit, seed, x0, precision, chunk_rows=0):
     o.precision = _PREC[precision]
     o.chunk_rows = int(chunk_rows)
     keep = None
-    if x0 is not None:
+    if x0 is not None and hasattr(x0, "data_ptr"):
+        # a CUDA tensor (column-major, ld = npw): passed as a device pointer
+        assert x0.stride(0) == 1 and (x0.shape[1] <= 1 or x0.stride(1) == x0.shape[0])
+        keep = x0
+        o.x0 = x0.data_ptr()
+    elif x0 is not None:
         keep = np.asfortranarray(x0, dtype=np.complex128)
         o.x0 = keep.ctypes.data
     return o, keep
