@@ -30,6 +30,8 @@ WORKLOADS = {
                   name="Si-512 (4x4x4 diamond cells, a=10.26 bohr), Gamma, Ecut=10 Ha"),
     "si8": dict(species="Si", n=1, ecut=10.0, nb=24,
                 name="Si-8 (diamond cell, a=10.26 bohr), Gamma, Ecut=10 Ha"),
+    "si1728": dict(species="Si", n=6, ecut=8.0, nb=3840, onthefly=True,
+                   name="Si-1728 (6x6x6 diamond cells, a=10.26 bohr), Gamma, Ecut=8 Ha"),
 }
 E2E_STEPS = 20                      # e2e: full steps (tol 0, no locking) through pw_eigsolve
 SOLVE_TOL, SOLVE_MAXIT = 5e-6, 200  # time to solution (Si-512 mixed converges in ~120 steps)
@@ -61,6 +63,8 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the solve to tolerance and its FP64 reference (|delta eps|)")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-si1728", action="store_true",
+                    help="skip the Si-1728 step measured after the Si-512 line's work")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default FFT plan and K split instead of the autotuner's")
     ap.add_argument("--serve-requests", type=int, default=16)
@@ -140,6 +144,54 @@ def accuracy_run(pw, torch, cell, nb, x0, barrier):
                     "polish; reference: FP64 LOBPCG from the mixed block to max residual <= 5e-7 (each "
                     "reference value within its residual of an exact eigenvalue); reach = first step whose "
                     "Ritz values are all within the target of the reference"}
+
+
+def si1728_step(pw, torch, args):
+    """One mixed LOBPCG step of the 1,728-atom cell (Ecut 8 Ha, npw 251,967,
+    grid 128^3, 3,840 bands, 6,912 projectors generated on the fly, tall
+    products in plane-wave chunks), timed with CUDA events after one warm-up
+    step: the steady step with P (Rayleigh-Ritz order 11,520)."""
+    import gc
+    import numpy as np
+    import synth
+    gc.collect()
+    torch.cuda.empty_cache()
+    wl = WORKLOADS["si1728"]
+    ci = synth.cell_inputs(wl["species"], wl["n"], 0)
+    t0 = time.perf_counter()
+    cell = pw.Cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], wl["ecut"], precision="mixed")
+    pw.pw_cell_set_projectors(cell.h, True)
+    tune = None
+    if not args.no_autotune:
+        fr = pw.pw_cell_autotune_fft(cell.h, 256, precision="mixed")
+        tune = {"L": fr.best.L, "R": fr.best.R, "compact": fr.best.compact, "batch_mib": fr.best.batch_bytes >> 20,
+                "ms_best_256_bands": fr.ms_best, "ms_default": fr.ms_default}
+    nb = wl["nb"]
+    s = pw.pw_solver_create(cell.h, nb, tol=0.0, seed=0, precision="mixed")
+    t_setup = time.perf_counter() - t0
+    try:
+        w = pw.pw_subspace_step(cell.h, s)
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = pw.pw_subspace_step(cell.h, s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        eig, _ = pw.pw_solver_eigs(s, nb)
+    finally:
+        pw.pw_solver_destroy(s)
+        cell.close()
+    return {"workload": wl["name"], "npw": cell.npw, "grid": list(cell.grid), "nbands": nb,
+            "nproj": cell.nproj, "projectors": "generated on the fly", "nsub": r.nsub,
+            "ms_per_step": ms, "iters_per_s": 1e3 / ms, "warmup_step_ms": w.ms, "warmup_nsub": w.nsub,
+            "setup_s": t_setup, "finite": bool(np.isfinite(eig).all()),
+            "stage_ms": {k: getattr(r, "ms_" + k) for k in ["resid", "hpsi", "gram", "rr", "rot"]},
+            "rr_ms": {nm: r.ms_rr_part[i] for i, nm in
+                      enumerate(["chol_inv", "transform", "tridiag", "dc", "backtransform"])},
+            "autotune_fft": tune}
 
 
 # ------------------------------------------------------------------ helpers --
@@ -409,8 +461,14 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl")
     wl = WORKLOADS[args.workload]
+    if args.workload == "si1728":
+        # the largest cell: the step alone (FP64 comparison, full solves and the
+        # extra Si-1728 object of the default line do not fit a short run)
+        args.no_fp64 = args.no_e2e = args.no_accuracy = args.no_si1728 = True
     ci = synth.cell_inputs(wl["species"], wl["n"], 0)
     cell = pw.Cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], wl["ecut"], precision=args.precision)
+    if wl.get("onthefly"):
+        pw.pw_cell_set_projectors(cell.h, True)
     nb = wl["nb"]
     stream = torch.cuda.current_stream()
     tune = None
@@ -538,6 +596,9 @@ def run_gpu(args):
         out["accuracy"] = accuracy_run(pw, torch, cell, nb, x0, torch.cuda.synchronize)
     if rank == 0 and not args.no_serve:
         out["serving"] = serve_sample(args)
+    if rank == 0 and not args.no_si1728 and args.precision == "mixed":
+        cell.close()
+        out["si1728"] = si1728_step(pw, torch, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sec, note, parts = oracle_sample(wl)
         out["cpu_baseline"] = {"value": 1.0 / sec, "unit": "iters/s", "cores": cpu_cores(),
