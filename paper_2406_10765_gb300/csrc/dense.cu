@@ -1124,7 +1124,7 @@ __global__ void __launch_bounds__(32 * BT_WARPS) k_build_T(const double2 *G, con
   for (int c = lane; c < b; c += 32) T[r + (long)c * b] = c >= r ? tr[c] : make_double2(0.0, 0.0);
 }
 
-void build_tree(pw_dense_ws *ws, int n) {
+void build_tree(pw_dense_ws *ws, int n, cudaStream_t st) {
   ws->levels.clear();
   std::function<void(int, int, int)> rec = [&](int lo, int hi, int depth) {
     if (hi - lo <= 1) return;
@@ -1145,8 +1145,12 @@ void build_tree(pw_dense_ws *ws, int n) {
     flat.insert(flat.end(), ws->levels[l].begin(), ws->levels[l].end());
     ws->max_level_nodes = std::max(ws->max_level_nodes, (int)ws->levels[l].size() / 3);
   }
-  if (!flat.empty())
-    cudaMemcpy(ws->nodes, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice);
+  // ordered on the solve's stream (after the kernels that read the previous
+  // tree, before the ones that read this one)
+  if (!flat.empty()) {
+    cudaMemcpyAsync(ws->nodes, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+  }
   ws->tree_n = n;
 }
 
@@ -1301,7 +1305,7 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
 
   // 2. divide and conquer
   if (ws->ev[3]) cudaEventRecord(ws->ev[3], st);
-  if (ws->tree_n != n) build_tree(ws, n);
+  if (ws->tree_n != n) build_tree(ws, n, st);
   DcArrays a{lam, ws->Z, ws->W, ws->U, ws->Ds, ws->zs, ws->DK, ws->zK, ws->tauK, ws->zh,
              ws->lamK, ws->dD, ws->lnew, ws->perm, ws->colK, ws->orig, ws->dcol, ws->src,
              (int *)ws->p /* defl scratch: n ints fit in n double2 */, ws->knode, ws->rhonode,

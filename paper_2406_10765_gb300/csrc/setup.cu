@@ -91,11 +91,14 @@ static bool fft_plan(int n, pw_fft_axis &ax) {
   return r == 1 && n >= 2;
 }
 
-static pw_status upload(void **dst, const void *src, size_t bytes, size_t *acc) {
+// Host tables to the device, ordered on the caller's stream: a plain
+// cudaMemcpy from pageable memory may return before its DMA has landed, and
+// kernels on a non-blocking stream are not ordered after it
+static pw_status upload(void **dst, const void *src, size_t bytes, size_t *acc, cudaStream_t st) {
   if (bytes == 0) { *dst = nullptr; return PW_OK; }
   if (cudaMalloc(dst, bytes) != cudaSuccess) { cudaGetLastError(); *dst = nullptr; return PW_ERR_OOM; }
   *acc += bytes;
-  PW_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+  PW_CUDA(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st));
   return PW_OK;
 }
 
@@ -300,7 +303,7 @@ extern "C" pw_status pw_setup_cell(const pw_cell_desc *d, void *stream, pw_cell 
   size_t acc = 0;
   pw_status s;
 #define UP(dst, vec)                                                                           \
-  s = upload((void **)&(dst), (vec).data(), (vec).size() * sizeof((vec)[0]), &acc);            \
+  s = upload((void **)&(dst), (vec).data(), (vec).size() * sizeof((vec)[0]), &acc, st);        \
   if (s != PW_OK) { pw_destroy_cell(c); return s; }
   UP(c->d_gcol, gcol);
   UP(c->d_gz, gz);
@@ -356,10 +359,10 @@ extern "C" pw_status pw_setup_cell(const pw_cell_desc *d, void *stream, pw_cell 
       }
       double *dfx, *dfy, *dfz, *ddep;
       size_t tmp = 0;
-      if ((s = upload((void **)&dfx, f[0].data(), f[0].size() * 8, &tmp)) != PW_OK ||
-          (s = upload((void **)&dfy, f[1].data(), f[1].size() * 8, &tmp)) != PW_OK ||
-          (s = upload((void **)&dfz, f[2].data(), f[2].size() * 8, &tmp)) != PW_OK ||
-          (s = upload((void **)&ddep, d->vdepth, (size_t)d->natom * 8, &tmp)) != PW_OK) {
+      if ((s = upload((void **)&dfx, f[0].data(), f[0].size() * 8, &tmp, st)) != PW_OK ||
+          (s = upload((void **)&dfy, f[1].data(), f[1].size() * 8, &tmp, st)) != PW_OK ||
+          (s = upload((void **)&dfz, f[2].data(), f[2].size() * 8, &tmp, st)) != PW_OK ||
+          (s = upload((void **)&ddep, d->vdepth, (size_t)d->natom * 8, &tmp, st)) != PW_OK) {
         pw_destroy_cell(c); return s;
       }
       pw_count_launch();
@@ -394,10 +397,10 @@ extern "C" pw_status pw_setup_cell(const pw_cell_desc *d, void *stream, pw_cell 
     // tables stay with the cell (projector regeneration); uploaded straight
     // into it, so a failure part-way is released by pw_destroy_cell
     size_t tmp = 0;
-    if ((s = upload((void **)&c->d_m, c->m_host.data(), c->m_host.size() * 4, &tmp)) != PW_OK ||
-        (s = upload((void **)&c->d_ph[0], ph[0].data(), ph[0].size() * 16, &tmp)) != PW_OK ||
-        (s = upload((void **)&c->d_ph[1], ph[1].data(), ph[1].size() * 16, &tmp)) != PW_OK ||
-        (s = upload((void **)&c->d_ph[2], ph[2].data(), ph[2].size() * 16, &tmp)) != PW_OK) {
+    if ((s = upload((void **)&c->d_m, c->m_host.data(), c->m_host.size() * 4, &tmp, st)) != PW_OK ||
+        (s = upload((void **)&c->d_ph[0], ph[0].data(), ph[0].size() * 16, &tmp, st)) != PW_OK ||
+        (s = upload((void **)&c->d_ph[1], ph[1].data(), ph[1].size() * 16, &tmp, st)) != PW_OK ||
+        (s = upload((void **)&c->d_ph[2], ph[2].data(), ph[2].size() * 16, &tmp, st)) != PW_OK) {
       pw_destroy_cell(c); return s;
     }
     double rp = d->pwidth;

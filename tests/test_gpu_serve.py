@@ -95,3 +95,22 @@ def test_serve_autotuned_plans_within_tolerance():
         assert a["status"] == 0 and b["status"] == 0, (a["status"], b["status"])
         assert np.abs(a["eig"] - b["eig"]).max() <= 2e-6
         assert b["max_resid"] <= 5e-6 and b["orth_err"] <= 1e-10
+
+
+def test_serve_eight_slots_equals_alone():
+    # eight requests of the seeded stream on eight slots at once (non-blocking
+    # streams, many cells set up concurrently): each result bitwise equal to
+    # the request served alone.  Cell tables and the divide-and-conquer tree
+    # are uploaded in order on the request's stream; a plain pageable copy
+    # may return before its DMA lands, and non-blocking streams do not wait
+    # for it.
+    import paper_2406_10765_gb300 as pw
+    reqs = synth.serving_requests(2000, rate_per_s=1000.0, seed=2024)[:8]
+    for r in reqs:
+        r["n"] = min(r["n"], 2)
+        r["nbands"] = round(1.125 * 2 * 8 * r["n"] ** 3)
+    mix = pw.pw_serve(reqs, max_slots=8, precision="mixed")
+    for r, m in zip(reqs, mix):
+        assert m["status"] == 0, m["status"]
+        alone = pw.pw_serve([dict(r, t_arrival=0.0)], max_slots=1, precision="mixed")[0]
+        assert np.array_equal(alone["eig"], m["eig"])
