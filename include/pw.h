@@ -402,6 +402,16 @@ pw_status pw_zgemm_f64tc(char opA, char opB, int m, int n, int k, const double *
  * pipe.  Results agree to FP64 rounding.  Errors: PW_ERR_ARG. */
 pw_status pw_dense_products(int mode);
 
+/* Captured CUDA graphs for the eigensolver of the Rayleigh-Ritz step (its
+ * three stages: Householder tridiagonalisation, divide and conquer,
+ * back-transformation), process-wide: with on = 1 (default) a stage whose
+ * order and wanted-pair count repeat on the same workspace is captured once
+ * and replayed (thousands of kernel launches per stage become one graph
+ * launch); with 0 every launch is issued directly.  Graphs are used only on
+ * streams other than the legacy default stream.  Results are the same.
+ * Errors: PW_ERR_ARG. */
+pw_status pw_dense_graphs(int on);
+
 /* ---- Autotuner: the plan and tile-shape choices of the hot kernels ----
  * Sec. III-D picks, for each execution step, the process count that runs it
  * fastest among the candidates that fit in memory.  On one GPU the matching

@@ -185,6 +185,14 @@ def pw_dense_products(mode):
     _check(_dense_products(int(mode)), "pw_dense_products")
 
 
+_dense_graphs = _sig("pw_dense_graphs", ct.c_int, [ct.c_int])
+
+
+def pw_dense_graphs(on):
+    """1: capture and replay the eigensolver stages as CUDA graphs (non-default streams); 0: direct launches."""
+    _check(_dense_graphs(int(on)), "pw_dense_graphs")
+
+
 _launches = _sig("pw_kernel_launches", ct.c_uint64, [])
 
 

@@ -1173,7 +1173,7 @@ pw_status pw_dense_gemm(pw_dense_ws *ws, char opA, char opB, int m, int n, int k
                                   std::max(pw_oz_ws_bytes(ws->nmax, 256, ws->nmax),
                                            pw_oz_ws_bytes(ws->nmax, ws->nbmax, ws->nmax)));
       void *p = nullptr;
-      if (cudaMalloc(&p, big) == cudaSuccess) { ws->oz.buf = p; ws->oz.bytes = big; }
+      if (cudaMalloc(&p, big) == cudaSuccess) { ws->oz.buf = p; ws->oz.bytes = big; ++ws->oz.gen; }
       else cudaGetLastError();
     }
     return pw_zgemm_oz(&ws->oz, opA, opB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, st, herm);
@@ -1235,6 +1235,8 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
 }
 
 void pw_dense_free(pw_dense_ws *ws) {
+  for (auto &g : ws->graphs) cudaGraphExecDestroy(g.exec);
+  ws->graphs.clear();
   pw_oz_free(&ws->oz);
   void *ptrs[] = {ws->G, ws->A, ws->T, ws->Linv, ws->Y, ws->dscale, ws->piv, ws->flag, ws->d, ws->e,
                   ws->lam, ws->tau, ws->p, ws->w, ws->part, ws->Z, ws->W, ws->U, ws->Ds, ws->zs,
@@ -1260,11 +1262,11 @@ void pw_dense_stage_ms(pw_dense_ws *ws, float out[5]) {
 // ======================================================================
 // Hermitian eigensolver
 // ======================================================================
-pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam, double2 *Y,
-                         cudaStream_t st) {
-  if (n <= 0 || nb <= 0 || nb > n || n > ws->nmax || nb > ws->nbmax) return PW_ERR_ARG;
+namespace {
+// The three stages of the eigensolver, each a fixed launch sequence for a
+// given (n, nb) on a given workspace (so each can be captured as a graph).
+pw_status stage_tridiag(pw_dense_ws *ws, int n, double2 *A, cudaStream_t st) {
   // 1. Householder tridiagonalisation: panels of TPB columns (lower triangle)
-  if (ws->ev[2]) cudaEventRecord(ws->ev[2], st);
   PW_CUDA(cudaMemsetAsync(ws->ticket, 0, sizeof(unsigned), st));
   {
     const double2 mone = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
@@ -1303,9 +1305,11 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
   }
   PW_TRY(pw_check_launch("tridiag"));
 
+  return PW_OK;
+}
+
+pw_status stage_dc(pw_dense_ws *ws, int n, int nb, double *lam, cudaStream_t st) {
   // 2. divide and conquer
-  if (ws->ev[3]) cudaEventRecord(ws->ev[3], st);
-  if (ws->tree_n != n) build_tree(ws, n, st);
   DcArrays a{lam, ws->Z, ws->W, ws->U, ws->Ds, ws->zs, ws->DK, ws->zK, ws->tauK, ws->zh,
              ws->lamK, ws->dD, ws->lnew, ws->perm, ws->colK, ws->orig, ws->dcol, ws->src,
              (int *)ws->p /* defl scratch: n ints fit in n double2 */, ws->knode, ws->rhonode,
@@ -1341,8 +1345,11 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
   }
   PW_TRY(pw_check_launch("divide and conquer"));
 
+  return PW_OK;
+}
+
+pw_status stage_backtransform(pw_dense_ws *ws, int n, int nb, const double2 *A, double2 *Y, cudaStream_t st) {
   // 3. back-transformation of the wanted columns
-  if (ws->ev[4]) cudaEventRecord(ws->ev[4], st);
   pw_count_launch();
   k_bt_init<<<(unsigned)(((long)n * nb + 255) / 256), 256, 0, st>>>(ws->Z, n, nb, Y);
   // Y = H_0 H_1 ... H_{n-2} Z, blocks of BTB reflectors from the last:
@@ -1365,6 +1372,86 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
     }
   }
   return pw_check_launch("back-transform");
+}
+
+std::atomic<int> g_graphs{1};
+
+// A stage through the workspace's graph cache: the first call of a key runs
+// directly (and grows any workspace it needs); a key seen twice in a row is
+// captured (thread-local capture mode) and then replayed.  Graphs bake in
+// buffer addresses: an entry is dropped when the workspace's product buffers
+// were reallocated since its capture (generation).  Not on the legacy default
+// stream (which cannot be captured) or a stream already being captured.
+template <typename F>
+pw_status run_stage(pw_dense_ws *ws, int stage, int n, int nb, const void *p0, const void *p1, cudaStream_t st,
+                    F &&fn) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!g_graphs.load() || st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread ||
+      cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return fn();
+  // the product buffers' generation and the product mode both decide what a
+  // capture holds
+  const unsigned gen = 2 * ws->oz.gen + (unsigned)pw_dense_products_mode();
+  for (auto it = ws->graphs.begin(); it != ws->graphs.end(); ++it) {
+    if (it->stage == stage && it->n == n && it->nb == nb && it->p0 == p0 && it->p1 == p1) {
+      if (it->gen == gen) {
+        PW_CUDA(cudaGraphLaunch(it->exec, st));
+        pw_count_launches(it->kernels);
+        return PW_OK;
+      }
+      cudaGraphExecDestroy(it->exec);
+      ws->graphs.erase(it);
+      break;
+    }
+  }
+  const bool repeat = ws->last_key[stage][0] == n && ws->last_key[stage][1] == nb;
+  ws->last_key[stage][0] = n;
+  ws->last_key[stage][1] = nb;
+  if (!repeat) return fn();
+  cudaGraph_t g = nullptr;
+  PW_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const uint64_t k0 = pw_thread_launches();
+  const pw_status r = fn();
+  const uint64_t nk = pw_thread_launches() - k0;
+  const cudaError_t ce = cudaStreamEndCapture(st, &g);
+  cudaGraphExec_t exec = nullptr;
+  if (r != PW_OK || ce != cudaSuccess || !g || 2 * ws->oz.gen + (unsigned)pw_dense_products_mode() != gen ||
+      cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
+    // capture did not work out: clear the error and run the stage directly
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return fn();
+  }
+  cudaGraphDestroy(g);
+  if (ws->graphs.size() >= 6) {
+    cudaGraphExecDestroy(ws->graphs.front().exec);
+    ws->graphs.erase(ws->graphs.begin());
+  }
+  ws->graphs.push_back({stage, n, nb, p0, p1, gen, exec, nk});
+  PW_CUDA(cudaGraphLaunch(exec, st));
+  return PW_OK;
+}
+}  // namespace
+
+extern "C" pw_status pw_dense_graphs(int on) {
+  if (on != 0 && on != 1) return PW_ERR_ARG;
+  g_graphs.store(on);
+  return PW_OK;
+}
+
+pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam, double2 *Y,
+                         cudaStream_t st) {
+  if (n <= 0 || nb <= 0 || nb > n || n > ws->nmax || nb > ws->nbmax) return PW_ERR_ARG;
+  // 1. Householder tridiagonalisation: panels of TPB columns (lower triangle)
+  if (ws->ev[2]) cudaEventRecord(ws->ev[2], st);
+  PW_TRY(run_stage(ws, 0, n, nb, A, nullptr, st, [&] { return stage_tridiag(ws, n, A, st); }));
+  // 2. divide and conquer (the merge tree is built and uploaded outside any capture)
+  if (ws->ev[3]) cudaEventRecord(ws->ev[3], st);
+  if (ws->tree_n != n) build_tree(ws, n, st);
+  PW_TRY(run_stage(ws, 1, n, nb, lam, nullptr, st, [&] { return stage_dc(ws, n, nb, lam, st); }));
+  // 3. back-transformation of the wanted columns
+  if (ws->ev[4]) cudaEventRecord(ws->ev[4], st);
+  return run_stage(ws, 2, n, nb, A, Y, st, [&] { return stage_backtransform(ws, n, nb, A, Y, st); });
 }
 
 // ======================================================================

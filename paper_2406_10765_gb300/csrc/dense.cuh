@@ -29,6 +29,17 @@ struct pw_dense_ws {
   double *rhonode = nullptr;
   double2 *gemm_ws = nullptr; size_t gemm_ws_elems = 0;
   pw_oz_ws oz;                // FP64-accurate tensor-core products (slices, partial sums)
+  // captured eigensolver stages (tridiagonalisation, divide and conquer,
+  // back-transformation) keyed by stage, order, wanted pairs and buffers
+  struct graph_entry {
+    int stage, n, nb;
+    const void *p0, *p1;
+    unsigned gen;
+    cudaGraphExec_t exec;
+    uint64_t kernels;         // kernel launches the capture holds
+  };
+  std::vector<graph_entry> graphs;
+  int last_key[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
   // blocked back-transformation: reflector panel, its Gram, T, two work blocks
   double2 *Vb = nullptr, *Gv = nullptr, *Tb = nullptr, *Wk = nullptr, *Wk2 = nullptr;
   unsigned *ticket = nullptr;   // last-block-done counter of the Householder steps

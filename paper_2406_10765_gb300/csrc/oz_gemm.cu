@@ -558,6 +558,22 @@ pw_status slice_operand(char op, int bside, const double2 *X, int ld, int nrows,
 
 int g_max_parts = 16;
 
+// the kernel's shared-memory opt-in, once per device (outside any later
+// stream capture: the first product on a device runs uncaptured)
+pw_status allow_smem() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  PW_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return PW_ERR_ARG;
+  std::lock_guard<std::mutex> g(mu);
+  if (!done[dev]) {
+    PW_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    done[dev] = true;
+  }
+  return PW_OK;
+}
+
 }  // namespace
 
 size_t pw_oz_ws_bytes(int m, int n, int k) {
@@ -598,12 +614,14 @@ pw_status oz_block(pw_oz_ws *w, char opA, char opB, int mb, int nb, int k, doubl
     if (w->buf) cudaFree(w->buf);
     w->buf = nullptr;
     w->bytes = 0;
+    ++w->gen;
     if (cudaMalloc(&w->buf, need) != cudaSuccess) { cudaGetLastError(); return PW_ERR_OOM; }
     w->bytes = need;
   }
   if (!w->err) {
     if (cudaMalloc((void **)&w->err, 16) != cudaSuccess) { cudaGetLastError(); return PW_ERR_OOM; }
     PW_CUDA(cudaMemsetAsync(w->err, 0, 16, st));
+    ++w->gen;
   }
   unsigned char *p = (unsigned char *)w->buf;
   __half *sa = (__half *)p, *sb = (__half *)(p + abytes);
@@ -613,7 +631,7 @@ pw_status oz_block(pw_oz_ws *w, char opA, char opB, int mb, int nb, int k, doubl
   CUtensorMap ma, mbm;
   if (!make_map(&ma, sa, kpad, (long)S * arows, BM) || !make_map(&mbm, sb, kpad, (long)S * brows, BN))
     return PW_ERR_CUDA;
-  PW_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  PW_TRY(allow_smem());
   const int mtiles = arows / BM, ntiles = brows / BN, tiles = mtiles * ntiles;
   // K split when the tiles alone leave SMs idle (>= 8 chunks per part)
   const int nch = (kblocks + CHUNK_KB - 1) / CHUNK_KB;
@@ -625,6 +643,7 @@ pw_status oz_block(pw_oz_ws *w, char opA, char opB, int mb, int nb, int k, doubl
       if (w->part) cudaFree(w->part);
       w->part = nullptr;
       w->part_bytes = 0;
+      ++w->gen;
       if (cudaMalloc((void **)&w->part, pbytes) != cudaSuccess) { cudaGetLastError(); parts = 1; }
       else w->part_bytes = pbytes;
     }

@@ -15,6 +15,7 @@ struct pw_oz_ws {
   double2 *part = nullptr;    // K-split partial results
   size_t part_bytes = 0;
   int *err = nullptr;         // device error word (a bounded wait ran out)
+  unsigned gen = 0;           // bumped whenever buf or part is reallocated
 };
 
 // C = alpha op(A) op(B) + beta C, column-major complex128, op in {N, C};

@@ -26,6 +26,8 @@
 void pw_last_cuda_error(cudaError_t e, const char *file, int line);
 // count of kernel launches issued by the library (diagnostics; see pw_kernel_launches)
 void pw_count_launch();
+void pw_count_launches(uint64_t n);
+uint64_t pw_thread_launches();   // this thread's count (captures count their kernels)
 pw_status pw_check_launch(const char *what);
 
 // --------------------------------------------------------------------------

@@ -22,7 +22,18 @@
 static thread_local char g_err[256];
 static std::atomic<unsigned long long> g_launches{0};
 
-void pw_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local unsigned long long g_thread_launches = 0;
+
+void pw_count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++g_thread_launches;
+}
+// a replayed graph runs the kernels its capture counted
+void pw_count_launches(uint64_t n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  g_thread_launches += n;
+}
+uint64_t pw_thread_launches() { return g_thread_launches; }
 extern "C" uint64_t pw_kernel_launches(void) { return g_launches.load(); }
 
 void pw_last_cuda_error(cudaError_t e, const char *file, int line) {

@@ -157,3 +157,35 @@ def test_fp64_steps_same_in_both_product_modes():
         st = O.lobpcg_step(orc, st)
     assert np.abs(eigs[0] - eigs[1]).max() < 1e-11
     assert np.abs(eigs[1] - st.lam).max() < 1e-9
+
+
+def test_graph_replay_same_steps_on_a_side_stream():
+    # on a non-default stream the eigensolver stages are captured once their
+    # order repeats and replayed as CUDA graphs: the steps are bitwise the
+    # same as with direct launches, and follow the oracle
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 2, 10.0)
+    nb = 144
+    x0 = synth.draw_x0(0, 64, orc.npw, nb)
+    st = O.lobpcg_init(orc, x0)
+    for _ in range(4):
+        st = O.lobpcg_step(orc, st)
+    side = torch.cuda.Stream()
+    eigs, launches = [], []
+    for on in (1, 0):
+        pw.pw_dense_graphs(on)
+        try:
+            with torch.cuda.stream(side):
+                s = pw.pw_solver_create(lib.h, nb, tol=0.0, x0=x0)
+                k0 = pw.pw_kernel_launches()
+                for _ in range(4):          # nsub 288, then 432 three times: captured, replayed
+                    pw.pw_subspace_step(lib.h, s)
+                launches.append(pw.pw_kernel_launches() - k0)
+                eigs.append(pw.pw_solver_eigs(s, nb)[0])
+                pw.pw_solver_destroy(s)
+            side.synchronize()
+        finally:
+            pw.pw_dense_graphs(1)
+    assert np.array_equal(eigs[0], eigs[1])
+    assert launches[0] == launches[1]        # replays count the kernels they run
+    assert np.abs(eigs[0] - st.lam).max() < 1e-9
