@@ -67,34 +67,44 @@ def parse():
                     help="skip the Si-1728 step measured after the Si-512 line's work")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default FFT plan and K split instead of the autotuner's")
-    ap.add_argument("--serve-requests", type=int, default=16)
-    ap.add_argument("--serve-rate", type=float, default=0.5)
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="requests per arrival rate (a prefix of the seeded 2000-request stream)")
+    ap.add_argument("--serve-rates", default="0.5,1,2",
+                    help="Poisson arrival rates (requests/s) of the serving sweep")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving sweep and print its line")
     return ap.parse_args()
 
 
-def serve_sample(args):
-    """A bounded prefix of the seeded 2000-request serving stream (Si/C, n in
-    1..3, Ecut ~ U[8, 12], bands = 1.125 x occupied, Poisson arrivals), served
-    with continuous batching in mixed precision: solves/s and p50/p99 latency."""
+def serve_sweep(args):
+    """Served fixed-potential eigensolves at several Poisson arrival rates:
+    for each rate the first N requests of the seeded 2000-request stream
+    (Si/C diamond cells, n in 1..3, Ecut ~ U[8, 12] Ha, bands = 1.125 x
+    occupied), continuous batching in mixed precision: solves/s over the
+    wall time and p50/p99 latency (arrival to result)."""
     import numpy as np
     import synth
     import paper_2406_10765_gb300 as pw
-    reqs = synth.serving_requests(2000, rate_per_s=args.serve_rate, seed=2024)[:args.serve_requests]
-    t0 = time.perf_counter()
-    out = pw.pw_serve(reqs, max_slots=4, precision="mixed", autotune=not args.no_autotune)
-    wall = time.perf_counter() - t0
-    ok = [o for o in out if o["status"] in (0, -5)]
-    lat = np.array([o["latency"] for o in ok])
-    return {"metric": "served fixed-potential eigensolves", "solves_per_s": len(ok) / wall,
-            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "requests": len(reqs), "completed": len(ok),
-            "converged": sum(o["status"] == 0 for o in out),
-            "status_counts": {str(k): sum(o["status"] == k for o in out)
-                              for k in sorted(set(o["status"] for o in out))},
-            "max_resid": float(max(o["max_resid"] for o in ok)),
-            "arrival_rate_per_s": args.serve_rate, "slots": 4, "precision": "mixed",
-            "autotune": not args.no_autotune,
-            "sample": f"first {len(reqs)} requests of the seeded 2000-request stream"}
+    out = []
+    for rate in [float(x) for x in args.serve_rates.split(",") if x]:
+        reqs = synth.serving_requests(2000, rate_per_s=rate, seed=2024)[:args.serve_requests]
+        t0 = time.perf_counter()
+        res = pw.pw_serve(reqs, max_slots=args.serve_slots, precision="mixed", autotune=not args.no_autotune)
+        wall = time.perf_counter() - t0
+        ok = [o for o in res if o["status"] in (0, -5)]
+        lat = np.array([o["latency"] for o in ok])
+        out.append({"arrival_rate_per_s": rate, "requests": len(reqs), "completed": len(ok),
+                    "converged": sum(o["status"] == 0 for o in res),
+                    "status_counts": {str(k): sum(o["status"] == k for o in res)
+                                      for k in sorted(set(o["status"] for o in res))},
+                    "solves_per_s": len(ok) / wall, "wall_s": wall,
+                    "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                    "max_resid": float(max(o["max_resid"] for o in ok)),
+                    "last_arrival_s": float(reqs[-1]["t_arrival"])})
+    return {"metric": "served fixed-potential eigensolves", "slots": args.serve_slots, "precision": "mixed",
+            "autotune": not args.no_autotune, "rates": out,
+            "sample": f"first {args.serve_requests} requests of the seeded 2000-request stream at each rate"}
 
 
 def accuracy_run(pw, torch, cell, nb, x0, barrier):
@@ -299,13 +309,17 @@ def tc_flops(stage, fl, n, nb):
     """Complex-product flops (8 per complex multiply-add) of a tensor-core stage
     of the mixed step: the Gram S^H S (Hermitian half), the transform
     S M, H S M (triangular M: half) and S~^H H S~ (Hermitian half), the
-    rotations P' = S C_P and X' = S~ Y."""
+    rotations: with H blocks carried X' = S C, H X' = HS C, P' = S C_P and
+    H P' = HS C_P (C_P's first nb rows zero: skipped), else P' = S C_P and
+    X' = S~ Y."""
     npw = fl["npw"]
     if stage == "gram":
         return 4.0 * npw * n * n
     if stage == "transform":
         return 2 * 4.0 * npw * n * n + 4.0 * npw * n * n
     if stage == "rot":
+        if fl.get("carried"):
+            return 2 * (8.0 * npw * n * nb + 8.0 * npw * (n - nb) * nb)
         return 8.0 * npw * n * nb + 8.0 * npw * (n - nb) * nb
     return 0.0
 
@@ -517,6 +531,8 @@ def run_gpu(args):
     ns = reps[-1].nsub
     k_act = reps[-1].nactive
     fl = step_flops(cell.npw, nb, ns, k_act, cell.nproj, cell.grid, reps[-1].hpsi_cols)
+    # mixed: H applied only to W means H X and H P were carried (4 rotation products)
+    fl["carried"] = args.precision == "mixed" and reps[-1].hpsi_cols == k_act
     fft = None
     if tune is not None:
         # the local part of H psi (FFT kernels, V multiply, kinetic), timed by
@@ -595,7 +611,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_accuracy and args.precision == "mixed":
         out["accuracy"] = accuracy_run(pw, torch, cell, nb, x0, torch.cuda.synchronize)
     if rank == 0 and not args.no_serve:
-        out["serving"] = serve_sample(args)
+        out["serving"] = serve_sweep(args)
     if rank == 0 and not args.no_si1728 and args.precision == "mixed":
         cell.close()
         out["si1728"] = si1728_step(pw, torch, args)
@@ -609,9 +625,22 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_serve_only(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    sv = serve_sweep(args)
+    last = sv["rates"][-1]
+    print(json.dumps({"metric": "served fixed-potential eigensolves (solves/s)", "value": last["solves_per_s"],
+                      "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+                      "config": {"workload": "seeded serving stream (Si/C, n 1..3, Ecut 8-12 Ha)"},
+                      "serving": sv}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.serve_only:
+        run_serve_only(a)
     else:
         run_gpu(a)

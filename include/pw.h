@@ -149,6 +149,13 @@ typedef struct {
                            split-FP16 products (Gram, S M, rotations); 0 picks
                            chunks whose split operands stay under ~8 GB.  Bounds
                            the solver's scratch; results agree to rounding. */
+  int h_blocks;         /* PW_MIXED: 0 (default) apply H to [X W P] every
+                           step; 1 carry H X and H P through the split-FP16
+                           rotations (one H application per step, to W) while
+                           the largest residual norm is above 1e-3, then apply
+                           H to [X W P], no band locks while carrying; 2 always
+                           carry (stalls near 1e-4: the carried blocks hold the
+                           split products' error).  FP64 always carries. */
 } pw_solve_opts;
 
 typedef struct {

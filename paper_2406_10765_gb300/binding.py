@@ -45,7 +45,7 @@ class pw_cell_desc(ct.Structure):
 class pw_solve_opts(ct.Structure):
     _fields_ = [("nbands", ct.c_int), ("tol", ct.c_double), ("maxit", ct.c_int),
                 ("seed", ct.c_uint64), ("x0", ct.c_void_p), ("precision", ct.c_int),
-                ("chunk_rows", ct.c_int)]
+                ("chunk_rows", ct.c_int), ("h_blocks", ct.c_int)]
 
 
 class pw_step_report(ct.Structure):
@@ -347,11 +347,12 @@ def pw_destroy_cell(cell):
     _destroy(cell)
 
 
-def _opts(nbands, tol, maxit, seed, x0, precision, chunk_rows=0):
+def _opts(nbands, tol, maxit, seed, x0, precision, chunk_rows=0, h_blocks=0):
     o = pw_solve_opts()
     o.nbands, o.tol, o.maxit, o.seed = int(nbands), float(tol), int(maxit), int(seed)
     o.precision = _PREC[precision]
     o.chunk_rows = int(chunk_rows)
+    o.h_blocks = int(h_blocks)
     keep = None
     if x0 is not None and hasattr(x0, "data_ptr"):
         # a CUDA tensor (column-major, ld = npw): passed as a device pointer
@@ -365,8 +366,8 @@ def _opts(nbands, tol, maxit, seed, x0, precision, chunk_rows=0):
 
 
 def pw_solver_create(cell, nbands, tol=1e-8, maxit=200, seed=0, x0=None, precision="fp64",
-                     stream=None, chunk_rows=0):
-    o, keep = _opts(nbands, tol, maxit, seed, x0, precision, chunk_rows)
+                     stream=None, chunk_rows=0, h_blocks=0):
+    o, keep = _opts(nbands, tol, maxit, seed, x0, precision, chunk_rows, h_blocks)
     h = ct.c_void_p()
     _check(_screate(cell, ct.byref(o), _stream(stream), ct.byref(h)), "pw_solver_create")
     del keep
@@ -425,8 +426,8 @@ def pw_solver_destroy(solver):
 
 
 def pw_eigsolve(cell, nbands, tol=1e-8, maxit=200, seed=0, x0=None, precision="fp64",
-                psi_out=None, stream=None, raise_noconv=True, chunk_rows=0):
-    o, keep = _opts(nbands, tol, maxit, seed, x0, precision, chunk_rows)
+                psi_out=None, stream=None, raise_noconv=True, chunk_rows=0, h_blocks=0):
+    o, keep = _opts(nbands, tol, maxit, seed, x0, precision, chunk_rows, h_blocks)
     eig = np.zeros(nbands)
     rep = pw_solve_report()
     ptr = _dptr(psi_out) if psi_out is not None else ct.c_void_p()

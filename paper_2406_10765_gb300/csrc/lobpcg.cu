@@ -53,7 +53,6 @@ struct pw_solver {
   int chunk_rows = 0;            // rows per chunk of the tall split products (0: automatic)
   float *rmax = nullptr;
   int *d_err = nullptr;
-  double2 *Cz = nullptr;
   // mixed precision applies H to the whole basis [X W P] every step instead of
   // carrying H X and H P through the rotations (their split-precision errors
   // would be amplified by ill-conditioned coefficients near convergence)
@@ -61,8 +60,21 @@ struct pw_solver {
   // mixed precision with fresh H: the Rayleigh-Ritz left Y in the dense
   // workspace and S~ = S M in S2, and the rotation writes X' = S~ Y to HS2
   bool ytilde = false, x_in_hs2 = false;
+  bool xh_swapped = false;        // carried rotation left X' in HS and H X' in S
+  bool hst_split_valid = false;   // opHST holds the split of the current H S
   bool hx_valid = true;    // HS[:, 0:nb] == H X for the current X
+  // mixed precision: 0 recompute H X and H P every step; 1 carry them
+  // through the rotations while the largest residual is above kCarryTol,
+  // then recompute; 2 always carry
+  int h_blocks = 0;
 };
+
+// Residual level below which the mixed solve stops carrying H X and H P
+// through the split-precision rotations and applies H to [X W P] afresh: the
+// carried blocks hold the split products' error (~1e-6 of |HS| |C|, larger
+// when the basis is ill-conditioned near convergence), harmless against
+// residuals well above it.
+constexpr double kCarryTol = 1e-3;
 
 namespace {
 
@@ -290,6 +302,7 @@ pw_status tall_times_coef(pw_solver *s, const double2 *X, int ns, pw_tc_operand 
 // there too, and finish in FP64 (eigensolve, C = M Y).
 pw_status rr_mixed_from_gram(pw_solver *s, int ns, int *chol_ok) {
   const int npw = s->npw, nb = s->nb, ldg = 3 * nb;
+  s->hst_split_valid = false;
   PW_TRY(pw_rr_factor(&s->dws, ns, s->G, ldg, s->Mx, ldg, chol_ok, s->st, piv_tol(s)));
   if (!*chol_ok) return PW_OK;
   PW_TRY(pw_tc_operand_alloc(&s->opM, 2 * ns, 2 * ns, s->st));
@@ -298,14 +311,13 @@ pw_status rr_mixed_from_gram(pw_solver *s, int ns, int *chol_ok) {
   PW_TRY(tall_times_coef(s, s->S, ns, &s->opST, false, &s->opM, 2 * ns, s->S2, 0, 1));
   s->st_split_valid = tall_chunk(s, ns) >= npw;   // opST holds the split of all of S
   PW_TRY(tall_times_coef(s, s->HS, ns, &s->opHST, false, &s->opM, 2 * ns, s->HS2, 0, 1));
+  s->hst_split_valid = tall_chunk(s, ns) >= npw;  // opHST holds the split of all of H S
   // A~ = S~^H (H S~)
   PW_TRY(tall_gram(s, s->S2, s->HS2, ns, s->A, ldg));
-  if (s->fresh_h) {
-    // X' = S~ Y on the tensor cores; only the P part of C = M Y in FP64
-    s->ytilde = true;
-    return pw_rr_finish_tall(&s->dws, ns, nb, s->A, ldg, s->Mx, ldg, s->theta, s->C, ldg, s->st);
-  }
-  return pw_rr_finish(&s->dws, ns, nb, s->A, ldg, s->Mx, ldg, s->theta, s->C, ldg, s->st);
+  // X' = S~ Y (and H X' = H S~ Y) on the tensor cores; only the P part of
+  // C = M Y in FP64
+  s->ytilde = true;
+  return pw_rr_finish_tall(&s->dws, ns, nb, s->A, ldg, s->Mx, ldg, s->theta, s->C, ldg, s->st);
 }
 
 // Rayleigh-Ritz on the first ns columns of (S, HS) -> theta, C (ns x nb, ld 3nb).
@@ -334,18 +346,13 @@ pw_status subspace_rr(pw_solver *s, int ns, int *chol_ok) {
                           piv_tol(s));
 }
 
-__global__ void k_zero_top_rows(const double2 *C, int ld, int nrows_zero, int nrows, int ncols,
-                                double2 *out) {
-  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (idx >= (long)nrows * ncols) return;
-  const int t = (int)(idx % nrows), j = (int)(idx / nrows);
-  out[t + (long)j * ld] = t < nrows_zero ? make_double2(0.0, 0.0) : C[t + (long)j * ld];
-}
-
 // after a rotation the new block becomes S (and HS): X' sits in S2 (H X' in
 // HS2), or, after the tensor-core S~ Y rotation, in HS2
 void swap_rotated(pw_solver *s) {
-  if (s->x_in_hs2) {
+  if (s->xh_swapped) {
+    std::swap(s->S, s->HS);
+    s->xh_swapped = false;
+  } else if (s->x_in_hs2) {
     std::swap(s->S, s->HS2);
     s->x_in_hs2 = false;
   } else {
@@ -368,30 +375,25 @@ pw_status rotate(pw_solver *s, int ns, bool with_p) {
       PW_TRY(pw_tc_split_coef(s->C, n3, ns, nb, nullptr, &s->opCP, s->st));
       PW_TRY(tall_times_coef(s, s->S, ns, &s->opST, s->st_split_valid, &s->opCP, 2 * nb, s->P,
                              (2 * nb) / 64, 0));
+      // carried H blocks: H P' = H S C_P (opHST may still hold the split of H S)
+      if (!s->fresh_h)
+        PW_TRY(tall_times_coef(s, s->HS, ns, &s->opHST, s->hst_split_valid, &s->opCP, 2 * nb, s->HP,
+                               (2 * nb) / 64, 0));
+    }
+    PW_TRY(pw_tc_split_coef(s->dws.Y, ns, ns, nb, nullptr, &s->opC, s->st));
+    s->st_split_valid = false;
+    s->hst_split_valid = false;
+    if (!s->fresh_h) {
+      // X' = S~ Y into HS and H X' = H S~ Y into S (both consumed above); the
+      // swap that follows makes them the new S and H S
+      PW_TRY(tall_times_coef(s, s->S2, ns, &s->opST, false, &s->opC, 2 * nb, s->HS, 0, 0));
+      PW_TRY(tall_times_coef(s, s->HS2, ns, &s->opHST, false, &s->opC, 2 * nb, s->S, 0, 0));
+      s->xh_swapped = true;
+      return PW_OK;
     }
     // X' = S~ Y into HS2 (H S~ is no longer needed)
-    PW_TRY(pw_tc_split_coef(s->dws.Y, ns, ns, nb, nullptr, &s->opC, s->st));
     PW_TRY(tall_times_coef(s, s->S2, ns, &s->opST, false, &s->opC, 2 * nb, s->HS2, 0, 0));
-    s->st_split_valid = false;
     s->x_in_hs2 = true;
-    return PW_OK;
-  }
-  if (s->precision == PW_MIXED) {
-    PW_TRY(pw_tc_operand_alloc(&s->opC, 2 * nb, 2 * ns, s->st));
-    PW_TRY(pw_tc_split_coef(s->C, n3, ns, nb, nullptr, &s->opC, s->st));
-    const pw_tc_operand *cp = nullptr;
-    if (with_p) {
-      pw_count_launch();
-      k_zero_top_rows<<<(unsigned)(((long)ns * nb + 255) / 256), 256, 0, s->st>>>(s->C, n3, nb, ns, nb, s->Cz);
-      PW_TRY(pw_check_launch("zero_top_rows"));
-      PW_TRY(pw_tc_operand_alloc(&s->opCP, 2 * nb, 2 * ns, s->st));
-      PW_TRY(pw_tc_split_coef(s->Cz, n3, ns, nb, nullptr, &s->opCP, s->st));
-      cp = &s->opCP;
-    }
-    const bool pre = s->st_split_valid && s->opST.kpad == pw_tc_kpad(2 * ns);
-    PW_TRY(tall_times_coef(s, s->S, ns, &s->opST, pre, &s->opC, 2 * nb, s->S2, 0, 0, cp, s->P));
-    if (!s->fresh_h)
-      PW_TRY(tall_times_coef(s, s->HS, ns, &s->opHST, false, &s->opC, 2 * nb, s->HS2, 0, 0, cp, s->HP));
     return PW_OK;
   }
   if (with_p && ns > nb) {
@@ -466,7 +468,6 @@ extern "C" void pw_solver_destroy(pw_solver *s) {
   for (pw_tc_operand *o : ops) pw_tc_operand_free(o);
   if (s->rmax) cudaFree(s->rmax);
   if (s->d_err) cudaFree(s->d_err);
-  if (s->Cz) cudaFree(s->Cz);
   pw_dense_free(&s->dws);
   pw_oz_free(&s->oz);
   delete s;
@@ -477,7 +478,8 @@ extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, voi
   if (!out) return PW_ERR_ARG;
   *out = nullptr;
   if (!cell || !o || o->nbands < 1 || 3 * o->nbands > cell->npw || !(o->tol >= 0.0) ||
-      (o->precision != PW_FP64 && o->precision != PW_MIXED) || o->chunk_rows < 0)
+      (o->precision != PW_FP64 && o->precision != PW_MIXED) || o->chunk_rows < 0 || o->h_blocks < 0 ||
+      o->h_blocks > 2)
     return PW_ERR_ARG;
   pw_solver *s = new pw_solver();
   s->cell = cell;
@@ -486,7 +488,9 @@ extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, voi
   s->tol = o->tol;
   s->maxit = o->maxit;
   s->precision = o->precision;
-  s->fresh_h = o->precision == PW_MIXED;
+  s->h_blocks = o->h_blocks;
+  // mixed: carried H blocks from the start in modes 1 and 2
+  s->fresh_h = o->precision == PW_MIXED && o->h_blocks == 0;
   s->chunk_rows = o->chunk_rows;
   s->st = (cudaStream_t)stream;
   const int nb = s->nb, npw = s->npw, n3 = 3 * nb;
@@ -503,7 +507,7 @@ extern "C" pw_status pw_solver_create(pw_cell *cell, const pw_solve_opts *o, voi
       (r = alloc((void **)&s->stats, 3 * (size_t)nb * 8, &acc)) ||
       (r = alloc((void **)&s->act, nb * 4, &acc)) || (r = alloc((void **)&s->rmax, (size_t)npw * 4, &acc)) ||
       (r = alloc((void **)&s->d_err, 16, &acc)) ||
-      (r = alloc((void **)&s->Cz, (size_t)n3 * nb * 16, &acc)) || (r = pw_dense_alloc(&s->dws, n3, nb))) {
+      (r = pw_dense_alloc(&s->dws, n3, nb))) {
     pw_solver_destroy(s);
     return r;
   }
@@ -551,11 +555,24 @@ extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_repor
   const int nb = s->nb, npw = s->npw, n3 = 3 * nb;
   std::vector<double> st_h;
   PW_TRY(refresh_stats(s, st_h));
+  if (s->precision == PW_MIXED && s->h_blocks == 1 && !s->fresh_h) {
+    double r0 = 0.0;
+    for (int j = 0; j < nb; ++j) r0 = fmax(r0, s->resid_h[j]);
+    if (r0 <= kCarryTol) {
+      // from here on H is applied afresh each step (and once now to X)
+      s->fresh_h = true;
+      s->hx_valid = false;
+      PW_TRY(refresh_stats(s, st_h));
+    }
+  }
   double rmax = 0.0;
   std::vector<int> act;
   for (int j = 0; j < nb; ++j) {
     rmax = fmax(rmax, s->resid_h[j]);
-    s->active[j] = s->active[j] && (s->resid_h[j] > s->tol);
+    // carried H X gives residual norms only to the split products' error
+    // (~1e-4): no band locks on them; locking starts with fresh H
+    const bool carried = s->precision == PW_MIXED && !s->fresh_h;
+    s->active[j] = s->active[j] && (carried || s->resid_h[j] > s->tol);
     if (s->active[j]) act.push_back(j);
   }
   const int k = (int)act.size();
@@ -609,6 +626,26 @@ extern "C" pw_status pw_subspace_step(pw_cell *cell, pw_solver *s, pw_step_repor
     } else {
       PW_TRY(pw_rayleigh_ritz(&s->dws, ns, nb, s->G, n3, s->A, n3, s->theta, s->C, n3, &ok, s->st,
                               piv_tol(s)));
+    }
+  }
+  if (!ok && s->precision == PW_MIXED && !s->fresh_h) {
+    // the pencil broke down with carried H blocks: apply H afresh to X (and
+    // P) and take the step again, H applied every step from now on
+    s->fresh_h = true;
+    PW_TRY(solver_apply_H(s, s->S, s->HS, nb));
+    hp_applied = 0;
+    ns = nb + k;
+    dropped = 0;
+    if (s->haveP) {
+      PW_TRY(solver_apply_H(s, s->S + (size_t)(nb + k) * npw, s->HS + (size_t)(nb + k) * npw, k));
+      hp_applied = 1;
+      ns = nb + 2 * k;
+    }
+    PW_TRY(subspace_rr(s, ns, &ok));
+    if (!ok && s->haveP) {
+      ns = nb + k;
+      dropped = 1;
+      PW_TRY(rr_mixed_from_gram(s, ns, &ok));
     }
   }
   if (!ok) return PW_ERR_CHOL;

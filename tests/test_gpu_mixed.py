@@ -180,3 +180,48 @@ def test_mixed_steps_si512_full_size_sampled():
         assert abs(r - resid[j]) < 1e-5 * max(1.0, r), (j, r, resid[j])
     g = xs.conj().T @ xs
     assert np.abs(g - np.eye(len(cols))).max() < 1e-5
+
+
+def test_mixed_h_blocks_carried_then_fresh_si64():
+    # H X and H P carried through the split-precision rotations hold the
+    # split products' error: carried all the way (h_blocks 2) the residual
+    # stalls near 1e-4 and the eigenvalues stay far above 1e-6 Ha off; carried
+    # only while the residual is above 1e-3 and applied afresh after that (1)
+    # the solve reaches 5e-6 and the FP64 eigenvalues to 1e-6 Ha, as applying
+    # H to [X W P] every step (0, the default) does
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 2, 10.0, precision="mixed")
+    nb = 144
+    x0 = synth.draw_x0(0, 64, orc.npw, nb)
+    ref, _, _ = pw.pw_eigsolve(lib.h, nb, tol=1e-9, maxit=400, x0=x0, precision="fp64")
+    s = pw.pw_solver_create(lib.h, nb, tol=0.0, x0=x0, precision="mixed", h_blocks=2)
+    floor = np.inf
+    for _ in range(100):
+        pw.pw_subspace_step(lib.h, s)
+        e, r = pw.pw_solver_eigs(s, nb)
+        floor = min(floor, r.max())
+    pw.pw_solver_destroy(s)
+    assert floor > 3e-5
+    assert np.abs(e - ref).max() > 1e-6
+    for hb in (0, 1):
+        e, rep, st = pw.pw_eigsolve(lib.h, nb, tol=5e-6, maxit=400, x0=x0, precision="mixed", h_blocks=hb)
+        assert st == 0 and rep.max_resid <= 5e-6
+        assert np.abs(e - ref).max() <= 1e-6
+
+
+def test_mixed_step_reports_h_columns():
+    # far from convergence mode 1 applies H once per step, to W; the default
+    # applies it to X, W and P
+    import paper_2406_10765_gb300 as pw
+    lib, orc, _ = cells("Si", 1, 10.0, precision="mixed")
+    nb = 24
+    s = pw.pw_solver_create(lib.h, nb, tol=0.0, seed=1, precision="mixed", h_blocks=1)
+    rep = pw.pw_subspace_step(lib.h, s)
+    rep = pw.pw_subspace_step(lib.h, s)
+    assert rep.max_resid > 1e-3 and rep.hpsi_cols == rep.nactive
+    pw.pw_solver_destroy(s)
+    s = pw.pw_solver_create(lib.h, nb, tol=0.0, seed=1, precision="mixed")
+    pw.pw_subspace_step(lib.h, s)
+    rep = pw.pw_subspace_step(lib.h, s)
+    assert rep.hpsi_cols == nb + 2 * rep.nactive
+    pw.pw_solver_destroy(s)
