@@ -278,7 +278,18 @@ typedef struct {
                            plan (pw_cell_autotune_fft on its bands) and later
                            requests of that grid reuse it; the tensor-core K
                            splits follow pw_autotune_gemm's process-wide mode */
+  int batch_fft;        /* PW_MIXED, 1: the FFT local parts of H psi of the
+                           requests running at once that share a grid size and
+                           plan run in one launch per kernel (up to 16 cells'
+                           band blocks, uneven band counts and spheres); a
+                           request waits at most batch_window_us for partners.
+                           Results are the same as unbatched. */
+  double batch_window_us;  /* 0 -> 100 */
 } pw_serve_opts;
+
+/* Launches of the cross-request FFT batching of pw_serve in this process and
+ * the band blocks (one per request per launch) they carried. */
+void pw_fft_batch_stats(uint64_t *launches, uint64_t *jobs);
 
 /* Device-memory footprint model used to admit a request (bytes). */
 size_t pw_request_footprint(const pw_request *req, int precision);

@@ -71,7 +71,8 @@ class pw_result(ct.Structure):
 
 class pw_serve_opts(ct.Structure):
     _fields_ = [("max_slots", ct.c_int), ("hbm_budget", ct.c_size_t), ("precision", ct.c_int),
-                ("time_scale", ct.c_double), ("autotune", ct.c_int)]
+                ("time_scale", ct.c_double), ("autotune", ct.c_int), ("batch_fft", ct.c_int),
+                ("batch_window_us", ct.c_double)]
 
 
 class pw_solve_report(ct.Structure):
@@ -218,7 +219,18 @@ def pw_request_footprint(r, precision="fp64"):
     return int(_footprint(ct.byref(_mkreq(r)), _PREC[precision]))
 
 
-def pw_serve(requests, max_slots=4, hbm_budget=0, precision="fp64", time_scale=1.0, autotune=False):
+_batch_stats = _sig("pw_fft_batch_stats", None, [ct.POINTER(ct.c_uint64), ct.POINTER(ct.c_uint64)])
+
+
+def pw_fft_batch_stats():
+    """(launches, band blocks) of the serving loop's cross-request FFT launches so far."""
+    a, b = ct.c_uint64(), ct.c_uint64()
+    _batch_stats(ct.byref(a), ct.byref(b))
+    return a.value, b.value
+
+
+def pw_serve(requests, max_slots=4, hbm_budget=0, precision="fp64", time_scale=1.0, autotune=False,
+             batch_fft=True, batch_window_us=0.0):
     """Serve a list of request dicts (species, n, ecut, nbands, seed, t_arrival[, tol, maxit]).
     Returns a list of dicts with eig (numpy), status, iters, timings."""
     n = len(requests)
@@ -231,6 +243,8 @@ def pw_serve(requests, max_slots=4, hbm_budget=0, precision="fp64", time_scale=1
     o.max_slots, o.hbm_budget, o.precision, o.time_scale = int(max_slots), int(hbm_budget), \
         _PREC[precision], float(time_scale)
     o.autotune = 1 if autotune else 0
+    o.batch_fft = 1 if batch_fft else 0
+    o.batch_window_us = float(batch_window_us)
     _check(_serve(ct.byref(o), reqs, n, res), "pw_serve")
     out = []
     for i in range(n):

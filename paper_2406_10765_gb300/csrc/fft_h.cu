@@ -353,9 +353,12 @@ __global__ void __launch_bounds__(256) k_grid_fft_axis(double2 *__restrict__ g, 
   }
 }
 
+// shared-memory opt-in for a kernel whose launches need `bytes`: set to the
+// largest size, so threads launching it for different grids never lower it
+// under each other
 template <typename K> static pw_status allow_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024)
-    PW_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    PW_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   return PW_OK;
 }
 
@@ -384,6 +387,12 @@ pw_status apply_local_t(pw_cell *c, const double2 *psi, int ld, int nb, double2 
   const double scale = 1.0 / ((double)Nx * Ny * Nz);
   for (int b0 = 0; b0 < nb; b0 += batch) {
     const int nbb = std::min(batch, nb - b0);
+    if (reg && c->fft_hook) {
+      // serving: this batch of bands joins a launch shared with other cells
+      const pw_fft_job job{c, psi + (long)b0 * ld, hpsi + (long)b0 * ld, ld, nbb, Z, scale};
+      PW_TRY(c->fft_hook(c->fft_hook_ctx, job, reg, fp32, cp, st));
+      continue;
+    }
     if (reg) {
       PW_TRY((fp32 ? reg->run32[cp] : reg->run64[cp])(c, psi + (long)b0 * ld, ld, nbb, hpsi + (long)b0 * ld, Z,
                                                       scale, st));

@@ -22,6 +22,10 @@
 // fft_reg_*.cu instantiates the kernels of a few plans, so the translation
 // units compile in parallel.
 #pragma once
+#include <string.h>
+
+#include <algorithm>
+
 #include "pw_internal.cuh"
 
 namespace {
@@ -191,19 +195,17 @@ __device__ __forceinline__ void fft_lines_reg(C *buf, int nlines, int ls, int es
 }
 
 // ---------------------------------------------------------------- K1 ----
+// z-columns bx*ZCB.. of one band: scatter the sphere into the z-lines,
+// inverse FFT along z, store the z-pencils Zb[z][column]
 template <typename C, int L, int R>
-__global__ void __launch_bounds__(ZTHREADS) k_sphere_to_z_reg(const double2 *__restrict__ psi, int ld,
-                                                              const int *__restrict__ colstart,
-                                                              const int *__restrict__ gcol,
-                                                              const int *__restrict__ gz, int ncol,
-                                                              const C *__restrict__ twz,
-                                                              C *__restrict__ Z) {
+__device__ __forceinline__ void sphere_to_z_body(int bx, const double2 *__restrict__ p,
+                                                 const int *__restrict__ colstart, const int *__restrict__ gcol,
+                                                 const int *__restrict__ gz, int ncol, const C *__restrict__ twz,
+                                                 C *__restrict__ Zb) {
   constexpr int Nz = L * R, ls = Nz + 1;
   __shared__ C lines[ZCB * ls];
-  const int c0 = blockIdx.x * ZCB;
+  const int c0 = bx * ZCB;
   const int nc = min(ZCB, ncol - c0);
-  const int b = blockIdx.y;
-  const double2 *p = psi + (long)b * ld;
   LineTw<C, L, R> t;
   t.init(twz, (threadIdx.x & 31) % L);
   for (int i = threadIdx.x; i < nc * ls; i += blockDim.x) lines[i] = czero_r<C>();
@@ -214,11 +216,22 @@ __global__ void __launch_bounds__(ZTHREADS) k_sphere_to_z_reg(const double2 *__r
   __syncthreads();
   fft_lines_reg<C, L, R>(lines, nc, ls, 1, twz, t, true);
   __syncthreads();
-  C *Zb = Z + (long)b * Nz * ncol;
   for (int i = threadIdx.x; i < nc * Nz; i += blockDim.x) {
     const int z = i / nc, cl = i % nc;
     Zb[(long)z * ncol + c0 + cl] = lines[cl * ls + z];
   }
+}
+
+template <typename C, int L, int R>
+__global__ void __launch_bounds__(ZTHREADS) k_sphere_to_z_reg(const double2 *__restrict__ psi, int ld,
+                                                              const int *__restrict__ colstart,
+                                                              const int *__restrict__ gcol,
+                                                              const int *__restrict__ gz, int ncol,
+                                                              const C *__restrict__ twz,
+                                                              C *__restrict__ Z) {
+  const int b = blockIdx.y;
+  sphere_to_z_body<C, L, R>(blockIdx.x, psi + (long)b * ld, colstart, gcol, gz, ncol, twz,
+                            Z + (long)b * (L * R) * ncol);
 }
 
 // ---------------------------------------------------------------- K2 ----
@@ -237,15 +250,12 @@ __host__ __device__ inline size_t plane_smem_bytes(int mxmax, bool cp, int nthre
   return ((size_t)N * compact_stride(mxmax) + (size_t)(nthreads / 32) * (32 / L) * N) * sizeof(C);
 }
 
+// plane z of one band: its z-pencils Zp[column] through the y and x
+// transforms, V(r), and back (P: the block's dynamic shared memory)
 template <typename C, typename T, int L, int R, bool CP>
-__global__ void __launch_bounds__(RegPlaneThreads<C, R>::value) k_plane_reg(C *__restrict__ Z, int ncol,
-                                                                         const int *__restrict__ colxy,
-                                                                         int mxmax, const C *__restrict__ twx,
-                                                                         int Nz, const T *__restrict__ V) {
+__device__ __forceinline__ void plane_body(C *P, int z, C *__restrict__ Zp, int ncol, const int *__restrict__ colxy,
+                                           int mxmax, const C *__restrict__ twx, const T *__restrict__ V) {
   constexpr int N = L * R, G = 32 / L;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C *P = reinterpret_cast<C *>(smem_raw);
-  const int z = blockIdx.x, b = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int gid = lane / L, l = lane % L;
   const int nxe = 2 * mxmax + 1;
@@ -257,7 +267,6 @@ __global__ void __launch_bounds__(RegPlaneThreads<C, R>::value) k_plane_reg(C *_
   C *rowbuf = P + (long)N * ps + (long)(warp * G + gid) * N;   // compact only
   LineTw<C, L, R> t;
   t.init(twx, l);
-  C *Zp = Z + ((long)b * Nz + z) * ncol;
   for (int i = threadIdx.x; i < N * ps; i += blockDim.x) P[i] = czero_r<C>();
   __syncthreads();
   for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
@@ -344,7 +353,48 @@ __global__ void __launch_bounds__(RegPlaneThreads<C, R>::value) k_plane_reg(C *_
   }
 }
 
+template <typename C, typename T, int L, int R, bool CP>
+__global__ void __launch_bounds__(RegPlaneThreads<C, R>::value) k_plane_reg(C *__restrict__ Z, int ncol,
+                                                                         const int *__restrict__ colxy,
+                                                                         int mxmax, const C *__restrict__ twx,
+                                                                         int Nz, const T *__restrict__ V) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int z = blockIdx.x, b = blockIdx.y;
+  plane_body<C, T, L, R, CP>(reinterpret_cast<C *>(smem_raw), z, Z + ((long)b * Nz + z) * ncol, ncol, colxy,
+                             mxmax, twx, V);
+}
+
 // ---------------------------------------------------------------- K3 ----
+// z-columns bx*ZCB.. of one band: forward FFT along z, gather onto the
+// sphere, hpsi = kin psi + scale (V psi)
+template <typename C, int L, int R>
+__device__ __forceinline__ void z_to_sphere_body(int bx, const C *__restrict__ Zb, int ncol,
+                                                 const C *__restrict__ twz, const int *__restrict__ colstart,
+                                                 const int *__restrict__ gcol, const int *__restrict__ gz,
+                                                 const double *__restrict__ kin, const double2 *__restrict__ p,
+                                                 double2 *__restrict__ h, double scale) {
+  constexpr int Nz = L * R, ls = Nz + 1;
+  __shared__ C lines[ZCB * ls];
+  const int c0 = bx * ZCB;
+  const int nc = min(ZCB, ncol - c0);
+  LineTw<C, L, R> t;
+  t.init(twz, (threadIdx.x & 31) % L);
+  for (int i = threadIdx.x; i < nc * Nz; i += blockDim.x) {
+    const int z = i / nc, cl = i % nc;
+    lines[cl * ls + z] = Zb[(long)z * ncol + c0 + cl];
+  }
+  __syncthreads();
+  fft_lines_reg<C, L, R>(lines, nc, ls, 1, twz, t, false);
+  __syncthreads();
+  const int g0 = colstart[c0], g1 = colstart[c0 + nc];
+  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+    const C v = lines[(gcol[g] - c0) * ls + gz[g]];
+    const double k = kin[g];
+    const double2 x = p[g];
+    h[g] = make_double2(k * x.x + scale * (double)v.x, k * x.y + scale * (double)v.y);
+  }
+}
+
 template <typename C, int L, int R>
 __global__ void __launch_bounds__(ZTHREADS) k_z_to_sphere_reg(const C *__restrict__ Z, int ncol,
                                                               const C *__restrict__ twz,
@@ -354,30 +404,62 @@ __global__ void __launch_bounds__(ZTHREADS) k_z_to_sphere_reg(const C *__restric
                                                               const double *__restrict__ kin,
                                                               const double2 *__restrict__ psi, int ld,
                                                               double2 *__restrict__ hpsi, double scale) {
-  constexpr int Nz = L * R, ls = Nz + 1;
-  __shared__ C lines[ZCB * ls];
-  const int c0 = blockIdx.x * ZCB;
-  const int nc = min(ZCB, ncol - c0);
   const int b = blockIdx.y;
-  LineTw<C, L, R> t;
-  t.init(twz, (threadIdx.x & 31) % L);
-  const C *Zb = Z + (long)b * Nz * ncol;
-  for (int i = threadIdx.x; i < nc * Nz; i += blockDim.x) {
-    const int z = i / nc, cl = i % nc;
-    lines[cl * ls + z] = Zb[(long)z * ncol + c0 + cl];
-  }
-  __syncthreads();
-  fft_lines_reg<C, L, R>(lines, nc, ls, 1, twz, t, false);
-  __syncthreads();
-  const int g0 = colstart[c0], g1 = colstart[c0 + nc];
-  const double2 *p = psi + (long)b * ld;
-  double2 *h = hpsi + (long)b * ld;
-  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
-    const C v = lines[(gcol[g] - c0) * ls + gz[g]];
-    const double k = kin[g];
-    const double2 x = p[g];
-    h[g] = make_double2(k * x.x + scale * (double)v.x, k * x.y + scale * (double)v.y);
-  }
+  z_to_sphere_body<C, L, R>(blockIdx.x, Z + (long)b * (L * R) * ncol, ncol, twz, colstart, gcol, gz, kin,
+                            psi + (long)b * ld, hpsi + (long)b * ld, scale);
+}
+
+// ------------------------------------------------- several cells at once ----
+// The local part of H psi for bands of several cells (requests) that share
+// the grid size and plan, in one launch per kernel: blockIdx.y runs over the
+// bands of all cells, each block finds its cell in the job table (passed by
+// value) and runs the same body as the one-cell kernels, so every band's
+// arithmetic is that of the one-cell launch.
+template <typename C, typename T> struct RegJob {
+  const double2 *psi;
+  double2 *hpsi;
+  C *Z;
+  const T *V;
+  const double *kin;
+  const int *colstart, *gcol, *gz, *colxy;
+  const C *twz, *twx;
+  int ld, nb, b0, ncol, mxmax, pad;
+  double scale;
+};
+template <typename C, typename T> struct RegJobs {
+  int n, pad;
+  RegJob<C, T> j[PW_FFT_BATCH_MAX];
+};
+template <typename C, typename T>
+__device__ __forceinline__ int job_of(const RegJobs<C, T> &J, int band) {
+  int j = 0;
+  while (j + 1 < J.n && band >= J.j[j + 1].b0) ++j;
+  return j;
+}
+
+template <typename C, typename T, int L, int R>
+__global__ void __launch_bounds__(ZTHREADS) k_sphere_to_z_multi(const __grid_constant__ RegJobs<C, T> J) {
+  const RegJob<C, T> &q = J.j[job_of(J, blockIdx.y)];
+  if ((int)blockIdx.x * ZCB >= q.ncol) return;
+  const int b = blockIdx.y - q.b0;
+  sphere_to_z_body<C, L, R>(blockIdx.x, q.psi + (long)b * q.ld, q.colstart, q.gcol, q.gz, q.ncol, q.twz,
+                            q.Z + (long)b * (L * R) * q.ncol);
+}
+template <typename C, typename T, int L, int R, bool CP>
+__global__ void __launch_bounds__(RegPlaneThreads<C, R>::value) k_plane_multi(const __grid_constant__ RegJobs<C, T> J) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const RegJob<C, T> &q = J.j[job_of(J, blockIdx.y)];
+  const int z = blockIdx.x, b = blockIdx.y - q.b0;
+  plane_body<C, T, L, R, CP>(reinterpret_cast<C *>(smem_raw), z, q.Z + ((long)b * (L * R) + z) * q.ncol, q.ncol,
+                             q.colxy, q.mxmax, q.twx, q.V);
+}
+template <typename C, typename T, int L, int R>
+__global__ void __launch_bounds__(ZTHREADS) k_z_to_sphere_multi(const __grid_constant__ RegJobs<C, T> J) {
+  const RegJob<C, T> &q = J.j[job_of(J, blockIdx.y)];
+  if ((int)blockIdx.x * ZCB >= q.ncol) return;
+  const int b = blockIdx.y - q.b0;
+  z_to_sphere_body<C, L, R>(blockIdx.x, q.Z + (long)b * (L * R) * q.ncol, q.ncol, q.twz, q.colstart, q.gcol,
+                            q.gz, q.kin, q.psi + (long)b * q.ld, q.hpsi + (long)b * q.ld, q.scale);
 }
 
 template <typename C> __host__ __device__ inline const C *twtab(const pw_fft_axis &a);
@@ -391,9 +473,11 @@ pw_status run_batch(pw_cell *c, const double2 *psi, int ld, int nbb, double2 *hp
   if (2 * c->mxmax + 1 > N) return PW_ERR_ARG;
   const size_t plane_bytes = plane_smem_bytes<C, L, R>(c->mxmax, CP, RegPlaneThreads<C, R>::value);
   if (plane_bytes > 227 * 1024) return PW_ERR_ARG;
+  // the opt-in is set to the largest size (threads launching this plan for
+  // cells of different sphere extents then never lower it under each other)
   if (plane_bytes > 48 * 1024)
     PW_CUDA(cudaFuncSetAttribute(k_plane_reg<C, T, L, R, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)plane_bytes));
+                                 227 * 1024));
   const dim3 gcols((c->ncol + ZCB - 1) / ZCB, nbb);
   pw_count_launch();
   k_sphere_to_z_reg<C, L, R><<<gcols, ZTHREADS, 0, st>>>(psi, ld, c->d_colstart, c->d_gcol, c->d_gz,
@@ -500,7 +584,7 @@ pw_status density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, C *Z, c
   if (plane_bytes > 227 * 1024) return PW_ERR_ARG;
   if (plane_bytes > 48 * 1024)
     PW_CUDA(cudaFuncSetAttribute(k_density_reg<C, L, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)plane_bytes));
+                                 227 * 1024));
   const dim3 gcols((c->ncol + ZCB - 1) / ZCB, nbb);
   pw_count_launch();
   k_sphere_to_z_reg<C, L, R><<<gcols, ZTHREADS, 0, st>>>(psi, ld, c->d_colstart, c->d_gcol, c->d_gz,
@@ -509,6 +593,63 @@ pw_status density_batch(pw_cell *c, const double2 *psi, int ld, int nbb, C *Z, c
   k_density_reg<C, L, R><<<dim3(N, ngroups), RegPlaneThreads<C, R>::value, plane_bytes, st>>>(
       Z, c->ncol, c->d_colxy, c->mxmax, twtab<C>(c->ax[0]), nbb, occ, part);
   return pw_check_launch("density (register FFT)");
+}
+
+// several cells' bands in one launch per kernel (the cells share this plan)
+template <typename C, typename T, int L, int R, bool CP>
+pw_status run_multi(const pw_fft_job *jobs, int n, cudaStream_t st) {
+  constexpr int N = L * R;
+  if (n < 1 || n > PW_FFT_BATCH_MAX) return PW_ERR_ARG;
+  RegJobs<C, T> J;
+  memset(&J, 0, sizeof J);
+  J.n = n;
+  int bands = 0, colblocks = 0;
+  size_t plane_bytes = 0;
+  for (int i = 0; i < n; ++i) {
+    pw_cell *c = jobs[i].c;
+    if (c->N[0] != N || c->N[1] != N || c->N[2] != N || 2 * c->mxmax + 1 > N) return PW_ERR_ARG;
+    RegJob<C, T> &q = J.j[i];
+    q.psi = jobs[i].psi;
+    q.hpsi = jobs[i].hpsi;
+    q.Z = (C *)jobs[i].Z;
+    q.V = (const T *)(sizeof(C) == sizeof(float2) ? (const void *)c->d_Vf : (const void *)c->d_V);
+    q.kin = c->d_kin;
+    q.colstart = c->d_colstart;
+    q.gcol = c->d_gcol;
+    q.gz = c->d_gz;
+    q.colxy = c->d_colxy;
+    q.twz = twtab<C>(c->ax[2]);
+    q.twx = twtab<C>(c->ax[0]);
+    q.ld = jobs[i].ld;
+    q.nb = jobs[i].nb;
+    q.b0 = bands;
+    q.ncol = c->ncol;
+    q.mxmax = c->mxmax;
+    q.scale = jobs[i].scale;
+    bands += jobs[i].nb;
+    colblocks = std::max(colblocks, (c->ncol + ZCB - 1) / ZCB);
+    plane_bytes = std::max(plane_bytes, plane_smem_bytes<C, L, R>(c->mxmax, CP, RegPlaneThreads<C, R>::value));
+  }
+  if (plane_bytes > 227 * 1024) return PW_ERR_ARG;
+  if (plane_bytes > 48 * 1024)
+    PW_CUDA(cudaFuncSetAttribute(k_plane_multi<C, T, L, R, CP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 227 * 1024));
+  pw_count_launch();
+  k_sphere_to_z_multi<C, T, L, R><<<dim3(colblocks, bands), ZTHREADS, 0, st>>>(J);
+  pw_count_launch();
+  k_plane_multi<C, T, L, R, CP><<<dim3(N, bands), RegPlaneThreads<C, R>::value, plane_bytes, st>>>(J);
+  pw_count_launch();
+  k_z_to_sphere_multi<C, T, L, R><<<dim3(colblocks, bands), ZTHREADS, 0, st>>>(J);
+  return pw_check_launch("local part of several cells (register FFT)");
+}
+
+template <int L, int R, bool CP>
+pw_status reg_multi64(const pw_fft_job *jobs, int n, cudaStream_t st) {
+  return run_multi<double2, double, L, R, CP>(jobs, n, st);
+}
+template <int L, int R, bool CP>
+pw_status reg_multi32(const pw_fft_job *jobs, int n, cudaStream_t st) {
+  return run_multi<float2, float, L, R, CP>(jobs, n, st);
 }
 
 // entry points of one plan, as stored in the plan tables
@@ -544,4 +685,5 @@ pw_status reg_dens32(pw_cell *c, const double2 *psi, int ld, int nbb, void *Z, c
 #define PW_REG_PLAN(LL, RR)                                                                           \
   { (LL) * (RR), LL, RR, {reg_run64<LL, RR, false>, reg_run64<LL, RR, true>},                          \
     {reg_run32<LL, RR, false>, reg_run32<LL, RR, true>}, reg_dens64<LL, RR>, reg_dens32<LL, RR>,         \
-    reg_smem<LL, RR> }
+    reg_smem<LL, RR>, {reg_multi64<LL, RR, false>, reg_multi64<LL, RR, true>},                           \
+    {reg_multi32<LL, RR, false>, reg_multi32<LL, RR, true>} }

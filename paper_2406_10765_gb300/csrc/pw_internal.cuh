@@ -63,6 +63,18 @@ struct pw_fft_axis {
   float2 *tw32;
 };
 
+struct pw_cell;
+// Bands of one cell for a launch that covers several cells (fft_reg.cuh
+// run_multi): the cell, its bands psi / hpsi (ld), its z-pencil buffer.
+#define PW_FFT_BATCH_MAX 16
+struct pw_fft_job {
+  pw_cell *c;
+  const double2 *psi;
+  double2 *hpsi;
+  int ld, nb;
+  void *Z;
+  double scale;
+};
 struct pw_cell {
   int precision;
   double L[3];
@@ -106,6 +118,12 @@ struct pw_cell {
   double2 *d_B = nullptr; size_t B_elems = 0;   // nproj x nb projections
   double2 *d_gemm_ws = nullptr; size_t gemm_ws_elems = 0;
   struct pw_oz_ws *oz = nullptr;   // FP64-accurate tensor-core products (FP64 projector terms)
+  // set by the serving loop: the local part of H psi goes to a launch shared
+  // with other requests' cells (register plans only); returns once that
+  // launch is ordered on `st`
+  pw_status (*fft_hook)(void *ctx, const pw_fft_job &job, const struct pw_reg_plan *plan, int fp32, int cp,
+                        cudaStream_t st) = nullptr;
+  void *fft_hook_ctx = nullptr;
   size_t bytes = 0;
   // mixed-precision operands (split FP16), built on first use: beta as rows
   // over G (for beta^H psi) and as rows over projectors (for beta (D B))
@@ -137,6 +155,7 @@ size_t pw_local_zbytes_per_band(const pw_cell *c);
 // sphere's x-columns (1) in shared memory; smem: its shared-memory bytes.
 typedef pw_status (*pw_reg_run_fn)(pw_cell *, const double2 *, int, int, double2 *, void *, double,
                                    cudaStream_t);
+typedef pw_status (*pw_reg_multi_fn)(const pw_fft_job *, int, cudaStream_t);
 struct pw_reg_plan {
   int N, L, R;
   pw_reg_run_fn run64[2], run32[2];
@@ -145,6 +164,7 @@ struct pw_reg_plan {
   pw_status (*dens32)(pw_cell *, const double2 *, int, int, void *, const double *, int, double *,
                       cudaStream_t);
   size_t (*smem)(const pw_cell *, int fp32, int compact);
+  pw_reg_multi_fn multi64[2], multi32[2];
 };
 int pw_reg_plan_count();
 const pw_reg_plan *pw_reg_plan_at(int i);

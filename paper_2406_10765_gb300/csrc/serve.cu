@@ -23,6 +23,7 @@
 #include <map>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "pw_internal.cuh"
@@ -102,6 +103,103 @@ extern "C" size_t pw_request_footprint(const pw_request *r, int precision) {
 
 namespace {
 
+std::atomic<unsigned long long> g_batch_launches{0}, g_batch_jobs{0};
+
+// The local parts of H psi of concurrent requests that share a grid size,
+// FFT plan and precision run in one launch per kernel (fft_reg.cuh
+// run_multi).  A request thread that reaches its FFT becomes the leader for
+// its key if none is gathering: it waits until every request solving with the
+// same key has a job pending, or the window has passed, then launches all
+// pending jobs of the key (at most PW_FFT_BATCH_MAX) on the batch stream,
+// ordered after each job's stream (events) and before its continuation.
+// Other threads wait until their job is done.  Every band's arithmetic is
+// that of the one-cell launch, so results do not depend on the batching.
+struct FftBatcher {
+  typedef std::tuple<const pw_reg_plan *, int, int> Key;
+  struct Job {
+    pw_fft_job job;
+    Key key;
+    cudaStream_t st;
+    bool taken;       // in a leader's launch (no longer pending)
+    bool done;        // that launch is ordered on st; status set
+    pw_status status;
+  };
+  std::mutex mu;
+  std::condition_variable cv;
+  std::vector<Job *> pending;
+  std::map<Key, bool> leading;
+  std::map<Key, int> solving;   // requests solving with this key (expected participants)
+  cudaStream_t bst = nullptr;
+  double window_s = 100e-6;
+
+  int count(const Key &k) const {
+    int n = 0;
+    for (const Job *j : pending) n += j->key == k;
+    return n;
+  }
+  pw_status launch(const std::vector<Job *> &take) {
+    const Job &j0 = *take[0];
+    std::vector<pw_fft_job> jobs;
+    for (const Job *t : take) {
+      cudaEvent_t e;
+      PW_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      PW_CUDA(cudaEventRecord(e, t->st));
+      PW_CUDA(cudaStreamWaitEvent(bst, e, 0));
+      cudaEventDestroy(e);
+      jobs.push_back(t->job);
+    }
+    const pw_reg_plan *plan = std::get<0>(j0.key);
+    const int fp32 = std::get<1>(j0.key), cp = std::get<2>(j0.key);
+    PW_TRY((fp32 ? plan->multi32[cp] : plan->multi64[cp])(jobs.data(), (int)jobs.size(), bst));
+    cudaEvent_t done;
+    PW_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    PW_CUDA(cudaEventRecord(done, bst));
+    for (const Job *t : take) PW_CUDA(cudaStreamWaitEvent(t->st, done, 0));
+    cudaEventDestroy(done);
+    g_batch_launches.fetch_add(1);
+    g_batch_jobs.fetch_add(take.size());
+    return PW_OK;
+  }
+};
+
+pw_status fft_hook(void *ctx, const pw_fft_job &job, const pw_reg_plan *plan, int fp32, int cp, cudaStream_t st) {
+  FftBatcher &B = *(FftBatcher *)ctx;
+  FftBatcher::Job me{job, FftBatcher::Key(plan, fp32, cp), st, false, false, PW_OK};
+  std::unique_lock<std::mutex> lk(B.mu);
+  B.pending.push_back(&me);
+  B.cv.notify_all();
+  for (;;) {
+    if (me.done) return me.status;
+    // a job another leader has taken waits for that launch, whatever the
+    // leader flag says meanwhile
+    if (!me.taken && !B.leading[me.key]) {
+      B.leading[me.key] = true;
+      const int want = std::min(PW_FFT_BATCH_MAX, std::max(1, B.solving[me.key]));
+      const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(B.window_s);
+      B.cv.wait_until(lk, deadline, [&] { return B.count(me.key) >= want; });
+      // this job first, then the others of the key in arrival order
+      std::vector<FftBatcher::Job *> take{&me};
+      for (FftBatcher::Job *j : B.pending)
+        if (j != &me && j->key == me.key && (int)take.size() < PW_FFT_BATCH_MAX) take.push_back(j);
+      for (FftBatcher::Job *t : take) {
+        B.pending.erase(std::find(B.pending.begin(), B.pending.end(), t));
+        t->taken = true;
+      }
+      B.leading[me.key] = false;
+      lk.unlock();
+      const pw_status r = B.launch(take);
+      lk.lock();
+      for (FftBatcher::Job *t : take) {
+        t->status = r;
+        t->done = true;
+      }
+      B.cv.notify_all();
+      continue;
+    }
+    B.cv.wait(lk, [&] { return me.done || (!me.taken && !B.leading[me.key]); });
+  }
+}
+
 struct Job {
   int idx;
 };
@@ -122,6 +220,7 @@ struct Server {
   // L = -1 and later requests use the default plan meanwhile
   std::mutex plan_mu;
   std::map<std::array<int, 3>, pw_fft_plan> plans;
+  FftBatcher batcher;           // used when opts->batch_fft
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
@@ -177,6 +276,17 @@ void run_one(Server &sv, int i, int device) {
       s = pw_cell_set_fft_plan(cell, sv.opts->precision, &p);
     }
   }
+  // the cell's mixed-precision FFTs join launches shared with other requests
+  FftBatcher::Key key(nullptr, 1, 0);
+  const bool batched = s == PW_OK && sv.opts->batch_fft && sv.opts->precision == PW_MIXED &&
+                       pw_reg_plan_at(pw_cell_fft_plan(cell, 1)) != nullptr;
+  if (batched) {
+    key = FftBatcher::Key(pw_reg_plan_at(pw_cell_fft_plan(cell, 1)), 1, pw_cell_fft_compact(cell, 1));
+    cell->fft_hook = fft_hook;
+    cell->fft_hook_ctx = &sv.batcher;
+    std::lock_guard<std::mutex> lk(sv.batcher.mu);
+    sv.batcher.solving[key] += 1;
+  }
   pw_solve_report rep;
   memset(&rep, 0, sizeof rep);
   if (s == PW_OK) {
@@ -193,6 +303,11 @@ void run_one(Server &sv, int i, int device) {
       s = pw_eigsolve(cell, &o, out.eig, nullptr, 0, &rep, st);
     }
   }
+  if (batched) {
+    std::lock_guard<std::mutex> lk(sv.batcher.mu);
+    sv.batcher.solving[key] -= 1;
+    sv.batcher.cv.notify_all();
+  }
   out.iters = rep.iters;
   out.max_resid = rep.max_resid;
   out.orth_err = rep.orth_err;
@@ -204,6 +319,11 @@ void run_one(Server &sv, int i, int device) {
 }
 
 }  // namespace
+
+extern "C" void pw_fft_batch_stats(uint64_t *launches, uint64_t *jobs) {
+  if (launches) *launches = g_batch_launches.load();
+  if (jobs) *jobs = g_batch_jobs.load();
+}
 
 extern "C" pw_status pw_serve(const pw_serve_opts *opts, const pw_request *req, int nreq,
                               pw_result *res) {
@@ -222,6 +342,10 @@ extern "C" pw_status pw_serve(const pw_serve_opts *opts, const pw_request *req, 
   }
   Server sv;
   sv.opts = opts;
+  if (opts->batch_fft) {
+    PW_CUDA(cudaStreamCreateWithFlags(&sv.batcher.bst, cudaStreamNonBlocking));
+    if (opts->batch_window_us > 0) sv.batcher.window_s = opts->batch_window_us * 1e-6;
+  }
   sv.req = req;
   sv.res = res;
   sv.nreq = nreq;
@@ -296,6 +420,10 @@ extern "C" pw_status pw_serve(const pw_serve_opts *opts, const pw_request *req, 
   }
   sv.cv.notify_all();
   for (auto &t : workers) t.join();
+  if (sv.batcher.bst) {
+    cudaStreamSynchronize(sv.batcher.bst);
+    cudaStreamDestroy(sv.batcher.bst);
+  }
   // latencies are measured against the (scaled) arrival time
   for (int i = 0; i < nreq; ++i)
     if (res[i].t_done >= 0 && res[i].status != PW_ERR_BUSY) res[i].latency = res[i].t_done - req[i].t_arrival * scale;

@@ -114,3 +114,23 @@ def test_serve_eight_slots_equals_alone():
         assert m["status"] == 0, m["status"]
         alone = pw.pw_serve([dict(r, t_arrival=0.0)], max_slots=1, precision="mixed")[0]
         assert np.array_equal(alone["eig"], m["eig"])
+
+
+def test_serve_cross_request_fft_batching():
+    # six C-8 requests (all on the 16^3 grid, different Ecut: uneven spheres)
+    # running at once: their FFT local parts share launches (one launch per
+    # kernel carries several requests' band blocks), and every result is
+    # bitwise the same as with each request launching its own kernels
+    import paper_2406_10765_gb300 as pw
+    reqs = [dict(species="C", n=1, ecut=8.0 + 0.7 * i, nbands=18, seed=100 + i, t_arrival=0.0)
+            for i in range(6)]
+    l0, j0 = pw.pw_fft_batch_stats()
+    a = pw.pw_serve(reqs, max_slots=6, precision="mixed", batch_fft=True, batch_window_us=500.0)
+    l1, j1 = pw.pw_fft_batch_stats()
+    b = pw.pw_serve(reqs, max_slots=6, precision="mixed", batch_fft=False)
+    assert pw.pw_fft_batch_stats() == (l1, j1)
+    assert len({x["npw"] for x in a}) > 1
+    for x, y in zip(a, b):
+        assert x["status"] == 0 and y["status"] == 0
+        assert np.array_equal(x["eig"], y["eig"])
+    assert l1 > l0 and (j1 - j0) > (l1 - l0)       # some launches carried several requests
