@@ -41,7 +41,10 @@ DEPS_TARGET = 1e-6                  # |delta eps| of the metric, Ha
 # capture of the same kernels: (stage, n, nb) -> (bytes, summary)
 # DRAM bytes per stage from an ncu capture of the same kernels, when the
 # kernels have not changed since (else traffic is null with a note)
-NCU_TRAFFIC = {}
+# DRAM bytes of the dominant stage per instance, scaled from a one-kernel
+# capture (profiles/householder_phemv_n3456.md: k_phemv at m = 3,255, 16.7 B
+# per lower-triangle entry, times n^3 / 6 entries for the whole reduction)
+NCU_TRAFFIC = {("tridiag", 3456, 1152): 16.73 * 3456 ** 3 / 6}
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of the part (no FP64 tensor path)
 FP32_PEAK_TFLOPS = 80.5     # nominal FP32 rate: 152 SMs x 128 lanes x 2 x 2.07 GHz
 METRIC = "Si-512 eigensolver iters/s"
@@ -272,7 +275,10 @@ def roofline(stage, rr_part, fl, n, nb, precision, fft=None):
     if dom == "tridiag":
         ach = hemv_flops / (t_ms * 1e-3) / 1e12
         roof.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=ach / FP64_PEAK_TFLOPS,
-                    traffic=NCU_TRAFFIC.get(("tridiag", n, nb)), algorithmic_flops=hemv_flops,
+                    traffic=NCU_TRAFFIC.get(("tridiag", n, nb)),
+                    traffic_source="profiles/householder_phemv_n3456.md (k_phemv bytes per entry, scaled "
+                                   "to the n^3/6 entries of the reduction)" if ("tridiag", n, nb) in NCU_TRAFFIC
+                    else None, algorithmic_flops=hemv_flops,
                     peak_source="nominal FP64 rate: 152 SMs x 2.07 GHz x 2 DFMA/clk (measured DFMA 1.20); "
                                 "FP64 work counted: the Hermitian products, 8 n^3 / 3")
     elif dom in ("gram", "rot", "transform") and mixed and tc_peak:

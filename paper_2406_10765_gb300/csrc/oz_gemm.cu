@@ -454,23 +454,38 @@ __global__ void __launch_bounds__(256) k_oz_slice_contig(const double2 *__restri
   }
 }
 
-// row maxima of the strided rows (one thread per row, reads coalesced across rows)
-__global__ void k_oz_rowexp(const double2 *__restrict__ X, int ld, int nrows, int k, int *__restrict__ e) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrows) return;
-  unsigned long long mb = 0;
-  for (int t = 0; t < k; ++t) {
-    const double2 v = X[r + (long)t * ld];
-    mb = max(mb, max(abs_bits(v.x), abs_bits(v.y)));
+// row maxima of the strided rows as ordered bits: block (32 rows, 8 warps)
+// over a 256-long K range, lane = row (reads coalesced across rows), the
+// warps' maxima combined in shared memory, then one atomicMax per row into mx
+// (cleared before)
+constexpr int RX_K = 256;
+__global__ void __launch_bounds__(256) k_oz_rowmax(const double2 *__restrict__ X, int ld, int nrows, int k,
+                                                   unsigned long long *__restrict__ mx) {
+  __shared__ unsigned long long sh[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = blockIdx.x * 32 + lane;
+  const int t0 = blockIdx.y * RX_K, t1 = min(k, t0 + RX_K);
+  unsigned long long m = 0;
+  if (r < nrows)
+    for (int t = t0 + w; t < t1; t += 8) {
+      const double2 v = X[r + (long)t * ld];
+      m = max(m, max(abs_bits(v.x), abs_bits(v.y)));
+    }
+  sh[w][lane] = m;
+  __syncthreads();
+  if (w == 0 && r < nrows) {
+#pragma unroll
+    for (int q = 1; q < 8; ++q) m = max(m, sh[q][lane]);
+    atomicMax(&mx[r], m);
   }
-  e[r] = row_exp(mb);
 }
 
 // strided rows: 32 rows x 64 K tile through shared memory (reads along r,
 // writes along K)
 __global__ void __launch_bounds__(256) k_oz_slice_strided(const double2 *__restrict__ X, int ld, int nrows, int k,
                                                           int conj, int bside, int kpad, int rows_total,
-                                                          const int *__restrict__ e, __half *__restrict__ out) {
+                                                          const unsigned long long *__restrict__ mx,
+                                                          int *__restrict__ e, __half *__restrict__ out) {
   __shared__ double2 tileS[64][33];
   const int r0 = blockIdx.x * 32, t0 = blockIdx.y * 64;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -486,7 +501,8 @@ __global__ void __launch_bounds__(256) k_oz_slice_strided(const double2 *__restr
   for (int rr = ty; rr < 32; rr += 8) {
     const int r = r0 + rr;
     if (r >= nrows) continue;
-    const int ex = e[r];
+    const int ex = row_exp(mx[r]);
+    if (blockIdx.y == 0 && tx == 0) e[r] = ex;
     for (int tt = tx; tt < 64; tt += 32) {
       const int t = t0 + tt;
       if (2 * t >= kpad) continue;
@@ -540,18 +556,19 @@ bool make_map(CUtensorMap *map, const void *base, int kpad, long rows, int box_r
 //   A side: op = 'N': rows of X (m x k) -> strided; op = 'C': columns of X (k x m) -> contiguous, conj
 //   B side: op = 'N': columns of X (k x n) -> contiguous; op = 'C': rows of X (n x k) -> strided, conj
 pw_status slice_operand(char op, int bside, const double2 *X, int ld, int nrows, int k, int kpad,
-                        int rows_total, __half *out, int *e, cudaStream_t st) {
+                        int rows_total, __half *out, int *e, unsigned long long *mx, cudaStream_t st) {
   const bool contig = bside ? op == 'N' : op == 'C';
   const int conj = op == 'C';
   if (contig) {
     pw_count_launch();
     k_oz_slice_contig<<<nrows, 256, 0, st>>>(X, ld, k, conj, bside, kpad, rows_total, out, e);
   } else {
+    PW_CUDA(cudaMemsetAsync(mx, 0, (size_t)nrows * sizeof(unsigned long long), st));
     pw_count_launch();
-    k_oz_rowexp<<<(nrows + 255) / 256, 256, 0, st>>>(X, ld, nrows, k, e);
+    k_oz_rowmax<<<dim3((nrows + 31) / 32, (k + RX_K - 1) / RX_K), 256, 0, st>>>(X, ld, nrows, k, mx);
     pw_count_launch();
     k_oz_slice_strided<<<dim3((nrows + 31) / 32, (kpad / 2 + 63) / 64), 256, 0, st>>>(
-        X, ld, nrows, k, conj, bside, kpad, rows_total, e, out);
+        X, ld, nrows, k, conj, bside, kpad, rows_total, mx, e, out);
   }
   return pw_check_launch("oz slice");
 }
@@ -578,7 +595,8 @@ pw_status allow_smem() {
 
 size_t pw_oz_ws_bytes(int m, int n, int k) {
   const size_t kpad = ((size_t)2 * k + BK - 1) / BK * BK;
-  return (size_t)S * (m + 2 * (size_t)n) * kpad * 2 + ((size_t)m + n) * 4 + 4096;
+  const size_t arows = ((size_t)m + BM - 1) / BM * BM, brows = (2 * (size_t)n + BN - 1) / BN * BN;
+  return (size_t)S * (arows + brows) * kpad * 2 + (arows + brows) * 4 + std::max(arows, brows) * 8 + 4096;
 }
 
 void pw_oz_free(pw_oz_ws *w) {
@@ -609,7 +627,8 @@ pw_status oz_block(pw_oz_ws *w, char opA, char opB, int mb, int nb, int k, doubl
   // then never reads another slice's rows)
   const int arows = (mb + BM - 1) / BM * BM, brows = (2 * nb + BN - 1) / BN * BN;
   const size_t abytes = (size_t)S * arows * kpad * 2, bbytes = (size_t)S * brows * kpad * 2;
-  const size_t need = abytes + bbytes + ((size_t)arows + brows) * 4 + 1024;
+  const size_t mxrows = (size_t)std::max(arows, brows);
+  const size_t need = abytes + bbytes + ((size_t)arows + brows) * 4 + 256 + mxrows * 8 + 1024;
   if (need > w->bytes) {
     if (w->buf) cudaFree(w->buf);
     w->buf = nullptr;
@@ -626,8 +645,10 @@ pw_status oz_block(pw_oz_ws *w, char opA, char opB, int mb, int nb, int k, doubl
   unsigned char *p = (unsigned char *)w->buf;
   __half *sa = (__half *)p, *sb = (__half *)(p + abytes);
   int *ea = (int *)(p + abytes + bbytes), *eb = ea + arows;
-  PW_TRY(slice_operand(opA, 0, A, lda, mb, k, kpad, arows, sa, ea, st));
-  PW_TRY(slice_operand(opB, 1, B, ldb, nb, k, kpad, brows, sb, eb, st));
+  unsigned long long *mx =
+      (unsigned long long *)(((uintptr_t)(eb + brows) + 255) & ~(uintptr_t)255);   // strided row maxima
+  PW_TRY(slice_operand(opA, 0, A, lda, mb, k, kpad, arows, sa, ea, mx, st));
+  PW_TRY(slice_operand(opB, 1, B, ldb, nb, k, kpad, brows, sb, eb, mx, st));
   CUtensorMap ma, mbm;
   if (!make_map(&ma, sa, kpad, (long)S * arows, BM) || !make_map(&mbm, sb, kpad, (long)S * brows, BN))
     return PW_ERR_CUDA;

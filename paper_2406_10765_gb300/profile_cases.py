@@ -12,6 +12,9 @@ times after one warm-up):
   tcgemm      split-FP16 tensor-core A^H A, A: 104,415 x 1,152 complex
   heev        FP64 Hermitian eigensolver, n = 1,152 (Householder, D&C);
               --n 3456 gives the Si-512 Rayleigh-Ritz order
+  ozgemm      FP64-accurate tensor-core product C = M Y of the Rayleigh-Ritz
+              finish at Si-512 (M 3,456 x 3,456 upper triangular, Y 3,456 x
+              1,152 complex), against numpy in FP64
   hpsi512     FP64 H psi on 16 bands of the Si 512-atom cell (grid 96^3)
   hpsi512mix  mixed-precision H psi on --nb bands (default 1152) of the same cell
   projmodes   H psi of the Si-512 cell with resident and with on-the-fly
@@ -93,6 +96,19 @@ def main():
             C = pw.pw_zgemm_tc("C", A, A)
         torch.cuda.synchronize()
         print("tcgemm done", float(C.abs().max()))
+    elif a.case == "ozgemm":
+        n, nb = 3456, 1152
+        rng = np.random.default_rng(0)
+        M = np.triu(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+        Y = rng.standard_normal((n, nb)) + 1j * rng.standard_normal((n, nb))
+        Md = torch.from_numpy(np.asfortranarray(M)).cuda().T.contiguous().T
+        Yd = torch.from_numpy(np.asfortranarray(Y)).cuda().T.contiguous().T
+        for _ in range(1 + a.reps):
+            C = pw.pw_zgemm_f64tc("N", "N", Md, Yd)
+        torch.cuda.synchronize()
+        ref = M @ Y
+        err = np.abs(C.cpu().numpy() - ref).max() / np.abs(ref).max()
+        print(f"ozgemm: {n} x {nb} x {n}, max error / max |C| {err:.2e}")
     elif a.case == "heev":
         n = a.n
         rng = np.random.default_rng(0)

@@ -26,7 +26,10 @@ def test_roofline_dominant_fp64_stage():
     assert math.isclose(roof["achieved"], ach, rel_tol=1e-12)
     assert math.isclose(roof["frac"], ach / bench.FP64_PEAK_TFLOPS, rel_tol=1e-12)
     assert roof["unit"] == "TFLOP/s" and roof["ms"] == 204.0
-    assert roof["traffic"] is None          # no capture of the current kernels recorded
+    # DRAM traffic of the reduction, scaled from the one-kernel capture
+    assert math.isclose(roof["traffic"], 16.73 * n ** 3 / 6)
+    other = bench.roofline(_stage(rr), rr, fl, 3000, nb, "mixed")
+    assert other["traffic"] is None
     st = roof["stages"]
     assert math.isclose(st["householder_fp64"]["frac"], roof["frac"])
 
