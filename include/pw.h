@@ -430,6 +430,15 @@ pw_status pw_dense_products(int mode);
  * Errors: PW_ERR_ARG. */
 pw_status pw_dense_graphs(int on);
 
+/* Householder reduction of the eigensolver, process-wide: coop = 0 (default)
+ * chains three kernels per column with programmatic dependent launch;
+ * coop = 1 (where the device supports cooperative launch) runs each panel of
+ * 32 columns as one cooperative launch whose phases (column update,
+ * Hermitian product, row sums) are separated by grid-wide barriers, its
+ * launches ordered one after another across streams.  Same arithmetic (to
+ * rounding).  Errors: PW_ERR_ARG. */
+pw_status pw_householder_panels(int coop);
+
 /* ---- Autotuner: the plan and tile-shape choices of the hot kernels ----
  * Sec. III-D picks, for each execution step, the process count that runs it
  * fastest among the candidates that fit in memory.  On one GPU the matching

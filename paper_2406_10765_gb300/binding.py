@@ -194,6 +194,14 @@ def pw_dense_graphs(on):
     _check(_dense_graphs(int(on)), "pw_dense_graphs")
 
 
+_hh_panels = _sig("pw_householder_panels", ct.c_int, [ct.c_int])
+
+
+def pw_householder_panels(coop):
+    """0 (default): three chained kernels per Householder column; 1: one cooperative launch per panel."""
+    _check(_hh_panels(int(coop)), "pw_householder_panels")
+
+
 _launches = _sig("pw_kernel_launches", ct.c_uint64, [])
 
 

@@ -18,9 +18,14 @@
 
 #include <algorithm>
 #include <functional>
+#include <mutex>
 #include <vector>
 
 #include <atomic>
+
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
 
 #include "dense.cuh"
 
@@ -346,9 +351,12 @@ __device__ __forceinline__ void cmacc(double2 &s, double2 a, double2 b) {
 }
 
 // alpha = -1/2 tau (p^H v) from the per-block partial dots (block-wide sum)
-__device__ double2 panel_alpha(const double2 *dotpart, int ndot, double2 t, double *sh) {
+// (stride: the partial sums run over `stride` threads, blockDim.x by default;
+// the cooperative panel kernel uses k_pcol's 128 to reproduce its sums)
+__device__ double2 panel_alpha(const double2 *dotpart, int ndot, double2 t, double *sh, int stride = 0) {
   double sr = 0.0, si = 0.0;
-  for (int q = threadIdx.x; q < ndot; q += blockDim.x) {
+  const int st = stride > 0 ? stride : (int)blockDim.x;
+  for (int q = threadIdx.x; q < ndot && (int)threadIdx.x < st; q += st) {
     const double2 v = __ldcg(&dotpart[q]);
     sr += v.x;
     si += v.y;
@@ -633,6 +641,248 @@ __global__ void __launch_bounds__(256) k_pfinal(const double2 *A, int n, int c, 
     double2 w = p[r - o];
     cmac(w, al, A[r + (long)c * n]);
     P[r + (long)(b + i) * n] = w;
+  }
+}
+
+// ----------------------------------------------------------------------
+// One panel in one cooperative launch: the per-column work of k_pcol,
+// k_phemv and k_prows (and k_pfinal after the panel's last column) as phases
+// of a persistent grid separated by grid-wide barriers, so the chain of three
+// dependent launches per column becomes three barriers.  Same arithmetic as
+// the chained kernels; every block derives the reflector scalars itself from
+// the norm partials (one barrier fewer than a leader block would need).
+// ----------------------------------------------------------------------
+constexpr int CO_THREADS = 256;
+constexpr int CO_QMAX = (TPB + 7) / 8;     // panel columns per thread, 8 warps (phase C)
+constexpr int CO_QMAX4 = (TPB + 3) / 4;    // the same with 4 warps (phase A, k_pcol's split)
+
+__global__ void __launch_bounds__(CO_THREADS) k_panel_coop(double2 *A, int n, int j0, int b, double2 *P,
+                                                           double2 *p, double2 *dotpart, double2 *tau, double *d,
+                                                           double *e, double *nrm_part, double2 *hscal_g,
+                                                           double2 *part, int nmax, double2 *ucorr) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double sh[32];
+  __shared__ double2 tile[TT][TT + 1];
+  __shared__ double2 vrow[TT], vcol[TT], rpart[4][TT + 1], cpart[4][TT + 1];
+  __shared__ double2 s_vc[TPB], s_wc[TPB], s_u[8][33];
+  double2 *V = P, *W = P + (long)b * n;
+  const int nblk = gridDim.x;
+  const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
+  int ndot = 0;
+  double2 tk = make_double2(0.0, 0.0), scal = make_double2(0.0, 0.0);
+  for (int i = 0; i < b; ++i) {
+    const int c = j0 + i, o = c + 1, m = n - o;
+    // ---- phase A: column c receives the panel's earlier rank-2 updates.
+    // Two 32-row blocks per pass, four warps each, in k_pcol's order.
+    double2 al = make_double2(0.0, 0.0);
+    if (i > 0) {
+      al = panel_alpha(dotpart, ndot, tk, sh, PCOL_THREADS);   // tk: tau of column c - 1
+      if (threadIdx.x < i) {
+        const int q = threadIdx.x;
+        s_vc[q] = V[c + (long)q * n];
+        if (q < i - 1) s_wc[q] = W[c + (long)q * n];
+      }
+      if (threadIdx.x == 0) s_wc[i - 1] = cadd(__ldcg(&p[0]), al);
+    }
+    __syncthreads();
+    const int nrb = (n - c + 31) / 32;
+    const int half = g >> 2, gq = g & 3;
+    for (int rb0 = 2 * blockIdx.x; rb0 < nrb; rb0 += 2 * nblk) {
+      const int rb = rb0 + half;
+      const int r = c + rb * 32 + rl;
+      double2 u = make_double2(0.0, 0.0);
+      if (i > 0 && rb < nrb && r < n) {
+#pragma unroll
+        for (int t = 0; t < CO_QMAX4; ++t) {
+          const int q = gq + 4 * t;
+          if (q >= i) break;
+          const double2 vq = V[r + (long)q * n];
+          double2 wq;
+          if (q == i - 1) {
+            wq = __ldcg(&p[r - c]);
+            cmac(wq, al, vq);
+            W[r + (long)q * n] = wq;
+          } else {
+            wq = W[r + (long)q * n];
+          }
+          cmacc(u, s_wc[q], vq);
+          cmacc(u, s_vc[q], wq);
+        }
+      }
+      s_u[g][rl] = u;
+      __syncthreads();
+      if (gq == 0 && rb < nrb) {
+        double nrm = 0.0;
+        if (r < n) {
+          double2 a = A[r + (long)c * n];
+          if (i > 0) {
+            const int h4 = 4 * half;
+            a = csub(a, cadd(cadd(s_u[h4][rl], s_u[h4 + 1][rl]), cadd(s_u[h4 + 2][rl], s_u[h4 + 3][rl])));
+            A[r + (long)c * n] = a;
+          }
+          if (r > c + 1) nrm = a.x * a.x + a.y * a.y;
+        }
+        nrm = warp_sum(nrm);
+        if (rl == 0) nrm_part[rb] = nrm;
+      }
+      __syncthreads();
+    }
+    grid.sync();
+    // reflector scalars from x = A[c+1:, c] (every block, one warp, in the
+    // order of k_pcol's last block)
+    {
+      if (g == 0) {
+        double xn2 = 0.0;
+        for (int q = rl; q < nrb; q += 32) xn2 += __ldcg(&nrm_part[q]);
+        xn2 = warp_sum(xn2);
+        if (rl == 0) sh[0] = xn2;
+      }
+      __syncthreads();
+      const double xn2 = sh[0];
+      __syncthreads();
+      const double2 alpha = __ldcg(&A[(c + 1) + (long)c * n]);
+      double beta;
+      if (xn2 == 0.0 && alpha.y == 0.0) {
+        beta = alpha.x;
+        tk = make_double2(0.0, 0.0);
+        scal = make_double2(0.0, 0.0);
+      } else {
+        beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2), alpha.x);
+        tk = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+        const double2 den = make_double2(alpha.x - beta, alpha.y);
+        const double qq = 1.0 / (den.x * den.x + den.y * den.y);
+        scal = make_double2(den.x * qq, -den.y * qq);
+      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d[c] = __ldcg(&A[c + (long)c * n]).x;
+        tau[c] = tk;
+        e[c] = beta;
+        *hscal_g = scal;
+      }
+    }
+    // ---- phase B: lower-tile partials of A22 v, the corrections W^H v and
+    // V^H v, and the copy of v into the panel
+    const double2 *xk = A + o + (long)c * n;
+    const int nT = (m + TT - 1) / TT, ntiles = nT * (nT + 1) / 2, nwr = (m + 255) / 256;
+    const int tasks = ntiles + 2 * i + nwr;
+    for (int task = blockIdx.x; task < tasks; task += nblk) {
+      if (task >= ntiles + 2 * i) {
+        const int x = (task - ntiles - 2 * i) * blockDim.x + threadIdx.x;
+        if (x < m) {
+          const double2 v = refl_entry(xk, x, scal);
+          P[o + x + (long)i * n] = v;
+          P[o + x + (long)(2 * b + i) * n] = v;
+        }
+        continue;
+      }
+      if (task >= ntiles) {
+        const int q2 = task - ntiles, q = q2 >> 1;
+        const double2 *col = P + (long)((q2 & 1) ? q : b + q) * n;   // odd: V[:, q], even: W[:, q]
+        double2 sacc = make_double2(0.0, 0.0);
+        for (int x = threadIdx.x; x < m; x += blockDim.x) cmacc(sacc, col[o + x], refl_entry(xk, x, scal));
+        sacc.x = block_sum(sacc.x, sh);
+        sacc.y = block_sum(sacc.y, sh);
+        if (threadIdx.x == 0) ucorr[q2] = sacc;
+        continue;
+      }
+      int I = (int)((sqrtf(8.0f * task + 1.0f) - 1.0f) * 0.5f);
+      while ((I + 1) * (I + 2) / 2 <= task) ++I;
+      while (I * (I + 1) / 2 > task) --I;
+      const int J = task - I * (I + 1) / 2;
+      const int x0 = TT * I, y0 = TT * J;
+      {
+        const int wq = threadIdx.x >> 5, yc = y0 + rl;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int rr = wq * 4 + q, xr = x0 + rr;
+          double2 a = make_double2(0.0, 0.0);
+          if (xr < m && yc < m && (I != J || yc <= xr)) a = A[(o + xr) + (long)(o + yc) * n];
+          tile[rr][rl] = a;
+        }
+      }
+      if (threadIdx.x < TT) {
+        const int xr = x0 + threadIdx.x, yc = y0 + threadIdx.x;
+        vrow[threadIdx.x] = xr < m ? refl_entry(xk, xr, scal) : make_double2(0.0, 0.0);
+        vcol[threadIdx.x] = yc < m ? refl_entry(xk, yc, scal) : make_double2(0.0, 0.0);
+      }
+      __syncthreads();
+      {
+        const int k = g & 3;
+        double2 sacc = make_double2(0.0, 0.0);
+        if (threadIdx.x < 128) {
+#pragma unroll
+          for (int cl = 8 * k; cl < 8 * k + 8; ++cl) cmac(sacc, tile[rl][cl], vcol[cl]);
+          rpart[k][rl] = sacc;
+        } else {
+#pragma unroll
+          for (int rr = 8 * k; rr < 8 * k + 8; ++rr)
+            if (I != J || rr > rl) cmacc(sacc, tile[rr][rl], vrow[rr]);
+          cpart[k][rl] = sacc;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < TT) {
+        const int l = threadIdx.x;
+        const double2 rs = cadd(cadd(rpart[0][l], rpart[1][l]), cadd(rpart[2][l], rpart[3][l]));
+        const double2 cs = cadd(cadd(cpart[0][l], cpart[1][l]), cadd(cpart[2][l], cpart[3][l]));
+        if (I != J) {
+          if (x0 + l < m) part[(long)J * nmax + x0 + l] = rs;
+          if (y0 + l < m) part[(long)I * nmax + y0 + l] = cs;
+        } else if (x0 + l < m) {
+          part[(long)J * nmax + x0 + l] = cadd(rs, cs);
+        }
+      }
+      __syncthreads();
+    }
+    grid.sync();
+    // ---- phase C: y = partial sums - V (W^H v) - W (V^H v), p = tau y, v in
+    // place of x, partial dots p^H v
+    ndot = (m + 31) / 32;
+    double2 *xc = A + o + (long)c * n;
+    for (int rb = blockIdx.x; rb < ndot; rb += nblk) {
+      const int x = rb * 32 + rl;
+      double2 y = make_double2(0.0, 0.0);
+      if (x < m) {
+        for (int q = g; q < nT; q += 8) y = cadd(y, __ldcg(&part[(long)q * nmax + x]));
+#pragma unroll
+        for (int t = 0; t < CO_QMAX; ++t) {
+          const int q = g + 8 * t;
+          if (q >= i) break;
+          const double2 uw = __ldcg(&ucorr[2 * q]), uv = __ldcg(&ucorr[2 * q + 1]);
+          cmac(y, P[o + x + (long)q * n], make_double2(-uw.x, -uw.y));         // - V[r,q] (W^H v)_q
+          cmac(y, P[o + x + (long)(b + q) * n], make_double2(-uv.x, -uv.y));   // - W[r,q] (V^H v)_q
+        }
+      }
+      s_u[g][rl] = y;
+      __syncthreads();
+      if (g == 0) {
+        double2 pv = make_double2(0.0, 0.0);
+        if (x < m) {
+#pragma unroll
+          for (int q = 1; q < 8; ++q) y = cadd(y, s_u[q][rl]);
+          const double2 pr = cmul(tk, y);
+          p[x] = pr;
+          const double2 v = refl_entry(xc, x, scal);
+          xc[x] = v;
+          cmacc(pv, pr, v);
+        }
+        pv.x = warp_sum(pv.x);
+        pv.y = warp_sum(pv.y);
+        if (rl == 0) dotpart[rb] = pv;
+      }
+      __syncthreads();
+    }
+    grid.sync();
+  }
+  // W[:, b-1] = p + alpha v for the panel's last column
+  {
+    const int cl = j0 + b - 1, o = cl + 1;
+    const double2 al = panel_alpha(dotpart, ndot, tk, sh);
+    for (int r = o + blockIdx.x * blockDim.x + threadIdx.x; r < n; r += nblk * blockDim.x) {
+      double2 w = __ldcg(&p[r - o]);
+      cmac(w, al, A[r + (long)cl * n]);
+      W[r + (long)(b - 1) * n] = w;
+    }
   }
 }
 
@@ -1265,7 +1515,85 @@ void pw_dense_stage_ms(pw_dense_ws *ws, float out[5]) {
 namespace {
 // The three stages of the eigensolver, each a fixed launch sequence for a
 // given (n, nb) on a given workspace (so each can be captured as a graph).
+// measured slower than the chained kernels at n = 3,456 (277 against 204 ms:
+// two 256-thread blocks per SM leave the FP64 pipe short of warps, and
+// three grid barriers per column cost more than PDL's launch overlap)
+std::atomic<int> g_coop{0};
+
+// grid of the cooperative panel kernel on the current device (0: not
+// available): blocks that fit at once, at most two per SM
+int coop_grid() {
+  static std::mutex mu;
+  static int grid[64];
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!done[dev]) {
+    int coop = 0, sms = 0, per = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_panel_coop, CO_THREADS, 0) != cudaSuccess) {
+      cudaGetLastError();
+      per = 0;
+    }
+    grid[dev] = coop ? std::min(per, 2) * sms : 0;
+    done[dev] = true;
+  }
+  return grid[dev];
+}
+
+// Cooperative grids fill the device; two of them partly resident at once
+// (concurrent solves on other streams) could each wait at a grid barrier for
+// blocks that only the other's exit would make room for.  So every
+// cooperative launch on a device is ordered after the previous one, through
+// one event recorded behind each launch (host mutex, then stream wait).
+pw_status launch_panel_coop(cudaLaunchConfig_t &cfg, double2 *A, int n, int j0, int b, pw_dense_ws *ws) {
+  static std::mutex mu;
+  static cudaEvent_t last[64] = {};
+  int dev = 0;
+  PW_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return PW_ERR_ARG;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!last[dev]) PW_CUDA(cudaEventCreateWithFlags(&last[dev], cudaEventDisableTiming));
+  else PW_CUDA(cudaStreamWaitEvent(cfg.stream, last[dev], 0));
+  pw_count_launch();
+  PW_CUDA(cudaLaunchKernelEx(&cfg, k_panel_coop, A, n, j0, b, ws->panel, ws->p, ws->w, ws->tau, ws->d, ws->e,
+                             ws->nrm_part, ws->hscal, ws->part, ws->nmax, ws->ucorr));
+  PW_CUDA(cudaEventRecord(last[dev], cfg.stream));
+  return PW_OK;
+}
+
+// the reduction with one cooperative launch per panel (three grid barriers
+// per column) and the panel's rank-64 update
+pw_status tridiag_coop(pw_dense_ws *ws, int n, double2 *A, int grid, cudaStream_t st) {
+  const double2 mone = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
+  for (int j0 = 0; j0 + 1 < n; j0 += TPB) {
+    const int b = std::min(TPB, n - 1 - j0);
+    PW_CUDA(cudaMemsetAsync(ws->panel, 0, (size_t)n * 3 * b * sizeof(double2), st));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(CO_THREADS);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PW_TRY(launch_panel_coop(cfg, A, n, j0, b, ws));
+    const int t = j0 + b, m2 = n - t;
+    if (m2 > 0)
+      PW_TRY(pw_dense_gemm(ws, 'N', 'C', m2, m2, 2 * b, mone, ws->panel + t, n, ws->panel + (long)b * n + t, n,
+                           one, A + t + (long)t * n, n, st, 2));
+  }
+  pw_count_launch();
+  k_last_diag_plain<<<1, 1, 0, st>>>(A, n, ws->d);
+  return pw_check_launch("tridiag (cooperative panels)");
+}
+
 pw_status stage_tridiag(pw_dense_ws *ws, int n, double2 *A, cudaStream_t st) {
+  const int grid = g_coop.load() ? coop_grid() : 0;
+  if (grid > 0) return tridiag_coop(ws, n, A, grid, st);
   // 1. Householder tridiagonalisation: panels of TPB columns (lower triangle)
   PW_CUDA(cudaMemsetAsync(ws->ticket, 0, sizeof(unsigned), st));
   {
@@ -1433,6 +1761,12 @@ pw_status run_stage(pw_dense_ws *ws, int stage, int n, int nb, const void *p0, c
 }
 }  // namespace
 
+extern "C" pw_status pw_householder_panels(int coop) {
+  if (coop != 0 && coop != 1) return PW_ERR_ARG;
+  g_coop.store(coop);
+  return PW_OK;
+}
+
 extern "C" pw_status pw_dense_graphs(int on) {
   if (on != 0 && on != 1) return PW_ERR_ARG;
   g_graphs.store(on);
@@ -1444,7 +1778,10 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
   if (n <= 0 || nb <= 0 || nb > n || n > ws->nmax || nb > ws->nbmax) return PW_ERR_ARG;
   // 1. Householder tridiagonalisation: panels of TPB columns (lower triangle)
   if (ws->ev[2]) cudaEventRecord(ws->ev[2], st);
-  PW_TRY(run_stage(ws, 0, n, nb, A, nullptr, st, [&] { return stage_tridiag(ws, n, A, st); }));
+  // with cooperative panels the stage is ~5 launches per 32 columns and is
+  // ordered across streams by an event, so it runs uncaptured
+  if (g_coop.load() && coop_grid() > 0) PW_TRY(stage_tridiag(ws, n, A, st));
+  else PW_TRY(run_stage(ws, 0, n, nb, A, nullptr, st, [&] { return stage_tridiag(ws, n, A, st); }));
   // 2. divide and conquer (the merge tree is built and uploaded outside any capture)
   if (ws->ev[3]) cudaEventRecord(ws->ev[3], st);
   if (ws->tree_n != n) build_tree(ws, n, st);

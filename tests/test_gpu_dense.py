@@ -52,20 +52,24 @@ def test_heev_argument_errors():
     assert B._heev(4, 5, ct.c_void_p(1), ct.c_void_p(1), ct.c_void_p(1), st) == B.PW_ERR_ARG
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_heev_large_both_product_modes(mode):
+@pytest.mark.parametrize("mode,coop", [(0, 0), (1, 0), (1, 1)])
+def test_heev_large_both_product_modes(mode, coop):
     # order 1,700: the panel updates, back-transformation and their K-split
     # products run on the FP64-accurate tensor-core path (mode 1) or the FP64
-    # pipe (mode 0); both match LAPACK at the same tolerances
+    # pipe (mode 0), the Householder columns as chained kernels (coop 0) or
+    # one cooperative launch per panel (coop 1); all match LAPACK at the same
+    # tolerances
     import paper_2406_10765_gb300 as pw
     n, nb = 1700, 600
     A = _herm(n, 17, "rand")
     pw.pw_dense_products(mode)
+    pw.pw_householder_panels(coop)
     try:
         w, Y = pw.pw_heev(torch.from_numpy(A).cuda(), nb)
         torch.cuda.synchronize()
     finally:
         pw.pw_dense_products(1)
+        pw.pw_householder_panels(0)
     w = w.cpu().numpy()
     Y = Y.cpu().numpy()
     ref = np.linalg.eigvalsh(A)
@@ -73,3 +77,27 @@ def test_heev_large_both_product_modes(mode):
     assert np.abs(w - ref).max() < 1e-13 * scale * n ** 0.5
     assert np.abs(A @ Y - Y * w[:nb]).max() < 1e-12 * scale
     assert np.abs(Y.conj().T @ Y - np.eye(nb)).max() < 1e-12
+
+
+def test_heev_cooperative_panels_match_chained():
+    # the cooperative panel kernel runs the chained kernels' arithmetic in the
+    # same order (the compiler may contract multiply-adds differently in the
+    # two kernels, so the last bits can differ): eigenvalues to rounding and
+    # the same wanted subspace, on small and ragged orders
+    import paper_2406_10765_gb300 as pw
+    for n, nb in [(2, 1), (33, 11), (130, 40), (515, 170)]:
+        A = _herm(n, n + 3, "rand")
+        out = []
+        for coop in (0, 1):
+            pw.pw_householder_panels(coop)
+            try:
+                w, Y = pw.pw_heev(torch.from_numpy(A).cuda(), nb)
+                torch.cuda.synchronize()
+                out.append((w.cpu().numpy(), Y.cpu().numpy()))
+            finally:
+                pw.pw_householder_panels(0)
+        scale = max(1.0, np.abs(out[0][0]).max())
+        assert np.abs(out[0][0] - out[1][0]).max() < 1e-13 * scale * n ** 0.5, n
+        Ya, Yb = out[0][1], out[1][1]
+        assert np.abs(Ya @ Ya.conj().T - Yb @ Yb.conj().T).max() < 1e-10, n
+        assert np.abs(A @ Yb - Yb * out[1][0][:nb]).max() < 1e-12 * scale, n
