@@ -430,14 +430,20 @@ pw_status pw_dense_products(int mode);
  * Errors: PW_ERR_ARG. */
 pw_status pw_dense_graphs(int on);
 
-/* Householder reduction of the eigensolver, process-wide: coop = 0 (default)
- * chains three kernels per column with programmatic dependent launch;
- * coop = 1 (where the device supports cooperative launch) runs each panel of
- * 32 columns as one cooperative launch whose phases (column update,
- * Hermitian product, row sums) are separated by grid-wide barriers, its
- * launches ordered one after another across streams.  Same arithmetic (to
- * rounding).  Errors: PW_ERR_ARG. */
-pw_status pw_householder_panels(int coop);
+/* Householder reduction of the eigensolver (Syevd, Sec. III-D),
+ * process-wide.  mode = 0 (default) chains three kernels per column with
+ * programmatic dependent launch; while the product mode (pw_dense_products)
+ * is 1, the Hermitian products A22 v of panels whose trailing order is at
+ * least 512 run on the FP16 tensor cores at FP64 accuracy (the panel's
+ * trailing matrix split once into integer digit slices), the others on the
+ * FP64 pipe.  mode = 2: the same chain with every Hermitian product on the
+ * FP64 pipe.  mode = 1 (where the device supports cooperative launch): each
+ * panel of 32 columns as one cooperative launch whose phases (column update,
+ * Hermitian product on the FP64 pipe, row sums) are separated by grid-wide
+ * barriers, its launches ordered one after another across streams.  All
+ * modes give the same tridiagonal matrix to FP64 rounding.
+ * Errors: PW_ERR_ARG. */
+pw_status pw_householder_panels(int mode);
 
 /* ---- Autotuner: the plan and tile-shape choices of the hot kernels ----
  * Sec. III-D picks, for each execution step, the process count that runs it

@@ -197,9 +197,11 @@ def pw_dense_graphs(on):
 _hh_panels = _sig("pw_householder_panels", ct.c_int, [ct.c_int])
 
 
-def pw_householder_panels(coop):
-    """0 (default): three chained kernels per Householder column; 1: one cooperative launch per panel."""
-    _check(_hh_panels(int(coop)), "pw_householder_panels")
+def pw_householder_panels(mode):
+    """0 (default): chained kernels per Householder column, Hermitian products of
+    large panels on the tensor cores; 1: one cooperative launch per panel; 2:
+    chained kernels, every Hermitian product on the FP64 pipe."""
+    _check(_hh_panels(int(mode)), "pw_householder_panels")
 
 
 _launches = _sig("pw_kernel_launches", ct.c_uint64, [])

@@ -371,15 +371,35 @@ __device__ __forceinline__ double2 refl_entry(const double2 *xcol, int x, double
   return x == 0 ? make_double2(1.0, 0.0) : cmul(xcol[x], scal);
 }
 
+// Sum over the 32 lanes of each of 32 values per lane, by halving exchanges
+// (31 shuffles): lane L returns the sum of component L.
+__device__ __forceinline__ double warp_transpose_sum(double (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int bit = 16; bit >= 1; bit >>= 1) {
+    const bool up = (lane & bit) != 0;
+#pragma unroll
+    for (int j = 0; j < bit; ++j) {
+      const double send = up ? v[j] : v[j + bit];
+      const double keep = up ? v[j + bit] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
+  }
+  return v[0];
+}
+
 // 32 rows per block; the four warps split the panel's previous updates
-// (q = warp mod 4) so that the FP64 work lands on all four SM sub-partitions
+// (q = warp mod 4) so that the FP64 work lands on all four SM sub-partitions.
+// With dotp, also the block's partial dots W[:, q]^H x and V[:, q]^H x (q < i)
+// over the rows below the reflector's head (rows >= c + 2), for the
+// tensor-core Hermitian product: dotp[block * 64 + 2q (W) / 2q + 1 (V)].
 __global__ void __launch_bounds__(PCOL_THREADS) k_pcol(double2 *A, int n, int c, int i, double2 *P, int b,
                                                        const double2 *p, const double2 *dotpart, int ndot,
                                                        double2 *tau, double *d, double *e, double *nrm_part,
-                                                       double2 *hscal, unsigned *ticket) {
+                                                       double2 *hscal, unsigned *ticket, double2 *dotp) {
   __shared__ double sh[32];
   __shared__ unsigned s_ticket;
-  __shared__ double2 s_vc[TPB], s_wc[TPB], s_u[4][33];
+  __shared__ double2 s_vc[TPB], s_wc[TPB], s_u[4][33], s_x[32];
   double2 *V = P, *W = P + (long)b * n;
   const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int r = c + blockIdx.x * 32 + rl;
@@ -427,6 +447,7 @@ __global__ void __launch_bounds__(PCOL_THREADS) k_pcol(double2 *A, int n, int c,
           wq = __ldcg(&p[r - c]);
           cmac(wq, al, vq);
           W[r + (long)q * n] = wq;
+          wq_r[t] = wq;
         }
         cmacc(u, s_wc[q], vq);
         cmacc(u, s_vc[q], wq);
@@ -435,16 +456,40 @@ __global__ void __launch_bounds__(PCOL_THREADS) k_pcol(double2 *A, int n, int c,
     s_u[g][rl] = u;
     __syncthreads();
   }
-  if (g != 0) return;
-  double nrm = 0.0;
-  if (r < n) {
+  if (g == 0 && r < n) {
     if (i == 0) a = A[r + (long)c * n];
     if (i > 0) {
       a = csub(a, cadd(cadd(s_u[0][rl], s_u[1][rl]), cadd(s_u[2][rl], s_u[3][rl])));
       A[r + (long)c * n] = a;
     }
-    if (r > c + 1) nrm = a.x * a.x + a.y * a.y;
   }
+  if (dotp && i > 0) {
+    if (g == 0) s_x[rl] = (r < n && r > c + 1) ? a : make_double2(0.0, 0.0);
+    __syncthreads();
+    const double2 x = s_x[rl];
+    double v[32];
+#pragma unroll
+    for (int t = 0; t < QMAX; ++t) {
+      const int q = g + 4 * t;
+      double2 dw = make_double2(0.0, 0.0), dv = make_double2(0.0, 0.0);
+      if (q < i) {
+        cmacc(dw, wq_r[t], x);
+        cmacc(dv, vq_r[t], x);
+      }
+      v[4 * t] = dw.x;
+      v[4 * t + 1] = dw.y;
+      v[4 * t + 2] = dv.x;
+      v[4 * t + 3] = dv.y;
+    }
+#pragma unroll
+    for (int t = QMAX; t < 8; ++t) v[4 * t] = v[4 * t + 1] = v[4 * t + 2] = v[4 * t + 3] = 0.0;
+    const double sum = warp_transpose_sum(v);
+    const int q = g + 4 * (rl >> 2);
+    if (q < i) ((double *)dotp)[2 * ((long)blockIdx.x * 64 + 2 * q + ((rl >> 1) & 1)) + (rl & 1)] = sum;
+  }
+  if (g != 0) return;
+  double nrm = 0.0;
+  if (r < n && r > c + 1) nrm = a.x * a.x + a.y * a.y;
   nrm = warp_sum(nrm);
   if (rl == 0) {
     nrm_part[blockIdx.x] = nrm;
@@ -571,11 +616,12 @@ __global__ void __launch_bounds__(256) k_phemv(const double2 *A, int n, int c, i
   }
 }
 
-// 32 rows per block, 8 thread groups over the partial slots and corrections:
-// y = sum of partials - V[:, <i] u_W - W[:, <i] u_V, p = tau_c y, v stored in
-// place of x, partial dots p^H v
+// 32 rows per block, 8 thread groups over the partial slots s0..nT-1 and the
+// corrections: y = sum of partials - V[:, <i] u_W - W[:, <i] u_V, p = tau_c y,
+// v stored in place of x, partial dots p^H v.  part[s * nmax + x] holds slot
+// s of row o + x.
 __global__ void __launch_bounds__(256) k_prows(double2 *A, int n, int c, int i, const double2 *P, int b,
-                                               const double2 *part, int nT, int nmax, const double2 *ucorr,
+                                               const double2 *part, int s0, int nT, int nmax, const double2 *ucorr,
                                                const double2 *tau, const double2 *hscal, double2 *p,
                                                double2 *dotpart) {
   __shared__ double2 red[8][33];
@@ -598,7 +644,7 @@ __global__ void __launch_bounds__(256) k_prows(double2 *A, int n, int c, int i, 
   pdl_trigger();
   double2 y = make_double2(0.0, 0.0);
   if (x < m) {
-    for (int s = g; s < nT; s += 8) y = cadd(y, part[(long)s * nmax + x]);
+    for (int s = s0 + g; s < nT; s += 8) y = cadd(y, part[(long)s * nmax + x]);
 #pragma unroll
     for (int t = 0; t < QMAX; ++t) {
       const int q = g + 8 * t;
@@ -1466,7 +1512,17 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
        get((void **)&ws->kLR, (size_t)nmax * 8 + 64) && get((void **)&ws->kneed, (size_t)nmax * 4 + 64);
   ok = ok && get((void **)&ws->ticket, 64) && get((void **)&ws->panel, (size_t)nmax * 3 * TPB * 16) &&
        get((void **)&ws->ucorr, 2 * TPB * 16) && get((void **)&ws->hscal, 16) && get((void **)&ws->Li, CB * CB * 16) &&
-       get((void **)&ws->nrm_part, (size_t)(nmax / 32 + 2) * 8);
+       get((void **)&ws->nrm_part, (size_t)(nmax / 32 + 2) * 8) &&
+       get((void **)&ws->hsmax, (size_t)(nmax / TPB + 2) * 8) &&
+       get((void **)&ws->dotp, (size_t)(nmax / 32 + 2) * 64 * 16);
+  if (ok && pw_hs_bytes(nmax)) {
+    // zeroed once: a slice tile is only read where the panel's slicing wrote it
+    ok = get(&ws->hsl, pw_hs_bytes(nmax)) && cudaMemset(ws->hsl, 0, pw_hs_bytes(nmax)) == cudaSuccess;
+  }
+  if (ok && !ws->oz.err) {
+    ok = cudaMalloc((void **)&ws->oz.err, 16) == cudaSuccess && cudaMemset(ws->oz.err, 0, 16) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); ws->oz.err = nullptr; }
+  }
   ok = ok && get((void **)&ws->Vb, (size_t)nmax * BTB * 16) && get((void **)&ws->Gv, BTB * BTB * 16) &&
        get((void **)&ws->Tb, BTB * BTB * 16) && get((void **)&ws->Wk, (size_t)BTB * nbmax * 16) &&
        get((void **)&ws->Wk2, (size_t)BTB * nbmax * 16);
@@ -1494,7 +1550,7 @@ void pw_dense_free(pw_dense_ws *ws) {
                   ws->orig, ws->dcol, ws->src, ws->nodes, ws->knode, ws->rhonode, ws->ctype, ws->qL, ws->qR,
                   ws->kLR, ws->kneed, ws->gemm_ws,
                   ws->Vb, ws->Gv, ws->Tb, ws->Wk, ws->Wk2, ws->ticket, ws->panel, ws->ucorr,
-                  ws->hscal, ws->nrm_part, ws->Li};
+                  ws->hscal, ws->nrm_part, ws->Li, ws->hsl, ws->hsmax, ws->dotp};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : ws->ev)
@@ -1592,32 +1648,47 @@ pw_status tridiag_coop(pw_dense_ws *ws, int n, double2 *A, int grid, cudaStream_
 }
 
 pw_status stage_tridiag(pw_dense_ws *ws, int n, double2 *A, cudaStream_t st) {
-  const int grid = g_coop.load() ? coop_grid() : 0;
+  const int mode = g_coop.load();
+  const int grid = mode == 1 ? coop_grid() : 0;
   if (grid > 0) return tridiag_coop(ws, n, A, grid, st);
+  // Hermitian products on the tensor cores for the panels of trailing order
+  // >= PW_HS_MIN_ORDER (slices of each such panel's trailing matrix first)
+  const bool hs = mode == 0 && ws->hsl && pw_dense_products_mode() == 1 && n - 1 >= PW_HS_MIN_ORDER;
   // 1. Householder tridiagonalisation: panels of TPB columns (lower triangle)
   PW_CUDA(cudaMemsetAsync(ws->ticket, 0, sizeof(unsigned), st));
+  if (hs) PW_CUDA(cudaMemsetAsync(ws->hsmax, 0, (size_t)(n / TPB + 2) * 8, st));
   {
     const double2 mone = make_double2(-1.0, 0.0), one = make_double2(1.0, 0.0);
     double2 *dotpart = ws->w;
     for (int j0 = 0; j0 + 1 < n; j0 += TPB) {
       const int b = std::min(TPB, n - 1 - j0);
+      const bool ptc = hs && n - j0 - 1 >= PW_HS_MIN_ORDER;
       PW_CUDA(cudaMemsetAsync(ws->panel, 0, (size_t)n * 3 * b * sizeof(double2), st));
+      if (ptc) PW_TRY(pw_hs_slice(ws, A, n, j0, st));
       int ndot = 0;
       for (int i = 0; i < b; ++i) {
         const int c = j0 + i, m = n - c - 1;
+        const int npcol = (n - c + 31) / 32;
         pw_count_launch();
-        PW_CUDA(launch_pdl(k_pcol, (n - c + 31) / 32, PCOL_THREADS, st, A, n, c, i, ws->panel, b,
+        PW_CUDA(launch_pdl(k_pcol, npcol, PCOL_THREADS, st, A, n, c, i, ws->panel, b,
                            (const double2 *)ws->p, (const double2 *)dotpart, ndot, ws->tau, ws->d, ws->e,
-                           ws->nrm_part, ws->hscal, ws->ticket));
-        const int nT = (m + TT - 1) / TT, ntiles = nT * (nT + 1) / 2, nwr = (m + 255) / 256;
-        pw_count_launch();
-        PW_CUDA(launch_pdl(k_phemv, ntiles + 2 * i + nwr, 256, st, (const double2 *)A, n, c, i, ws->panel,
-                           b, ntiles, ws->part, ws->nmax, ws->ucorr, (const double2 *)ws->hscal));
+                           ws->nrm_part, ws->hscal, ws->ticket, ptc ? ws->dotp : (double2 *)nullptr));
+        int s0 = 0, nT = (m + TT - 1) / TT;
+        const double2 *part = ws->part;
+        if (ptc) {
+          PW_TRY(pw_hs_hemv(ws, A, n, c, i, b, j0, npcol, &nT, st));
+          part = ws->part + (c + 1);
+        } else {
+          const int ntiles = nT * (nT + 1) / 2, nwr = (m + 255) / 256;
+          pw_count_launch();
+          PW_CUDA(launch_pdl(k_phemv, ntiles + 2 * i + nwr, 256, st, (const double2 *)A, n, c, i, ws->panel,
+                             b, ntiles, ws->part, ws->nmax, ws->ucorr, (const double2 *)ws->hscal));
+        }
         ndot = (m + 31) / 32;
         pw_count_launch();
-        PW_CUDA(launch_pdl(k_prows, ndot, 256, st, A, n, c, i, (const double2 *)ws->panel, b,
-                           (const double2 *)ws->part, nT, ws->nmax, (const double2 *)ws->ucorr,
-                           (const double2 *)ws->tau, (const double2 *)ws->hscal, ws->p, dotpart));
+        PW_CUDA(launch_pdl(k_prows, ndot, 256, st, A, n, c, i, (const double2 *)ws->panel, b, part, s0, nT,
+                           ws->nmax, (const double2 *)ws->ucorr, (const double2 *)ws->tau,
+                           (const double2 *)ws->hscal, ws->p, dotpart));
       }
       const int cl = j0 + b - 1, ml = n - cl - 1;
       pw_count_launch();
@@ -1704,6 +1775,12 @@ pw_status stage_backtransform(pw_dense_ws *ws, int n, int nb, const double2 *A, 
 
 std::atomic<int> g_graphs{1};
 
+// what a captured stage depends on besides its key: the product buffers'
+// generation, the product mode and the panel mode
+unsigned stage_gen(const pw_dense_ws *ws) {
+  return (2 * ws->oz.gen + (unsigned)pw_dense_products_mode()) * 3 + (unsigned)g_coop.load();
+}
+
 // A stage through the workspace's graph cache: the first call of a key runs
 // directly (and grows any workspace it needs); a key seen twice in a row is
 // captured (thread-local capture mode) and then replayed.  Graphs bake in
@@ -1719,7 +1796,7 @@ pw_status run_stage(pw_dense_ws *ws, int stage, int n, int nb, const void *p0, c
     return fn();
   // the product buffers' generation and the product mode both decide what a
   // capture holds
-  const unsigned gen = 2 * ws->oz.gen + (unsigned)pw_dense_products_mode();
+  const unsigned gen = stage_gen(ws);
   for (auto it = ws->graphs.begin(); it != ws->graphs.end(); ++it) {
     if (it->stage == stage && it->n == n && it->nb == nb && it->p0 == p0 && it->p1 == p1) {
       if (it->gen == gen) {
@@ -1743,7 +1820,7 @@ pw_status run_stage(pw_dense_ws *ws, int stage, int n, int nb, const void *p0, c
   const uint64_t nk = pw_thread_launches() - k0;
   const cudaError_t ce = cudaStreamEndCapture(st, &g);
   cudaGraphExec_t exec = nullptr;
-  if (r != PW_OK || ce != cudaSuccess || !g || 2 * ws->oz.gen + (unsigned)pw_dense_products_mode() != gen ||
+  if (r != PW_OK || ce != cudaSuccess || !g || stage_gen(ws) != gen ||
       cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) {
     // capture did not work out: clear the error and run the stage directly
     if (g) cudaGraphDestroy(g);
@@ -1761,9 +1838,9 @@ pw_status run_stage(pw_dense_ws *ws, int stage, int n, int nb, const void *p0, c
 }
 }  // namespace
 
-extern "C" pw_status pw_householder_panels(int coop) {
-  if (coop != 0 && coop != 1) return PW_ERR_ARG;
-  g_coop.store(coop);
+extern "C" pw_status pw_householder_panels(int mode) {
+  if (mode < 0 || mode > 2) return PW_ERR_ARG;
+  g_coop.store(mode);
   return PW_OK;
 }
 
@@ -1780,7 +1857,7 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
   if (ws->ev[2]) cudaEventRecord(ws->ev[2], st);
   // with cooperative panels the stage is ~5 launches per 32 columns and is
   // ordered across streams by an event, so it runs uncaptured
-  if (g_coop.load() && coop_grid() > 0) PW_TRY(stage_tridiag(ws, n, A, st));
+  if (g_coop.load() == 1 && coop_grid() > 0) PW_TRY(stage_tridiag(ws, n, A, st));
   else PW_TRY(run_stage(ws, 0, n, nb, A, nullptr, st, [&] { return stage_tridiag(ws, n, A, st); }));
   // 2. divide and conquer (the merge tree is built and uploaded outside any capture)
   if (ws->ev[3]) cudaEventRecord(ws->ev[3], st);
@@ -1927,6 +2004,7 @@ extern "C" pw_status pw_heev(int n, int nb, void *A, double *w, void *Y, void *s
   PW_TRY(pw_dense_alloc(&ws, n, nb));
   pw_status r = pw_heev_lowest(&ws, n, nb, (double2 *)A, w, (double2 *)Y, st);
   if (r == PW_OK && cudaStreamSynchronize(st) != cudaSuccess) r = PW_ERR_CUDA;
+  if (r == PW_OK) r = pw_oz_check(&ws.oz, st);
   pw_dense_free(&ws);
   return r;
 }

@@ -47,6 +47,12 @@ struct pw_dense_ws {
   // norms of a column, the panel correction dots
   double2 *panel = nullptr, *ucorr = nullptr, *hscal = nullptr;
   double2 *Li = nullptr;      // inverse of the current Cholesky diagonal block (CB x CB)
+  // tensor-core Hermitian products of the reduction: digit slices of the
+  // panel's trailing tiles, the trailing matrix's maximum per panel (ordered
+  // bits), k_pcol's partial dots W^H x, V^H x (64 per block)
+  void *hsl = nullptr;
+  unsigned long long *hsmax = nullptr;
+  double2 *dotp = nullptr;
   double *nrm_part = nullptr;
   // host side tree for the current n
   int tree_n = -1;
@@ -73,6 +79,20 @@ int pw_dense_products_mode();
 void pw_dense_stage_ms(pw_dense_ws *ws, float out[5]);
 
 pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax);
+
+// Hermitian products of the Householder reduction on the tensor cores
+// (hemv_tc.cu): used for the panels whose trailing order is at least
+// PW_HS_MIN_ORDER when the product mode is 1.  pw_hs_bytes: slice buffer
+// bytes for order nmax (0 below the threshold).  pw_hs_slice: the slices of
+// the trailing matrix of the panel starting at column j0.  pw_hs_hemv: the
+// product for column c (panel index i, width b): partials into ws->part
+// (*nslots slots per row, part[s * nmax + row] with the global row index),
+// ucorr and v into the panel, as the FP64 k_phemv does.
+#define PW_HS_MIN_ORDER 512
+size_t pw_hs_bytes(int nmax);
+pw_status pw_hs_slice(pw_dense_ws *ws, const double2 *A, int n, int j0, cudaStream_t st);
+pw_status pw_hs_hemv(pw_dense_ws *ws, const double2 *A, int n, int c, int i, int b, int j0, int ndotblk,
+                     int *nslots, cudaStream_t st);
 void pw_dense_free(pw_dense_ws *ws);
 
 // Lowest nb Ritz pairs of the pencil (A, G), both n x n Hermitian (device,

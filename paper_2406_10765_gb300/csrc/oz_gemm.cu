@@ -42,11 +42,12 @@
 
 #include "oz_gemm.cuh"
 #include "pw_internal.cuh"
+#include "umma.cuh"
 
 namespace {
 
-constexpr int S = PW_OZ_SLICES;       // slices per operand
-constexpr int BETA = 7;               // bits per slice
+using namespace pw_umma;
+
 constexpr int NG = S;                 // accumulator groups g = 2..S+1
 constexpr int BM = 128, BN = 64, BK = 32;   // real rows, real columns, real K per stage
 constexpr int A_T = BM * BK * 2;      // 8 KB per slice
@@ -58,39 +59,7 @@ constexpr int SMEM_BYTES = NSTAGE * STAGE + 1024 + 512;
 constexpr int TMEM_COLS = 512;
 constexpr int EPI_WARPS = 8;
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
-constexpr long long WAIT_CYCLES = 2000000000ll;   // ~1 s
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// bounded wait: false after WAIT_CYCLES clocks without the phase completing
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  if (mbar_try(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_try(bar, parity))
-    if (clock64() - t0 > WAIT_CYCLES) return false;
-  return true;
-}
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -100,68 +69,9 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
 }
 // shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 32
 // FP16), 8-row groups 512 B apart
-__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFF) >> 4);   // start address
-  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset
-  d |= (uint64_t)1 << 46;                   // descriptor version (sm_100 family)
-  d |= (uint64_t)4 << 61;                   // swizzle: 64B
-  return d;
-}
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) { return smem_desc(addr, 16, 512, 4); }
 // instruction descriptor, kind::f16: FP16 A and B, FP32 D, both K-major, M = 128, N = 64
-__host__ __device__ constexpr uint32_t idesc_oz() {
-  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
-__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// x 2^k by exponent arithmetic (x finite); results below the normal range are zero
-__device__ __forceinline__ double scale_pow2(double x, int k) {
-  const long long b = __double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex == 0) return __longlong_as_double(b & (long long)0x8000000000000000ull);
-  const int en = ex + k;
-  if (en <= 0) return __longlong_as_double(b & (long long)0x8000000000000000ull);
-  if (en >= 0x7FF) return __longlong_as_double((b & (long long)0x8000000000000000ull) | 0x7FF0000000000000ll);
-  return __longlong_as_double(b + ((long long)k << 52));
-}
-
-// An FP32 accumulator value holding an integer |v| < 2^22, as an int: adding
-// 1.5 * 2^23 puts the integer into the low mantissa bits
-__device__ __forceinline__ int f2i_exact(uint32_t bits) {
-  const float v = __uint_as_float(bits) + 12582912.0f;
-  return __float_as_int(v) - 0x4B400000;
-}
-
-// v 2^sh into the 64-bit fixed-point sum (sh < 0: rounded to nearest)
-__device__ __forceinline__ long long shifted(int v, int sh) {
-  if (sh >= 0) return (long long)v << sh;
-  return ((long long)v + (1ll << (-sh - 1))) >> (-sh);
-}
-
+__host__ __device__ constexpr uint32_t idesc_oz() { return idesc_f16(BM, BN, false); }
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               int a_slice_rows, int b_slice_rows, int m, int n, int kblocks, int mtiles, int ntiles,
@@ -364,45 +274,6 @@ __global__ void k_oz_mirror(double2 *C, int ldc, int n) {
 }
 
 // ------------------------------------------------------------- slicing ----
-// |x| as ordered integer bits
-__device__ __forceinline__ unsigned long long abs_bits(double x) {
-  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-}
-// exponent e with max 2^e in [1/2, 1) from the bits of the row maximum
-__device__ __forceinline__ int row_exp(unsigned long long mb) {
-  const int ex = (int)(mb >> 52);
-  if (ex == 0) return 0;                 // zero (or subnormal) row: any scale works
-  return 1022 - ex;                      // max in [2^(ex-1023), 2^(ex-1022)) -> [1/2, 1)
-}
-// the S digits of x 2^e (|x 2^e| < 1), as FP16 integers: the fixed-point value
-// F = round(x 2^(e + 56)) is peeled from the top, BETA bits at a time, each
-// digit rounded to nearest (integer arithmetic only)
-__device__ __forceinline__ void digits(double x, int e, __half *out) {
-  const long long b = __double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  long long F = 0;
-  if (ex != 0) {
-    const long long mant = (b & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;   // 53 bits
-    const int sa = ex - 1075 + e + 56;                                     // F = mant 2^sa
-    if (sa >= 0) F = mant << sa;
-    else if (sa > -64) F = (mant + (1ll << (-sa - 1))) >> (-sa);
-    if (b < 0) F = -F;
-  }
-#pragma unroll
-  for (int p = 1; p <= S; ++p) {
-    const int sh = 56 - BETA * p;
-    long long dgt;
-    if (sh > 0) {
-      dgt = (F + (1ll << (sh - 1))) >> sh;
-      F -= dgt << sh;
-    } else {
-      dgt = F;
-      F = 0;
-    }
-    out[p - 1] = __int2half_rn((int)dgt);
-  }
-}
-
 // Slices of the real rows of an operand.  The complex "row" r over k is
 //   contiguous:  v_kappa = X[kappa + r ld]      (a column of X)
 //   strided:     v_kappa = X[r + kappa ld]      (a row of X)

@@ -52,18 +52,20 @@ def test_heev_argument_errors():
     assert B._heev(4, 5, ct.c_void_p(1), ct.c_void_p(1), ct.c_void_p(1), st) == B.PW_ERR_ARG
 
 
-@pytest.mark.parametrize("mode,coop", [(0, 0), (1, 0), (1, 1)])
-def test_heev_large_both_product_modes(mode, coop):
+@pytest.mark.parametrize("mode,panels", [(0, 0), (1, 0), (1, 1), (1, 2)])
+def test_heev_large_both_product_modes(mode, panels):
     # order 1,700: the panel updates, back-transformation and their K-split
     # products run on the FP64-accurate tensor-core path (mode 1) or the FP64
-    # pipe (mode 0), the Householder columns as chained kernels (coop 0) or
-    # one cooperative launch per panel (coop 1); all match LAPACK at the same
-    # tolerances
+    # pipe (mode 0); the Householder columns as chained kernels with the
+    # Hermitian products of the large panels on the tensor cores (panels 0,
+    # mode 1), one cooperative launch per panel (panels 1) or chained kernels
+    # with every Hermitian product on the FP64 pipe (panels 2); all match
+    # LAPACK at the same tolerances
     import paper_2406_10765_gb300 as pw
     n, nb = 1700, 600
     A = _herm(n, 17, "rand")
     pw.pw_dense_products(mode)
-    pw.pw_householder_panels(coop)
+    pw.pw_householder_panels(panels)
     try:
         w, Y = pw.pw_heev(torch.from_numpy(A).cuda(), nb)
         torch.cuda.synchronize()
@@ -80,15 +82,16 @@ def test_heev_large_both_product_modes(mode, coop):
 
 
 def test_heev_cooperative_panels_match_chained():
-    # the cooperative panel kernel runs the chained kernels' arithmetic in the
-    # same order (the compiler may contract multiply-adds differently in the
-    # two kernels, so the last bits can differ): eigenvalues to rounding and
-    # the same wanted subspace, on small and ragged orders
+    # the cooperative panel kernel runs the FP64-pipe chained kernels'
+    # arithmetic in the same order (the compiler may contract multiply-adds
+    # differently in the two kernels, so the last bits can differ):
+    # eigenvalues to rounding and the same wanted subspace, on small and
+    # ragged orders
     import paper_2406_10765_gb300 as pw
     for n, nb in [(2, 1), (33, 11), (130, 40), (515, 170)]:
         A = _herm(n, n + 3, "rand")
         out = []
-        for coop in (0, 1):
+        for coop in (2, 1):
             pw.pw_householder_panels(coop)
             try:
                 w, Y = pw.pw_heev(torch.from_numpy(A).cuda(), nb)
@@ -101,3 +104,44 @@ def test_heev_cooperative_panels_match_chained():
         Ya, Yb = out[0][1], out[1][1]
         assert np.abs(Ya @ Ya.conj().T - Yb @ Yb.conj().T).max() < 1e-10, n
         assert np.abs(A @ Yb - Yb * out[1][0][:nb]).max() < 1e-12 * scale, n
+
+
+@pytest.mark.parametrize("n,nb,kind", [(513, 171, "rand"), (640, 200, "degenerate"), (1000, 333, "cluster"),
+                                       (1301, 420, "rand"), (700, 250, "range")])
+def test_heev_tensor_hermitian_products_match_fp64(n, nb, kind):
+    # the Hermitian products of the panels with trailing order >= 512 on the
+    # tensor cores (slices of the trailing matrix) against the same chain on
+    # the FP64 pipe, and both against LAPACK: ragged orders (partial 128-row
+    # tiles, a panel boundary inside a tile), degenerate and clustered
+    # spectra, and a matrix whose entries span six orders of magnitude (one
+    # scale for the whole trailing matrix: the error is normwise; the FP64
+    # products on the tensor cores are accurate relative to row and column
+    # maxima, so much wider ranges lose digits against LAPACK in either mode)
+    import paper_2406_10765_gb300 as pw
+    if kind == "range":
+        rng = np.random.default_rng(n)
+        d = 10.0 ** rng.uniform(-3, 3, n)
+        M = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        A = (M + M.conj().T) * np.sqrt(np.outer(d, d)) * 1e-6 + np.diag(d)
+    else:
+        A = _herm(n, n + 5, kind)
+    ref = np.linalg.eigvalsh(A)
+    scale = max(1.0, np.abs(ref).max())
+    out = []
+    for panels in (0, 2):
+        pw.pw_householder_panels(panels)
+        try:
+            w, Y = pw.pw_heev(torch.from_numpy(A).cuda(), nb)
+            torch.cuda.synchronize()
+        finally:
+            pw.pw_householder_panels(0)
+        w, Y = w.cpu().numpy(), Y.cpu().numpy()
+        assert np.abs(w - ref).max() < 1e-13 * scale * n ** 0.5, (panels, np.abs(w - ref).max() / scale)
+        assert np.abs(A @ Y - Y * w[:nb]).max() < 1e-12 * scale, panels
+        assert np.abs(Y.conj().T @ Y - np.eye(nb)).max() < 1e-12, panels
+        out.append((w, Y))
+    assert np.abs(out[0][0] - out[1][0]).max() < 1e-13 * scale * n ** 0.5
+    if kind == "rand":
+        # a gap after the wanted pairs: the same wanted subspace
+        Ya, Yb = out[0][1], out[1][1]
+        assert np.abs(Ya @ Ya.conj().T - Yb @ Yb.conj().T).max() < 1e-9
