@@ -37,14 +37,9 @@ E2E_STEPS = 20                      # e2e: full steps (tol 0, no locking) throug
 SOLVE_TOL, SOLVE_MAXIT = 5e-6, 200  # time to solution (Si-512 mixed converges in ~120 steps)
 REF_TOL, REF_MAXIT = 5e-7, 80       # FP64 reference solve started from the mixed result
 DEPS_TARGET = 1e-6                  # |delta eps| of the metric, Ha
-# DRAM bytes (read + write) of one instance of a sub-stage, from one ncu
-# capture of the same kernels: (stage, n, nb) -> (bytes, summary)
-# DRAM bytes per stage from an ncu capture of the same kernels, when the
-# kernels have not changed since (else traffic is null with a note)
-# DRAM bytes of the dominant stage per instance, scaled from a one-kernel
-# capture (profiles/householder_phemv_n3456.md: k_phemv at m = 3,255, 16.7 B
-# per lower-triangle entry, times n^3 / 6 entries for the whole reduction)
-NCU_TRAFFIC = {("tridiag", 3456, 1152): 16.73 * 3456 ** 3 / 6}
+# Householder reduction: panels of 32 columns whose trailing order is at
+# least this run their Hermitian products on the tensor cores
+HS_MIN_ORDER = 512
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of the part (no FP64 tensor path)
 FP32_PEAK_TFLOPS = 80.5     # nominal FP32 rate: 152 SMs x 128 lanes x 2 x 2.07 GHz
 METRIC = "Si-512 eigensolver iters/s"
@@ -242,69 +237,78 @@ def measured_peaks():
         return {}
 
 
-def roofline(stage, rr_part, fl, n, nb, precision, fft=None):
-    """Roofline of the dominant sub-stage, timed by the solver's CUDA events,
-    plus the per-stage fractions.
+def hemv_slice_bytes(n):
+    """Digit-slice bytes the tensor-core Hermitian products of the Householder
+    reduction stream: each column c of a panel (32 columns from j0) whose
+    trailing order n - j0 - 1 is at least HS_MIN_ORDER reads every lower
+    trailing tile (128 x 128, real and imaginary parts, eight FP16 slices:
+    512 KB) from tile (c + 1) // 128 on."""
+    nt = (n + 127) // 128
+    total = 0
+    for j0 in range(0, n - 1, 32):
+        if n - j0 - 1 < HS_MIN_ORDER:
+            break
+        for c in range(j0, min(j0 + 32, n - 1)):
+            ntp = nt - (c + 1) // 128
+            total += ntp * (ntp + 1) // 2 * 512 * 1024
+    return total
 
-    FP64-ALU work: the Householder reduction's Hermitian matrix-vector
-    products, sum_c 8 (n - c)^2 = 8 n^3 / 3 flop (its rank-64 panel updates,
-    the other 8 n^3 / 3, and every other product of the Rayleigh-Ritz solve
-    run on the FP64-accurate tensor-core path), against the nominal FP64 rate.
-    Tensor-core stages count the tensor flops they issue (split-FP16: three
-    slice products per real multiply-add) against the measured sustained
-    16-bit rate.  The FFT stage counts its algorithmic c64 bytes against the
-    measured HBM copy rate and its flops against the nominal FP32 rate.
+
+def roofline(stage, rr_part, fl, n, nb, precision, fft=None):
+    """Roofline of the dominant kernel, timed by the solver's CUDA events,
+    plus the per-stage figures.
+
+    Mixed precision: the dominant kernel is the split-FP16 tcgen05 GEMM
+    (k_tc_gemm: S^H S, S M, H S M, S~^H H S~ and the rotations); it counts the
+    tensor flops it issues (three slice products per real multiply-add) over
+    its three stages' time against the measured sustained 16-bit rate.  The
+    Householder stage counts the digit-slice bytes its tensor-core Hermitian
+    products stream against the measured HBM copy rate (its time also holds
+    the per-column FP64 kernels, the slicing and the panel updates).  The FFT
+    stage counts its algorithmic c64 bytes against the HBM rate and its flops
+    against the nominal FP32 rate.
     """
     mixed = precision == "mixed"
     parts = {k: v for k, v in stage.items() if k != "rr"}
     parts.update(rr_part)
-    names = {"tridiag": "Householder reduction: k_phemv + k_pcol + k_prows (FP64 ALU), panel updates on "
-                        "the FP64-accurate tensor-core product",
-             "chol_inv": "Cholesky + triangular inverse (k_potf2, k_trsm_inv, k_trinv_small, k_oz_gemm)",
-             "backtransform": "compact-WY back-transformation (k_build_T + k_oz_gemm)",
-             "transform": "S~ = S M, H S~ = HS M, S~^H H S~ (k_tc_gemm)", "dc": "divide and conquer (k_dc_*)",
-             "gram": "S^H S (k_tc_gemm)", "rot": "rotations (k_tc_gemm)",
-             "hpsi": "H on [X W P] (FFT kernels + projector k_tc_gemm)", "resid": "residuals"}
-    dom = max(parts, key=parts.get)
-    t_ms = parts[dom]
-    roof = {"bound": None, "kernel": names.get(dom, dom), "stage": dom, "ms": t_ms}
     peaks = measured_peaks()
     tc_peak = peaks.get("bf16_tflops_sustained")
     hbm = peaks.get("hbm_gbs")
-    hemv_flops = 8.0 * n ** 3 / 3
-    if dom == "tridiag":
-        ach = hemv_flops / (t_ms * 1e-3) / 1e12
-        roof.update(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s", frac=ach / FP64_PEAK_TFLOPS,
-                    traffic=NCU_TRAFFIC.get(("tridiag", n, nb)),
-                    traffic_source="profiles/householder_phemv_n3456.md (k_phemv bytes per entry, scaled "
-                                   "to the n^3/6 entries of the reduction)" if ("tridiag", n, nb) in NCU_TRAFFIC
-                    else None, algorithmic_flops=hemv_flops,
-                    peak_source="nominal FP64 rate: 152 SMs x 2.07 GHz x 2 DFMA/clk (measured DFMA 1.20); "
-                                "FP64 work counted: the Hermitian products, 8 n^3 / 3")
-    elif dom in ("gram", "rot", "transform") and mixed and tc_peak:
-        tfl = 3 * tc_flops(dom, fl, n, nb)
+    tc_stages = [k for k in ("gram", "transform", "rot") if parts.get(k)]
+    if mixed and tc_peak and tc_stages:
+        t_ms = sum(parts[k] for k in tc_stages)
+        tfl = sum(3 * tc_flops(k, fl, n, nb) for k in tc_stages)
         ach = tfl / (t_ms * 1e-3) / 1e12
-        roof.update(bound="tensor", achieved=ach, peak=tc_peak, unit="TFLOP/s", frac=ach / tc_peak, traffic=None,
-                    peak_source="of measured: bf16 sustained (fp16 has the same nominal rate)")
+        roof = {"bound": "tensor", "kernel": "k_tc_gemm (split-FP16 tcgen05 GEMM: S^H S; S M, H S M, "
+                                              "S~^H H S~; rotations)",
+                "stage": "tc_gemm", "ms": t_ms, "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s",
+                "frac": ach / tc_peak, "traffic": None, "algorithmic_flops": tfl,
+                "peak_source": "of measured: bf16 sustained (fp16 has the same nominal rate)"}
+    else:
+        dom = max(parts, key=parts.get)
+        roof = {"bound": None, "kernel": dom, "stage": dom, "ms": parts[dom]}
     # per-stage figures
     st = {}
     if mixed and tc_peak:
-        for k in ("gram", "transform", "rot"):
-            if parts.get(k):
-                tfl = 3 * tc_flops(k, fl, n, nb)
-                a = tfl / (parts[k] * 1e-3) / 1e12
-                st["tc_gemm_" + k] = {"ms": parts[k], "tensor_tflops": a, "peak": tc_peak, "frac": a / tc_peak,
-                                      "unit": "TFLOP/s (split-FP16 slice products, of measured sustained)"}
+        for k in tc_stages:
+            tfl = 3 * tc_flops(k, fl, n, nb)
+            a = tfl / (parts[k] * 1e-3) / 1e12
+            st["tc_gemm_" + k] = {"ms": parts[k], "tensor_tflops": a, "peak": tc_peak, "frac": a / tc_peak,
+                                  "unit": "TFLOP/s (split-FP16 slice products, of measured sustained)"}
     if fft and hbm:
         a = fft["bytes"] / (fft["ms"] * 1e-3) / 1e9
         f = fft["flops"] / (fft["ms"] * 1e-3) / 1e12
         st["fft"] = {"ms": fft["ms"], "bands": fft["bands"], "achieved_gbs": a, "hbm_peak_gbs": hbm,
                      "frac_hbm": a / hbm, "tflops": f, "fp32_peak_tflops": FP32_PEAK_TFLOPS,
                      "frac_fp32": f / FP32_PEAK_TFLOPS, "bytes": fft["bytes"], "source": fft["source"]}
-    if parts.get("tridiag"):
-        a = hemv_flops / (parts["tridiag"] * 1e-3) / 1e12
-        st["householder_fp64"] = {"ms": parts["tridiag"], "tflops": a, "peak": FP64_PEAK_TFLOPS,
-                                  "frac": a / FP64_PEAK_TFLOPS}
+    if parts.get("tridiag") and hbm:
+        sb = hemv_slice_bytes(n)
+        a = sb / (parts["tridiag"] * 1e-3) / 1e9
+        st["householder"] = {"ms": parts["tridiag"], "hemv_slice_bytes": sb, "achieved_gbs": a,
+                             "hbm_peak_gbs": hbm, "frac_hbm": a / hbm,
+                             "note": "slice bytes of the tensor-core Hermitian products over the whole "
+                                     "reduction's time (which also holds k_pcol, k_prows, the slicing and "
+                                     "the panel updates)"}
     roof["stages"] = st
     roof["stage_ms"] = stage
     roof["rr_ms"] = rr_part

@@ -13,25 +13,20 @@ def _stage(rr_ms):
     return {"resid": 3.0, "hpsi": 80.0, "gram": 19.0, "rr": sum(rr_ms.values()), "rot": 22.0}
 
 
-def test_roofline_dominant_fp64_stage():
+def test_hemv_slice_bytes():
     import bench
-    n, nb = 3456, 1152
-    rr = {"chol_inv": 41.0, "transform": 60.0, "tridiag": 204.0, "dc": 47.0, "backtransform": 25.0}
-    fl = bench.step_flops(104415, nb, n, nb, 2048, (96, 96, 96), hcols=n)
-    roof = bench.roofline(_stage(rr), rr, fl, n, nb, "mixed")
-    assert roof["stage"] == "tridiag" and roof["bound"] == "alu"
-    # FP64-ALU work of the Householder reduction: the Hermitian products,
-    # sum_c 8 (n - c)^2 = 8 n^3 / 3 flop, over the stage's time
-    ach = 8 * n ** 3 / 3 / 0.204 / 1e12
-    assert math.isclose(roof["achieved"], ach, rel_tol=1e-12)
-    assert math.isclose(roof["frac"], ach / bench.FP64_PEAK_TFLOPS, rel_tol=1e-12)
-    assert roof["unit"] == "TFLOP/s" and roof["ms"] == 204.0
-    # DRAM traffic of the reduction, scaled from the one-kernel capture
-    assert math.isclose(roof["traffic"], 16.73 * n ** 3 / 6)
-    other = bench.roofline(_stage(rr), rr, fl, 3000, nb, "mixed")
-    assert other["traffic"] is None
-    st = roof["stages"]
-    assert math.isclose(st["householder_fp64"]["frac"], roof["frac"])
+    # below the threshold every Hermitian product runs on the FP64 pipe
+    assert bench.hemv_slice_bytes(512) == 0
+    # order 513: one panel (columns 0..31, trailing order 512); five 128-row
+    # tile rows, 15 lower tiles of 512 KB read per column
+    assert bench.hemv_slice_bytes(513) == 32 * 15 * 512 * 1024
+    # order 700: panels at 0, 32, 64, 96, 128, 160 (trailing order >= 512);
+    # six tile rows; columns 127..191 start at tile 1 (15 tiles), the rest
+    # at tile 0 (21 tiles)
+    assert bench.hemv_slice_bytes(700) == (127 * 21 + 65 * 15) * 512 * 1024
+    # roughly 16 bytes per real entry of the lower triangle per column
+    n = 3456
+    assert 0.9 < bench.hemv_slice_bytes(n) / (32 * n ** 3 / 6) < 1.3
 
 
 def test_roofline_tensor_stage_counts():
@@ -41,16 +36,25 @@ def test_roofline_tensor_stage_counts():
     fl = bench.step_flops(npw, nb, n, nb, 2048, (96, 96, 96), hcols=n)
     roof = bench.roofline(_stage(rr) | {"hpsi": 0.1, "gram": 19.0, "rot": 22.0, "resid": 0.1}, rr, fl, n, nb,
                           "mixed")
-    assert roof["stage"] == "transform"
     peak = bench.measured_peaks().get("bf16_tflops_sustained")
     if peak:
-        # S M and H S M (triangular M: half of 8 npw n^2 each) and S~^H H S~
-        # (Hermitian half), three split-FP16 slice products each
-        t = 3 * (2 * 4.0 * npw * n * n + 4.0 * npw * n * n)
-        assert roof["bound"] == "tensor"
-        assert math.isclose(roof["achieved"], t / 60e-3 / 1e12, rel_tol=1e-12)
+        # the split-FP16 GEMM over its three stages: S^H S (Hermitian half,
+        # 4 npw n^2), S M and H S M (triangular M: half of 8 npw n^2 each) and
+        # S~^H H S~ (Hermitian half), the rotations S~ Y and S C_P (C_P's
+        # first nb rows zero); three split-FP16 slice products each
+        t_gram = 4.0 * npw * n * n
+        t_tr = 2 * 4.0 * npw * n * n + 4.0 * npw * n * n
+        t_rot = 8.0 * npw * n * nb + 8.0 * npw * (n - nb) * nb
+        assert roof["stage"] == "tc_gemm" and roof["bound"] == "tensor"
+        assert math.isclose(roof["ms"], 19.0 + 60.0 + 22.0)
+        assert math.isclose(roof["achieved"], 3 * (t_gram + t_tr + t_rot) / 101e-3 / 1e12, rel_tol=1e-12)
+        assert math.isclose(roof["frac"], roof["achieved"] / peak, rel_tol=1e-12)
         g = roof["stages"]["tc_gemm_gram"]
-        assert math.isclose(g["tensor_tflops"], 3 * 4.0 * npw * n * n / 19e-3 / 1e12, rel_tol=1e-12)
+        assert math.isclose(g["tensor_tflops"], 3 * t_gram / 19e-3 / 1e12, rel_tol=1e-12)
+    hbm = bench.measured_peaks().get("hbm_gbs")
+    if hbm:
+        h = roof["stages"]["householder"]
+        assert math.isclose(h["achieved_gbs"], bench.hemv_slice_bytes(n) / 2e-3 / 1e9, rel_tol=1e-12)
 
 
 def test_step_flops_model():
