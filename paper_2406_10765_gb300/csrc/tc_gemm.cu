@@ -165,6 +165,26 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// 32 columns into TMEM; the caller waits (tcgen05.wait::st) before the
+// columns are read again
+__device__ __forceinline__ void tmem_st32_async(uint32_t taddr, const float *v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
@@ -184,12 +204,21 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-// error-free sum s + x = t + err, err accumulated into e
-__device__ __forceinline__ void two_sum_acc(float &s, float &e, float x) {
-  const float t = s + x;
-  const float z = t - s;
-  e += (s - (t - z)) + (x - z);
-  s = t;
+// error-free sums s + x = t + err (Knuth's two-sum: t = s + x, z = t - s,
+// err = (s - (t - z)) + (x - z)), err accumulated into e, on two lanes of
+// packed FP32: one instruction per two round-to-nearest additions
+__device__ __forceinline__ void two_sum_acc2(float &s0, float &s1, float &e0, float &e1, float x0, float x1) {
+  const float2 s = make_float2(s0, s1), x = make_float2(x0, x1);
+  const float2 t = __fadd2_rn(s, x);
+  const float2 z = __fadd2_rn(t, make_float2(-s.x, -s.y));
+  const float2 u = __fadd2_rn(t, make_float2(-z.x, -z.y));
+  const float2 a = __fadd2_rn(s, make_float2(-u.x, -u.y));
+  const float2 b = __fadd2_rn(x, make_float2(-z.x, -z.y));
+  const float2 e = __fadd2_rn(make_float2(e0, e1), __fadd2_rn(a, b));
+  s0 = t.x;
+  s1 = t.y;
+  e0 = e.x;
+  e1 = e.y;
 }
 
 // Epilogue destinations (complex128 output, column-major, ldc):
@@ -368,9 +397,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         float v[32], e[32];
         tmem_ld32x2(base + c0, cmp_base + c0, v, e);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) two_sum_acc(sum[c0 + i], e[i], v[i]);
-        tmem_st32(cmp_base + c0, e);
+        for (int i = 0; i < 32; i += 2) two_sum_acc2(sum[c0 + i], sum[c0 + i + 1], e[i], e[i + 1], v[i], v[i + 1]);
+        tmem_st32_async(cmp_base + c0, e);
       }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce[b]);
