@@ -52,6 +52,7 @@ constexpr int EPI_COLS = BN / 2;
 // (~2.5e-8 relative per MMA); two blocks keep the bias below ~1e-6
 constexpr int CHUNK_KB = 2;
 constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
+constexpr int GROUP_M = 16;                  // tile rows per group of the launch order
 constexpr long long WAIT_CYCLES = 2000000000ll;   // ~1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -272,9 +273,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t *acce = accf + 2;             // [2] accumulator drained
   uint32_t *tmem_slot = (uint32_t *)(acce + 2);
 
+  // grouped tile order: GROUP_M tile rows at a time, the row index varying
+  // fastest, so that a wave of CTAs shares a few A row blocks and B column
+  // blocks (its operands stay in L2) instead of sweeping all of B
   const int tile = blockIdx.x;
-  const int mt = tile / ntiles, nt = tile % ntiles;
-  if (mt >= mtiles) return;
+  const int grp = tile / (GROUP_M * ntiles), m_first = grp * GROUP_M;
+  const int gsz = min(GROUP_M, mtiles - m_first), rem = tile - grp * GROUP_M * ntiles;
+  const int mt = m_first + rem % gsz, nt = rem / gsz;
+  if (mt >= mtiles || nt >= ntiles) return;
   const int m0 = mt * BM, n0 = nt * BN;
   // Hermitian products: skip tiles strictly below the diagonal (rows are
   // interleaved re/im pairs of output row i = r / 2)
