@@ -28,15 +28,12 @@
 namespace cg = cooperative_groups;
 
 #include "dense.cuh"
+#include "house.cuh"
 
 namespace {
 
 constexpr double kEps = 2.220446049250313e-16;
 
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 __device__ __forceinline__ double warp_prod(double v) {
   for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -46,24 +43,6 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// block-wide sum of one double (blockDim.x multiple of 32, <= 1024)
-__device__ double block_sum(double v, double *sh) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (threadIdx.x < 32) {
-    r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-    r = warp_sum(r);
-    if (threadIdx.x == 0) sh[0] = r;
-  }
-  __syncthreads();
-  r = sh[0];
-  __syncthreads();
-  return r;
-}
 __device__ double block_max(double v, double *sh) {
   v = warp_max(v);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -317,9 +296,6 @@ constexpr int TPB = 32;
 // before it reads anything the predecessor wrote, and only then lets its own
 // successor launch.  So before its wait a kernel may read data written two or
 // more launches back (k_phemv loads its tile of the trailing matrix there).
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg = {};
@@ -336,70 +312,15 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, cu
 }
 constexpr int PCOL_THREADS = 128;
 
-// s += a b and s += conj(a) b, four FMAs each
-__device__ __forceinline__ void cmac(double2 &s, double2 a, double2 b) {
-  s.x = fma(a.x, b.x, s.x);
-  s.x = fma(-a.y, b.y, s.x);
-  s.y = fma(a.x, b.y, s.y);
-  s.y = fma(a.y, b.x, s.y);
-}
-__device__ __forceinline__ void cmacc(double2 &s, double2 a, double2 b) {
-  s.x = fma(a.x, b.x, s.x);
-  s.x = fma(a.y, b.y, s.x);
-  s.y = fma(a.x, b.y, s.y);
-  s.y = fma(-a.y, b.x, s.y);
-}
-
-// alpha = -1/2 tau (p^H v) from the per-block partial dots (block-wide sum)
-// (stride: the partial sums run over `stride` threads, blockDim.x by default;
-// the cooperative panel kernel uses k_pcol's 128 to reproduce its sums)
-__device__ double2 panel_alpha(const double2 *dotpart, int ndot, double2 t, double *sh, int stride = 0) {
-  double sr = 0.0, si = 0.0;
-  const int st = stride > 0 ? stride : (int)blockDim.x;
-  for (int q = threadIdx.x; q < ndot && (int)threadIdx.x < st; q += st) {
-    const double2 v = __ldcg(&dotpart[q]);
-    sr += v.x;
-    si += v.y;
-  }
-  sr = block_sum(sr, sh);
-  si = block_sum(si, sh);
-  return cmul(make_double2(-0.5 * t.x, -0.5 * t.y), make_double2(sr, si));
-}
-
-// v_c entry x (x = row - (c+1)) from the stored column and the scale
-__device__ __forceinline__ double2 refl_entry(const double2 *xcol, int x, double2 scal) {
-  return x == 0 ? make_double2(1.0, 0.0) : cmul(xcol[x], scal);
-}
-
-// Sum over the 32 lanes of each of 32 values per lane, by halving exchanges
-// (31 shuffles): lane L returns the sum of component L.
-__device__ __forceinline__ double warp_transpose_sum(double (&v)[32]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int bit = 16; bit >= 1; bit >>= 1) {
-    const bool up = (lane & bit) != 0;
-#pragma unroll
-    for (int j = 0; j < bit; ++j) {
-      const double send = up ? v[j] : v[j + bit];
-      const double keep = up ? v[j + bit] : v[j];
-      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
-    }
-  }
-  return v[0];
-}
-
 // 32 rows per block; the four warps split the panel's previous updates
-// (q = warp mod 4) so that the FP64 work lands on all four SM sub-partitions.
-// With dotp, also the block's partial dots W[:, q]^H x and V[:, q]^H x (q < i)
-// over the rows below the reflector's head (rows >= c + 2), for the
-// tensor-core Hermitian product: dotp[block * 64 + 2q (W) / 2q + 1 (V)].
+// (q = warp mod 4) so that the FP64 work lands on all four SM sub-partitions
 __global__ void __launch_bounds__(PCOL_THREADS) k_pcol(double2 *A, int n, int c, int i, double2 *P, int b,
                                                        const double2 *p, const double2 *dotpart, int ndot,
                                                        double2 *tau, double *d, double *e, double *nrm_part,
-                                                       double2 *hscal, unsigned *ticket, double2 *dotp) {
+                                                       double2 *hscal, unsigned *ticket) {
   __shared__ double sh[32];
   __shared__ unsigned s_ticket;
-  __shared__ double2 s_vc[TPB], s_wc[TPB], s_u[4][33], s_x[32];
+  __shared__ double2 s_vc[TPB], s_wc[TPB], s_u[4][33];
   double2 *V = P, *W = P + (long)b * n;
   const int rl = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int r = c + blockIdx.x * 32 + rl;
@@ -447,7 +368,6 @@ __global__ void __launch_bounds__(PCOL_THREADS) k_pcol(double2 *A, int n, int c,
           wq = __ldcg(&p[r - c]);
           cmac(wq, al, vq);
           W[r + (long)q * n] = wq;
-          wq_r[t] = wq;
         }
         cmacc(u, s_wc[q], vq);
         cmacc(u, s_vc[q], wq);
@@ -462,30 +382,6 @@ __global__ void __launch_bounds__(PCOL_THREADS) k_pcol(double2 *A, int n, int c,
       a = csub(a, cadd(cadd(s_u[0][rl], s_u[1][rl]), cadd(s_u[2][rl], s_u[3][rl])));
       A[r + (long)c * n] = a;
     }
-  }
-  if (dotp && i > 0) {
-    if (g == 0) s_x[rl] = (r < n && r > c + 1) ? a : make_double2(0.0, 0.0);
-    __syncthreads();
-    const double2 x = s_x[rl];
-    double v[32];
-#pragma unroll
-    for (int t = 0; t < QMAX; ++t) {
-      const int q = g + 4 * t;
-      double2 dw = make_double2(0.0, 0.0), dv = make_double2(0.0, 0.0);
-      if (q < i) {
-        cmacc(dw, wq_r[t], x);
-        cmacc(dv, vq_r[t], x);
-      }
-      v[4 * t] = dw.x;
-      v[4 * t + 1] = dw.y;
-      v[4 * t + 2] = dv.x;
-      v[4 * t + 3] = dv.y;
-    }
-#pragma unroll
-    for (int t = QMAX; t < 8; ++t) v[4 * t] = v[4 * t + 1] = v[4 * t + 2] = v[4 * t + 3] = 0.0;
-    const double sum = warp_transpose_sum(v);
-    const int q = g + 4 * (rl >> 2);
-    if (q < i) ((double *)dotp)[2 * ((long)blockIdx.x * 64 + 2 * q + ((rl >> 1) & 1)) + (rl & 1)] = sum;
   }
   if (g != 0) return;
   double nrm = 0.0;
@@ -1513,8 +1409,7 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax) {
   ok = ok && get((void **)&ws->ticket, 64) && get((void **)&ws->panel, (size_t)nmax * 3 * TPB * 16) &&
        get((void **)&ws->ucorr, 2 * TPB * 16) && get((void **)&ws->hscal, 16) && get((void **)&ws->Li, CB * CB * 16) &&
        get((void **)&ws->nrm_part, (size_t)(nmax / 32 + 2) * 8) &&
-       get((void **)&ws->hsmax, (size_t)(nmax / TPB + 2) * 8) &&
-       get((void **)&ws->dotp, (size_t)(nmax / 32 + 2) * 64 * 16);
+       get((void **)&ws->hsmax, (size_t)(nmax / TPB + 2) * 8);
   if (ok && pw_hs_bytes(nmax)) {
     // zeroed once: a slice tile is only read where the panel's slicing wrote it
     ok = get(&ws->hsl, pw_hs_bytes(nmax)) && cudaMemset(ws->hsl, 0, pw_hs_bytes(nmax)) == cudaSuccess;
@@ -1550,7 +1445,7 @@ void pw_dense_free(pw_dense_ws *ws) {
                   ws->orig, ws->dcol, ws->src, ws->nodes, ws->knode, ws->rhonode, ws->ctype, ws->qL, ws->qR,
                   ws->kLR, ws->kneed, ws->gemm_ws,
                   ws->Vb, ws->Gv, ws->Tb, ws->Wk, ws->Wk2, ws->ticket, ws->panel, ws->ucorr,
-                  ws->hscal, ws->nrm_part, ws->Li, ws->hsl, ws->hsmax, ws->dotp};
+                  ws->hscal, ws->nrm_part, ws->Li, ws->hsl, ws->hsmax};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : ws->ev)
@@ -1568,6 +1463,25 @@ void pw_dense_stage_ms(pw_dense_ws *ws, float out[5]) {
 // ======================================================================
 // Hermitian eigensolver
 // ======================================================================
+// Cooperative grids fill the device; two of them partly resident at once
+// (concurrent solves on other streams) could each wait at a grid barrier for
+// blocks that only the other's exit would make room for.  So every
+// cooperative launch on a device is ordered after the previous one, through
+// one event recorded behind each launch (host mutex, then stream wait).
+pw_status pw_coop_ordered(cudaStream_t st, const std::function<pw_status()> &launch) {
+  static std::mutex mu;
+  static cudaEvent_t last[64] = {};
+  int dev = 0;
+  PW_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return PW_ERR_ARG;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!last[dev]) PW_CUDA(cudaEventCreateWithFlags(&last[dev], cudaEventDisableTiming));
+  else PW_CUDA(cudaStreamWaitEvent(st, last[dev], 0));
+  PW_TRY(launch());
+  PW_CUDA(cudaEventRecord(last[dev], st));
+  return PW_OK;
+}
+
 namespace {
 // The three stages of the eigensolver, each a fixed launch sequence for a
 // given (n, nb) on a given workspace (so each can be captured as a graph).
@@ -1599,25 +1513,13 @@ int coop_grid() {
   return grid[dev];
 }
 
-// Cooperative grids fill the device; two of them partly resident at once
-// (concurrent solves on other streams) could each wait at a grid barrier for
-// blocks that only the other's exit would make room for.  So every
-// cooperative launch on a device is ordered after the previous one, through
-// one event recorded behind each launch (host mutex, then stream wait).
 pw_status launch_panel_coop(cudaLaunchConfig_t &cfg, double2 *A, int n, int j0, int b, pw_dense_ws *ws) {
-  static std::mutex mu;
-  static cudaEvent_t last[64] = {};
-  int dev = 0;
-  PW_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return PW_ERR_ARG;
-  std::lock_guard<std::mutex> lk(mu);
-  if (!last[dev]) PW_CUDA(cudaEventCreateWithFlags(&last[dev], cudaEventDisableTiming));
-  else PW_CUDA(cudaStreamWaitEvent(cfg.stream, last[dev], 0));
-  pw_count_launch();
-  PW_CUDA(cudaLaunchKernelEx(&cfg, k_panel_coop, A, n, j0, b, ws->panel, ws->p, ws->w, ws->tau, ws->d, ws->e,
-                             ws->nrm_part, ws->hscal, ws->part, ws->nmax, ws->ucorr));
-  PW_CUDA(cudaEventRecord(last[dev], cfg.stream));
-  return PW_OK;
+  return pw_coop_ordered(cfg.stream, [&]() -> pw_status {
+    pw_count_launch();
+    PW_CUDA(cudaLaunchKernelEx(&cfg, k_panel_coop, A, n, j0, b, ws->panel, ws->p, ws->w, ws->tau, ws->d, ws->e,
+                               ws->nrm_part, ws->hscal, ws->part, ws->nmax, ws->ucorr));
+    return PW_OK;
+  });
 }
 
 // the reduction with one cooperative launch per panel (three grid barriers
@@ -1652,8 +1554,11 @@ pw_status stage_tridiag(pw_dense_ws *ws, int n, double2 *A, cudaStream_t st) {
   const int grid = mode == 1 ? coop_grid() : 0;
   if (grid > 0) return tridiag_coop(ws, n, A, grid, st);
   // Hermitian products on the tensor cores for the panels of trailing order
-  // >= PW_HS_MIN_ORDER (slices of each such panel's trailing matrix first)
-  const bool hs = mode == 0 && ws->hsl && pw_dense_products_mode() == 1 && n - 1 >= PW_HS_MIN_ORDER;
+  // >= PW_HS_MIN_ORDER (slices of each such panel's trailing matrix first):
+  // chained per column (mode 0) or one cooperative launch per panel (mode 3)
+  const bool hs = (mode == 0 || mode == 3) && ws->hsl && pw_dense_products_mode() == 1 &&
+                  n - 1 >= PW_HS_MIN_ORDER;
+  const int hgrid = hs && mode == 3 ? pw_hs_panel_grid() : 0;
   // 1. Householder tridiagonalisation: panels of TPB columns (lower triangle)
   PW_CUDA(cudaMemsetAsync(ws->ticket, 0, sizeof(unsigned), st));
   if (hs) PW_CUDA(cudaMemsetAsync(ws->hsmax, 0, (size_t)(n / TPB + 2) * 8, st));
@@ -1665,6 +1570,14 @@ pw_status stage_tridiag(pw_dense_ws *ws, int n, double2 *A, cudaStream_t st) {
       const bool ptc = hs && n - j0 - 1 >= PW_HS_MIN_ORDER;
       PW_CUDA(cudaMemsetAsync(ws->panel, 0, (size_t)n * 3 * b * sizeof(double2), st));
       if (ptc) PW_TRY(pw_hs_slice(ws, A, n, j0, st));
+      if (ptc && hgrid > 0) {
+        PW_TRY(pw_hs_panel(ws, A, n, j0, b, hgrid, st));
+        const int t = j0 + b, m2 = n - t;
+        if (m2 > 0)
+          PW_TRY(pw_dense_gemm(ws, 'N', 'C', m2, m2, 2 * b, mone, ws->panel + t, n, ws->panel + (long)b * n + t,
+                               n, one, A + t + (long)t * n, n, st, 2));
+        continue;
+      }
       int ndot = 0;
       for (int i = 0; i < b; ++i) {
         const int c = j0 + i, m = n - c - 1;
@@ -1672,11 +1585,11 @@ pw_status stage_tridiag(pw_dense_ws *ws, int n, double2 *A, cudaStream_t st) {
         pw_count_launch();
         PW_CUDA(launch_pdl(k_pcol, npcol, PCOL_THREADS, st, A, n, c, i, ws->panel, b,
                            (const double2 *)ws->p, (const double2 *)dotpart, ndot, ws->tau, ws->d, ws->e,
-                           ws->nrm_part, ws->hscal, ws->ticket, ptc ? ws->dotp : (double2 *)nullptr));
+                           ws->nrm_part, ws->hscal, ws->ticket));
         int s0 = 0, nT = (m + TT - 1) / TT;
         const double2 *part = ws->part;
         if (ptc) {
-          PW_TRY(pw_hs_hemv(ws, A, n, c, i, b, j0, npcol, &nT, st));
+          PW_TRY(pw_hs_hemv(ws, A, n, c, i, b, j0, &nT, st));
           part = ws->part + (c + 1);
         } else {
           const int ntiles = nT * (nT + 1) / 2, nwr = (m + 255) / 256;
@@ -1778,7 +1691,7 @@ std::atomic<int> g_graphs{1};
 // what a captured stage depends on besides its key: the product buffers'
 // generation, the product mode and the panel mode
 unsigned stage_gen(const pw_dense_ws *ws) {
-  return (2 * ws->oz.gen + (unsigned)pw_dense_products_mode()) * 3 + (unsigned)g_coop.load();
+  return (2 * ws->oz.gen + (unsigned)pw_dense_products_mode()) * 4 + (unsigned)g_coop.load();
 }
 
 // A stage through the workspace's graph cache: the first call of a key runs
@@ -1839,7 +1752,7 @@ pw_status run_stage(pw_dense_ws *ws, int stage, int n, int nb, const void *p0, c
 }  // namespace
 
 extern "C" pw_status pw_householder_panels(int mode) {
-  if (mode < 0 || mode > 2) return PW_ERR_ARG;
+  if (mode < 0 || mode > 3) return PW_ERR_ARG;
   g_coop.store(mode);
   return PW_OK;
 }
@@ -1857,7 +1770,7 @@ pw_status pw_heev_lowest(pw_dense_ws *ws, int n, int nb, double2 *A, double *lam
   if (ws->ev[2]) cudaEventRecord(ws->ev[2], st);
   // with cooperative panels the stage is ~5 launches per 32 columns and is
   // ordered across streams by an event, so it runs uncaptured
-  if (g_coop.load() == 1 && coop_grid() > 0) PW_TRY(stage_tridiag(ws, n, A, st));
+  if ((g_coop.load() == 1 && coop_grid() > 0) || g_coop.load() == 3) PW_TRY(stage_tridiag(ws, n, A, st));
   else PW_TRY(run_stage(ws, 0, n, nb, A, nullptr, st, [&] { return stage_tridiag(ws, n, A, st); }));
   // 2. divide and conquer (the merge tree is built and uploaded outside any capture)
   if (ws->ev[3]) cudaEventRecord(ws->ev[3], st);

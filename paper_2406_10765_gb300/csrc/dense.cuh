@@ -1,5 +1,7 @@
 // FP64 dense linear algebra of the Rayleigh-Ritz step, on the GPU.
 #pragma once
+#include <functional>
+
 #include "oz_gemm.cuh"
 #include "pw_internal.cuh"
 
@@ -49,10 +51,9 @@ struct pw_dense_ws {
   double2 *Li = nullptr;      // inverse of the current Cholesky diagonal block (CB x CB)
   // tensor-core Hermitian products of the reduction: digit slices of the
   // panel's trailing tiles, the trailing matrix's maximum per panel (ordered
-  // bits), k_pcol's partial dots W^H x, V^H x (64 per block)
+  // bits)
   void *hsl = nullptr;
   unsigned long long *hsmax = nullptr;
-  double2 *dotp = nullptr;
   double *nrm_part = nullptr;
   // host side tree for the current n
   int tree_n = -1;
@@ -91,8 +92,17 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax);
 #define PW_HS_MIN_ORDER 512
 size_t pw_hs_bytes(int nmax);
 pw_status pw_hs_slice(pw_dense_ws *ws, const double2 *A, int n, int j0, cudaStream_t st);
-pw_status pw_hs_hemv(pw_dense_ws *ws, const double2 *A, int n, int c, int i, int b, int j0, int ndotblk,
-                     int *nslots, cudaStream_t st);
+pw_status pw_hs_hemv(pw_dense_ws *ws, const double2 *A, int n, int c, int i, int b, int j0, int *nslots,
+                     cudaStream_t st);
+// All columns of the panel at j0 (width b, trailing order >= PW_HS_MIN_ORDER,
+// its slices written) in one cooperative launch of `grid` CTAs (from
+// pw_hs_panel_grid, 0 when the device cannot hold one per SM), leaving the
+// panel [V | W | V], tau, d, e as the chained kernels and k_pfinal do.
+int pw_hs_panel_grid();
+pw_status pw_hs_panel(pw_dense_ws *ws, double2 *A, int n, int j0, int b, int grid, cudaStream_t st);
+// Runs `launch` (one cooperative launch on st) after the previous
+// cooperative launch on the current device, whatever its stream.
+pw_status pw_coop_ordered(cudaStream_t st, const std::function<pw_status()> &launch);
 void pw_dense_free(pw_dense_ws *ws);
 
 // Lowest nb Ritz pairs of the pencil (A, G), both n x n Hermitian (device,

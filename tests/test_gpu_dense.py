@@ -52,15 +52,16 @@ def test_heev_argument_errors():
     assert B._heev(4, 5, ct.c_void_p(1), ct.c_void_p(1), ct.c_void_p(1), st) == B.PW_ERR_ARG
 
 
-@pytest.mark.parametrize("mode,panels", [(0, 0), (1, 0), (1, 1), (1, 2)])
+@pytest.mark.parametrize("mode,panels", [(0, 0), (1, 0), (1, 1), (1, 2), (1, 3)])
 def test_heev_large_both_product_modes(mode, panels):
     # order 1,700: the panel updates, back-transformation and their K-split
     # products run on the FP64-accurate tensor-core path (mode 1) or the FP64
     # pipe (mode 0); the Householder columns as chained kernels with the
     # Hermitian products of the large panels on the tensor cores (panels 0,
-    # mode 1), one cooperative launch per panel (panels 1) or chained kernels
-    # with every Hermitian product on the FP64 pipe (panels 2); all match
-    # LAPACK at the same tolerances
+    # mode 1), one cooperative launch per panel (panels 1), chained kernels
+    # with every Hermitian product on the FP64 pipe (panels 2) or one
+    # cooperative launch per large panel with its products on the tensor
+    # cores (panels 3); all match LAPACK at the same tolerances
     import paper_2406_10765_gb300 as pw
     n, nb = 1700, 600
     A = _herm(n, 17, "rand")
@@ -128,7 +129,7 @@ def test_heev_tensor_hermitian_products_match_fp64(n, nb, kind):
     ref = np.linalg.eigvalsh(A)
     scale = max(1.0, np.abs(ref).max())
     out = []
-    for panels in (0, 2):
+    for panels in (0, 2, 3):
         pw.pw_householder_panels(panels)
         try:
             w, Y = pw.pw_heev(torch.from_numpy(A).cuda(), nb)
@@ -140,8 +141,11 @@ def test_heev_tensor_hermitian_products_match_fp64(n, nb, kind):
         assert np.abs(A @ Y - Y * w[:nb]).max() < 1e-12 * scale, panels
         assert np.abs(Y.conj().T @ Y - np.eye(nb)).max() < 1e-12, panels
         out.append((w, Y))
-    assert np.abs(out[0][0] - out[1][0]).max() < 1e-13 * scale * n ** 0.5
+    for k in (1, 2):
+        assert np.abs(out[0][0] - out[k][0]).max() < 1e-13 * scale * n ** 0.5
     if kind == "rand":
         # a gap after the wanted pairs: the same wanted subspace
-        Ya, Yb = out[0][1], out[1][1]
-        assert np.abs(Ya @ Ya.conj().T - Yb @ Yb.conj().T).max() < 1e-9
+        Ya = out[0][1]
+        for k in (1, 2):
+            Yb = out[k][1]
+            assert np.abs(Ya @ Ya.conj().T - Yb @ Yb.conj().T).max() < 1e-9
