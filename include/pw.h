@@ -440,7 +440,10 @@ pw_status pw_dense_graphs(int on);
  * FP64 pipe.  mode = 1 (where the device supports cooperative launch): each
  * panel of 32 columns as one cooperative launch whose phases (column update,
  * Hermitian product on the FP64 pipe, row sums) are separated by grid-wide
- * barriers, its launches ordered one after another across streams.  All
+ * barriers.  mode = 3: as mode 0, with each panel that uses the tensor-core
+ * products run as one cooperative launch (one CTA per SM; column update,
+ * tensor-core product, row sums separated by grid-wide barriers).
+ * Cooperative launches are ordered one after another across streams.  All
  * modes give the same tridiagonal matrix to FP64 rounding.
  * Errors: PW_ERR_ARG. */
 pw_status pw_householder_panels(int mode);

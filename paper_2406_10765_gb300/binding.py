@@ -199,8 +199,9 @@ _hh_panels = _sig("pw_householder_panels", ct.c_int, [ct.c_int])
 
 def pw_householder_panels(mode):
     """0 (default): chained kernels per Householder column, Hermitian products of
-    large panels on the tensor cores; 1: one cooperative launch per panel; 2:
-    chained kernels, every Hermitian product on the FP64 pipe."""
+    large panels on the tensor cores; 1: one cooperative launch per panel (FP64
+    products); 2: chained kernels, every Hermitian product on the FP64 pipe;
+    3: as 0 with each tensor-core panel in one cooperative launch."""
     _check(_hh_panels(int(mode)), "pw_householder_panels")
 
 
