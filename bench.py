@@ -39,7 +39,7 @@ REF_TOL, REF_MAXIT = 5e-7, 80       # FP64 reference solve started from the mixe
 DEPS_TARGET = 1e-6                  # |delta eps| of the metric, Ha
 # Householder reduction: panels of 32 columns whose trailing order is at
 # least this run their Hermitian products on the tensor cores
-HS_MIN_ORDER = 512
+HS_MIN_ORDER = 1024
 FP64_PEAK_TFLOPS = 1.25     # nominal FP64 rate of the part (no FP64 tensor path)
 FP32_PEAK_TFLOPS = 80.5     # nominal FP32 rate: 152 SMs x 128 lanes x 2 x 2.07 GHz
 METRIC = "Si-512 eigensolver iters/s"

@@ -434,7 +434,7 @@ pw_status pw_dense_graphs(int on);
  * process-wide.  mode = 0 (default) chains three kernels per column with
  * programmatic dependent launch; while the product mode (pw_dense_products)
  * is 1, the Hermitian products A22 v of panels whose trailing order is at
- * least 512 run on the FP16 tensor cores at FP64 accuracy (the panel's
+ * least 1024 run on the FP16 tensor cores at FP64 accuracy (the panel's
  * trailing matrix split once into integer digit slices), the others on the
  * FP64 pipe.  mode = 2: the same chain with every Hermitian product on the
  * FP64 pipe.  mode = 1 (where the device supports cooperative launch): each

@@ -89,7 +89,7 @@ pw_status pw_dense_alloc(pw_dense_ws *ws, int nmax, int nbmax);
 // product for column c (panel index i, width b): partials into ws->part
 // (*nslots slots per row, part[s * nmax + row] with the global row index),
 // ucorr and v into the panel, as the FP64 k_phemv does.
-#define PW_HS_MIN_ORDER 512
+#define PW_HS_MIN_ORDER 1024
 size_t pw_hs_bytes(int nmax);
 pw_status pw_hs_slice(pw_dense_ws *ws, const double2 *A, int n, int j0, cudaStream_t st);
 pw_status pw_hs_hemv(pw_dense_ws *ws, const double2 *A, int n, int c, int i, int b, int j0, int *nslots,

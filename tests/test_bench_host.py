@@ -16,17 +16,17 @@ def _stage(rr_ms):
 def test_hemv_slice_bytes():
     import bench
     # below the threshold every Hermitian product runs on the FP64 pipe
-    assert bench.hemv_slice_bytes(512) == 0
-    # order 513: one panel (columns 0..31, trailing order 512); five 128-row
-    # tile rows, 15 lower tiles of 512 KB read per column
-    assert bench.hemv_slice_bytes(513) == 32 * 15 * 512 * 1024
-    # order 700: panels at 0, 32, 64, 96, 128, 160 (trailing order >= 512);
-    # six tile rows; columns 127..191 start at tile 1 (15 tiles), the rest
-    # at tile 0 (21 tiles)
-    assert bench.hemv_slice_bytes(700) == (127 * 21 + 65 * 15) * 512 * 1024
+    assert bench.hemv_slice_bytes(1024) == 0
+    # order 1025: one panel (columns 0..31, trailing order 1024); nine
+    # 128-row tile rows, 45 lower tiles of 512 KB read per column
+    assert bench.hemv_slice_bytes(1025) == 32 * 45 * 512 * 1024
+    # order 1200: panels at 0, 32, ..., 160 (trailing order >= 1024); ten
+    # tile rows; columns 127..191 start at tile 1 (45 tiles), the rest at
+    # tile 0 (55 tiles)
+    assert bench.hemv_slice_bytes(1200) == (127 * 55 + 65 * 45) * 512 * 1024
     # roughly 16 bytes per real entry of the lower triangle per column
     n = 3456
-    assert 0.9 < bench.hemv_slice_bytes(n) / (32 * n ** 3 / 6) < 1.3
+    assert 0.8 < bench.hemv_slice_bytes(n) / (32 * n ** 3 / 6) < 1.3
 
 
 def test_roofline_tensor_stage_counts():

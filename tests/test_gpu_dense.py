@@ -107,10 +107,10 @@ def test_heev_cooperative_panels_match_chained():
         assert np.abs(A @ Yb - Yb * out[1][0][:nb]).max() < 1e-12 * scale, n
 
 
-@pytest.mark.parametrize("n,nb,kind", [(513, 171, "rand"), (640, 200, "degenerate"), (1000, 333, "cluster"),
-                                       (1301, 420, "rand"), (700, 250, "range")])
+@pytest.mark.parametrize("n,nb,kind", [(1025, 341, "rand"), (1100, 300, "degenerate"), (1200, 333, "cluster"),
+                                       (1301, 420, "rand"), (1150, 250, "range")])
 def test_heev_tensor_hermitian_products_match_fp64(n, nb, kind):
-    # the Hermitian products of the panels with trailing order >= 512 on the
+    # the Hermitian products of the panels with trailing order >= 1024 on the
     # tensor cores (slices of the trailing matrix) against the same chain on
     # the FP64 pipe, and both against LAPACK: ragged orders (partial 128-row
     # tiles, a panel boundary inside a tile), degenerate and clustered
