@@ -404,17 +404,7 @@ __global__ void __launch_bounds__(PCOL_THREADS) k_pcol(double2 *A, int n, int c,
   const double2 alpha = __ldcg(&A[(c + 1) + (long)c * n]);
   double beta;
   double2 tk, scal;
-  if (xn2 == 0.0 && alpha.y == 0.0) {
-    beta = alpha.x;
-    tk = make_double2(0.0, 0.0);
-    scal = make_double2(0.0, 0.0);
-  } else {
-    beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2), alpha.x);
-    tk = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-    const double2 den = make_double2(alpha.x - beta, alpha.y);
-    const double qq = 1.0 / (den.x * den.x + den.y * den.y);
-    scal = make_double2(den.x * qq, -den.y * qq);
-  }
+  reflector_scalars(xn2, alpha, beta, tk, scal);
   d[c] = __ldcg(&A[c + (long)c * n]).x;
   tau[c] = tk;
   e[c] = beta;

@@ -706,17 +706,7 @@ __global__ void __launch_bounds__(NTHR_PANEL, 1) k_panel_tc(const __grid_constan
       const double xn2 = sh[0];
       __syncthreads();
       double beta;
-      if (xn2 == 0.0 && alpha.y == 0.0) {
-        beta = alpha.x;
-        tk = make_double2(0.0, 0.0);
-        scal = make_double2(0.0, 0.0);
-      } else {
-        beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2), alpha.x);
-        tk = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-        const double2 den = make_double2(alpha.x - beta, alpha.y);
-        const double qq = 1.0 / (den.x * den.x + den.y * den.y);
-        scal = make_double2(den.x * qq, -den.y * qq);
-      }
+      reflector_scalars(xn2, alpha, beta, tk, scal);
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.d[c] = __ldcg(&a.A[c + (long)c * n]).x;
         a.tau[c] = tk;

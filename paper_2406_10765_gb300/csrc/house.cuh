@@ -69,4 +69,22 @@ __device__ __forceinline__ double2 refl_entry(const double2 *xcol, int x, double
   return x == 0 ? make_double2(1.0, 0.0) : cmul(xcol[x], scal);
 }
 
+// Reflector of x = (alpha, x_2..) with ||x_2..||^2 = xn2: beta, tau and the
+// scale s of v = x s below its unit head (tau = 0 and s = 0 when x is
+// already a multiple of the first unit vector with a real head)
+__device__ __forceinline__ void reflector_scalars(double xn2, double2 alpha, double &beta, double2 &tk,
+                                                  double2 &scal) {
+  if (xn2 == 0.0 && alpha.y == 0.0) {
+    beta = alpha.x;
+    tk = make_double2(0.0, 0.0);
+    scal = make_double2(0.0, 0.0);
+  } else {
+    beta = -copysign(sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2), alpha.x);
+    tk = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+    const double2 den = make_double2(alpha.x - beta, alpha.y);
+    const double qq = 1.0 / (den.x * den.x + den.y * den.y);
+    scal = make_double2(den.x * qq, -den.y * qq);
+  }
+}
+
 }  // namespace
