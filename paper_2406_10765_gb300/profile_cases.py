@@ -10,6 +10,8 @@ times after one warm-up):
   step512mix  one mixed-precision LOBPCG step on the Si 512-atom cell (the
               bench workload; solver creation included)
   tcgemm      split-FP16 tensor-core A^H A, A: 104,415 x 1,152 complex
+  smgemm      split-FP16 tensor-core S M, S: 30,000 x 3,456, M: 3,456 x 3,456
+              complex (the shape class of the Rayleigh-Ritz transform S M)
   heev        FP64 Hermitian eigensolver, n = 1,152 (Householder, D&C);
               --n 3456 gives the Si-512 Rayleigh-Ritz order
   ozgemm      FP64-accurate tensor-core product C = M Y of the Rayleigh-Ritz
@@ -96,6 +98,15 @@ def main():
             C = pw.pw_zgemm_tc("C", A, A)
         torch.cuda.synchronize()
         print("tcgemm done", float(C.abs().max()))
+    elif a.case == "smgemm":
+        g = torch.Generator(device="cuda").manual_seed(0)
+        npw, n = 30000, 3456
+        S = (torch.randn(n, npw, dtype=torch.complex128, device="cuda", generator=g) * 1e-2).T
+        M = torch.randn(n, n, dtype=torch.complex128, device="cuda", generator=g).T
+        for _ in range(a.reps + 1):
+            C = pw.pw_zgemm_tc("N", S, M)
+        torch.cuda.synchronize()
+        print("smgemm done", float(C.abs().max()))
     elif a.case == "ozgemm":
         n, nb = 3456, 1152
         rng = np.random.default_rng(0)
