@@ -104,6 +104,7 @@ __global__ void k_copy_herm(const double2 *M, int ld, int n, double2 *out) {
 }
 
 constexpr int CB = 32;   // Cholesky / inverse block
+constexpr int DC_TC_MIN_HALF = 512;   // merge levels with larger halves: products on the tensor cores
 
 // unblocked Cholesky of the diagonal block at j0 (size b <= 32), in place
 // Li (b x b, ld CB) = L11^-1 as well, for the row solves of the panel below
@@ -1192,6 +1193,39 @@ __global__ void __launch_bounds__(256) k_dc_gemm(const int *nodes, int n, DcArra
     }
 }
 
+// The merge product of k_dc_gemm for one node and half (upper rows lo..mid
+// or lower rows mid..hi) as a dense real product on zero-padded operands, for
+// the FP64-accurate tensor-core path: Zg[r, k] = Z[row0 + r, colK[lo + ql[k]]]
+// (k < kq), Ug[k, t] = U[lo + ql[k], lo + t] (k < kq, t < kneed), zero beyond;
+// kq and kneed stay on the device (kmax, tmax bound them)
+__global__ void k_dc_gather_z(int lo, int mid, int hi, int node, int half, int n, DcArrays a, int kmax,
+                              double *Zg) {
+  const int rows = half ? hi - mid : mid - lo, row0 = half ? mid : lo;
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)rows * kmax) return;
+  const int r = (int)(idx % rows), k = (int)(idx / rows);
+  const int kq = a.kLR[2 * node + half];
+  const int *ql = (half ? a.qR : a.qL) + lo;
+  Zg[idx] = k < kq ? a.Z[(row0 + r) + (long)a.colK[lo + ql[k]] * n] : 0.0;
+}
+__global__ void k_dc_gather_u(int lo, int node, int half, int n, DcArrays a, int kmax, int tmax, double *Ug) {
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)kmax * tmax) return;
+  const int k = (int)(idx % kmax), t = (int)(idx / kmax);
+  const int kq = a.kLR[2 * node + half], kneed = a.kneed[node];
+  const int *ql = (half ? a.qR : a.qL) + lo;
+  Ug[idx] = (k < kq && t < kneed) ? a.U[(lo + ql[k]) + (long)(lo + t) * n] : 0.0;
+}
+// W[row0 + r, lo + t] = Wt[r, t] for t < kneed (k_dc_gemm's output columns)
+__global__ void k_dc_scatter_w(int lo, int mid, int hi, int node, int half, int n, DcArrays a, int tmax,
+                               const double *Wt) {
+  const int rows = half ? hi - mid : mid - lo, row0 = half ? mid : lo;
+  const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (idx >= (long)rows * tmax) return;
+  const int r = (int)(idx % rows), t = (int)(idx / rows);
+  if (t < a.kneed[node]) a.W[(row0 + r) + (long)(lo + t) * n] = Wt[idx];
+}
+
 // final order: rank of each (value, source index) among the node's eigenvalues;
 // kneed = roots among the `keep` lowest (the roots are in increasing order)
 __global__ void k_dc_rank(const int *nodes, DcArrays a, int keep) {
@@ -1638,8 +1672,40 @@ pw_status stage_dc(pw_dense_ws *ws, int n, int nb, double *lam, cudaStream_t st)
     const int keep = l == 0 ? nb : n;
     pw_count_launch();
     k_dc_rank<<<dim3((maxsize + 127) / 128, nn), 128, 0, st>>>(nodes, a, keep);
-    pw_count_launch();
-    k_dc_gemm<<<dim3((maxsize + 63) / 64 + 1, (maxsize + 63) / 64, nn), 256, 0, st>>>(nodes, n, a);
+    // levels whose halves all have >= 512 rows: their merge products on the
+    // FP64-accurate tensor-core path (real operands gathered into ws->T)
+    int minhalf = n;
+    bool fits = true;   // the gathered operands and the product fit in ws->T (2 nmax^2 doubles)
+    for (int q = 0; q < nn; ++q) {
+      const int lo = ws->levels[l][3 * q], mid = ws->levels[l][3 * q + 1], hi = ws->levels[l][3 * q + 2];
+      minhalf = std::min(minhalf, std::min(mid - lo, hi - mid));
+      const size_t sz = hi - lo, rows = std::max(mid - lo, hi - mid), tm = std::min<size_t>(sz, keep);
+      fits = fits && rows * sz + sz * tm + rows * tm <= 2 * (size_t)ws->nmax * ws->nmax;
+    }
+    if (pw_dense_products_mode() == 1 && minhalf >= DC_TC_MIN_HALF && fits) {
+      for (int q = 0; q < nn; ++q) {
+        const int lo = ws->levels[l][3 * q], mid = ws->levels[l][3 * q + 1], hi = ws->levels[l][3 * q + 2];
+        const int node = q, size = hi - lo;   // per-node arrays are indexed within the level
+        const int kmax = size, tmax = std::min(size, keep);
+        for (int half = 0; half < 2; ++half) {
+          const int rows = half ? hi - mid : mid - lo;
+          double *Zg = (double *)ws->T, *Ug = Zg + (size_t)rows * kmax, *Wt = Ug + (size_t)kmax * tmax;
+          pw_count_launch();
+          k_dc_gather_z<<<(unsigned)(((long)rows * kmax + 255) / 256), 256, 0, st>>>(lo, mid, hi, node, half, n, a,
+                                                                                     kmax, Zg);
+          pw_count_launch();
+          k_dc_gather_u<<<(unsigned)(((long)kmax * tmax + 255) / 256), 256, 0, st>>>(lo, node, half, n, a, kmax,
+                                                                                     tmax, Ug);
+          PW_TRY(pw_dgemm_oz(&ws->oz, rows, tmax, kmax, Zg, rows, Ug, kmax, Wt, rows, st));
+          pw_count_launch();
+          k_dc_scatter_w<<<(unsigned)(((long)rows * tmax + 255) / 256), 256, 0, st>>>(lo, mid, hi, node, half, n,
+                                                                                      a, tmax, Wt);
+        }
+      }
+    } else {
+      pw_count_launch();
+      k_dc_gemm<<<dim3((maxsize + 63) / 64 + 1, (maxsize + 63) / 64, nn), 256, 0, st>>>(nodes, n, a);
+    }
     pw_count_launch();
     k_dc_copy_defl<<<dim3(maxsize, nn), 128, 0, st>>>(nodes, n, a);
     pw_count_launch();

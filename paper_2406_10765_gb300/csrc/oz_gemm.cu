@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               int a_slice_rows, int b_slice_rows, int m, int n, int kblocks, int mtiles, int ntiles,
               const int *__restrict__ ea, const int *__restrict__ eb, double2 alpha, double2 beta,
               double2 *__restrict__ C, int ldc, int herm, int ioff, int joff, double2 *__restrict__ part,
-              int *__restrict__ err) {
+              int *__restrict__ err, int real_out) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + NSTAGE * STAGE);
@@ -90,7 +90,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int mt = tile / ntiles, nt = tile % ntiles;
   if (mt >= mtiles) return;
   const int m0 = mt * BM;              // complex rows m0 .. m0 + 127 (of this block)
-  const int j0 = nt * (BN / 2);        // complex columns j0 .. j0 + 31
+  // complex columns j0 .. j0 + 31, or with real_out (real operands: one
+  // slice row per real column of B, output real, ld ldc in doubles) real
+  // columns j0 .. j0 + 63
+  const int j0 = nt * (real_out ? BN : BN / 2);
   const int gm0 = ioff + m0, gj0 = joff + j0;   // the same in the whole product
   // Hermitian output, upper part (mirrored later): skip tiles strictly below
   // the diagonal; lower part: tiles holding no element with j/64 <= i/64
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int p = 0; p < S; ++p) {
           tma_load_2d(st + p * A_T, &mapA, &full[s], x, p * a_slice_rows + m0);
-          tma_load_2d(st + S * A_T + p * B_T, &mapB, &full[s], x, p * b_slice_rows + 2 * j0);
+          tma_load_2d(st + S * A_T + p * B_T, &mapB, &full[s], x, p * b_slice_rows + (real_out ? j0 : 2 * j0));
         }
       }
     }
@@ -210,7 +213,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
     const int i = m0 + q * 32 + lane;              // complex output row
-    if (ok && i < m) {
+    if (ok && i < m && real_out) {
+      double *Cr = (double *)C;
+      const int ka = -Lfix - ea[i];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        const int j = j0 + h * 32 + t;
+        if (j >= n) continue;
+        double r = alpha.x * scale_pow2((double)acc[t], ka - eb[j]);
+        if (beta.x != 0.0) r += beta.x * Cr[i + (long)j * ldc];
+        Cr[i + (long)j * ldc] = r;
+      }
+    } else if (ok && i < m) {
       const int jb = j0 + h * 16;                  // first complex column of this thread
       const int ka = -Lfix - ea[i];
 #pragma unroll
@@ -397,6 +411,83 @@ __global__ void __launch_bounds__(256) k_oz_slice_strided(const double2 *__restr
   }
 }
 
+// Slices of real rows (the real mode, C = A B with real A, B): row r of A
+// is strided (A[r + t lda]), row j of the B side is column j of B,
+// contiguous (B[t + j ldb]); out: [S][rows_total][kpad] FP16, e: row
+// exponents.  Row maxima of the strided rows come from k_ozr_rowmax (mx,
+// cleared before).
+__global__ void __launch_bounds__(256) k_ozr_slice_contig(const double *__restrict__ X, int ld, int k, int kpad,
+                                                          int rows_total, __half *__restrict__ out,
+                                                          int *__restrict__ e) {
+  __shared__ unsigned long long shm[8];
+  const int r = blockIdx.x;
+  const double *x = X + (long)r * ld;
+  unsigned long long mb = 0;
+  for (int t = threadIdx.x; t < k; t += blockDim.x) mb = max(mb, abs_bits(x[t]));
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mb;
+  __syncthreads();
+  mb = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mb = max(mb, shm[w]);
+  const int ex = row_exp(mb);
+  if (threadIdx.x == 0) e[r] = ex;
+  const long slice = (long)rows_total * kpad;
+  for (int t2 = threadIdx.x; t2 < kpad / 2; t2 += blockDim.x) {
+    const int t = 2 * t2;
+    __half d0[S], d1[S];
+    digits(t < k ? x[t] : 0.0, ex, d0);
+    digits(t + 1 < k ? x[t + 1] : 0.0, ex, d1);
+    __half *o = out + (long)r * kpad + t;
+#pragma unroll
+    for (int p = 0; p < S; ++p) *(__half2 *)(o + p * slice) = __halves2half2(d0[p], d1[p]);
+  }
+}
+__global__ void __launch_bounds__(256) k_ozr_rowmax(const double *__restrict__ X, int ld, int nrows, int k,
+                                                    unsigned long long *__restrict__ mx) {
+  __shared__ unsigned long long sh[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = blockIdx.x * 32 + lane;
+  const int t0 = blockIdx.y * RX_K, t1 = min(k, t0 + RX_K);
+  unsigned long long m = 0;
+  if (r < nrows)
+    for (int t = t0 + w; t < t1; t += 8) m = max(m, abs_bits(X[r + (long)t * ld]));
+  sh[w][lane] = m;
+  __syncthreads();
+  if (w == 0 && r < nrows) {
+#pragma unroll
+    for (int q = 1; q < 8; ++q) m = max(m, sh[q][lane]);
+    atomicMax(&mx[r], m);
+  }
+}
+__global__ void __launch_bounds__(256) k_ozr_slice_strided(const double *__restrict__ X, int ld, int nrows, int k,
+                                                           int kpad, int rows_total,
+                                                           const unsigned long long *__restrict__ mx,
+                                                           int *__restrict__ e, __half *__restrict__ out) {
+  __shared__ double tileS[64][33];
+  const int r0 = blockIdx.x * 32, t0 = blockIdx.y * 64;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int tt = ty; tt < 64; tt += 8) {
+    const int r = r0 + tx, t = t0 + tt;
+    tileS[tt][tx] = (r < nrows && t < k) ? X[r + (long)t * ld] : 0.0;
+  }
+  __syncthreads();
+  const long slice = (long)rows_total * kpad;
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int r = r0 + rr;
+    if (r >= nrows) continue;
+    const int ex = row_exp(mx[r]);
+    if (blockIdx.y == 0 && tx == 0) e[r] = ex;
+    const int t = t0 + 2 * tx;
+    if (t >= kpad) continue;
+    __half d0[S], d1[S];
+    digits(tileS[2 * tx][rr], ex, d0);
+    digits(tileS[2 * tx + 1][rr], ex, d1);
+    __half *o = out + (long)r * kpad + t;
+#pragma unroll
+    for (int p = 0; p < S; ++p) *(__half2 *)(o + p * slice) = __halves2half2(d0[p], d1[p]);
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -543,7 +634,7 @@ pw_status oz_block(pw_oz_ws *w, char opA, char opB, int mb, int nb, int k, doubl
   pw_count_launch();
   k_oz_gemm<<<dim3(tiles, parts), NTHREADS, SMEM_BYTES, st>>>(ma, mbm, arows, brows, mb, nb, kblocks, mtiles,
                                                                ntiles, ea, eb, alpha, beta, C, ldc, herm, ioff,
-                                                               joff, parts > 1 ? w->part : nullptr, w->err);
+                                                               joff, parts > 1 ? w->part : nullptr, w->err, 0);
   PW_TRY(pw_check_launch("oz gemm"));
   if (parts > 1) {
     pw_count_launch();
@@ -560,6 +651,54 @@ const double2 *at(const double2 *X, char op, int ld, long r, long t) {
   return op == 'N' ? X + r + t * (long)ld : X + t + r * (long)ld;
 }
 }  // namespace
+
+pw_status pw_dgemm_oz(pw_oz_ws *w, int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                      double *C, int ldc, cudaStream_t st) {
+  if (m <= 0 || n <= 0 || k <= 0 || lda < m || ldb < k || ldc < m) return PW_ERR_ARG;
+  const int kpad = (k + BK - 1) / BK * BK;
+  const int kblocks = kpad / BK;
+  const int arows = (m + BM - 1) / BM * BM, brows = (n + BN - 1) / BN * BN;
+  const size_t abytes = (size_t)S * arows * kpad * 2, bbytes = (size_t)S * brows * kpad * 2;
+  const size_t need = abytes + bbytes + ((size_t)arows + brows) * 4 + 256 + (size_t)arows * 8 + 1024;
+  if (need > w->bytes) {
+    if (w->buf) cudaFree(w->buf);
+    w->buf = nullptr;
+    w->bytes = 0;
+    ++w->gen;
+    if (cudaMalloc(&w->buf, need) != cudaSuccess) { cudaGetLastError(); return PW_ERR_OOM; }
+    w->bytes = need;
+  }
+  if (!w->err) {
+    if (cudaMalloc((void **)&w->err, 16) != cudaSuccess) { cudaGetLastError(); return PW_ERR_OOM; }
+    PW_CUDA(cudaMemsetAsync(w->err, 0, 16, st));
+    ++w->gen;
+  }
+  unsigned char *p = (unsigned char *)w->buf;
+  __half *sa = (__half *)p, *sb = (__half *)(p + abytes);
+  int *ea = (int *)(p + abytes + bbytes), *eb = ea + arows;
+  unsigned long long *mx = (unsigned long long *)(((uintptr_t)(eb + brows) + 255) & ~(uintptr_t)255);
+  // A: strided rows (row maxima first); B: its columns, contiguous.  Slice
+  // rows past m and n are never written: they only feed output rows and
+  // columns that are not stored
+  PW_CUDA(cudaMemsetAsync(mx, 0, (size_t)m * 8, st));
+  pw_count_launch();
+  k_ozr_rowmax<<<dim3((m + 31) / 32, (k + RX_K - 1) / RX_K), 256, 0, st>>>(A, lda, m, k, mx);
+  pw_count_launch();
+  k_ozr_slice_strided<<<dim3((m + 31) / 32, (kpad + 63) / 64), 256, 0, st>>>(A, lda, m, k, kpad, arows, mx, ea, sa);
+  pw_count_launch();
+  k_ozr_slice_contig<<<n, 256, 0, st>>>(B, ldb, k, kpad, brows, sb, eb);
+  PW_TRY(pw_check_launch("oz real slices"));
+  CUtensorMap ma, mbm;
+  if (!make_map(&ma, sa, kpad, (long)S * arows, BM) || !make_map(&mbm, sb, kpad, (long)S * brows, BN))
+    return PW_ERR_CUDA;
+  PW_TRY(allow_smem());
+  const int mtiles = arows / BM, ntiles = brows / BN;
+  pw_count_launch();
+  k_oz_gemm<<<dim3(mtiles * ntiles, 1), NTHREADS, SMEM_BYTES, st>>>(
+      ma, mbm, arows, brows, m, n, kblocks, mtiles, ntiles, ea, eb, make_double2(1.0, 0.0), make_double2(0.0, 0.0),
+      (double2 *)C, ldc, 0, 0, 0, nullptr, w->err, 1);
+  return pw_check_launch("oz gemm (real)");
+}
 
 pw_status pw_zgemm_oz(pw_oz_ws *w, char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
                       int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc, cudaStream_t st,

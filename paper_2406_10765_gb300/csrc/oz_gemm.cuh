@@ -26,6 +26,12 @@ struct pw_oz_ws {
 pw_status pw_zgemm_oz(pw_oz_ws *w, char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
                       int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc, cudaStream_t st,
                       int herm);
+// C = A B for real column-major A (m x k, lda), B (k x n, ldb), C (m x n,
+// ldc): the same slice arithmetic on real rows (A's rows strided, B's
+// columns contiguous), error per entry <= ~K 2^-55 max_k|a_ik| max_k|b_kj|.
+// Asynchronous on st.
+pw_status pw_dgemm_oz(pw_oz_ws *w, int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+                      double *C, int ldc, cudaStream_t st);
 // Dispatch of an FP64 product: the tensor-core path when the process-wide
 // mode (pw_dense_products) is 1, w is given and the product has at least
 // ~8M complex multiply-adds; else the FP64 pipe (pw_zgemm_ex with ws).
