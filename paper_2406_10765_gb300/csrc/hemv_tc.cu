@@ -6,8 +6,8 @@
 // panel's rank-2 corrections are applied through V and W), so it is split
 // once per panel into integer digit slices and every column's product reads
 // the slices instead of the FP64 matrix:
-//   * A22 / 2^-eA = sum_p a_p 2^(-7p) (p = 1..8, the digit split of the FP64
-//     oz product with one scale for the whole trailing matrix), and
+//   * A22 2^eA = sum_p a_p 2^(-7p) (p = 1..8, the digit split of the
+//     FP64-accurate product, one scale for the whole trailing matrix), and
 //     v / 2 = sum_q b_q 2^(-7q) (|v| <= 1 for a Householder vector whose head
 //     is 1);
 //   * the products a_p b_q with p + q = g (g = 2..9) are summed in one FP32
@@ -35,14 +35,18 @@
 // are stored as full Hermitian blocks and give only A v; off-diagonal tiles
 // give A v for their rows and A^H v for their columns.
 //
-// Kernel: persistent, one CTA per SM, each CTA a contiguous range of work
-// units (tile, real or imaginary part: eight sub-tiles each).  Warp 0 =
-// bulk-copy producer (six 32 KB stages), warp 1 = MMA issuer (one thread),
-// warps 2..5 = B-operand builders and epilogue, warps 6..7 = v into the panel
-// and the panel's correction dots; B operands and accumulators
-// are double-buffered, so a unit's MMAs run while the previous unit's sums
-// are read and the next unit's digits of v are written.  Every mbarrier wait
-// is bounded; on timeout the CTA records an error word and leaves in order.
+// Kernel (k_hemv_tc, one column per launch, chained with k_pcol and k_prows
+// by programmatic dependent launch): persistent, one CTA per SM, each CTA a
+// contiguous range of work units (tile, real or imaginary part, and for
+// short trailing orders a piece of its eight slices, so that every SM has
+// work).  Warp 0 = bulk-copy producer (six 32 KB stages), warp 1 = MMA
+// issuer (one thread), warps 2..5 = B-operand builders and epilogue, warps
+// 6..7 = v into the panel and the panel's correction dots; B operands and
+// accumulators are double-buffered, so a unit's MMAs run while the previous
+// unit's sums are read and the next unit's digits of v are written.  The
+// same roles run inside k_panel_tc, one cooperative launch per panel.
+// Every mbarrier wait is bounded; on timeout the CTA records an error word
+// and leaves in order.
 #include <cuda_fp16.h>
 
 #include <mutex>
@@ -72,7 +76,6 @@ constexpr int BKC = BROWS * 16;              // bytes per K chunk (512)
 constexpr int BDIR = (HT / 8) * BKC;         // 8 KB
 constexpr int TMEM_COLS = 128;               // per buffer: D_row[h], D_col[h] (two 64-K halves), 16 columns each
 constexpr int LFIX = 54;                     // binary point of the per-tile fixed-point sums
-constexpr int DOT_LD = 64;                   // partial dots per row block (2 x 32 panel columns)
 constexpr int TPB_HS = 32;                   // panel width of the reduction
 constexpr int NBAR_FIXED = 5;                // bready[2], mdone[2], fin
 // dynamic shared memory of a CTA running the product with NS stages of one
