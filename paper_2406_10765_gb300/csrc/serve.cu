@@ -26,6 +26,7 @@
 #include <tuple>
 #include <vector>
 
+#include "dense.cuh"
 #include "pw_internal.cuh"
 
 namespace {
@@ -96,6 +97,7 @@ extern "C" size_t pw_request_footprint(const pw_request *r, int precision) {
   b += 64.0 * 1048576;                                                     // FFT z-pencils (cap)
   b += (4 * npw * n3 + 2 * npw * nb) * 16;                                  // S, S2, HS, HS2, P, HP
   b += n3 * n3 * 16 * 6 + n3 * n3 * 8 * 3;                                  // G, A, dense workspace
+  b += (double)pw_hs_bytes((int)n3);                                        // Householder digit slices
   if (precision == PW_MIXED)
     b += (npw * 2 * n3 * 2 * 3 + nproj * 2 * npw * 4 * 2) * 2.0;            // split operands
   return (size_t)(1.1 * b);

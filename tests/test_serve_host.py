@@ -19,6 +19,16 @@ def test_footprint_model_monotone():
     assert 1e10 < big < 2e11
 
 
+def test_footprint_counts_householder_slices():
+    # a Rayleigh-Ritz order of 1,024 or more (3 x 342 bands) adds the digit
+    # slices of the tensor-core Hermitian products: 9 tile rows, 45 lower
+    # tiles of 512 KB, on top of what one more band costs
+    import paper_2406_10765_gb300 as pw
+    base = dict(species="Si", n=2, ecut=10.0, nbands=340, seed=0)
+    f340, f341, f342 = (pw.pw_request_footprint(dict(base, nbands=b)) for b in (340, 341, 342))
+    assert f342 - f341 > (f341 - f340) + 45 * 512 * 1024
+
+
 def test_request_stream_shape():
     reqs = synth.serving_requests(2000, rate_per_s=5.0, seed=1)
     sp = np.array([r["species"] == "Si" for r in reqs])
