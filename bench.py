@@ -386,7 +386,8 @@ class Clocks:
 
 def oracle_sample(wl, seed=0, frac_rows=32, apply_bands=8, rr_div=2):
     """One sampled oracle step: time its components on bounded pieces of the
-    workload and scale them to a full step.  Returns (seconds_per_step, note, cores)."""
+    workload and scale them to a full step.  Returns (seconds_per_step, note,
+    pieces) with pieces[name] = {measured_s, scale, scaled_s}."""
     import numpy as np
     import synth
     from oracle import pw_oracle as O
@@ -398,23 +399,27 @@ def oracle_sample(wl, seed=0, frac_rows=32, apply_bands=8, rr_div=2):
     ns = 3 * nb
     rng = np.random.default_rng(seed)
     t = {}
+
+    def piece(name, sec, scale):
+        t[name] = {"measured_s": sec, "scale": scale, "scaled_s": sec * scale}
+
     kb = min(apply_bands, nb)
     X = synth.draw_x0(seed, len(ci["tau"]), npw, kb)
     t0 = time.perf_counter()
     O.apply_H(cell, X)
-    t["hpsi"] = (time.perf_counter() - t0) * nb / kb
+    piece("hpsi", time.perf_counter() - t0, nb / kb)
     rows = max(ns, npw // frac_rows)
     S = rng.standard_normal((rows, ns)) + 1j * rng.standard_normal((rows, ns))
     t0 = time.perf_counter()
     S.conj().T @ S
     S.conj().T @ S
-    t["gram"] = (time.perf_counter() - t0) * npw / rows
+    piece("gram", time.perf_counter() - t0, npw / rows)
     C = rng.standard_normal((ns, nb)) + 1j * rng.standard_normal((ns, nb))
     t0 = time.perf_counter()
     for _ in range(2):
         S @ C
         S[:, nb:] @ C[nb:]
-    t["rot"] = (time.perf_counter() - t0) * npw / rows
+    piece("rot", time.perf_counter() - t0, npw / rows)
     m = ns // rr_div
     Ssm = rng.standard_normal((4 * m, m)) + 1j * rng.standard_normal((4 * m, m))
     Hs = rng.standard_normal((4 * m, 4 * m))
@@ -423,8 +428,8 @@ def oracle_sample(wl, seed=0, frac_rows=32, apply_bands=8, rr_div=2):
     t0 = time.perf_counter()
     O.rayleigh_ritz(Ssm, HSsm, m // 3)
     # the Gram products inside rayleigh_ritz are at 4m rows; cubic part dominates
-    t["rr"] = (time.perf_counter() - t0) * rr_div ** 3
-    total = sum(t.values())
+    piece("rr", time.perf_counter() - t0, rr_div ** 3)
+    total = sum(v["scaled_s"] for v in t.values())
     note = (f"oracle components timed on bounded pieces and scaled to one full step: H on {kb} of "
             f"{nb} bands (x{nb // kb}); S^H S, S^H HS and the 4 rotations on {rows} of {npw} rows "
             f"(x{npw / rows:.1f}); Rayleigh-Ritz at order {m} of {ns} (x{rr_div ** 3}, cubic)")
@@ -451,10 +456,11 @@ def run_reference(args):
     wl = WORKLOADS[args.workload]
     for _ in range(args.warmup):
         oracle_sample(wl)
-    secs = []
+    secs, measured = [], []
     for _ in range(args.steps):
         s, note, parts = oracle_sample(wl)
         secs.append(s)
+        measured.append(sum(p["measured_s"] for p in parts.values()))
     sec = sum(secs) / len(secs)
     v = 1.0 / sec
     cores = cpu_cores()
@@ -465,7 +471,8 @@ def run_reference(args):
            "config": {"workload": wl["name"], "nbands": wl["nb"], "precision": "fp64",
                       "implementation": "FP64 numpy/scipy oracle on host cores"},
            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": cores, "kind": "oracle",
-                            "sample": note},
+                            "sample": note, "extrapolated": True, "pieces": parts,
+                            "measured_s_per_step": sum(measured) / len(measured)},
            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -628,7 +635,8 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sec, note, parts = oracle_sample(wl)
         out["cpu_baseline"] = {"value": 1.0 / sec, "unit": "iters/s", "cores": cpu_cores(),
-                               "kind": "oracle", "sample": note}
+                               "kind": "oracle", "sample": note, "extrapolated": True, "pieces": parts,
+                               "measured_s_per_step": sum(p["measured_s"] for p in parts.values())}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -69,3 +69,16 @@ def test_step_flops_model():
     # H applied to X, W and P in mixed precision
     g = bench.step_flops(npw, nb, ns, nb, nproj, grid, hcols=ns)
     assert math.isclose(g["fft"] / f["fft"], ns / nb)
+
+
+def test_cpu_baseline_sample_is_stated_as_extrapolated():
+    # the oracle's sampled step (small workload): every piece carries its
+    # measured seconds and its scale, the step is their scaled sum
+    import bench
+    sec, note, parts = bench.oracle_sample(bench.WORKLOADS["si8"])
+    assert set(parts) == {"hpsi", "gram", "rot", "rr"}
+    for p in parts.values():
+        assert p["measured_s"] > 0 and p["scale"] >= 1
+        assert math.isclose(p["scaled_s"], p["measured_s"] * p["scale"], rel_tol=1e-12)
+    assert math.isclose(sec, sum(p["scaled_s"] for p in parts.values()), rel_tol=1e-12)
+    assert "scaled" in note
