@@ -176,13 +176,6 @@ __global__ void k_gather_cols(const double2 *src, int ld, int npw, const int *ac
   dst[g + (long)a * ld] = src[g + (long)act[a] * ld];
 }
 
-__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
-  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
 // random start: entry (g, j) = (u1 - 1/2) + i (u2 - 1/2), counters 5 natom + 2 (j npw + g) (+1)
 __global__ void k_random_block(double2 *X, int ld, int npw, int nb, uint64_t seed, uint64_t base) {
   const long idx = blockIdx.x * (long)blockDim.x + threadIdx.x;

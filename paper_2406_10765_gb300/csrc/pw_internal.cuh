@@ -37,6 +37,16 @@ template <typename T> struct cpx_t;
 template <> struct cpx_t<double> { typedef double2 type; };
 template <> struct cpx_t<float> { typedef float2 type; };
 
+// SplitMix64 (Steele, Lea and Flood 2014) in counter form: output i of the
+// stream `seed`; the seeded synthetic inputs (start blocks, serving
+// requests) draw from it on the host and on the device
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
   C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
 }
