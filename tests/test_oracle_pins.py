@@ -80,6 +80,12 @@ def test_grid_rule():
     for ecut, L in [(10.0, 10.26), (8.0, 6.74)]:
         m = O.sphere(ecut, [L] * 3)
         assert 2 * np.abs(m).max() < O.grid_size_1d(ecut, L)
+    # each axis of a cell with three different lengths gets its own grid
+    cell = O.make_cell(np.array([6.0, 9.0, 13.0]), np.array([[0.3, 1.1, 2.0]]), np.array([-1.0]),
+                       np.array([[0.7, 0.9, 1.1, 1.3]]), 6.0)
+    assert cell.Ns == (12, 16, 24)        # 1.5 sqrt(2 Ecut) L / pi = 9.9, 14.9, 21.5
+    for k in range(3):
+        assert 2 * np.abs(cell.m[:, k]).max() < cell.Ns[k]
 
 
 # ------------------------------------------------------------------ FFT ----
@@ -316,6 +322,37 @@ def test_rayleigh_ritz_breakdown_and_solution():
     assert np.abs(X.conj().T @ X - np.eye(4)).max() < 1e-12
 
 
+def test_rayleigh_ritz_pivot_threshold():
+    """The drop test fires on a scaled pivot <= 1e-14 even where the Cholesky
+    itself succeeds.  The last pivot of the Jacobi-scaled Gram is the squared
+    distance of the last unit column from the span of the others, computed
+    here by least squares: at 3e-15 the step must report a breakdown, at
+    3e-13 it must not."""
+    import scipy.linalg as sla
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((60, 5)) + 1j * rng.standard_normal((60, 5))
+    A /= np.linalg.norm(A, axis=0)
+    b = rng.standard_normal(60) + 1j * rng.standard_normal(60)
+    b -= A @ np.linalg.lstsq(A, b, rcond=None)[0]            # b orthogonal to span(A)
+    Hm = rng.standard_normal((60, 60))
+    Hm = Hm + Hm.T
+    for piv, breaks in [(3e-15, True), (3e-13, False)]:
+        # last column a_1 + e b: distance^2 / norm^2 = e^2 |b|^2 / (1 + e^2 |b|^2)
+        e = math.sqrt(piv / (1 - piv)) / np.linalg.norm(b)
+        S = np.hstack([A, (A[:, 1] + e * b)[:, None]])
+        u = S[:, -1] / np.linalg.norm(S[:, -1])
+        dist2 = np.linalg.norm(u - A @ np.linalg.lstsq(A, u, rcond=None)[0]) ** 2
+        assert abs(dist2 / piv - 1) < 1e-2
+        G = S.conj().T @ S
+        d = 1 / np.sqrt(np.real(np.diag(G)))
+        sla.cholesky(d[:, None] * G * d[None, :], lower=True)   # factorises either way
+        if breaks:
+            with pytest.raises(O.CholeskyBreakdown):
+                O.rayleigh_ritz(S, Hm @ S, 2)
+        else:
+            O.rayleigh_ritz(S, Hm @ S, 2)
+
+
 def _rr_pencil(S, HS, nb):
     """Lowest nb eigenvalues of the pencil (S^H H S, S^H S) by scipy's
     generalized Hermitian solver: a route that shares nothing with the
@@ -324,6 +361,22 @@ def _rr_pencil(S, HS, nb):
     A = S.conj().T @ HS
     B = S.conj().T @ S
     return sla.eigh(0.5 * (A + A.conj().T), 0.5 * (B + B.conj().T), eigvals_only=True)[:nb]
+
+
+def _w_from_definition(cell, st):
+    """W written out: R = H X - X Lambda, each column scaled by the TPA ratio
+    p / (p + 16 x^4), p = 27 + 18 x + 12 x^2 + 8 x^3, x = 1/2|G|^2 / E_kin."""
+    R = O.apply_H(cell, st.X) - st.X * st.lam[None, :]
+    ek = (cell.kin[:, None] * np.abs(st.X) ** 2).sum(0) / (np.abs(st.X) ** 2).sum(0)
+    x = cell.kin[:, None] / ek[None, :]
+    p = 27 + 18 * x + 12 * x ** 2 + 8 * x ** 3
+    return p / (p + 16 * x ** 4) * R
+
+
+def _outside(V, Q):
+    """Relative size of the part of V's columns outside span(Q)."""
+    c, *_ = np.linalg.lstsq(Q, V, rcond=None)
+    return np.abs(V - Q @ c).max() / np.abs(V).max()
 
 
 def test_lobpcg_step_drops_p_on_breakdown():
@@ -339,12 +392,7 @@ def test_lobpcg_step_drops_p_on_breakdown():
     st.P, st.HP = st.X @ Q, st.HX @ Q
     nxt = O.lobpcg_step(cell, st)
     assert nxt.dropped_p == 1
-    # W from its definition: R = H X - X Lambda, TPA on 1/2|G|^2 / E_kin
-    R = O.apply_H(cell, st.X) - st.X * st.lam[None, :]
-    ek = (cell.kin[:, None] * np.abs(st.X) ** 2).sum(0) / (np.abs(st.X) ** 2).sum(0)
-    x = cell.kin[:, None] / ek[None, :]
-    p = 27 + 18 * x + 12 * x ** 2 + 8 * x ** 3
-    W = p / (p + 16 * x ** 4) * R
+    W = _w_from_definition(cell, st)
     S = np.hstack([st.X, W])
     ref = _rr_pencil(S, O.apply_H(cell, S), nb)
     assert np.abs(nxt.lam - ref).max() < 1e-10
@@ -373,6 +421,41 @@ def test_lobpcg_step_keeps_p_when_it_is_independent():
     S = np.hstack([st.X, W, P])
     ref = _rr_pencil(S, O.apply_H(cell, S), nb)
     assert np.abs(nxt.lam - ref).max() < 1e-10
+
+
+def test_lobpcg_step_direction_update():
+    """The new direction carries no X component (Knyazev's method in the
+    Hetmaniuk-Lehoucq form): P' lies in span([W, P]) and X' - P' in
+    span(X), so X' = X C_X + P'.  The H blocks follow the same
+    combinations: HX' = H X' and HP' = H P'."""
+    cell, _ = _cell("Si", 1, 10.0)
+    nb = 6
+    st = O.lobpcg_init(cell, synth.draw_x0(3, 8, cell.npw, nb))
+    P = synth.draw_x0(5, 8, cell.npw, nb)
+    st.P, st.HP = P, O.apply_H(cell, P)
+    nxt = O.lobpcg_step(cell, st)
+    W = _w_from_definition(cell, st)
+    assert _outside(nxt.P, np.hstack([W, P])) < 1e-10
+    assert _outside(nxt.X - nxt.P, st.X) < 1e-10
+    # and P' is a real direction, not a copy of X'
+    assert _outside(nxt.P, st.X) > 1e-3
+    assert np.abs(nxt.HX - O.apply_H(cell, nxt.X)).max() < 1e-10 * np.abs(nxt.HX).max()
+    assert np.abs(nxt.HP - O.apply_H(cell, nxt.P)).max() < 1e-10 * np.abs(nxt.HP).max()
+
+
+def test_lobpcg_init_is_the_ritz_block_of_the_start():
+    """The first block: orthonormal, H X carried exactly, and the Ritz values
+    of span(X0), i.e. the generalized eigenvalues of (X0^H H X0, X0^H X0),
+    with X^H H X diagonal."""
+    cell, _ = _cell("Si", 1, 10.0)
+    nb = 6
+    X0 = synth.draw_x0(3, 8, cell.npw, nb)
+    st = O.lobpcg_init(cell, X0)
+    assert np.abs(st.X.conj().T @ st.X - np.eye(nb)).max() < 1e-12
+    assert np.abs(st.HX - O.apply_H(cell, st.X)).max() < 1e-10 * np.abs(st.HX).max()
+    assert np.abs(st.lam - _rr_pencil(X0, O.apply_H(cell, X0), nb)).max() < 1e-10
+    assert np.abs(st.X.conj().T @ st.HX - np.diag(st.lam)).max() < 1e-10
+    assert _outside(st.X, X0) < 1e-12
 
 
 def test_lobpcg_init_breakdown_on_dependent_start():
@@ -418,6 +501,18 @@ def test_hartree_single_mode_closed_form():
     assert np.abs(V - ref).max() < 1e-12
 
 
+def test_hartree_sine_mode_sign():
+    # an odd mode fixes the direction of both transforms: n = A sin(G.r)
+    # gives V_H = 4 pi A sin(G.r) / |G|^2 (a flipped exponent flips its sign)
+    Ls = np.array([7.0, 8.0, 9.0])
+    Ns = (16, 18, 24)
+    G = 2 * np.pi * np.array([1, 3, -2]) / Ls
+    r = [Ls[a] * np.arange(Ns[a]) / Ns[a] for a in range(3)]
+    phase = G[0] * r[0][:, None, None] + G[1] * r[1][None, :, None] + G[2] * r[2][None, None, :]
+    V = O.hartree_potential(Ls, Ns, 0.21 * np.sin(phase))
+    assert np.abs(V - 4 * np.pi * 0.21 * np.sin(phase) / (G @ G)).max() < 1e-12
+
+
 def test_hartree_superposition_and_zero_mean():
     rng = np.random.default_rng(0)
     Ls, Ns = np.array([6.0, 6.0, 6.0]), (12, 12, 12)
@@ -458,3 +553,28 @@ def test_scf_mixing_converges_to_a_fixed_point():
     d = [np.abs(n_out - n_in).max() for _, n_in, n_out in h]
     assert d[-1] < 1e-4 * d[0]
     assert all(d[k + 2] < d[k] for k in range(len(d) - 2))
+    # the limit is a fixed point of the Kohn-Sham map: the lowest 8 bands of
+    # V_loc + V_H[n] + v_x[n], doubly occupied, give back n
+    n = h[-1][2]
+    V = cell.V + O.hartree_potential(cell.Ls, cell.Ns, n) + O.slater_exchange(n)
+    ks = O.make_cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], 8.0, V=V)
+    _, X = O.dense_eigs(ks, 8)
+    n2 = O.electron_density(ks, X, np.full(8, 2.0))
+    assert np.abs(n2 - n).max() < 10 * d[-1]
+    # and not of the bare potential
+    _, X0 = O.dense_eigs(cell, 8)
+    assert np.abs(O.electron_density(cell, X0, np.full(8, 2.0)) - n).max() > 1e3 * d[-1]
+
+
+def test_scf_linear_mixing_is_a_geometric_series():
+    # with no V_Hxc every iteration sees the same potential, so n_out is the
+    # same density n* each time and n_in after k iterations is the partial
+    # sum alpha sum_{i<k} (1 - alpha)^i n* = (1 - (1 - alpha)^k) n*
+    ci = synth.cell_inputs("C", 1, 0)
+    cell = O.make_cell(ci["L"], ci["tau"], ci["depth"], ci["dkb"], 8.0)
+    alpha = 0.3
+    h = O.scf(cell, 8, mix=alpha, niter=4, hxc_scale=0.0)
+    nstar = h[0][2]
+    for k, (_, n_in, n_out) in enumerate(h):
+        assert np.abs(n_out - nstar).max() < 1e-12 * np.abs(nstar).max()
+        assert np.abs(n_in - (1 - (1 - alpha) ** k) * nstar).max() < 1e-12 * np.abs(nstar).max()
