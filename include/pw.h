@@ -400,7 +400,7 @@ pw_status pw_zgemm_tc(char opA, int m, int n, int k, const void *A, int lda, con
  * slice products whose weights reach 2^-63 are accumulated exactly (FP32
  * tensor-core sums over 64-wide K chunks are integers below 2^22) into a
  * 64-bit fixed-point sum and converted to FP64 once.  Error per entry at
- * most ~2K 2^-55 max_k |op(A)_ik| max_k |op(B)_kj|, within the FP64 product
+ * most 11K 2^-55 max_k |op(A)_ik| max_k |op(B)_kj|, within the FP64 product
  * bound for rows without large internal range.
  *   C (m x n) = alpha op(A) op(B) + beta C,  op in {'N', 'C'}:
  *   op(A) = A (m x k, lda >= m) or A^H (A k x m, lda >= k);

@@ -19,7 +19,10 @@
 //   * the epilogue adds the groups into a 64-bit fixed-point sum per output
 //     and writes one FP64 partial per tile, summed with the other tiles'
 //     partials in FP64 by the row kernel of the reduction.
-// The error per output is at most ~K 2^-55 max|A22| (normwise FP64).
+// The error per output is at most 10 K 2^-55 max|A22| for trailing order K
+// (2K real terms, each off by at most 1.25 2^-55 in scaled units: the
+// digit roundings and the dropped pairs; the scales add a factor of 4):
+// normwise FP64.
 //
 // Storage: the lower-triangle tiles of 128 x 128 (anchored at row and column
 // 0, so every tile starts on a 256-byte boundary) are written per panel in

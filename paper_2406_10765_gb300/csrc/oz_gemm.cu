@@ -22,9 +22,12 @@
 //     binary point 2^-L, into a 64-bit integer per output (exact except for
 //     a rounding of the lowest groups below 2^-L), and at the end converts
 //     to FP64 and removes the row and column scales.
-// The error is at most ~K' 2^-55 max|a_i| max|b_j| per entry (the row and
-// column maxima), inside the usual FP64 bound K' u |a||b| for rows without
-// large internal dynamic range.
+// The error is at most 5.5 K' 2^-55 max|a_i| max|b_j| per entry (the row and
+// column maxima; each real term is off by at most 1.375 2^-55 in scaled
+// units -- the 2^-57 roundings of both digit expansions and the dropped
+// pairs -- and the scales add a factor of at most 4), plus the final
+// rounding to FP64: inside the usual FP64 bound K' u |a||b| for rows
+// without large internal dynamic range.
 //
 // Kernel: tile of 128 complex rows x 32 complex columns (128 x 64 real) per
 // CTA; warp 0 = TMA producer, warp 1 = MMA issuer (one thread), warps 2..9 =

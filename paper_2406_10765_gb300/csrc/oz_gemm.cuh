@@ -21,14 +21,14 @@ struct pw_oz_ws {
 // C = alpha op(A) op(B) + beta C, column-major complex128, op in {N, C};
 // herm as pw_zgemm_ex (0 plain, 1 Hermitian upper + mirror, 2 tiles with
 // j/64 <= i/64 only, 3 op(A) upper triangular, 4 op(B) lower triangular,
-// 5 op(A) lower triangular).  Error per entry <= ~2K 2^-55 max_k|op(A)_ik|
+// 5 op(A) lower triangular).  Error per entry <= 11K 2^-55 max_k|op(A)_ik|
 // max_k|op(B)_kj|.  Asynchronous on st.
 pw_status pw_zgemm_oz(pw_oz_ws *w, char opA, char opB, int m, int n, int k, double2 alpha, const double2 *A,
                       int lda, const double2 *B, int ldb, double2 beta, double2 *C, int ldc, cudaStream_t st,
                       int herm);
 // C = A B for real column-major A (m x k, lda), B (k x n, ldb), C (m x n,
 // ldc): the same slice arithmetic on real rows (A's rows strided, B's
-// columns contiguous), error per entry <= ~K 2^-55 max_k|a_ik| max_k|b_kj|.
+// columns contiguous), error per entry <= 5.5K 2^-55 max_k|a_ik| max_k|b_kj|.
 // Asynchronous on st.
 pw_status pw_dgemm_oz(pw_oz_ws *w, int m, int n, int k, const double *A, int lda, const double *B, int ldb,
                       double *C, int ldc, cudaStream_t st);
