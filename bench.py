@@ -625,18 +625,30 @@ def run_gpu(args):
                       "note": f"pw_eigsolve (tol 0, {args.e2e_steps} full steps) from a pinned host start "
                               "block: upload, H X0, initial Rayleigh-Ritz, the steps, FP64 polish, "
                               "eigenvalues back to the host"}
+
+    def section(key, fn):
+        # a rank-0 part of the line after the timed steps: a failure is
+        # recorded under its key instead of losing the measured line
+        try:
+            out[key] = fn()
+        except Exception as exc:
+            out[key] = {"error": f"{type(exc).__name__}: {exc}"}
+
+    def cpu_baseline():
+        sec, note, parts = oracle_sample(wl)
+        return {"value": 1.0 / sec, "unit": "iters/s", "cores": cpu_cores(),
+                "kind": "oracle", "sample": note, "extrapolated": True, "pieces": parts,
+                "measured_s_per_step": sum(p["measured_s"] for p in parts.values())}
+
     if rank == 0 and not args.no_accuracy and args.precision == "mixed":
-        out["accuracy"] = accuracy_run(pw, torch, cell, nb, x0, torch.cuda.synchronize)
+        section("accuracy", lambda: accuracy_run(pw, torch, cell, nb, x0, torch.cuda.synchronize))
     if rank == 0 and not args.no_serve:
-        out["serving"] = serve_sweep(args)
+        section("serving", lambda: serve_sweep(args))
     if rank == 0 and not args.no_si1728 and args.precision == "mixed":
         cell.close()
-        out["si1728"] = si1728_step(pw, torch, args)
+        section("si1728", lambda: si1728_step(pw, torch, args))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sec, note, parts = oracle_sample(wl)
-        out["cpu_baseline"] = {"value": 1.0 / sec, "unit": "iters/s", "cores": cpu_cores(),
-                               "kind": "oracle", "sample": note, "extrapolated": True, "pieces": parts,
-                               "measured_s_per_step": sum(p["measured_s"] for p in parts.values())}
+        section("cpu_baseline", cpu_baseline)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
