@@ -255,7 +255,7 @@ void run_one(Server &sv, int i, int device) {
       std::lock_guard<std::mutex> lk(sv.plan_mu);
       auto it = sv.plans.find(g);
       if (it == sv.plans.end()) {
-        sv.plans[g] = pw_fft_plan{-1, 0, 0};
+        sv.plans[g] = pw_fft_plan{-1, 0, 0, 0};
         tune = true;
       } else if (it->second.L >= 0) {
         p = it->second;
