@@ -12,6 +12,11 @@ Everything is float64 / complex128, written as the plain definition with numpy
 and scipy library primitives (FFT, matmul, Cholesky, Hermitian eigensolver)
 as single steps, and no blocking or reordering beyond the definition.
 
+Every function here is pinned to something other than itself in
+tests/test_oracle_pins.py (brute force, closed forms, invariants, textbook
+special cases); tests/test_oracle_mutants.py plants mistakes in each
+function's source and checks that the pins fail.
+
 The problem (Sec. II-A, Eq. 1): H X = X Lambda for the lowest nb eigenpairs of
 the plane-wave Hamiltonian, in Hartree atomic units,
 
