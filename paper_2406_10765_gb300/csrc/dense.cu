@@ -110,6 +110,7 @@ constexpr int DC_TC_MIN_HALF = 512;   // merge levels with larger halves: produc
 // Li (b x b, ld CB) = L11^-1 as well, for the row solves of the panel below
 __global__ void k_potf2(double2 *A, int n, int j0, int b, double *piv, int *flag, double2 *Li) {
   __shared__ double2 L[CB][CB + 1];
+  __shared__ double s_inv;
   __shared__ int bad;
   const int t = threadIdx.x;
   for (int e = t; e < b * b; e += blockDim.x) {
@@ -119,14 +120,18 @@ __global__ void k_potf2(double2 *A, int n, int j0, int b, double *piv, int *flag
   if (t == 0) bad = 0;
   __syncthreads();
   for (int c = 0; c < b; ++c) {
+    // the pivot's square root and reciprocal once, by one thread (FP64
+    // division runs on the narrow FP64 pipe of this part)
     if (t == 0) {
       const double p = L[c][c].x;
       piv[j0 + c] = p;
-      if (!(p > 0.0)) { bad = 1; L[c][c] = make_double2(1.0, 0.0); }
-      else L[c][c] = make_double2(sqrt(p), 0.0);
+      const double d = p > 0.0 ? sqrt(p) : 1.0;
+      if (!(p > 0.0)) bad = 1;
+      L[c][c] = make_double2(d, 0.0);
+      s_inv = 1.0 / d;
     }
     __syncthreads();
-    const double inv = 1.0 / L[c][c].x;
+    const double inv = s_inv;
     for (int i = c + 1 + t; i < b; i += blockDim.x) { L[i][c].x *= inv; L[i][c].y *= inv; }
     __syncthreads();
     for (int e = t; e < b * b; e += blockDim.x) {
@@ -149,14 +154,16 @@ __global__ void k_potf2(double2 *A, int n, int j0, int b, double *piv, int *flag
   // removes L_il (i > l) from the rows below; only the original L entries are
   // read, and each step's updates are spread over the whole block
   __shared__ double2 X[CB][CB + 1];
+  __shared__ double s_dinv[CB];
   for (int e = t; e < b * b; e += blockDim.x) {
     const int i = e % b, j = e / b;
     X[i][j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   }
+  if (t < b) s_dinv[t] = 1.0 / L[t][t].x;
   __syncthreads();
   for (int l = 0; l < b; ++l) {
     if (t <= l) {
-      const double inv = 1.0 / L[l][l].x;
+      const double inv = s_dinv[l];
       X[l][t].x *= inv;
       X[l][t].y *= inv;
     }
