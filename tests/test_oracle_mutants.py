@@ -140,6 +140,8 @@ MUTANTS = [
      ["test_lobpcg_step_direction_update"]),
     ("step_retry_drops_w", "lobpcg_step", "k = nb + int(act.sum())", "k = nb",
      ["test_lobpcg_step_drops_p_on_breakdown"]),
+    ("dense_eigs_real_part", "dense_eigs", "return sla.eigh(H)\n", "return sla.eigh(H.real)\n",
+     ["test_dense_eigs_against_cyclic_jacobi"]),
     ("dense_eigs_off_by_one", "dense_eigs", "subset_by_index=[0, nb - 1]", "subset_by_index=[1, nb]",
      ["test_lobpcg_vs_dense_and_bounds"]),
     ("convergence_on_smallest_residual", "eigsolve", "if rn.max() <= tol:", "if rn.min() <= tol:",
