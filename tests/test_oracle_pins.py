@@ -336,6 +336,23 @@ def test_lobpcg_vs_dense_and_bounds():
     assert np.abs(X.conj().T @ X - np.eye(nb)).max() < 1e-12
 
 
+def test_kato_temple_bound_on_a_loose_solve():
+    # Ritz pairs stopped at max residual 1e-3: each Ritz value is within
+    # ||r||^2 / delta of its eigenvalue (Kato-Temple; delta = distance to the
+    # rest of the spectrum), far inside the first-order Weyl bound ||r||
+    cell, _ = _cell("C", 1, 8.0, seed=2)
+    nb = 18
+    w = np.linalg.eigvalsh(O.dense_H(cell))
+    lam, X, it, rn = O.eigsolve(cell, synth.draw_x0(2, 8, cell.npw, nb), tol=1e-3, maxit=300)
+    assert rn.max() <= 1e-3 and rn.max() > 1e-5
+    for i in range(nb):
+        j = np.argmin(np.abs(w - lam[i]))
+        assert j == i
+        delta = np.abs(np.delete(w, j) - lam[i]).min()
+        assert abs(lam[i] - w[j]) <= rn[i] ** 2 / delta
+        assert lam[i] >= w[j] - 1e-12          # Ritz values bound from above
+
+
 def test_lobpcg_seed_independence():
     cell, _ = _cell("C", 1, 8.0, seed=1)
     a = O.eigsolve(cell, synth.draw_x0(11, 8, cell.npw, 12), tol=1e-9)[0]
